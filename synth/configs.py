@@ -1,0 +1,124 @@
+"""Problem descriptions for the synthetic workloads.
+
+A problem is a plain dict of input data:
+
+    {"regions":  [{"eps": float, "kappa": float}, ...],
+     "surfaces": [{"verts": f64[nv,3], "tris": i32[nt,3], "inner": int, "outer": int}, ...],
+     "charges":  {"xyz": f64[nc,3], "q": f64[nc], "region": int}}
+
+Triangles are wound counter-clockwise seen from the surface's outer region.
+Nothing here evaluates the method; the oracle and the CUDA library both read
+these dicts.
+"""
+from __future__ import annotations
+
+import functools
+
+import numpy as np
+
+from .meshes import icosphere, octasphere
+from .molecule import gaussian_surface, synthetic_atoms
+
+EPS_IN, EPS_OUT, KAPPA = 4.0, 80.0, 0.125
+
+
+def sphere_problem(level=4, radius=4.0, charges="both", eps_in=EPS_IN, eps_out=EPS_OUT,
+                   kappa=KAPPA, mesh="octa"):
+    """Kirkwood sphere: one surface, charges at the centre and/or 2 A off-centre.
+
+    level 4 octasphere = 2,048 panels (level 3: 512, level 5: 8,192).
+    """
+    v, t = (octasphere if mesh == "octa" else icosphere)(level, radius)
+    xyz = {"centre": [[0.0, 0.0, 0.0]], "off": [[2.0, 0.0, 0.0]],
+           "both": [[0.0, 0.0, 0.0], [2.0, 0.0, 0.0]]}[charges]
+    xyz = np.array(xyz, dtype=np.float64)
+    return {
+        "regions": [{"eps": eps_in, "kappa": 0.0}, {"eps": eps_out, "kappa": kappa}],
+        "surfaces": [{"verts": v, "tris": t, "inner": 0, "outer": 1}],
+        "charges": {"xyz": xyz, "q": np.ones(xyz.shape[0]), "region": 0},
+    }
+
+
+def layered_sphere_problem(level=3, a=4.0, b=6.0, stern_level=None, eps=(4.0, 80.0, 80.0),
+                           kappa=(0.0, 0.0, 0.125), charges="both"):
+    """Sphere with a concentric Stern layer: protein | Stern (r<b) | solvent."""
+    v1, t1 = octasphere(level, a)
+    v2, t2 = octasphere(stern_level if stern_level is not None else level, b)
+    xyz = {"centre": [[0.0, 0.0, 0.0]], "off": [[2.0, 0.0, 0.0]],
+           "both": [[0.0, 0.0, 0.0], [2.0, 0.0, 0.0]]}[charges]
+    xyz = np.array(xyz, dtype=np.float64)
+    return {
+        "regions": [{"eps": eps[i], "kappa": kappa[i]} for i in range(3)],
+        "surfaces": [{"verts": v1, "tris": t1, "inner": 0, "outer": 1},
+                     {"verts": v2, "tris": t2, "inner": 1, "outer": 2}],
+        "charges": {"xyz": xyz, "q": np.ones(xyz.shape[0]), "region": 0},
+    }
+
+
+def cavity_sphere_problem(level=3, eps_cav=80.0):
+    """Cavity r < 1.5 | protein shell to 4 | Stern to 6 | solvent, charge at 2.5 A."""
+    vc, tc = octasphere(max(level - 1, 1), 1.5)
+    v1, t1 = octasphere(level, 4.0)
+    v2, t2 = octasphere(level, 6.0)
+    return {
+        "regions": [{"eps": eps_cav, "kappa": 0.0}, {"eps": 4.0, "kappa": 0.0},
+                    {"eps": 80.0, "kappa": 0.0}, {"eps": 80.0, "kappa": 0.125}],
+        "surfaces": [{"verts": vc, "tris": tc, "inner": 0, "outer": 1},
+                     {"verts": v1, "tris": t1, "inner": 1, "outer": 2},
+                     {"verts": v2, "tris": t2, "inner": 2, "outer": 3}],
+        "charges": {"xyz": np.array([[2.5, 0.0, 0.0]]), "q": np.ones(1), "region": 1},
+    }
+
+
+# Grid spacings (A) of the marching-tetrahedra mesher that give the stated
+# panel counts for the seeded molecules below.
+PROTEIN_SPACING = 1.65      # ~40k panels for the 2,000-atom seed-2 molecule
+STERN_SPACING = 1.02        # ~60k panels for its +2 A Stern surface
+
+
+@functools.lru_cache(maxsize=8)
+def protein_atoms(n_atoms=2000, seed=2, cavities=False):
+    radius = 20.0 * (n_atoms / 2000.0) ** (1.0 / 3.0)
+    exclude = ()
+    if cavities:
+        exclude = (((7.0, 0.0, 0.0), 3.0 + 2.0 + 1.4), ((-7.0, 0.0, 0.0), 3.0 + 2.0 + 1.4))
+    return synthetic_atoms(n_atoms, radius, seed, exclude=exclude)
+
+
+def protein_problem(n_atoms=2000, seed=2, spacing=PROTEIN_SPACING):
+    """Synthetic globular protein, single dielectric interface (~40k panels)."""
+    at = protein_atoms(n_atoms, seed)
+    v, t = gaussian_surface(at["xyz"], at["radius"], spacing)
+    return {
+        "regions": [{"eps": EPS_IN, "kappa": 0.0}, {"eps": EPS_OUT, "kappa": KAPPA}],
+        "surfaces": [{"verts": v, "tris": t, "inner": 0, "outer": 1}],
+        "charges": {"xyz": at["xyz"].copy(), "q": at["q"].copy(), "region": 0},
+    }
+
+
+def multisurface_problem(n_atoms=2000, seed=3, spacing=PROTEIN_SPACING,
+                         stern_spacing=STERN_SPACING, cavity_level=3):
+    """Protein SES + Stern surface (+2 A) + two 3 A solvent-filled cavities.
+
+    Regions: 0 cav1, 1 cav2, 2 protein (charged), 3 Stern (eps_out, kappa 0),
+    4 solvent (eps_out, kappa).  Surfaces: C1, C2, SES, Stern.
+    """
+    at = protein_atoms(n_atoms, seed, cavities=True)
+    vs, ts = gaussian_surface(at["xyz"], at["radius"], spacing)
+    vt, tt = gaussian_surface(at["xyz"], at["radius"], stern_spacing, radius_offset=2.0)
+    c1v, c1t = icosphere(cavity_level, 3.0, (7.0, 0.0, 0.0))
+    c2v, c2t = icosphere(cavity_level, 3.0, (-7.0, 0.0, 0.0))
+    return {
+        "regions": [{"eps": EPS_OUT, "kappa": 0.0}, {"eps": EPS_OUT, "kappa": 0.0},
+                    {"eps": EPS_IN, "kappa": 0.0}, {"eps": EPS_OUT, "kappa": 0.0},
+                    {"eps": EPS_OUT, "kappa": KAPPA}],
+        "surfaces": [{"verts": c1v, "tris": c1t, "inner": 0, "outer": 2},
+                     {"verts": c2v, "tris": c2t, "inner": 1, "outer": 2},
+                     {"verts": vs, "tris": ts, "inner": 2, "outer": 3},
+                     {"verts": vt, "tris": tt, "inner": 3, "outer": 4}],
+        "charges": {"xyz": at["xyz"].copy(), "q": at["q"].copy(), "region": 2},
+    }
+
+
+def panel_count(problem):
+    return sum(int(np.asarray(s["tris"]).shape[0]) for s in problem["surfaces"])
