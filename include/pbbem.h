@@ -1,0 +1,166 @@
+/* pbbem: treecode-accelerated boundary-element Poisson-Boltzmann solver for B300 (sm_103a).
+ *
+ * The library computes the electrostatic solvation energy of molecules in
+ * implicit solvent with the boundary-integral formulation of Cooper, Bardhan &
+ * Barba (arXiv:1309.4018): flat triangular panels with constant phi and
+ * dphi/dn, centroid collocation (Sec. 2.2, Eqs. nBEM_disc, matrix, matel),
+ * several interacting surfaces (molecular surface, Stern layer,
+ * solvent-filled cavities; Sec. 2.2 "Multi-surface problems"), a
+ * Cartesian-Taylor treecode for every matrix-vector product (Sec. 2.3, Eqs.
+ * nbody, taylor, multexp, MAC) and a Krylov solver (Sec. 2.3, last
+ * paragraph); the reaction potential and energies follow Eqs. reac_integral,
+ * solv, bind_energy and total_energy.
+ *
+ * Units: Angstrom, elementary charge, relative permittivity, kappa in 1/A,
+ * energies in kJ/mol.
+ *
+ * Conventions shared by every entry point:
+ *   - All functions return PB_OK (0) or one of the PB_E* codes below; the
+ *     message of the last failure is pb_last_error(ctx).
+ *   - Host input arrays are copied during the call; the library never keeps a
+ *     caller pointer.  Output arrays are caller-allocated and written in full.
+ *   - All device memory is owned by the library and released by the matching
+ *     *_destroy call.
+ *   - A context serves one host thread at a time; its work runs on one CUDA
+ *     stream (pb_ctx_stream).
+ *   - Triangles are wound counter-clockwise seen from the surface's outer
+ *     region, so the normal (v1 - v0) x (v2 - v0) points from the inner
+ *     region to the outer region.
+ *   - The unknown vector of a problem has 2 N entries, N the total panel
+ *     count: surface by surface, phi on the panels of that surface followed
+ *     by dphi/dn taken on its inner side.  The two row blocks of a surface
+ *     are the equation of its inner region, then that of its outer region.
+ */
+#ifndef PBBEM_H
+#define PBBEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PB_OK 0
+#define PB_EINVAL 1      /* bad argument or malformed input (message says which) */
+#define PB_ENOMEM 2      /* device or host allocation failed */
+#define PB_ECUDA 3       /* a CUDA call failed */
+#define PB_ENOCONV 4     /* GMRES reached max_iter; the partial result is still written */
+#define PB_ETIMEOUT 5    /* a bounded device-side wait gave up */
+#define PB_ENOTSETUP 6   /* pb_setup has not been called since the last input change */
+
+#define PB_FP64 0        /* every treecode step in FP64 */
+#define PB_MIXED 1       /* P2P, P2M, M2M, M2P in FP32 (compensated sums); Krylov, near field, energy FP64 */
+
+typedef struct pb_ctx pb_ctx;
+typedef struct pb_problem pb_problem;
+
+/* Parameters (Tables 1, 3, 4 and 6).  A zero field takes the default in brackets. */
+typedef struct {
+    int K;             /* Gauss points per panel in the regular case: 1, 3, 7 or 19 [3] */
+    int K_fine;        /* Gauss points per panel in the near-singular region: 1, 3, 7 or 19 [19] */
+    int N_k;           /* Gauss points per triangle side, semi-analytical self integral, 1..32 [5] */
+    double thres;      /* near-singular region |x - c_j| < thres * L_j, L_j = sqrt(2 A_j) [2.0] */
+    int P;             /* Taylor expansion order, 0..12 [6] */
+    double theta;      /* MAC parameter (Eq. MAC); negative selects direct summation [0.5] */
+    int ncrit;         /* a box with >= ncrit sources is split [300] */
+    double gmres_tol;  /* relative residual tolerance [1e-4] */
+    int restart;       /* GMRES restart length, 1..200 [50] */
+    int max_iter;      /* total GMRES iteration cap [1000] */
+    int precision;     /* PB_FP64 or PB_MIXED [PB_FP64] */
+} pb_params;
+
+typedef struct {
+    double dG_solv;        /* solvation energy, kJ/mol (Eq. solv) */
+    double residual;       /* final true relative residual ||b - A x|| / ||b|| */
+    int iterations;        /* GMRES iterations */
+    int converged;         /* 1 if residual < gmres_tol */
+    int matvecs;           /* treecode evaluations during the solve */
+    int pad_;
+    double setup_ms;       /* time of the last pb_setup (device, CUDA events) */
+    double solve_ms;       /* time of this solve (device, CUDA events) */
+    int64_t p2p_pairs;     /* direct (target, source point) pairs per treecode evaluation */
+    int64_t m2p_pairs;     /* (target, box, kernel) expansion evaluations per treecode evaluation */
+    int64_t near_pairs;    /* near-singular (target, panel) corrections */
+    int64_t near_excluded; /* near-singular panels left uncorrected (a point fell in an accepted box) */
+} pb_result;
+
+/* Context: one CUDA device, one stream. */
+int pb_ctx_create(int device, pb_ctx **out);
+void pb_ctx_destroy(pb_ctx *ctx);
+const char *pb_last_error(pb_ctx *ctx);
+/* The cudaStream_t all work of this context is issued on (for event timing). */
+void *pb_ctx_stream(pb_ctx *ctx);
+
+/* Problem: regions, surfaces and charges (Sec. 2.1, Eq. pde; Sec. 2.2). */
+int pb_problem_create(pb_ctx *ctx, pb_problem **out);
+void pb_problem_destroy(pb_problem *pb);
+/* A region with permittivity eps > 0 and inverse Debye length kappa >= 0
+ * (kappa = 0: Poisson/Laplace kernel; > 0: linearised PB/Yukawa kernel).
+ * Regions are numbered 0, 1, ... in call order. */
+int pb_add_region(pb_problem *pb, double eps, double kappa, int *region_id);
+/* A closed triangle mesh separating region `inner` from region `outer`.
+ * verts: nv x 3 doubles; tris: nt x 3 vertex indices.  PB_EINVAL on an
+ * index out of range or an unknown region; pb_setup fails with PB_EINVAL on
+ * a zero-area triangle. */
+int pb_add_surface(pb_problem *pb, const double *verts, int64_t nv, const int32_t *tris,
+                   int64_t nt, int inner, int outer, int *surface_id);
+/* Point charges (Eq. pde) inside region `region` (which must have kappa = 0). */
+int pb_set_charges(pb_problem *pb, const double *xyz, const double *q, int64_t nc, int region);
+
+/* Geometry, octrees, interaction lists, near-singular corrections and the
+ * right-hand side (Sec. 2.3: built once, reused by every iteration). */
+int pb_setup(pb_problem *pb, const pb_params *params);
+int64_t pb_num_unknowns(pb_problem *pb);  /* 2 N, or -1 before pb_setup */
+
+/* y = A x for the assembled operator (one treecode evaluation, Sec. 2.3
+ * "Treecode-accelerated BEM").  x, y: 2 N doubles; on the host if
+ * device_ptrs == 0, else device pointers of this context's device (the call
+ * is ordered on the context stream and returns when y is complete). */
+int pb_apply_operator(pb_problem *pb, const double *x, double *y, int device_ptrs);
+/* b of Eq. matrix (2 N host doubles). */
+int pb_rhs(pb_problem *pb, double *b);
+/* Solve A x = b by restarted GMRES on the device, then dG (Eqs. reac_integral, solv).
+ * x0: optional initial guess (2 N host doubles) or NULL for zero. */
+int pb_solve(pb_problem *pb, const double *x0, pb_result *out);
+/* The solution of the last pb_solve (2 N host doubles). */
+int pb_get_solution(pb_problem *pb, double *x);
+/* Reaction potential at the charges (Eq. reac_integral) for a given unknown
+ * vector x (host, 2 N); phi_reac: nc doubles in the 1/(4 pi) units of the kernels. */
+int pb_reaction_potential(pb_problem *pb, const double *x, double *phi_reac);
+/* Coulomb energy 1/2 C sum_{i != j} q_i q_j / (eps_R r_ij) of the charges, kJ/mol
+ * (the Coulomb term of Eq. total_energy). */
+int pb_coulomb_energy(pb_problem *pb, double *out);
+
+/* Introspection of the integer work (Sec. 2.3, Eq. MAC), for bit-exact checks.
+ * Octree over the Gauss points of surface `surface` (point j*K + k is Gauss
+ * point k of panel j).  Nodes are numbered breadth first, children in octant
+ * order.  Sizes first, then arrays of those sizes. */
+typedef struct {
+    int64_t n_points;
+    int32_t n_nodes;
+    int32_t n_leaves;
+    double corner[3];
+    double side;
+} pb_tree_info;
+int pb_tree_info_get(pb_problem *pb, int surface, pb_tree_info *out);
+/* keys: n_points sorted Morton keys; perm: sorted position -> point index;
+ * node_level, node_start, node_count, node_first_child (-1 for a leaf),
+ * node_nchild: n_nodes each.  Any pointer may be NULL. */
+int pb_tree_export(pb_problem *pb, int surface, uint64_t *keys, int32_t *perm,
+                   int32_t *node_level, int64_t *node_start, int64_t *node_count,
+                   int32_t *node_first_child, int32_t *node_nchild);
+/* Interaction lists of the targets of `target_surface` (-1: the charges) against
+ * the octree of `source_surface`, indexed by the targets' input order.
+ * counts[0..5]: total M2P entries, P2P entries, near entries, excluded near
+ * panels, targets whose own panel had a point in an accepted box, targets.
+ * Arrays (any may be NULL): m2p_ptr/p2p_ptr/near_ptr (targets + 1 each),
+ * m2p_nodes, p2p_nodes (node ids, depth-first pre-order per target),
+ * near_panels (ascending per target).  PB_EINVAL if the pair never interacts. */
+int pb_lists_export(pb_problem *pb, int target_surface, int source_surface, int64_t *counts,
+                    int64_t *m2p_ptr, int32_t *m2p_nodes, int64_t *p2p_ptr,
+                    int32_t *p2p_nodes, int64_t *near_ptr, int32_t *near_panels);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PBBEM_H */

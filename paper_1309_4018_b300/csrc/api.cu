@@ -1,0 +1,678 @@
+// C-ABI of the pbbem library (include/pbbem.h): problem assembly, setup,
+// treecode operator application, device GMRES solve and energies.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "geometry.cuh"
+#include "gmres.cuh"
+#include "model.cuh"
+#include "tree.cuh"
+#include "treecode.cuh"
+
+using namespace pb;
+
+struct pb_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::string err;
+};
+
+namespace {
+
+struct SurfIn {
+    std::vector<double> v;
+    std::vector<int32_t> t;
+    int inner, outer;
+};
+
+// One (pair, kernel) contribution cK * K + cV * V to a row block or to the
+// reaction potential.
+struct Term {
+    int pair, kidx;
+    double cK, cV;
+};
+
+}  // namespace
+
+struct pb_problem {
+    pb_ctx *ctx = nullptr;
+    std::vector<Region> regions;
+    std::vector<SurfIn> sin;
+    std::vector<double> cxyz, cq;
+    int cregion = -1;
+    bool is_setup = false;
+    Params prm;
+    // device data
+    std::vector<SurfDev> S;
+    std::vector<Tree> T;
+    std::vector<Targets> G;               // one per surface, then the charges
+    std::vector<Pair> pairs;              // surface-target pairs
+    std::vector<Pair> cpairs;             // charge-target pairs
+    std::vector<std::vector<Term>> rows;  // per (surface, side)
+    std::vector<Term> reac;
+    std::vector<bool> need_far;           // per tree: some pair uses its moments
+    std::vector<int64_t> off;             // panel offsets
+    int64_t N = 0;
+    DevBuf<double> b, x, y, r, xin, yout;
+    DevBuf<double> cq_d, cxyz_d, phi_reac, energy;
+    Gmres gm;
+    double setup_ms = 0.0;
+    bool have_solution = false;
+};
+
+namespace {
+
+int fail_ctx(pb_ctx *c, const Error &e) {
+    if (c) c->err = e.msg;
+    return e.code;
+}
+
+template <typename F>
+int guard(pb_ctx *c, F &&f) {
+    try {
+        f();
+        if (c) c->err.clear();
+        return PB_OK;
+    } catch (const Error &e) {
+        return fail_ctx(c, e);
+    } catch (const std::bad_alloc &) {
+        return fail_ctx(c, Error{PB_ENOMEM, "host allocation failed"});
+    } catch (const std::exception &e) {
+        return fail_ctx(c, Error{PB_EINVAL, e.what()});
+    }
+}
+
+void set_device(pb_ctx *c) { PB_CUDA_TRY(cudaSetDevice(c->device)); }
+
+Params resolve(const pb_params *p) {
+    Params r;
+    if (p) {
+        if (p->K) r.K = p->K;
+        if (p->K_fine) r.K_fine = p->K_fine;
+        if (p->N_k) r.N_k = p->N_k;
+        if (p->thres != 0.0) r.thres = p->thres;
+        if (p->P) r.P = p->P;
+        if (p->theta != 0.0) r.theta = p->theta;
+        if (p->ncrit) r.ncrit = p->ncrit;
+        if (p->gmres_tol != 0.0) r.tol = p->gmres_tol;
+        if (p->restart) r.restart = p->restart;
+        if (p->max_iter) r.max_iter = p->max_iter;
+        r.precision = p->precision;
+    }
+    if (!valid_rule(r.K)) fail(PB_EINVAL, "K must be 1, 3, 7 or 19");
+    if (!valid_rule(r.K_fine)) fail(PB_EINVAL, "K_fine must be 1, 3, 7 or 19");
+    if (r.N_k < 1 || r.N_k > 32) fail(PB_EINVAL, "N_k must be in 1..32");
+    if (r.P < 0 || r.P > kMaxP) fail(PB_EINVAL, "P must be in 0..12");
+    if (r.ncrit < 1) fail(PB_EINVAL, "ncrit must be >= 1");
+    if (r.restart < 1 || r.restart > 200) fail(PB_EINVAL, "restart must be in 1..200");
+    if (r.max_iter < 1) fail(PB_EINVAL, "max_iter must be >= 1");
+    if (!(r.tol > 0.0)) fail(PB_EINVAL, "gmres_tol must be > 0");
+    if (!(r.thres >= 0.0)) fail(PB_EINVAL, "thres must be >= 0");
+    if (!std::isfinite(r.theta)) fail(PB_EINVAL, "theta must be finite");
+    if (r.precision != PB_FP64 && r.precision != PB_MIXED) fail(PB_EINVAL, "unknown precision");
+    return r;
+}
+
+int find_pair(std::vector<Pair> &v, int tgt, int tree) {
+    for (size_t i = 0; i < v.size(); ++i)
+        if (v[i].tgt == tgt && v[i].tree == tree) return (int)i;
+    v.emplace_back();
+    v.back().tgt = tgt;
+    v.back().tree = tree;
+    return (int)v.size() - 1;
+}
+
+int kernel_slot(Pair &p, double kappa) {
+    for (size_t i = 0; i < p.kappas.size(); ++i)
+        if (p.kappas[i] == kappa) return (int)i;
+    p.kappas.push_back(kappa);
+    return (int)p.kappas.size() - 1;
+}
+
+void setup_problem(pb_problem *pb) {
+    pb_ctx *c = pb->ctx;
+    cudaStream_t s = c->stream;
+    const Params &prm = pb->prm;
+    const int ns = (int)pb->sin.size();
+    if (ns == 0) fail(PB_EINVAL, "no surface");
+    for (const auto &si : pb->sin)
+        if (si.inner < 0 || si.inner >= (int)pb->regions.size() || si.outer < 0 ||
+            si.outer >= (int)pb->regions.size() || si.inner == si.outer)
+            fail(PB_EINVAL, "surface references an unknown region");
+    PB_CUDA_TRY(cudaEventRecord(c->ev0, s));
+    upload_rules();
+    upload_term_tables();
+    pb->S.clear(); pb->T.clear(); pb->G.clear(); pb->pairs.clear(); pb->cpairs.clear();
+    pb->S.resize(ns);
+    pb->T.resize(ns);
+    pb->off.assign(ns + 1, 0);
+    for (int t = 0; t < ns; ++t) {
+        SurfDev &S = pb->S[t];
+        const SurfIn &si = pb->sin[t];
+        S.n = (int64_t)si.t.size() / 3;
+        S.nv = (int64_t)si.v.size() / 3;
+        S.inner = si.inner;
+        S.outer = si.outer;
+        S.off = pb->off[t];
+        pb->off[t + 1] = pb->off[t] + S.n;
+        S.verts.upload(si.v.data(), si.v.size(), s);
+        S.tris.upload(si.t.data(), si.t.size(), s);
+        surface_geometry(S, prm.K, s);
+        build_tree(pb->T[t], S, prm.K, prm.ncrit, s);
+    }
+    pb->N = pb->off[ns];
+    pb->G.resize(ns + 1);
+    for (int t = 0; t < ns; ++t) build_targets(pb->G[t], pb->S[t].cen.p, pb->S[t].n, t, s);
+    const int64_t nc = (int64_t)pb->cq.size();
+    pb->cq_d.upload(pb->cq.data(), nc, s);
+    pb->cxyz_d.upload(pb->cxyz.data(), 3 * nc, s);
+    build_targets(pb->G[ns], pb->cxyz_d.p, nc, -1, s);
+    // block structure (multi-surface rule): row (s, R) gets sigma (K - c V) of every t in dR
+    pb->rows.assign(2 * ns, {});
+    auto eps = [&](int R) { return pb->regions[R].eps; };
+    for (int sf = 0; sf < ns; ++sf) {
+        const int Rs[2] = {pb->S[sf].inner, pb->S[sf].outer};
+        for (int side = 0; side < 2; ++side) {
+            const int R = Rs[side];
+            for (int t = 0; t < ns; ++t) {
+                const bool in = pb->S[t].inner == R, out = pb->S[t].outer == R;
+                if (!in && !out) continue;
+                const double sigma = in ? 1.0 : -1.0;
+                const double cc = in ? 1.0 : eps(pb->S[t].inner) / eps(R);
+                const int pi = find_pair(pb->pairs, sf, t);
+                const int ki = kernel_slot(pb->pairs[pi], pb->regions[R].kappa);
+                pb->rows[2 * sf + side].push_back(Term{pi, ki, sigma, -sigma * cc});
+            }
+            if (pb->rows[2 * sf + side].size() > 8) fail(PB_EINVAL, "a region is bounded by more than 8 surfaces");
+        }
+    }
+    pb->reac.clear();
+    if (nc > 0) {
+        const int Rc = pb->cregion;
+        for (int t = 0; t < ns; ++t) {
+            const bool in = pb->S[t].inner == Rc, out = pb->S[t].outer == Rc;
+            if (!in && !out) continue;
+            const double sigma = in ? 1.0 : -1.0;
+            const double cc = in ? 1.0 : eps(pb->S[t].inner) / eps(Rc);
+            const int pi = find_pair(pb->cpairs, ns, t);
+            const int ki = kernel_slot(pb->cpairs[pi], pb->regions[Rc].kappa);
+            pb->reac.push_back(Term{pi, ki, -sigma, sigma * cc});
+        }
+        if (pb->reac.size() > 8) fail(PB_EINVAL, "the charged region is bounded by more than 8 surfaces");
+    }
+    pb->need_far.assign(ns, false);
+    auto prepare = [&](Pair &P, bool charges) {
+        const Targets &G = pb->G[P.tgt];
+        const Tree &Tr = pb->T[P.tree];
+        const SurfDev &src = pb->S[P.tree];
+        const bool use_self = !charges && P.tgt == P.tree;
+        build_lists(P, G, Tr, src, prm, use_self, s);
+        if (P.n_m2p > 0) pb->need_far[P.tree] = true;
+        const size_t nk = P.kappas.size();
+        P.VK.resize(nk); P.dV.resize(nk); P.dK.resize(nk); P.selfV.resize(nk);
+        for (size_t k = 0; k < nk; ++k) {
+            P.VK[k].alloc(2 * std::max<int64_t>(1, G.n));
+            P.dV[k].alloc(std::max<int64_t>(1, P.n_near));
+            P.dK[k].alloc(std::max<int64_t>(1, P.n_near));
+            near_values(P, G, src, prm.K, prm.K_fine, P.kappas[k], P.dV[k].p, P.dK[k].p, s);
+            if (use_self) {
+                P.selfV[k].alloc(src.n);
+                self_integrals(src, prm.N_k, P.kappas[k], P.selfV[k].p, s);
+            }
+        }
+    };
+    for (auto &P : pb->pairs) prepare(P, false);
+    for (auto &P : pb->cpairs) prepare(P, true);
+    // right-hand side
+    pb->b.alloc(2 * pb->N);
+    pb->b.zero(s);
+    if (nc > 0) {
+        const Region &Rg = pb->regions[pb->cregion];
+        for (int sf = 0; sf < ns; ++sf) {
+            const int Rs[2] = {pb->S[sf].inner, pb->S[sf].outer};
+            for (int side = 0; side < 2; ++side)
+                if (Rs[side] == pb->cregion)
+                    rhs_rows(pb->S[sf], nc, pb->cq_d.p, pb->cxyz_d.p, Rg.kappa, Rg.eps,
+                             pb->b.p + 2 * pb->off[sf] + side * pb->S[sf].n, s);
+        }
+    }
+    pb->x.alloc(2 * pb->N);
+    pb->x.zero(s);
+    pb->y.alloc(2 * pb->N);
+    pb->r.alloc(2 * pb->N);
+    pb->phi_reac.alloc(std::max<int64_t>(1, nc));
+    pb->energy.alloc(1);
+    pb->gm.init(2 * pb->N, prm.restart, s);
+    PB_CUDA_TRY(cudaEventRecord(c->ev1, s));
+    PB_CUDA_TRY(cudaEventSynchronize(c->ev1));
+    float ms = 0.f;
+    PB_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    pb->setup_ms = ms;
+    pb->is_setup = true;
+    pb->have_solution = false;
+}
+
+// y = A x, both device pointers of 2N doubles.
+void apply_operator(pb_problem *pb, const double *xd, double *yd) {
+    cudaStream_t s = pb->ctx->stream;
+    const Params &prm = pb->prm;
+    const bool mixed = prm.precision == PB_MIXED;
+    const int ns = (int)pb->S.size();
+    for (int t = 0; t < ns; ++t) {
+        const double *phi = xd + 2 * pb->off[t];
+        const double *dphi = phi + pb->S[t].n;
+        compute_strengths(pb->T[t], pb->S[t], phi, dphi, mixed, s);
+        if (pb->need_far[t]) upward_pass(pb->T[t], prm.P, mixed, s);
+    }
+    for (auto &P : pb->pairs) {
+        const bool use_self = P.tgt == P.tree;
+        const Targets &G = pb->G[P.tgt];
+        const Tree &Tr = pb->T[P.tree];
+        const double *phi = xd + 2 * pb->off[P.tree];
+        const double *dphi = phi + pb->S[P.tree].n;
+        launch_p2p(P, G, Tr, use_self, mixed, s);
+        launch_m2p(P, G, Tr, prm.P, mixed, s);
+        launch_near(P, G, use_self, phi, dphi, s);
+    }
+    for (int sf = 0; sf < ns; ++sf) {
+        for (int side = 0; side < 2; ++side) {
+            CombineRow row{};
+            const auto &terms = pb->rows[2 * sf + side];
+            row.nterm = (int)terms.size();
+            for (int k = 0; k < row.nterm; ++k) {
+                const Pair &P = pb->pairs[terms[k].pair];
+                row.term[k] = CombineTerm{P.VK[terms[k].kidx].p, pb->G[P.tgt].n, terms[k].cK, terms[k].cV};
+            }
+            launch_combine(pb->S[sf].n, pb->G[sf].rank.p, xd + 2 * pb->off[sf], 0.5, row,
+                           yd + 2 * pb->off[sf] + side * pb->S[sf].n, s);
+        }
+    }
+}
+
+// phi_reac at the charges (input order) for the unknowns x (device); then
+// energy = 1/2 C sum_k q_k 4 pi phi_reac (device scalar).
+void reaction(pb_problem *pb, const double *xd) {
+    cudaStream_t s = pb->ctx->stream;
+    const Params &prm = pb->prm;
+    const bool mixed = prm.precision == PB_MIXED;
+    const int ns = (int)pb->S.size();
+    const int64_t nc = (int64_t)pb->cq.size();
+    if (nc == 0) {
+        pb->energy.zero(s);
+        return;
+    }
+    for (int t = 0; t < ns; ++t) {
+        bool used = false;
+        for (auto &P : pb->cpairs) used = used || P.tree == t;
+        if (!used) continue;
+        const double *phi = xd + 2 * pb->off[t];
+        compute_strengths(pb->T[t], pb->S[t], phi, phi + pb->S[t].n, mixed, s);
+        if (pb->need_far[t]) upward_pass(pb->T[t], prm.P, mixed, s);
+    }
+    for (auto &P : pb->cpairs) {
+        const Targets &G = pb->G[P.tgt];
+        const Tree &Tr = pb->T[P.tree];
+        const double *phi = xd + 2 * pb->off[P.tree];
+        launch_p2p(P, G, Tr, false, mixed, s);
+        launch_m2p(P, G, Tr, prm.P, mixed, s);
+        launch_near(P, G, false, phi, phi + pb->S[P.tree].n, s);
+    }
+    CombineRow row{};
+    row.nterm = (int)pb->reac.size();
+    for (int k = 0; k < row.nterm; ++k) {
+        const Pair &P = pb->cpairs[pb->reac[k].pair];
+        row.term[k] = CombineTerm{P.VK[pb->reac[k].kidx].p, nc, pb->reac[k].cK, pb->reac[k].cV};
+    }
+    launch_combine(nc, pb->G[ns].rank.p, nullptr, 0.0, row, pb->phi_reac.p, s);
+    weighted_sum(pb->cq_d.p, pb->phi_reac.p, nc, 0.5 * kKjPerMol * 4.0 * kPi, pb->energy.p, s);
+}
+
+void require_setup(pb_problem *pb) {
+    if (!pb->is_setup) fail(PB_ENOTSETUP, "pb_setup has not been called since the last input change");
+}
+
+void solve(pb_problem *pb, const double *x0, pb_result *out) {
+    require_setup(pb);
+    pb_ctx *c = pb->ctx;
+    cudaStream_t s = c->stream;
+    const Params &prm = pb->prm;
+    const int64_t n2 = 2 * pb->N;
+    Gmres &gm = pb->gm;
+    PB_CUDA_TRY(cudaEventRecord(c->ev0, s));
+    if (x0) PB_CUDA_TRY(cudaMemcpyAsync(pb->x.p, x0, n2 * sizeof(double), cudaMemcpyHostToDevice, s));
+    else pb->x.zero(s);
+    const double bnorm = norm2_device(pb->b.p, n2, gm, s);
+    int iters = 0, matvecs = 0;
+    double rel = 0.0;
+    bool zero_x = x0 == nullptr;
+    if (bnorm == 0.0) {
+        pb->x.zero(s);
+    } else {
+        gm.set_bnorm(bnorm, s);
+        while (true) {
+            if (zero_x) {
+                PB_CUDA_TRY(cudaMemcpyAsync(pb->r.p, pb->b.p, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            } else {
+                apply_operator(pb, pb->x.p, pb->y.p);
+                ++matvecs;
+                axpby(1.0, pb->b.p, -1.0, pb->y.p, pb->r.p, n2, s);
+            }
+            zero_x = false;
+            const double beta = gm.start_cycle(pb->r.p, s);
+            rel = beta / bnorm;
+            if (!(rel >= prm.tol) || iters >= prm.max_iter) break;
+            int k = 0;
+            for (int j = 0; j < gm.m; ++j) {
+                apply_operator(pb, gm.basis(j), gm.w.p);
+                ++matvecs;
+                gm.arnoldi_step(j, s);
+                ++iters;
+                k = j + 1;
+                const double est = gm.residual_estimate(s);
+                if (!(est >= prm.tol) || iters >= prm.max_iter) break;
+            }
+            gm.update_solution(k, pb->x.p, s);
+        }
+    }
+    reaction(pb, pb->x.p);
+    double dG = 0.0;
+    PB_CUDA_TRY(cudaMemcpyAsync(&dG, pb->energy.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PB_CUDA_TRY(cudaEventRecord(c->ev1, s));
+    PB_CUDA_TRY(cudaEventSynchronize(c->ev1));
+    float ms = 0.f;
+    PB_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    pb->have_solution = true;
+    if (out) {
+        std::memset(out, 0, sizeof(*out));
+        out->dG_solv = dG;
+        out->residual = rel;
+        out->iterations = iters;
+        out->converged = rel < prm.tol;
+        out->matvecs = matvecs;
+        out->setup_ms = pb->setup_ms;
+        out->solve_ms = ms;
+        for (auto &P : pb->pairs) {
+            out->p2p_pairs += P.p2p_pairs;
+            out->m2p_pairs += P.n_m2p * (int64_t)P.kappas.size();
+            out->near_pairs += P.n_near;
+            out->near_excluded += P.near_excl;
+        }
+    }
+    if (!(rel < prm.tol)) fail(PB_ENOCONV, "GMRES reached max_iter before the tolerance");
+}
+
+}  // namespace
+
+extern "C" {
+
+int pb_ctx_create(int device, pb_ctx **out) {
+    if (!out) return PB_EINVAL;
+    *out = nullptr;
+    auto c = std::make_unique<pb_ctx>();
+    c->device = device;
+    int rc = guard(nullptr, [&] {
+        int nd = 0;
+        PB_CUDA_TRY(cudaGetDeviceCount(&nd));
+        if (device < 0 || device >= nd) fail(PB_EINVAL, "no such CUDA device");
+        set_device(c.get());
+        PB_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        PB_CUDA_TRY(cudaEventCreate(&c->ev0));
+        PB_CUDA_TRY(cudaEventCreate(&c->ev1));
+    });
+    if (rc != PB_OK) return rc;
+    *out = c.release();
+    return PB_OK;
+}
+
+void pb_ctx_destroy(pb_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char *pb_last_error(pb_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+void *pb_ctx_stream(pb_ctx *c) { return c ? (void *)c->stream : nullptr; }
+
+int pb_problem_create(pb_ctx *c, pb_problem **out) {
+    if (!c || !out) return PB_EINVAL;
+    *out = new pb_problem();
+    (*out)->ctx = c;
+    return PB_OK;
+}
+
+void pb_problem_destroy(pb_problem *pb) {
+    if (!pb) return;
+    cudaSetDevice(pb->ctx->device);
+    cudaStreamSynchronize(pb->ctx->stream);
+    delete pb;
+}
+
+int pb_add_region(pb_problem *pb, double eps, double kappa, int *region_id) {
+    if (!pb) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        if (!(eps > 0.0) || !(kappa >= 0.0) || !std::isfinite(eps) || !std::isfinite(kappa))
+            fail(PB_EINVAL, "region needs eps > 0 and kappa >= 0");
+        pb->regions.push_back(Region{eps, kappa});
+        pb->is_setup = false;
+        if (region_id) *region_id = (int)pb->regions.size() - 1;
+    });
+}
+
+int pb_add_surface(pb_problem *pb, const double *verts, int64_t nv, const int32_t *tris, int64_t nt, int inner,
+                   int outer, int *surface_id) {
+    if (!pb) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        if (!verts || !tris || nv < 3 || nt < 1) fail(PB_EINVAL, "empty surface");
+        if (inner < 0 || outer < 0 || inner >= (int)pb->regions.size() || outer >= (int)pb->regions.size() ||
+            inner == outer)
+            fail(PB_EINVAL, "surface references an unknown region");
+        if (nt > ((int64_t)1 << 29) / 19) fail(PB_EINVAL, "too many triangles");
+        SurfIn si;
+        si.v.assign(verts, verts + 3 * nv);
+        si.t.assign(tris, tris + 3 * nt);
+        for (double v : si.v)
+            if (!std::isfinite(v)) fail(PB_EINVAL, "non-finite vertex coordinate");
+        for (int32_t i : si.t)
+            if (i < 0 || i >= nv) fail(PB_EINVAL, "triangle vertex index out of range");
+        si.inner = inner;
+        si.outer = outer;
+        pb->sin.push_back(std::move(si));
+        pb->is_setup = false;
+        if (surface_id) *surface_id = (int)pb->sin.size() - 1;
+    });
+}
+
+int pb_set_charges(pb_problem *pb, const double *xyz, const double *q, int64_t nc, int region) {
+    if (!pb) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        if (nc < 0 || (nc > 0 && (!xyz || !q))) fail(PB_EINVAL, "bad charge arrays");
+        if (region < 0 || region >= (int)pb->regions.size()) fail(PB_EINVAL, "unknown charge region");
+        if (pb->regions[region].kappa != 0.0) fail(PB_EINVAL, "charges must sit in a kappa = 0 region");
+        pb->cxyz.assign(xyz, xyz + 3 * nc);
+        pb->cq.assign(q, q + nc);
+        for (double v : pb->cxyz)
+            if (!std::isfinite(v)) fail(PB_EINVAL, "non-finite charge position");
+        pb->cregion = region;
+        pb->is_setup = false;
+    });
+}
+
+int pb_setup(pb_problem *pb, const pb_params *params) {
+    if (!pb) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        set_device(pb->ctx);
+        pb->is_setup = false;
+        pb->prm = resolve(params);
+        setup_problem(pb);
+    });
+}
+
+int64_t pb_num_unknowns(pb_problem *pb) { return (pb && pb->is_setup) ? 2 * pb->N : -1; }
+
+int pb_apply_operator(pb_problem *pb, const double *x, double *y, int device_ptrs) {
+    if (!pb || !x || !y) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        require_setup(pb);
+        set_device(pb->ctx);
+        cudaStream_t s = pb->ctx->stream;
+        const int64_t n2 = 2 * pb->N;
+        if (device_ptrs) {
+            apply_operator(pb, x, y);
+        } else {
+            pb->xin.upload(x, n2, s);
+            pb->yout.alloc(n2);
+            apply_operator(pb, pb->xin.p, pb->yout.p);
+            pb->yout.download(y, n2, s);
+        }
+        PB_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+int pb_rhs(pb_problem *pb, double *bh) {
+    if (!pb || !bh) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        require_setup(pb);
+        pb->b.download(bh, 2 * pb->N, pb->ctx->stream);
+        PB_CUDA_TRY(cudaStreamSynchronize(pb->ctx->stream));
+    });
+}
+
+int pb_solve(pb_problem *pb, const double *x0, pb_result *out) {
+    if (!pb) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        set_device(pb->ctx);
+        solve(pb, x0, out);
+    });
+}
+
+int pb_get_solution(pb_problem *pb, double *xh) {
+    if (!pb || !xh) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        require_setup(pb);
+        if (!pb->have_solution) fail(PB_EINVAL, "no solution yet");
+        pb->x.download(xh, 2 * pb->N, pb->ctx->stream);
+        PB_CUDA_TRY(cudaStreamSynchronize(pb->ctx->stream));
+    });
+}
+
+int pb_reaction_potential(pb_problem *pb, const double *xh, double *phi) {
+    if (!pb || !xh || !phi) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        require_setup(pb);
+        set_device(pb->ctx);
+        cudaStream_t s = pb->ctx->stream;
+        pb->xin.upload(xh, 2 * pb->N, s);
+        reaction(pb, pb->xin.p);
+        pb->phi_reac.download(phi, pb->cq.size(), s);
+        PB_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+int pb_coulomb_energy(pb_problem *pb, double *out) {
+    if (!pb || !out) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        require_setup(pb);
+        set_device(pb->ctx);
+        cudaStream_t s = pb->ctx->stream;
+        const int64_t nc = (int64_t)pb->cq.size();
+        if (nc == 0) { *out = 0.0; return; }
+        TmpBuf<double> rowv(nc, s);
+        coulomb_rows(pb->cxyz_d.p, pb->cq_d.p, nc, rowv.p, s);
+        weighted_sum(pb->cq_d.p, rowv.p, nc, 0.5 * kKjPerMol / pb->regions[pb->cregion].eps, pb->energy.p, s);
+        PB_CUDA_TRY(cudaMemcpyAsync(out, pb->energy.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+        PB_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+int pb_tree_info_get(pb_problem *pb, int surface, pb_tree_info *out) {
+    if (!pb || !out) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        require_setup(pb);
+        if (surface < 0 || surface >= (int)pb->T.size()) fail(PB_EINVAL, "no such surface");
+        const Tree &T = pb->T[surface];
+        out->n_points = T.npts;
+        out->n_nodes = T.nnodes;
+        out->n_leaves = T.nleaves;
+        for (int a = 0; a < 3; ++a) out->corner[a] = T.corner[a];
+        out->side = T.side;
+    });
+}
+
+int pb_tree_export(pb_problem *pb, int surface, uint64_t *keys, int32_t *perm, int32_t *node_level,
+                   int64_t *node_start, int64_t *node_count, int32_t *node_first_child, int32_t *node_nchild) {
+    if (!pb) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        require_setup(pb);
+        if (surface < 0 || surface >= (int)pb->T.size()) fail(PB_EINVAL, "no such surface");
+        const Tree &T = pb->T[surface];
+        cudaStream_t s = pb->ctx->stream;
+        if (keys) T.keys.download(keys, T.npts, s);
+        if (perm) T.perm.download(perm, T.npts, s);
+        if (node_level) T.level.download(node_level, T.nnodes, s);
+        if (node_start) T.start.download(node_start, T.nnodes, s);
+        if (node_count) T.count.download(node_count, T.nnodes, s);
+        if (node_first_child) T.first_child.download(node_first_child, T.nnodes, s);
+        if (node_nchild) T.nchild.download(node_nchild, T.nnodes, s);
+        PB_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+int pb_lists_export(pb_problem *pb, int target_surface, int source_surface, int64_t *counts, int64_t *m2p_ptr,
+                    int32_t *m2p_nodes, int64_t *p2p_ptr, int32_t *p2p_nodes, int64_t *near_ptr,
+                    int32_t *near_panels) {
+    if (!pb) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        require_setup(pb);
+        const int ns = (int)pb->S.size();
+        if (target_surface < -1 || target_surface >= ns || source_surface < 0 || source_surface >= ns)
+            fail(PB_EINVAL, "no such surface");
+        const int tg = target_surface < 0 ? ns : target_surface;
+        std::vector<Pair> &v = target_surface < 0 ? pb->cpairs : pb->pairs;
+        const Pair *P = nullptr;
+        for (auto &q : v)
+            if (q.tgt == tg && q.tree == source_surface) P = &q;
+        if (!P) fail(PB_EINVAL, "these surfaces do not interact");
+        const Targets &G = pb->G[tg];
+        cudaStream_t s = pb->ctx->stream;
+        const int64_t m = G.n;
+        if (counts) {
+            counts[0] = P->n_m2p; counts[1] = P->n_p2p; counts[2] = P->n_near;
+            counts[3] = P->near_excl; counts[4] = P->self_excl; counts[5] = m;
+        }
+        std::vector<int32_t> order(m);
+        G.order.download(order.data(), m, s);
+        PB_CUDA_TRY(cudaStreamSynchronize(s));
+        auto reorder = [&](const DevBuf<int64_t> &dptr, const DevBuf<int32_t> &dent, int64_t total, int64_t *hptr,
+                           int32_t *hent) {
+            if (!hptr && !hent) return;
+            std::vector<int64_t> ptr(m + 1);
+            std::vector<int32_t> ent(std::max<int64_t>(1, total));
+            dptr.download(ptr.data(), m + 1, s);
+            if (total) dent.download(ent.data(), total, s);
+            PB_CUDA_TRY(cudaStreamSynchronize(s));
+            std::vector<int64_t> len(m);
+            for (int64_t q = 0; q < m; ++q) len[order[q]] = ptr[q + 1] - ptr[q];
+            std::vector<int64_t> optr(m + 1, 0);
+            for (int64_t i = 0; i < m; ++i) optr[i + 1] = optr[i] + len[i];
+            if (hptr) std::copy(optr.begin(), optr.end(), hptr);
+            if (hent)
+                for (int64_t q = 0; q < m; ++q)
+                    std::copy(ent.begin() + ptr[q], ent.begin() + ptr[q + 1], hent + optr[order[q]]);
+        };
+        reorder(P->m2p_ptr, P->m2p_node, P->n_m2p, m2p_ptr, m2p_nodes);
+        reorder(P->p2p_ptr, P->p2p_node, P->n_p2p, p2p_ptr, p2p_nodes);
+        reorder(P->near_ptr, P->near_panel, P->n_near, near_ptr, near_panels);
+    });
+}
+
+}  // extern "C"

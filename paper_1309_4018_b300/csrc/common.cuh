@@ -1,0 +1,114 @@
+// Shared definitions of the pbbem CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pbbem.h"
+
+namespace pb {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kInv4Pi = 1.0 / (4.0 * kPi);
+// e^2 N_A / (4 pi eps0 * 1 Angstrom) / 1000 in kJ/mol (CODATA 2018)
+constexpr double kKjPerMol = 1389.3545764;
+constexpr int kMaxLevel = 21;
+constexpr int kMaxP = 12;
+
+inline int nterms(int P) { return (P + 1) * (P + 2) * (P + 3) / 6; }
+
+// ---------------------------------------------------------------- errors
+struct Error {
+    int code;
+    std::string msg;
+};
+
+#define PB_CUDA_TRY(call)                                                                       \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            throw ::pb::Error{PB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};   \
+    } while (0)
+
+#define PB_LAUNCH_CHECK() PB_CUDA_TRY(cudaGetLastError())
+
+inline void fail(int code, const std::string &m) { throw Error{code, m}; }
+
+// ---------------------------------------------------------------- device buffer
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count) {
+        if (count == n && p) return;
+        release();
+        if (count == 0) return;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            throw Error{PB_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed"};
+        }
+        n = count;
+    }
+    void zero(cudaStream_t s) {
+        if (n) PB_CUDA_TRY(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+    }
+    void upload(const T *h, size_t count, cudaStream_t s) {
+        alloc(count);
+        if (count) PB_CUDA_TRY(cudaMemcpyAsync(p, h, count * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
+    void download(T *h, size_t count, cudaStream_t s) const {
+        if (count) PB_CUDA_TRY(cudaMemcpyAsync(h, p, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    }
+};
+
+// Stream-ordered temporary: allocated and freed on the stream that uses it,
+// so its release waits for the kernels queued before it.
+template <typename T>
+struct TmpBuf {
+    T *p = nullptr;
+    cudaStream_t s = 0;
+    TmpBuf(size_t count, cudaStream_t st) : s(st) {
+        if (count) {
+            cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), st);
+            if (e != cudaSuccess) {
+                p = nullptr;
+                throw Error{PB_ENOMEM, "cudaMallocAsync of " + std::to_string(count * sizeof(T)) + " bytes failed"};
+            }
+        }
+    }
+    TmpBuf(const TmpBuf &) = delete;
+    TmpBuf &operator=(const TmpBuf &) = delete;
+    ~TmpBuf() {
+        if (p) cudaFreeAsync(p, s);
+    }
+};
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------- primitives (scan_sort.cu)
+// out[i] = sum_{j < i} in[j]; out has n + 1 entries (out[n] = total).  Deterministic.
+void exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+void exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
+// Sort (key, idx) pairs ascending by key then idx (a total order: equals a
+// stable sort by key when idx is the input position).  n arbitrary.
+void sort_key_index(uint64_t *keys, int32_t *idx, int64_t n, cudaStream_t s);
+
+}  // namespace pb

@@ -1,0 +1,21 @@
+// Setup-phase geometry and quadrature entry points (geometry.cu).
+#pragma once
+
+#include "model.cuh"
+
+namespace pb {
+
+void upload_rules();
+bool valid_rule(int K);
+// Centroids, unit normals, areas, L = sqrt(2A), and the K Gauss points of every panel.
+void surface_geometry(SurfDev &S, int K, cudaStream_t s);
+// dV, dK per near entry of Pr: K_fine-rule minus K-rule values (FP64).
+void near_values(const Pair &Pr, const Targets &G, const SurfDev &src, int K, int K_fine, double kappa, double *dV,
+                 double *dK, cudaStream_t s);
+// Semi-analytical V_ii of every panel of S (input order).
+void self_integrals(const SurfDev &S, int N_k, double kappa, double *out, cudaStream_t s);
+// b_i = sum_k q_k G(c_i, r_k) / eps for the panels of S (input order).
+void rhs_rows(const SurfDev &S, int64_t nc, const double *q, const double *xyz, double kappa, double eps, double *b,
+              cudaStream_t s);
+
+}  // namespace pb

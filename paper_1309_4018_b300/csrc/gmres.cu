@@ -1,0 +1,277 @@
+// Device-resident restarted GMRES in FP64 (Sec. 2.3, last paragraph: a Krylov
+// solver with one treecode evaluation per iteration; stopping tolerance
+// gmres_tol of Tables 1 and 3) and the energy reductions (Eqs. solv, total_energy).
+//
+// Arnoldi uses classical Gram-Schmidt applied twice (CGS2): two block
+// projections per step instead of j sequential ones, with the orthogonality
+// of modified Gram-Schmidt.  The Hessenberg least-squares problem is reduced by
+// Givens rotations on the device; the host only reads the residual estimate.
+// All reductions use a fixed block count and a fixed combination order, so
+// results do not depend on scheduling.
+#include "gmres.cuh"
+
+namespace pb {
+
+namespace {
+
+constexpr int kRedBlocks = 296;   // 2 x 148 SMs
+constexpr int kRedThreads = 256;
+
+// partial[v * kRedBlocks + block] = sum over the block's slice of V[v] . w
+__global__ void __launch_bounds__(kRedThreads) mdot_kernel(const double *__restrict__ V, int64_t ld, int nv,
+                                                           const double *__restrict__ w, int64_t n,
+                                                           double *__restrict__ partial) {
+    __shared__ double sm[kRedThreads / 32];
+    const int64_t per = (n + kRedBlocks - 1) / kRedBlocks;
+    const int64_t lo = blockIdx.x * per, hi = min(n, lo + per);
+    for (int v = 0; v < nv; ++v) {
+        const double *Vv = V + v * ld;
+        double s = 0.0;
+        for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) s += Vv[i] * w[i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < kRedThreads / 32; ++k) t += sm[k];
+            partial[v * kRedBlocks + blockIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// out[v] (+)= sum_b partial[v][b]; one warp per vector, fixed order.
+__global__ void mdot_finish_kernel(const double *__restrict__ partial, int nv, double *__restrict__ out, int accumulate) {
+    const int v = blockIdx.x;
+    if (v >= nv) return;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < kRedBlocks; b += 32) s += partial[v * kRedBlocks + b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[v] = accumulate ? out[v] + s : s;
+}
+
+// w -= sum_v V[v] h[v]
+__global__ void project_out_kernel(const double *__restrict__ V, int64_t ld, int nv, const double *__restrict__ h,
+                                   double *__restrict__ w, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = w[i];
+    for (int v = 0; v < nv; ++v) s -= V[v * ld + i] * h[v];
+    w[i] = s;
+}
+
+__global__ void scale_copy_kernel(const double *__restrict__ src, const double *__restrict__ num_sq,
+                                  double *__restrict__ dst, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double d = sqrt(*num_sq);
+    dst[i] = d > 0.0 ? src[i] / d : 0.0;
+}
+
+__global__ void axpby_kernel(double a, const double *__restrict__ x, double b, const double *__restrict__ y,
+                             double *__restrict__ out, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a * x[i] + b * y[i];
+}
+
+__global__ void add_kernel(double *a, const double *b, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] += b[i];
+}
+
+// Arnoldi column j: H[0..j][j] in hcol; nrm2 = ||w||^2.  Applies the previous
+// rotations, forms the new one, updates g and the residual estimate.
+__global__ void givens_kernel(GmresState *st, int j, const double *__restrict__ hcol, const double *__restrict__ nrm2) {
+    if (threadIdx.x != 0) return;
+    const int m = st->m;
+    double *col = st->H + (int64_t)j * (m + 1);   // column-major (m + 1) x m
+    for (int i = 0; i <= j; ++i) col[i] = hcol[i];
+    const double hn = sqrt(*nrm2);
+    col[j + 1] = hn;
+    st->hnext = hn;
+    for (int i = 0; i < j; ++i) {
+        const double t = st->cs[i] * col[i] + st->sn[i] * col[i + 1];
+        col[i + 1] = -st->sn[i] * col[i] + st->cs[i] * col[i + 1];
+        col[i] = t;
+    }
+    const double den = hypot(col[j], col[j + 1]);
+    const double c = den > 0.0 ? col[j] / den : 1.0, s = den > 0.0 ? col[j + 1] / den : 0.0;
+    st->cs[j] = c;
+    st->sn[j] = s;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    st->g[j + 1] = -s * st->g[j];
+    st->g[j] = c * st->g[j];
+    st->res_est = fabs(st->g[j + 1]) / st->bnorm;
+}
+
+// y = H[0..k)^-1 g (back substitution) into st->y.
+__global__ void back_solve_kernel(GmresState *st, int k) {
+    if (threadIdx.x != 0) return;
+    const int m = st->m;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = st->g[i];
+        for (int c = i + 1; c < k; ++c) s -= st->H[(int64_t)c * (m + 1) + i] * st->y[c];
+        st->y[i] = s / st->H[(int64_t)i * (m + 1) + i];
+    }
+}
+
+// x += sum_c V[c] y[c]
+__global__ void update_x_kernel(const double *__restrict__ V, int64_t ld, int k, const GmresState *st,
+                                double *__restrict__ x, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = x[i];
+    for (int c = 0; c < k; ++c) s += V[c * ld + i] * st->y[c];
+    x[i] = s;
+}
+
+__global__ void init_cycle_kernel(GmresState *st, const double *__restrict__ beta2) {
+    if (threadIdx.x != 0) return;
+    const double beta = sqrt(*beta2);
+    for (int i = 0; i <= st->m; ++i) st->g[i] = 0.0;
+    st->g[0] = beta;
+    st->beta = beta;
+}
+
+// ---------------------------------------------------------------- energies
+// out = scale * sum_k q_k phi[k] (fixed-order reduction in one block).
+__global__ void weighted_sum_kernel(const double *__restrict__ q, const double *__restrict__ phi, int64_t n,
+                                    double scale, double *__restrict__ out) {
+    __shared__ double sm[1024];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += q[i] * phi[i];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = scale * sm[0];
+}
+
+// rowv[i] = sum_{j != i} q_j / r_ij
+__global__ void coulomb_rows_kernel(const double *__restrict__ xyz, const double *__restrict__ q, int64_t n,
+                                    double *__restrict__ rowv) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    double s = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        const double dx = x - xyz[3 * j], dy = y - xyz[3 * j + 1], dz = z - xyz[3 * j + 2];
+        s += q[j] / sqrt(dx * dx + dy * dy + dz * dz);
+    }
+    rowv[i] = s;
+}
+
+void dot_device(const double *V, int64_t ld, int nv, const double *w, int64_t n, double *partial, double *out,
+                cudaStream_t s) {
+    mdot_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(V, ld, nv, w, n, partial);
+    PB_LAUNCH_CHECK();
+    mdot_finish_kernel<<<nv, 32, 0, s>>>(partial, nv, out, 0);
+    PB_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+void Gmres::init(int64_t n_, int m_, cudaStream_t s) {
+    n = n_;
+    m = m_;
+    ld = (n + 31) / 32 * 32;
+    V.alloc((size_t)(m + 1) * ld);
+    w.alloc(n);
+    partial.alloc((size_t)kRedBlocks * (m + 2));
+    hcol.alloc(m + 2);
+    h2.alloc(m + 2);
+    scal.alloc(4);
+    H.alloc((size_t)(m + 1) * m);
+    cs.alloc(m); sn.alloc(m); g.alloc(m + 1); y.alloc(m);
+    st.alloc(1);
+    GmresState h{};
+    h.m = m;
+    h.H = H.p; h.cs = cs.p; h.sn = sn.p; h.g = g.p; h.y = y.p;
+    h.bnorm = 1.0;
+    PB_CUDA_TRY(cudaMemcpyAsync(st.p, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    PB_CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+void Gmres::set_bnorm(double bn, cudaStream_t s) {
+    PB_CUDA_TRY(cudaMemcpyAsync(&st.p->bnorm, &bn, sizeof(double), cudaMemcpyHostToDevice, s));
+    PB_CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+double Gmres::start_cycle(const double *r, cudaStream_t s) {
+    dot_device(r, ld, 1, r, n, partial.p, scal.p, s);
+    scale_copy_kernel<<<div_up(n, 256), 256, 0, s>>>(r, scal.p, V.p, n);
+    PB_LAUNCH_CHECK();
+    init_cycle_kernel<<<1, 1, 0, s>>>(st.p, scal.p);
+    PB_LAUNCH_CHECK();
+    double b2 = 0.0;
+    PB_CUDA_TRY(cudaMemcpyAsync(&b2, scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PB_CUDA_TRY(cudaStreamSynchronize(s));
+    return std::sqrt(b2);
+}
+
+void Gmres::arnoldi_step(int j, cudaStream_t s) {
+    const int nv = j + 1;
+    dot_device(V.p, ld, nv, w.p, n, partial.p, hcol.p, s);
+    project_out_kernel<<<div_up(n, 256), 256, 0, s>>>(V.p, ld, nv, hcol.p, w.p, n);
+    PB_LAUNCH_CHECK();
+    dot_device(V.p, ld, nv, w.p, n, partial.p, h2.p, s);
+    project_out_kernel<<<div_up(n, 256), 256, 0, s>>>(V.p, ld, nv, h2.p, w.p, n);
+    PB_LAUNCH_CHECK();
+    add_kernel_launch(hcol.p, h2.p, nv, s);
+    dot_device(w.p, ld, 1, w.p, n, partial.p, scal.p + 1, s);
+    scale_copy_kernel<<<div_up(n, 256), 256, 0, s>>>(w.p, scal.p + 1, V.p + (int64_t)(j + 1) * ld, n);
+    PB_LAUNCH_CHECK();
+    givens_kernel<<<1, 1, 0, s>>>(st.p, j, hcol.p, scal.p + 1);
+    PB_LAUNCH_CHECK();
+}
+
+double Gmres::residual_estimate(cudaStream_t s) {
+    double r = 0.0;
+    PB_CUDA_TRY(cudaMemcpyAsync(&r, &st.p->res_est, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PB_CUDA_TRY(cudaStreamSynchronize(s));
+    return r;
+}
+
+void Gmres::update_solution(int k, double *x, cudaStream_t s) {
+    if (k <= 0) return;
+    back_solve_kernel<<<1, 1, 0, s>>>(st.p, k);
+    PB_LAUNCH_CHECK();
+    update_x_kernel<<<div_up(n, 256), 256, 0, s>>>(V.p, ld, k, st.p, x, n);
+    PB_LAUNCH_CHECK();
+}
+
+void add_kernel_launch(double *a, const double *b, int n, cudaStream_t s) {
+    add_kernel<<<div_up(n, 256), 256, 0, s>>>(a, b, n);
+    PB_LAUNCH_CHECK();
+}
+
+void axpby(double a, const double *x, double b, const double *y, double *out, int64_t n, cudaStream_t s) {
+    if (!n) return;
+    axpby_kernel<<<div_up(n, 256), 256, 0, s>>>(a, x, b, y, out, n);
+    PB_LAUNCH_CHECK();
+}
+
+double norm2_device(const double *x, int64_t n, Gmres &G, cudaStream_t s) {
+    dot_device(x, 0, 1, x, n, G.partial.p, G.scal.p + 2, s);
+    double h = 0.0;
+    PB_CUDA_TRY(cudaMemcpyAsync(&h, G.scal.p + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PB_CUDA_TRY(cudaStreamSynchronize(s));
+    return std::sqrt(h);
+}
+
+void weighted_sum(const double *q, const double *phi, int64_t n, double scale, double *out, cudaStream_t s) {
+    weighted_sum_kernel<<<1, 1024, 0, s>>>(q, phi, n, scale, out);
+    PB_LAUNCH_CHECK();
+}
+
+void coulomb_rows(const double *xyz, const double *q, int64_t n, double *rowv, cudaStream_t s) {
+    if (!n) return;
+    coulomb_rows_kernel<<<div_up(n, 128), 128, 0, s>>>(xyz, q, n, rowv);
+    PB_LAUNCH_CHECK();
+}
+
+}  // namespace pb

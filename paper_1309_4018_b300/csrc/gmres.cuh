@@ -1,0 +1,40 @@
+// Device GMRES state and vector/energy helpers (gmres.cu).
+#pragma once
+
+#include <cmath>
+
+#include "common.cuh"
+
+namespace pb {
+
+// Small Krylov state kept on the device (pointers into Gmres buffers).
+struct GmresState {
+    int m;
+    int pad_;
+    double *H, *cs, *sn, *g, *y;
+    double bnorm, beta, hnext, res_est;
+};
+
+struct Gmres {
+    int64_t n = 0, ld = 0;
+    int m = 0;
+    DevBuf<double> V, w, partial, hcol, h2, scal, H, cs, sn, g, y;
+    DevBuf<GmresState> st;
+    void init(int64_t n, int m, cudaStream_t s);
+    void set_bnorm(double bn, cudaStream_t s);
+    double start_cycle(const double *r, cudaStream_t s);   // v_0 = r / ||r||; returns ||r||
+    double *basis(int j) { return V.p + (int64_t)j * ld; }
+    void arnoldi_step(int j, cudaStream_t s);              // needs w = A v_j
+    double residual_estimate(cudaStream_t s);
+    void update_solution(int k, double *x, cudaStream_t s);
+};
+
+void add_kernel_launch(double *a, const double *b, int n, cudaStream_t s);
+void axpby(double a, const double *x, double b, const double *y, double *out, int64_t n, cudaStream_t s);
+double norm2_device(const double *x, int64_t n, Gmres &G, cudaStream_t s);
+// *out = scale * sum_k q_k phi_k (device scalar)
+void weighted_sum(const double *q, const double *phi, int64_t n, double scale, double *out, cudaStream_t s);
+// rowv[i] = sum_{j != i} q_j / r_ij
+void coulomb_rows(const double *xyz, const double *q, int64_t n, double *rowv, cudaStream_t s);
+
+}  // namespace pb

@@ -1,0 +1,89 @@
+// Device-side data model of one problem: surfaces, octrees, target sets and
+// the per-(target set, octree) interaction data of the treecode.
+#pragma once
+
+#include "common.cuh"
+
+namespace pb {
+
+struct Params {
+    int K = 3, K_fine = 19, N_k = 5;
+    double thres = 2.0;
+    int P = 6;
+    double theta = 0.5;
+    int ncrit = 300;
+    double tol = 1e-4;
+    int restart = 50, max_iter = 1000;
+    int precision = PB_FP64;
+};
+
+struct Region {
+    double eps, kappa;
+};
+
+// Geometry of one surface on the device (panels in input order).
+struct SurfDev {
+    int64_t n = 0, nv = 0;
+    int inner = -1, outer = -1;
+    int64_t off = 0;                 // first panel in the concatenated panel list
+    DevBuf<double> verts;            // nv * 3
+    DevBuf<int32_t> tris;            // n * 3
+    DevBuf<double> cen, nrm;         // n * 3
+    DevBuf<double> area, L;          // n
+    DevBuf<double> gy, gwa;          // K Gauss points: n*K*3, n*K (point j*K + k)
+};
+
+// Octree over the K * n Gauss points of one surface (the treecode sources).
+struct Tree {
+    int64_t npts = 0;
+    double corner[3] = {0, 0, 0}, side = 1.0, origin[3] = {0, 0, 0};
+    int nnodes = 0, nleaves = 0, nlevels = 0;
+    std::vector<int> level_off;      // nodes of level l: [level_off[l], level_off[l+1])
+    DevBuf<uint64_t> keys;           // sorted Morton keys
+    DevBuf<int32_t> perm;            // sorted position -> point index
+    DevBuf<int32_t> level, first_child, nchild, parent, node_leaf;
+    DevBuf<int64_t> start, count;
+    DevBuf<double> centre, rb2;      // centre: nnodes * 3
+    DevBuf<int32_t> leaf_node;       // leaf index (Morton order) -> node
+    DevBuf<int32_t> point_leaf;      // point index (input order) -> leaf index
+    // sorted source data
+    DevBuf<double> ys;               // npts * 3 (absolute, FP64)
+    DevBuf<double> was;              // npts weight * area
+    DevBuf<int32_t> pids;            // npts owning panel (within the surface)
+    DevBuf<float4> pos32;            // (x, y, z relative to origin, weight*area) FP32
+    // per-evaluation source strengths
+    DevBuf<double> src64;            // npts * 8: x, y, z, s, dx, dy, dz, pid
+    DevBuf<float4> srcA32, srcB32;   // (x, y, z, s) and (dx, dy, dz, pid bits)
+    DevBuf<double> mom64;            // nnodes * 2 * nterms: M then D
+    DevBuf<float> mom32;
+};
+
+// Evaluation points: panel centroids of one surface, or the charges.
+struct Targets {
+    int64_t n = 0;
+    int surface = -1;                // -1: charges
+    DevBuf<double> xs;               // sorted positions n * 3
+    DevBuf<int32_t> order;           // sorted position -> input index
+    DevBuf<int32_t> rank;            // input index -> sorted position
+    DevBuf<int32_t> self_panel;      // sorted position -> own panel (surface targets) or -1
+};
+
+// Interaction of one target set with one octree, for one or two kernels.
+struct Pair {
+    int tgt = 0;                     // index into the problem's target sets
+    int tree = 0;                    // source surface
+    std::vector<double> kappas;      // distinct kernels (kappa = 0: Laplace)
+    DevBuf<int64_t> m2p_ptr, p2p_ptr, near_ptr;
+    DevBuf<int32_t> m2p_node, p2p_node, near_panel;
+    int64_t n_m2p = 0, n_p2p = 0, n_near = 0, near_excl = 0, self_excl = 0, p2p_pairs = 0;
+    // per warp of 32 sorted targets: union of the lists with lane masks
+    DevBuf<int64_t> gp2p_ptr, gm2p_ptr;
+    DevBuf<int2> gp2p, gm2p;         // (leaf index | node, lane mask)
+    int64_t n_gp2p = 0, n_gm2p = 0;
+    // near-singular corrections per kernel: dV, dK per near entry; self V per panel
+    std::vector<DevBuf<double>> dV, dK, selfV;
+    // outputs per kernel: V then K per sorted target (2 * n)
+    std::vector<DevBuf<double>> VK;
+};
+
+}  // namespace pb

@@ -1,0 +1,671 @@
+// Octree construction and per-target interaction lists (Sec. 2.3, Eq. MAC).
+//
+// Integer decisions (Morton keys, splits, MAC, near-singular test) use FP64
+// arithmetic written with explicit round-to-nearest intrinsics, so no multiply
+// is fused with an add and the results are reproducible bit for bit:
+//   root cube   centre = (lo + hi) / 2, side = max extent * (1 + 2^-20)
+//   key         q_a = min(2^21 - 1, floor((p_a - corner_a) * (2^21 / side))),
+//               bits interleaved with x the most significant of each triple
+//   split       a box with >= ncrit sources below level 21 splits into its
+//               non-empty octants; nodes numbered breadth first
+//   MAC         accept when (side_l^2 * 0.75) < theta^2 ((dx^2 + dy^2) + dz^2),
+//               box centre corner + (i + 0.5) side_l (Eq. MAC, r_b the half diagonal)
+//   near        |x_i - c_j|^2 < (thres L_j)^2, L_j = sqrt(2 A_j), for panels whose
+//               Gauss points all lie in the target's direct-sum leaves
+#include <algorithm>
+#include <cmath>
+
+#include "model.cuh"
+#include "tree.cuh"
+
+namespace pb {
+
+namespace {
+
+__global__ void bbox_kernel(const double *__restrict__ p, int64_t n, double *__restrict__ out) {
+    __shared__ double sm[6][32];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+        for (int a = 0; a < 3; ++a) {
+            double v = p[3 * i + a];
+            lo[a] = fmin(lo[a], v);
+            hi[a] = fmax(hi[a], v);
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) { sm[a][warp] = lo[a]; sm[3 + a][warp] = hi[a]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int a = 0; a < 3; ++a) {
+            double l = sm[a][0], h = sm[3 + a][0];
+            for (int w = 1; w < nw; ++w) { l = fmin(l, sm[a][w]); h = fmax(h, sm[3 + a][w]); }
+            out[a] = l;
+            out[3 + a] = h;
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t spread3(uint64_t v) {
+    uint64_t r = 0;
+    for (int b = 0; b < 21; ++b) r |= ((v >> b) & 1ull) << (3 * b);
+    return r;
+}
+
+__global__ void morton_kernel(const double *__restrict__ p, int64_t n, double cx, double cy, double cz,
+                              double scale, uint64_t *__restrict__ keys, int32_t *__restrict__ idx) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double c[3] = {cx, cy, cz};
+    uint64_t q[3];
+    for (int a = 0; a < 3; ++a) {
+        double f = floor(__dmul_rn(__dsub_rn(p[3 * i + a], c[a]), scale));
+        f = fmin(fmax(f, 0.0), 2097151.0);
+        q[a] = (uint64_t)f;
+    }
+    keys[i] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+    idx[i] = (int32_t)i;
+}
+
+// For every node of one level: count the non-empty octants of the nodes that split.
+__global__ void split_count_kernel(int lvl, int nb, int nodes_begin, const int64_t *__restrict__ start,
+                                   const int64_t *__restrict__ count, const uint64_t *__restrict__ keys, int ncrit,
+                                   int32_t *__restrict__ nchild, int32_t *__restrict__ child_bounds /*nodes*9*/) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb) return;
+    const int b = nodes_begin + t;
+    const int64_t s = start[b], c = count[b];
+    int nc = 0;
+    if (c >= ncrit && lvl < kMaxLevel) {
+        const int sh = 3 * (kMaxLevel - 1 - lvl);
+        int64_t prev = 0;
+        child_bounds[9 * t] = 0;
+        for (int o = 1; o <= 8; ++o) {
+            // first position in [s, s + c) whose octant digit is >= o
+            int64_t lo = 0, hi = c;
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                int d = (int)((keys[s + mid] >> sh) & 7ull);
+                if (d < o) lo = mid + 1; else hi = mid;
+            }
+            child_bounds[9 * t + o] = (int32_t)lo;
+            if (lo > prev) ++nc;
+            prev = lo;
+        }
+    }
+    nchild[b] = nc;
+}
+
+__global__ void split_write_kernel(int lvl, int nb, int nodes_begin, int nodes_end, const int64_t *__restrict__ cscan,
+                                   const int32_t *__restrict__ child_bounds, int64_t *__restrict__ start,
+                                   int64_t *__restrict__ count, int32_t *__restrict__ level,
+                                   int32_t *__restrict__ first_child, int32_t *__restrict__ nchild,
+                                   int32_t *__restrict__ parent, int64_t *__restrict__ ijk /*nodes*3*/) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb) return;
+    const int b = nodes_begin + t;
+    const int nc = nchild[b];
+    if (nc == 0) { first_child[b] = -1; return; }
+    int c = nodes_end + (int)cscan[t];
+    first_child[b] = c;
+    const int64_t s = start[b];
+    for (int o = 0; o < 8; ++o) {
+        const int64_t cs = child_bounds[9 * t + o], ce = child_bounds[9 * t + o + 1];
+        if (ce > cs) {
+            start[c] = s + cs;
+            count[c] = ce - cs;
+            level[c] = lvl + 1;
+            parent[c] = b;
+            nchild[c] = 0;
+            first_child[c] = -1;
+            ijk[3 * c + 0] = 2 * ijk[3 * b + 0] + ((o >> 2) & 1);
+            ijk[3 * c + 1] = 2 * ijk[3 * b + 1] + ((o >> 1) & 1);
+            ijk[3 * c + 2] = 2 * ijk[3 * b + 2] + (o & 1);
+            ++c;
+        }
+    }
+}
+
+__global__ void node_geom_kernel(int nnodes, const int32_t *__restrict__ level, const int64_t *__restrict__ ijk,
+                                 double cx, double cy, double cz, double side, double *__restrict__ centre,
+                                 double *__restrict__ rb2) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nnodes) return;
+    const double sl = ldexp(side, -level[b]);
+    const double c[3] = {cx, cy, cz};
+    for (int a = 0; a < 3; ++a)
+        centre[3 * b + a] = __dadd_rn(c[a], __dmul_rn(__dadd_rn((double)ijk[3 * b + a], 0.5), sl));
+    rb2[b] = __dmul_rn(__dmul_rn(sl, sl), 0.75);
+}
+
+__global__ void leaf_flag_kernel(int nnodes, const int32_t *__restrict__ nchild, const int64_t *__restrict__ start,
+                                 int32_t *__restrict__ head /*npts*/) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nnodes) return;
+    if (nchild[b] == 0) head[start[b]] = 1;
+}
+
+__global__ void leaf_index_kernel(int nnodes, const int32_t *__restrict__ nchild, const int64_t *__restrict__ start,
+                                  const int64_t *__restrict__ count, const int64_t *__restrict__ hscan,
+                                  const int32_t *__restrict__ perm, int32_t *__restrict__ node_leaf,
+                                  int32_t *__restrict__ leaf_node, int32_t *__restrict__ point_leaf) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nnodes) return;
+    if (nchild[b] != 0) { node_leaf[b] = -1; return; }
+    const int li = (int)hscan[start[b]];
+    node_leaf[b] = li;
+    leaf_node[li] = b;
+    for (int64_t q = start[b]; q < start[b] + count[b]; ++q) point_leaf[perm[q]] = li;
+}
+
+__global__ void gather_sources_kernel(int64_t n, int K, const int32_t *__restrict__ perm, const double *__restrict__ gy,
+                                      const double *__restrict__ gwa, double ox, double oy, double oz,
+                                      double *__restrict__ ys, double *__restrict__ was, int32_t *__restrict__ pids,
+                                      float4 *__restrict__ pos32) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int p = perm[q];
+    const double x = gy[3 * p], y = gy[3 * p + 1], z = gy[3 * p + 2];
+    ys[3 * q] = x; ys[3 * q + 1] = y; ys[3 * q + 2] = z;
+    was[q] = gwa[p];
+    pids[q] = p / K;
+    pos32[q] = make_float4((float)(x - ox), (float)(y - oy), (float)(z - oz), (float)gwa[p]);
+}
+
+__global__ void gather_targets_kernel(int64_t n, const int32_t *__restrict__ order, const double *__restrict__ x,
+                                      double *__restrict__ xs, int32_t *__restrict__ selfp, int32_t *__restrict__ rank,
+                                      int has_self) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int i = order[q];
+    rank[i] = (int32_t)q;
+    xs[3 * q] = x[3 * i]; xs[3 * q + 1] = x[3 * i + 1]; xs[3 * q + 2] = x[3 * i + 2];
+    selfp[q] = has_self ? i : -1;
+}
+
+// ---------------------------------------------------------------- traversal (Eq. MAC)
+constexpr int kStack = 192;
+
+template <bool FILL>
+__global__ void traverse_kernel(int64_t ntg, const double *__restrict__ xs, const double *__restrict__ centre,
+                                const double *__restrict__ rb2, const int32_t *__restrict__ first_child,
+                                const int32_t *__restrict__ nchild, double theta2, int direct,
+                                int32_t *__restrict__ m2p_cnt, int32_t *__restrict__ p2p_cnt,
+                                const int64_t *__restrict__ m2p_ptr, const int64_t *__restrict__ p2p_ptr,
+                                int32_t *__restrict__ m2p_node, int32_t *__restrict__ p2p_node,
+                                int32_t *__restrict__ err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntg) return;
+    const double x = xs[3 * i], y = xs[3 * i + 1], z = xs[3 * i + 2];
+    int stack[kStack];
+    int sp = 0;
+    stack[sp++] = 0;
+    int nm = 0, np = 0;
+    int64_t mo = FILL ? m2p_ptr[i] : 0, po = FILL ? p2p_ptr[i] : 0;
+    while (sp > 0) {
+        const int b = stack[--sp];
+        const double dx = __dsub_rn(x, centre[3 * b]);
+        const double dy = __dsub_rn(y, centre[3 * b + 1]);
+        const double dz = __dsub_rn(z, centre[3 * b + 2]);
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        if (!direct && rb2[b] < __dmul_rn(theta2, d2)) {
+            if (FILL) m2p_node[mo + nm] = b;
+            ++nm;
+        } else if (nchild[b] == 0) {
+            if (FILL) p2p_node[po + np] = b;
+            ++np;
+        } else {
+            const int fc = first_child[b], nc = nchild[b];
+            if (sp + nc > kStack) { atomicExch(err, 1); return; }
+            for (int c = fc + nc - 1; c >= fc; --c) stack[sp++] = c;
+        }
+    }
+    if (!FILL) { m2p_cnt[i] = nm; p2p_cnt[i] = np; }
+}
+
+// Union of the lists of 32 consecutive sorted targets with per-lane masks.
+// One warp per group; entries are collected chunk by chunk of the index range
+// in shared memory, so the union comes out in ascending index order.
+constexpr int kUnionChunk = 8192;
+
+template <bool FILL>
+__global__ void group_union_kernel(int64_t ntg, int64_t ngroups, const int64_t *__restrict__ ptr,
+                                   const int32_t *__restrict__ ent, int nidx, int32_t *__restrict__ gcount,
+                                   const int64_t *__restrict__ gptr, int2 *__restrict__ gent) {
+    extern __shared__ uint32_t smask[];
+    const int64_t g = blockIdx.x;
+    if (g >= ngroups) return;
+    const int lane = threadIdx.x;
+    const int64_t t = g * 32 + lane;
+    const int64_t b0 = t < ntg ? ptr[t] : 0, b1 = t < ntg ? ptr[t + 1] : 0;
+    int total = 0;
+    const int64_t out = FILL ? gptr[g] : 0;
+    for (int c0 = 0; c0 < nidx; c0 += kUnionChunk) {
+        const int c1 = min(nidx, c0 + kUnionChunk);
+        for (int k = lane; k < c1 - c0; k += 32) smask[k] = 0u;
+        __syncwarp();
+        for (int64_t e = b0; e < b1; ++e) {
+            const int v = ent[e];
+            if (v >= c0 && v < c1) atomicOr(&smask[v - c0], 1u << lane);
+        }
+        __syncwarp();
+        for (int k0 = 0; k0 < c1 - c0; k0 += 32) {
+            const int k = k0 + lane;
+            const uint32_t m = (k < c1 - c0) ? smask[k] : 0u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, m != 0u);
+            if (FILL && m != 0u) {
+                const int pos = __popc(bal & ((1u << lane) - 1u));
+                gent[out + total + pos] = make_int2(c0 + k, (int)m);
+            }
+            total += __popc(bal);
+        }
+        __syncwarp();
+    }
+    if (!FILL && lane == 0) gcount[g] = total;
+}
+
+// ---------------------------------------------------------------- near-singular lists
+__device__ __forceinline__ bool in_sorted(const int32_t *__restrict__ a, int64_t n, int v) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo < n && a[lo] == v;
+}
+
+__device__ __forceinline__ bool is_near(double x, double y, double z, const double *__restrict__ cen,
+                                        const double *__restrict__ L, double thres, int j) {
+    const double dx = __dsub_rn(x, cen[3 * j]);
+    const double dy = __dsub_rn(y, cen[3 * j + 1]);
+    const double dz = __dsub_rn(z, cen[3 * j + 2]);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    const double tl = __dmul_rn(thres, L[j]);
+    return d2 < __dmul_rn(tl, tl);
+}
+
+template <bool FILL>
+__global__ void near_kernel(int64_t ntg, int K, const double *__restrict__ xs, const int32_t *__restrict__ selfp,
+                            int use_self, const int64_t *__restrict__ p2p_ptr, const int32_t *__restrict__ p2p_leafidx,
+                            const int32_t *__restrict__ leaf_node, const int64_t *__restrict__ start,
+                            const int64_t *__restrict__ count, const int32_t *__restrict__ perm,
+                            const int32_t *__restrict__ point_leaf, const double *__restrict__ cen,
+                            const double *__restrict__ L, double thres, int32_t *__restrict__ ncount,
+                            int32_t *__restrict__ excl, int32_t *__restrict__ self_excl,
+                            const int64_t *__restrict__ near_ptr, int32_t *__restrict__ near_panel,
+                            const int64_t *__restrict__ m2p_ptr, const int32_t *__restrict__ m2p_node,
+                            const double *__restrict__ centre, const double *__restrict__ rb2, double reach) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntg) return;
+    const double x = xs[3 * i], y = xs[3 * i + 1], z = xs[3 * i + 2];
+    const int me = use_self ? selfp[i] : -1;
+    const int64_t l0 = p2p_ptr[i], l1 = p2p_ptr[i + 1];
+    const int32_t *lst = p2p_leafidx + l0;
+    const int64_t nl = l1 - l0;
+    int cnt = 0, ex = 0;
+    const int64_t o = FILL ? near_ptr[i] : 0;
+    for (int64_t e = 0; e < nl; ++e) {
+        const int b = leaf_node[lst[e]];
+        for (int64_t q = start[b]; q < start[b] + count[b]; ++q) {
+            const int pt = perm[q];
+            const int j = pt / K, k = pt - j * K;
+            if (j == me || !is_near(x, y, z, cen, L, thres, j)) continue;
+            // handle panel j once, at its lowest-numbered point inside the direct leaves
+            bool first = true;
+            for (int kk = 0; kk < k; ++kk)
+                if (in_sorted(lst, nl, point_leaf[j * K + kk])) { first = false; break; }
+            if (!first) continue;
+            // points 0..k-1 lie outside the direct leaves when k > 0
+            bool all = k == 0;
+            for (int kk = k + 1; all && kk < K; ++kk)
+                if (!in_sorted(lst, nl, point_leaf[j * K + kk])) all = false;
+            if (all) {
+                if (FILL) near_panel[o + cnt] = j;
+                ++cnt;
+            } else {
+                ++ex;
+            }
+        }
+    }
+    if (FILL) {
+        // ascending panel order
+        int32_t *a = near_panel + o;
+        for (int u = 1; u < cnt; ++u) {
+            int v = a[u], w = u - 1;
+            while (w >= 0 && a[w] > v) { a[w + 1] = a[w]; --w; }
+            a[w + 1] = v;
+        }
+    } else {
+        // near panels lying wholly in accepted boxes: only boxes that can hold a
+        // point within `reach` (>= thres L_j + panel radius) of the target are scanned
+        for (int64_t e = m2p_ptr[i]; e < m2p_ptr[i + 1]; ++e) {
+            const int b = m2p_node[e];
+            const double bx = x - centre[3 * b], by = y - centre[3 * b + 1], bz = z - centre[3 * b + 2];
+            const double rr = reach + sqrt(rb2[b]);
+            if (bx * bx + by * by + bz * bz >= rr * rr) continue;
+            for (int64_t q = start[b]; q < start[b] + count[b]; ++q) {
+                const int pt = perm[q];
+                const int j = pt / K;
+                if (pt - j * K != 0 || j == me || !is_near(x, y, z, cen, L, thres, j)) continue;
+                bool any = false;
+                for (int kk = 0; kk < K && !any; ++kk) any = in_sorted(lst, nl, point_leaf[j * K + kk]);
+                if (!any) ++ex;
+            }
+        }
+        ncount[i] = cnt;
+        excl[i] = ex;
+        int se = 0;
+        if (me >= 0)
+            for (int kk = 0; kk < K; ++kk)
+                if (!in_sorted(lst, nl, point_leaf[me * K + kk])) se = 1;
+        self_excl[i] = se;
+    }
+}
+
+// max_j (thres L_j + max_v |v - c_j|) over the panels of a surface (one block).
+__global__ void reach_kernel(int64_t n, const double *__restrict__ v, const int32_t *__restrict__ t,
+                             const double *__restrict__ cen, const double *__restrict__ L, double thres,
+                             double *__restrict__ out) {
+    __shared__ double sm[1024];
+    double m = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        double r = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const int a = t[3 * j + c];
+            const double dx = v[3 * a] - cen[3 * j], dy = v[3 * a + 1] - cen[3 * j + 1], dz = v[3 * a + 2] - cen[3 * j + 2];
+            r = fmax(r, sqrt(dx * dx + dy * dy + dz * dz));
+        }
+        m = fmax(m, thres * L[j] + r);
+    }
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sm[0] * (1.0 + 1e-12) + 1e-12;
+}
+
+__global__ void node_to_leaf_kernel(int64_t n, const int32_t *__restrict__ nodes, const int32_t *__restrict__ node_leaf,
+                                    int32_t *__restrict__ out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) out[e] = node_leaf[nodes[e]];
+}
+
+__global__ void sum_i32_kernel(const int32_t *__restrict__ a, int64_t n, unsigned long long *out) {
+    unsigned long long s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += (unsigned long long)a[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+__global__ void p2p_pairs_kernel(int64_t ntg, const int64_t *__restrict__ ptr, const int32_t *__restrict__ nodes,
+                                 const int64_t *__restrict__ count, unsigned long long *out) {
+    unsigned long long s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ntg; i += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) s += (unsigned long long)count[nodes[e]];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+int64_t device_sum_i32(const int32_t *a, int64_t n, cudaStream_t s) {
+    TmpBuf<unsigned long long> d(1, s);
+    PB_CUDA_TRY(cudaMemsetAsync(d.p, 0, sizeof(unsigned long long), s));
+    if (n > 0) {
+        sum_i32_kernel<<<std::min<int64_t>(1024, div_up(n, 256)), 256, 0, s>>>(a, n, d.p);
+        PB_LAUNCH_CHECK();
+    }
+    unsigned long long h = 0;
+    PB_CUDA_TRY(cudaMemcpyAsync(&h, d.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PB_CUDA_TRY(cudaStreamSynchronize(s));
+    return (int64_t)h;
+}
+
+void root_cube_from(const double *d_points, int64_t n, cudaStream_t s, double corner[3], double &side) {
+    TmpBuf<double> bb(6, s);
+    bbox_kernel<<<1, 1024, 0, s>>>(d_points, n, bb.p);
+    PB_LAUNCH_CHECK();
+    double h[6];
+    PB_CUDA_TRY(cudaMemcpyAsync(h, bb.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PB_CUDA_TRY(cudaStreamSynchronize(s));
+    // plain IEEE double arithmetic, one operation per statement (the host is
+    // compiled without contraction)
+    double centre[3], ext[3];
+    for (int a = 0; a < 3; ++a) {
+        centre[a] = (h[a] + h[3 + a]) * 0.5;
+        ext[a] = h[3 + a] - h[a];
+    }
+    const double m = std::max(std::max(ext[0], ext[1]), ext[2]);
+    side = m * (1.0 + 0x1p-20);
+    if (side == 0.0 || !std::isfinite(side)) side = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        const double half = side * 0.5;
+        corner[a] = centre[a] - half;
+    }
+}
+
+}  // namespace
+
+int64_t read_i64(const int64_t *d, cudaStream_t s) {
+    int64_t h = 0;
+    PB_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PB_CUDA_TRY(cudaStreamSynchronize(s));
+    return h;
+}
+
+void morton_sort(const double *d_points, int64_t n, cudaStream_t s, double corner[3], double &side,
+                 DevBuf<uint64_t> &keys, DevBuf<int32_t> &perm) {
+    root_cube_from(d_points, n, s, corner, side);
+    keys.alloc(n);
+    perm.alloc(n);
+    const double scale = 2097152.0 / side;
+    if (n) {
+        morton_kernel<<<div_up(n, 256), 256, 0, s>>>(d_points, n, corner[0], corner[1], corner[2], scale, keys.p, perm.p);
+        PB_LAUNCH_CHECK();
+        sort_key_index(keys.p, perm.p, n, s);
+    }
+}
+
+void build_tree(Tree &T, const SurfDev &S, int K, int ncrit, cudaStream_t s) {
+    const int64_t n = S.n * K;
+    T.npts = n;
+    morton_sort(S.gy.p, n, s, T.corner, T.side, T.keys, T.perm);
+    for (int a = 0; a < 3; ++a) T.origin[a] = T.corner[a] + 0.5 * T.side;
+    // level-by-level splitting; capacity bound: every level holds disjoint nodes
+    const int64_t maxn = std::min<int64_t>((int64_t)1 + 8LL * (kMaxLevel + 1) * (n / std::max(1, ncrit) + 1),
+                                           2 * n + 64);
+    T.level.alloc(maxn); T.first_child.alloc(maxn); T.nchild.alloc(maxn); T.parent.alloc(maxn);
+    T.start.alloc(maxn); T.count.alloc(maxn);
+    TmpBuf<int64_t> ijk(3 * maxn, s);
+    {
+        int32_t l0 = 0, fc = -1, nc = 0, par = -1;
+        int64_t st = 0, ct = n, z3[3] = {0, 0, 0};
+        PB_CUDA_TRY(cudaMemcpyAsync(T.level.p, &l0, 4, cudaMemcpyHostToDevice, s));
+        PB_CUDA_TRY(cudaMemcpyAsync(T.first_child.p, &fc, 4, cudaMemcpyHostToDevice, s));
+        PB_CUDA_TRY(cudaMemcpyAsync(T.nchild.p, &nc, 4, cudaMemcpyHostToDevice, s));
+        PB_CUDA_TRY(cudaMemcpyAsync(T.parent.p, &par, 4, cudaMemcpyHostToDevice, s));
+        PB_CUDA_TRY(cudaMemcpyAsync(T.start.p, &st, 8, cudaMemcpyHostToDevice, s));
+        PB_CUDA_TRY(cudaMemcpyAsync(T.count.p, &ct, 8, cudaMemcpyHostToDevice, s));
+        PB_CUDA_TRY(cudaMemcpyAsync(ijk.p, z3, 24, cudaMemcpyHostToDevice, s));
+        PB_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    T.level_off.assign(1, 0);
+    int lb = 0, le = 1, lvl = 0;
+    while (true) {
+        T.level_off.push_back(le);
+        const int nb = le - lb;
+        TmpBuf<int32_t> bounds((size_t)nb * 9, s);
+        TmpBuf<int64_t> cscan(nb + 1, s);
+        split_count_kernel<<<div_up(nb, 128), 128, 0, s>>>(lvl, nb, lb, T.start.p, T.count.p, T.keys.p, ncrit,
+                                                           T.nchild.p, bounds.p);
+        PB_LAUNCH_CHECK();
+        exclusive_scan_i32_to_i64(T.nchild.p + lb, cscan.p, nb, s);
+        const int64_t nnew = read_i64(cscan.p + nb, s);
+        if (le + nnew > maxn) fail(PB_ENOMEM, "octree node capacity exceeded");
+        split_write_kernel<<<div_up(nb, 128), 128, 0, s>>>(lvl, nb, lb, le, cscan.p, bounds.p, T.start.p, T.count.p,
+                                                           T.level.p, T.first_child.p, T.nchild.p, T.parent.p, ijk.p);
+        PB_LAUNCH_CHECK();
+        if (nnew == 0) break;
+        lb = le;
+        le = le + (int)nnew;
+        ++lvl;
+    }
+    T.nnodes = le;
+    T.nlevels = lvl + 1;
+    T.centre.alloc(3 * (size_t)T.nnodes);
+    T.rb2.alloc(T.nnodes);
+    node_geom_kernel<<<div_up(T.nnodes, 128), 128, 0, s>>>(T.nnodes, T.level.p, ijk.p, T.corner[0], T.corner[1],
+                                                           T.corner[2], T.side, T.centre.p, T.rb2.p);
+    PB_LAUNCH_CHECK();
+    // leaves in Morton order (= depth-first pre-order)
+    TmpBuf<int32_t> head(n, s);
+    TmpBuf<int64_t> hscan(n + 1, s);
+    PB_CUDA_TRY(cudaMemsetAsync(head.p, 0, n * sizeof(int32_t), s));
+    leaf_flag_kernel<<<div_up(T.nnodes, 128), 128, 0, s>>>(T.nnodes, T.nchild.p, T.start.p, head.p);
+    PB_LAUNCH_CHECK();
+    exclusive_scan_i32_to_i64(head.p, hscan.p, n, s);
+    T.nleaves = (int)read_i64(hscan.p + n, s);
+    T.node_leaf.alloc(T.nnodes);
+    T.leaf_node.alloc(T.nleaves);
+    T.point_leaf.alloc(n);
+    leaf_index_kernel<<<div_up(T.nnodes, 128), 128, 0, s>>>(T.nnodes, T.nchild.p, T.start.p, T.count.p, hscan.p,
+                                                            T.perm.p, T.node_leaf.p, T.leaf_node.p, T.point_leaf.p);
+    PB_LAUNCH_CHECK();
+    // sorted source geometry
+    T.ys.alloc(3 * n); T.was.alloc(n); T.pids.alloc(n); T.pos32.alloc(n);
+    gather_sources_kernel<<<div_up(n, 256), 256, 0, s>>>(n, K, T.perm.p, S.gy.p, S.gwa.p, T.origin[0], T.origin[1],
+                                                         T.origin[2], T.ys.p, T.was.p, T.pids.p, T.pos32.p);
+    PB_LAUNCH_CHECK();
+    T.src64.alloc(8 * n); T.srcA32.alloc(n); T.srcB32.alloc(n);
+}
+
+void build_targets(Targets &G, const double *d_x, int64_t n, int surface, cudaStream_t s) {
+    G.n = n;
+    G.surface = surface;
+    double corner[3], side;
+    DevBuf<uint64_t> keys;
+    morton_sort(d_x, n, s, corner, side, keys, G.order);
+    G.xs.alloc(3 * n);
+    G.self_panel.alloc(n);
+    G.rank.alloc(n);
+    if (n) {
+        gather_targets_kernel<<<div_up(n, 256), 256, 0, s>>>(n, G.order.p, d_x, G.xs.p, G.self_panel.p, G.rank.p,
+                                                             surface >= 0);
+        PB_LAUNCH_CHECK();
+    }
+    PB_CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
+                 cudaStream_t s) {
+    const int64_t m = G.n;
+    TmpBuf<int32_t> mc(m, s), pc(m, s), err(1, s);
+    PB_CUDA_TRY(cudaMemsetAsync(err.p, 0, 4, s));
+    const double theta2 = prm.theta * prm.theta;
+    const int direct = prm.theta <= 0.0;
+    Pr.m2p_ptr.alloc(m + 1);
+    Pr.p2p_ptr.alloc(m + 1);
+    if (m) {
+        traverse_kernel<false><<<div_up(m, 128), 128, 0, s>>>(m, G.xs.p, T.centre.p, T.rb2.p, T.first_child.p,
+                                                              T.nchild.p, theta2, direct, mc.p, pc.p, nullptr, nullptr,
+                                                              nullptr, nullptr, err.p);
+        PB_LAUNCH_CHECK();
+    }
+    exclusive_scan_i32_to_i64(mc.p, Pr.m2p_ptr.p, m, s);
+    exclusive_scan_i32_to_i64(pc.p, Pr.p2p_ptr.p, m, s);
+    Pr.n_m2p = read_i64(Pr.m2p_ptr.p + m, s);
+    Pr.n_p2p = read_i64(Pr.p2p_ptr.p + m, s);
+    Pr.m2p_node.alloc(std::max<int64_t>(1, Pr.n_m2p));
+    Pr.p2p_node.alloc(std::max<int64_t>(1, Pr.n_p2p));
+    if (m) {
+        traverse_kernel<true><<<div_up(m, 128), 128, 0, s>>>(m, G.xs.p, T.centre.p, T.rb2.p, T.first_child.p,
+                                                             T.nchild.p, theta2, direct, nullptr, nullptr,
+                                                             Pr.m2p_ptr.p, Pr.p2p_ptr.p, Pr.m2p_node.p, Pr.p2p_node.p,
+                                                             err.p);
+        PB_LAUNCH_CHECK();
+    }
+    int herr = 0;
+    PB_CUDA_TRY(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, s));
+    PB_CUDA_TRY(cudaStreamSynchronize(s));
+    if (herr) fail(PB_EINVAL, "octree traversal stack overflow");
+    // direct-sum pair count
+    {
+        TmpBuf<unsigned long long> d(1, s);
+        PB_CUDA_TRY(cudaMemsetAsync(d.p, 0, 8, s));
+        if (m) {
+            p2p_pairs_kernel<<<std::min<int64_t>(1024, div_up(m, 256)), 256, 0, s>>>(m, Pr.p2p_ptr.p, Pr.p2p_node.p,
+                                                                                    T.count.p, d.p);
+            PB_LAUNCH_CHECK();
+        }
+        unsigned long long h = 0;
+        PB_CUDA_TRY(cudaMemcpyAsync(&h, d.p, 8, cudaMemcpyDeviceToHost, s));
+        PB_CUDA_TRY(cudaStreamSynchronize(s));
+        Pr.p2p_pairs = (int64_t)h;
+    }
+    // P2P leaf indices per target (ascending = pre-order)
+    TmpBuf<int32_t> pleaf(std::max<int64_t>(1, Pr.n_p2p), s);
+    if (Pr.n_p2p) {
+        node_to_leaf_kernel<<<div_up(Pr.n_p2p, 256), 256, 0, s>>>(Pr.n_p2p, Pr.p2p_node.p, T.node_leaf.p, pleaf.p);
+        PB_LAUNCH_CHECK();
+    }
+    // warp-group unions
+    const int64_t ng = (m + 31) / 32;
+    auto unions = [&](const int64_t *ptr, const int32_t *ent, int nidx, DevBuf<int64_t> &gptr, DevBuf<int2> &gent,
+                      int64_t &total) {
+        TmpBuf<int32_t> gc(std::max<int64_t>(1, ng), s);
+        gptr.alloc(ng + 1);
+        const size_t shm = kUnionChunk * sizeof(uint32_t);
+        if (ng) {
+            group_union_kernel<false><<<(unsigned)ng, 32, shm, s>>>(m, ng, ptr, ent, nidx, gc.p, nullptr, nullptr);
+            PB_LAUNCH_CHECK();
+        }
+        exclusive_scan_i32_to_i64(gc.p, gptr.p, ng, s);
+        total = read_i64(gptr.p + ng, s);
+        gent.alloc(std::max<int64_t>(1, total));
+        if (ng) {
+            group_union_kernel<true><<<(unsigned)ng, 32, shm, s>>>(m, ng, ptr, ent, nidx, nullptr, gptr.p, gent.p);
+            PB_LAUNCH_CHECK();
+        }
+    };
+    unions(Pr.p2p_ptr.p, pleaf.p, T.nleaves, Pr.gp2p_ptr, Pr.gp2p, Pr.n_gp2p);
+    unions(Pr.m2p_ptr.p, Pr.m2p_node.p, T.nnodes, Pr.gm2p_ptr, Pr.gm2p, Pr.n_gm2p);
+    // near-singular lists
+    TmpBuf<int32_t> nc(m, s), ex(m, s), se(m, s);
+    TmpBuf<double> reach_d(1, s);
+    reach_kernel<<<1, 1024, 0, s>>>(src.n, src.verts.p, src.tris.p, src.cen.p, src.L.p, prm.thres, reach_d.p);
+    PB_LAUNCH_CHECK();
+    double reach = 0.0;
+    PB_CUDA_TRY(cudaMemcpyAsync(&reach, reach_d.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PB_CUDA_TRY(cudaStreamSynchronize(s));
+    Pr.near_ptr.alloc(m + 1);
+    if (m) {
+        near_kernel<false><<<div_up(m, 128), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self,
+                                                          Pr.p2p_ptr.p, pleaf.p, T.leaf_node.p, T.start.p, T.count.p,
+                                                          T.perm.p, T.point_leaf.p, src.cen.p, src.L.p, prm.thres,
+                                                          nc.p, ex.p, se.p, nullptr, nullptr, Pr.m2p_ptr.p,
+                                                          Pr.m2p_node.p, T.centre.p, T.rb2.p, reach);
+        PB_LAUNCH_CHECK();
+    }
+    exclusive_scan_i32_to_i64(nc.p, Pr.near_ptr.p, m, s);
+    Pr.n_near = read_i64(Pr.near_ptr.p + m, s);
+    Pr.near_excl = device_sum_i32(ex.p, m, s);
+    Pr.self_excl = device_sum_i32(se.p, m, s);
+    Pr.near_panel.alloc(std::max<int64_t>(1, Pr.n_near));
+    if (m) {
+        near_kernel<true><<<div_up(m, 128), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self,
+                                                         Pr.p2p_ptr.p, pleaf.p, T.leaf_node.p, T.start.p, T.count.p,
+                                                         T.perm.p, T.point_leaf.p, src.cen.p, src.L.p, prm.thres,
+                                                         nullptr, nullptr, nullptr, Pr.near_ptr.p, Pr.near_panel.p,
+                                                         Pr.m2p_ptr.p, Pr.m2p_node.p, T.centre.p, T.rb2.p, reach);
+        PB_LAUNCH_CHECK();
+    }
+    PB_CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+}  // namespace pb

@@ -1,0 +1,22 @@
+// Setup-phase entry points of the octree and interaction-list code (tree.cu).
+#pragma once
+
+#include "model.cuh"
+
+namespace pb {
+
+// Root cube of the points, Morton keys and the (key, index) sort.
+void morton_sort(const double *d_points, int64_t n, cudaStream_t s, double corner[3], double &side,
+                 DevBuf<uint64_t> &keys, DevBuf<int32_t> &perm);
+// Octree over the K Gauss points of every panel of S (point j*K + k).
+void build_tree(Tree &T, const SurfDev &S, int K, int ncrit, cudaStream_t s);
+// Morton-sorted copy of target positions d_x (n * 3, input order).
+void build_targets(Targets &G, const double *d_x, int64_t n, int surface, cudaStream_t s);
+// M2P / P2P lists, their warp-group unions and the near-singular lists of
+// targets G against tree T (built over surface src).  use_self: the targets are
+// the panels of the tree's own surface, so each skips its own panel.
+void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
+                 cudaStream_t s);
+int64_t read_i64(const int64_t *d, cudaStream_t s);
+
+}  // namespace pb

@@ -1,0 +1,703 @@
+// Treecode evaluation kernels: one application of the BEM operator (Sec. 2.3,
+// Eqs. nbody, taylor, multexp, MAC; "Treecode-accelerated BEM").
+//
+// Sources are the Gauss points y_p of the panels of one surface, with
+// single-layer strength s_p = w_p A_j dphi_j and double-layer dipole
+// d_p = w_p A_j phi_j n_j.  For a target x and kernel G (Laplace 1/(4 pi r) or
+// Yukawa exp(-kappa r)/(4 pi r)) every block sum is split into
+//   V(x) = sum_p s_p G(x, y_p)            K(x) = sum_p d_p . grad_y G(x, y_p)
+// evaluated by direct summation over the leaves that fail the MAC (P2P) and
+// by the Taylor expansion sum_k a^k M^k, sum_k a^k D^k over the accepted boxes
+// (M2P), with M^k = sum_p s_p (y_p - y_c)^k and
+// D^k = sum_p sum_l d_{p,l} k_l (y_p - y_c)^(k - e_l) (P2M at the leaves,
+// M2M shifts towards the root).
+//
+// The Taylor coefficients a^k = (1/k!) D_y^k G(x, y_c) follow from the
+// recurrences (u = y_c - x, r = |u|, n = |k|; b^k the coefficients of
+// exp(-kappa r); both start from a^0 = exp(-kappa r)/r, b^0 = exp(-kappa r)):
+//   n r^2 a^k = -(2n-1) sum_j u_j a^(k-e_j) - (n-1) sum_j a^(k-2e_j)
+//               - kappa (sum_j u_j b^(k-e_j) + sum_j b^(k-2e_j))
+//   n b^k     = -kappa (sum_j u_j a^(k-e_j) + sum_j a^(k-2e_j))
+// obtained by taking Taylor coefficients of r^2 d_j G = -u_j (G + kappa H),
+// d_j H = -kappa u_j G (H = exp(-kappa r)); with kappa = 0 this is the Laplace
+// recurrence of Duan & Krasny, with kappa > 0 the screened-Coulomb form of
+// Li, Johnston & Krasny that the paper cites.
+#include <algorithm>
+
+#include "treecode.cuh"
+
+namespace pb {
+
+namespace {
+
+__constant__ int c_terms[3 * 455];   // (k1, k2, k3) of every term, graded order
+__constant__ double c_binom[13][13];
+
+__host__ __device__ constexpr int term_index(int k1, int k2, int k3) {
+    // graded by n = |k|, then k1 descending, then k2 descending
+    return (k1 + k2 + k3) * (k1 + k2 + k3 + 1) * (k1 + k2 + k3 + 2) / 6 + (k2 + k3) * (k2 + k3 + 1) / 2 + k3;
+}
+
+// ---------------------------------------------------------------- source strengths
+__global__ void strengths64_kernel(int64_t n, const double *__restrict__ ys, const double *__restrict__ was,
+                                   const int32_t *__restrict__ pids, const double *__restrict__ nrm,
+                                   const double *__restrict__ phi, const double *__restrict__ dphi,
+                                   double *__restrict__ src) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int j = pids[q];
+    const double w = was[q];
+    const double f = w * phi[j];
+    double *o = src + 8 * q;
+    o[0] = ys[3 * q]; o[1] = ys[3 * q + 1]; o[2] = ys[3 * q + 2];
+    o[3] = w * dphi[j];
+    o[4] = f * nrm[3 * j]; o[5] = f * nrm[3 * j + 1]; o[6] = f * nrm[3 * j + 2];
+    o[7] = (double)j;
+}
+
+__global__ void strengths32_kernel(int64_t n, const float4 *__restrict__ pos, const double *__restrict__ was,
+                                   const int32_t *__restrict__ pids, const double *__restrict__ nrm,
+                                   const double *__restrict__ phi, const double *__restrict__ dphi,
+                                   float4 *__restrict__ A, float4 *__restrict__ B) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int j = pids[q];
+    const double w = was[q];
+    const double f = w * phi[j];
+    const float4 p = pos[q];
+    A[q] = make_float4(p.x, p.y, p.z, (float)(w * dphi[j]));
+    B[q] = make_float4((float)(f * nrm[3 * j]), (float)(f * nrm[3 * j + 1]), (float)(f * nrm[3 * j + 2]),
+                       __int_as_float(j));
+}
+
+// ---------------------------------------------------------------- P2M (leaves)
+template <typename T>
+struct SrcView;
+
+template <>
+struct SrcView<double> {
+    const double *src;
+    __device__ void get(int64_t q, const double c[3], double &x, double &y, double &z, double &s, double &dx,
+                        double &dy, double &dz) const {
+        const double *o = src + 8 * q;
+        x = o[0] - c[0]; y = o[1] - c[1]; z = o[2] - c[2];
+        s = o[3]; dx = o[4]; dy = o[5]; dz = o[6];
+    }
+};
+
+template <>
+struct SrcView<float> {
+    const float4 *A, *B;
+    __device__ void get(int64_t q, const float c[3], float &x, float &y, float &z, float &s, float &dx, float &dy,
+                        float &dz) const {
+        const float4 a = A[q], b = B[q];
+        x = a.x - c[0]; y = a.y - c[1]; z = a.z - c[2];
+        s = a.w; dx = b.x; dy = b.y; dz = b.z;
+    }
+};
+
+constexpr int kP2MChunk = 32;
+
+// One block per leaf; each thread owns up to 4 moment terms and sums over the
+// leaf's sources in order (deterministic).
+template <typename T>
+__global__ void __launch_bounds__(128) p2m_kernel(int nleaves, const int32_t *__restrict__ leaf_node,
+                                                  const int64_t *__restrict__ start, const int64_t *__restrict__ count,
+                                                  const double *__restrict__ centre, double ox, double oy, double oz,
+                                                  SrcView<T> sv, int P, int NT, T *__restrict__ mom) {
+    __shared__ T pw[3][kP2MChunk][kMaxP + 1];
+    __shared__ T sd[kP2MChunk][4];
+    const int node = leaf_node[blockIdx.x];
+    const int64_t s0 = start[node], cnt = count[node];
+    T c[3];
+    if (sizeof(T) == 8) {
+        c[0] = (T)centre[3 * node]; c[1] = (T)centre[3 * node + 1]; c[2] = (T)centre[3 * node + 2];
+    } else {
+        c[0] = (T)(centre[3 * node] - ox); c[1] = (T)(centre[3 * node + 1] - oy); c[2] = (T)(centre[3 * node + 2] - oz);
+    }
+    T accM[4] = {0, 0, 0, 0}, accD[4] = {0, 0, 0, 0};
+    for (int64_t c0 = 0; c0 < cnt; c0 += kP2MChunk) {
+        const int m = (int)(cnt - c0 < kP2MChunk ? cnt - c0 : kP2MChunk);
+        __syncthreads();
+        if (threadIdx.x < m) {
+            T x, y, z, s, dx, dy, dz;
+            sv.get(s0 + c0 + threadIdx.x, c, x, y, z, s, dx, dy, dz);
+            T px = 1, py = 1, pz = 1;
+            for (int e = 0; e <= P; ++e) {
+                pw[0][threadIdx.x][e] = px; pw[1][threadIdx.x][e] = py; pw[2][threadIdx.x][e] = pz;
+                px *= x; py *= y; pz *= z;
+            }
+            sd[threadIdx.x][0] = s; sd[threadIdx.x][1] = dx; sd[threadIdx.x][2] = dy; sd[threadIdx.x][3] = dz;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int k = threadIdx.x + 128 * r;
+            if (k >= NT) break;
+            const int k1 = c_terms[3 * k], k2 = c_terms[3 * k + 1], k3 = c_terms[3 * k + 2];
+            T aM = accM[r], aD = accD[r];
+            for (int j = 0; j < m; ++j) {
+                const T mono = pw[0][j][k1] * pw[1][j][k2] * pw[2][j][k3];
+                aM += sd[j][0] * mono;
+                T dsum = 0;
+                if (k1) dsum += sd[j][1] * (T)k1 * pw[0][j][k1 - 1] * pw[1][j][k2] * pw[2][j][k3];
+                if (k2) dsum += sd[j][2] * (T)k2 * pw[0][j][k1] * pw[1][j][k2 - 1] * pw[2][j][k3];
+                if (k3) dsum += sd[j][3] * (T)k3 * pw[0][j][k1] * pw[1][j][k2] * pw[2][j][k3 - 1];
+                aD += dsum;
+            }
+            accM[r] = aM;
+            accD[r] = aD;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int k = threadIdx.x + 128 * r;
+        if (k >= NT) break;
+        mom[(int64_t)node * 2 * NT + k] = accM[r];
+        mom[(int64_t)node * 2 * NT + NT + k] = accD[r];
+    }
+}
+
+// ---------------------------------------------------------------- M2M (one level, bottom-up)
+// M_parent^k = sum_children sum_{l <= k} C(k, l) (y_child - y_parent)^(k-l) M_child^l;
+// the dipole moments D shift with the same rule.
+template <typename T>
+__global__ void m2m_kernel(int nb, int nodes_begin, const int32_t *__restrict__ first_child,
+                           const int32_t *__restrict__ nchild, const double *__restrict__ centre, int P, int NT,
+                           T *__restrict__ mom) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = (int)(gid / NT), k = (int)(gid % NT);
+    if (t >= nb) return;
+    const int b = nodes_begin + t;
+    const int nc = nchild[b];
+    if (nc == 0) return;
+    const int k1 = c_terms[3 * k], k2 = c_terms[3 * k + 1], k3 = c_terms[3 * k + 2];
+    T accM = 0, accD = 0;
+    for (int c = first_child[b]; c < first_child[b] + nc; ++c) {
+        const T h[3] = {(T)(centre[3 * c] - centre[3 * b]), (T)(centre[3 * c + 1] - centre[3 * b + 1]),
+                        (T)(centre[3 * c + 2] - centre[3 * b + 2])};
+        const T *mc = mom + (int64_t)c * 2 * NT;
+        T hp[3][kMaxP + 1];
+        for (int a = 0; a < 3; ++a) {
+            hp[a][0] = 1;
+            for (int e = 1; e <= P; ++e) hp[a][e] = hp[a][e - 1] * h[a];
+        }
+        for (int l1 = 0; l1 <= k1; ++l1)
+            for (int l2 = 0; l2 <= k2; ++l2)
+                for (int l3 = 0; l3 <= k3; ++l3) {
+                    const T coef = (T)(c_binom[k1][l1] * c_binom[k2][l2] * c_binom[k3][l3]) * hp[0][k1 - l1] *
+                                   hp[1][k2 - l2] * hp[2][k3 - l3];
+                    const int li = term_index(l1, l2, l3);
+                    accM += coef * mc[li];
+                    accD += coef * mc[NT + li];
+                }
+    }
+    mom[(int64_t)b * 2 * NT + k] = accM;
+    mom[(int64_t)b * 2 * NT + NT + k] = accD;
+}
+
+// ---------------------------------------------------------------- P2P, FP32 (mixed precision)
+// One warp per group of 32 consecutive sorted targets.  The warp walks the
+// union of its targets' direct-sum leaves; each leaf's sources are staged 32 at
+// a time in shared memory and broadcast to all lanes, and a lane accumulates
+// only the leaves in its own list (lane mask).  FP32 partial sums of each
+// 32-source chunk are added into (hi, lo) FP32 pairs with Neumaier's
+// compensated summation.
+struct KSet {
+    float kap[2];
+};
+
+__device__ __forceinline__ void comp_add(float &hi, float &lo, float v) {
+    const float t = hi + v;
+    lo += (fabsf(hi) >= fabsf(v)) ? ((hi - t) + v) : ((v - t) + hi);
+    hi = t;
+}
+
+template <int NK, bool Y0, bool Y1>
+__global__ void __launch_bounds__(128) p2p32_kernel(int64_t ntg, int64_t ngroups, const double *__restrict__ xs,
+                                                    double ox, double oy, double oz, const int32_t *__restrict__ selfp,
+                                                    int use_self, const int64_t *__restrict__ gptr,
+                                                    const int2 *__restrict__ gent, const int32_t *__restrict__ leaf_node,
+                                                    const int64_t *__restrict__ start, const int64_t *__restrict__ count,
+                                                    const float4 *__restrict__ A, const float4 *__restrict__ B,
+                                                    KSet ks, double *__restrict__ VK0, double *__restrict__ VK1) {
+    __shared__ float4 sA[4][32], sB[4][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * 4 + warp;
+    if (g >= ngroups) return;
+    const int64_t t = g * 32 + lane;
+    const bool valid = t < ntg;
+    float tx = 0.f, ty = 0.f, tz = 0.f;
+    int me = -1;
+    if (valid) {
+        tx = (float)(xs[3 * t] - ox);
+        ty = (float)(xs[3 * t + 1] - oy);
+        tz = (float)(xs[3 * t + 2] - oz);
+        if (use_self) me = selfp[t];
+    }
+    const float k0 = ks.kap[0], k1 = ks.kap[1];
+    const float l2e0 = -k0 * 1.4426950408889634f, l2e1 = -k1 * 1.4426950408889634f;
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    const int64_t e0 = gptr[g], e1 = gptr[g + 1];
+    for (int64_t e = e0; e < e1; ++e) {
+        const int2 en = gent[e];
+        const bool active = valid && ((en.y >> lane) & 1);
+        const int node = leaf_node[en.x];
+        const int64_t s0 = start[node];
+        const int cnt = (int)count[node];
+        for (int c0 = 0; c0 < cnt; c0 += 32) {
+            const int m = min(32, cnt - c0);
+            if (lane < m) {
+                sA[warp][lane] = A[s0 + c0 + lane];
+                sB[warp][lane] = B[s0 + c0 + lane];
+            }
+            __syncwarp();
+            if (active) {
+                float p[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+                for (int j = 0; j < m; ++j) {
+                    const float4 a = sA[warp][j];
+                    const float4 b = sB[warp][j];
+                    const float dx = tx - a.x, dy = ty - a.y, dz = tz - a.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float inv = (__float_as_int(b.w) == me) ? 0.f : rsqrtf(r2);
+                    const float sv = a.w * inv;
+                    const float rd = fmaf(dx, b.x, fmaf(dy, b.y, dz * b.z));
+                    const float kv = rd * (inv * inv * inv);
+                    if (!Y0) {
+                        p[0] += sv;
+                        p[1] += kv;
+                    } else {
+                        const float rho = r2 * inv;
+                        const float ex = exp2f(l2e0 * rho);
+                        p[0] = fmaf(sv, ex, p[0]);
+                        p[1] = fmaf(kv * ex, fmaf(k0, rho, 1.f), p[1]);
+                    }
+                    if (NK == 2) {
+                        if (!Y1) {
+                            p[2] += sv;
+                            p[3] += kv;
+                        } else {
+                            const float rho = r2 * inv;
+                            const float ex = exp2f(l2e1 * rho);
+                            p[2] = fmaf(sv, ex, p[2]);
+                            p[3] = fmaf(kv * ex, fmaf(k1, rho, 1.f), p[3]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < 2 * NK; ++a) comp_add(hi[a], lo[a], p[a]);
+            }
+            __syncwarp();
+        }
+    }
+    if (valid) {
+        VK0[t] = ((double)hi[0] + (double)lo[0]) * kInv4Pi;
+        VK0[ntg + t] = ((double)hi[1] + (double)lo[1]) * kInv4Pi;
+        if (NK == 2) {
+            VK1[t] = ((double)hi[2] + (double)lo[2]) * kInv4Pi;
+            VK1[ntg + t] = ((double)hi[3] + (double)lo[3]) * kInv4Pi;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- P2P, FP64
+template <int NK, bool Y0, bool Y1>
+__global__ void __launch_bounds__(128) p2p64_kernel(int64_t ntg, int64_t ngroups, const double *__restrict__ xs,
+                                                    const int32_t *__restrict__ selfp, int use_self,
+                                                    const int64_t *__restrict__ gptr, const int2 *__restrict__ gent,
+                                                    const int32_t *__restrict__ leaf_node,
+                                                    const int64_t *__restrict__ start, const int64_t *__restrict__ count,
+                                                    const double *__restrict__ src, double kap0, double kap1,
+                                                    double *__restrict__ VK0, double *__restrict__ VK1) {
+    __shared__ double4 sA[4][32], sB[4][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * 4 + warp;
+    if (g >= ngroups) return;
+    const int64_t t = g * 32 + lane;
+    const bool valid = t < ntg;
+    double tx = 0, ty = 0, tz = 0;
+    int me = -1;
+    if (valid) {
+        tx = xs[3 * t]; ty = xs[3 * t + 1]; tz = xs[3 * t + 2];
+        if (use_self) me = selfp[t];
+    }
+    double acc[4] = {0, 0, 0, 0};
+    const int64_t e0 = gptr[g], e1 = gptr[g + 1];
+    const double4 *src4 = reinterpret_cast<const double4 *>(src);
+    for (int64_t e = e0; e < e1; ++e) {
+        const int2 en = gent[e];
+        const bool active = valid && ((en.y >> lane) & 1);
+        const int node = leaf_node[en.x];
+        const int64_t s0 = start[node];
+        const int cnt = (int)count[node];
+        for (int c0 = 0; c0 < cnt; c0 += 32) {
+            const int m = min(32, cnt - c0);
+            if (lane < m) {
+                sA[warp][lane] = src4[2 * (s0 + c0 + lane)];
+                sB[warp][lane] = src4[2 * (s0 + c0 + lane) + 1];
+            }
+            __syncwarp();
+            if (active) {
+                for (int j = 0; j < m; ++j) {
+                    const double4 a = sA[warp][j];
+                    const double4 b = sB[warp][j];
+                    if ((int)b.w == me) continue;
+                    const double dx = tx - a.x, dy = ty - a.y, dz = tz - a.z;
+                    const double r2 = dx * dx + dy * dy + dz * dz;
+                    const double rho = sqrt(r2);
+                    const double inv = 1.0 / rho;
+                    const double sv = a.w * inv;
+                    const double rd = dx * b.x + dy * b.y + dz * b.z;
+                    const double kv = rd * inv * inv * inv;
+                    if (!Y0) {
+                        acc[0] += sv;
+                        acc[1] += kv;
+                    } else {
+                        const double ex = exp(-kap0 * rho);
+                        acc[0] += sv * ex;
+                        acc[1] += kv * ex * (1.0 + kap0 * rho);
+                    }
+                    if (NK == 2) {
+                        if (!Y1) {
+                            acc[2] += sv;
+                            acc[3] += kv;
+                        } else {
+                            const double ex = exp(-kap1 * rho);
+                            acc[2] += sv * ex;
+                            acc[3] += kv * ex * (1.0 + kap1 * rho);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (valid) {
+        VK0[t] = acc[0] * kInv4Pi;
+        VK0[ntg + t] = acc[1] * kInv4Pi;
+        if (NK == 2) {
+            VK1[t] = acc[2] * kInv4Pi;
+            VK1[ntg + t] = acc[3] * kInv4Pi;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- M2P
+// a^k and contraction with the box moments, fully unrolled for a fixed order P
+// so that every coefficient index is a compile-time constant.
+template <int P, bool YUK, typename T>
+__device__ __forceinline__ void m2p_eval(T ux, T uy, T uz, T kappa, const T *__restrict__ mom, T &V, T &K) {
+    constexpr int NT = (P + 1) * (P + 2) * (P + 3) / 6;
+    T a[NT];
+    T b[YUK ? NT : 1];
+    const T r2 = ux * ux + uy * uy + uz * uz;
+    T rinv;
+    if constexpr (sizeof(T) == 4) rinv = rsqrtf(r2); else rinv = rsqrt(r2);
+    const T ir2 = rinv * rinv;
+    T e0 = (T)1;
+    if (YUK) {
+        if constexpr (sizeof(T) == 4) e0 = __expf(-kappa * r2 * rinv); else e0 = exp(-kappa * r2 * rinv);
+    }
+    a[0] = e0 * rinv;
+    if (YUK) b[0] = e0;
+    V = a[0] * mom[0];
+    K = a[0] * mom[NT];
+#pragma unroll
+    for (int n = 1; n <= P; ++n) {
+        const T c1 = (T)(2 * n - 1) / (T)n, c2 = (T)(n - 1) / (T)n;
+        const T kn = kappa / (T)n;
+#pragma unroll
+        for (int k1 = n; k1 >= 0; --k1) {
+#pragma unroll
+            for (int k2 = n - k1; k2 >= 0; --k2) {
+                const int k3 = n - k1 - k2;
+                const int i = term_index(k1, k2, k3);
+                T s1 = 0, s2 = 0, t1 = 0, t2 = 0;
+                if (k1 >= 1) { s1 += ux * a[term_index(k1 - 1, k2, k3)]; if (YUK) t1 += ux * b[term_index(k1 - 1, k2, k3)]; }
+                if (k2 >= 1) { s1 += uy * a[term_index(k1, k2 - 1, k3)]; if (YUK) t1 += uy * b[term_index(k1, k2 - 1, k3)]; }
+                if (k3 >= 1) { s1 += uz * a[term_index(k1, k2, k3 - 1)]; if (YUK) t1 += uz * b[term_index(k1, k2, k3 - 1)]; }
+                if (k1 >= 2) { s2 += a[term_index(k1 - 2, k2, k3)]; if (YUK) t2 += b[term_index(k1 - 2, k2, k3)]; }
+                if (k2 >= 2) { s2 += a[term_index(k1, k2 - 2, k3)]; if (YUK) t2 += b[term_index(k1, k2 - 2, k3)]; }
+                if (k3 >= 2) { s2 += a[term_index(k1, k2, k3 - 2)]; if (YUK) t2 += b[term_index(k1, k2, k3 - 2)]; }
+                T ai = c1 * s1 + c2 * s2;
+                if (YUK) ai += kn * (t1 + t2);
+                a[i] = -ai * ir2;
+                if (YUK) b[i] = -kn * (s1 + s2);
+                V += a[i] * mom[i];
+                K += a[i] * mom[NT + i];
+            }
+        }
+    }
+}
+
+// Runtime-order variant for orders without a compiled specialisation (local arrays).
+template <bool YUK, typename T>
+__device__ void m2p_eval_rt(int P, T ux, T uy, T uz, T kappa, const T *__restrict__ mom, T &V, T &K) {
+    const int NT = (P + 1) * (P + 2) * (P + 3) / 6;
+    T a[455];
+    T b[YUK ? 455 : 1];
+    const T r2 = ux * ux + uy * uy + uz * uz;
+    const T r = sqrt(r2);
+    const T ir2 = (T)1 / r2;
+    const T e0 = YUK ? (T)exp(-kappa * r) : (T)1;
+    a[0] = e0 / r;
+    if (YUK) b[0] = e0;
+    V = a[0] * mom[0];
+    K = a[0] * mom[NT];
+    for (int i = 1; i < NT; ++i) {
+        const int k1 = c_terms[3 * i], k2 = c_terms[3 * i + 1], k3 = c_terms[3 * i + 2];
+        const int n = k1 + k2 + k3;
+        T s1 = 0, s2 = 0, t1 = 0, t2 = 0;
+        if (k1 >= 1) { s1 += ux * a[term_index(k1 - 1, k2, k3)]; if (YUK) t1 += ux * b[term_index(k1 - 1, k2, k3)]; }
+        if (k2 >= 1) { s1 += uy * a[term_index(k1, k2 - 1, k3)]; if (YUK) t1 += uy * b[term_index(k1, k2 - 1, k3)]; }
+        if (k3 >= 1) { s1 += uz * a[term_index(k1, k2, k3 - 1)]; if (YUK) t1 += uz * b[term_index(k1, k2, k3 - 1)]; }
+        if (k1 >= 2) { s2 += a[term_index(k1 - 2, k2, k3)]; if (YUK) t2 += b[term_index(k1 - 2, k2, k3)]; }
+        if (k2 >= 2) { s2 += a[term_index(k1, k2 - 2, k3)]; if (YUK) t2 += b[term_index(k1, k2 - 2, k3)]; }
+        if (k3 >= 2) { s2 += a[term_index(k1, k2, k3 - 2)]; if (YUK) t2 += b[term_index(k1, k2, k3 - 2)]; }
+        T ai = ((T)(2 * n - 1) * s1 + (T)(n - 1) * s2) / (T)n;
+        if (YUK) ai += kappa / (T)n * (t1 + t2);
+        a[i] = -ai * ir2;
+        if (YUK) b[i] = -kappa / (T)n * (s1 + s2);
+        V += a[i] * mom[i];
+        K += a[i] * mom[NT + i];
+    }
+}
+
+// One warp per group of 32 sorted targets walking the union of their
+// accepted boxes; each lane evaluates the boxes of its own list.
+template <int P, bool YUK, typename T>
+__global__ void __launch_bounds__(128) m2p_kernel(int64_t ntg, int64_t ngroups, int Prt, const double *__restrict__ xs,
+                                                  double ox, double oy, double oz, const int64_t *__restrict__ gptr,
+                                                  const int2 *__restrict__ gent, const double *__restrict__ centre,
+                                                  const T *__restrict__ mom, double kappa, double *__restrict__ VK) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * 4 + warp;
+    if (g >= ngroups) return;
+    const int64_t t = g * 32 + lane;
+    const bool valid = t < ntg;
+    const int Pe = P >= 0 ? P : Prt;
+    const int NT = (Pe + 1) * (Pe + 2) * (Pe + 3) / 6;
+    double x = 0, y = 0, z = 0;
+    if (valid) {
+        x = xs[3 * t] - ox; y = xs[3 * t + 1] - oy; z = xs[3 * t + 2] - oz;
+    }
+    const T tx = (T)x, ty = (T)y, tz = (T)z;
+    double accV = 0, accK = 0;
+    for (int64_t e = gptr[g]; e < gptr[g + 1]; ++e) {
+        const int2 en = gent[e];
+        if (!(valid && ((en.y >> lane) & 1))) continue;
+        const int b = en.x;
+        const T ux = (T)(centre[3 * b] - ox) - tx;
+        const T uy = (T)(centre[3 * b + 1] - oy) - ty;
+        const T uz = (T)(centre[3 * b + 2] - oz) - tz;
+        T V, K;
+        if constexpr (P >= 0) m2p_eval<(P >= 0 ? P : 0), YUK, T>(ux, uy, uz, (T)kappa, mom + (int64_t)b * 2 * NT, V, K);
+        else m2p_eval_rt<YUK, T>(Prt, ux, uy, uz, (T)kappa, mom + (int64_t)b * 2 * NT, V, K);
+        accV += (double)V;
+        accK += (double)K;
+    }
+    if (valid) {
+        VK[t] += accV * kInv4Pi;
+        VK[ntg + t] += accK * kInv4Pi;
+    }
+}
+
+// ---------------------------------------------------------------- near field and combine
+__global__ void near_apply_kernel(int64_t ntg, const int64_t *__restrict__ ptr, const int32_t *__restrict__ pan,
+                                  const double *__restrict__ dV, const double *__restrict__ dK,
+                                  const double *__restrict__ selfV, const int32_t *__restrict__ selfp, int use_self,
+                                  const double *__restrict__ phi, const double *__restrict__ dphi,
+                                  double *__restrict__ VK) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntg) return;
+    double V = VK[i], K = VK[ntg + i];
+    for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
+        const int j = pan[e];
+        V += dV[e] * dphi[j];
+        K += dK[e] * phi[j];
+    }
+    if (use_self) {
+        const int me = selfp[i];
+        V += selfV[me] * dphi[me];
+    }
+    VK[i] = V;
+    VK[ntg + i] = K;
+}
+
+__global__ void combine_kernel(int64_t n, const int32_t *__restrict__ rank, const double *__restrict__ phi_s,
+                               double half, CombineRow row, double *__restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int r = rank[i];
+    double v = phi_s ? half * phi_s[i] : 0.0;
+    for (int k = 0; k < row.nterm; ++k) {
+        const CombineTerm &tm = row.term[k];
+        v += tm.cK * tm.VK[tm.ntg + r] + tm.cV * tm.VK[r];
+    }
+    y[i] = v;
+}
+
+template <typename T>
+void launch_m2p_typed(int P, bool yuk, int64_t ntg, int64_t ng, const double *xs, const double o[3], const Pair &Pr,
+                      const Tree &Tr, const T *mom, double kappa, double *VK, cudaStream_t s) {
+    const unsigned grid = (unsigned)((ng + 3) / 4);
+#define PB_M2P_CASE(PP)                                                                                     \
+    case PP:                                                                                                \
+        if (yuk) m2p_kernel<PP, true, T><<<grid, 128, 0, s>>>(ntg, ng, P, xs, o[0], o[1], o[2],            \
+                                                              Pr.gm2p_ptr.p, Pr.gm2p.p, Tr.centre.p, mom,   \
+                                                              kappa, VK);                                  \
+        else m2p_kernel<PP, false, T><<<grid, 128, 0, s>>>(ntg, ng, P, xs, o[0], o[1], o[2], Pr.gm2p_ptr.p, \
+                                                           Pr.gm2p.p, Tr.centre.p, mom, kappa, VK);         \
+        break;
+    switch (P) {
+        PB_M2P_CASE(0)
+        PB_M2P_CASE(1)
+        PB_M2P_CASE(2)
+        PB_M2P_CASE(3)
+        PB_M2P_CASE(4)
+        PB_M2P_CASE(5)
+        PB_M2P_CASE(6)
+        PB_M2P_CASE(7)
+        PB_M2P_CASE(8)
+        default:
+            if (yuk) m2p_kernel<-1, true, T><<<grid, 128, 0, s>>>(ntg, ng, P, xs, o[0], o[1], o[2], Pr.gm2p_ptr.p,
+                                                                  Pr.gm2p.p, Tr.centre.p, mom, kappa, VK);
+            else m2p_kernel<-1, false, T><<<grid, 128, 0, s>>>(ntg, ng, P, xs, o[0], o[1], o[2], Pr.gm2p_ptr.p,
+                                                               Pr.gm2p.p, Tr.centre.p, mom, kappa, VK);
+    }
+#undef PB_M2P_CASE
+    PB_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+void upload_term_tables() {
+    int terms[3 * 455];
+    int i = 0;
+    for (int n = 0; n <= kMaxP; ++n)
+        for (int k1 = n; k1 >= 0; --k1)
+            for (int k2 = n - k1; k2 >= 0; --k2) {
+                const int k3 = n - k1 - k2;
+                if (term_index(k1, k2, k3) != i) fail(PB_ECUDA, "term table layout");
+                terms[3 * i] = k1; terms[3 * i + 1] = k2; terms[3 * i + 2] = k3;
+                ++i;
+            }
+    PB_CUDA_TRY(cudaMemcpyToSymbol(c_terms, terms, sizeof(terms)));
+    double bin[13][13] = {};
+    for (int n = 0; n <= 12; ++n) {
+        bin[n][0] = 1.0;
+        for (int k = 1; k <= n; ++k) bin[n][k] = bin[n][k - 1] * (n - k + 1) / k;
+    }
+    PB_CUDA_TRY(cudaMemcpyToSymbol(c_binom, bin, sizeof(bin)));
+}
+
+void compute_strengths(Tree &Tr, const SurfDev &S, const double *phi, const double *dphi, bool mixed, cudaStream_t s) {
+    const int64_t n = Tr.npts;
+    if (!n) return;
+    if (mixed) {
+        strengths32_kernel<<<div_up(n, 256), 256, 0, s>>>(n, Tr.pos32.p, Tr.was.p, Tr.pids.p, S.nrm.p, phi, dphi,
+                                                          Tr.srcA32.p, Tr.srcB32.p);
+    } else {
+        strengths64_kernel<<<div_up(n, 256), 256, 0, s>>>(n, Tr.ys.p, Tr.was.p, Tr.pids.p, S.nrm.p, phi, dphi,
+                                                          Tr.src64.p);
+    }
+    PB_LAUNCH_CHECK();
+}
+
+void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s) {
+    const int NT = nterms(P);
+    if (mixed) {
+        Tr.mom32.alloc((size_t)Tr.nnodes * 2 * NT);
+        SrcView<float> sv{Tr.srcA32.p, Tr.srcB32.p};
+        p2m_kernel<float><<<Tr.nleaves, 128, 0, s>>>(Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p,
+                                                     Tr.origin[0], Tr.origin[1], Tr.origin[2], sv, P, NT, Tr.mom32.p);
+    } else {
+        Tr.mom64.alloc((size_t)Tr.nnodes * 2 * NT);
+        SrcView<double> sv{Tr.src64.p};
+        p2m_kernel<double><<<Tr.nleaves, 128, 0, s>>>(Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p,
+                                                      Tr.origin[0], Tr.origin[1], Tr.origin[2], sv, P, NT, Tr.mom64.p);
+    }
+    PB_LAUNCH_CHECK();
+    for (int l = Tr.nlevels - 2; l >= 0; --l) {
+        const int b0 = Tr.level_off[l], nb = Tr.level_off[l + 1] - b0;
+        const int64_t work = (int64_t)nb * NT;
+        if (mixed)
+            m2m_kernel<float><<<div_up(work, 128), 128, 0, s>>>(nb, b0, Tr.first_child.p, Tr.nchild.p, Tr.centre.p, P,
+                                                                NT, Tr.mom32.p);
+        else
+            m2m_kernel<double><<<div_up(work, 128), 128, 0, s>>>(nb, b0, Tr.first_child.p, Tr.nchild.p, Tr.centre.p,
+                                                                 P, NT, Tr.mom64.p);
+        PB_LAUNCH_CHECK();
+    }
+}
+
+void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self, bool mixed, cudaStream_t s) {
+    const int64_t ntg = G.n, ng = (ntg + 31) / 32;
+    if (!ng) return;
+    const unsigned grid = (unsigned)((ng + 3) / 4);
+    const int nk = (int)Pr.kappas.size();
+    const double k0 = Pr.kappas[0], k1 = nk > 1 ? Pr.kappas[1] : 0.0;
+    const bool y0 = k0 != 0.0, y1 = k1 != 0.0;
+    double *V0 = Pr.VK[0].p, *V1 = nk > 1 ? Pr.VK[1].p : nullptr;
+    const int32_t *sp = G.self_panel.p;
+    const int us = use_self ? 1 : 0;
+    if (mixed) {
+        KSet ks{{(float)k0, (float)k1}};
+#define PB_P2P32(NK, A, B)                                                                                   \
+    p2p32_kernel<NK, A, B><<<grid, 128, 0, s>>>(ntg, ng, G.xs.p, Tr.origin[0], Tr.origin[1], Tr.origin[2], sp, \
+                                                us, Pr.gp2p_ptr.p, Pr.gp2p.p, Tr.leaf_node.p, Tr.start.p,     \
+                                                Tr.count.p, Tr.srcA32.p, Tr.srcB32.p, ks, V0, V1)
+        if (nk == 1) { if (y0) PB_P2P32(1, true, false); else PB_P2P32(1, false, false); }
+        else if (!y0 && y1) PB_P2P32(2, false, true);
+        else if (y0 && !y1) PB_P2P32(2, true, false);
+        else if (y0 && y1) PB_P2P32(2, true, true);
+        else PB_P2P32(2, false, false);
+#undef PB_P2P32
+    } else {
+#define PB_P2P64(NK, A, B)                                                                                      \
+    p2p64_kernel<NK, A, B><<<grid, 128, 0, s>>>(ntg, ng, G.xs.p, sp, us, Pr.gp2p_ptr.p, Pr.gp2p.p, Tr.leaf_node.p, \
+                                                Tr.start.p, Tr.count.p, Tr.src64.p, k0, k1, V0, V1)
+        if (nk == 1) { if (y0) PB_P2P64(1, true, false); else PB_P2P64(1, false, false); }
+        else if (!y0 && y1) PB_P2P64(2, false, true);
+        else if (y0 && !y1) PB_P2P64(2, true, false);
+        else if (y0 && y1) PB_P2P64(2, true, true);
+        else PB_P2P64(2, false, false);
+#undef PB_P2P64
+    }
+    PB_LAUNCH_CHECK();
+}
+
+void launch_m2p(const Pair &Pr, const Targets &G, const Tree &Tr, int P, bool mixed, cudaStream_t s) {
+    const int64_t ntg = G.n, ng = (ntg + 31) / 32;
+    if (!ng || Pr.n_gm2p == 0) return;
+    for (size_t k = 0; k < Pr.kappas.size(); ++k) {
+        const double kap = Pr.kappas[k];
+        if (mixed) {
+            launch_m2p_typed<float>(P, kap != 0.0, ntg, ng, G.xs.p, Tr.origin, Pr, Tr, Tr.mom32.p, kap, Pr.VK[k].p, s);
+        } else {
+            const double zero[3] = {0.0, 0.0, 0.0};
+            launch_m2p_typed<double>(P, kap != 0.0, ntg, ng, G.xs.p, zero, Pr, Tr, Tr.mom64.p, kap, Pr.VK[k].p, s);
+        }
+    }
+}
+
+void launch_near(const Pair &Pr, const Targets &G, bool use_self, const double *phi, const double *dphi,
+                 cudaStream_t s) {
+    if (!G.n) return;
+    for (size_t k = 0; k < Pr.kappas.size(); ++k) {
+        near_apply_kernel<<<div_up(G.n, 128), 128, 0, s>>>(G.n, Pr.near_ptr.p, Pr.near_panel.p, Pr.dV[k].p, Pr.dK[k].p,
+                                                          use_self ? Pr.selfV[k].p : nullptr, G.self_panel.p,
+                                                          use_self ? 1 : 0, phi, dphi, Pr.VK[k].p);
+        PB_LAUNCH_CHECK();
+    }
+}
+
+void launch_combine(int64_t n, const int32_t *rank, const double *phi_s, double half, const CombineRow &row, double *y,
+                    cudaStream_t s) {
+    if (!n) return;
+    combine_kernel<<<div_up(n, 256), 256, 0, s>>>(n, rank, phi_s, half, row, y);
+    PB_LAUNCH_CHECK();
+}
+
+}  // namespace pb

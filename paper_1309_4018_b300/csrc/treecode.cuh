@@ -1,0 +1,34 @@
+// Evaluation-phase entry points of the treecode (treecode.cu).
+#pragma once
+
+#include "model.cuh"
+
+namespace pb {
+
+// One contribution cK * K + cV * V of a block sum, read at a target's sorted rank.
+struct CombineTerm {
+    const double *VK;   // V at [0, ntg), K at [ntg, 2 ntg)
+    int64_t ntg;
+    double cK, cV;
+};
+struct CombineRow {
+    int nterm;
+    CombineTerm term[8];
+};
+
+void upload_term_tables();
+// Source strengths s_p, d_p of the Gauss points of tree Tr from phi, dphi of its surface.
+void compute_strengths(Tree &Tr, const SurfDev &S, const double *phi, const double *dphi, bool mixed, cudaStream_t s);
+// P2M at the leaves, then M2M level by level to the root.
+void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s);
+// Direct sums into Pr.VK (overwrites).
+void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self, bool mixed, cudaStream_t s);
+// Far-field sums added into Pr.VK.
+void launch_m2p(const Pair &Pr, const Targets &G, const Tree &Tr, int P, bool mixed, cudaStream_t s);
+// Near-singular and self corrections added into Pr.VK.
+void launch_near(const Pair &Pr, const Targets &G, bool use_self, const double *phi, const double *dphi, cudaStream_t s);
+// y[i] = half * phi_s[i] (0 if phi_s is null) + sum_terms (cK K + cV V)[rank[i]] for i < n.
+void launch_combine(int64_t n, const int32_t *rank, const double *phi_s, double half, const CombineRow &row, double *y,
+                    cudaStream_t s);
+
+}  // namespace pb

@@ -1,0 +1,281 @@
+"""Thin ctypes binding of the pbbem C-ABI (include/pbbem.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Importing this module loads ``libpbbem.so`` (built in-tree by
+``paper_1309_4018_b300/build.py``); if it is missing the import fails loudly —
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpbbem.so")
+
+PB_OK, PB_EINVAL, PB_ENOMEM, PB_ECUDA, PB_ENOCONV, PB_ETIMEOUT, PB_ENOTSETUP = range(7)
+PB_FP64, PB_MIXED = 0, 1
+_ERRNAMES = {1: "PB_EINVAL", 2: "PB_ENOMEM", 3: "PB_ECUDA", 4: "PB_ENOCONV", 5: "PB_ETIMEOUT",
+             6: "PB_ENOTSETUP"}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"pbbem CUDA library not built: {LIB_PATH} is missing "
+                      "(run paper_1309_4018_b300/build.py)")
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class pb_params(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("K_fine", ctypes.c_int), ("N_k", ctypes.c_int),
+                ("thres", ctypes.c_double), ("P", ctypes.c_int), ("theta", ctypes.c_double),
+                ("ncrit", ctypes.c_int), ("gmres_tol", ctypes.c_double), ("restart", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class pb_result(ctypes.Structure):
+    _fields_ = [("dG_solv", ctypes.c_double), ("residual", ctypes.c_double),
+                ("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("matvecs", ctypes.c_int),
+                ("pad_", ctypes.c_int), ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("p2p_pairs", ctypes.c_int64), ("m2p_pairs", ctypes.c_int64),
+                ("near_pairs", ctypes.c_int64), ("near_excluded", ctypes.c_int64)]
+
+
+class pb_tree_info(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("n_nodes", ctypes.c_int32), ("n_leaves", ctypes.c_int32),
+                ("corner", ctypes.c_double * 3), ("side", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+_SIGS = {
+    "pb_ctx_create": ([_int, ctypes.POINTER(_vp)], _int),
+    "pb_ctx_destroy": ([_vp], None),
+    "pb_last_error": ([_vp], ctypes.c_char_p),
+    "pb_ctx_stream": ([_vp], _vp),
+    "pb_problem_create": ([_vp, ctypes.POINTER(_vp)], _int),
+    "pb_problem_destroy": ([_vp], None),
+    "pb_add_region": ([_vp, _dbl, _dbl, ctypes.POINTER(_int)], _int),
+    "pb_add_surface": ([_vp, _vp, _i64, _vp, _i64, _int, _int, ctypes.POINTER(_int)], _int),
+    "pb_set_charges": ([_vp, _vp, _vp, _i64, _int], _int),
+    "pb_setup": ([_vp, ctypes.POINTER(pb_params)], _int),
+    "pb_num_unknowns": ([_vp], _i64),
+    "pb_apply_operator": ([_vp, _vp, _vp, _int], _int),
+    "pb_rhs": ([_vp, _vp], _int),
+    "pb_solve": ([_vp, _vp, ctypes.POINTER(pb_result)], _int),
+    "pb_get_solution": ([_vp, _vp], _int),
+    "pb_reaction_potential": ([_vp, _vp, _vp], _int),
+    "pb_coulomb_energy": ([_vp, ctypes.POINTER(_dbl)], _int),
+    "pb_tree_info_get": ([_vp, _int, ctypes.POINTER(pb_tree_info)], _int),
+    "pb_tree_export": ([_vp, _int, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _int),
+    "pb_lists_export": ([_vp, _int, _int, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _int),
+}
+for _name, (_args, _ret) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _ret
+
+EXPORTED = tuple(_SIGS)
+
+
+class PBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+class Context:
+    """One CUDA device and stream (pb_ctx)."""
+
+    def __init__(self, device: int = 0):
+        h = _vp()
+        rc = _lib.pb_ctx_create(device, ctypes.byref(h))
+        if rc != PB_OK:
+            raise PBError(rc, "pb_ctx_create failed")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def stream(self) -> int:
+        return _lib.pb_ctx_stream(self._h) or 0
+
+    def check(self, rc):
+        if rc != PB_OK:
+            raise PBError(rc, _lib.pb_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pb_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+@dataclass
+class Result:
+    dG_solv: float
+    residual: float
+    iterations: int
+    converged: bool
+    matvecs: int
+    setup_ms: float
+    solve_ms: float
+    p2p_pairs: int
+    m2p_pairs: int
+    near_pairs: int
+    near_excluded: int
+
+
+def make_params(**kw) -> pb_params:
+    p = pb_params()
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": PB_FP64, "mixed": PB_MIXED}[v]
+        setattr(p, k, v)
+    return p
+
+
+class Problem:
+    """A molecule: regions, surfaces and charges (pb_problem)."""
+
+    def __init__(self, ctx: Context):
+        self.ctx = ctx
+        h = _vp()
+        ctx.check(_lib.pb_problem_create(ctx.handle, ctypes.byref(h)))
+        self._h = h
+        self.n_charges = 0
+
+    @classmethod
+    def from_dict(cls, ctx: Context, d: dict) -> "Problem":
+        """Build from the plain input description used by the synthetic workloads."""
+        pb = cls(ctx)
+        for r in d["regions"]:
+            pb.add_region(r["eps"], r["kappa"])
+        for s in d["surfaces"]:
+            pb.add_surface(s["verts"], s["tris"], s["inner"], s["outer"])
+        ch = d.get("charges")
+        if ch is not None:
+            pb.set_charges(ch["xyz"], ch["q"], ch["region"])
+        return pb
+
+    def add_region(self, eps, kappa) -> int:
+        rid = _int()
+        self.ctx.check(_lib.pb_add_region(self._h, float(eps), float(kappa), ctypes.byref(rid)))
+        return rid.value
+
+    def add_surface(self, verts, tris, inner, outer) -> int:
+        v = np.ascontiguousarray(verts, dtype=np.float64)
+        t = np.ascontiguousarray(tris, dtype=np.int32)
+        sid = _int()
+        self.ctx.check(_lib.pb_add_surface(self._h, _ptr(v), v.shape[0], _ptr(t), t.shape[0], int(inner),
+                                           int(outer), ctypes.byref(sid)))
+        return sid.value
+
+    def set_charges(self, xyz, q, region):
+        x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        qq = np.ascontiguousarray(q, dtype=np.float64).ravel()
+        self.ctx.check(_lib.pb_set_charges(self._h, _ptr(x), _ptr(qq), qq.size, int(region)))
+        self.n_charges = qq.size
+
+    def setup(self, **params):
+        p = make_params(**params)
+        self.ctx.check(_lib.pb_setup(self._h, ctypes.byref(p)))
+
+    @property
+    def n_unknowns(self) -> int:
+        return int(_lib.pb_num_unknowns(self._h))
+
+    def apply(self, x):
+        """y = A x.  x: numpy array (host) or a CUDA torch tensor (device pointers)."""
+        if hasattr(x, "data_ptr"):
+            import torch
+            y = torch.empty_like(x)
+            self.ctx.check(_lib.pb_apply_operator(self._h, _vp(x.data_ptr()), _vp(y.data_ptr()), 1))
+            return y
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.empty_like(xx)
+        self.ctx.check(_lib.pb_apply_operator(self._h, _ptr(xx), _ptr(y), 0))
+        return y
+
+    def apply_device(self, x_ptr: int, y_ptr: int):
+        """y = A x on raw device pointers (2 N doubles each)."""
+        self.ctx.check(_lib.pb_apply_operator(self._h, _vp(x_ptr), _vp(y_ptr), 1))
+
+    def rhs(self):
+        b = np.empty(self.n_unknowns)
+        self.ctx.check(_lib.pb_rhs(self._h, _ptr(b)))
+        return b
+
+    def solve(self, x0=None, check=True) -> Result:
+        r = pb_result()
+        xx = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        rc = _lib.pb_solve(self._h, _ptr(xx), ctypes.byref(r))
+        if check or rc not in (PB_OK, PB_ENOCONV):
+            self.ctx.check(rc)
+        return Result(r.dG_solv, r.residual, r.iterations, bool(r.converged), r.matvecs, r.setup_ms,
+                      r.solve_ms, r.p2p_pairs, r.m2p_pairs, r.near_pairs, r.near_excluded)
+
+    def solution(self):
+        x = np.empty(self.n_unknowns)
+        self.ctx.check(_lib.pb_get_solution(self._h, _ptr(x)))
+        return x
+
+    def reaction_potential(self, x):
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.empty(self.n_charges)
+        self.ctx.check(_lib.pb_reaction_potential(self._h, _ptr(xx), _ptr(out)))
+        return out
+
+    def coulomb_energy(self) -> float:
+        e = _dbl()
+        self.ctx.check(_lib.pb_coulomb_energy(self._h, ctypes.byref(e)))
+        return e.value
+
+    def tree(self, surface: int) -> dict:
+        info = pb_tree_info()
+        self.ctx.check(_lib.pb_tree_info_get(self._h, surface, ctypes.byref(info)))
+        n, m = info.n_points, info.n_nodes
+        out = dict(keys=np.empty(n, np.uint64), perm=np.empty(n, np.int32), level=np.empty(m, np.int32),
+                   start=np.empty(m, np.int64), count=np.empty(m, np.int64),
+                   first_child=np.empty(m, np.int32), nchild=np.empty(m, np.int32))
+        self.ctx.check(_lib.pb_tree_export(self._h, surface, *[_ptr(out[k]) for k in
+                                                               ("keys", "perm", "level", "start", "count",
+                                                                "first_child", "nchild")]))
+        out.update(corner=np.array(info.corner[:]), side=info.side, n_leaves=info.n_leaves)
+        return out
+
+    def lists(self, target_surface: int, source_surface: int) -> dict:
+        counts = np.zeros(6, np.int64)
+        self.ctx.check(_lib.pb_lists_export(self._h, target_surface, source_surface, _ptr(counts),
+                                            None, None, None, None, None, None))
+        m = int(counts[5])
+        out = dict(m2p_ptr=np.empty(m + 1, np.int64), m2p=np.empty(max(1, counts[0]), np.int32),
+                   p2p_ptr=np.empty(m + 1, np.int64), p2p=np.empty(max(1, counts[1]), np.int32),
+                   near_ptr=np.empty(m + 1, np.int64), near=np.empty(max(1, counts[2]), np.int32))
+        self.ctx.check(_lib.pb_lists_export(self._h, target_surface, source_surface, _ptr(counts),
+                                            *[_ptr(out[k]) for k in ("m2p_ptr", "m2p", "p2p_ptr", "p2p",
+                                                                     "near_ptr", "near")]))
+        out["m2p"] = out["m2p"][:counts[0]]
+        out["p2p"] = out["p2p"][:counts[1]]
+        out["near"] = out["near"][:counts[2]]
+        out.update(n_near_excluded=int(counts[3]), n_self_excluded=int(counts[4]))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pb_problem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

@@ -1,0 +1,69 @@
+"""GPU parity of the FP64 direct-summation path against the dense oracle (Sec. 2.2).
+
+theta < 0 turns the treecode into direct summation over every leaf, so the
+CUDA operator must equal the oracle's dense collocation matrix (same K-point,
+K_fine-point and semi-analytical rules) to rounding: relative L2 <= 1e-12.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import problem, rel_l2
+from oracle import dense as OD
+from oracle.closed_forms import kirkwood_energy, layered_sphere_energy
+from synth.configs import cavity_sphere_problem, layered_sphere_problem, sphere_problem
+
+pytestmark = pytest.mark.gpu
+
+DIRECT = dict(theta=-1.0, precision="fp64", ncrit=64)
+
+
+@pytest.mark.parametrize("level,K", [(3, 3), (4, 3), (3, 1), (2, 7)])
+def test_direct_matvec_matches_dense(level, K):
+    d = sphere_problem(level=level, charges="both")
+    pb = problem(d, K=K, **DIRECT)
+    A = OD.operator_matrix(d, dict(K=K))
+    rng = np.random.default_rng(level)
+    for _ in range(2):
+        x = rng.normal(size=A.shape[0])
+        assert rel_l2(pb.apply(x), A @ x) <= 1e-12
+    assert rel_l2(pb.rhs(), OD.rhs(d)) <= 1e-13
+
+
+def test_direct_matvec_multisurface():
+    for d in (layered_sphere_problem(level=2, charges="both"), cavity_sphere_problem(level=2)):
+        pb = problem(d, **DIRECT)
+        A = OD.operator_matrix(d)
+        x = np.random.default_rng(7).normal(size=A.shape[0])
+        assert rel_l2(pb.apply(x), A @ x) <= 1e-12
+        assert rel_l2(pb.rhs(), OD.rhs(d)) <= 1e-13
+
+
+def test_direct_solve_energy_kirkwood_sphere():
+    # the 2,048-panel sphere, K = 3, eps 4/80, kappa 0.125, GMRES tol 1e-8
+    d = sphere_problem(level=4, charges="both")
+    pb = problem(d, gmres_tol=1e-8, **DIRECT)
+    r = pb.solve()
+    ref = OD.solve_dense(d)
+    assert r.converged and r.residual < 1e-8
+    assert abs(r.dG_solv - ref["dG"]) <= 1e-6 * abs(ref["dG"])
+    ex = kirkwood_energy(4, 4, 80, 0.125, d["charges"]["xyz"], d["charges"]["q"])
+    assert abs(r.dG_solv - ex) <= 5e-3 * abs(ex)
+    # reaction potential of the solution against the oracle's reaction matrix
+    x = pb.solution()
+    assert rel_l2(pb.reaction_potential(x), ref["Rm"] @ x) <= 1e-12
+
+
+def test_direct_solve_energy_multisurface():
+    d = layered_sphere_problem(level=3, charges="both")
+    pb = problem(d, gmres_tol=1e-10, **DIRECT)
+    r = pb.solve()
+    ref = OD.solve_dense(d)
+    assert abs(r.dG_solv - ref["dG"]) <= 1e-6 * abs(ref["dG"])
+    ex = layered_sphere_energy([4.0, 6.0], [4, 80, 80], [0, 0, 0.125], 0, d["charges"]["xyz"], d["charges"]["q"])
+    assert abs(r.dG_solv - ex) <= 2.5e-2 * abs(ex)
+
+
+def test_coulomb_energy():
+    d = sphere_problem(level=2, charges="both")
+    pb = problem(d, **DIRECT)
+    assert abs(pb.coulomb_energy() - OD.coulomb_energy(d["charges"]["xyz"], d["charges"]["q"], 4.0)) < 1e-12

@@ -1,0 +1,61 @@
+"""GPU treecode (P2P + P2M/M2M + M2P + near field) against the oracle treecode and dense operator."""
+import numpy as np
+import pytest
+
+from gpu_util import problem, rel_l2
+from oracle import dense as OD
+from oracle import formulation as F
+from oracle.treecode import TreecodeOracle
+from synth.configs import layered_sphere_problem, sphere_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def _rows_rel(out, y, d, rows):
+    num = den = 0.0
+    for (s, side), ref in out.items():
+        got = y[F.row_slice(d, s, side)][rows[s]]
+        num += ((got - ref) ** 2).sum()
+        den += (ref ** 2).sum()
+    return np.sqrt(num / den)
+
+
+@pytest.mark.parametrize("P", [2, 6, 10])
+def test_fp64_treecode_matches_oracle_treecode(P):
+    d = sphere_problem(level=4, charges="both")
+    prm = dict(theta=0.5, P=P, ncrit=40)
+    pb = problem(d, precision="fp64", **prm)
+    x = np.random.default_rng(P).normal(size=2 * 2048)
+    y = pb.apply(x)
+    tc = TreecodeOracle(d, prm)
+    rows = {0: np.arange(0, 2048, 61 if P < 10 else 257)}
+    assert _rows_rel(tc.matvec(x, rows), y, d, rows) <= 1e-12
+
+
+def test_fp64_treecode_multisurface():
+    d = layered_sphere_problem(level=3, charges="both")
+    prm = dict(theta=0.5, P=4, ncrit=25)
+    pb = problem(d, precision="fp64", **prm)
+    x = np.random.default_rng(3).normal(size=4 * 512)
+    y = pb.apply(x)
+    tc = TreecodeOracle(d, prm)
+    rows = {0: np.arange(0, 512, 23), 1: np.arange(5, 512, 29)}
+    assert _rows_rel(tc.matvec(x, rows), y, d, rows) <= 1e-12
+
+
+def test_mixed_matvec_close_to_dense():
+    d = sphere_problem(level=4, charges="both")
+    A = OD.operator_matrix(d)
+    x = np.random.default_rng(5).normal(size=A.shape[0])
+    yd = A @ x
+    pb = problem(d, precision="mixed", theta=-1.0, ncrit=64)
+    assert rel_l2(pb.apply(x), yd) <= 2e-6
+    pb2 = problem(d, precision="mixed", theta=0.5, P=6, ncrit=40)
+    assert rel_l2(pb2.apply(x), yd) <= 1e-4
+
+
+def test_mixed_energy_within_1e4_of_fp64():
+    d = sphere_problem(level=4, charges="both")
+    e64 = problem(d, precision="fp64", theta=-1.0, gmres_tol=1e-10).solve().dG_solv
+    em = problem(d, precision="mixed", theta=0.5, P=6, ncrit=40, gmres_tol=1e-6).solve().dG_solv
+    assert abs(em - e64) <= 1e-4 * abs(e64)
