@@ -1,0 +1,377 @@
+"""Benchmark: treecode BEM solve of the ~40k-panel synthetic protein on one B300.
+
+One step = one pass of the whole hot path on the synthetic globular protein
+(2,000 atoms, ~40k panels, K = 3 Gauss points, theta = 0.5, Taylor order 6,
+ncrit 300, FP32-mixed, GMRES tol 1e-4): geometry, Morton octree, interaction
+lists, near-singular corrections, right-hand side, device GMRES with one
+treecode matrix-vector product per iteration, reaction potential and
+solvation energy.  Inputs are resident in device memory when the timed region
+starts (pb_add_surface / pb_set_charges copy them to HBM); L2 is flushed
+between steps.
+
+Metric: matvec Ginteractions/s = direct (P2P) target-source pairs evaluated
+by all matvecs of the timed steps / timed device time.  The solve time, the
+per-phase matvec times, the FP64 treecode solve on the same GPU and the
+mixed-vs-FP64 energy error are reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the plain FP64 CPU oracle (dense matrix-free C/OpenMP
+operator) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "matvec Ginteractions/s & solve time to 1e-4 ΔG err: batched FP32-mixed vs FP64"
+WORKLOAD = "synthetic globular protein, 2000 atoms, ~40k panels, K=3, theta=0.5, P=6, ncrit=300"
+PARAMS = dict(K=3, K_fine=19, N_k=5, thres=2.0, P=6, theta=0.5, ncrit=300, gmres_tol=1e-4, restart=50,
+              max_iter=1000)
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP32_LANES_PER_SM = 128
+
+
+# ---------------------------------------------------------------- arithmetic counts
+def p2p_ops_per_pair(kernels):
+    """FP32 arithmetic instructions of one P2P pair in the mixed kernel (MUFU not counted).
+
+    Shared part: 3 differences, r^2 (3), self-mask select (1), s*inv (1),
+    d.(x-y) (3), kv = rd * inv^3 (3) = 14.  Per Laplace kernel: 2 adds.  Per
+    Yukawa kernel: rho, exponent scale, s*e fma, kv*e, 1+kappa*rho, fma = 6.
+    """
+    return 14 + sum(2 if k == 0.0 else 6 for k in kernels)
+
+
+def m2p_ops_per_box(P, yukawa):
+    """FP32 arithmetic instructions of one (target, box) M2P evaluation at order P.
+
+    Mirrors the fully unrolled recurrence: per term with c1 nonzero indices and
+    c2 indices >= 2: s1 (c1), s2 (c2 - 1), a = -(c1' s1 + c2' s2) / r^2 (2-3),
+    contraction with M and D (2); Yukawa adds t1, t2 and the b recurrence.
+    Per box: u (3), r^2 (3), 1/r^2 (1), a0, b0 and the first contraction (4-6).
+    """
+    ops = 3 + 3 + 1 + 1 + 2 + (3 if yukawa else 0)
+    for n in range(1, P + 1):
+        for k1 in range(n, -1, -1):
+            for k2 in range(n - k1, -1, -1):
+                k = (k1, k2, n - k1 - k2)
+                c1 = sum(1 for x in k if x >= 1)
+                c2 = sum(1 for x in k if x >= 2)
+                ops += c1 + max(c2 - 1, 0) + (2 if c2 else 1) + 1 + 2
+                if yukawa:
+                    ops += c1 + max(c2 - 1, 0) + (2 if c2 else 1) + (2 if c2 else 1)
+    return ops
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _peaks():
+    try:
+        with open(MEASURED) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def _traffic_record(kernel_file, kernel_name):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    src = os.path.join(ROOT, "paper_1309_4018_b300", "csrc", kernel_file)
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    for fn in sorted(os.listdir(os.path.join(ROOT, "profiles"))) if os.path.isdir(os.path.join(ROOT, "profiles")) else []:
+        if not fn.endswith(".md"):
+            continue
+        txt = open(os.path.join(ROOT, "profiles", fn)).read()
+        if f"kernel: {kernel_name}" not in txt:
+            continue
+        m = re.search(r"source_sha256: ([0-9a-f]{64})", txt)
+        b = re.search(r"dram_bytes_per_launch: ([0-9.eE+]+)", txt)
+        if m and b and m.group(1) == digest:
+            return float(b.group(1))
+    return None
+
+
+def _problem():
+    from synth.configs import protein_problem
+    return protein_problem()
+
+
+# ---------------------------------------------------------------- reference arm (CPU oracle)
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    from oracle.cdense import DenseOperator
+    d = _problem()
+    op = DenseOperator(d, PARAMS)
+    n = op.sd[0].n
+    ns = n * PARAMS["K"]
+    sample = np.linspace(0, n - 1, 2048).astype(np.int64)
+    rows = {0: sample}
+    x = np.random.default_rng(0).normal(size=op.n)
+    cores = len(os.sched_getaffinity(0))
+    for _ in range(args.warmup):
+        op.apply(x, rows)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        op.apply(x, rows)
+        times.append(time.perf_counter() - t0)
+    pairs = sample.size * ns
+    t = float(np.sum(times))
+    value = pairs * args.steps / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Ginteractions/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "panels": n, "sources": ns, "l2": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": "Ginteractions/s", "cores": cores, "kind": "oracle",
+                             "sample": f"dense FP64 matrix-free operator rows for {sample.size} of {n} targets "
+                                       f"against all {ns} Gauss points, both kernels, per step"},
+            "e2e": {"value": value, "unit": "Ginteractions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(d):
+    """The oracle (dense FP64 C/OpenMP operator) on a bounded sample, in Ginteractions/s."""
+    from oracle.cdense import DenseOperator
+    op = DenseOperator(d, PARAMS)
+    n = op.sd[0].n
+    ns = n * PARAMS["K"]
+    sample = np.linspace(0, n - 1, 8192).astype(np.int64)
+    x = np.random.default_rng(0).normal(size=op.n)
+    op.apply(x, {0: sample[:8]})
+    t0 = time.perf_counter()
+    op.apply(x, {0: sample})
+    t = time.perf_counter() - t0
+    return {"value": sample.size * ns / t / 1e9, "unit": "Ginteractions/s",
+            "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": f"dense FP64 matrix-free operator: {sample.size} of {n} target rows against all {ns} "
+                      f"Gauss points, Laplace and Yukawa kernels ({t:.1f} s)"}
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1309_4018_b300.build import build
+    build()
+    from paper_1309_4018_b300 import pbbem
+
+    d = _problem()
+    surf = d["surfaces"][0]
+    ch = d["charges"]
+    ctx = pbbem.Context(local)
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+
+    def make_problem():
+        return pbbem.Problem.from_dict(ctx, d)
+
+    pb = make_problem()
+    nsrc = surf["tris"].shape[0] * PARAMS["K"]
+
+    def step(prob):
+        prob.setup(precision="mixed", **PARAMS)
+        return prob.solve()
+
+    for _ in range(args.warmup):
+        r = step(pb)
+    # timed steps (device time on the library stream, L2 flushed before each)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    results = []
+    launches0 = pbbem.launch_count()
+    _barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev[i][0].record(stream)
+            results.append(step(pb))
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    launches = pbbem.launch_count() - launches0
+    _barrier(ws)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = _max_over_ranks(float(np.sum(step_ms)) / 1e3, ws)
+    r = results[-1]
+    pairs_per_step = r.p2p_pairs * r.matvecs
+    value = ws * pairs_per_step * args.steps / t_total / 1e9
+
+    # per-phase matvec profile, dominant kernel and its roofline
+    x = np.random.default_rng(0).normal(size=pb.n_unknowns)
+    prof = pb.profile(x, reps=20)
+    peaks, peak_kind = _peaks()
+    clocks = clk.summary()
+    fmax = float(peaks.get("sm_max_mhz", 2032.0)) * 1e6
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = nsm * FP32_LANES_PER_SM * fmax / 1e12      # FP32 Tinstr/s
+    kernels = [d["regions"][0]["kappa"], d["regions"][1]["kappa"]]
+    p2p_ops = r.p2p_pairs * p2p_ops_per_pair(kernels)
+    m2p_ops = (r.m2p_pairs // 2) * (m2p_ops_per_box(PARAMS["P"], False) + m2p_ops_per_box(PARAMS["P"], True))
+    cand = {"p2p32": (prof["p2p"], p2p_ops), "m2p32": (prof["m2p"], m2p_ops)}
+    dom = max(cand, key=lambda k: cand[k][0])
+    dom_ms, dom_ops = cand[dom]
+    achieved = dom_ops / (dom_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "FP32 Tinstr/s",
+                "frac": achieved / alu_peak, "peak_source": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                                             f"{fmax / 1e6:.0f} MHz ({peak_kind} sm_max_mhz)",
+                "traffic": _traffic_record("treecode.cu", dom),
+                "frac_at_measured_clock": (achieved / (alu_peak * clocks["sm_mhz"] * 1e6 / fmax))
+                if clocks["sm_mhz"] else None,
+                "other": {k: {"ms": v[0], "Tinstr_s": v[1] / (v[0] / 1e3) / 1e12,
+                              "frac": v[1] / (v[0] / 1e3) / 1e12 / alu_peak} for k, v in cand.items()}}
+
+    # end to end through the public API with host buffers (H2D inside the timed region)
+    e2e_t = []
+    for i in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p2 = make_problem()
+        r2 = step(p2)
+        e2e_t.append(time.perf_counter() - t0)
+        p2.close()
+    h2d = surf["verts"].size * 8 + surf["tris"].size * 4 + ch["xyz"].size * 8 + ch["q"].size * 8
+    cycles = (r2.iterations + PARAMS["restart"] - 1) // PARAMS["restart"] + 1
+    d2h = 8 * (2 + cycles + r2.iterations)
+    e2e_val = ws * r2.p2p_pairs * r2.matvecs / float(np.mean(e2e_t)) / 1e9
+
+    # FP64 treecode on the same GPU and the energy error of the mixed form
+    p64 = make_problem()
+    p64.setup(precision="fp64", **dict(PARAMS, gmres_tol=1e-8))
+    r64 = p64.solve()
+    rel_err = abs(r.dG_solv - r64.dG_solv) / abs(r64.dG_solv)
+
+    if rank == 0:
+        cpu = cpu_baseline(d)
+        line = {
+            "metric": METRIC, "value": value, "unit": "Ginteractions/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "panels": int(surf["tris"].shape[0]), "sources": nsrc,
+                       "charges": int(ch["q"].size), "precision": "FP32-mixed (Krylov, near field, energy FP64)",
+                       "gmres_tol": PARAMS["gmres_tol"], "l2": "flushed (256 MB write) before every step",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "solve_time_s": r.solve_ms / 1e3 + r.setup_ms / 1e3,
+            "setup_ms": r.setup_ms, "gmres_ms": r.solve_ms, "iterations": r.iterations, "matvecs": r.matvecs,
+            "dG_kJ_mol": r.dG_solv, "dG_rel_err_vs_fp64": rel_err,
+            "p2p_pairs_per_matvec": r.p2p_pairs, "m2p_evals_per_matvec": r.m2p_pairs,
+            "matvec_phase_ms": prof,
+            "matvec_gint_per_s": r.p2p_pairs / (prof["total"] / 1e3) / 1e9,
+            "dense_equivalent_gint_per_s": surf["tris"].shape[0] * nsrc / (prof["total"] / 1e3) / 1e9,
+            "fp64": {"solve_time_s": (r64.solve_ms + r64.setup_ms) / 1e3, "iterations": r64.iterations,
+                     "gmres_tol": 1e-8, "dG_kJ_mol": r64.dG_solv,
+                     "speedup_mixed_vs_fp64": (r64.solve_ms + r64.setup_ms) / (r.solve_ms + r.setup_ms)},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "Ginteractions/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "seconds_per_step": float(np.mean(e2e_t))},
+            "gpu_launches": int(launches), "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -17,8 +17,10 @@
  * Conventions shared by every entry point:
  *   - All functions return PB_OK (0) or one of the PB_E* codes below; the
  *     message of the last failure is pb_last_error(ctx).
- *   - Host input arrays are copied during the call; the library never keeps a
- *     caller pointer.  Output arrays are caller-allocated and written in full.
+ *   - Host input arrays are copied during the call (surfaces and charges go
+ *     straight to device memory, so pb_setup reads only device-resident
+ *     inputs); the library never keeps a caller pointer.  Output arrays are
+ *     caller-allocated and written in full.
  *   - All device memory is owned by the library and released by the matching
  *     *_destroy call.
  *   - A context serves one host thread at a time; its work runs on one CUDA
@@ -67,6 +69,8 @@ typedef struct {
     int restart;       /* GMRES restart length, 1..200 [50] */
     int max_iter;      /* total GMRES iteration cap [1000] */
     int precision;     /* PB_FP64 or PB_MIXED [PB_FP64] */
+    int no_precond;    /* 1: plain GMRES; 0: right-preconditioned by the inverse of every
+                          panel's 2x2 self block (not in the paper; same solution) [0] */
 } pb_params;
 
 typedef struct {
@@ -130,6 +134,15 @@ int pb_reaction_potential(pb_problem *pb, const double *x, double *phi_reac);
 /* Coulomb energy 1/2 C sum_{i != j} q_i q_j / (eps_R r_ij) of the charges, kJ/mol
  * (the Coulomb term of Eq. total_energy). */
 int pb_coulomb_energy(pb_problem *pb, double *out);
+
+/* Per-phase device time of one operator application (CUDA events on the
+ * context stream), averaged over `reps` applications to a fixed random-free
+ * vector x (host, 2 N).  phase_ms[0..5]: source strengths + P2M/M2M, P2P,
+ * M2P, near-singular corrections, block combine, total.  Not in the paper:
+ * instrumentation for the per-phase timings of the measurement. */
+int pb_profile_operator(pb_problem *pb, const double *x, int reps, double *phase_ms);
+/* Number of kernels this library has launched since it was loaded. */
+long long pb_launch_count(void);
 
 /* Introspection of the integer work (Sec. 2.3, Eq. MAC), for bit-exact checks.
  * Octree over the Gauss points of surface `surface` (point j*K + k is Gauss

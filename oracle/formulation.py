@@ -92,3 +92,41 @@ def row_slice(problem, s, side):
     off = offsets(problem)
     n = n_panels(problem)
     return slice(2 * off[s] + side * n[s], 2 * off[s] + (side + 1) * n[s])
+
+
+def block_jacobi(problem, self_V):
+    """Right preconditioner from the 2x2 self blocks of every panel.
+
+    The paper names no preconditioner; this optional variant inverts, panel by
+    panel, the diagonal entries of the four (s, s) blocks: [1/2, cV_in V_in,ii;
+    1/2, cV_out V_out,ii], with K_ii = 0 and cV = -sigma c of the row's region.
+    self_V(s, kappa) -> semi-analytical V_ii of the panels of surface s.
+    Returns z -> M^-1 z on the 2N unknown vector.
+    """
+    eps = [r["eps"] for r in problem["regions"]]
+    kap = [r["kappa"] for r in problem["regions"]]
+    blocks_ = []
+    for s, surf in enumerate(problem["surfaces"]):
+        coef = []
+        for R in (surf["inner"], surf["outer"]):
+            sg, c = sigma_c(problem, R, s)
+            coef.append(-sg * c * self_V(s, kap[R]))
+        a11 = 0.5
+        a12 = coef[0]
+        a21 = 0.5
+        a22 = coef[1]
+        det = a11 * a22 - a12 * a21
+        blocks_.append((a22 / det, -a12 / det, -a21 / det, a11 / det))
+    us = unknown_slices(problem)
+
+    def apply(z):
+        out = np.empty_like(z)
+        for s, (m11, m12, m21, m22) in enumerate(blocks_):
+            ps, ds = us[s]
+            u1 = z[row_slice(problem, s, 0)]
+            u2 = z[row_slice(problem, s, 1)]
+            out[ps] = m11 * u1 + m12 * u2
+            out[ds] = m21 * u1 + m22 * u2
+        return out
+
+    return apply

@@ -8,14 +8,21 @@ Gram-Schmidt, the Hessenberg least-squares problem reduced by Givens
 rotations, stop when |g_{j+1}| / ||b|| < tol, restart after m steps, and on
 reaching the estimate check the true residual ||b - A x|| / ||b|| and restart
 if it is still above tol.
+
+Optional right preconditioning (solve A M^-1 u = b, x = M^-1 u) keeps the
+stopping test on the true residual of A x = b.
 """
 from __future__ import annotations
 
 import numpy as np
 
 
-def gmres(apply_A, b, tol=1e-4, restart=50, max_iter=1000, x0=None):
-    """Returns (x, iterations, relative true residual, history of estimates)."""
+def gmres(apply_A, b, tol=1e-4, restart=50, max_iter=1000, x0=None, M_inv=None):
+    """Returns (x, iterations, relative true residual, history of estimates).
+
+    M_inv: optional right preconditioner z -> M^-1 z.
+    """
+    prec = M_inv if M_inv is not None else (lambda z: z)
     b = np.asarray(b, dtype=np.float64)
     n = b.size
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
@@ -39,7 +46,7 @@ def gmres(apply_A, b, tol=1e-4, restart=50, max_iter=1000, x0=None):
         V[0] = r / beta
         j_done = 0
         for j in range(m):
-            w = apply_A(V[j])
+            w = apply_A(prec(V[j]))
             for i in range(j + 1):
                 H[i, j] = np.dot(V[i], w)
                 w = w - H[i, j] * V[i]
@@ -63,4 +70,4 @@ def gmres(apply_A, b, tol=1e-4, restart=50, max_iter=1000, x0=None):
             if abs(g[j + 1]) / bnorm < tol or it >= max_iter:
                 break
         y = np.linalg.solve(np.triu(H[:j_done, :j_done]), g[:j_done])
-        x = x + V[:j_done].T @ y
+        x = x + prec(V[:j_done].T @ y)

@@ -15,6 +15,10 @@
 
 using namespace pb;
 
+namespace pb {
+std::atomic<long long> g_launches{0};
+}
+
 struct pb_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -25,9 +29,10 @@ struct pb_ctx {
 namespace {
 
 struct SurfIn {
-    std::vector<double> v;
-    std::vector<int32_t> t;
-    int inner, outer;
+    int64_t nv = 0, nt = 0;
+    DevBuf<double> v;      // device copy made when the surface is added
+    DevBuf<int32_t> t;
+    int inner = -1, outer = -1;
 };
 
 // One (pair, kernel) contribution cK * K + cV * V to a row block or to the
@@ -58,7 +63,7 @@ struct pb_problem {
     std::vector<bool> need_far;           // per tree: some pair uses its moments
     std::vector<int64_t> off;             // panel offsets
     int64_t N = 0;
-    DevBuf<double> b, x, y, r, xin, yout;
+    DevBuf<double> b, x, y, r, xin, yout, z1, z2, minv;
     DevBuf<double> cq_d, cxyz_d, phi_reac, energy;
     Gmres gm;
     double setup_ms = 0.0;
@@ -103,6 +108,7 @@ Params resolve(const pb_params *p) {
         if (p->restart) r.restart = p->restart;
         if (p->max_iter) r.max_iter = p->max_iter;
         r.precision = p->precision;
+        r.precond = p->no_precond == 0;
     }
     if (!valid_rule(r.K)) fail(PB_EINVAL, "K must be 1, 3, 7 or 19");
     if (!valid_rule(r.K_fine)) fail(PB_EINVAL, "K_fine must be 1, 3, 7 or 19");
@@ -154,14 +160,16 @@ void setup_problem(pb_problem *pb) {
     for (int t = 0; t < ns; ++t) {
         SurfDev &S = pb->S[t];
         const SurfIn &si = pb->sin[t];
-        S.n = (int64_t)si.t.size() / 3;
-        S.nv = (int64_t)si.v.size() / 3;
+        S.n = si.nt;
+        S.nv = si.nv;
         S.inner = si.inner;
         S.outer = si.outer;
         S.off = pb->off[t];
         pb->off[t + 1] = pb->off[t] + S.n;
-        S.verts.upload(si.v.data(), si.v.size(), s);
-        S.tris.upload(si.t.data(), si.t.size(), s);
+        S.verts.alloc(3 * S.nv);
+        S.tris.alloc(3 * S.n);
+        PB_CUDA_TRY(cudaMemcpyAsync(S.verts.p, si.v.p, 3 * S.nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        PB_CUDA_TRY(cudaMemcpyAsync(S.tris.p, si.t.p, 3 * S.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
         surface_geometry(S, prm.K, s);
         build_tree(pb->T[t], S, prm.K, prm.ncrit, s);
     }
@@ -169,8 +177,6 @@ void setup_problem(pb_problem *pb) {
     pb->G.resize(ns + 1);
     for (int t = 0; t < ns; ++t) build_targets(pb->G[t], pb->S[t].cen.p, pb->S[t].n, t, s);
     const int64_t nc = (int64_t)pb->cq.size();
-    pb->cq_d.upload(pb->cq.data(), nc, s);
-    pb->cxyz_d.upload(pb->cxyz.data(), 3 * nc, s);
     build_targets(pb->G[ns], pb->cxyz_d.p, nc, -1, s);
     // block structure (multi-surface rule): row (s, R) gets sigma (K - c V) of every t in dR
     pb->rows.assign(2 * ns, {});
@@ -248,6 +254,21 @@ void setup_problem(pb_problem *pb) {
     pb->phi_reac.alloc(std::max<int64_t>(1, nc));
     pb->energy.alloc(1);
     pb->gm.init(2 * pb->N, prm.restart, s);
+    // block-Jacobi right preconditioner from every panel's 2x2 self block
+    pb->z1.alloc(2 * pb->N);
+    pb->z2.alloc(2 * pb->N);
+    pb->minv.alloc(4 * pb->N);
+    for (int sf = 0; sf < ns; ++sf) {
+        const double *sa[2] = {nullptr, nullptr};
+        double cv[2] = {0.0, 0.0};
+        for (int side = 0; side < 2; ++side)
+            for (const Term &tm : pb->rows[2 * sf + side]) {
+                const Pair &P = pb->pairs[tm.pair];
+                if (P.tree == sf) { sa[side] = P.selfV[tm.kidx].p; cv[side] = tm.cV; }
+            }
+        if (!sa[0] || !sa[1]) fail(PB_EINVAL, "internal: missing self block");
+        block_jacobi_inverse(pb->S[sf].n, cv[0], sa[0], cv[1], sa[1], pb->minv.p + 4 * pb->off[sf], s);
+    }
     PB_CUDA_TRY(cudaEventRecord(c->ev1, s));
     PB_CUDA_TRY(cudaEventSynchronize(c->ev1));
     float ms = 0.f;
@@ -257,28 +278,37 @@ void setup_problem(pb_problem *pb) {
     pb->have_solution = false;
 }
 
+// Optional event marks between the phases of one operator application.
+struct PhaseEvents {
+    cudaEvent_t ev[6];
+};
+
 // y = A x, both device pointers of 2N doubles.
-void apply_operator(pb_problem *pb, const double *xd, double *yd) {
+void apply_operator(pb_problem *pb, const double *xd, double *yd, PhaseEvents *ph = nullptr) {
     cudaStream_t s = pb->ctx->stream;
     const Params &prm = pb->prm;
     const bool mixed = prm.precision == PB_MIXED;
     const int ns = (int)pb->S.size();
+    auto mark = [&](int k) {
+        if (ph) PB_CUDA_TRY(cudaEventRecord(ph->ev[k], s));
+    };
+    mark(0);
     for (int t = 0; t < ns; ++t) {
         const double *phi = xd + 2 * pb->off[t];
         const double *dphi = phi + pb->S[t].n;
         compute_strengths(pb->T[t], pb->S[t], phi, dphi, mixed, s);
         if (pb->need_far[t]) upward_pass(pb->T[t], prm.P, mixed, s);
     }
+    mark(1);
+    for (auto &P : pb->pairs) launch_p2p(P, pb->G[P.tgt], pb->T[P.tree], P.tgt == P.tree, mixed, s);
+    mark(2);
+    for (auto &P : pb->pairs) launch_m2p(P, pb->G[P.tgt], pb->T[P.tree], prm.P, mixed, s);
+    mark(3);
     for (auto &P : pb->pairs) {
-        const bool use_self = P.tgt == P.tree;
-        const Targets &G = pb->G[P.tgt];
-        const Tree &Tr = pb->T[P.tree];
         const double *phi = xd + 2 * pb->off[P.tree];
-        const double *dphi = phi + pb->S[P.tree].n;
-        launch_p2p(P, G, Tr, use_self, mixed, s);
-        launch_m2p(P, G, Tr, prm.P, mixed, s);
-        launch_near(P, G, use_self, phi, dphi, s);
+        launch_near(P, pb->G[P.tgt], P.tgt == P.tree, phi, phi + pb->S[P.tree].n, s);
     }
+    mark(4);
     for (int sf = 0; sf < ns; ++sf) {
         for (int side = 0; side < 2; ++side) {
             CombineRow row{};
@@ -292,6 +322,7 @@ void apply_operator(pb_problem *pb, const double *xd, double *yd) {
                            yd + 2 * pb->off[sf] + side * pb->S[sf].n, s);
         }
     }
+    mark(5);
 }
 
 // phi_reac at the charges (input order) for the unknowns x (device); then
@@ -332,6 +363,15 @@ void reaction(pb_problem *pb, const double *xd) {
     weighted_sum(pb->cq_d.p, pb->phi_reac.p, nc, 0.5 * kKjPerMol * 4.0 * kPi, pb->energy.p, s);
 }
 
+// z = M^-1 u (block-Jacobi), both 2N device vectors.
+void apply_precond(pb_problem *pb, const double *u, double *z) {
+    cudaStream_t s = pb->ctx->stream;
+    for (size_t sf = 0; sf < pb->S.size(); ++sf) {
+        const int64_t n = pb->S[sf].n, o = 2 * pb->off[sf];
+        block_jacobi_apply(n, pb->minv.p + 4 * pb->off[sf], u + o, u + o + n, z + o, z + o + n, s);
+    }
+}
+
 void require_setup(pb_problem *pb) {
     if (!pb->is_setup) fail(PB_ENOTSETUP, "pb_setup has not been called since the last input change");
 }
@@ -368,7 +408,12 @@ void solve(pb_problem *pb, const double *x0, pb_result *out) {
             if (!(rel >= prm.tol) || iters >= prm.max_iter) break;
             int k = 0;
             for (int j = 0; j < gm.m; ++j) {
-                apply_operator(pb, gm.basis(j), gm.w.p);
+                if (prm.precond) {
+                    apply_precond(pb, gm.basis(j), pb->z1.p);
+                    apply_operator(pb, pb->z1.p, gm.w.p);
+                } else {
+                    apply_operator(pb, gm.basis(j), gm.w.p);
+                }
                 ++matvecs;
                 gm.arnoldi_step(j, s);
                 ++iters;
@@ -376,7 +421,13 @@ void solve(pb_problem *pb, const double *x0, pb_result *out) {
                 const double est = gm.residual_estimate(s);
                 if (!(est >= prm.tol) || iters >= prm.max_iter) break;
             }
-            gm.update_solution(k, pb->x.p, s);
+            if (prm.precond && k > 0) {
+                basis_combination(gm, k, pb->z1.p, s);
+                apply_precond(pb, pb->z1.p, pb->z2.p);
+                axpby(1.0, pb->x.p, 1.0, pb->z2.p, pb->x.p, n2, s);
+            } else {
+                gm.update_solution(k, pb->x.p, s);
+            }
         }
     }
     reaction(pb, pb->x.p);
@@ -477,13 +528,17 @@ int pb_add_surface(pb_problem *pb, const double *verts, int64_t nv, const int32_
             inner == outer)
             fail(PB_EINVAL, "surface references an unknown region");
         if (nt > ((int64_t)1 << 29) / 19) fail(PB_EINVAL, "too many triangles");
+        for (int64_t i = 0; i < 3 * nv; ++i)
+            if (!std::isfinite(verts[i])) fail(PB_EINVAL, "non-finite vertex coordinate");
+        for (int64_t i = 0; i < 3 * nt; ++i)
+            if (tris[i] < 0 || tris[i] >= nv) fail(PB_EINVAL, "triangle vertex index out of range");
+        set_device(pb->ctx);
         SurfIn si;
-        si.v.assign(verts, verts + 3 * nv);
-        si.t.assign(tris, tris + 3 * nt);
-        for (double v : si.v)
-            if (!std::isfinite(v)) fail(PB_EINVAL, "non-finite vertex coordinate");
-        for (int32_t i : si.t)
-            if (i < 0 || i >= nv) fail(PB_EINVAL, "triangle vertex index out of range");
+        si.nv = nv;
+        si.nt = nt;
+        si.v.upload(verts, 3 * nv, pb->ctx->stream);
+        si.t.upload(tris, 3 * nt, pb->ctx->stream);
+        PB_CUDA_TRY(cudaStreamSynchronize(pb->ctx->stream));
         si.inner = inner;
         si.outer = outer;
         pb->sin.push_back(std::move(si));
@@ -498,10 +553,14 @@ int pb_set_charges(pb_problem *pb, const double *xyz, const double *q, int64_t n
         if (nc < 0 || (nc > 0 && (!xyz || !q))) fail(PB_EINVAL, "bad charge arrays");
         if (region < 0 || region >= (int)pb->regions.size()) fail(PB_EINVAL, "unknown charge region");
         if (pb->regions[region].kappa != 0.0) fail(PB_EINVAL, "charges must sit in a kappa = 0 region");
+        for (int64_t i = 0; i < 3 * nc; ++i)
+            if (!std::isfinite(xyz[i])) fail(PB_EINVAL, "non-finite charge position");
+        set_device(pb->ctx);
         pb->cxyz.assign(xyz, xyz + 3 * nc);
         pb->cq.assign(q, q + nc);
-        for (double v : pb->cxyz)
-            if (!std::isfinite(v)) fail(PB_EINVAL, "non-finite charge position");
+        pb->cq_d.upload(q, nc, pb->ctx->stream);
+        pb->cxyz_d.upload(xyz, 3 * nc, pb->ctx->stream);
+        PB_CUDA_TRY(cudaStreamSynchronize(pb->ctx->stream));
         pb->cregion = region;
         pb->is_setup = false;
     });
@@ -593,6 +652,37 @@ int pb_coulomb_energy(pb_problem *pb, double *out) {
         PB_CUDA_TRY(cudaStreamSynchronize(s));
     });
 }
+
+int pb_profile_operator(pb_problem *pb, const double *xh, int reps, double *phase_ms) {
+    if (!pb || !xh || !phase_ms || reps < 1) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        require_setup(pb);
+        set_device(pb->ctx);
+        cudaStream_t s = pb->ctx->stream;
+        const int64_t n2 = 2 * pb->N;
+        pb->xin.upload(xh, n2, s);
+        pb->yout.alloc(n2);
+        PhaseEvents ph;
+        for (auto &e : ph.ev) PB_CUDA_TRY(cudaEventCreate(&e));
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        for (int r = 0; r < reps; ++r) {
+            apply_operator(pb, pb->xin.p, pb->yout.p, &ph);
+            PB_CUDA_TRY(cudaEventSynchronize(ph.ev[5]));
+            for (int k = 0; k < 5; ++k) {
+                float ms = 0.f;
+                PB_CUDA_TRY(cudaEventElapsedTime(&ms, ph.ev[k], ph.ev[k + 1]));
+                acc[k] += ms;
+            }
+            float tot = 0.f;
+            PB_CUDA_TRY(cudaEventElapsedTime(&tot, ph.ev[0], ph.ev[5]));
+            acc[5] += tot;
+        }
+        for (auto &e : ph.ev) cudaEventDestroy(e);
+        for (int k = 0; k < 6; ++k) phase_ms[k] = acc[k] / reps;
+    });
+}
+
+long long pb_launch_count(void) { return pb::g_launches.load(); }
 
 int pb_tree_info_get(pb_problem *pb, int surface, pb_tree_info *out) {
     if (!pb || !out) return PB_EINVAL;

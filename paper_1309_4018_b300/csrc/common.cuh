@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -33,7 +34,14 @@ struct Error {
             throw ::pb::Error{PB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};   \
     } while (0)
 
-#define PB_LAUNCH_CHECK() PB_CUDA_TRY(cudaGetLastError())
+// Every kernel launch of the library is followed by PB_LAUNCH_CHECK, which
+// also counts it (pb_launch_count).
+extern std::atomic<long long> g_launches;
+#define PB_LAUNCH_CHECK()                            \
+    do {                                             \
+        ::pb::g_launches.fetch_add(1, std::memory_order_relaxed); \
+        PB_CUDA_TRY(cudaGetLastError());             \
+    } while (0)
 
 inline void fail(int code, const std::string &m) { throw Error{code, m}; }
 

@@ -165,6 +165,36 @@ __global__ void coulomb_rows_kernel(const double *__restrict__ xyz, const double
     rowv[i] = s;
 }
 
+__global__ void bj_inverse_kernel(int64_t n, double cin, const double *__restrict__ sa_in, double cout,
+                                  const double *__restrict__ sa_out, double *__restrict__ minv) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a11 = 0.5, a12 = cin * sa_in[i], a21 = 0.5, a22 = cout * sa_out[i];
+    const double det = a11 * a22 - a12 * a21;
+    minv[4 * i] = a22 / det;
+    minv[4 * i + 1] = -a12 / det;
+    minv[4 * i + 2] = -a21 / det;
+    minv[4 * i + 3] = a11 / det;
+}
+
+__global__ void bj_apply_kernel(int64_t n, const double *__restrict__ minv, const double *__restrict__ u1,
+                                const double *__restrict__ u2, double *__restrict__ z1, double *__restrict__ z2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a = u1[i], b = u2[i];
+    z1[i] = minv[4 * i] * a + minv[4 * i + 1] * b;
+    z2[i] = minv[4 * i + 2] * a + minv[4 * i + 3] * b;
+}
+
+__global__ void combination_kernel(const double *__restrict__ V, int64_t ld, int k, const GmresState *st,
+                                   double *__restrict__ out, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int c = 0; c < k; ++c) s += V[c * ld + i] * st->y[c];
+    out[i] = s;
+}
+
 void dot_device(const double *V, int64_t ld, int nv, const double *w, int64_t n, double *partial, double *out,
                 cudaStream_t s) {
     mdot_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(V, ld, nv, w, n, partial);
@@ -241,6 +271,27 @@ void Gmres::update_solution(int k, double *x, cudaStream_t s) {
     back_solve_kernel<<<1, 1, 0, s>>>(st.p, k);
     PB_LAUNCH_CHECK();
     update_x_kernel<<<div_up(n, 256), 256, 0, s>>>(V.p, ld, k, st.p, x, n);
+    PB_LAUNCH_CHECK();
+}
+
+void block_jacobi_inverse(int64_t n, double cV_in, const double *sa_in, double cV_out, const double *sa_out,
+                          double *minv, cudaStream_t s) {
+    if (!n) return;
+    bj_inverse_kernel<<<div_up(n, 256), 256, 0, s>>>(n, cV_in, sa_in, cV_out, sa_out, minv);
+    PB_LAUNCH_CHECK();
+}
+
+void block_jacobi_apply(int64_t n, const double *minv, const double *u_in, const double *u_out, double *z_phi,
+                        double *z_dphi, cudaStream_t s) {
+    if (!n) return;
+    bj_apply_kernel<<<div_up(n, 256), 256, 0, s>>>(n, minv, u_in, u_out, z_phi, z_dphi);
+    PB_LAUNCH_CHECK();
+}
+
+void basis_combination(const Gmres &G, int k, double *out, cudaStream_t s) {
+    back_solve_kernel<<<1, 1, 0, s>>>(G.st.p, k);
+    PB_LAUNCH_CHECK();
+    combination_kernel<<<div_up(G.n, 256), 256, 0, s>>>(G.V.p, G.ld, k, G.st.p, out, G.n);
     PB_LAUNCH_CHECK();
 }
 

@@ -29,6 +29,15 @@ struct Gmres {
     void update_solution(int k, double *x, cudaStream_t s);
 };
 
+// Inverse 2x2 self blocks of one surface's panels: minv = 4 n doubles (m11, m12, m21, m22 per panel).
+void block_jacobi_inverse(int64_t n, double cV_in, const double *sa_in, double cV_out, const double *sa_out,
+                          double *minv, cudaStream_t s);
+// z = M^-1 u for one surface: (z_phi, z_dphi)_i = Minv_i (u_in, u_out)_i.
+void block_jacobi_apply(int64_t n, const double *minv, const double *u_in, const double *u_out, double *z_phi,
+                        double *z_dphi, cudaStream_t s);
+// x = sum_c V[c] y[c] (k basis vectors) written into out.
+void basis_combination(const Gmres &G, int k, double *out, cudaStream_t s);
+
 void add_kernel_launch(double *a, const double *b, int n, cudaStream_t s);
 void axpby(double a, const double *x, double b, const double *y, double *out, int64_t n, cudaStream_t s);
 double norm2_device(const double *x, int64_t n, Gmres &G, cudaStream_t s);

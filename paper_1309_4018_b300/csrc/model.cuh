@@ -15,6 +15,7 @@ struct Params {
     double tol = 1e-4;
     int restart = 50, max_iter = 1000;
     int precision = PB_FP64;
+    bool precond = true;
 };
 
 struct Region {

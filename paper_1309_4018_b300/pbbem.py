@@ -31,7 +31,7 @@ class pb_params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("K_fine", ctypes.c_int), ("N_k", ctypes.c_int),
                 ("thres", ctypes.c_double), ("P", ctypes.c_int), ("theta", ctypes.c_double),
                 ("ncrit", ctypes.c_int), ("gmres_tol", ctypes.c_double), ("restart", ctypes.c_int),
-                ("max_iter", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("no_precond", ctypes.c_int)]
 
 
 class pb_result(ctypes.Structure):
@@ -69,6 +69,8 @@ _SIGS = {
     "pb_get_solution": ([_vp, _vp], _int),
     "pb_reaction_potential": ([_vp, _vp, _vp], _int),
     "pb_coulomb_energy": ([_vp, ctypes.POINTER(_dbl)], _int),
+    "pb_profile_operator": ([_vp, _vp, _int, _vp], _int),
+    "pb_launch_count": ([], ctypes.c_longlong),
     "pb_tree_info_get": ([_vp, _int, ctypes.POINTER(pb_tree_info)], _int),
     "pb_tree_export": ([_vp, _int, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _int),
     "pb_lists_export": ([_vp, _int, _int, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _int),
@@ -79,6 +81,11 @@ for _name, (_args, _ret) in _SIGS.items():
     _f.restype = _ret
 
 EXPORTED = tuple(_SIGS)
+
+
+def launch_count() -> int:
+    """Kernels launched by the library since it was loaded."""
+    return int(_lib.pb_launch_count())
 
 
 class PBError(RuntimeError):
@@ -241,6 +248,13 @@ class Problem:
         e = _dbl()
         self.ctx.check(_lib.pb_coulomb_energy(self._h, ctypes.byref(e)))
         return e.value
+
+    def profile(self, x, reps: int = 10) -> dict:
+        """Average device ms per phase of one operator application."""
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.zeros(6)
+        self.ctx.check(_lib.pb_profile_operator(self._h, _ptr(xx), int(reps), _ptr(out)))
+        return dict(zip(("upward", "p2p", "m2p", "near", "combine", "total"), out.tolist()))
 
     def tree(self, surface: int) -> dict:
         info = pb_tree_info()

@@ -72,8 +72,8 @@ def cavity_sphere_problem(level=3, eps_cav=80.0):
 
 # Grid spacings (A) of the marching-tetrahedra mesher that give the stated
 # panel counts for the seeded molecules below.
-PROTEIN_SPACING = 1.65      # ~40k panels for the 2,000-atom seed-2 molecule
-STERN_SPACING = 1.02        # ~60k panels for its +2 A Stern surface
+PROTEIN_SPACING = 1.17      # ~40k panels for the 2,000-atom seed-2 molecule
+STERN_SPACING = 1.16        # ~60k panels for the +2 A Stern surface of the seed-3 molecule
 
 
 @functools.lru_cache(maxsize=8)

@@ -6,7 +6,14 @@ generator.  Its molecular surface is the level set rho(x) = 1 of the Gaussian
 density rho(x) = sum_a exp(-beta (|x - x_a|^2 / R_a^2 - 1)), triangulated by
 marching tetrahedra on a uniform grid (a Kuhn split of every grid cube into six
 tetrahedra, which has no ambiguous cases and gives a closed, consistently
-oriented surface).  Only the outer connected component is kept.
+oriented surface).  Only the outer connected component is kept.  A few rounds
+of Laplacian vertex smoothing, each followed by a Newton projection back onto
+the level set, even out the thin triangles marching tetrahedra leaves.
+
+beta = 0.5 gives a smooth, solvent-excluded-like envelope (the probe-rolled
+surface of a protein has no atom-scale crevices); sharper densities
+(beta ~ 2.3) give folded van der Waals-like surfaces whose panels nearly touch,
+where the K-point integration of the boundary operator breaks down.
 
 This module produces inputs only; it holds none of the boundary-element
 arithmetic, and both the oracle and the CUDA path read its output.
@@ -18,7 +25,8 @@ from scipy.sparse import coo_matrix
 from scipy.sparse.csgraph import connected_components
 from scipy.spatial import cKDTree
 
-BETA = 2.3
+BETA = 0.5
+CUTOFF = 2.7        # an atom contributes to rho within CUTOFF * R_a
 
 
 def synthetic_atoms(n_atoms: int, ball_radius: float, seed: int,
@@ -50,7 +58,7 @@ def synthetic_atoms(n_atoms: int, ball_radius: float, seed: int,
     return {"xyz": pts, "radius": radius, "q": q}
 
 
-def _density_grid(xyz, radius, lo, h, shape, beta=BETA, cutoff=2.7):
+def _density_grid(xyz, radius, lo, h, shape, beta=BETA, cutoff=CUTOFF):
     """rho on grid nodes lo + h*(i,j,k); each atom contributes within cutoff*R."""
     rho = np.zeros(shape, dtype=np.float64)
     axes = [lo[d] + h * np.arange(shape[d]) for d in range(3)]
@@ -164,8 +172,51 @@ def outer_component(verts, tris):
     return verts[used], remap[tris]
 
 
+def density_and_gradient(p, xyz, radius, beta=BETA, cutoff=CUTOFF, tree=None):
+    """rho and grad rho at points p [m,3] (same truncation as the grid)."""
+    p = np.asarray(p, dtype=np.float64)
+    tree = tree if tree is not None else cKDTree(xyz)
+    lists = tree.query_ball_point(p, cutoff * float(np.max(radius)))
+    cnt = np.array([len(l) for l in lists])
+    vi = np.repeat(np.arange(p.shape[0]), cnt)
+    ai = np.concatenate([np.asarray(l, dtype=np.int64) for l in lists]) if cnt.sum() else np.zeros(0, np.int64)
+    d = p[vi] - xyz[ai]
+    d2 = (d * d).sum(1)
+    R2 = radius[ai] ** 2
+    e = np.exp(-beta * (d2 / R2 - 1.0))
+    e[d2 > (cutoff * cutoff) * R2] = 0.0
+    rho = np.bincount(vi, weights=e, minlength=p.shape[0])
+    g = np.stack([np.bincount(vi, weights=e * (-2.0 * beta) * d[:, k] / R2, minlength=p.shape[0])
+                  for k in range(3)], 1)
+    return rho, g
+
+
+def smooth_on_level_set(verts, tris, xyz, radius, beta=BETA, iters=5, relax=0.5, level=1.0):
+    """Laplacian smoothing of the vertices, each round projected back onto rho = level."""
+    v = np.array(verts, dtype=np.float64)
+    t = np.asarray(tris, dtype=np.int64)
+    nv = v.shape[0]
+    e = np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]])
+    e = np.concatenate([e, e[:, ::-1]])
+    e = np.unique(e, axis=0)
+    deg = np.bincount(e[:, 0], minlength=nv).astype(np.float64)
+    tree = cKDTree(xyz)
+    for _ in range(iters):
+        avg = np.stack([np.bincount(e[:, 0], weights=v[e[:, 1], k], minlength=nv) for k in range(3)], 1)
+        v = v + relax * (avg / deg[:, None] - v)
+        for _ in range(3):
+            f, g = density_and_gradient(v, xyz, radius, beta, tree=tree)
+            g2 = (g * g).sum(1)
+            step = np.where(g2 > 1e-12, (f - level) / np.maximum(g2, 1e-12), 0.0)
+            dv = step[:, None] * g
+            n = np.sqrt((dv * dv).sum(1))
+            dv *= np.minimum(1.0, 0.3 / np.maximum(n, 1e-30))[:, None]
+            v = v - dv
+    return v
+
+
 def gaussian_surface(xyz, radius, spacing: float, radius_offset: float = 0.0,
-                     beta: float = BETA, margin: float = 4.0):
+                     beta: float = BETA, margin: float = 4.0, smooth_iters: int = 5):
     """Closed outward-oriented triangulation of the level set rho = 1.
 
     radius_offset enlarges every atomic radius (a Stern surface uses +2 A).
@@ -178,4 +229,12 @@ def gaussian_surface(xyz, radius, spacing: float, radius_offset: float = 0.0,
     rho = _density_grid(xyz, r, lo, spacing, shape, beta=beta)
     v, t = marching_tetrahedra(rho, lo, spacing)
     v, t = outer_component(v, t)
+    if smooth_iters:
+        v = smooth_on_level_set(v, t, xyz, r, beta=beta, iters=smooth_iters)
+        # smoothing must not fold a triangle over: outward normals still point down the density
+        a, b, c = v[t[:, 0]], v[t[:, 1]], v[t[:, 2]]
+        nrm = np.cross(b - a, c - a)
+        _, g = density_and_gradient((a + b + c) / 3.0, xyz, r, beta)
+        if np.any(np.einsum("ij,ij->i", nrm, g) >= 0.0):
+            raise RuntimeError("surface smoothing inverted a triangle; use a finer grid")
     return v, t.astype(np.int32)

@@ -67,3 +67,12 @@ def test_coulomb_energy():
     d = sphere_problem(level=2, charges="both")
     pb = problem(d, **DIRECT)
     assert abs(pb.coulomb_energy() - OD.coulomb_energy(d["charges"]["xyz"], d["charges"]["q"], 4.0)) < 1e-12
+
+
+def test_preconditioner_does_not_change_the_solution():
+    d = sphere_problem(level=3, charges="both")
+    r1 = problem(d, gmres_tol=1e-10, **DIRECT).solve()
+    r0 = problem(d, gmres_tol=1e-10, no_precond=1, **DIRECT).solve()
+    assert r1.converged and r0.converged
+    assert abs(r1.dG_solv - r0.dG_solv) <= 1e-8 * abs(r0.dG_solv)
+    assert r1.iterations <= r0.iterations

@@ -179,3 +179,28 @@ def test_gmres_matches_lu():
     assert res < 1e-10
     xs = np.linalg.solve(A, b)
     assert np.linalg.norm(x - xs) < 1e-8 * np.linalg.norm(xs)
+
+
+def test_block_jacobi_preconditioned_gmres_same_solution():
+    # right preconditioning changes the iteration count, not the solution
+    from oracle.formulation import block_jacobi
+    from oracle.dense import surfaces_data
+    pr = layered_sphere_problem(level=2, charges="both")
+    sd = surfaces_data(pr)
+    A = operator_matrix(pr, sdata=sd)
+    b = rhs(pr, sdata=sd)
+    M = block_jacobi(pr, lambda s, k: sd[s].self_V(k, 5))
+    x, it, res, _ = gmres(lambda v: A @ v, b, tol=1e-11, restart=30, M_inv=M)
+    xs = np.linalg.solve(A, b)
+    assert res < 1e-11 and np.linalg.norm(x - xs) < 1e-9 * np.linalg.norm(xs)
+    # applying M to the block-diagonal part of A gives the identity on each 2x2 block
+    D = np.zeros_like(A)
+    for s in range(2):
+        for side in (0, 1):
+            rs = F.row_slice(pr, s, side)
+            for c in F.unknown_slices(pr)[s]:
+                D[rs, c] = np.diag(np.diag(A[rs, c]))
+    cols = np.random.default_rng(0).choice(A.shape[0], 5, replace=False)
+    for j in cols:
+        e = np.zeros(A.shape[0]); e[j] = 1.0
+        assert np.allclose(M(D @ e), e, atol=1e-12)
