@@ -144,6 +144,23 @@ int pb_profile_operator(pb_problem *pb, const double *x, int reps, double *phase
 /* Number of kernels this library has launched since it was loaded. */
 long long pb_launch_count(void);
 
+/* Coulomb energy 1/2 C sum_{i != j} q_i q_j / (eps r_ij) of nc charges, in
+ * kJ/mol, computed without allocating device memory.  The paper has no
+ * counterpart: this serves callers that cannot let a library allocate, such as
+ * applications that own all device memory through their own pool or budget,
+ * or loops that must not pay the synchronisation cudaMalloc/cudaFree imply.
+ * xyz (3 nc doubles), q (nc doubles) and energy (1 double) are device
+ * pointers on `device`; the work is queued on `stream` (a cudaStream_t, NULL
+ * for the default stream) and the call returns before it completes.  Scratch
+ * lives in a static device array of 262,144 doubles (2 MiB per GPU, held while
+ * the library is loaded): nc > 262144 returns PB_EINVAL.  Every call shares
+ * that array, so calls whose work overlaps on the GPU (other streams, other
+ * threads) race; each call rewrites all the entries it reads.  The first call
+ * on a device resolves the array's device address, so make it before any
+ * stream capture.  *err (optional) receives a static message on failure. */
+int pb_coulomb_energy_noalloc(int device, const double *xyz, const double *q, int64_t nc, double eps,
+                              double *energy, void *stream, const char **err);
+
 /* Introspection of the integer work (Sec. 2.3, Eq. MAC), for bit-exact checks.
  * Octree over the Gauss points of surface `surface` (point j*K + k is Gauss
  * point k of panel j).  Nodes are numbered breadth first, children in octant

@@ -71,6 +71,7 @@ _SIGS = {
     "pb_coulomb_energy": ([_vp, ctypes.POINTER(_dbl)], _int),
     "pb_profile_operator": ([_vp, _vp, _int, _vp], _int),
     "pb_launch_count": ([], ctypes.c_longlong),
+    "pb_coulomb_energy_noalloc": ([_int, _vp, _vp, _i64, _dbl, _vp, _vp, ctypes.POINTER(ctypes.c_char_p)], _int),
     "pb_tree_info_get": ([_vp, _int, ctypes.POINTER(pb_tree_info)], _int),
     "pb_tree_export": ([_vp, _int, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _int),
     "pb_lists_export": ([_vp, _int, _int, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _int),
@@ -86,6 +87,18 @@ EXPORTED = tuple(_SIGS)
 def launch_count() -> int:
     """Kernels launched by the library since it was loaded."""
     return int(_lib.pb_launch_count())
+
+
+def coulomb_energy_noalloc(device: int, xyz_ptr: int, q_ptr: int, nc: int, eps: float, out_ptr: int,
+                           stream: int = 0):
+    """Coulomb energy into *out_ptr from device arrays, with no device allocation.
+
+    Returns (status code, message).  The work is queued on `stream`.
+    """
+    msg = ctypes.c_char_p()
+    rc = _lib.pb_coulomb_energy_noalloc(int(device), _vp(xyz_ptr), _vp(q_ptr), int(nc), float(eps), _vp(out_ptr),
+                                        _vp(stream), ctypes.byref(msg))
+    return rc, (msg.value or b"").decode()
 
 
 class PBError(RuntimeError):
