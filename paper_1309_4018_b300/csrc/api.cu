@@ -244,7 +244,8 @@ void setup_problem(pb_problem *pb) {
             for (int side = 0; side < 2; ++side)
                 if (Rs[side] == pb->cregion)
                     rhs_rows(pb->S[sf], nc, pb->cq_d.p, pb->cxyz_d.p, Rg.kappa, Rg.eps,
-                             pb->b.p + 2 * pb->off[sf] + side * pb->S[sf].n, s);
+                             pb->b.p + 2 * pb->off[sf] + side * pb->S[sf].n,
+                             prm.precision == PB_MIXED ? pb->T[sf].origin : nullptr, s);
         }
     }
     pb->x.alloc(2 * pb->N);

@@ -119,23 +119,28 @@ __device__ void panel_rule_sums(const double x[3], const double *__restrict__ v,
 
 // Near-singular corrections: for each near entry (target i, panel j) the
 // K_fine-rule value minus the K-rule value that the direct sum evaluates.
-__global__ void near_values_kernel(int64_t ntg, const double *__restrict__ xs, const int64_t *__restrict__ ptr,
-                                   const int32_t *__restrict__ pan, const double *__restrict__ v,
-                                   const int32_t *__restrict__ t, const double *__restrict__ nrm,
-                                   const double *__restrict__ area, int slotK, int slotF, double kappa,
-                                   double *__restrict__ dV, double *__restrict__ dK) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ntg) return;
-    const double x[3] = {xs[3 * i], xs[3 * i + 1], xs[3 * i + 2]};
-    for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
-        const int j = pan[e];
-        const double nj[3] = {nrm[3 * j], nrm[3 * j + 1], nrm[3 * j + 2]};
-        double vf, kf, vk, kk;
-        panel_rule_sums(x, v, t, j, nj, area[j], c_rules[slotF], kappa, vf, kf);
-        panel_rule_sums(x, v, t, j, nj, area[j], c_rules[slotK], kappa, vk, kk);
-        dV[e] = vf - vk;
-        dK[e] = kf - kk;
+// One thread per entry; its target is found by binary search in the CSR offsets.
+__global__ void near_values_kernel(int64_t ntg, int64_t nnear, const double *__restrict__ xs,
+                                   const int64_t *__restrict__ ptr, const int32_t *__restrict__ pan,
+                                   const double *__restrict__ v, const int32_t *__restrict__ t,
+                                   const double *__restrict__ nrm, const double *__restrict__ area, int slotK, int slotF,
+                                   double kappa, double *__restrict__ dV, double *__restrict__ dK) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnear) return;
+    int64_t lo = 0, hi = ntg;  // last i with ptr[i] <= e
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (ptr[mid] <= e) lo = mid; else hi = mid;
     }
+    const int64_t i = lo;
+    const double x[3] = {xs[3 * i], xs[3 * i + 1], xs[3 * i + 2]};
+    const int j = pan[e];
+    const double nj[3] = {nrm[3 * j], nrm[3 * j + 1], nrm[3 * j + 2]};
+    double vf, kf, vk, kk;
+    panel_rule_sums(x, v, t, j, nj, area[j], c_rules[slotF], kappa, vf, kf);
+    panel_rule_sums(x, v, t, j, nj, area[j], c_rules[slotK], kappa, vk, kk);
+    dV[e] = vf - vk;
+    dK[e] = kf - kk;
 }
 
 // Semi-analytical single-layer self integral at the centroid (Zhu et al.
@@ -195,6 +200,45 @@ __global__ void rhs_kernel(int64_t n, const double *__restrict__ cen, int64_t nc
         s += q[k] * (kappa == 0.0 ? 1.0 : exp(-kappa * r)) / r;
     }
     b[i] = s * kInv4Pi / eps;
+}
+
+// Mixed-precision right-hand side: charges staged in shared memory as FP32
+// (relative to an origin near the molecule), FP32 terms, each 256-charge tile
+// summed in FP32 and added into a compensated (hi, lo) FP32 pair.
+__global__ void __launch_bounds__(256) rhs32_kernel(int64_t n, const double *__restrict__ cen, int64_t nc,
+                                                    const double *__restrict__ q, const double *__restrict__ xyz,
+                                                    double ox, double oy, double oz, float kappa, double eps,
+                                                    double *__restrict__ b) {
+    __shared__ float4 sc[256];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float x = 0.f, y = 0.f, z = 0.f;
+    if (i < n) {
+        x = (float)(cen[3 * i] - ox); y = (float)(cen[3 * i + 1] - oy); z = (float)(cen[3 * i + 2] - oz);
+    }
+    const float l2k = -kappa * 1.4426950408889634f;
+    float hi = 0.f, lo = 0.f;
+    for (int64_t c0 = 0; c0 < nc; c0 += 256) {
+        const int64_t c = c0 + threadIdx.x;
+        __syncthreads();
+        if (c < nc)
+            sc[threadIdx.x] = make_float4((float)(xyz[3 * c] - ox), (float)(xyz[3 * c + 1] - oy),
+                                          (float)(xyz[3 * c + 2] - oz), (float)q[c]);
+        __syncthreads();
+        const int m = (int)(nc - c0 < 256 ? nc - c0 : 256);
+        float p = 0.f;
+        for (int k = 0; k < m; ++k) {
+            const float4 ch = sc[k];
+            const float dx = x - ch.x, dy = y - ch.y, dz = z - ch.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float inv = rsqrtf(r2);
+            const float g = kappa == 0.f ? inv : inv * exp2f(l2k * r2 * inv);
+            p = fmaf(ch.w, g, p);
+        }
+        const float t = hi + p;
+        lo += (fabsf(hi) >= fabsf(p)) ? ((hi - t) + p) : ((p - t) + hi);
+        hi = t;
+    }
+    if (i < n) b[i] = ((double)hi + (double)lo) * kInv4Pi / eps;
 }
 
 // Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on P_n.
@@ -259,9 +303,10 @@ void surface_geometry(SurfDev &S, int K, cudaStream_t s) {
 void near_values(const Pair &Pr, const Targets &G, const SurfDev &src, int K, int K_fine, double kappa, double *dV,
                  double *dK, cudaStream_t s) {
     if (G.n == 0 || Pr.n_near == 0) return;
-    near_values_kernel<<<div_up(G.n, 64), 64, 0, s>>>(G.n, G.xs.p, Pr.near_ptr.p, Pr.near_panel.p, src.verts.p,
-                                                      src.tris.p, src.nrm.p, src.area.p, rule_slot(K), rule_slot(K_fine),
-                                                      kappa, dV, dK);
+    near_values_kernel<<<div_up(Pr.n_near, 128), 128, 0, s>>>(G.n, Pr.n_near, G.xs.p, Pr.near_ptr.p,
+                                                               Pr.near_panel.p, src.verts.p, src.tris.p, src.nrm.p,
+                                                               src.area.p, rule_slot(K), rule_slot(K_fine), kappa, dV,
+                                                               dK);
     PB_LAUNCH_CHECK();
 }
 
@@ -273,8 +318,13 @@ void self_integrals(const SurfDev &S, int N_k, double kappa, double *out, cudaSt
 }
 
 void rhs_rows(const SurfDev &S, int64_t nc, const double *q, const double *xyz, double kappa, double eps, double *b,
-              cudaStream_t s) {
-    rhs_kernel<<<div_up(S.n, 128), 128, 0, s>>>(S.n, S.cen.p, nc, q, xyz, kappa, eps, b);
+              const double *origin, cudaStream_t s) {
+    if (origin) {
+        rhs32_kernel<<<div_up(S.n, 256), 256, 0, s>>>(S.n, S.cen.p, nc, q, xyz, origin[0], origin[1], origin[2],
+                                                      (float)kappa, eps, b);
+    } else {
+        rhs_kernel<<<div_up(S.n, 128), 128, 0, s>>>(S.n, S.cen.p, nc, q, xyz, kappa, eps, b);
+    }
     PB_LAUNCH_CHECK();
 }
 

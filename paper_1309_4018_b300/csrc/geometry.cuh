@@ -14,8 +14,9 @@ void near_values(const Pair &Pr, const Targets &G, const SurfDev &src, int K, in
                  double *dK, cudaStream_t s);
 // Semi-analytical V_ii of every panel of S (input order).
 void self_integrals(const SurfDev &S, int N_k, double kappa, double *out, cudaStream_t s);
-// b_i = sum_k q_k G(c_i, r_k) / eps for the panels of S (input order).
+// b_i = sum_k q_k G(c_i, r_k) / eps for the panels of S (input order); FP64,
+// or FP32 with compensated tile sums relative to `origin` when it is not null.
 void rhs_rows(const SurfDev &S, int64_t nc, const double *q, const double *xyz, double kappa, double eps, double *b,
-              cudaStream_t s);
+              const double *origin, cudaStream_t s);
 
 }  // namespace pb

@@ -45,6 +45,7 @@ struct Tree {
     DevBuf<int32_t> level, first_child, nchild, parent, node_leaf;
     DevBuf<int64_t> start, count;
     DevBuf<double> centre, rb2;      // centre: nnodes * 3
+    DevBuf<float4> cen32;            // (centre - origin) in FP32, r_b^2
     DevBuf<int32_t> leaf_node;       // leaf index (Morton order) -> node
     DevBuf<int32_t> point_leaf;      // point index (input order) -> leaf index
     // sorted source data

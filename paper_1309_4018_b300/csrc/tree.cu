@@ -14,6 +14,7 @@
 //               Gauss points all lie in the target's direct-sum leaves
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "model.cuh"
 #include "tree.cuh"
@@ -141,6 +142,14 @@ __global__ void node_geom_kernel(int nnodes, const int32_t *__restrict__ level, 
     for (int a = 0; a < 3; ++a)
         centre[3 * b + a] = __dadd_rn(c[a], __dmul_rn(__dadd_rn((double)ijk[3 * b + a], 0.5), sl));
     rb2[b] = __dmul_rn(__dmul_rn(sl, sl), 0.75);
+}
+
+__global__ void centre32_kernel(int nnodes, const double *__restrict__ centre, const double *__restrict__ rb2,
+                                double ox, double oy, double oz, float4 *__restrict__ cen32) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nnodes) return;
+    cen32[b] = make_float4((float)(centre[3 * b] - ox), (float)(centre[3 * b + 1] - oy), (float)(centre[3 * b + 2] - oz),
+                           (float)rb2[b]);
 }
 
 __global__ void leaf_flag_kernel(int nnodes, const int32_t *__restrict__ nchild, const int64_t *__restrict__ start,
@@ -289,20 +298,26 @@ __device__ __forceinline__ bool is_near(double x, double y, double z, const doub
     return d2 < __dmul_rn(tl, tl);
 }
 
+// One warp per target: lanes walk the points of the target's direct-sum
+// leaves.  An FP32 distance test with a safety margin only prefilters; the
+// decision is the exact FP64 test above.  The fill pass writes the accepted
+// panels in any order and then sorts them ascending (deterministic result).
 template <bool FILL>
-__global__ void near_kernel(int64_t ntg, int K, const double *__restrict__ xs, const int32_t *__restrict__ selfp,
-                            int use_self, const int64_t *__restrict__ p2p_ptr, const int32_t *__restrict__ p2p_leafidx,
-                            const int32_t *__restrict__ leaf_node, const int64_t *__restrict__ start,
-                            const int64_t *__restrict__ count, const int32_t *__restrict__ perm,
-                            const int32_t *__restrict__ point_leaf, const double *__restrict__ cen,
-                            const double *__restrict__ L, double thres, int32_t *__restrict__ ncount,
-                            int32_t *__restrict__ excl, int32_t *__restrict__ self_excl,
-                            const int64_t *__restrict__ near_ptr, int32_t *__restrict__ near_panel,
-                            const int64_t *__restrict__ m2p_ptr, const int32_t *__restrict__ m2p_node,
-                            const double *__restrict__ centre, const double *__restrict__ rb2, double reach) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(128) near_kernel(
+    int64_t ntg, int K, const double *__restrict__ xs, const int32_t *__restrict__ selfp, int use_self,
+    const int64_t *__restrict__ p2p_ptr, const int32_t *__restrict__ p2p_leafidx, const int32_t *__restrict__ leaf_node,
+    const int64_t *__restrict__ start, const int64_t *__restrict__ count, const int32_t *__restrict__ perm,
+    const int32_t *__restrict__ pids, const int32_t *__restrict__ point_leaf, const double *__restrict__ cen,
+    const double *__restrict__ L, const float4 *__restrict__ pan32, double ox, double oy, double oz, double thres,
+    int32_t *__restrict__ ncount, int32_t *__restrict__ excl, int32_t *__restrict__ self_excl,
+    const int64_t *__restrict__ near_ptr, int32_t *__restrict__ near_panel, const int64_t *__restrict__ m2p_ptr,
+    const int32_t *__restrict__ m2p_node, const double *__restrict__ centre, const double *__restrict__ rb2,
+    double reach) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 4 + warp;
     if (i >= ntg) return;
     const double x = xs[3 * i], y = xs[3 * i + 1], z = xs[3 * i + 2];
+    const float fx = (float)(x - ox), fy = (float)(y - oy), fz = (float)(z - oz);
     const int me = use_self ? selfp[i] : -1;
     const int64_t l0 = p2p_ptr[i], l1 = p2p_ptr[i + 1];
     const int32_t *lst = p2p_leafidx + l0;
@@ -311,52 +326,76 @@ __global__ void near_kernel(int64_t ntg, int K, const double *__restrict__ xs, c
     const int64_t o = FILL ? near_ptr[i] : 0;
     for (int64_t e = 0; e < nl; ++e) {
         const int b = leaf_node[lst[e]];
-        for (int64_t q = start[b]; q < start[b] + count[b]; ++q) {
-            const int pt = perm[q];
-            const int j = pt / K, k = pt - j * K;
-            if (j == me || !is_near(x, y, z, cen, L, thres, j)) continue;
-            // handle panel j once, at its lowest-numbered point inside the direct leaves
-            bool first = true;
-            for (int kk = 0; kk < k; ++kk)
-                if (in_sorted(lst, nl, point_leaf[j * K + kk])) { first = false; break; }
-            if (!first) continue;
-            // points 0..k-1 lie outside the direct leaves when k > 0
-            bool all = k == 0;
-            for (int kk = k + 1; all && kk < K; ++kk)
-                if (!in_sorted(lst, nl, point_leaf[j * K + kk])) all = false;
-            if (all) {
-                if (FILL) near_panel[o + cnt] = j;
-                ++cnt;
-            } else {
-                ++ex;
+        const int64_t q0 = start[b], q1 = start[b] + count[b];
+        for (int64_t qb = q0; qb < q1; qb += 32) {
+            const int64_t q = qb + lane;
+            bool acc = false, exc = false;
+            int j = -1;
+            if (q < q1) {
+                j = pids[q];
+                const float4 pc = pan32[j];
+                const float dx = fx - pc.x, dy = fy - pc.y, dz = fz - pc.z;
+                const float d2 = dx * dx + dy * dy + dz * dz;
+                if (j != me && d2 < pc.w && is_near(x, y, z, cen, L, thres, j)) {
+                    const int k = perm[q] - j * K;
+                    // handle panel j once, at its lowest-numbered point inside the direct leaves
+                    bool first = true;
+                    for (int kk = 0; kk < k; ++kk)
+                        if (in_sorted(lst, nl, point_leaf[j * K + kk])) { first = false; break; }
+                    if (first) {
+                        // points 0..k-1 lie outside the direct leaves when k > 0
+                        bool all = k == 0;
+                        for (int kk = k + 1; all && kk < K; ++kk)
+                            if (!in_sorted(lst, nl, point_leaf[j * K + kk])) all = false;
+                        acc = all;
+                        exc = !all;
+                    }
+                }
             }
+            const uint32_t ba = __ballot_sync(0xffffffffu, acc);
+            if (FILL && acc) near_panel[o + cnt + __popc(ba & ((1u << lane) - 1u))] = j;
+            cnt += __popc(ba);
+            ex += __popc(__ballot_sync(0xffffffffu, exc));
         }
     }
     if (FILL) {
-        // ascending panel order
-        int32_t *a = near_panel + o;
-        for (int u = 1; u < cnt; ++u) {
-            int v = a[u], w = u - 1;
-            while (w >= 0 && a[w] > v) { a[w + 1] = a[w]; --w; }
-            a[w + 1] = v;
-        }
-    } else {
-        // near panels lying wholly in accepted boxes: only boxes that can hold a
-        // point within `reach` (>= thres L_j + panel radius) of the target are scanned
-        for (int64_t e = m2p_ptr[i]; e < m2p_ptr[i + 1]; ++e) {
-            const int b = m2p_node[e];
-            const double bx = x - centre[3 * b], by = y - centre[3 * b + 1], bz = z - centre[3 * b + 2];
-            const double rr = reach + sqrt(rb2[b]);
-            if (bx * bx + by * by + bz * bz >= rr * rr) continue;
-            for (int64_t q = start[b]; q < start[b] + count[b]; ++q) {
-                const int pt = perm[q];
-                const int j = pt / K;
-                if (pt - j * K != 0 || j == me || !is_near(x, y, z, cen, L, thres, j)) continue;
-                bool any = false;
-                for (int kk = 0; kk < K && !any; ++kk) any = in_sorted(lst, nl, point_leaf[j * K + kk]);
-                if (!any) ++ex;
+        __syncwarp();
+        if (lane == 0) {  // ascending panel order
+            int32_t *a = near_panel + o;
+            for (int u = 1; u < cnt; ++u) {
+                int v = a[u], w = u - 1;
+                while (w >= 0 && a[w] > v) { a[w + 1] = a[w]; --w; }
+                a[w + 1] = v;
             }
         }
+        return;
+    }
+    // near panels lying wholly in accepted boxes: only boxes that can hold a
+    // point within `reach` (>= thres L_j + panel radius) of the target are scanned
+    for (int64_t e = m2p_ptr[i]; e < m2p_ptr[i + 1]; ++e) {
+        const int b = m2p_node[e];
+        const double bx = x - centre[3 * b], by = y - centre[3 * b + 1], bz = z - centre[3 * b + 2];
+        const double rr = reach + sqrt(rb2[b]);
+        if (bx * bx + by * by + bz * bz >= rr * rr) continue;
+        const int64_t q0 = start[b], q1 = start[b] + count[b];
+        for (int64_t qb = q0; qb < q1; qb += 32) {
+            const int64_t q = qb + lane;
+            bool exc = false;
+            if (q < q1) {
+                const int j = pids[q];
+                const float4 pc = pan32[j];
+                const float dx = fx - pc.x, dy = fy - pc.y, dz = fz - pc.z;
+                if (perm[q] == j * K && j != me && dx * dx + dy * dy + dz * dz < pc.w &&
+                    is_near(x, y, z, cen, L, thres, j)) {
+                    bool any = false;
+                    for (int kk = 0; kk < K && !any; ++kk) any = in_sorted(lst, nl, point_leaf[j * K + kk]);
+                    exc = !any;
+                }
+            }
+            ex += __popc(__ballot_sync(0xffffffffu, exc));
+        }
+    }
+    if (lane == 0) {
         ncount[i] = cnt;
         excl[i] = ex;
         int se = 0;
@@ -367,13 +406,24 @@ __global__ void near_kernel(int64_t ntg, int K, const double *__restrict__ xs, c
     }
 }
 
-// max_j (thres L_j + max_v |v - c_j|) over the panels of a surface (one block).
+// FP32 copy of the panel centroids (relative to the tree origin) and a
+// conservative FP32 bound of the squared near-singular radius.
+__global__ void pan32_kernel(int64_t n, const double *__restrict__ cen, const double *__restrict__ L, double thres,
+                             double ox, double oy, double oz, float4 *__restrict__ pan32) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double tl = thres * L[j];
+    pan32[j] = make_float4((float)(cen[3 * j] - ox), (float)(cen[3 * j + 1] - oy), (float)(cen[3 * j + 2] - oz),
+                           (float)(tl * tl * (1.0 + 1e-3) + 1e-3));
+}
+
+// max_j (thres L_j + max_v |v - c_j|) over the panels of a surface; the
+// non-negative doubles are combined with an integer atomic max of their bits.
 __global__ void reach_kernel(int64_t n, const double *__restrict__ v, const int32_t *__restrict__ t,
                              const double *__restrict__ cen, const double *__restrict__ L, double thres,
-                             double *__restrict__ out) {
-    __shared__ double sm[1024];
+                             unsigned long long *__restrict__ out) {
     double m = 0.0;
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         double r = 0.0;
         for (int c = 0; c < 3; ++c) {
             const int a = t[3 * j + c];
@@ -382,13 +432,8 @@ __global__ void reach_kernel(int64_t n, const double *__restrict__ v, const int3
         }
         m = fmax(m, thres * L[j] + r);
     }
-    sm[threadIdx.x] = m;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + w]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out = sm[0] * (1.0 + 1e-12) + 1e-12;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m * (1.0 + 1e-12) + 1e-12));
 }
 
 __global__ void node_to_leaf_kernel(int64_t n, const int32_t *__restrict__ nodes, const int32_t *__restrict__ node_leaf,
@@ -523,6 +568,10 @@ void build_tree(Tree &T, const SurfDev &S, int K, int ncrit, cudaStream_t s) {
     node_geom_kernel<<<div_up(T.nnodes, 128), 128, 0, s>>>(T.nnodes, T.level.p, ijk.p, T.corner[0], T.corner[1],
                                                            T.corner[2], T.side, T.centre.p, T.rb2.p);
     PB_LAUNCH_CHECK();
+    T.cen32.alloc(T.nnodes);
+    centre32_kernel<<<div_up(T.nnodes, 128), 128, 0, s>>>(T.nnodes, T.centre.p, T.rb2.p, T.origin[0], T.origin[1],
+                                                          T.origin[2], T.cen32.p);
+    PB_LAUNCH_CHECK();
     // leaves in Morton order (= depth-first pre-order)
     TmpBuf<int32_t> head(n, s);
     TmpBuf<int64_t> hscan(n + 1, s);
@@ -637,19 +686,28 @@ void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, 
     unions(Pr.m2p_ptr.p, Pr.m2p_node.p, T.nnodes, Pr.gm2p_ptr, Pr.gm2p, Pr.n_gm2p);
     // near-singular lists
     TmpBuf<int32_t> nc(m, s), ex(m, s), se(m, s);
-    TmpBuf<double> reach_d(1, s);
-    reach_kernel<<<1, 1024, 0, s>>>(src.n, src.verts.p, src.tris.p, src.cen.p, src.L.p, prm.thres, reach_d.p);
+    TmpBuf<unsigned long long> reach_d(1, s);
+    PB_CUDA_TRY(cudaMemsetAsync(reach_d.p, 0, sizeof(unsigned long long), s));
+    reach_kernel<<<std::min<int64_t>(592, div_up(src.n, 256)), 256, 0, s>>>(src.n, src.verts.p, src.tris.p, src.cen.p,
+                                                                           src.L.p, prm.thres, reach_d.p);
     PB_LAUNCH_CHECK();
-    double reach = 0.0;
-    PB_CUDA_TRY(cudaMemcpyAsync(&reach, reach_d.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    unsigned long long rbits = 0;
+    PB_CUDA_TRY(cudaMemcpyAsync(&rbits, reach_d.p, sizeof(rbits), cudaMemcpyDeviceToHost, s));
+    TmpBuf<float4> pan32(std::max<int64_t>(1, src.n), s);
+    pan32_kernel<<<div_up(src.n, 256), 256, 0, s>>>(src.n, src.cen.p, src.L.p, prm.thres, T.origin[0], T.origin[1],
+                                                     T.origin[2], pan32.p);
+    PB_LAUNCH_CHECK();
     PB_CUDA_TRY(cudaStreamSynchronize(s));
+    double reach = 0.0;
+    std::memcpy(&reach, &rbits, sizeof(reach));
     Pr.near_ptr.alloc(m + 1);
     if (m) {
-        near_kernel<false><<<div_up(m, 128), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self,
-                                                          Pr.p2p_ptr.p, pleaf.p, T.leaf_node.p, T.start.p, T.count.p,
-                                                          T.perm.p, T.point_leaf.p, src.cen.p, src.L.p, prm.thres,
-                                                          nc.p, ex.p, se.p, nullptr, nullptr, Pr.m2p_ptr.p,
-                                                          Pr.m2p_node.p, T.centre.p, T.rb2.p, reach);
+        near_kernel<false><<<div_up(m, 4), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
+                                                        pleaf.p, T.leaf_node.p, T.start.p, T.count.p, T.perm.p,
+                                                        T.pids.p, T.point_leaf.p, src.cen.p, src.L.p, pan32.p,
+                                                        T.origin[0], T.origin[1], T.origin[2], prm.thres, nc.p, ex.p,
+                                                        se.p, nullptr, nullptr, Pr.m2p_ptr.p, Pr.m2p_node.p,
+                                                        T.centre.p, T.rb2.p, reach);
         PB_LAUNCH_CHECK();
     }
     exclusive_scan_i32_to_i64(nc.p, Pr.near_ptr.p, m, s);
@@ -658,11 +716,12 @@ void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, 
     Pr.self_excl = device_sum_i32(se.p, m, s);
     Pr.near_panel.alloc(std::max<int64_t>(1, Pr.n_near));
     if (m) {
-        near_kernel<true><<<div_up(m, 128), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self,
-                                                         Pr.p2p_ptr.p, pleaf.p, T.leaf_node.p, T.start.p, T.count.p,
-                                                         T.perm.p, T.point_leaf.p, src.cen.p, src.L.p, prm.thres,
-                                                         nullptr, nullptr, nullptr, Pr.near_ptr.p, Pr.near_panel.p,
-                                                         Pr.m2p_ptr.p, Pr.m2p_node.p, T.centre.p, T.rb2.p, reach);
+        near_kernel<true><<<div_up(m, 4), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
+                                                       pleaf.p, T.leaf_node.p, T.start.p, T.count.p, T.perm.p,
+                                                       T.pids.p, T.point_leaf.p, src.cen.p, src.L.p, pan32.p,
+                                                       T.origin[0], T.origin[1], T.origin[2], prm.thres, nullptr,
+                                                       nullptr, nullptr, Pr.near_ptr.p, Pr.near_panel.p, Pr.m2p_ptr.p,
+                                                       Pr.m2p_node.p, T.centre.p, T.rb2.p, reach);
         PB_LAUNCH_CHECK();
     }
     PB_CUDA_TRY(cudaStreamSynchronize(s));

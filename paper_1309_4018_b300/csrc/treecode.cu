@@ -160,40 +160,57 @@ __global__ void __launch_bounds__(128) p2m_kernel(int nleaves, const int32_t *__
 
 // ---------------------------------------------------------------- M2M (one level, bottom-up)
 // M_parent^k = sum_children sum_{l <= k} C(k, l) (y_child - y_parent)^(k-l) M_child^l;
-// the dipole moments D shift with the same rule.
+// the dipole moments D shift with the same rule.  One block per node of the
+// level: the children's moments (contiguous node ids), the powers of the
+// shifts and the binomials are staged in shared memory; one thread per term.
+constexpr int kM2MMaxShared = 8 * 2 * 455 * 8;
+
 template <typename T>
-__global__ void m2m_kernel(int nb, int nodes_begin, const int32_t *__restrict__ first_child,
-                           const int32_t *__restrict__ nchild, const double *__restrict__ centre, int P, int NT,
-                           T *__restrict__ mom) {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int t = (int)(gid / NT), k = (int)(gid % NT);
-    if (t >= nb) return;
-    const int b = nodes_begin + t;
+__global__ void __launch_bounds__(128) m2m_kernel(int nodes_begin, const int32_t *__restrict__ first_child,
+                                                  const int32_t *__restrict__ nchild,
+                                                  const double *__restrict__ centre, int P, int NT,
+                                                  T *__restrict__ mom) {
+    extern __shared__ __align__(16) unsigned char m2m_smem[];
+    T *smom = reinterpret_cast<T *>(m2m_smem);
+    __shared__ T hp[8][3][kMaxP + 1];
+    __shared__ T sbin[kMaxP + 1][kMaxP + 1];
+    const int b = nodes_begin + blockIdx.x;
     const int nc = nchild[b];
     if (nc == 0) return;
-    const int k1 = c_terms[3 * k], k2 = c_terms[3 * k + 1], k3 = c_terms[3 * k + 2];
-    T accM = 0, accD = 0;
-    for (int c = first_child[b]; c < first_child[b] + nc; ++c) {
-        const T h[3] = {(T)(centre[3 * c] - centre[3 * b]), (T)(centre[3 * c + 1] - centre[3 * b + 1]),
-                        (T)(centre[3 * c + 2] - centre[3 * b + 2])};
-        const T *mc = mom + (int64_t)c * 2 * NT;
-        T hp[3][kMaxP + 1];
-        for (int a = 0; a < 3; ++a) {
-            hp[a][0] = 1;
-            for (int e = 1; e <= P; ++e) hp[a][e] = hp[a][e - 1] * h[a];
-        }
-        for (int l1 = 0; l1 <= k1; ++l1)
-            for (int l2 = 0; l2 <= k2; ++l2)
-                for (int l3 = 0; l3 <= k3; ++l3) {
-                    const T coef = (T)(c_binom[k1][l1] * c_binom[k2][l2] * c_binom[k3][l3]) * hp[0][k1 - l1] *
-                                   hp[1][k2 - l2] * hp[2][k3 - l3];
-                    const int li = term_index(l1, l2, l3);
-                    accM += coef * mc[li];
-                    accD += coef * mc[NT + li];
-                }
+    const int fc = first_child[b];
+    for (int i = threadIdx.x; i < nc * 2 * NT; i += blockDim.x) smom[i] = mom[(int64_t)fc * 2 * NT + i];
+    for (int i = threadIdx.x; i < nc * 3; i += blockDim.x) {
+        const int c = i / 3, ax = i - 3 * c;
+        const T h = (T)(centre[3 * (fc + c) + ax] - centre[3 * b + ax]);
+        T v = 1;
+        for (int e = 0; e <= P; ++e) { hp[c][ax][e] = v; v *= h; }
     }
-    mom[(int64_t)b * 2 * NT + k] = accM;
-    mom[(int64_t)b * 2 * NT + NT + k] = accD;
+    for (int i = threadIdx.x; i < (P + 1) * (P + 1); i += blockDim.x) {
+        const int n = i / (P + 1), k = i - n * (P + 1);
+        sbin[n][k] = (T)c_binom[n][k];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < NT; k += blockDim.x) {
+        const int k1 = c_terms[3 * k], k2 = c_terms[3 * k + 1], k3 = c_terms[3 * k + 2];
+        T accM = 0, accD = 0;
+        for (int c = 0; c < nc; ++c) {
+            const T *mc = smom + c * 2 * NT;
+            for (int l1 = 0; l1 <= k1; ++l1) {
+                const T f1 = sbin[k1][l1] * hp[c][0][k1 - l1];
+                for (int l2 = 0; l2 <= k2; ++l2) {
+                    const T f2 = f1 * sbin[k2][l2] * hp[c][1][k2 - l2];
+                    for (int l3 = 0; l3 <= k3; ++l3) {
+                        const T coef = f2 * sbin[k3][l3] * hp[c][2][k3 - l3];
+                        const int li = term_index(l1, l2, l3);
+                        accM += coef * mc[li];
+                        accD += coef * mc[NT + li];
+                    }
+                }
+            }
+        }
+        mom[(int64_t)b * 2 * NT + k] = accM;
+        mom[(int64_t)b * 2 * NT + NT + k] = accD;
+    }
 }
 
 // ---------------------------------------------------------------- P2P, FP32 (mixed precision)
@@ -213,6 +230,9 @@ __device__ __forceinline__ void comp_add(float &hi, float &lo, float v) {
     hi = t;
 }
 
+// kSplit warps share one group of 32 targets and take its list entries in turn.
+constexpr int kSplit = 4;
+
 template <int NK, bool Y0, bool Y1>
 __global__ void __launch_bounds__(128) p2p32_kernel(int64_t ntg, int64_t ngroups, const double *__restrict__ xs,
                                                     double ox, double oy, double oz, const int32_t *__restrict__ selfp,
@@ -221,10 +241,10 @@ __global__ void __launch_bounds__(128) p2p32_kernel(int64_t ntg, int64_t ngroups
                                                     const int64_t *__restrict__ start, const int64_t *__restrict__ count,
                                                     const float4 *__restrict__ A, const float4 *__restrict__ B,
                                                     KSet ks, double *__restrict__ VK0, double *__restrict__ VK1) {
-    __shared__ float4 sA[4][32], sB[4][32];
+    __shared__ float4 sA[kSplit][32], sB[kSplit][32];
+    __shared__ float red[kSplit][2 * NK][2][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t g = (int64_t)blockIdx.x * 4 + warp;
-    if (g >= ngroups) return;
+    const int64_t g = blockIdx.x;
     const int64_t t = g * 32 + lane;
     const bool valid = t < ntg;
     float tx = 0.f, ty = 0.f, tz = 0.f;
@@ -237,9 +257,11 @@ __global__ void __launch_bounds__(128) p2p32_kernel(int64_t ntg, int64_t ngroups
     }
     const float k0 = ks.kap[0], k1 = ks.kap[1];
     const float l2e0 = -k0 * 1.4426950408889634f, l2e1 = -k1 * 1.4426950408889634f;
-    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    float hi[2 * NK], lo[2 * NK];
+#pragma unroll
+    for (int a = 0; a < 2 * NK; ++a) { hi[a] = 0.f; lo[a] = 0.f; }
     const int64_t e0 = gptr[g], e1 = gptr[g + 1];
-    for (int64_t e = e0; e < e1; ++e) {
+    for (int64_t e = e0 + warp; e < e1; e += kSplit) {
         const int2 en = gent[e];
         const bool active = valid && ((en.y >> lane) & 1);
         const int node = leaf_node[en.x];
@@ -291,12 +313,25 @@ __global__ void __launch_bounds__(128) p2p32_kernel(int64_t ntg, int64_t ngroups
             __syncwarp();
         }
     }
-    if (valid) {
-        VK0[t] = ((double)hi[0] + (double)lo[0]) * kInv4Pi;
-        VK0[ntg + t] = ((double)hi[1] + (double)lo[1]) * kInv4Pi;
+#pragma unroll
+    for (int a = 0; a < 2 * NK; ++a) {
+        red[warp][a][0][lane] = hi[a];
+        red[warp][a][1][lane] = lo[a];
+    }
+    __syncthreads();
+    if (warp == 0 && valid) {
+        double out[2 * NK];
+#pragma unroll
+        for (int a = 0; a < 2 * NK; ++a) {
+            double v = 0.0;
+            for (int w = 0; w < kSplit; ++w) v += (double)red[w][a][0][lane] + (double)red[w][a][1][lane];
+            out[a] = v * kInv4Pi;
+        }
+        VK0[t] = out[0];
+        VK0[ntg + t] = out[1];
         if (NK == 2) {
-            VK1[t] = ((double)hi[2] + (double)lo[2]) * kInv4Pi;
-            VK1[ntg + t] = ((double)hi[3] + (double)lo[3]) * kInv4Pi;
+            VK1[t] = out[2 % (2 * NK)];
+            VK1[ntg + t] = out[3 % (2 * NK)];
         }
     }
 }
@@ -310,10 +345,10 @@ __global__ void __launch_bounds__(128) p2p64_kernel(int64_t ntg, int64_t ngroups
                                                     const int64_t *__restrict__ start, const int64_t *__restrict__ count,
                                                     const double *__restrict__ src, double kap0, double kap1,
                                                     double *__restrict__ VK0, double *__restrict__ VK1) {
-    __shared__ double4 sA[4][32], sB[4][32];
+    __shared__ double4 sA[kSplit][32], sB[kSplit][32];
+    __shared__ double red[kSplit][4][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t g = (int64_t)blockIdx.x * 4 + warp;
-    if (g >= ngroups) return;
+    const int64_t g = blockIdx.x;
     const int64_t t = g * 32 + lane;
     const bool valid = t < ntg;
     double tx = 0, ty = 0, tz = 0;
@@ -325,7 +360,7 @@ __global__ void __launch_bounds__(128) p2p64_kernel(int64_t ntg, int64_t ngroups
     double acc[4] = {0, 0, 0, 0};
     const int64_t e0 = gptr[g], e1 = gptr[g + 1];
     const double4 *src4 = reinterpret_cast<const double4 *>(src);
-    for (int64_t e = e0; e < e1; ++e) {
+    for (int64_t e = e0 + warp; e < e1; e += kSplit) {
         const int2 en = gent[e];
         const bool active = valid && ((en.y >> lane) & 1);
         const int node = leaf_node[en.x];
@@ -373,12 +408,21 @@ __global__ void __launch_bounds__(128) p2p64_kernel(int64_t ntg, int64_t ngroups
             __syncwarp();
         }
     }
-    if (valid) {
-        VK0[t] = acc[0] * kInv4Pi;
-        VK0[ntg + t] = acc[1] * kInv4Pi;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) red[warp][a][lane] = acc[a];
+    __syncthreads();
+    if (warp == 0 && valid) {
+        double out[4];
+        for (int a = 0; a < 4; ++a) {
+            double v = 0.0;
+            for (int w = 0; w < kSplit; ++w) v += red[w][a][lane];
+            out[a] = v * kInv4Pi;
+        }
+        VK0[t] = out[0];
+        VK0[ntg + t] = out[1];
         if (NK == 2) {
-            VK1[t] = acc[2] * kInv4Pi;
-            VK1[ntg + t] = acc[3] * kInv4Pi;
+            VK1[t] = out[2];
+            VK1[ntg + t] = out[3];
         }
     }
 }
@@ -464,16 +508,20 @@ __device__ void m2p_eval_rt(int P, T ux, T uy, T uz, T kappa, const T *__restric
     }
 }
 
-// One warp per group of 32 sorted targets walking the union of their
-// accepted boxes; each lane evaluates the boxes of its own list.
+// One block of kSplit warps per group of 32 sorted targets; the warps take the
+// union of the group's accepted boxes in turn and each lane evaluates the
+// boxes of its own list.  FP32: box centres relative to the tree origin in
+// FP32, per-box results added into compensated (hi, lo) FP32 sums; FP64: all
+// in double.
 template <int P, bool YUK, typename T>
 __global__ void __launch_bounds__(128) m2p_kernel(int64_t ntg, int64_t ngroups, int Prt, const double *__restrict__ xs,
                                                   double ox, double oy, double oz, const int64_t *__restrict__ gptr,
                                                   const int2 *__restrict__ gent, const double *__restrict__ centre,
-                                                  const T *__restrict__ mom, double kappa, double *__restrict__ VK) {
+                                                  const float4 *__restrict__ cen32, const T *__restrict__ mom,
+                                                  double kappa, double *__restrict__ VK) {
+    __shared__ double red[kSplit][2][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t g = (int64_t)blockIdx.x * 4 + warp;
-    if (g >= ngroups) return;
+    const int64_t g = blockIdx.x;
     const int64_t t = g * 32 + lane;
     const bool valid = t < ntg;
     const int Pe = P >= 0 ? P : Prt;
@@ -483,23 +531,37 @@ __global__ void __launch_bounds__(128) m2p_kernel(int64_t ntg, int64_t ngroups, 
         x = xs[3 * t] - ox; y = xs[3 * t + 1] - oy; z = xs[3 * t + 2] - oz;
     }
     const T tx = (T)x, ty = (T)y, tz = (T)z;
-    double accV = 0, accK = 0;
-    for (int64_t e = gptr[g]; e < gptr[g + 1]; ++e) {
+    T hiV = 0, loV = 0, hiK = 0, loK = 0;
+    for (int64_t e = gptr[g] + warp; e < gptr[g + 1]; e += kSplit) {
         const int2 en = gent[e];
         if (!(valid && ((en.y >> lane) & 1))) continue;
         const int b = en.x;
-        const T ux = (T)(centre[3 * b] - ox) - tx;
-        const T uy = (T)(centre[3 * b + 1] - oy) - ty;
-        const T uz = (T)(centre[3 * b + 2] - oz) - tz;
+        T ux, uy, uz;
+        if constexpr (sizeof(T) == 4) {
+            const float4 c = cen32[b];
+            ux = c.x - tx; uy = c.y - ty; uz = c.z - tz;
+        } else {
+            ux = (T)centre[3 * b] - tx; uy = (T)centre[3 * b + 1] - ty; uz = (T)centre[3 * b + 2] - tz;
+        }
         T V, K;
         if constexpr (P >= 0) m2p_eval<(P >= 0 ? P : 0), YUK, T>(ux, uy, uz, (T)kappa, mom + (int64_t)b * 2 * NT, V, K);
         else m2p_eval_rt<YUK, T>(Prt, ux, uy, uz, (T)kappa, mom + (int64_t)b * 2 * NT, V, K);
-        accV += (double)V;
-        accK += (double)K;
+        if constexpr (sizeof(T) == 4) {
+            comp_add(hiV, loV, V);
+            comp_add(hiK, loK, K);
+        } else {
+            hiV += V;
+            hiK += K;
+        }
     }
-    if (valid) {
-        VK[t] += accV * kInv4Pi;
-        VK[ntg + t] += accK * kInv4Pi;
+    red[warp][0][lane] = (double)hiV + (double)loV;
+    red[warp][1][lane] = (double)hiK + (double)loK;
+    __syncthreads();
+    if (warp == 0 && valid) {
+        double v = 0.0, k = 0.0;
+        for (int w = 0; w < kSplit; ++w) { v += red[w][0][lane]; k += red[w][1][lane]; }
+        VK[t] += v * kInv4Pi;
+        VK[ntg + t] += k * kInv4Pi;
     }
 }
 
@@ -541,14 +603,14 @@ __global__ void combine_kernel(int64_t n, const int32_t *__restrict__ rank, cons
 template <typename T>
 void launch_m2p_typed(int P, bool yuk, int64_t ntg, int64_t ng, const double *xs, const double o[3], const Pair &Pr,
                       const Tree &Tr, const T *mom, double kappa, double *VK, cudaStream_t s) {
-    const unsigned grid = (unsigned)((ng + 3) / 4);
+    const unsigned grid = (unsigned)ng;
 #define PB_M2P_CASE(PP)                                                                                     \
     case PP:                                                                                                \
         if (yuk) m2p_kernel<PP, true, T><<<grid, 128, 0, s>>>(ntg, ng, P, xs, o[0], o[1], o[2],            \
-                                                              Pr.gm2p_ptr.p, Pr.gm2p.p, Tr.centre.p, mom,   \
-                                                              kappa, VK);                                  \
+                                                              Pr.gm2p_ptr.p, Pr.gm2p.p, Tr.centre.p,       \
+                                                              Tr.cen32.p, mom, kappa, VK);                                  \
         else m2p_kernel<PP, false, T><<<grid, 128, 0, s>>>(ntg, ng, P, xs, o[0], o[1], o[2], Pr.gm2p_ptr.p, \
-                                                           Pr.gm2p.p, Tr.centre.p, mom, kappa, VK);         \
+                                                           Pr.gm2p.p, Tr.centre.p, Tr.cen32.p, mom, kappa, VK); \
         break;
     switch (P) {
         PB_M2P_CASE(0)
@@ -562,9 +624,9 @@ void launch_m2p_typed(int P, bool yuk, int64_t ntg, int64_t ng, const double *xs
         PB_M2P_CASE(8)
         default:
             if (yuk) m2p_kernel<-1, true, T><<<grid, 128, 0, s>>>(ntg, ng, P, xs, o[0], o[1], o[2], Pr.gm2p_ptr.p,
-                                                                  Pr.gm2p.p, Tr.centre.p, mom, kappa, VK);
+                                                                  Pr.gm2p.p, Tr.centre.p, Tr.cen32.p, mom, kappa, VK);
             else m2p_kernel<-1, false, T><<<grid, 128, 0, s>>>(ntg, ng, P, xs, o[0], o[1], o[2], Pr.gm2p_ptr.p,
-                                                               Pr.gm2p.p, Tr.centre.p, mom, kappa, VK);
+                                                               Pr.gm2p.p, Tr.centre.p, Tr.cen32.p, mom, kappa, VK);
     }
 #undef PB_M2P_CASE
     PB_LAUNCH_CHECK();
@@ -573,6 +635,8 @@ void launch_m2p_typed(int P, bool yuk, int64_t ntg, int64_t ng, const double *xs
 }  // namespace
 
 void upload_term_tables() {
+    PB_CUDA_TRY(cudaFuncSetAttribute(m2m_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kM2MMaxShared));
+    PB_CUDA_TRY(cudaFuncSetAttribute(m2m_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kM2MMaxShared / 2));
     int terms[3 * 455];
     int i = 0;
     for (int n = 0; n <= kMaxP; ++n)
@@ -619,15 +683,14 @@ void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s) {
                                                       Tr.origin[0], Tr.origin[1], Tr.origin[2], sv, P, NT, Tr.mom64.p);
     }
     PB_LAUNCH_CHECK();
+    const size_t shm = (size_t)8 * 2 * NT * (mixed ? sizeof(float) : sizeof(double));
     for (int l = Tr.nlevels - 2; l >= 0; --l) {
         const int b0 = Tr.level_off[l], nb = Tr.level_off[l + 1] - b0;
-        const int64_t work = (int64_t)nb * NT;
         if (mixed)
-            m2m_kernel<float><<<div_up(work, 128), 128, 0, s>>>(nb, b0, Tr.first_child.p, Tr.nchild.p, Tr.centre.p, P,
-                                                                NT, Tr.mom32.p);
+            m2m_kernel<float><<<nb, 128, shm, s>>>(b0, Tr.first_child.p, Tr.nchild.p, Tr.centre.p, P, NT, Tr.mom32.p);
         else
-            m2m_kernel<double><<<div_up(work, 128), 128, 0, s>>>(nb, b0, Tr.first_child.p, Tr.nchild.p, Tr.centre.p,
-                                                                 P, NT, Tr.mom64.p);
+            m2m_kernel<double><<<nb, 128, shm, s>>>(b0, Tr.first_child.p, Tr.nchild.p, Tr.centre.p, P, NT,
+                                                    Tr.mom64.p);
         PB_LAUNCH_CHECK();
     }
 }
@@ -635,7 +698,7 @@ void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s) {
 void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self, bool mixed, cudaStream_t s) {
     const int64_t ntg = G.n, ng = (ntg + 31) / 32;
     if (!ng) return;
-    const unsigned grid = (unsigned)((ng + 3) / 4);
+    const unsigned grid = (unsigned)ng;
     const int nk = (int)Pr.kappas.size();
     const double k0 = Pr.kappas[0], k1 = nk > 1 ? Pr.kappas[1] : 0.0;
     const bool y0 = k0 != 0.0, y1 = k1 != 0.0;

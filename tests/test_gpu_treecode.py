@@ -59,3 +59,16 @@ def test_mixed_energy_within_1e4_of_fp64():
     e64 = problem(d, precision="fp64", theta=-1.0, gmres_tol=1e-10).solve().dG_solv
     em = problem(d, precision="mixed", theta=0.5, P=6, ncrit=40, gmres_tol=1e-6).solve().dG_solv
     assert abs(em - e64) <= 1e-4 * abs(e64)
+
+
+def test_mixed_rhs_close_to_oracle():
+    from synth.configs import protein_problem
+    d = protein_problem()
+    pb = problem(d, precision="mixed", theta=0.5, P=6, ncrit=300)
+    b = pb.rhs()
+    n = d["surfaces"][0]["tris"].shape[0]
+    rows = np.arange(0, n, 97)
+    sd = OD.surfaces_data(d)
+    ref = OD._green(sd[0].cen[rows], np.asarray(d["charges"]["xyz"]), 0.0) @ d["charges"]["q"] / 4.0
+    assert rel_l2(b[rows], ref) <= 1e-5
+    assert np.all(b[n:] == 0.0)
