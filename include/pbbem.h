@@ -136,9 +136,10 @@ int pb_reaction_potential(pb_problem *pb, const double *x, double *phi_reac);
 int pb_coulomb_energy(pb_problem *pb, double *out);
 
 /* Per-phase device time of one operator application (CUDA events on the
- * context stream), averaged over `reps` applications to a fixed random-free
+ * context stream), averaged over `reps` applications to the given unknown
  * vector x (host, 2 N).  phase_ms[0..5]: source strengths + P2M/M2M, P2P,
- * M2P, near-singular corrections, block combine, total.  Not in the paper:
+ * M2P, per-target gather of the partials with the near-singular and self
+ * corrections, block combine, total.  Not in the paper:
  * instrumentation for the per-phase timings of the measurement. */
 int pb_profile_operator(pb_problem *pb, const double *x, int reps, double *phase_ms);
 /* Number of kernels this library has launched since it was loaded. */

@@ -221,6 +221,12 @@ void setup_problem(pb_problem *pb) {
         if (P.n_m2p > 0) pb->need_far[P.tree] = true;
         const size_t nk = P.kappas.size();
         P.VK.resize(nk); P.dV.resize(nk); P.dK.resize(nk); P.selfV.resize(nk);
+        if (prm.precision == PB_MIXED) P.p2p_part32.alloc(2 * nk * std::max<int64_t>(1, P.n_p2p));
+        else P.p2p_part.alloc(2 * nk * std::max<int64_t>(1, P.n_p2p));
+        if (P.n_m2p > 0) {
+            if (prm.precision == PB_MIXED) P.m2p_part32.alloc(2 * nk * P.n_m2p);
+            else P.m2p_part64.alloc(2 * nk * P.n_m2p);
+        }
         for (size_t k = 0; k < nk; ++k) {
             P.VK[k].alloc(2 * std::max<int64_t>(1, G.n));
             P.dV[k].alloc(std::max<int64_t>(1, P.n_near));
@@ -234,6 +240,10 @@ void setup_problem(pb_problem *pb) {
     };
     for (auto &P : pb->pairs) prepare(P, false);
     for (auto &P : pb->cpairs) prepare(P, true);
+    if (prm.precision == PB_MIXED) {
+        for (auto &P : pb->pairs) { near_to_float(P, s); targets_to_float(P, pb->G[P.tgt], pb->T[P.tree], s); }
+        for (auto &P : pb->cpairs) { near_to_float(P, s); targets_to_float(P, pb->G[P.tgt], pb->T[P.tree], s); }
+    }
     // right-hand side
     pb->b.alloc(2 * pb->N);
     pb->b.zero(s);
@@ -307,7 +317,7 @@ void apply_operator(pb_problem *pb, const double *xd, double *yd, PhaseEvents *p
     mark(3);
     for (auto &P : pb->pairs) {
         const double *phi = xd + 2 * pb->off[P.tree];
-        launch_near(P, pb->G[P.tgt], P.tgt == P.tree, phi, phi + pb->S[P.tree].n, s);
+        launch_gather(P, pb->G[P.tgt], mixed, P.tgt == P.tree, phi, phi + pb->S[P.tree].n, s);
     }
     mark(4);
     for (int sf = 0; sf < ns; ++sf) {
@@ -352,7 +362,7 @@ void reaction(pb_problem *pb, const double *xd) {
         const double *phi = xd + 2 * pb->off[P.tree];
         launch_p2p(P, G, Tr, false, mixed, s);
         launch_m2p(P, G, Tr, prm.P, mixed, s);
-        launch_near(P, G, false, phi, phi + pb->S[P.tree].n, s);
+        launch_gather(P, G, mixed, false, phi, phi + pb->S[P.tree].n, s);
     }
     CombineRow row{};
     row.nterm = (int)pb->reac.size();

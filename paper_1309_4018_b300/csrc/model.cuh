@@ -78,10 +78,20 @@ struct Pair {
     DevBuf<int64_t> m2p_ptr, p2p_ptr, near_ptr;
     DevBuf<int32_t> m2p_node, p2p_node, near_panel;
     int64_t n_m2p = 0, n_p2p = 0, n_near = 0, near_excl = 0, self_excl = 0, p2p_pairs = 0;
-    // per warp of 32 sorted targets: union of the lists with lane masks
-    DevBuf<int64_t> gp2p_ptr, gm2p_ptr;
-    DevBuf<int2> gp2p, gm2p;         // (leaf index | node, lane mask)
-    int64_t n_gp2p = 0, n_gm2p = 0;
+    // Entry-major work: for every leaf (P2P) / box (M2P) the (sorted target,
+    // list entry) pairs that use it, grouped by leaf / box and packed 32 per
+    // work item (one warp); every pair writes one partial sum, and a gather
+    // adds each target's partials in its own list order.
+    DevBuf<int2> p2p_inv, m2p_inv;        // (target, CSR entry), grouped
+    DevBuf<int32_t> p2p_pos, m2p_pos;     // CSR entry -> grouped position
+    DevBuf<int4> p2p_items, m2p_items;    // (leaf | box, grouped start, count <= 32, 0)
+    int64_t n_p2p_items = 0, n_m2p_items = 0;
+    // partial records at grouped positions, interleaved per entry: (V, K) of
+    // every kernel (2 nk values)
+    DevBuf<double> p2p_part, m2p_part64;
+    DevBuf<float> p2p_part32, m2p_part32;
+    DevBuf<float> dV32, dK32;             // mixed path: near corrections in FP32, kernel-major
+    DevBuf<float4> x32;                   // sorted targets relative to the tree origin, FP32
     // near-singular corrections per kernel: dV, dK per near entry; self V per panel
     std::vector<DevBuf<double>> dV, dK, selfV;
     // outputs per kernel: V then K per sorted target (2 * n)

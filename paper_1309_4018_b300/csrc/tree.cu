@@ -237,45 +237,46 @@ __global__ void traverse_kernel(int64_t ntg, const double *__restrict__ xs, cons
     if (!FILL) { m2p_cnt[i] = nm; p2p_cnt[i] = np; }
 }
 
-// Union of the lists of 32 consecutive sorted targets with per-lane masks.
-// One warp per group; entries are collected chunk by chunk of the index range
-// in shared memory, so the union comes out in ascending index order.
-constexpr int kUnionChunk = 8192;
-
-template <bool FILL>
-__global__ void group_union_kernel(int64_t ntg, int64_t ngroups, const int64_t *__restrict__ ptr,
-                                   const int32_t *__restrict__ ent, int nidx, int32_t *__restrict__ gcount,
-                                   const int64_t *__restrict__ gptr, int2 *__restrict__ gent) {
-    extern __shared__ uint32_t smask[];
-    const int64_t g = blockIdx.x;
-    if (g >= ngroups) return;
-    const int lane = threadIdx.x;
-    const int64_t t = g * 32 + lane;
-    const int64_t b0 = t < ntg ? ptr[t] : 0, b1 = t < ntg ? ptr[t + 1] : 0;
-    int total = 0;
-    const int64_t out = FILL ? gptr[g] : 0;
-    for (int c0 = 0; c0 < nidx; c0 += kUnionChunk) {
-        const int c1 = min(nidx, c0 + kUnionChunk);
-        for (int k = lane; k < c1 - c0; k += 32) smask[k] = 0u;
-        __syncwarp();
-        for (int64_t e = b0; e < b1; ++e) {
-            const int v = ent[e];
-            if (v >= c0 && v < c1) atomicOr(&smask[v - c0], 1u << lane);
-        }
-        __syncwarp();
-        for (int k0 = 0; k0 < c1 - c0; k0 += 32) {
-            const int k = k0 + lane;
-            const uint32_t m = (k < c1 - c0) ? smask[k] : 0u;
-            const uint32_t bal = __ballot_sync(0xffffffffu, m != 0u);
-            if (FILL && m != 0u) {
-                const int pos = __popc(bal & ((1u << lane) - 1u));
-                gent[out + total + pos] = make_int2(c0 + k, (int)m);
-            }
-            total += __popc(bal);
-        }
-        __syncwarp();
+// ---------------------------------------------------------------- entry-major grouping
+// key(e) = leaf index of a P2P entry (remap = node_leaf) or node id of an M2P entry.
+__global__ void inv_count_kernel(int64_t m, const int64_t *__restrict__ ptr, const int32_t *__restrict__ ent,
+                                 const int32_t *__restrict__ remap, int32_t *__restrict__ cnt) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m) return;
+    for (int64_t e = ptr[t]; e < ptr[t + 1]; ++e) {
+        const int key = remap ? remap[ent[e]] : ent[e];
+        atomicAdd(&cnt[key], 1);
     }
-    if (!FILL && lane == 0) gcount[g] = total;
+}
+
+// The order of the pairs inside one key's group does not matter: every pair
+// writes its own partial, and the gather reads them back in list order.
+__global__ void inv_fill_kernel(int64_t m, const int64_t *__restrict__ ptr, const int32_t *__restrict__ ent,
+                                const int32_t *__restrict__ remap, const int64_t *__restrict__ off,
+                                int32_t *__restrict__ cursor, int2 *__restrict__ inv, int32_t *__restrict__ pos) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m) return;
+    for (int64_t e = ptr[t]; e < ptr[t + 1]; ++e) {
+        const int key = remap ? remap[ent[e]] : ent[e];
+        const int64_t p = off[key] + atomicAdd(&cursor[key], 1);
+        inv[p] = make_int2((int)t, (int)e);
+        pos[e] = (int32_t)p;
+    }
+}
+
+__global__ void item_count_kernel(int nkeys, const int64_t *__restrict__ off, int32_t *__restrict__ nitems) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nkeys) return;
+    nitems[k] = (int)((off[k + 1] - off[k] + 31) / 32);
+}
+
+__global__ void item_fill_kernel(int nkeys, const int64_t *__restrict__ off, const int64_t *__restrict__ ioff,
+                                 int4 *__restrict__ items) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nkeys) return;
+    const int64_t c = off[k + 1] - off[k];
+    for (int64_t w = 0; 32 * w < c; ++w)
+        items[ioff[k] + w] = make_int4(k, (int)(off[k] + 32 * w), (int)(c - 32 * w < 32 ? c - 32 * w : 32), 0);
 }
 
 // ---------------------------------------------------------------- near-singular lists
@@ -663,27 +664,36 @@ void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, 
         node_to_leaf_kernel<<<div_up(Pr.n_p2p, 256), 256, 0, s>>>(Pr.n_p2p, Pr.p2p_node.p, T.node_leaf.p, pleaf.p);
         PB_LAUNCH_CHECK();
     }
-    // warp-group unions
-    const int64_t ng = (m + 31) / 32;
-    auto unions = [&](const int64_t *ptr, const int32_t *ent, int nidx, DevBuf<int64_t> &gptr, DevBuf<int2> &gent,
-                      int64_t &total) {
-        TmpBuf<int32_t> gc(std::max<int64_t>(1, ng), s);
-        gptr.alloc(ng + 1);
-        const size_t shm = kUnionChunk * sizeof(uint32_t);
-        if (ng) {
-            group_union_kernel<false><<<(unsigned)ng, 32, shm, s>>>(m, ng, ptr, ent, nidx, gc.p, nullptr, nullptr);
+    // entry-major grouping of the lists
+    auto group = [&](const int64_t *ptr, const int32_t *ent, const int32_t *remap, int nkeys, int64_t nent,
+                     DevBuf<int2> &inv, DevBuf<int32_t> &pos, DevBuf<int4> &items, int64_t &nitems) {
+        TmpBuf<int32_t> cnt(std::max(1, nkeys), s), cursor(std::max(1, nkeys), s), nit(std::max(1, nkeys), s);
+        TmpBuf<int64_t> off(nkeys + 1, s), ioff(nkeys + 1, s);
+        PB_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * std::max(1, nkeys), s));
+        PB_CUDA_TRY(cudaMemsetAsync(cursor.p, 0, sizeof(int32_t) * std::max(1, nkeys), s));
+        inv.alloc(std::max<int64_t>(1, nent));
+        pos.alloc(std::max<int64_t>(1, nent));
+        if (m && nent) {
+            inv_count_kernel<<<div_up(m, 128), 128, 0, s>>>(m, ptr, ent, remap, cnt.p);
             PB_LAUNCH_CHECK();
         }
-        exclusive_scan_i32_to_i64(gc.p, gptr.p, ng, s);
-        total = read_i64(gptr.p + ng, s);
-        gent.alloc(std::max<int64_t>(1, total));
-        if (ng) {
-            group_union_kernel<true><<<(unsigned)ng, 32, shm, s>>>(m, ng, ptr, ent, nidx, nullptr, gptr.p, gent.p);
+        exclusive_scan_i32_to_i64(cnt.p, off.p, nkeys, s);
+        if (m && nent) {
+            inv_fill_kernel<<<div_up(m, 128), 128, 0, s>>>(m, ptr, ent, remap, off.p, cursor.p, inv.p, pos.p);
             PB_LAUNCH_CHECK();
         }
+        item_count_kernel<<<div_up(nkeys, 128), 128, 0, s>>>(nkeys, off.p, nit.p);
+        PB_LAUNCH_CHECK();
+        exclusive_scan_i32_to_i64(nit.p, ioff.p, nkeys, s);
+        nitems = read_i64(ioff.p + nkeys, s);
+        items.alloc(std::max<int64_t>(1, nitems));
+        item_fill_kernel<<<div_up(nkeys, 128), 128, 0, s>>>(nkeys, off.p, ioff.p, items.p);
+        PB_LAUNCH_CHECK();
     };
-    unions(Pr.p2p_ptr.p, pleaf.p, T.nleaves, Pr.gp2p_ptr, Pr.gp2p, Pr.n_gp2p);
-    unions(Pr.m2p_ptr.p, Pr.m2p_node.p, T.nnodes, Pr.gm2p_ptr, Pr.gm2p, Pr.n_gm2p);
+    group(Pr.p2p_ptr.p, Pr.p2p_node.p, T.node_leaf.p, T.nleaves, Pr.n_p2p, Pr.p2p_inv, Pr.p2p_pos, Pr.p2p_items,
+          Pr.n_p2p_items);
+    group(Pr.m2p_ptr.p, Pr.m2p_node.p, nullptr, T.nnodes, Pr.n_m2p, Pr.m2p_inv, Pr.m2p_pos, Pr.m2p_items,
+          Pr.n_m2p_items);
     // near-singular lists
     TmpBuf<int32_t> nc(m, s), ex(m, s), se(m, s);
     TmpBuf<unsigned long long> reach_d(1, s);

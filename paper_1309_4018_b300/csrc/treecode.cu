@@ -162,16 +162,19 @@ __global__ void __launch_bounds__(128) p2m_kernel(int nleaves, const int32_t *__
 // M_parent^k = sum_children sum_{l <= k} C(k, l) (y_child - y_parent)^(k-l) M_child^l;
 // the dipole moments D shift with the same rule.  One block per node of the
 // level: the children's moments (contiguous node ids), the powers of the
-// shifts and the binomials are staged in shared memory; one thread per term.
-constexpr int kM2MMaxShared = 8 * 2 * 455 * 8;
+// shifts and the binomials are staged in shared memory; one thread per
+// (child, term) forms that child's shifted term, then one thread per term adds
+// the children in order.
+constexpr int kM2MMaxShared = 2 * 8 * 2 * 455 * 8;
 
 template <typename T>
-__global__ void __launch_bounds__(128) m2m_kernel(int nodes_begin, const int32_t *__restrict__ first_child,
+__global__ void __launch_bounds__(256) m2m_kernel(int nodes_begin, const int32_t *__restrict__ first_child,
                                                   const int32_t *__restrict__ nchild,
                                                   const double *__restrict__ centre, int P, int NT,
                                                   T *__restrict__ mom) {
     extern __shared__ __align__(16) unsigned char m2m_smem[];
     T *smom = reinterpret_cast<T *>(m2m_smem);
+    T *spart = smom + 8 * 2 * NT;
     __shared__ T hp[8][3][kMaxP + 1];
     __shared__ T sbin[kMaxP + 1][kMaxP + 1];
     const int b = nodes_begin + blockIdx.x;
@@ -190,26 +193,31 @@ __global__ void __launch_bounds__(128) m2m_kernel(int nodes_begin, const int32_t
         sbin[n][k] = (T)c_binom[n][k];
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < NT; k += blockDim.x) {
+    for (int idx = threadIdx.x; idx < nc * NT; idx += blockDim.x) {
+        const int c = idx / NT, k = idx - c * NT;
         const int k1 = c_terms[3 * k], k2 = c_terms[3 * k + 1], k3 = c_terms[3 * k + 2];
+        const T *mc = smom + c * 2 * NT;
         T accM = 0, accD = 0;
-        for (int c = 0; c < nc; ++c) {
-            const T *mc = smom + c * 2 * NT;
-            for (int l1 = 0; l1 <= k1; ++l1) {
-                const T f1 = sbin[k1][l1] * hp[c][0][k1 - l1];
-                for (int l2 = 0; l2 <= k2; ++l2) {
-                    const T f2 = f1 * sbin[k2][l2] * hp[c][1][k2 - l2];
-                    for (int l3 = 0; l3 <= k3; ++l3) {
-                        const T coef = f2 * sbin[k3][l3] * hp[c][2][k3 - l3];
-                        const int li = term_index(l1, l2, l3);
-                        accM += coef * mc[li];
-                        accD += coef * mc[NT + li];
-                    }
+        for (int l1 = 0; l1 <= k1; ++l1) {
+            const T f1 = sbin[k1][l1] * hp[c][0][k1 - l1];
+            for (int l2 = 0; l2 <= k2; ++l2) {
+                const T f2 = f1 * sbin[k2][l2] * hp[c][1][k2 - l2];
+                for (int l3 = 0; l3 <= k3; ++l3) {
+                    const T coef = f2 * sbin[k3][l3] * hp[c][2][k3 - l3];
+                    const int li = term_index(l1, l2, l3);
+                    accM += coef * mc[li];
+                    accD += coef * mc[NT + li];
                 }
             }
         }
-        mom[(int64_t)b * 2 * NT + k] = accM;
-        mom[(int64_t)b * 2 * NT + NT + k] = accD;
+        spart[c * 2 * NT + k] = accM;
+        spart[c * 2 * NT + NT + k] = accD;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 2 * NT; k += blockDim.x) {
+        T acc = 0;
+        for (int c = 0; c < nc; ++c) acc += spart[c * 2 * NT + k];
+        mom[(int64_t)b * 2 * NT + k] = acc;
     }
 }
 
@@ -230,29 +238,35 @@ __device__ __forceinline__ void comp_add(float &hi, float &lo, float v) {
     hi = t;
 }
 
-// kSplit warps share one group of 32 targets and take its list entries in turn.
-constexpr int kSplit = 4;
-
+// Leaf-major: one warp per work item = one leaf and up to 32 (target, entry)
+// pairs that sum over it.  The leaf's sources are staged 32 at a time in
+// shared memory and broadcast; every lane owns one target.  FP32 partial sums
+// per 32-source chunk go into compensated (hi, lo) pairs; the pair's result is
+// stored in FP64 at its grouped position.
 template <int NK, bool Y0, bool Y1>
-__global__ void __launch_bounds__(128) p2p32_kernel(int64_t ntg, int64_t ngroups, const double *__restrict__ xs,
-                                                    double ox, double oy, double oz, const int32_t *__restrict__ selfp,
-                                                    int use_self, const int64_t *__restrict__ gptr,
-                                                    const int2 *__restrict__ gent, const int32_t *__restrict__ leaf_node,
+__global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, const int4 *__restrict__ items,
+                                                    const int2 *__restrict__ inv, int64_t npart,
+                                                    const float4 *__restrict__ x32,
+                                                    const int32_t *__restrict__ selfp, int use_self,
+                                                    const int32_t *__restrict__ leaf_node,
                                                     const int64_t *__restrict__ start, const int64_t *__restrict__ count,
                                                     const float4 *__restrict__ A, const float4 *__restrict__ B,
-                                                    KSet ks, double *__restrict__ VK0, double *__restrict__ VK1) {
-    __shared__ float4 sA[kSplit][32], sB[kSplit][32];
-    __shared__ float red[kSplit][2 * NK][2][32];
+                                                    KSet ks, float *__restrict__ part) {
+    __shared__ float4 sA[4][32], sB[4][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t g = blockIdx.x;
-    const int64_t t = g * 32 + lane;
-    const bool valid = t < ntg;
+    const int64_t item = (int64_t)blockIdx.x * 4 + warp;
+    if (item >= nitems) return;
+    const int4 it = items[item];
+    const bool valid = lane < it.z;
+    const int64_t slot = (int64_t)it.y + lane;
     float tx = 0.f, ty = 0.f, tz = 0.f;
     int me = -1;
     if (valid) {
-        tx = (float)(xs[3 * t] - ox);
-        ty = (float)(xs[3 * t + 1] - oy);
-        tz = (float)(xs[3 * t + 2] - oz);
+        const int t = inv[slot].x;
+        const float4 x = x32[t];
+        tx = x.x;
+        ty = x.y;
+        tz = x.z;
         if (use_self) me = selfp[t];
     }
     const float k0 = ks.kap[0], k1 = ks.kap[1];
@@ -260,170 +274,135 @@ __global__ void __launch_bounds__(128) p2p32_kernel(int64_t ntg, int64_t ngroups
     float hi[2 * NK], lo[2 * NK];
 #pragma unroll
     for (int a = 0; a < 2 * NK; ++a) { hi[a] = 0.f; lo[a] = 0.f; }
-    const int64_t e0 = gptr[g], e1 = gptr[g + 1];
-    for (int64_t e = e0 + warp; e < e1; e += kSplit) {
-        const int2 en = gent[e];
-        const bool active = valid && ((en.y >> lane) & 1);
-        const int node = leaf_node[en.x];
-        const int64_t s0 = start[node];
-        const int cnt = (int)count[node];
-        for (int c0 = 0; c0 < cnt; c0 += 32) {
-            const int m = min(32, cnt - c0);
-            if (lane < m) {
-                sA[warp][lane] = A[s0 + c0 + lane];
-                sB[warp][lane] = B[s0 + c0 + lane];
-            }
-            __syncwarp();
-            if (active) {
-                float p[4] = {0.f, 0.f, 0.f, 0.f};
+    const int node = leaf_node[it.x];
+    const int64_t s0 = start[node];
+    const int cnt = (int)count[node];
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+        const int m = min(32, cnt - c0);
+        if (lane < m) {
+            sA[warp][lane] = A[s0 + c0 + lane];
+            sB[warp][lane] = B[s0 + c0 + lane];
+        }
+        __syncwarp();
+        if (valid) {
+            float p[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 4
-                for (int j = 0; j < m; ++j) {
-                    const float4 a = sA[warp][j];
-                    const float4 b = sB[warp][j];
-                    const float dx = tx - a.x, dy = ty - a.y, dz = tz - a.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float inv = (__float_as_int(b.w) == me) ? 0.f : rsqrtf(r2);
-                    const float sv = a.w * inv;
-                    const float rd = fmaf(dx, b.x, fmaf(dy, b.y, dz * b.z));
-                    const float kv = rd * (inv * inv * inv);
-                    if (!Y0) {
-                        p[0] += sv;
-                        p[1] += kv;
+            for (int j = 0; j < m; ++j) {
+                const float4 a = sA[warp][j];
+                const float4 b = sB[warp][j];
+                const float dx = tx - a.x, dy = ty - a.y, dz = tz - a.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float inv = (__float_as_int(b.w) == me) ? 0.f : rsqrtf(r2);
+                const float sv = a.w * inv;
+                const float rd = fmaf(dx, b.x, fmaf(dy, b.y, dz * b.z));
+                const float kv = rd * (inv * inv * inv);
+                if (!Y0) {
+                    p[0] += sv;
+                    p[1] += kv;
+                } else {
+                    const float rho = r2 * inv;
+                    const float ex = exp2f(l2e0 * rho);
+                    p[0] = fmaf(sv, ex, p[0]);
+                    p[1] = fmaf(kv * ex, fmaf(k0, rho, 1.f), p[1]);
+                }
+                if (NK == 2) {
+                    if (!Y1) {
+                        p[2] += sv;
+                        p[3] += kv;
                     } else {
                         const float rho = r2 * inv;
-                        const float ex = exp2f(l2e0 * rho);
-                        p[0] = fmaf(sv, ex, p[0]);
-                        p[1] = fmaf(kv * ex, fmaf(k0, rho, 1.f), p[1]);
-                    }
-                    if (NK == 2) {
-                        if (!Y1) {
-                            p[2] += sv;
-                            p[3] += kv;
-                        } else {
-                            const float rho = r2 * inv;
-                            const float ex = exp2f(l2e1 * rho);
-                            p[2] = fmaf(sv, ex, p[2]);
-                            p[3] = fmaf(kv * ex, fmaf(k1, rho, 1.f), p[3]);
-                        }
+                        const float ex = exp2f(l2e1 * rho);
+                        p[2] = fmaf(sv, ex, p[2]);
+                        p[3] = fmaf(kv * ex, fmaf(k1, rho, 1.f), p[3]);
                     }
                 }
-#pragma unroll
-                for (int a = 0; a < 2 * NK; ++a) comp_add(hi[a], lo[a], p[a]);
             }
-            __syncwarp();
-        }
-    }
 #pragma unroll
-    for (int a = 0; a < 2 * NK; ++a) {
-        red[warp][a][0][lane] = hi[a];
-        red[warp][a][1][lane] = lo[a];
+            for (int a = 0; a < 2 * NK; ++a) comp_add(hi[a], lo[a], p[a]);
+        }
+        __syncwarp();
     }
-    __syncthreads();
-    if (warp == 0 && valid) {
-        double out[2 * NK];
+    if (valid) {
+        // interleaved record of the entry: (V0, K0[, V1, K1]), the compensated pair rounded once
+        float2 *rec = reinterpret_cast<float2 *>(part + (int64_t)2 * NK * slot);
 #pragma unroll
-        for (int a = 0; a < 2 * NK; ++a) {
-            double v = 0.0;
-            for (int w = 0; w < kSplit; ++w) v += (double)red[w][a][0][lane] + (double)red[w][a][1][lane];
-            out[a] = v * kInv4Pi;
-        }
-        VK0[t] = out[0];
-        VK0[ntg + t] = out[1];
-        if (NK == 2) {
-            VK1[t] = out[2 % (2 * NK)];
-            VK1[ntg + t] = out[3 % (2 * NK)];
-        }
+        for (int a = 0; a < NK; ++a) rec[a] = make_float2(hi[2 * a] + lo[2 * a], hi[2 * a + 1] + lo[2 * a + 1]);
     }
 }
 
 // ---------------------------------------------------------------- P2P, FP64
 template <int NK, bool Y0, bool Y1>
-__global__ void __launch_bounds__(128) p2p64_kernel(int64_t ntg, int64_t ngroups, const double *__restrict__ xs,
-                                                    const int32_t *__restrict__ selfp, int use_self,
-                                                    const int64_t *__restrict__ gptr, const int2 *__restrict__ gent,
-                                                    const int32_t *__restrict__ leaf_node,
+__global__ void __launch_bounds__(128) p2p64_kernel(int64_t nitems, const int4 *__restrict__ items,
+                                                    const int2 *__restrict__ inv, int64_t npart,
+                                                    const double *__restrict__ xs, const int32_t *__restrict__ selfp,
+                                                    int use_self, const int32_t *__restrict__ leaf_node,
                                                     const int64_t *__restrict__ start, const int64_t *__restrict__ count,
                                                     const double *__restrict__ src, double kap0, double kap1,
-                                                    double *__restrict__ VK0, double *__restrict__ VK1) {
-    __shared__ double4 sA[kSplit][32], sB[kSplit][32];
-    __shared__ double red[kSplit][4][32];
+                                                    double *__restrict__ part) {
+    __shared__ double4 sA[4][32], sB[4][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t g = blockIdx.x;
-    const int64_t t = g * 32 + lane;
-    const bool valid = t < ntg;
+    const int64_t item = (int64_t)blockIdx.x * 4 + warp;
+    if (item >= nitems) return;
+    const int4 it = items[item];
+    const bool valid = lane < it.z;
+    const int64_t slot = (int64_t)it.y + lane;
     double tx = 0, ty = 0, tz = 0;
     int me = -1;
     if (valid) {
+        const int t = inv[slot].x;
         tx = xs[3 * t]; ty = xs[3 * t + 1]; tz = xs[3 * t + 2];
         if (use_self) me = selfp[t];
     }
     double acc[4] = {0, 0, 0, 0};
-    const int64_t e0 = gptr[g], e1 = gptr[g + 1];
     const double4 *src4 = reinterpret_cast<const double4 *>(src);
-    for (int64_t e = e0 + warp; e < e1; e += kSplit) {
-        const int2 en = gent[e];
-        const bool active = valid && ((en.y >> lane) & 1);
-        const int node = leaf_node[en.x];
-        const int64_t s0 = start[node];
-        const int cnt = (int)count[node];
-        for (int c0 = 0; c0 < cnt; c0 += 32) {
-            const int m = min(32, cnt - c0);
-            if (lane < m) {
-                sA[warp][lane] = src4[2 * (s0 + c0 + lane)];
-                sB[warp][lane] = src4[2 * (s0 + c0 + lane) + 1];
-            }
-            __syncwarp();
-            if (active) {
-                for (int j = 0; j < m; ++j) {
-                    const double4 a = sA[warp][j];
-                    const double4 b = sB[warp][j];
-                    if ((int)b.w == me) continue;
-                    const double dx = tx - a.x, dy = ty - a.y, dz = tz - a.z;
-                    const double r2 = dx * dx + dy * dy + dz * dz;
-                    const double rho = sqrt(r2);
-                    const double inv = 1.0 / rho;
-                    const double sv = a.w * inv;
-                    const double rd = dx * b.x + dy * b.y + dz * b.z;
-                    const double kv = rd * inv * inv * inv;
-                    if (!Y0) {
-                        acc[0] += sv;
-                        acc[1] += kv;
+    const int node = leaf_node[it.x];
+    const int64_t s0 = start[node];
+    const int cnt = (int)count[node];
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+        const int m = min(32, cnt - c0);
+        if (lane < m) {
+            sA[warp][lane] = src4[2 * (s0 + c0 + lane)];
+            sB[warp][lane] = src4[2 * (s0 + c0 + lane) + 1];
+        }
+        __syncwarp();
+        if (valid) {
+            for (int j = 0; j < m; ++j) {
+                const double4 a = sA[warp][j];
+                const double4 b = sB[warp][j];
+                if ((int)b.w == me) continue;
+                const double dx = tx - a.x, dy = ty - a.y, dz = tz - a.z;
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                const double rho = sqrt(r2);
+                const double inv = 1.0 / rho;
+                const double sv = a.w * inv;
+                const double rd = dx * b.x + dy * b.y + dz * b.z;
+                const double kv = rd * inv * inv * inv;
+                if (!Y0) {
+                    acc[0] += sv;
+                    acc[1] += kv;
+                } else {
+                    const double ex = exp(-kap0 * rho);
+                    acc[0] += sv * ex;
+                    acc[1] += kv * ex * (1.0 + kap0 * rho);
+                }
+                if (NK == 2) {
+                    if (!Y1) {
+                        acc[2] += sv;
+                        acc[3] += kv;
                     } else {
-                        const double ex = exp(-kap0 * rho);
-                        acc[0] += sv * ex;
-                        acc[1] += kv * ex * (1.0 + kap0 * rho);
-                    }
-                    if (NK == 2) {
-                        if (!Y1) {
-                            acc[2] += sv;
-                            acc[3] += kv;
-                        } else {
-                            const double ex = exp(-kap1 * rho);
-                            acc[2] += sv * ex;
-                            acc[3] += kv * ex * (1.0 + kap1 * rho);
-                        }
+                        const double ex = exp(-kap1 * rho);
+                        acc[2] += sv * ex;
+                        acc[3] += kv * ex * (1.0 + kap1 * rho);
                     }
                 }
             }
-            __syncwarp();
         }
+        __syncwarp();
     }
+    if (valid) {
+        double2 *rec = reinterpret_cast<double2 *>(part + (int64_t)2 * NK * slot);
 #pragma unroll
-    for (int a = 0; a < 4; ++a) red[warp][a][lane] = acc[a];
-    __syncthreads();
-    if (warp == 0 && valid) {
-        double out[4];
-        for (int a = 0; a < 4; ++a) {
-            double v = 0.0;
-            for (int w = 0; w < kSplit; ++w) v += red[w][a][lane];
-            out[a] = v * kInv4Pi;
-        }
-        VK0[t] = out[0];
-        VK0[ntg + t] = out[1];
-        if (NK == 2) {
-            VK1[t] = out[2];
-            VK1[ntg + t] = out[3];
-        }
+        for (int a = 0; a < NK; ++a) rec[a] = make_double2(acc[2 * a], acc[2 * a + 1]);
     }
 }
 
@@ -508,85 +487,205 @@ __device__ void m2p_eval_rt(int P, T ux, T uy, T uz, T kappa, const T *__restric
     }
 }
 
-// One block of kSplit warps per group of 32 sorted targets; the warps take the
-// union of the group's accepted boxes in turn and each lane evaluates the
-// boxes of its own list.  FP32: box centres relative to the tree origin in
-// FP32, per-box results added into compensated (hi, lo) FP32 sums; FP64: all
-// in double.
+// Box-major: one warp per work item = one accepted box and up to 32
+// (target, entry) pairs that use it; the box's moments and centre are the
+// same for every lane, each lane runs the recurrences for its own target and
+// stores (V, K) at the pair's grouped position.
 template <int P, bool YUK, typename T>
-__global__ void __launch_bounds__(128) m2p_kernel(int64_t ntg, int64_t ngroups, int Prt, const double *__restrict__ xs,
-                                                  double ox, double oy, double oz, const int64_t *__restrict__ gptr,
-                                                  const int2 *__restrict__ gent, const double *__restrict__ centre,
-                                                  const float4 *__restrict__ cen32, const T *__restrict__ mom,
-                                                  double kappa, double *__restrict__ VK) {
-    __shared__ double red[kSplit][2][32];
+__global__ void __launch_bounds__(128) m2p_kernel(int64_t nitems, const int4 *__restrict__ items,
+                                                  const int2 *__restrict__ inv, int64_t npart, int Prt,
+                                                  const double *__restrict__ xs, const float4 *__restrict__ x32,
+                                                  const double *__restrict__ centre, const float4 *__restrict__ cen32,
+                                                  const T *__restrict__ mom, double kappa, int kslot, int nk,
+                                                  T *__restrict__ part) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t g = blockIdx.x;
-    const int64_t t = g * 32 + lane;
-    const bool valid = t < ntg;
+    const int64_t item = (int64_t)blockIdx.x * 4 + warp;
+    if (item >= nitems) return;
+    const int4 it = items[item];
+    if (lane >= it.z) return;
+    const int64_t slot = (int64_t)it.y + lane;
+    const int t = inv[slot].x;
+    const int b = it.x;
     const int Pe = P >= 0 ? P : Prt;
     const int NT = (Pe + 1) * (Pe + 2) * (Pe + 3) / 6;
-    double x = 0, y = 0, z = 0;
-    if (valid) {
-        x = xs[3 * t] - ox; y = xs[3 * t + 1] - oy; z = xs[3 * t + 2] - oz;
+    T ux, uy, uz;
+    if constexpr (sizeof(T) == 4) {
+        const float4 c = cen32[b];
+        const float4 x = x32[t];
+        ux = c.x - x.x;
+        uy = c.y - x.y;
+        uz = c.z - x.z;
+    } else {
+        ux = centre[3 * b] - xs[3 * t];
+        uy = centre[3 * b + 1] - xs[3 * t + 1];
+        uz = centre[3 * b + 2] - xs[3 * t + 2];
     }
-    const T tx = (T)x, ty = (T)y, tz = (T)z;
-    T hiV = 0, loV = 0, hiK = 0, loK = 0;
-    for (int64_t e = gptr[g] + warp; e < gptr[g + 1]; e += kSplit) {
-        const int2 en = gent[e];
-        if (!(valid && ((en.y >> lane) & 1))) continue;
-        const int b = en.x;
-        T ux, uy, uz;
-        if constexpr (sizeof(T) == 4) {
-            const float4 c = cen32[b];
-            ux = c.x - tx; uy = c.y - ty; uz = c.z - tz;
-        } else {
-            ux = (T)centre[3 * b] - tx; uy = (T)centre[3 * b + 1] - ty; uz = (T)centre[3 * b + 2] - tz;
-        }
-        T V, K;
-        if constexpr (P >= 0) m2p_eval<(P >= 0 ? P : 0), YUK, T>(ux, uy, uz, (T)kappa, mom + (int64_t)b * 2 * NT, V, K);
-        else m2p_eval_rt<YUK, T>(Prt, ux, uy, uz, (T)kappa, mom + (int64_t)b * 2 * NT, V, K);
-        if constexpr (sizeof(T) == 4) {
-            comp_add(hiV, loV, V);
-            comp_add(hiK, loK, K);
-        } else {
-            hiV += V;
-            hiK += K;
+    T V, K;
+    if constexpr (P >= 0) m2p_eval<(P >= 0 ? P : 0), YUK, T>(ux, uy, uz, (T)kappa, mom + (int64_t)b * 2 * NT, V, K);
+    else m2p_eval_rt<YUK, T>(Prt, ux, uy, uz, (T)kappa, mom + (int64_t)b * 2 * NT, V, K);
+    // interleaved record of the entry: (V, K) of every kernel
+    T *rec = part + (int64_t)2 * nk * slot + 2 * kslot;
+    rec[0] = V;
+    rec[1] = K;
+}
+
+// One warp per target: V and K of every kernel = its P2P and M2P partials
+// (FP64 sums) plus the near-singular corrections and the self term, times
+// 1/(4 pi) for the treecode part.  Lanes take the list entries in turn and a
+// fixed butterfly combines them, so the result does not depend on scheduling.
+struct NearArgs {
+    const int64_t *ptr;
+    const int32_t *panel;
+    const double *dV[2], *dK[2], *selfV[2];
+    const int32_t *selfp;
+    int use_self;
+    const double *phi, *dphi;
+};
+
+struct NearArgs32 {
+    const int64_t *ptr;
+    const int32_t *panel;
+    const float *dV[2], *dK[2];
+    const double *selfV[2];
+    const int32_t *selfp;
+    int use_self;
+    const double *phi, *dphi;
+};
+
+template <typename TM, int NK>
+__global__ void __launch_bounds__(128) gather_kernel(int64_t ntg, const int64_t *__restrict__ p2p_ptr,
+                                                     const int32_t *__restrict__ p2p_pos,
+                                                     const double *__restrict__ p2p_part,
+                                                     const int64_t *__restrict__ m2p_ptr,
+                                                     const int32_t *__restrict__ m2p_pos,
+                                                     const TM *__restrict__ m2p_part, NearArgs nr,
+                                                     double *__restrict__ VK0, double *__restrict__ VK1) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * 4 + warp;
+    if (t >= ntg) return;
+    double acc[2 * NK], far[2 * NK];
+#pragma unroll
+    for (int a = 0; a < 2 * NK; ++a) { acc[a] = 0.0; far[a] = 0.0; }
+    for (int64_t e = p2p_ptr[t] + lane; e < p2p_ptr[t + 1]; e += 32) {
+        const double2 *rec = reinterpret_cast<const double2 *>(p2p_part + (int64_t)2 * NK * p2p_pos[e]);
+#pragma unroll
+        for (int a = 0; a < NK; ++a) {
+            const double2 v = rec[a];
+            acc[2 * a] += v.x;
+            acc[2 * a + 1] += v.y;
         }
     }
-    red[warp][0][lane] = (double)hiV + (double)loV;
-    red[warp][1][lane] = (double)hiK + (double)loK;
-    __syncthreads();
-    if (warp == 0 && valid) {
-        double v = 0.0, k = 0.0;
-        for (int w = 0; w < kSplit; ++w) { v += red[w][0][lane]; k += red[w][1][lane]; }
-        VK[t] += v * kInv4Pi;
-        VK[ntg + t] += k * kInv4Pi;
+    if (m2p_part)
+        for (int64_t e = m2p_ptr[t] + lane; e < m2p_ptr[t + 1]; e += 32) {
+            const TM *rec = m2p_part + (int64_t)2 * NK * m2p_pos[e];
+#pragma unroll
+            for (int a = 0; a < 2 * NK; ++a) far[a] += (double)rec[a];
+        }
+#pragma unroll
+    for (int a = 0; a < 2 * NK; ++a) acc[a] = (acc[a] + far[a]) * kInv4Pi;
+    for (int64_t e = nr.ptr[t] + lane; e < nr.ptr[t + 1]; e += 32) {
+        const int j = nr.panel[e];
+        const double ph = nr.phi[j], dph = nr.dphi[j];
+#pragma unroll
+        for (int a = 0; a < NK; ++a) {
+            acc[2 * a] += nr.dV[a][e] * dph;
+            acc[2 * a + 1] += nr.dK[a][e] * ph;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 2 * NK; ++a)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o);
+    if (lane == 0) {
+        if (nr.use_self) {
+            const int me = nr.selfp[t];
+#pragma unroll
+            for (int a = 0; a < NK; ++a) acc[2 * a] += nr.selfV[a][me] * nr.dphi[me];
+        }
+        VK0[t] = acc[0];
+        VK0[ntg + t] = acc[1];
+        if (NK == 2) {
+            VK1[t] = acc[2 % (2 * NK)];
+            VK1[ntg + t] = acc[3 % (2 * NK)];
+        }
+    }
+}
+
+// Mixed precision: the same gather entirely in FP32, every sum compensated
+// (TwoSum into (hi, lo) pairs, pairs combined by a fixed butterfly): the FP64
+// pipe of the B300 is too narrow for ~10^3 conversions and adds per target.
+__device__ __forceinline__ void two_add(float &hi, float &lo, float v) {
+    const float s = hi + v;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (v - bb);
+    hi = s;
+}
+
+template <int NK>
+__global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_t *__restrict__ p2p_ptr,
+                                                       const int32_t *__restrict__ p2p_pos,
+                                                       const float *__restrict__ p2p_part,
+                                                       const int64_t *__restrict__ m2p_ptr,
+                                                       const int32_t *__restrict__ m2p_pos,
+                                                       const float *__restrict__ m2p_part, NearArgs32 nr,
+                                                       double *__restrict__ VK0, double *__restrict__ VK1) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * 4 + warp;
+    if (t >= ntg) return;
+    float hi[2 * NK], lo[2 * NK], nh[2 * NK], nl[2 * NK];
+#pragma unroll
+    for (int a = 0; a < 2 * NK; ++a) { hi[a] = 0.f; lo[a] = 0.f; nh[a] = 0.f; nl[a] = 0.f; }
+    for (int64_t e = p2p_ptr[t] + lane; e < p2p_ptr[t + 1]; e += 32) {
+        const float *rec = p2p_part + (int64_t)2 * NK * p2p_pos[e];
+#pragma unroll
+        for (int a = 0; a < 2 * NK; ++a) two_add(hi[a], lo[a], rec[a]);
+    }
+    if (m2p_part)
+        for (int64_t e = m2p_ptr[t] + lane; e < m2p_ptr[t + 1]; e += 32) {
+            const float *rec = m2p_part + (int64_t)2 * NK * m2p_pos[e];
+#pragma unroll
+            for (int a = 0; a < 2 * NK; ++a) two_add(hi[a], lo[a], rec[a]);
+        }
+    for (int64_t e = nr.ptr[t] + lane; e < nr.ptr[t + 1]; e += 32) {
+        const int j = nr.panel[e];
+        const float ph = (float)nr.phi[j], dph = (float)nr.dphi[j];
+#pragma unroll
+        for (int a = 0; a < NK; ++a) {
+            two_add(nh[2 * a], nl[2 * a], nr.dV[a][e] * dph);
+            two_add(nh[2 * a + 1], nl[2 * a + 1], nr.dK[a][e] * ph);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 2 * NK; ++a)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi[a], o), ol = __shfl_xor_sync(0xffffffffu, lo[a], o);
+            const float ph = __shfl_xor_sync(0xffffffffu, nh[a], o), pl = __shfl_xor_sync(0xffffffffu, nl[a], o);
+            two_add(hi[a], lo[a], oh);
+            lo[a] += ol;
+            two_add(nh[a], nl[a], ph);
+            nl[a] += pl;
+        }
+    if (lane == 0) {
+        double out[2 * NK];
+#pragma unroll
+        for (int a = 0; a < 2 * NK; ++a)
+            out[a] = ((double)hi[a] + (double)lo[a]) * kInv4Pi + (double)nh[a] + (double)nl[a];
+        if (nr.use_self) {
+            const int me = nr.selfp[t];
+#pragma unroll
+            for (int a = 0; a < NK; ++a) out[2 * a] += nr.selfV[a][me] * nr.dphi[me];
+        }
+        VK0[t] = out[0];
+        VK0[ntg + t] = out[1];
+        if (NK == 2) {
+            VK1[t] = out[2 % (2 * NK)];
+            VK1[ntg + t] = out[3 % (2 * NK)];
+        }
     }
 }
 
 // ---------------------------------------------------------------- near field and combine
-__global__ void near_apply_kernel(int64_t ntg, const int64_t *__restrict__ ptr, const int32_t *__restrict__ pan,
-                                  const double *__restrict__ dV, const double *__restrict__ dK,
-                                  const double *__restrict__ selfV, const int32_t *__restrict__ selfp, int use_self,
-                                  const double *__restrict__ phi, const double *__restrict__ dphi,
-                                  double *__restrict__ VK) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ntg) return;
-    double V = VK[i], K = VK[ntg + i];
-    for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
-        const int j = pan[e];
-        V += dV[e] * dphi[j];
-        K += dK[e] * phi[j];
-    }
-    if (use_self) {
-        const int me = selfp[i];
-        V += selfV[me] * dphi[me];
-    }
-    VK[i] = V;
-    VK[ntg + i] = K;
-}
-
 __global__ void combine_kernel(int64_t n, const int32_t *__restrict__ rank, const double *__restrict__ phi_s,
                                double half, CombineRow row, double *__restrict__ y) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -601,16 +700,17 @@ __global__ void combine_kernel(int64_t n, const int32_t *__restrict__ rank, cons
 }
 
 template <typename T>
-void launch_m2p_typed(int P, bool yuk, int64_t ntg, int64_t ng, const double *xs, const double o[3], const Pair &Pr,
-                      const Tree &Tr, const T *mom, double kappa, double *VK, cudaStream_t s) {
-    const unsigned grid = (unsigned)ng;
-#define PB_M2P_CASE(PP)                                                                                     \
-    case PP:                                                                                                \
-        if (yuk) m2p_kernel<PP, true, T><<<grid, 128, 0, s>>>(ntg, ng, P, xs, o[0], o[1], o[2],            \
-                                                              Pr.gm2p_ptr.p, Pr.gm2p.p, Tr.centre.p,       \
-                                                              Tr.cen32.p, mom, kappa, VK);                                  \
-        else m2p_kernel<PP, false, T><<<grid, 128, 0, s>>>(ntg, ng, P, xs, o[0], o[1], o[2], Pr.gm2p_ptr.p, \
-                                                           Pr.gm2p.p, Tr.centre.p, Tr.cen32.p, mom, kappa, VK); \
+void launch_m2p_typed(int P, bool yuk, const Pair &Pr, const double *xs, const double o[3], const Tree &Tr,
+                      const T *mom, double kappa, int kslot, int nk, T *part, cudaStream_t s) {
+    const int64_t ni = Pr.n_m2p_items;
+    const unsigned grid = (unsigned)((ni + 3) / 4);
+    const int64_t np = Pr.n_m2p;
+#define PB_M2P_ARGS \
+    ni, Pr.m2p_items.p, Pr.m2p_inv.p, np, P, xs, Pr.x32.p, Tr.centre.p, Tr.cen32.p, mom, kappa, kslot, nk, part
+#define PB_M2P_CASE(PP)                                                                                  \
+    case PP:                                                                                             \
+        if (yuk) m2p_kernel<PP, true, T><<<grid, 128, 0, s>>>(PB_M2P_ARGS);                              \
+        else m2p_kernel<PP, false, T><<<grid, 128, 0, s>>>(PB_M2P_ARGS);                                 \
         break;
     switch (P) {
         PB_M2P_CASE(0)
@@ -623,12 +723,11 @@ void launch_m2p_typed(int P, bool yuk, int64_t ntg, int64_t ng, const double *xs
         PB_M2P_CASE(7)
         PB_M2P_CASE(8)
         default:
-            if (yuk) m2p_kernel<-1, true, T><<<grid, 128, 0, s>>>(ntg, ng, P, xs, o[0], o[1], o[2], Pr.gm2p_ptr.p,
-                                                                  Pr.gm2p.p, Tr.centre.p, Tr.cen32.p, mom, kappa, VK);
-            else m2p_kernel<-1, false, T><<<grid, 128, 0, s>>>(ntg, ng, P, xs, o[0], o[1], o[2], Pr.gm2p_ptr.p,
-                                                               Pr.gm2p.p, Tr.centre.p, Tr.cen32.p, mom, kappa, VK);
+            if (yuk) m2p_kernel<-1, true, T><<<grid, 128, 0, s>>>(PB_M2P_ARGS);
+            else m2p_kernel<-1, false, T><<<grid, 128, 0, s>>>(PB_M2P_ARGS);
     }
 #undef PB_M2P_CASE
+#undef PB_M2P_ARGS
     PB_LAUNCH_CHECK();
 }
 
@@ -683,34 +782,34 @@ void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s) {
                                                       Tr.origin[0], Tr.origin[1], Tr.origin[2], sv, P, NT, Tr.mom64.p);
     }
     PB_LAUNCH_CHECK();
-    const size_t shm = (size_t)8 * 2 * NT * (mixed ? sizeof(float) : sizeof(double));
+    const size_t shm = (size_t)2 * 8 * 2 * NT * (mixed ? sizeof(float) : sizeof(double));
     for (int l = Tr.nlevels - 2; l >= 0; --l) {
         const int b0 = Tr.level_off[l], nb = Tr.level_off[l + 1] - b0;
         if (mixed)
-            m2m_kernel<float><<<nb, 128, shm, s>>>(b0, Tr.first_child.p, Tr.nchild.p, Tr.centre.p, P, NT, Tr.mom32.p);
+            m2m_kernel<float><<<nb, 256, shm, s>>>(b0, Tr.first_child.p, Tr.nchild.p, Tr.centre.p, P, NT, Tr.mom32.p);
         else
-            m2m_kernel<double><<<nb, 128, shm, s>>>(b0, Tr.first_child.p, Tr.nchild.p, Tr.centre.p, P, NT,
+            m2m_kernel<double><<<nb, 256, shm, s>>>(b0, Tr.first_child.p, Tr.nchild.p, Tr.centre.p, P, NT,
                                                     Tr.mom64.p);
         PB_LAUNCH_CHECK();
     }
 }
 
 void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self, bool mixed, cudaStream_t s) {
-    const int64_t ntg = G.n, ng = (ntg + 31) / 32;
-    if (!ng) return;
-    const unsigned grid = (unsigned)ng;
+    const int64_t ni = Pr.n_p2p_items;
+    if (!ni) return;
+    const unsigned grid = (unsigned)((ni + 3) / 4);
     const int nk = (int)Pr.kappas.size();
     const double k0 = Pr.kappas[0], k1 = nk > 1 ? Pr.kappas[1] : 0.0;
     const bool y0 = k0 != 0.0, y1 = k1 != 0.0;
-    double *V0 = Pr.VK[0].p, *V1 = nk > 1 ? Pr.VK[1].p : nullptr;
     const int32_t *sp = G.self_panel.p;
     const int us = use_self ? 1 : 0;
+    const int64_t np = Pr.n_p2p;
     if (mixed) {
         KSet ks{{(float)k0, (float)k1}};
-#define PB_P2P32(NK, A, B)                                                                                   \
-    p2p32_kernel<NK, A, B><<<grid, 128, 0, s>>>(ntg, ng, G.xs.p, Tr.origin[0], Tr.origin[1], Tr.origin[2], sp, \
-                                                us, Pr.gp2p_ptr.p, Pr.gp2p.p, Tr.leaf_node.p, Tr.start.p,     \
-                                                Tr.count.p, Tr.srcA32.p, Tr.srcB32.p, ks, V0, V1)
+#define PB_P2P32(NK, A, B)                                                                                      \
+    p2p32_kernel<NK, A, B><<<grid, 128, 0, s>>>(ni, Pr.p2p_items.p, Pr.p2p_inv.p, np, Pr.x32.p, sp, us,          \
+                                                Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.srcA32.p, Tr.srcB32.p, ks, \
+                                                Pr.p2p_part32.p)
         if (nk == 1) { if (y0) PB_P2P32(1, true, false); else PB_P2P32(1, false, false); }
         else if (!y0 && y1) PB_P2P32(2, false, true);
         else if (y0 && !y1) PB_P2P32(2, true, false);
@@ -718,9 +817,10 @@ void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self,
         else PB_P2P32(2, false, false);
 #undef PB_P2P32
     } else {
-#define PB_P2P64(NK, A, B)                                                                                      \
-    p2p64_kernel<NK, A, B><<<grid, 128, 0, s>>>(ntg, ng, G.xs.p, sp, us, Pr.gp2p_ptr.p, Pr.gp2p.p, Tr.leaf_node.p, \
-                                                Tr.start.p, Tr.count.p, Tr.src64.p, k0, k1, V0, V1)
+#define PB_P2P64(NK, A, B)                                                                                       \
+    p2p64_kernel<NK, A, B><<<grid, 128, 0, s>>>(ni, Pr.p2p_items.p, Pr.p2p_inv.p, np, G.xs.p, sp, us,             \
+                                                Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.src64.p, k0, k1,      \
+                                                Pr.p2p_part.p)
         if (nk == 1) { if (y0) PB_P2P64(1, true, false); else PB_P2P64(1, false, false); }
         else if (!y0 && y1) PB_P2P64(2, false, true);
         else if (y0 && !y1) PB_P2P64(2, true, false);
@@ -732,26 +832,102 @@ void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self,
 }
 
 void launch_m2p(const Pair &Pr, const Targets &G, const Tree &Tr, int P, bool mixed, cudaStream_t s) {
-    const int64_t ntg = G.n, ng = (ntg + 31) / 32;
-    if (!ng || Pr.n_gm2p == 0) return;
+    if (Pr.n_m2p_items == 0) return;
     for (size_t k = 0; k < Pr.kappas.size(); ++k) {
         const double kap = Pr.kappas[k];
+        const int nk = (int)Pr.kappas.size();
         if (mixed) {
-            launch_m2p_typed<float>(P, kap != 0.0, ntg, ng, G.xs.p, Tr.origin, Pr, Tr, Tr.mom32.p, kap, Pr.VK[k].p, s);
+            launch_m2p_typed<float>(P, kap != 0.0, Pr, G.xs.p, Tr.origin, Tr, Tr.mom32.p, kap, (int)k, nk,
+                                    Pr.m2p_part32.p, s);
         } else {
             const double zero[3] = {0.0, 0.0, 0.0};
-            launch_m2p_typed<double>(P, kap != 0.0, ntg, ng, G.xs.p, zero, Pr, Tr, Tr.mom64.p, kap, Pr.VK[k].p, s);
+            launch_m2p_typed<double>(P, kap != 0.0, Pr, G.xs.p, zero, Tr, Tr.mom64.p, kap, (int)k, nk,
+                                     Pr.m2p_part64.p, s);
         }
     }
 }
 
-void launch_near(const Pair &Pr, const Targets &G, bool use_self, const double *phi, const double *dphi,
-                 cudaStream_t s) {
+void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, const double *phi,
+                   const double *dphi, cudaStream_t s) {
+    const int64_t ntg = G.n;
+    if (!ntg) return;
+    const int nk = (int)Pr.kappas.size();
+    const bool far = Pr.n_m2p_items > 0;
+    double *V0 = Pr.VK[0].p, *V1 = nk > 1 ? Pr.VK[1].p : nullptr;
+    const unsigned grid = (unsigned)((ntg + 3) / 4);
+    if (mixed) {
+        NearArgs32 nr{};
+        nr.ptr = Pr.near_ptr.p;
+        nr.panel = Pr.near_panel.p;
+        for (int k = 0; k < nk; ++k) {
+            nr.dV[k] = Pr.dV32.p + (int64_t)k * Pr.n_near;
+            nr.dK[k] = Pr.dK32.p + (int64_t)k * Pr.n_near;
+            nr.selfV[k] = use_self ? Pr.selfV[k].p : nullptr;
+        }
+        nr.selfp = G.self_panel.p;
+        nr.use_self = use_self ? 1 : 0;
+        nr.phi = phi;
+        nr.dphi = dphi;
+        const float *mp = far ? Pr.m2p_part32.p : nullptr;
+        if (nk == 1)
+            gather32_kernel<1><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_pos.p, Pr.p2p_part32.p, Pr.m2p_ptr.p,
+                                                    Pr.m2p_pos.p, mp, nr, V0, V1);
+        else
+            gather32_kernel<2><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_pos.p, Pr.p2p_part32.p, Pr.m2p_ptr.p,
+                                                    Pr.m2p_pos.p, mp, nr, V0, V1);
+    } else {
+        NearArgs nr{};
+        nr.ptr = Pr.near_ptr.p;
+        nr.panel = Pr.near_panel.p;
+        for (int k = 0; k < nk; ++k) {
+            nr.dV[k] = Pr.dV[k].p;
+            nr.dK[k] = Pr.dK[k].p;
+            nr.selfV[k] = use_self ? Pr.selfV[k].p : nullptr;
+        }
+        nr.selfp = G.self_panel.p;
+        nr.use_self = use_self ? 1 : 0;
+        nr.phi = phi;
+        nr.dphi = dphi;
+        const double *mp = far ? Pr.m2p_part64.p : nullptr;
+        if (nk == 1)
+            gather_kernel<double, 1><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_pos.p, Pr.p2p_part.p, Pr.m2p_ptr.p,
+                                                          Pr.m2p_pos.p, mp, nr, V0, V1);
+        else
+            gather_kernel<double, 2><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_pos.p, Pr.p2p_part.p, Pr.m2p_ptr.p,
+                                                          Pr.m2p_pos.p, mp, nr, V0, V1);
+    }
+    PB_LAUNCH_CHECK();
+}
+
+__global__ void targets32_kernel(int64_t n, const double *__restrict__ xs, double ox, double oy, double oz,
+                                 float4 *__restrict__ x32) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x32[i] = make_float4((float)(xs[3 * i] - ox), (float)(xs[3 * i + 1] - oy), (float)(xs[3 * i + 2] - oz), 0.f);
+}
+
+void targets_to_float(Pair &Pr, const Targets &G, const Tree &Tr, cudaStream_t s) {
+    Pr.x32.alloc(std::max<int64_t>(1, G.n));
     if (!G.n) return;
-    for (size_t k = 0; k < Pr.kappas.size(); ++k) {
-        near_apply_kernel<<<div_up(G.n, 128), 128, 0, s>>>(G.n, Pr.near_ptr.p, Pr.near_panel.p, Pr.dV[k].p, Pr.dK[k].p,
-                                                          use_self ? Pr.selfV[k].p : nullptr, G.self_panel.p,
-                                                          use_self ? 1 : 0, phi, dphi, Pr.VK[k].p);
+    targets32_kernel<<<div_up(G.n, 256), 256, 0, s>>>(G.n, G.xs.p, Tr.origin[0], Tr.origin[1], Tr.origin[2], Pr.x32.p);
+    PB_LAUNCH_CHECK();
+}
+
+// Near-singular corrections of the mixed path, rounded once to FP32.
+__global__ void to_float_kernel(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+void near_to_float(Pair &Pr, cudaStream_t s) {
+    const int nk = (int)Pr.kappas.size();
+    const int64_t n = Pr.n_near;
+    Pr.dV32.alloc(std::max<int64_t>(1, nk * n));
+    Pr.dK32.alloc(std::max<int64_t>(1, nk * n));
+    if (!n) return;
+    for (int k = 0; k < nk; ++k) {
+        to_float_kernel<<<div_up(n, 256), 256, 0, s>>>(n, Pr.dV[k].p, Pr.dV32.p + (int64_t)k * n);
+        PB_LAUNCH_CHECK();
+        to_float_kernel<<<div_up(n, 256), 256, 0, s>>>(n, Pr.dK[k].p, Pr.dK32.p + (int64_t)k * n);
         PB_LAUNCH_CHECK();
     }
 }

@@ -21,13 +21,19 @@ void upload_term_tables();
 void compute_strengths(Tree &Tr, const SurfDev &S, const double *phi, const double *dphi, bool mixed, cudaStream_t s);
 // P2M at the leaves, then M2M level by level to the root.
 void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s);
-// Direct sums into Pr.VK (overwrites).
+// Direct-sum partials of every (target, leaf) list entry.
 void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self, bool mixed, cudaStream_t s);
-// Far-field sums added into Pr.VK.
+// Far-field partials of every (target, box) list entry and kernel.
 void launch_m2p(const Pair &Pr, const Targets &G, const Tree &Tr, int P, bool mixed, cudaStream_t s);
-// Near-singular and self corrections added into Pr.VK.
-void launch_near(const Pair &Pr, const Targets &G, bool use_self, const double *phi, const double *dphi, cudaStream_t s);
+// Pr.VK = each target's partials, plus its near-singular corrections and (use_self)
+// its own panel's semi-analytical term, with phi, dphi of the source surface (overwrites).
+void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, const double *phi,
+                   const double *dphi, cudaStream_t s);
 // y[i] = half * phi_s[i] (0 if phi_s is null) + sum_terms (cK K + cV V)[rank[i]] for i < n.
+// FP32 target positions relative to the tree origin (mixed path).
+void targets_to_float(Pair &Pr, const Targets &G, const Tree &Tr, cudaStream_t s);
+// FP32 copies of the near-singular corrections for the mixed path.
+void near_to_float(Pair &Pr, cudaStream_t s);
 void launch_combine(int64_t n, const int32_t *rank, const double *phi_s, double half, const CombineRow &row, double *y,
                     cudaStream_t s);
 

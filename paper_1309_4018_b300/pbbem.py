@@ -267,7 +267,7 @@ class Problem:
         xx = np.ascontiguousarray(x, dtype=np.float64)
         out = np.zeros(6)
         self.ctx.check(_lib.pb_profile_operator(self._h, _ptr(xx), int(reps), _ptr(out)))
-        return dict(zip(("upward", "p2p", "m2p", "near", "combine", "total"), out.tolist()))
+        return dict(zip(("upward", "p2p", "m2p", "gather_near", "combine", "total"), out.tolist()))
 
     def tree(self, surface: int) -> dict:
         info = pb_tree_info()
