@@ -227,11 +227,21 @@ void setup_problem(pb_problem *pb) {
             if (prm.precision == PB_MIXED) P.m2p_part32.alloc(2 * nk * P.n_m2p);
             else P.m2p_part64.alloc(2 * nk * P.n_m2p);
         }
+        const bool mixed = prm.precision == PB_MIXED;
+        if (mixed) {
+            P.dV32.alloc(std::max<int64_t>(1, (int64_t)nk * P.n_near));
+            P.dK32.alloc(std::max<int64_t>(1, (int64_t)nk * P.n_near));
+        }
         for (size_t k = 0; k < nk; ++k) {
             P.VK[k].alloc(2 * std::max<int64_t>(1, G.n));
-            P.dV[k].alloc(std::max<int64_t>(1, P.n_near));
-            P.dK[k].alloc(std::max<int64_t>(1, P.n_near));
-            near_values(P, G, src, prm.K, prm.K_fine, P.kappas[k], P.dV[k].p, P.dK[k].p, s);
+            if (mixed) {
+                near_values32(P, G, src, prm.K, prm.K_fine, P.kappas[k], P.dV32.p + (int64_t)k * P.n_near,
+                              P.dK32.p + (int64_t)k * P.n_near, s);
+            } else {
+                P.dV[k].alloc(std::max<int64_t>(1, P.n_near));
+                P.dK[k].alloc(std::max<int64_t>(1, P.n_near));
+                near_values(P, G, src, prm.K, prm.K_fine, P.kappas[k], P.dV[k].p, P.dK[k].p, s);
+            }
             if (use_self) {
                 P.selfV[k].alloc(src.n);
                 self_integrals(src, prm.N_k, P.kappas[k], P.selfV[k].p, s);
@@ -241,8 +251,8 @@ void setup_problem(pb_problem *pb) {
     for (auto &P : pb->pairs) prepare(P, false);
     for (auto &P : pb->cpairs) prepare(P, true);
     if (prm.precision == PB_MIXED) {
-        for (auto &P : pb->pairs) { near_to_float(P, s); targets_to_float(P, pb->G[P.tgt], pb->T[P.tree], s); }
-        for (auto &P : pb->cpairs) { near_to_float(P, s); targets_to_float(P, pb->G[P.tgt], pb->T[P.tree], s); }
+        for (auto &P : pb->pairs) targets_to_float(P, pb->G[P.tgt], pb->T[P.tree], s);
+        for (auto &P : pb->cpairs) targets_to_float(P, pb->G[P.tgt], pb->T[P.tree], s);
     }
     // right-hand side
     pb->b.alloc(2 * pb->N);

@@ -143,6 +143,58 @@ __global__ void near_values_kernel(int64_t ntg, int64_t nnear, const double *__r
     dK[e] = kf - kk;
 }
 
+// Mixed path: the same corrections in FP32, with positions taken relative to
+// the panel's first vertex (differences of nearby points stay exact enough).
+__device__ void panel_rule_sums32(const float xr[3], const float e1[3], const float e2[3], const float nrm[3],
+                                  float area, const TriRule &R, float kappa, float &V, float &K) {
+    float sv = 0.f, sk = 0.f;
+    for (int k = 0; k < R.n; ++k) {
+        const float l1 = (float)R.l[k][1], l2 = (float)R.l[k][2];
+        const float rx = xr[0] - (l1 * e1[0] + l2 * e2[0]);
+        const float ry = xr[1] - (l1 * e1[1] + l2 * e2[1]);
+        const float rz = xr[2] - (l1 * e1[2] + l2 * e2[2]);
+        const float r2 = rx * rx + ry * ry + rz * rz;
+        const float inv = rsqrtf(r2);
+        const float rho = r2 * inv;
+        const float rn = rx * nrm[0] + ry * nrm[1] + rz * nrm[2];
+        const float e = kappa == 0.f ? 1.f : __expf(-kappa * rho);
+        const float wa = (float)R.w[k] * area;
+        sv += wa * e * inv;
+        sk += wa * rn * (1.f + kappa * rho) * e * inv * inv * inv;
+    }
+    V = sv * (float)kInv4Pi;
+    K = sk * (float)kInv4Pi;
+}
+
+__global__ void near_values32_kernel(int64_t ntg, int64_t nnear, const double *__restrict__ xs,
+                                     const int64_t *__restrict__ ptr, const int32_t *__restrict__ pan,
+                                     const double *__restrict__ v, const int32_t *__restrict__ t,
+                                     const double *__restrict__ nrm, const double *__restrict__ area, int slotK,
+                                     int slotF, float kappa, float *__restrict__ dV, float *__restrict__ dK) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnear) return;
+    int64_t lo = 0, hi = ntg;  // last i with ptr[i] <= e
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (ptr[mid] <= e) lo = mid; else hi = mid;
+    }
+    const int64_t i = lo;
+    const int j = pan[e];
+    const int a = t[3 * j], b = t[3 * j + 1], c = t[3 * j + 2];
+    float xr[3], e1[3], e2[3], nj[3];
+    for (int d = 0; d < 3; ++d) {
+        xr[d] = (float)(xs[3 * i + d] - v[3 * a + d]);
+        e1[d] = (float)(v[3 * b + d] - v[3 * a + d]);
+        e2[d] = (float)(v[3 * c + d] - v[3 * a + d]);
+        nj[d] = (float)nrm[3 * j + d];
+    }
+    float vf, kf, vk, kk;
+    panel_rule_sums32(xr, e1, e2, nj, (float)area[j], c_rules[slotF], kappa, vf, kf);
+    panel_rule_sums32(xr, e1, e2, nj, (float)area[j], c_rules[slotK], kappa, vk, kk);
+    dV[e] = vf - vk;
+    dK[e] = kf - kk;
+}
+
 // Semi-analytical single-layer self integral at the centroid (Zhu et al.
 // technique, N_k Gauss points per side).  Each edge at in-plane distance h
 // from the centroid contributes int F(h cosh s) / cosh s ds over
@@ -307,6 +359,16 @@ void near_values(const Pair &Pr, const Targets &G, const SurfDev &src, int K, in
                                                                Pr.near_panel.p, src.verts.p, src.tris.p, src.nrm.p,
                                                                src.area.p, rule_slot(K), rule_slot(K_fine), kappa, dV,
                                                                dK);
+    PB_LAUNCH_CHECK();
+}
+
+void near_values32(const Pair &Pr, const Targets &G, const SurfDev &src, int K, int K_fine, double kappa, float *dV,
+                   float *dK, cudaStream_t s) {
+    if (G.n == 0 || Pr.n_near == 0) return;
+    near_values32_kernel<<<div_up(Pr.n_near, 128), 128, 0, s>>>(G.n, Pr.n_near, G.xs.p, Pr.near_ptr.p,
+                                                                 Pr.near_panel.p, src.verts.p, src.tris.p, src.nrm.p,
+                                                                 src.area.p, rule_slot(K), rule_slot(K_fine),
+                                                                 (float)kappa, dV, dK);
     PB_LAUNCH_CHECK();
 }
 

@@ -12,6 +12,9 @@ void surface_geometry(SurfDev &S, int K, cudaStream_t s);
 // dV, dK per near entry of Pr: K_fine-rule minus K-rule values (FP64).
 void near_values(const Pair &Pr, const Targets &G, const SurfDev &src, int K, int K_fine, double kappa, double *dV,
                  double *dK, cudaStream_t s);
+// The same corrections evaluated in FP32 (mixed path).
+void near_values32(const Pair &Pr, const Targets &G, const SurfDev &src, int K, int K_fine, double kappa, float *dV,
+                   float *dK, cudaStream_t s);
 // Semi-analytical V_ii of every panel of S (input order).
 void self_integrals(const SurfDev &S, int N_k, double kappa, double *out, cudaStream_t s);
 // b_i = sum_k q_k G(c_i, r_k) / eps for the panels of S (input order); FP64,

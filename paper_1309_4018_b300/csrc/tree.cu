@@ -23,12 +23,13 @@ namespace pb {
 
 namespace {
 
-__global__ void bbox_kernel(const double *__restrict__ p, int64_t n, double *__restrict__ out) {
-    __shared__ double sm[6][32];
+// Per-block min/max of a strided slice (min and max are exact: any order gives the same box).
+__global__ void bbox_blocks_kernel(const double *__restrict__ p, int64_t n, double *__restrict__ part) {
+    __shared__ double sm[6][8];
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         for (int a = 0; a < 3; ++a) {
-            double v = p[3 * i + a];
+            const double v = p[3 * i + a];
             lo[a] = fmin(lo[a], v);
             hi[a] = fmax(hi[a], v);
         }
@@ -41,15 +42,24 @@ __global__ void bbox_kernel(const double *__restrict__ p, int64_t n, double *__r
     if (lane == 0)
         for (int a = 0; a < 3; ++a) { sm[a][warp] = lo[a]; sm[3 + a][warp] = hi[a]; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = blockDim.x >> 5;
+    if (threadIdx.x == 0)
         for (int a = 0; a < 3; ++a) {
             double l = sm[a][0], h = sm[3 + a][0];
-            for (int w = 1; w < nw; ++w) { l = fmin(l, sm[a][w]); h = fmax(h, sm[3 + a][w]); }
-            out[a] = l;
-            out[3 + a] = h;
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { l = fmin(l, sm[a][w]); h = fmax(h, sm[3 + a][w]); }
+            part[6 * blockIdx.x + a] = l;
+            part[6 * blockIdx.x + 3 + a] = h;
         }
-    }
+}
+
+__global__ void bbox_final_kernel(const double *__restrict__ part, int nb, double *__restrict__ out) {
+    if (threadIdx.x != 0) return;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = 0; b < nb; ++b)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], part[6 * b + a]);
+            hi[a] = fmax(hi[a], part[6 * b + 3 + a]);
+        }
+    for (int a = 0; a < 3; ++a) { out[a] = lo[a]; out[3 + a] = hi[a]; }
 }
 
 __device__ __forceinline__ uint64_t spread3(uint64_t v) {
@@ -239,29 +249,31 @@ __global__ void traverse_kernel(int64_t ntg, const double *__restrict__ xs, cons
 
 // ---------------------------------------------------------------- entry-major grouping
 // key(e) = leaf index of a P2P entry (remap = node_leaf) or node id of an M2P entry.
-__global__ void inv_count_kernel(int64_t m, const int64_t *__restrict__ ptr, const int32_t *__restrict__ ent,
-                                 const int32_t *__restrict__ remap, int32_t *__restrict__ cnt) {
+__global__ void owner_kernel(int64_t m, const int64_t *__restrict__ ptr, int32_t *__restrict__ owner) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m) return;
-    for (int64_t e = ptr[t]; e < ptr[t + 1]; ++e) {
-        const int key = remap ? remap[ent[e]] : ent[e];
-        atomicAdd(&cnt[key], 1);
-    }
+    for (int64_t e = ptr[t]; e < ptr[t + 1]; ++e) owner[e] = (int32_t)t;
+}
+
+__global__ void inv_count_kernel(int64_t nent, const int32_t *__restrict__ ent, const int32_t *__restrict__ remap,
+                                 int32_t *__restrict__ cnt) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nent) return;
+    const int key = remap ? remap[ent[e]] : ent[e];
+    atomicAdd(&cnt[key], 1);
 }
 
 // The order of the pairs inside one key's group does not matter: every pair
 // writes its own partial, and the gather reads them back in list order.
-__global__ void inv_fill_kernel(int64_t m, const int64_t *__restrict__ ptr, const int32_t *__restrict__ ent,
+__global__ void inv_fill_kernel(int64_t nent, const int32_t *__restrict__ owner, const int32_t *__restrict__ ent,
                                 const int32_t *__restrict__ remap, const int64_t *__restrict__ off,
                                 int32_t *__restrict__ cursor, int2 *__restrict__ inv, int32_t *__restrict__ pos) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= m) return;
-    for (int64_t e = ptr[t]; e < ptr[t + 1]; ++e) {
-        const int key = remap ? remap[ent[e]] : ent[e];
-        const int64_t p = off[key] + atomicAdd(&cursor[key], 1);
-        inv[p] = make_int2((int)t, (int)e);
-        pos[e] = (int32_t)p;
-    }
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nent) return;
+    const int key = remap ? remap[ent[e]] : ent[e];
+    const int64_t p = off[key] + atomicAdd(&cursor[key], 1);
+    inv[p] = make_int2(owner[e], (int)e);
+    pos[e] = (int32_t)p;
 }
 
 __global__ void item_count_kernel(int nkeys, const int64_t *__restrict__ off, int32_t *__restrict__ nitems) {
@@ -312,9 +324,9 @@ __global__ void __launch_bounds__(128) near_kernel(
     const double *__restrict__ L, const float4 *__restrict__ pan32, double ox, double oy, double oz, double thres,
     int32_t *__restrict__ ncount, int32_t *__restrict__ excl, int32_t *__restrict__ self_excl,
     const int64_t *__restrict__ near_ptr, int32_t *__restrict__ near_panel, const int64_t *__restrict__ m2p_ptr,
-    const int32_t *__restrict__ m2p_node, const double *__restrict__ centre, const double *__restrict__ rb2,
-    double reach) {
+    const int32_t *__restrict__ m2p_node, const float4 *__restrict__ cen32, double reach) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float freach = (float)reach;
     const int64_t i = (int64_t)blockIdx.x * 4 + warp;
     if (i >= ntg) return;
     const double x = xs[3 * i], y = xs[3 * i + 1], z = xs[3 * i + 2];
@@ -327,6 +339,11 @@ __global__ void __launch_bounds__(128) near_kernel(
     const int64_t o = FILL ? near_ptr[i] : 0;
     for (int64_t e = 0; e < nl; ++e) {
         const int b = leaf_node[lst[e]];
+        // a leaf farther than reach + r_b holds no point of a near panel (FP32 with margin)
+        const float4 bc = cen32[b];
+        const float bx = fx - bc.x, by = fy - bc.y, bz = fz - bc.z;
+        const float rr = freach + sqrtf(bc.w);
+        if (bx * bx + by * by + bz * bz > rr * rr * 1.0001f + 1e-3f) continue;
         const int64_t q0 = start[b], q1 = start[b] + count[b];
         for (int64_t qb = q0; qb < q1; qb += 32) {
             const int64_t q = qb + lane;
@@ -372,28 +389,41 @@ __global__ void __launch_bounds__(128) near_kernel(
         return;
     }
     // near panels lying wholly in accepted boxes: only boxes that can hold a
-    // point within `reach` (>= thres L_j + panel radius) of the target are scanned
-    for (int64_t e = m2p_ptr[i]; e < m2p_ptr[i + 1]; ++e) {
-        const int b = m2p_node[e];
-        const double bx = x - centre[3 * b], by = y - centre[3 * b + 1], bz = z - centre[3 * b + 2];
-        const double rr = reach + sqrt(rb2[b]);
-        if (bx * bx + by * by + bz * bz >= rr * rr) continue;
-        const int64_t q0 = start[b], q1 = start[b] + count[b];
-        for (int64_t qb = q0; qb < q1; qb += 32) {
-            const int64_t q = qb + lane;
-            bool exc = false;
-            if (q < q1) {
-                const int j = pids[q];
-                const float4 pc = pan32[j];
-                const float dx = fx - pc.x, dy = fy - pc.y, dz = fz - pc.z;
-                if (perm[q] == j * K && j != me && dx * dx + dy * dy + dz * dz < pc.w &&
-                    is_near(x, y, z, cen, L, thres, j)) {
-                    bool any = false;
-                    for (int kk = 0; kk < K && !any; ++kk) any = in_sorted(lst, nl, point_leaf[j * K + kk]);
-                    exc = !any;
+    // point within `reach` (>= thres L_j + panel radius) of the target are
+    // scanned; lanes test the boxes in turn (FP32 with margin)
+    for (int64_t eb = m2p_ptr[i]; eb < m2p_ptr[i + 1]; eb += 32) {
+        const int64_t e = eb + lane;
+        bool hit = false;
+        int bsel = -1;
+        if (e < m2p_ptr[i + 1]) {
+            bsel = m2p_node[e];
+            const float4 bc = cen32[bsel];
+            const float bx = fx - bc.x, by = fy - bc.y, bz = fz - bc.z;
+            const float rr = freach + sqrtf(bc.w);
+            hit = bx * bx + by * by + bz * bz <= rr * rr * 1.0001f + 1e-3f;
+        }
+        uint32_t hits = __ballot_sync(0xffffffffu, hit);
+        while (hits) {
+            const int src = __ffs(hits) - 1;
+            hits &= hits - 1;
+            const int b = __shfl_sync(0xffffffffu, bsel, src);
+            const int64_t q0 = start[b], q1 = start[b] + count[b];
+            for (int64_t qb = q0; qb < q1; qb += 32) {
+                const int64_t q = qb + lane;
+                bool exc = false;
+                if (q < q1) {
+                    const int j = pids[q];
+                    const float4 pc = pan32[j];
+                    const float dx = fx - pc.x, dy = fy - pc.y, dz = fz - pc.z;
+                    if (perm[q] == j * K && j != me && dx * dx + dy * dy + dz * dz < pc.w &&
+                        is_near(x, y, z, cen, L, thres, j)) {
+                        bool any = false;
+                        for (int kk = 0; kk < K && !any; ++kk) any = in_sorted(lst, nl, point_leaf[j * K + kk]);
+                        exc = !any;
+                    }
                 }
+                ex += __popc(__ballot_sync(0xffffffffu, exc));
             }
-            ex += __popc(__ballot_sync(0xffffffffu, exc));
         }
     }
     if (lane == 0) {
@@ -475,7 +505,11 @@ int64_t device_sum_i32(const int32_t *a, int64_t n, cudaStream_t s) {
 
 void root_cube_from(const double *d_points, int64_t n, cudaStream_t s, double corner[3], double &side) {
     TmpBuf<double> bb(6, s);
-    bbox_kernel<<<1, 1024, 0, s>>>(d_points, n, bb.p);
+    const int nb = (int)std::min<int64_t>(256, std::max<int64_t>(1, (n + 4095) / 4096));
+    TmpBuf<double> part(6 * nb, s);
+    bbox_blocks_kernel<<<nb, 256, 0, s>>>(d_points, n, part.p);
+    PB_LAUNCH_CHECK();
+    bbox_final_kernel<<<1, 32, 0, s>>>(part.p, nb, bb.p);
     PB_LAUNCH_CHECK();
     double h[6];
     PB_CUDA_TRY(cudaMemcpyAsync(h, bb.p, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -673,13 +707,16 @@ void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, 
         PB_CUDA_TRY(cudaMemsetAsync(cursor.p, 0, sizeof(int32_t) * std::max(1, nkeys), s));
         inv.alloc(std::max<int64_t>(1, nent));
         pos.alloc(std::max<int64_t>(1, nent));
+        TmpBuf<int32_t> owner(std::max<int64_t>(1, nent), s);
         if (m && nent) {
-            inv_count_kernel<<<div_up(m, 128), 128, 0, s>>>(m, ptr, ent, remap, cnt.p);
+            owner_kernel<<<div_up(m, 128), 128, 0, s>>>(m, ptr, owner.p);
+            PB_LAUNCH_CHECK();
+            inv_count_kernel<<<div_up(nent, 256), 256, 0, s>>>(nent, ent, remap, cnt.p);
             PB_LAUNCH_CHECK();
         }
         exclusive_scan_i32_to_i64(cnt.p, off.p, nkeys, s);
         if (m && nent) {
-            inv_fill_kernel<<<div_up(m, 128), 128, 0, s>>>(m, ptr, ent, remap, off.p, cursor.p, inv.p, pos.p);
+            inv_fill_kernel<<<div_up(nent, 256), 256, 0, s>>>(nent, owner.p, ent, remap, off.p, cursor.p, inv.p, pos.p);
             PB_LAUNCH_CHECK();
         }
         item_count_kernel<<<div_up(nkeys, 128), 128, 0, s>>>(nkeys, off.p, nit.p);
@@ -717,7 +754,7 @@ void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, 
                                                         T.pids.p, T.point_leaf.p, src.cen.p, src.L.p, pan32.p,
                                                         T.origin[0], T.origin[1], T.origin[2], prm.thres, nc.p, ex.p,
                                                         se.p, nullptr, nullptr, Pr.m2p_ptr.p, Pr.m2p_node.p,
-                                                        T.centre.p, T.rb2.p, reach);
+                                                        T.cen32.p, reach);
         PB_LAUNCH_CHECK();
     }
     exclusive_scan_i32_to_i64(nc.p, Pr.near_ptr.p, m, s);
@@ -731,7 +768,7 @@ void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, 
                                                        T.pids.p, T.point_leaf.p, src.cen.p, src.L.p, pan32.p,
                                                        T.origin[0], T.origin[1], T.origin[2], prm.thres, nullptr,
                                                        nullptr, nullptr, Pr.near_ptr.p, Pr.near_panel.p, Pr.m2p_ptr.p,
-                                                       Pr.m2p_node.p, T.centre.p, T.rb2.p, reach);
+                                                       Pr.m2p_node.p, T.cen32.p, reach);
         PB_LAUNCH_CHECK();
     }
     PB_CUDA_TRY(cudaStreamSynchronize(s));

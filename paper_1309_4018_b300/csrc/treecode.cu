@@ -912,26 +912,6 @@ void targets_to_float(Pair &Pr, const Targets &G, const Tree &Tr, cudaStream_t s
     PB_LAUNCH_CHECK();
 }
 
-// Near-singular corrections of the mixed path, rounded once to FP32.
-__global__ void to_float_kernel(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (float)a[i];
-}
-
-void near_to_float(Pair &Pr, cudaStream_t s) {
-    const int nk = (int)Pr.kappas.size();
-    const int64_t n = Pr.n_near;
-    Pr.dV32.alloc(std::max<int64_t>(1, nk * n));
-    Pr.dK32.alloc(std::max<int64_t>(1, nk * n));
-    if (!n) return;
-    for (int k = 0; k < nk; ++k) {
-        to_float_kernel<<<div_up(n, 256), 256, 0, s>>>(n, Pr.dV[k].p, Pr.dV32.p + (int64_t)k * n);
-        PB_LAUNCH_CHECK();
-        to_float_kernel<<<div_up(n, 256), 256, 0, s>>>(n, Pr.dK[k].p, Pr.dK32.p + (int64_t)k * n);
-        PB_LAUNCH_CHECK();
-    }
-}
-
 void launch_combine(int64_t n, const int32_t *rank, const double *phi_s, double half, const CombineRow &row, double *y,
                     cudaStream_t s) {
     if (!n) return;

@@ -32,8 +32,6 @@ void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, 
 // y[i] = half * phi_s[i] (0 if phi_s is null) + sum_terms (cK K + cV V)[rank[i]] for i < n.
 // FP32 target positions relative to the tree origin (mixed path).
 void targets_to_float(Pair &Pr, const Targets &G, const Tree &Tr, cudaStream_t s);
-// FP32 copies of the near-singular corrections for the mixed path.
-void near_to_float(Pair &Pr, cudaStream_t s);
 void launch_combine(int64_t n, const int32_t *rank, const double *phi_s, double half, const CombineRow &row, double *y,
                     cudaStream_t s);
 
