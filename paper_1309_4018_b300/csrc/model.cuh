@@ -82,7 +82,7 @@ struct Pair {
     // list entry) pairs that use it, grouped by leaf / box and packed 32 per
     // work item (one warp); every pair writes one partial sum, and a gather
     // adds each target's partials in its own list order.
-    DevBuf<int2> p2p_inv, m2p_inv;        // (target, CSR entry), grouped
+    DevBuf<int32_t> p2p_inv, m2p_inv;     // target of every grouped (target, entry) pair
     DevBuf<int32_t> p2p_pos, m2p_pos;     // CSR entry -> grouped position
     DevBuf<int4> p2p_items, m2p_items;    // (leaf | box, grouped start, count <= 32, 0)
     int64_t n_p2p_items = 0, n_m2p_items = 0;

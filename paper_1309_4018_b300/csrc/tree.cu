@@ -267,12 +267,12 @@ __global__ void inv_count_kernel(int64_t nent, const int32_t *__restrict__ ent, 
 // writes its own partial, and the gather reads them back in list order.
 __global__ void inv_fill_kernel(int64_t nent, const int32_t *__restrict__ owner, const int32_t *__restrict__ ent,
                                 const int32_t *__restrict__ remap, const int64_t *__restrict__ off,
-                                int32_t *__restrict__ cursor, int2 *__restrict__ inv, int32_t *__restrict__ pos) {
+                                int32_t *__restrict__ cursor, int32_t *__restrict__ inv, int32_t *__restrict__ pos) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nent) return;
     const int key = remap ? remap[ent[e]] : ent[e];
     const int64_t p = off[key] + atomicAdd(&cursor[key], 1);
-    inv[p] = make_int2(owner[e], (int)e);
+    inv[p] = owner[e];
     pos[e] = (int32_t)p;
 }
 
@@ -700,7 +700,7 @@ void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, 
     }
     // entry-major grouping of the lists
     auto group = [&](const int64_t *ptr, const int32_t *ent, const int32_t *remap, int nkeys, int64_t nent,
-                     DevBuf<int2> &inv, DevBuf<int32_t> &pos, DevBuf<int4> &items, int64_t &nitems) {
+                     DevBuf<int32_t> &inv, DevBuf<int32_t> &pos, DevBuf<int4> &items, int64_t &nitems) {
         TmpBuf<int32_t> cnt(std::max(1, nkeys), s), cursor(std::max(1, nkeys), s), nit(std::max(1, nkeys), s);
         TmpBuf<int64_t> off(nkeys + 1, s), ioff(nkeys + 1, s);
         PB_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * std::max(1, nkeys), s));

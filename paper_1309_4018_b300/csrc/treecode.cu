@@ -245,7 +245,7 @@ __device__ __forceinline__ void comp_add(float &hi, float &lo, float v) {
 // stored in FP64 at its grouped position.
 template <int NK, bool Y0, bool Y1>
 __global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, const int4 *__restrict__ items,
-                                                    const int2 *__restrict__ inv, int64_t npart,
+                                                    const int32_t *__restrict__ inv, int64_t npart,
                                                     const float4 *__restrict__ x32,
                                                     const int32_t *__restrict__ selfp, int use_self,
                                                     const int32_t *__restrict__ leaf_node,
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, const int4 *
     float tx = 0.f, ty = 0.f, tz = 0.f;
     int me = -1;
     if (valid) {
-        const int t = inv[slot].x;
+        const int t = inv[slot];
         const float4 x = x32[t];
         tx = x.x;
         ty = x.y;
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, const int4 *
 // ---------------------------------------------------------------- P2P, FP64
 template <int NK, bool Y0, bool Y1>
 __global__ void __launch_bounds__(128) p2p64_kernel(int64_t nitems, const int4 *__restrict__ items,
-                                                    const int2 *__restrict__ inv, int64_t npart,
+                                                    const int32_t *__restrict__ inv, int64_t npart,
                                                     const double *__restrict__ xs, const int32_t *__restrict__ selfp,
                                                     int use_self, const int32_t *__restrict__ leaf_node,
                                                     const int64_t *__restrict__ start, const int64_t *__restrict__ count,
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(128) p2p64_kernel(int64_t nitems, const int4 *
     double tx = 0, ty = 0, tz = 0;
     int me = -1;
     if (valid) {
-        const int t = inv[slot].x;
+        const int t = inv[slot];
         tx = xs[3 * t]; ty = xs[3 * t + 1]; tz = xs[3 * t + 2];
         if (use_self) me = selfp[t];
     }
@@ -454,6 +454,57 @@ __device__ __forceinline__ void m2p_eval(T ux, T uy, T uz, T kappa, const T *__r
     }
 }
 
+// Laplace and Yukawa coefficients for the same (target, box) in one pass: the
+// moments of each term are loaded once and contracted with both.
+template <int P, typename T>
+__device__ __forceinline__ void m2p_eval_ly(T ux, T uy, T uz, T kappa, const T *__restrict__ mom, T &VL, T &KL,
+                                            T &VY, T &KY) {
+    constexpr int NT = (P + 1) * (P + 2) * (P + 3) / 6;
+    T a[NT], ay[NT], b[NT];
+    const T r2 = ux * ux + uy * uy + uz * uz;
+    T rinv;
+    if constexpr (sizeof(T) == 4) rinv = rsqrtf(r2); else rinv = rsqrt(r2);
+    const T ir2 = rinv * rinv;
+    T e0;
+    if constexpr (sizeof(T) == 4) e0 = __expf(-kappa * r2 * rinv); else e0 = exp(-kappa * r2 * rinv);
+    a[0] = rinv;
+    ay[0] = e0 * rinv;
+    b[0] = e0;
+    {
+        const T m = mom[0], d = mom[NT];
+        VL = a[0] * m; KL = a[0] * d;
+        VY = ay[0] * m; KY = ay[0] * d;
+    }
+#pragma unroll
+    for (int n = 1; n <= P; ++n) {
+        const T c1 = (T)(2 * n - 1) / (T)n, c2 = (T)(n - 1) / (T)n;
+        const T kn = kappa / (T)n;
+#pragma unroll
+        for (int k1 = n; k1 >= 0; --k1) {
+#pragma unroll
+            for (int k2 = n - k1; k2 >= 0; --k2) {
+                const int k3 = n - k1 - k2;
+                const int i = term_index(k1, k2, k3);
+                T s1 = 0, s2 = 0, y1 = 0, y2 = 0, t1 = 0, t2 = 0;
+                if (k1 >= 1) { const int j = term_index(k1 - 1, k2, k3); s1 += ux * a[j]; y1 += ux * ay[j]; t1 += ux * b[j]; }
+                if (k2 >= 1) { const int j = term_index(k1, k2 - 1, k3); s1 += uy * a[j]; y1 += uy * ay[j]; t1 += uy * b[j]; }
+                if (k3 >= 1) { const int j = term_index(k1, k2, k3 - 1); s1 += uz * a[j]; y1 += uz * ay[j]; t1 += uz * b[j]; }
+                if (k1 >= 2) { const int j = term_index(k1 - 2, k2, k3); s2 += a[j]; y2 += ay[j]; t2 += b[j]; }
+                if (k2 >= 2) { const int j = term_index(k1, k2 - 2, k3); s2 += a[j]; y2 += ay[j]; t2 += b[j]; }
+                if (k3 >= 2) { const int j = term_index(k1, k2, k3 - 2); s2 += a[j]; y2 += ay[j]; t2 += b[j]; }
+                a[i] = -(c1 * s1 + c2 * s2) * ir2;
+                ay[i] = -(c1 * y1 + c2 * y2 + kn * (t1 + t2)) * ir2;
+                b[i] = -kn * (y1 + y2);
+                const T m = mom[i], d = mom[NT + i];
+                VL += a[i] * m;
+                KL += a[i] * d;
+                VY += ay[i] * m;
+                KY += ay[i] * d;
+            }
+        }
+    }
+}
+
 // Runtime-order variant for orders without a compiled specialisation (local arrays).
 template <bool YUK, typename T>
 __device__ void m2p_eval_rt(int P, T ux, T uy, T uz, T kappa, const T *__restrict__ mom, T &V, T &K) {
@@ -493,7 +544,7 @@ __device__ void m2p_eval_rt(int P, T ux, T uy, T uz, T kappa, const T *__restric
 // stores (V, K) at the pair's grouped position.
 template <int P, bool YUK, typename T>
 __global__ void __launch_bounds__(128) m2p_kernel(int64_t nitems, const int4 *__restrict__ items,
-                                                  const int2 *__restrict__ inv, int64_t npart, int Prt,
+                                                  const int32_t *__restrict__ inv, int64_t npart, int Prt,
                                                   const double *__restrict__ xs, const float4 *__restrict__ x32,
                                                   const double *__restrict__ centre, const float4 *__restrict__ cen32,
                                                   const T *__restrict__ mom, double kappa, int kslot, int nk,
@@ -504,7 +555,7 @@ __global__ void __launch_bounds__(128) m2p_kernel(int64_t nitems, const int4 *__
     const int4 it = items[item];
     if (lane >= it.z) return;
     const int64_t slot = (int64_t)it.y + lane;
-    const int t = inv[slot].x;
+    const int t = inv[slot];
     const int b = it.x;
     const int Pe = P >= 0 ? P : Prt;
     const int NT = (Pe + 1) * (Pe + 2) * (Pe + 3) / 6;
@@ -527,6 +578,28 @@ __global__ void __launch_bounds__(128) m2p_kernel(int64_t nitems, const int4 *__
     T *rec = part + (int64_t)2 * nk * slot + 2 * kslot;
     rec[0] = V;
     rec[1] = K;
+}
+
+// Box-major M2P for a pair whose two kernels are Laplace (slot 0) and Yukawa
+// (slot 1): both recurrences in one pass, one record (VL, KL, VY, KY) per pair.
+template <int P>
+__global__ void __launch_bounds__(128) m2p_ly32_kernel(int64_t nitems, const int4 *__restrict__ items,
+                                                       const int32_t *__restrict__ inv, const float4 *__restrict__ x32,
+                                                       const float4 *__restrict__ cen32, const float *__restrict__ mom,
+                                                       float kappa, float4 *__restrict__ part) {
+    constexpr int NT = (P + 1) * (P + 2) * (P + 3) / 6;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * 4 + warp;
+    if (item >= nitems) return;
+    const int4 it = items[item];
+    if (lane >= it.z) return;
+    const int64_t slot = (int64_t)it.y + lane;
+    const int b = it.x;
+    const float4 c = cen32[b];
+    const float4 x = x32[inv[slot]];
+    float VL, KL, VY, KY;
+    m2p_eval_ly<P, float>(c.x - x.x, c.y - x.y, c.z - x.z, kappa, mom + (int64_t)b * 2 * NT, VL, KL, VY, KY);
+    part[slot] = make_float4(VL, KL, VY, KY);
 }
 
 // One warp per target: V and K of every kernel = its P2P and M2P partials
@@ -833,6 +906,23 @@ void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self,
 
 void launch_m2p(const Pair &Pr, const Targets &G, const Tree &Tr, int P, bool mixed, cudaStream_t s) {
     if (Pr.n_m2p_items == 0) return;
+    if (mixed && Pr.kappas.size() == 2 && Pr.kappas[0] == 0.0 && Pr.kappas[1] != 0.0 && P <= 8) {
+        const int64_t ni = Pr.n_m2p_items;
+        const unsigned grid = (unsigned)((ni + 3) / 4);
+        float4 *part = reinterpret_cast<float4 *>(Pr.m2p_part32.p);
+        const float kap = (float)Pr.kappas[1];
+#define PB_LY(PP)                                                                                              \
+    case PP:                                                                                                   \
+        m2p_ly32_kernel<PP><<<grid, 128, 0, s>>>(ni, Pr.m2p_items.p, Pr.m2p_inv.p, Pr.x32.p, Tr.cen32.p, Tr.mom32.p, \
+                                                 kap, part);                                                   \
+        break;
+        switch (P) {
+            PB_LY(0) PB_LY(1) PB_LY(2) PB_LY(3) PB_LY(4) PB_LY(5) PB_LY(6) PB_LY(7) PB_LY(8)
+        }
+#undef PB_LY
+        PB_LAUNCH_CHECK();
+        return;
+    }
     for (size_t k = 0; k < Pr.kappas.size(); ++k) {
         const double kap = Pr.kappas[k];
         const int nk = (int)Pr.kappas.size();
