@@ -96,17 +96,20 @@ struct SrcView<float> {
     }
 };
 
-constexpr int kP2MChunk = 32;
+constexpr int kP2MChunk = 128;
 
-// One block per leaf; each thread owns up to 4 moment terms and sums over the
-// leaf's sources in order (deterministic).
+// One block per leaf: each thread computes the powers of one source's offset
+// from the leaf centre (128 sources per chunk), then each thread owns up to 4
+// moment terms and sums over the chunk's sources in order (deterministic).
 template <typename T>
 __global__ void __launch_bounds__(128) p2m_kernel(int nleaves, const int32_t *__restrict__ leaf_node,
                                                   const int64_t *__restrict__ start, const int64_t *__restrict__ count,
                                                   const double *__restrict__ centre, double ox, double oy, double oz,
                                                   SrcView<T> sv, int P, int NT, T *__restrict__ mom) {
-    __shared__ T pw[3][kP2MChunk][kMaxP + 1];
-    __shared__ T sd[kP2MChunk][4];
+    constexpr int CH = sizeof(T) == 4 ? kP2MChunk : kP2MChunk / 2;   // FP64 tiles stay under 48 KB
+    __shared__ T pw[3][kMaxP + 1][CH];
+    __shared__ T sd[4][CH];
+    __shared__ int sterm[3 * 455];
     const int node = leaf_node[blockIdx.x];
     const int64_t s0 = start[node], cnt = count[node];
     T c[3];
@@ -115,34 +118,35 @@ __global__ void __launch_bounds__(128) p2m_kernel(int nleaves, const int32_t *__
     } else {
         c[0] = (T)(centre[3 * node] - ox); c[1] = (T)(centre[3 * node + 1] - oy); c[2] = (T)(centre[3 * node + 2] - oz);
     }
+    for (int i = threadIdx.x; i < 3 * NT; i += blockDim.x) sterm[i] = c_terms[i];
     T accM[4] = {0, 0, 0, 0}, accD[4] = {0, 0, 0, 0};
-    for (int64_t c0 = 0; c0 < cnt; c0 += kP2MChunk) {
-        const int m = (int)(cnt - c0 < kP2MChunk ? cnt - c0 : kP2MChunk);
+    for (int64_t c0 = 0; c0 < cnt; c0 += CH) {
+        const int m = (int)(cnt - c0 < CH ? cnt - c0 : CH);
         __syncthreads();
         if (threadIdx.x < m) {
             T x, y, z, s, dx, dy, dz;
             sv.get(s0 + c0 + threadIdx.x, c, x, y, z, s, dx, dy, dz);
             T px = 1, py = 1, pz = 1;
             for (int e = 0; e <= P; ++e) {
-                pw[0][threadIdx.x][e] = px; pw[1][threadIdx.x][e] = py; pw[2][threadIdx.x][e] = pz;
+                pw[0][e][threadIdx.x] = px; pw[1][e][threadIdx.x] = py; pw[2][e][threadIdx.x] = pz;
                 px *= x; py *= y; pz *= z;
             }
-            sd[threadIdx.x][0] = s; sd[threadIdx.x][1] = dx; sd[threadIdx.x][2] = dy; sd[threadIdx.x][3] = dz;
+            sd[0][threadIdx.x] = s; sd[1][threadIdx.x] = dx; sd[2][threadIdx.x] = dy; sd[3][threadIdx.x] = dz;
         }
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int k = threadIdx.x + 128 * r;
             if (k >= NT) break;
-            const int k1 = c_terms[3 * k], k2 = c_terms[3 * k + 1], k3 = c_terms[3 * k + 2];
+            const int k1 = sterm[3 * k], k2 = sterm[3 * k + 1], k3 = sterm[3 * k + 2];
             T aM = accM[r], aD = accD[r];
             for (int j = 0; j < m; ++j) {
-                const T mono = pw[0][j][k1] * pw[1][j][k2] * pw[2][j][k3];
-                aM += sd[j][0] * mono;
+                const T p1 = pw[0][k1][j], p2 = pw[1][k2][j], p3 = pw[2][k3][j];
+                aM += sd[0][j] * (p1 * p2 * p3);
                 T dsum = 0;
-                if (k1) dsum += sd[j][1] * (T)k1 * pw[0][j][k1 - 1] * pw[1][j][k2] * pw[2][j][k3];
-                if (k2) dsum += sd[j][2] * (T)k2 * pw[0][j][k1] * pw[1][j][k2 - 1] * pw[2][j][k3];
-                if (k3) dsum += sd[j][3] * (T)k3 * pw[0][j][k1] * pw[1][j][k2] * pw[2][j][k3 - 1];
+                if (k1) dsum += sd[1][j] * (T)k1 * pw[0][k1 - 1][j] * p2 * p3;
+                if (k2) dsum += sd[2][j] * (T)k2 * p1 * pw[1][k2 - 1][j] * p3;
+                if (k3) dsum += sd[3][j] * (T)k3 * p1 * p2 * pw[2][k3 - 1][j];
                 aD += dsum;
             }
             accM[r] = aM;
@@ -160,12 +164,13 @@ __global__ void __launch_bounds__(128) p2m_kernel(int nleaves, const int32_t *__
 
 // ---------------------------------------------------------------- M2M (one level, bottom-up)
 // M_parent^k = sum_children sum_{l <= k} C(k, l) (y_child - y_parent)^(k-l) M_child^l;
-// the dipole moments D shift with the same rule.  One block per node of the
-// level: the children's moments (contiguous node ids), the powers of the
-// shifts and the binomials are staged in shared memory; one thread per
-// (child, term) forms that child's shifted term, then one thread per term adds
-// the children in order.
-constexpr int kM2MMaxShared = 2 * 8 * 2 * 455 * 8;
+// the dipole moments D shift with the same rule.  The shift factorises by
+// axis, so it is applied as three one-dimensional passes (z, then y, then x),
+// each output term summing at most P + 1 inputs; a term with |k| <= P only
+// reads terms with |l| <= |k|, so the truncated set is closed under the
+// passes.  One block per node of the level; the children (contiguous node
+// ids) are shifted in parallel in shared memory and added in child order.
+constexpr int kM2MMaxShared = 2 * 8 * 2 * 455 * 8 + 3 * 455 * 4;
 
 template <typename T>
 __global__ void __launch_bounds__(256) m2m_kernel(int nodes_begin, const int32_t *__restrict__ first_child,
@@ -173,15 +178,17 @@ __global__ void __launch_bounds__(256) m2m_kernel(int nodes_begin, const int32_t
                                                   const double *__restrict__ centre, int P, int NT,
                                                   T *__restrict__ mom) {
     extern __shared__ __align__(16) unsigned char m2m_smem[];
-    T *smom = reinterpret_cast<T *>(m2m_smem);
-    T *spart = smom + 8 * 2 * NT;
+    T *buf0 = reinterpret_cast<T *>(m2m_smem);          // nc x 2NT
+    T *buf1 = buf0 + 8 * 2 * NT;                        // nc x 2NT
+    int *sterm = reinterpret_cast<int *>(buf1 + 8 * 2 * NT);
     __shared__ T hp[8][3][kMaxP + 1];
     __shared__ T sbin[kMaxP + 1][kMaxP + 1];
     const int b = nodes_begin + blockIdx.x;
     const int nc = nchild[b];
     if (nc == 0) return;
     const int fc = first_child[b];
-    for (int i = threadIdx.x; i < nc * 2 * NT; i += blockDim.x) smom[i] = mom[(int64_t)fc * 2 * NT + i];
+    for (int i = threadIdx.x; i < nc * 2 * NT; i += blockDim.x) buf0[i] = mom[(int64_t)fc * 2 * NT + i];
+    for (int i = threadIdx.x; i < 3 * NT; i += blockDim.x) sterm[i] = c_terms[i];
     for (int i = threadIdx.x; i < nc * 3; i += blockDim.x) {
         const int c = i / 3, ax = i - 3 * c;
         const T h = (T)(centre[3 * (fc + c) + ax] - centre[3 * b + ax]);
@@ -193,31 +200,28 @@ __global__ void __launch_bounds__(256) m2m_kernel(int nodes_begin, const int32_t
         sbin[n][k] = (T)c_binom[n][k];
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nc * NT; idx += blockDim.x) {
-        const int c = idx / NT, k = idx - c * NT;
-        const int k1 = c_terms[3 * k], k2 = c_terms[3 * k + 1], k3 = c_terms[3 * k + 2];
-        const T *mc = smom + c * 2 * NT;
-        T accM = 0, accD = 0;
-        for (int l1 = 0; l1 <= k1; ++l1) {
-            const T f1 = sbin[k1][l1] * hp[c][0][k1 - l1];
-            for (int l2 = 0; l2 <= k2; ++l2) {
-                const T f2 = f1 * sbin[k2][l2] * hp[c][1][k2 - l2];
-                for (int l3 = 0; l3 <= k3; ++l3) {
-                    const T coef = f2 * sbin[k3][l3] * hp[c][2][k3 - l3];
-                    const int li = term_index(l1, l2, l3);
-                    accM += coef * mc[li];
-                    accD += coef * mc[NT + li];
-                }
+    T *src = buf0, *dst = buf1;
+    for (int ax = 2; ax >= 0; --ax) {
+        for (int idx = threadIdx.x; idx < nc * 2 * NT; idx += blockDim.x) {
+            const int c = idx / (2 * NT), r = idx - c * 2 * NT;
+            const int half = r >= NT ? NT : 0, k = r - half;
+            int kk[3] = {sterm[3 * k], sterm[3 * k + 1], sterm[3 * k + 2]};
+            const int kax = kk[ax];
+            const T *sc = src + c * 2 * NT + half;
+            T acc = 0;
+            for (int l = 0; l <= kax; ++l) {
+                kk[ax] = l;
+                acc += sbin[kax][l] * hp[c][ax][kax - l] * sc[term_index(kk[0], kk[1], kk[2])];
             }
+            dst[idx] = acc;
         }
-        spart[c * 2 * NT + k] = accM;
-        spart[c * 2 * NT + NT + k] = accD;
+        __syncthreads();
+        T *tmp = src; src = dst; dst = tmp;
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < 2 * NT; k += blockDim.x) {
+    for (int r = threadIdx.x; r < 2 * NT; r += blockDim.x) {
         T acc = 0;
-        for (int c = 0; c < nc; ++c) acc += spart[c * 2 * NT + k];
-        mom[(int64_t)b * 2 * NT + k] = acc;
+        for (int c = 0; c < nc; ++c) acc += src[c * 2 * NT + r];
+        mom[(int64_t)b * 2 * NT + r] = acc;
     }
 }
 
@@ -808,7 +812,7 @@ void launch_m2p_typed(int P, bool yuk, const Pair &Pr, const double *xs, const d
 
 void upload_term_tables() {
     PB_CUDA_TRY(cudaFuncSetAttribute(m2m_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kM2MMaxShared));
-    PB_CUDA_TRY(cudaFuncSetAttribute(m2m_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kM2MMaxShared / 2));
+    PB_CUDA_TRY(cudaFuncSetAttribute(m2m_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kM2MMaxShared));
     int terms[3 * 455];
     int i = 0;
     for (int n = 0; n <= kMaxP; ++n)
@@ -855,7 +859,7 @@ void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s) {
                                                       Tr.origin[0], Tr.origin[1], Tr.origin[2], sv, P, NT, Tr.mom64.p);
     }
     PB_LAUNCH_CHECK();
-    const size_t shm = (size_t)2 * 8 * 2 * NT * (mixed ? sizeof(float) : sizeof(double));
+    const size_t shm = (size_t)2 * 8 * 2 * NT * (mixed ? sizeof(float) : sizeof(double)) + 3 * NT * sizeof(int);
     for (int l = Tr.nlevels - 2; l >= 0; --l) {
         const int b0 = Tr.level_off[l], nb = Tr.level_off[l + 1] - b0;
         if (mixed)
