@@ -87,3 +87,45 @@ def self_single_layer_laplace_exact(verts, tris):
         h, u1, u2 = _edge_params(c, va, vb)
         total += h * (np.arcsinh(u2 / h) - np.arcsinh(u1 / h))
     return total / FOUR_PI
+
+
+def _dF_dkappa(rho, kappa):
+    """d/dkappa of the Yukawa radial integral (1 - exp(-kappa rho)) / kappa.
+
+    Closed form (kappa rho exp(-kappa rho) + expm1(-kappa rho)) / kappa^2; for
+    kappa rho < 0.1 its power series rho^2 sum_{n>=2} (-1)^(n-1) (n-1)/n! (kappa rho)^(n-2),
+    which avoids the cancellation; at kappa = 0 it is -rho^2 / 2.
+    """
+    x = kappa * rho
+    series = np.zeros_like(rho)
+    fact = 1.0
+    for n in range(2, 16):
+        fact *= n
+        series += (-1.0) ** (n - 1) * (n - 1) / fact * x ** (n - 2)
+    series *= rho * rho
+    if kappa == 0.0:
+        return series
+    closed = (x * np.exp(-x) + np.expm1(-x)) / (kappa * kappa)
+    return np.where(x < 0.1, series, closed)
+
+
+def self_single_layer_dkappa(verts, tris, kappa: float, Nk: int = 5):
+    """d V_ii / d kappa of the Yukawa self integral by the same semi-analytical rule.
+
+    The radial integral of dG_Y/dkappa = -exp(-kappa r) / (4 pi) is the kappa
+    derivative of (1 - exp(-kappa rho)) / kappa; the angular integral uses the
+    same N_k-point rule in s = asinh(u / h) as self_single_layer.
+    """
+    c, edges = _edges(verts, tris)
+    xi, wi = gauss_legendre(Nk)
+    total = np.zeros(c.shape[0])
+    for va, vb in edges:
+        h, u1, u2 = _edge_params(c, va, vb)
+        s1 = np.arcsinh(u1 / h)
+        s2 = np.arcsinh(u2 / h)
+        half = 0.5 * (s2 - s1)
+        mid = 0.5 * (s2 + s1)
+        for x, w in zip(xi, wi):
+            ch = np.cosh(mid + half * x)
+            total += w * half * _dF_dkappa(h * ch, kappa) / ch
+    return total / FOUR_PI
