@@ -135,6 +135,43 @@ int pb_reaction_potential(pb_problem *pb, const double *x, double *phi_reac);
  * (the Coulomb term of Eq. total_energy). */
 int pb_coulomb_energy(pb_problem *pb, double *out);
 
+/* Adjoint gradient of the solvation energy (Eq. solv) of the last pb_solve.
+ * With E = c0 q^T Rm x (Rm: the reaction-potential map of Eq.
+ * reac_integral, c0 = C/2 * 4 pi), A x = b = B q, and the adjoint
+ * A^T lambda = c0 Rm^T q solved by GMRES on the transposed treecode operator
+ * (same parameters, tolerance and preconditioner as the forward solve):
+ *   dE/dq_k   = c0 (Rm x)_k + (B^T lambda)_k
+ *   dE/dr_k   = c0 q_k grad(Rm x)_k + q_k lambda^T grad_k B
+ *   dE/dp     = c0 q^T (dRm/dp) x + lambda^T (db/dp - (dA/dp) x),  p = eps_R or kappa_R
+ * for every region R (the paper computes no gradients: this is the adjoint of
+ * its discrete operator).  The kappa derivatives use the kernel derivatives
+ * dG/dkappa and the derivative of the near-singular and semi-analytical
+ * rules; the near/far rule choice is held fixed.  The charged region's
+ * kappa derivative is the one-sided derivative at kappa = 0.
+ * Arrays are caller-owned host buffers (NULL: not wanted): dq [nc], dxyz
+ * [3 nc], deps [n_regions], dkappa [n_regions].  Units: kJ/mol per e, per A,
+ * per unit eps, and kJ/mol * A.  Needs a converged pb_solve since the last
+ * pb_setup (else PB_EINVAL); PB_ENOCONV if the adjoint GMRES reaches
+ * max_iter (the arrays are still written).  dkappa with P > 8 needs
+ * ~14 KB of local memory per device thread. */
+typedef struct {
+    double *dq;
+    double *dxyz;
+    double *deps;
+    double *dkappa;
+    double energy;      /* out: dG_solv of the solution differentiated */
+    double residual;    /* out: relative residual of the adjoint solve */
+    int iterations;     /* out: adjoint GMRES iterations */
+    int matvecs;        /* out: transposed treecode evaluations */
+    double grad_ms;     /* out: device time of the whole gradient (CUDA events) */
+} pb_grad;
+int pb_gradient(pb_problem *pb, pb_grad *g);
+/* y = A^T x for the assembled operator by the transposed treecode (sources at
+ * the collocation points, targets at the Gauss points).  x in row order, y in
+ * unknown order, 2 N doubles each; host or device pointers as in
+ * pb_apply_operator. */
+int pb_apply_transpose(pb_problem *pb, const double *x, double *y, int device_ptrs);
+
 /* Per-phase device time of one operator application (CUDA events on the
  * context stream), averaged over `reps` applications to the given unknown
  * vector x (host, 2 N).  phase_ms[0..5]: source strengths + P2M/M2M, P2P,

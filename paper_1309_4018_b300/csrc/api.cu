@@ -7,9 +7,11 @@
 #include <string>
 #include <vector>
 
+#include "adjoint.cuh"
 #include "geometry.cuh"
 #include "gmres.cuh"
 #include "model.cuh"
+#include "problem.cuh"
 #include "tree.cuh"
 #include "treecode.cuh"
 
@@ -18,57 +20,6 @@ using namespace pb;
 namespace pb {
 std::atomic<long long> g_launches{0};
 }
-
-struct pb_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    std::string err;
-};
-
-namespace {
-
-struct SurfIn {
-    int64_t nv = 0, nt = 0;
-    DevBuf<double> v;      // device copy made when the surface is added
-    DevBuf<int32_t> t;
-    int inner = -1, outer = -1;
-};
-
-// One (pair, kernel) contribution cK * K + cV * V to a row block or to the
-// reaction potential.
-struct Term {
-    int pair, kidx;
-    double cK, cV;
-};
-
-}  // namespace
-
-struct pb_problem {
-    pb_ctx *ctx = nullptr;
-    std::vector<Region> regions;
-    std::vector<SurfIn> sin;
-    std::vector<double> cxyz, cq;
-    int cregion = -1;
-    bool is_setup = false;
-    Params prm;
-    // device data
-    std::vector<SurfDev> S;
-    std::vector<Tree> T;
-    std::vector<Targets> G;               // one per surface, then the charges
-    std::vector<Pair> pairs;              // surface-target pairs
-    std::vector<Pair> cpairs;             // charge-target pairs
-    std::vector<std::vector<Term>> rows;  // per (surface, side)
-    std::vector<Term> reac;
-    std::vector<bool> need_far;           // per tree: some pair uses its moments
-    std::vector<int64_t> off;             // panel offsets
-    int64_t N = 0;
-    DevBuf<double> b, x, y, r, xin, yout, z1, z2, minv;
-    DevBuf<double> cq_d, cxyz_d, phi_reac, energy;
-    Gmres gm;
-    double setup_ms = 0.0;
-    bool have_solution = false;
-};
 
 namespace {
 
@@ -151,6 +102,7 @@ void setup_problem(pb_problem *pb) {
             si.outer >= (int)pb->regions.size() || si.inner == si.outer)
             fail(PB_EINVAL, "surface references an unknown region");
     PB_CUDA_TRY(cudaEventRecord(c->ev0, s));
+    pb->adj.reset();
     upload_rules();
     upload_term_tables();
     pb->S.clear(); pb->T.clear(); pb->G.clear(); pb->pairs.clear(); pb->cpairs.clear();
@@ -192,7 +144,7 @@ void setup_problem(pb_problem *pb) {
                 const double cc = in ? 1.0 : eps(pb->S[t].inner) / eps(R);
                 const int pi = find_pair(pb->pairs, sf, t);
                 const int ki = kernel_slot(pb->pairs[pi], pb->regions[R].kappa);
-                pb->rows[2 * sf + side].push_back(Term{pi, ki, sigma, -sigma * cc});
+                pb->rows[2 * sf + side].push_back(Term{pi, ki, sigma, -sigma * cc, R});
             }
             if (pb->rows[2 * sf + side].size() > 8) fail(PB_EINVAL, "a region is bounded by more than 8 surfaces");
         }
@@ -207,7 +159,7 @@ void setup_problem(pb_problem *pb) {
             const double cc = in ? 1.0 : eps(pb->S[t].inner) / eps(Rc);
             const int pi = find_pair(pb->cpairs, ns, t);
             const int ki = kernel_slot(pb->cpairs[pi], pb->regions[Rc].kappa);
-            pb->reac.push_back(Term{pi, ki, -sigma, sigma * cc});
+            pb->reac.push_back(Term{pi, ki, -sigma, sigma * cc, Rc});
         }
         if (pb->reac.size() > 8) fail(PB_EINVAL, "the charged region is bounded by more than 8 surfaces");
     }
@@ -299,13 +251,12 @@ void setup_problem(pb_problem *pb) {
     pb->have_solution = false;
 }
 
-// Optional event marks between the phases of one operator application.
-struct PhaseEvents {
-    cudaEvent_t ev[6];
-};
+}  // namespace
 
-// y = A x, both device pointers of 2N doubles.
-void apply_operator(pb_problem *pb, const double *xd, double *yd, PhaseEvents *ph = nullptr) {
+namespace pb {
+
+// y = A x, both device pointers of 2N doubles; optional event marks between the phases.
+void apply_operator(pb_problem *pb, const double *xd, double *yd, PhaseEvents *ph) {
     cudaStream_t s = pb->ctx->stream;
     const Params &prm = pb->prm;
     const bool mixed = prm.precision == PB_MIXED;
@@ -393,6 +344,63 @@ void apply_precond(pb_problem *pb, const double *u, double *z) {
     }
 }
 
+KrylovStats run_gmres(pb_problem *pb, const DevOp &op, const DevOp &precond, const double *b, double *x,
+                      bool x_zero) {
+    cudaStream_t s = pb->ctx->stream;
+    const Params &prm = pb->prm;
+    const int64_t n2 = 2 * pb->N;
+    Gmres &gm = pb->gm;
+    KrylovStats st;
+    if (x_zero) PB_CUDA_TRY(cudaMemsetAsync(x, 0, n2 * sizeof(double), s));
+    const double bnorm = norm2_device(b, n2, gm, s);
+    if (bnorm == 0.0) {
+        PB_CUDA_TRY(cudaMemsetAsync(x, 0, n2 * sizeof(double), s));
+        return st;
+    }
+    gm.set_bnorm(bnorm, s);
+    bool zero_x = x_zero;
+    while (true) {
+        if (zero_x) {
+            PB_CUDA_TRY(cudaMemcpyAsync(pb->r.p, b, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        } else {
+            op(x, pb->y.p);
+            ++st.matvecs;
+            axpby(1.0, b, -1.0, pb->y.p, pb->r.p, n2, s);
+        }
+        zero_x = false;
+        const double beta = gm.start_cycle(pb->r.p, s);
+        st.rel = beta / bnorm;
+        if (!(st.rel >= prm.tol) || st.iters >= prm.max_iter) break;
+        int k = 0;
+        for (int j = 0; j < gm.m; ++j) {
+            if (precond) {
+                precond(gm.basis(j), pb->z1.p);
+                op(pb->z1.p, gm.w.p);
+            } else {
+                op(gm.basis(j), gm.w.p);
+            }
+            ++st.matvecs;
+            gm.arnoldi_step(j, s);
+            ++st.iters;
+            k = j + 1;
+            const double est = gm.residual_estimate(s);
+            if (!(est >= prm.tol) || st.iters >= prm.max_iter) break;
+        }
+        if (precond && k > 0) {
+            basis_combination(gm, k, pb->z1.p, s);
+            precond(pb->z1.p, pb->z2.p);
+            axpby(1.0, x, 1.0, pb->z2.p, x, n2, s);
+        } else {
+            gm.update_solution(k, x, s);
+        }
+    }
+    return st;
+}
+
+}  // namespace pb
+
+namespace {
+
 void require_setup(pb_problem *pb) {
     if (!pb->is_setup) fail(PB_ENOTSETUP, "pb_setup has not been called since the last input change");
 }
@@ -403,54 +411,12 @@ void solve(pb_problem *pb, const double *x0, pb_result *out) {
     cudaStream_t s = c->stream;
     const Params &prm = pb->prm;
     const int64_t n2 = 2 * pb->N;
-    Gmres &gm = pb->gm;
     PB_CUDA_TRY(cudaEventRecord(c->ev0, s));
     if (x0) PB_CUDA_TRY(cudaMemcpyAsync(pb->x.p, x0, n2 * sizeof(double), cudaMemcpyHostToDevice, s));
-    else pb->x.zero(s);
-    const double bnorm = norm2_device(pb->b.p, n2, gm, s);
-    int iters = 0, matvecs = 0;
-    double rel = 0.0;
-    bool zero_x = x0 == nullptr;
-    if (bnorm == 0.0) {
-        pb->x.zero(s);
-    } else {
-        gm.set_bnorm(bnorm, s);
-        while (true) {
-            if (zero_x) {
-                PB_CUDA_TRY(cudaMemcpyAsync(pb->r.p, pb->b.p, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-            } else {
-                apply_operator(pb, pb->x.p, pb->y.p);
-                ++matvecs;
-                axpby(1.0, pb->b.p, -1.0, pb->y.p, pb->r.p, n2, s);
-            }
-            zero_x = false;
-            const double beta = gm.start_cycle(pb->r.p, s);
-            rel = beta / bnorm;
-            if (!(rel >= prm.tol) || iters >= prm.max_iter) break;
-            int k = 0;
-            for (int j = 0; j < gm.m; ++j) {
-                if (prm.precond) {
-                    apply_precond(pb, gm.basis(j), pb->z1.p);
-                    apply_operator(pb, pb->z1.p, gm.w.p);
-                } else {
-                    apply_operator(pb, gm.basis(j), gm.w.p);
-                }
-                ++matvecs;
-                gm.arnoldi_step(j, s);
-                ++iters;
-                k = j + 1;
-                const double est = gm.residual_estimate(s);
-                if (!(est >= prm.tol) || iters >= prm.max_iter) break;
-            }
-            if (prm.precond && k > 0) {
-                basis_combination(gm, k, pb->z1.p, s);
-                apply_precond(pb, pb->z1.p, pb->z2.p);
-                axpby(1.0, pb->x.p, 1.0, pb->z2.p, pb->x.p, n2, s);
-            } else {
-                gm.update_solution(k, pb->x.p, s);
-            }
-        }
-    }
+    DevOp op = [pb](const double *u, double *v) { apply_operator(pb, u, v); };
+    DevOp pc;
+    if (prm.precond) pc = [pb](const double *u, double *z) { apply_precond(pb, u, z); };
+    const KrylovStats st = run_gmres(pb, op, pc, pb->b.p, pb->x.p, x0 == nullptr);
     reaction(pb, pb->x.p);
     double dG = 0.0;
     PB_CUDA_TRY(cudaMemcpyAsync(&dG, pb->energy.p, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -459,13 +425,14 @@ void solve(pb_problem *pb, const double *x0, pb_result *out) {
     float ms = 0.f;
     PB_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     pb->have_solution = true;
+    pb->dG = dG;
     if (out) {
         std::memset(out, 0, sizeof(*out));
         out->dG_solv = dG;
-        out->residual = rel;
-        out->iterations = iters;
-        out->converged = rel < prm.tol;
-        out->matvecs = matvecs;
+        out->residual = st.rel;
+        out->iterations = st.iters;
+        out->converged = st.rel < prm.tol;
+        out->matvecs = st.matvecs;
         out->setup_ms = pb->setup_ms;
         out->solve_ms = ms;
         for (auto &P : pb->pairs) {
@@ -475,7 +442,7 @@ void solve(pb_problem *pb, const double *x0, pb_result *out) {
             out->near_excluded += P.near_excl;
         }
     }
-    if (!(rel < prm.tol)) fail(PB_ENOCONV, "GMRES reached max_iter before the tolerance");
+    if (!(st.rel < prm.tol)) fail(PB_ENOCONV, "GMRES reached max_iter before the tolerance");
 }
 
 }  // namespace
@@ -632,6 +599,34 @@ int pb_solve(pb_problem *pb, const double *x0, pb_result *out) {
     return guard(pb->ctx, [&] {
         set_device(pb->ctx);
         solve(pb, x0, out);
+    });
+}
+
+int pb_gradient(pb_problem *pb, pb_grad *g) {
+    if (!pb || !g) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        require_setup(pb);
+        set_device(pb->ctx);
+        energy_gradient(pb, g);
+    });
+}
+
+int pb_apply_transpose(pb_problem *pb, const double *x, double *y, int device_ptrs) {
+    if (!pb || !x || !y) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        require_setup(pb);
+        set_device(pb->ctx);
+        cudaStream_t s = pb->ctx->stream;
+        const int64_t n2 = 2 * pb->N;
+        if (device_ptrs) {
+            apply_transpose(pb, x, y);
+        } else {
+            pb->xin.upload(x, n2, s);
+            pb->yout.alloc(n2);
+            apply_transpose(pb, pb->xin.p, pb->yout.p);
+            pb->yout.download(y, n2, s);
+        }
+        PB_CUDA_TRY(cudaStreamSynchronize(s));
     });
 }
 

@@ -7,18 +7,8 @@
 
 namespace pb {
 
-namespace {
-
 // Symmetric triangle rules (Dunavant 1985): barycentric nodes and weights
 // (weights sum to 1).  Regular rules K = 1, 3, 7; near-singular rules 7, 19.
-struct TriRule {
-    int n;
-    double l[19][3];
-    double w[19];
-};
-
-__constant__ TriRule c_rules[4];  // 1, 3, 7, 19 points
-
 TriRule make_rule(int K) {
     TriRule r{};
     r.n = 0;
@@ -52,6 +42,11 @@ TriRule make_rule(int K) {
 }
 
 int rule_slot(int K) { return K == 1 ? 0 : K == 3 ? 1 : K == 7 ? 2 : 3; }
+
+namespace {
+
+__constant__ TriRule c_rules[4];  // 1, 3, 7, 19 points
+
 
 __global__ void panel_geom_kernel(int64_t n, const double *__restrict__ v, const int32_t *__restrict__ t,
                                   double *__restrict__ cen, double *__restrict__ nrm, double *__restrict__ area,
@@ -240,6 +235,56 @@ __global__ void self_integral_kernel(int64_t n, const double *__restrict__ v, co
     out[i] = total * kInv4Pi;
 }
 
+// d V_ii / d kappa by the same rule: the radial integral of -exp(-kappa r) r dr
+// is the kappa derivative of F(rho) = (1 - exp(-kappa rho)) / kappa,
+// (kappa rho exp(-kappa rho) + expm1(-kappa rho)) / kappa^2, taken from its
+// power series rho^2 sum_{n>=2} (-1)^(n-1) (n-1)/n! (kappa rho)^(n-2) when
+// kappa rho < 0.1 (no cancellation; -rho^2/2 at kappa = 0).
+__device__ double dF_dkappa(double rho, double kappa) {
+    const double x = kappa * rho;
+    if (x < 0.1) {
+        double sum = 0.0, fact = 1.0, xp = 1.0;
+        for (int n = 2; n < 16; ++n) {
+            fact *= n;
+            sum += ((n & 1) ? 1.0 : -1.0) * (n - 1) / fact * xp;
+            xp *= x;
+        }
+        return rho * rho * sum;
+    }
+    return (x * exp(-x) + expm1(-x)) / (kappa * kappa);
+}
+
+__global__ void self_dkappa_kernel(int64_t n, const double *__restrict__ v, const int32_t *__restrict__ t,
+                                   const double *__restrict__ cen, GL gl, double kappa, double *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int idx[3] = {t[3 * i], t[3 * i + 1], t[3 * i + 2]};
+    const double c[3] = {cen[3 * i], cen[3 * i + 1], cen[3 * i + 2]};
+    double total = 0.0;
+    for (int e = 0; e < 3; ++e) {
+        const double *va = v + 3 * idx[e];
+        const double *vb = v + 3 * idx[(e + 1) % 3];
+        double d[3], len2 = 0.0;
+        for (int k = 0; k < 3; ++k) { d[k] = vb[k] - va[k]; len2 += d[k] * d[k]; }
+        const double len = sqrt(len2);
+        double s0 = 0.0;
+        for (int k = 0; k < 3; ++k) { d[k] /= len; s0 += (c[k] - va[k]) * d[k]; }
+        double h2 = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            const double f = c[k] - (va[k] + s0 * d[k]);
+            h2 += f * f;
+        }
+        const double h = sqrt(h2);
+        const double s1 = asinh(-s0 / h), s2 = asinh((len - s0) / h);
+        const double half = 0.5 * (s2 - s1), mid = 0.5 * (s2 + s1);
+        for (int q = 0; q < gl.n; ++q) {
+            const double ch = cosh(mid + half * gl.x[q]);
+            total += gl.w[q] * half * dF_dkappa(h * ch, kappa) / ch;
+        }
+    }
+    out[i] = total * kInv4Pi;
+}
+
 __global__ void rhs_kernel(int64_t n, const double *__restrict__ cen, int64_t nc, const double *__restrict__ q,
                            const double *__restrict__ xyz, double kappa, double eps, double *__restrict__ b) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -376,6 +421,13 @@ void self_integrals(const SurfDev &S, int N_k, double kappa, double *out, cudaSt
     if (N_k < 1 || N_k > 32) fail(PB_EINVAL, "N_k must be in 1..32");
     GL gl = gauss_legendre(N_k);
     self_integral_kernel<<<div_up(S.n, 128), 128, 0, s>>>(S.n, S.verts.p, S.tris.p, S.cen.p, gl, kappa, out);
+    PB_LAUNCH_CHECK();
+}
+
+void self_integrals_dkappa(const SurfDev &S, int N_k, double kappa, double *out, cudaStream_t s) {
+    if (N_k < 1 || N_k > 32) fail(PB_EINVAL, "N_k must be in 1..32");
+    GL gl = gauss_legendre(N_k);
+    self_dkappa_kernel<<<div_up(S.n, 128), 128, 0, s>>>(S.n, S.verts.p, S.tris.p, S.cen.p, gl, kappa, out);
     PB_LAUNCH_CHECK();
 }
 

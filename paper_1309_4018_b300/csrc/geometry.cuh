@@ -5,6 +5,15 @@
 
 namespace pb {
 
+// Symmetric triangle rule: barycentric nodes and weights (weights sum to 1).
+struct TriRule {
+    int n;
+    double l[19][3];
+    double w[19];
+};
+TriRule make_rule(int K);   // K = 1, 3, 7, 19
+int rule_slot(int K);       // index of rule K in a table {1, 3, 7, 19}
+
 void upload_rules();
 bool valid_rule(int K);
 // Centroids, unit normals, areas, L = sqrt(2A), and the K Gauss points of every panel.
@@ -17,6 +26,8 @@ void near_values32(const Pair &Pr, const Targets &G, const SurfDev &src, int K, 
                    float *dK, cudaStream_t s);
 // Semi-analytical V_ii of every panel of S (input order).
 void self_integrals(const SurfDev &S, int N_k, double kappa, double *out, cudaStream_t s);
+// Its kappa derivative by the same rule.
+void self_integrals_dkappa(const SurfDev &S, int N_k, double kappa, double *out, cudaStream_t s);
 // b_i = sum_k q_k G(c_i, r_k) / eps for the panels of S (input order); FP64,
 // or FP32 with compensated tile sums relative to `origin` when it is not null.
 void rhs_rows(const SurfDev &S, int64_t nc, const double *q, const double *xyz, double kappa, double eps, double *b,

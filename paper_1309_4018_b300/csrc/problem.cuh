@@ -1,0 +1,90 @@
+// Host-side state of a context and of one problem (shared by the C-ABI in
+// api.cu and the adjoint in adjoint.cu).
+#pragma once
+
+#include <functional>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "gmres.cuh"
+#include "model.cuh"
+
+struct pb_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::string err;
+};
+
+namespace pb {
+
+struct SurfIn {
+    int64_t nv = 0, nt = 0;
+    DevBuf<double> v;      // device copy made when the surface is added
+    DevBuf<int32_t> t;
+    int inner = -1, outer = -1;
+};
+
+// One (pair, kernel) contribution cK * K + cV * V of region `region` to a row
+// block or to the reaction potential.
+struct Term {
+    int pair, kidx;
+    double cK, cV;
+    int region;
+};
+
+struct AdjointState;   // adjoint.cuh
+
+}  // namespace pb
+
+struct pb_problem {
+    pb_ctx *ctx = nullptr;
+    std::vector<pb::Region> regions;
+    std::vector<pb::SurfIn> sin;
+    std::vector<double> cxyz, cq;
+    int cregion = -1;
+    bool is_setup = false;
+    pb::Params prm;
+    // device data
+    std::vector<pb::SurfDev> S;
+    std::vector<pb::Tree> T;
+    std::vector<pb::Targets> G;               // one per surface, then the charges
+    std::vector<pb::Pair> pairs;              // surface-target pairs
+    std::vector<pb::Pair> cpairs;             // charge-target pairs
+    std::vector<std::vector<pb::Term>> rows;  // per (surface, side)
+    std::vector<pb::Term> reac;
+    std::vector<bool> need_far;               // per tree: some pair uses its moments
+    std::vector<int64_t> off;                 // panel offsets
+    int64_t N = 0;
+    pb::DevBuf<double> b, x, y, r, xin, yout, z1, z2, minv;
+    pb::DevBuf<double> cq_d, cxyz_d, phi_reac, energy;
+    pb::Gmres gm;
+    double setup_ms = 0.0;
+    bool have_solution = false;
+    double dG = 0.0;                          // energy of the last solve
+    std::shared_ptr<pb::AdjointState> adj;   // built by the first gradient after setup
+};
+
+namespace pb {
+
+// Operator, preconditioner and reaction potential of a set-up problem (api.cu).
+struct PhaseEvents {
+    cudaEvent_t ev[6];
+};
+void apply_operator(pb_problem *pb, const double *xd, double *yd, PhaseEvents *ph = nullptr);
+void apply_precond(pb_problem *pb, const double *u, double *z);
+void reaction(pb_problem *pb, const double *xd);
+
+// Restarted, right-preconditioned GMRES on the problem's Krylov state (scratch
+// vectors r, y, z1, z2 of the problem): solves op(x) = b for the 2N-vector x
+// (device), starting from x (x_zero: from 0).  precond may be empty.
+struct KrylovStats {
+    int iters = 0, matvecs = 0;
+    double rel = 0.0;
+};
+using DevOp = std::function<void(const double *, double *)>;
+KrylovStats run_gmres(pb_problem *pb, const DevOp &op, const DevOp &precond, const double *b, double *x,
+                      bool x_zero);
+
+}  // namespace pb

@@ -190,21 +190,22 @@ __global__ void gather_sources_kernel(int64_t n, int K, const int32_t *__restric
     if (q >= n) return;
     const int p = perm[q];
     const double x = gy[3 * p], y = gy[3 * p + 1], z = gy[3 * p + 2];
+    const double w = gwa ? gwa[p] : 1.0;
     ys[3 * q] = x; ys[3 * q + 1] = y; ys[3 * q + 2] = z;
-    was[q] = gwa[p];
+    was[q] = w;
     pids[q] = p / K;
-    pos32[q] = make_float4((float)(x - ox), (float)(y - oy), (float)(z - oz), (float)gwa[p]);
+    pos32[q] = make_float4((float)(x - ox), (float)(y - oy), (float)(z - oz), (float)w);
 }
 
 __global__ void gather_targets_kernel(int64_t n, const int32_t *__restrict__ order, const double *__restrict__ x,
                                       double *__restrict__ xs, int32_t *__restrict__ selfp, int32_t *__restrict__ rank,
-                                      int has_self) {
+                                      int self_div) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     const int i = order[q];
     rank[i] = (int32_t)q;
     xs[3 * q] = x[3 * i]; xs[3 * q + 1] = x[3 * i + 1]; xs[3 * q + 2] = x[3 * i + 2];
-    selfp[q] = has_self ? i : -1;
+    selfp[q] = self_div > 0 ? i / self_div : -1;
 }
 
 // ---------------------------------------------------------------- traversal (Eq. MAC)
@@ -553,9 +554,12 @@ void morton_sort(const double *d_points, int64_t n, cudaStream_t s, double corne
 }
 
 void build_tree(Tree &T, const SurfDev &S, int K, int ncrit, cudaStream_t s) {
-    const int64_t n = S.n * K;
+    build_tree_points(T, S.gy.p, S.gwa.p, S.n * K, K, ncrit, s);
+}
+
+void build_tree_points(Tree &T, const double *pts, const double *wts, int64_t n, int K, int ncrit, cudaStream_t s) {
     T.npts = n;
-    morton_sort(S.gy.p, n, s, T.corner, T.side, T.keys, T.perm);
+    morton_sort(pts, n, s, T.corner, T.side, T.keys, T.perm);
     for (int a = 0; a < 3; ++a) T.origin[a] = T.corner[a] + 0.5 * T.side;
     // level-by-level splitting; capacity bound: every level holds disjoint nodes
     const int64_t maxn = std::min<int64_t>((int64_t)1 + 8LL * (kMaxLevel + 1) * (n / std::max(1, ncrit) + 1),
@@ -623,13 +627,13 @@ void build_tree(Tree &T, const SurfDev &S, int K, int ncrit, cudaStream_t s) {
     PB_LAUNCH_CHECK();
     // sorted source geometry
     T.ys.alloc(3 * n); T.was.alloc(n); T.pids.alloc(n); T.pos32.alloc(n);
-    gather_sources_kernel<<<div_up(n, 256), 256, 0, s>>>(n, K, T.perm.p, S.gy.p, S.gwa.p, T.origin[0], T.origin[1],
+    gather_sources_kernel<<<div_up(n, 256), 256, 0, s>>>(n, K, T.perm.p, pts, wts, T.origin[0], T.origin[1],
                                                          T.origin[2], T.ys.p, T.was.p, T.pids.p, T.pos32.p);
     PB_LAUNCH_CHECK();
     T.src64.alloc(8 * n); T.srcA32.alloc(n); T.srcB32.alloc(n);
 }
 
-void build_targets(Targets &G, const double *d_x, int64_t n, int surface, cudaStream_t s) {
+void build_targets(Targets &G, const double *d_x, int64_t n, int surface, cudaStream_t s, int points_per_panel) {
     G.n = n;
     G.surface = surface;
     double corner[3], side;
@@ -640,7 +644,7 @@ void build_targets(Targets &G, const double *d_x, int64_t n, int surface, cudaSt
     G.rank.alloc(n);
     if (n) {
         gather_targets_kernel<<<div_up(n, 256), 256, 0, s>>>(n, G.order.p, d_x, G.xs.p, G.self_panel.p, G.rank.p,
-                                                             surface >= 0);
+                                                             surface >= 0 ? points_per_panel : 0);
         PB_LAUNCH_CHECK();
     }
     PB_CUDA_TRY(cudaStreamSynchronize(s));
@@ -648,6 +652,11 @@ void build_targets(Targets &G, const double *d_x, int64_t n, int surface, cudaSt
 
 void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
                  cudaStream_t s) {
+    build_far_lists(Pr, G, T, prm, s);
+    build_near_lists(Pr, G, T, src, prm, use_self, s);
+}
+
+void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &prm, cudaStream_t s) {
     const int64_t m = G.n;
     TmpBuf<int32_t> mc(m, s), pc(m, s), err(1, s);
     PB_CUDA_TRY(cudaMemsetAsync(err.p, 0, 4, s));
@@ -692,12 +701,6 @@ void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, 
         PB_CUDA_TRY(cudaStreamSynchronize(s));
         Pr.p2p_pairs = (int64_t)h;
     }
-    // P2P leaf indices per target (ascending = pre-order)
-    TmpBuf<int32_t> pleaf(std::max<int64_t>(1, Pr.n_p2p), s);
-    if (Pr.n_p2p) {
-        node_to_leaf_kernel<<<div_up(Pr.n_p2p, 256), 256, 0, s>>>(Pr.n_p2p, Pr.p2p_node.p, T.node_leaf.p, pleaf.p);
-        PB_LAUNCH_CHECK();
-    }
     // entry-major grouping of the lists
     auto group = [&](const int64_t *ptr, const int32_t *ent, const int32_t *remap, int nkeys, int64_t nent,
                      DevBuf<int32_t> &inv, DevBuf<int32_t> &pos, DevBuf<int4> &items, int64_t &nitems) {
@@ -731,6 +734,17 @@ void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, 
           Pr.n_p2p_items);
     group(Pr.m2p_ptr.p, Pr.m2p_node.p, nullptr, T.nnodes, Pr.n_m2p, Pr.m2p_inv, Pr.m2p_pos, Pr.m2p_items,
           Pr.n_m2p_items);
+}
+
+void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
+                      cudaStream_t s) {
+    const int64_t m = G.n;
+    // P2P leaf indices per target (ascending = pre-order)
+    TmpBuf<int32_t> pleaf(std::max<int64_t>(1, Pr.n_p2p), s);
+    if (Pr.n_p2p) {
+        node_to_leaf_kernel<<<div_up(Pr.n_p2p, 256), 256, 0, s>>>(Pr.n_p2p, Pr.p2p_node.p, T.node_leaf.p, pleaf.p);
+        PB_LAUNCH_CHECK();
+    }
     // near-singular lists
     TmpBuf<int32_t> nc(m, s), ex(m, s), se(m, s);
     TmpBuf<unsigned long long> reach_d(1, s);

@@ -30,7 +30,7 @@ namespace pb {
 
 namespace {
 
-__constant__ int c_terms[3 * 455];   // (k1, k2, k3) of every term, graded order
+__constant__ int c_terms[3 * kMaxTerms1];   // (k1, k2, k3) of every term up to order kMaxP + 1, graded order
 __constant__ double c_binom[13][13];
 
 __host__ __device__ constexpr int term_index(int k1, int k2, int k3) {
@@ -172,11 +172,13 @@ __global__ void __launch_bounds__(128) p2m_kernel(int nleaves, const int32_t *__
 // ids) are shifted in parallel in shared memory and added in child order.
 constexpr int kM2MMaxShared = 2 * 8 * 2 * 455 * 8 + 3 * 455 * 4;
 
+// Each node holds `stride` values; one launch shifts the 2 NT values at
+// offset `base` (one (M, D) or two monopole sets).
 template <typename T>
 __global__ void __launch_bounds__(256) m2m_kernel(int nodes_begin, const int32_t *__restrict__ first_child,
                                                   const int32_t *__restrict__ nchild,
-                                                  const double *__restrict__ centre, int P, int NT,
-                                                  T *__restrict__ mom) {
+                                                  const double *__restrict__ centre, int P, int NT, int stride,
+                                                  int base, T *__restrict__ mom) {
     extern __shared__ __align__(16) unsigned char m2m_smem[];
     T *buf0 = reinterpret_cast<T *>(m2m_smem);          // nc x 2NT
     T *buf1 = buf0 + 8 * 2 * NT;                        // nc x 2NT
@@ -187,7 +189,10 @@ __global__ void __launch_bounds__(256) m2m_kernel(int nodes_begin, const int32_t
     const int nc = nchild[b];
     if (nc == 0) return;
     const int fc = first_child[b];
-    for (int i = threadIdx.x; i < nc * 2 * NT; i += blockDim.x) buf0[i] = mom[(int64_t)fc * 2 * NT + i];
+    for (int i = threadIdx.x; i < nc * 2 * NT; i += blockDim.x) {
+        const int c = i / (2 * NT), r = i - c * 2 * NT;
+        buf0[i] = mom[(int64_t)(fc + c) * stride + base + r];
+    }
     for (int i = threadIdx.x; i < 3 * NT; i += blockDim.x) sterm[i] = c_terms[i];
     for (int i = threadIdx.x; i < nc * 3; i += blockDim.x) {
         const int c = i / 3, ax = i - 3 * c;
@@ -221,7 +226,7 @@ __global__ void __launch_bounds__(256) m2m_kernel(int nodes_begin, const int32_t
     for (int r = threadIdx.x; r < 2 * NT; r += blockDim.x) {
         T acc = 0;
         for (int c = 0; c < nc; ++c) acc += src[c * 2 * NT + r];
-        mom[(int64_t)b * 2 * NT + r] = acc;
+        mom[(int64_t)b * stride + base + r] = acc;
     }
 }
 
@@ -343,7 +348,7 @@ __global__ void __launch_bounds__(128) p2p64_kernel(int64_t nitems, const int4 *
                                                     const int64_t *__restrict__ start, const int64_t *__restrict__ count,
                                                     const double *__restrict__ src, double kap0, double kap1,
                                                     double *__restrict__ part) {
-    __shared__ double4 sA[4][32], sB[4][32];
+    __shared__ dvec4 sA[4][32], sB[4][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * 4 + warp;
     if (item >= nitems) return;
@@ -358,7 +363,7 @@ __global__ void __launch_bounds__(128) p2p64_kernel(int64_t nitems, const int4 *
         if (use_self) me = selfp[t];
     }
     double acc[4] = {0, 0, 0, 0};
-    const double4 *src4 = reinterpret_cast<const double4 *>(src);
+    const dvec4 *src4 = reinterpret_cast<const dvec4 *>(src);
     const int node = leaf_node[it.x];
     const int64_t s0 = start[node];
     const int cnt = (int)count[node];
@@ -371,8 +376,8 @@ __global__ void __launch_bounds__(128) p2p64_kernel(int64_t nitems, const int4 *
         __syncwarp();
         if (valid) {
             for (int j = 0; j < m; ++j) {
-                const double4 a = sA[warp][j];
-                const double4 b = sB[warp][j];
+                const dvec4 a = sA[warp][j];
+                const dvec4 b = sB[warp][j];
                 if ((int)b.w == me) continue;
                 const double dx = tx - a.x, dy = ty - a.y, dz = tz - a.z;
                 const double r2 = dx * dx + dy * dy + dz * dz;
@@ -813,9 +818,9 @@ void launch_m2p_typed(int P, bool yuk, const Pair &Pr, const double *xs, const d
 void upload_term_tables() {
     PB_CUDA_TRY(cudaFuncSetAttribute(m2m_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kM2MMaxShared));
     PB_CUDA_TRY(cudaFuncSetAttribute(m2m_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kM2MMaxShared));
-    int terms[3 * 455];
+    int terms[3 * kMaxTerms1];
     int i = 0;
-    for (int n = 0; n <= kMaxP; ++n)
+    for (int n = 0; n <= kMaxP + 1; ++n)
         for (int k1 = n; k1 >= 0; --k1)
             for (int k2 = n - k1; k2 >= 0; --k2) {
                 const int k3 = n - k1 - k2;
@@ -859,14 +864,20 @@ void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s) {
                                                       Tr.origin[0], Tr.origin[1], Tr.origin[2], sv, P, NT, Tr.mom64.p);
     }
     PB_LAUNCH_CHECK();
+    m2m_pass(Tr, P, mixed, mixed ? (void *)Tr.mom32.p : (void *)Tr.mom64.p, 2 * NT, 0, s);
+}
+
+void m2m_pass(const Tree &Tr, int P, bool mixed, void *mom, int stride, int base, cudaStream_t s) {
+    const int NT = nterms(P);
     const size_t shm = (size_t)2 * 8 * 2 * NT * (mixed ? sizeof(float) : sizeof(double)) + 3 * NT * sizeof(int);
     for (int l = Tr.nlevels - 2; l >= 0; --l) {
         const int b0 = Tr.level_off[l], nb = Tr.level_off[l + 1] - b0;
         if (mixed)
-            m2m_kernel<float><<<nb, 256, shm, s>>>(b0, Tr.first_child.p, Tr.nchild.p, Tr.centre.p, P, NT, Tr.mom32.p);
+            m2m_kernel<float><<<nb, 256, shm, s>>>(b0, Tr.first_child.p, Tr.nchild.p, Tr.centre.p, P, NT, stride, base,
+                                                   (float *)mom);
         else
-            m2m_kernel<double><<<nb, 256, shm, s>>>(b0, Tr.first_child.p, Tr.nchild.p, Tr.centre.p, P, NT,
-                                                    Tr.mom64.p);
+            m2m_kernel<double><<<nb, 256, shm, s>>>(b0, Tr.first_child.p, Tr.nchild.p, Tr.centre.p, P, NT, stride,
+                                                    base, (double *)mom);
         PB_LAUNCH_CHECK();
     }
 }

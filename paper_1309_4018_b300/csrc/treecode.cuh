@@ -21,6 +21,9 @@ void upload_term_tables();
 void compute_strengths(Tree &Tr, const SurfDev &S, const double *phi, const double *dphi, bool mixed, cudaStream_t s);
 // P2M at the leaves, then M2M level by level to the root.
 void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s);
+// M2M level by level over moments `mom` (float if mixed, else double) holding
+// `stride` values per node; shifts the 2 nterms(P) values at offset `base`.
+void m2m_pass(const Tree &Tr, int P, bool mixed, void *mom, int stride, int base, cudaStream_t s);
 // Direct-sum partials of every (target, leaf) list entry.
 void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self, bool mixed, cudaStream_t s);
 // Far-field partials of every (target, box) list entry and kernel.

@@ -42,6 +42,12 @@ class pb_result(ctypes.Structure):
                 ("near_pairs", ctypes.c_int64), ("near_excluded", ctypes.c_int64)]
 
 
+class pb_grad(ctypes.Structure):
+    _fields_ = [("dq", ctypes.c_void_p), ("dxyz", ctypes.c_void_p), ("deps", ctypes.c_void_p),
+                ("dkappa", ctypes.c_void_p), ("energy", ctypes.c_double), ("residual", ctypes.c_double),
+                ("iterations", ctypes.c_int), ("matvecs", ctypes.c_int), ("grad_ms", ctypes.c_double)]
+
+
 class pb_tree_info(ctypes.Structure):
     _fields_ = [("n_points", ctypes.c_int64), ("n_nodes", ctypes.c_int32), ("n_leaves", ctypes.c_int32),
                 ("corner", ctypes.c_double * 3), ("side", ctypes.c_double)]
@@ -67,6 +73,8 @@ _SIGS = {
     "pb_rhs": ([_vp, _vp], _int),
     "pb_solve": ([_vp, _vp, ctypes.POINTER(pb_result)], _int),
     "pb_get_solution": ([_vp, _vp], _int),
+    "pb_gradient": ([_vp, ctypes.POINTER(pb_grad)], _int),
+    "pb_apply_transpose": ([_vp, _vp, _vp, _int], _int),
     "pb_reaction_potential": ([_vp, _vp, _vp], _int),
     "pb_coulomb_energy": ([_vp, ctypes.POINTER(_dbl)], _int),
     "pb_profile_operator": ([_vp, _vp, _int, _vp], _int),
@@ -175,6 +183,7 @@ class Problem:
         ctx.check(_lib.pb_problem_create(ctx.handle, ctypes.byref(h)))
         self._h = h
         self.n_charges = 0
+        self.n_regions = 0
 
     @classmethod
     def from_dict(cls, ctx: Context, d: dict) -> "Problem":
@@ -192,6 +201,7 @@ class Problem:
     def add_region(self, eps, kappa) -> int:
         rid = _int()
         self.ctx.check(_lib.pb_add_region(self._h, float(eps), float(kappa), ctypes.byref(rid)))
+        self.n_regions = rid.value + 1
         return rid.value
 
     def add_surface(self, verts, tris, inner, outer) -> int:
@@ -227,6 +237,32 @@ class Problem:
         y = np.empty_like(xx)
         self.ctx.check(_lib.pb_apply_operator(self._h, _ptr(xx), _ptr(y), 0))
         return y
+
+    def apply_transpose(self, x):
+        """y = A^T x by the transposed treecode.  x: numpy array (host) or a CUDA torch tensor."""
+        if hasattr(x, "data_ptr"):
+            import torch
+            y = torch.empty_like(x)
+            self.ctx.check(_lib.pb_apply_transpose(self._h, _vp(x.data_ptr()), _vp(y.data_ptr()), 1))
+            return y
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.empty_like(xx)
+        self.ctx.check(_lib.pb_apply_transpose(self._h, _ptr(xx), _ptr(y), 0))
+        return y
+
+    def gradient(self, check=True) -> dict:
+        """Adjoint gradient of the last solve's energy: dq, dxyz, deps, dkappa (per region) and stats."""
+        g = pb_grad()
+        out = dict(dq=np.empty(self.n_charges), dxyz=np.empty((self.n_charges, 3)),
+                   deps=np.empty(self.n_regions), dkappa=np.empty(self.n_regions))
+        g.dq, g.dxyz = out["dq"].ctypes.data, out["dxyz"].ctypes.data
+        g.deps, g.dkappa = out["deps"].ctypes.data, out["dkappa"].ctypes.data
+        rc = _lib.pb_gradient(self._h, ctypes.byref(g))
+        if check or rc not in (PB_OK, PB_ENOCONV):
+            self.ctx.check(rc)
+        out.update(energy=g.energy, residual=g.residual, iterations=g.iterations, matvecs=g.matvecs,
+                   grad_ms=g.grad_ms)
+        return out
 
     def apply_device(self, x_ptr: int, y_ptr: int):
         """y = A x on raw device pointers (2 N doubles each)."""
@@ -306,3 +342,45 @@ class Problem:
 
     def __del__(self):
         self.close()
+
+
+def _energy_autograd():
+    import torch
+
+    class Energy(torch.autograd.Function):
+        """Solvation energy (kJ/mol) as a differentiable function of (q, xyz, eps, kappa).
+
+        forward(problem_dict, q [nc], xyz [nc,3], eps [n_regions], kappa [n_regions], ctx=None, **params)
+        builds the problem with these values, sets it up, solves it and keeps the
+        adjoint gradient (pb_gradient) for backward.  The mesh is held fixed.
+        """
+
+        @staticmethod
+        def forward(fctx, problem, q, xyz, eps, kappa, context=None, params=None):
+            d = dict(problem)
+            d["regions"] = [{"eps": float(e), "kappa": float(k)}
+                            for e, k in zip(eps.detach().cpu().tolist(), kappa.detach().cpu().tolist())]
+            d["charges"] = dict(problem["charges"], q=q.detach().cpu().double().numpy(),
+                                xyz=xyz.detach().cpu().double().numpy())
+            c = context or Context(0)
+            pb = Problem.from_dict(c, d)
+            pb.setup(**(params or {}))
+            r = pb.solve()
+            g = pb.gradient()
+            pb.close()
+            fctx.save_for_backward(*[torch.as_tensor(g[k], dtype=q.dtype, device=q.device)
+                                     for k in ("dq", "dxyz", "deps", "dkappa")])
+            return torch.as_tensor(r.dG_solv, dtype=q.dtype, device=q.device)
+
+        @staticmethod
+        def backward(fctx, gout):
+            dq, dxyz, deps, dkap = fctx.saved_tensors
+            return None, gout * dq, gout * dxyz, gout * deps, gout * dkap, None, None
+
+    return Energy
+
+
+def __getattr__(name):
+    if name == "Energy":
+        return _energy_autograd()
+    raise AttributeError(name)
