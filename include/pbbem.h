@@ -126,6 +126,17 @@ int pb_rhs(pb_problem *pb, double *b);
 /* Solve A x = b by restarted GMRES on the device, then dG (Eqs. reac_integral, solv).
  * x0: optional initial guess (2 N host doubles) or NULL for zero. */
 int pb_solve(pb_problem *pb, const double *x0, pb_result *out);
+/* Solve n set-up problems of this context together (the binding triplet, a
+ * fleet of ligands): every problem runs its own GMRES on one of up to 8 pool
+ * streams, all advancing in lock step with one host synchronisation per
+ * iteration round, so small problems overlap on the GPU.  The call is ordered
+ * on the context stream.  out: n results (may be NULL).  PB_ENOCONV if any
+ * problem reached max_iter (every result is still written). */
+int pb_solve_batch(pb_ctx *ctx, pb_problem *const *probs, int n, pb_result *out);
+/* Binding energy (Eq. bind_energy): solves complex, receptor and ligand as one
+ * batch and returns ddG = E_cx - E_rec - E_lig with E = dG_solv + the Coulomb
+ * energy of the molecule's charges (Eq. total_energy), kJ/mol. */
+int pb_binding_energy(pb_ctx *ctx, pb_problem *cx, pb_problem *rec, pb_problem *lig, double *ddG);
 /* The solution of the last pb_solve (2 N host doubles). */
 int pb_get_solution(pb_problem *pb, double *x);
 /* Reaction potential at the charges (Eq. reac_integral) for a given unknown

@@ -975,7 +975,7 @@ const Pair &forward_of(const pb_problem *pb, const TPair &tp) {
 }
 
 void init_tpair(pb_problem *pb, AdjointState &A, TPair &tp, const Tree &Tr) {
-    cudaStream_t s = pb->ctx->stream;
+    cudaStream_t s = pb->stream;
     const Params &prm = pb->prm;
     const bool mixed = prm.precision == PB_MIXED;
     const Targets &G = A.GP[tp.tgt];
@@ -1030,7 +1030,7 @@ void init_tpair(pb_problem *pb, AdjointState &A, TPair &tp, const Tree &Tr) {
 }
 
 void prepare_adjoint(pb_problem *pb) {
-    cudaStream_t s = pb->ctx->stream;
+    cudaStream_t s = pb->stream;
     const Params &prm = pb->prm;
     const int ns = (int)pb->S.size();
     const int64_t nc = (int64_t)pb->cq.size();
@@ -1174,7 +1174,7 @@ void launch_m2pT_typed(int P, bool yuk, const TPair &tp, const Targets &G, const
 // terms of every row (the operator itself; not for the charge pairs).
 void apply_tpairs(pb_problem *pb, std::vector<TPair> &list, const double *u, double *out, bool half) {
     AdjointState &A = *pb->adj;
-    cudaStream_t s = pb->ctx->stream;
+    cudaStream_t s = pb->stream;
     const Params &prm = pb->prm;
     const bool mixed = prm.precision == PB_MIXED;
     const int ns = (int)pb->S.size();
@@ -1271,7 +1271,7 @@ void apply_tpairs(pb_problem *pb, std::vector<TPair> &list, const double *u, dou
 }
 
 void apply_precond_T(pb_problem *pb, const double *u, double *z) {
-    cudaStream_t s = pb->ctx->stream;
+    cudaStream_t s = pb->stream;
     AdjointState &A = *pb->adj;
     for (size_t sf = 0; sf < pb->S.size(); ++sf) {
         const int64_t n = pb->S[sf].n, o = 2 * pb->off[sf];
@@ -1337,8 +1337,7 @@ void apply_transpose(pb_problem *pb, const double *lam, double *out) {
 }
 
 void energy_gradient(pb_problem *pb, pb_grad *out) {
-    pb_ctx *c = pb->ctx;
-    cudaStream_t s = c->stream;
+    cudaStream_t s = pb->stream;
     const Params &prm = pb->prm;
     const int ns = (int)pb->S.size();
     const int64_t nc = (int64_t)pb->cq.size();
@@ -1346,7 +1345,7 @@ void energy_gradient(pb_problem *pb, pb_grad *out) {
     const int Rc = pb->cregion;
     if (!pb->have_solution) fail(PB_EINVAL, "pb_gradient needs a pb_solve since the last pb_setup");
     if (nc == 0) fail(PB_EINVAL, "pb_gradient needs charges");
-    PB_CUDA_TRY(cudaEventRecord(c->ev0, s));
+    PB_CUDA_TRY(cudaEventRecord(pb->ev0, s));
     if (!pb->adj) prepare_adjoint(pb);
     AdjointState &A = *pb->adj;
     const double *x = pb->x.p;
@@ -1475,10 +1474,10 @@ void energy_gradient(pb_problem *pb, pb_grad *out) {
     if (out->dxyz) A.dxyz_d.download(out->dxyz, 3 * nc, s);
     double energy = 0.0;
     PB_CUDA_TRY(cudaMemcpyAsync(&energy, pb->energy.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-    PB_CUDA_TRY(cudaEventRecord(c->ev1, s));
-    PB_CUDA_TRY(cudaEventSynchronize(c->ev1));
+    PB_CUDA_TRY(cudaEventRecord(pb->ev1, s));
+    PB_CUDA_TRY(cudaEventSynchronize(pb->ev1));
     float ms = 0.f;
-    PB_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    PB_CUDA_TRY(cudaEventElapsedTime(&ms, pb->ev0, pb->ev1));
     if (out->deps) std::copy(gh.begin(), gh.begin() + nreg, out->deps);
     if (out->dkappa) std::copy(gh.begin() + nreg, gh.end(), out->dkappa);
     out->energy = energy;

@@ -21,6 +21,12 @@ namespace pb {
 std::atomic<long long> g_launches{0};
 }
 
+pb_problem::~pb_problem() {
+    if (mv_exec) cudaGraphExecDestroy(mv_exec);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+}
+
 namespace {
 
 int fail_ctx(pb_ctx *c, const Error &e) {
@@ -92,8 +98,7 @@ int kernel_slot(Pair &p, double kappa) {
 }
 
 void setup_problem(pb_problem *pb) {
-    pb_ctx *c = pb->ctx;
-    cudaStream_t s = c->stream;
+    cudaStream_t s = pb->stream;
     const Params &prm = pb->prm;
     const int ns = (int)pb->sin.size();
     if (ns == 0) fail(PB_EINVAL, "no surface");
@@ -101,8 +106,12 @@ void setup_problem(pb_problem *pb) {
         if (si.inner < 0 || si.inner >= (int)pb->regions.size() || si.outer < 0 ||
             si.outer >= (int)pb->regions.size() || si.inner == si.outer)
             fail(PB_EINVAL, "surface references an unknown region");
-    PB_CUDA_TRY(cudaEventRecord(c->ev0, s));
+    PB_CUDA_TRY(cudaEventRecord(pb->ev0, s));
     pb->adj.reset();
+    if (pb->mv_exec) {
+        cudaGraphExecDestroy(pb->mv_exec);
+        pb->mv_exec = nullptr;
+    }
     upload_rules();
     upload_term_tables();
     pb->S.clear(); pb->T.clear(); pb->G.clear(); pb->pairs.clear(); pb->cpairs.clear();
@@ -242,10 +251,16 @@ void setup_problem(pb_problem *pb) {
         if (!sa[0] || !sa[1]) fail(PB_EINVAL, "internal: missing self block");
         block_jacobi_inverse(pb->S[sf].n, cv[0], sa[0], cv[1], sa[1], pb->minv.p + 4 * pb->off[sf], s);
     }
-    PB_CUDA_TRY(cudaEventRecord(c->ev1, s));
-    PB_CUDA_TRY(cudaEventSynchronize(c->ev1));
+    // moments for every tree with a far field, so that no operator application allocates
+    for (int t = 0; t < ns; ++t)
+        if (pb->need_far[t]) {
+            const size_t nm = (size_t)pb->T[t].nnodes * 2 * nterms(prm.P);
+            if (prm.precision == PB_MIXED) pb->T[t].mom32.alloc(nm); else pb->T[t].mom64.alloc(nm);
+        }
+    PB_CUDA_TRY(cudaEventRecord(pb->ev1, s));
+    PB_CUDA_TRY(cudaEventSynchronize(pb->ev1));
     float ms = 0.f;
-    PB_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    PB_CUDA_TRY(cudaEventElapsedTime(&ms, pb->ev0, pb->ev1));
     pb->setup_ms = ms;
     pb->is_setup = true;
     pb->have_solution = false;
@@ -257,7 +272,7 @@ namespace pb {
 
 // y = A x, both device pointers of 2N doubles; optional event marks between the phases.
 void apply_operator(pb_problem *pb, const double *xd, double *yd, PhaseEvents *ph) {
-    cudaStream_t s = pb->ctx->stream;
+    cudaStream_t s = pb->stream;
     const Params &prm = pb->prm;
     const bool mixed = prm.precision == PB_MIXED;
     const int ns = (int)pb->S.size();
@@ -300,7 +315,7 @@ void apply_operator(pb_problem *pb, const double *xd, double *yd, PhaseEvents *p
 // phi_reac at the charges (input order) for the unknowns x (device); then
 // energy = 1/2 C sum_k q_k 4 pi phi_reac (device scalar).
 void reaction(pb_problem *pb, const double *xd) {
-    cudaStream_t s = pb->ctx->stream;
+    cudaStream_t s = pb->stream;
     const Params &prm = pb->prm;
     const bool mixed = prm.precision == PB_MIXED;
     const int ns = (int)pb->S.size();
@@ -337,64 +352,157 @@ void reaction(pb_problem *pb, const double *xd) {
 
 // z = M^-1 u (block-Jacobi), both 2N device vectors.
 void apply_precond(pb_problem *pb, const double *u, double *z) {
-    cudaStream_t s = pb->ctx->stream;
+    cudaStream_t s = pb->stream;
     for (size_t sf = 0; sf < pb->S.size(); ++sf) {
         const int64_t n = pb->S[sf].n, o = 2 * pb->off[sf];
         block_jacobi_apply(n, pb->minv.p + 4 * pb->off[sf], u + o, u + o + n, z + o, z + o + n, s);
     }
 }
 
+void launch_operator_graph(pb_problem *pb, cudaStream_t s) {
+    if (!pb->mv_exec) {
+        cudaStream_t cs = pb->stream;
+        const long long k0 = g_launches.load();
+        PB_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaGraph_t graph = nullptr;
+        try {
+            apply_operator(pb, pb->z1.p, pb->gm.w.p);
+        } catch (...) {
+            cudaStreamEndCapture(cs, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+        }
+        PB_CUDA_TRY(cudaStreamEndCapture(cs, &graph));
+        const cudaError_t e = cudaGraphInstantiate(&pb->mv_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        PB_CUDA_TRY(e);
+        pb->mv_kernels = g_launches.load() - k0;
+        g_launches.fetch_sub(pb->mv_kernels);   // captured, not executed
+    }
+    PB_CUDA_TRY(cudaGraphLaunch(pb->mv_exec, s));
+    g_launches.fetch_add(pb->mv_kernels);
+}
+
+namespace {
+
+void sync_streams(const std::vector<KrylovJob *> &jobs, bool only_active) {
+    std::vector<cudaStream_t> done;
+    for (const KrylovJob *jb : jobs) {
+        if (only_active && jb->act == 0) continue;
+        cudaStream_t s = jb->pb->stream;
+        if (std::find(done.begin(), done.end(), s) != done.end()) continue;
+        done.push_back(s);
+        PB_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+}
+
+}  // namespace
+
+void run_krylov(std::vector<KrylovJob *> &jobs) {
+    for (KrylovJob *jb : jobs) {
+        pb_problem *pb = jb->pb;
+        jb->st = KrylovStats{};
+        jb->act = 0;
+        if (jb->x_zero) PB_CUDA_TRY(cudaMemsetAsync(jb->x, 0, 2 * pb->N * sizeof(double), pb->stream));
+        pb->gm.norm2_async(jb->b, pb->stream);
+    }
+    sync_streams(jobs, false);
+    for (KrylovJob *jb : jobs) {
+        pb_problem *pb = jb->pb;
+        jb->bnorm = std::sqrt(pb->gm.host(0));
+        if (jb->bnorm == 0.0) {
+            PB_CUDA_TRY(cudaMemsetAsync(jb->x, 0, 2 * pb->N * sizeof(double), pb->stream));
+            jb->phase = 3;
+        } else {
+            pb->gm.set_bnorm(jb->bnorm, pb->stream);
+            jb->phase = 1;
+        }
+    }
+    while (true) {
+        bool any = false;
+        for (KrylovJob *jb : jobs) {
+            pb_problem *pb = jb->pb;
+            cudaStream_t s = pb->stream;
+            Gmres &gm = pb->gm;
+            const int64_t n2 = 2 * pb->N;
+            jb->act = 0;
+            if (jb->phase == 1) {
+                if (jb->x_zero) {
+                    PB_CUDA_TRY(cudaMemcpyAsync(pb->r.p, jb->b, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                } else {
+                    jb->op(jb->x, pb->y.p);
+                    ++jb->st.matvecs;
+                    axpby(1.0, jb->b, -1.0, pb->y.p, pb->r.p, n2, s);
+                }
+                jb->x_zero = false;
+                gm.start_cycle(pb->r.p, s);
+                jb->act = 1;
+            } else if (jb->phase == 2) {
+                if (jb->graph_op) {
+                    if (jb->precond) jb->precond(gm.basis(jb->j), pb->z1.p);
+                    else PB_CUDA_TRY(cudaMemcpyAsync(pb->z1.p, gm.basis(jb->j), n2 * sizeof(double),
+                                                     cudaMemcpyDeviceToDevice, s));
+                    launch_operator_graph(pb, s);
+                } else if (jb->precond) {
+                    jb->precond(gm.basis(jb->j), pb->z1.p);
+                    jb->op(pb->z1.p, gm.w.p);
+                } else {
+                    jb->op(gm.basis(jb->j), gm.w.p);
+                }
+                ++jb->st.matvecs;
+                gm.arnoldi_step(jb->j, s);
+                jb->act = 2;
+            }
+            any = any || jb->act != 0;
+        }
+        if (!any) break;
+        sync_streams(jobs, true);
+        for (KrylovJob *jb : jobs) {
+            pb_problem *pb = jb->pb;
+            const Params &prm = pb->prm;
+            cudaStream_t s = pb->stream;
+            Gmres &gm = pb->gm;
+            if (jb->act == 1) {
+                jb->st.rel = std::sqrt(gm.host(1)) / jb->bnorm;
+                if (!(jb->st.rel >= prm.tol) || jb->st.iters >= prm.max_iter) {
+                    jb->phase = 3;
+                } else {
+                    jb->phase = 2;
+                    jb->j = 0;
+                }
+            } else if (jb->act == 2) {
+                ++jb->st.iters;
+                const int k = jb->j + 1;
+                const double est = gm.host(2);
+                if (!(est >= prm.tol) || jb->st.iters >= prm.max_iter || k == gm.m) {
+                    if (jb->precond) {
+                        basis_combination(gm, k, pb->z1.p, s);
+                        jb->precond(pb->z1.p, pb->z2.p);
+                        axpby(1.0, jb->x, 1.0, pb->z2.p, jb->x, 2 * pb->N, s);
+                    } else {
+                        gm.update_solution(k, jb->x, s);
+                    }
+                    jb->phase = 1;
+                } else {
+                    ++jb->j;
+                }
+            }
+        }
+    }
+}
+
 KrylovStats run_gmres(pb_problem *pb, const DevOp &op, const DevOp &precond, const double *b, double *x,
                       bool x_zero) {
-    cudaStream_t s = pb->ctx->stream;
-    const Params &prm = pb->prm;
-    const int64_t n2 = 2 * pb->N;
-    Gmres &gm = pb->gm;
-    KrylovStats st;
-    if (x_zero) PB_CUDA_TRY(cudaMemsetAsync(x, 0, n2 * sizeof(double), s));
-    const double bnorm = norm2_device(b, n2, gm, s);
-    if (bnorm == 0.0) {
-        PB_CUDA_TRY(cudaMemsetAsync(x, 0, n2 * sizeof(double), s));
-        return st;
-    }
-    gm.set_bnorm(bnorm, s);
-    bool zero_x = x_zero;
-    while (true) {
-        if (zero_x) {
-            PB_CUDA_TRY(cudaMemcpyAsync(pb->r.p, b, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        } else {
-            op(x, pb->y.p);
-            ++st.matvecs;
-            axpby(1.0, b, -1.0, pb->y.p, pb->r.p, n2, s);
-        }
-        zero_x = false;
-        const double beta = gm.start_cycle(pb->r.p, s);
-        st.rel = beta / bnorm;
-        if (!(st.rel >= prm.tol) || st.iters >= prm.max_iter) break;
-        int k = 0;
-        for (int j = 0; j < gm.m; ++j) {
-            if (precond) {
-                precond(gm.basis(j), pb->z1.p);
-                op(pb->z1.p, gm.w.p);
-            } else {
-                op(gm.basis(j), gm.w.p);
-            }
-            ++st.matvecs;
-            gm.arnoldi_step(j, s);
-            ++st.iters;
-            k = j + 1;
-            const double est = gm.residual_estimate(s);
-            if (!(est >= prm.tol) || st.iters >= prm.max_iter) break;
-        }
-        if (precond && k > 0) {
-            basis_combination(gm, k, pb->z1.p, s);
-            precond(pb->z1.p, pb->z2.p);
-            axpby(1.0, x, 1.0, pb->z2.p, x, n2, s);
-        } else {
-            gm.update_solution(k, x, s);
-        }
-    }
-    return st;
+    KrylovJob jb;
+    jb.pb = pb;
+    jb.op = op;
+    jb.precond = precond;
+    jb.b = b;
+    jb.x = x;
+    jb.x_zero = x_zero;
+    std::vector<KrylovJob *> jobs{&jb};
+    run_krylov(jobs);
+    return jb.st;
 }
 
 }  // namespace pb
@@ -405,44 +513,129 @@ void require_setup(pb_problem *pb) {
     if (!pb->is_setup) fail(PB_ENOTSETUP, "pb_setup has not been called since the last input change");
 }
 
-void solve(pb_problem *pb, const double *x0, pb_result *out) {
-    require_setup(pb);
-    pb_ctx *c = pb->ctx;
-    cudaStream_t s = c->stream;
-    const Params &prm = pb->prm;
-    const int64_t n2 = 2 * pb->N;
-    PB_CUDA_TRY(cudaEventRecord(c->ev0, s));
-    if (x0) PB_CUDA_TRY(cudaMemcpyAsync(pb->x.p, x0, n2 * sizeof(double), cudaMemcpyHostToDevice, s));
-    DevOp op = [pb](const double *u, double *v) { apply_operator(pb, u, v); };
-    DevOp pc;
-    if (prm.precond) pc = [pb](const double *u, double *z) { apply_precond(pb, u, z); };
-    const KrylovStats st = run_gmres(pb, op, pc, pb->b.p, pb->x.p, x0 == nullptr);
-    reaction(pb, pb->x.p);
-    double dG = 0.0;
-    PB_CUDA_TRY(cudaMemcpyAsync(&dG, pb->energy.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-    PB_CUDA_TRY(cudaEventRecord(c->ev1, s));
-    PB_CUDA_TRY(cudaEventSynchronize(c->ev1));
-    float ms = 0.f;
-    PB_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-    pb->have_solution = true;
-    pb->dG = dG;
-    if (out) {
-        std::memset(out, 0, sizeof(*out));
-        out->dG_solv = dG;
-        out->residual = st.rel;
-        out->iterations = st.iters;
-        out->converged = st.rel < prm.tol;
-        out->matvecs = st.matvecs;
-        out->setup_ms = pb->setup_ms;
-        out->solve_ms = ms;
-        for (auto &P : pb->pairs) {
-            out->p2p_pairs += P.p2p_pairs;
-            out->m2p_pairs += P.n_m2p * (int64_t)P.kappas.size();
-            out->near_pairs += P.n_near;
-            out->near_excluded += P.near_excl;
-        }
+void fill_result(pb_problem *pb, const KrylovStats &st, float ms, pb_result *out) {
+    std::memset(out, 0, sizeof(*out));
+    out->dG_solv = pb->dG;
+    out->residual = st.rel;
+    out->iterations = st.iters;
+    out->converged = st.rel < pb->prm.tol;
+    out->matvecs = st.matvecs;
+    out->setup_ms = pb->setup_ms;
+    out->solve_ms = ms;
+    for (auto &P : pb->pairs) {
+        out->p2p_pairs += P.p2p_pairs;
+        out->m2p_pairs += P.n_m2p * (int64_t)P.kappas.size();
+        out->near_pairs += P.n_near;
+        out->near_excluded += P.near_excl;
     }
-    if (!(st.rel < prm.tol)) fail(PB_ENOCONV, "GMRES reached max_iter before the tolerance");
+}
+
+// Solve every problem of `probs` (set up, distinct) by lock-step GMRES, each on
+// its current stream, then its reaction potential and energy.
+void solve_many(const std::vector<pb_problem *> &probs, const std::vector<const double *> &x0s,
+                std::vector<KrylovStats> &stats, std::vector<float> &ms) {
+    const size_t n = probs.size();
+    std::vector<KrylovJob> jobs(n);
+    std::vector<KrylovJob *> jp(n);
+    for (size_t i = 0; i < n; ++i) {
+        pb_problem *pb = probs[i];
+        require_setup(pb);
+        cudaStream_t s = pb->stream;
+        PB_CUDA_TRY(cudaEventRecord(pb->ev0, s));
+        const int64_t n2 = 2 * pb->N;
+        if (x0s[i]) PB_CUDA_TRY(cudaMemcpyAsync(pb->x.p, x0s[i], n2 * sizeof(double), cudaMemcpyHostToDevice, s));
+        KrylovJob &jb = jobs[i];
+        jb.pb = pb;
+        jb.op = [pb](const double *u, double *v) { apply_operator(pb, u, v); };
+        if (pb->prm.precond) jb.precond = [pb](const double *u, double *z) { apply_precond(pb, u, z); };
+        jb.b = pb->b.p;
+        jb.x = pb->x.p;
+        jb.x_zero = x0s[i] == nullptr;
+        jb.graph_op = true;
+        jp[i] = &jb;
+    }
+    run_krylov(jp);
+    for (size_t i = 0; i < n; ++i) {
+        pb_problem *pb = probs[i];
+        reaction(pb, pb->x.p);
+        PB_CUDA_TRY(cudaMemcpyAsync(pb->gm.hs.p + 3, pb->energy.p, sizeof(double), cudaMemcpyDeviceToHost,
+                                    pb->stream));
+        PB_CUDA_TRY(cudaEventRecord(pb->ev1, pb->stream));
+    }
+    stats.resize(n);
+    ms.resize(n);
+    for (size_t i = 0; i < n; ++i) {
+        pb_problem *pb = probs[i];
+        PB_CUDA_TRY(cudaEventSynchronize(pb->ev1));
+        PB_CUDA_TRY(cudaEventElapsedTime(&ms[i], pb->ev0, pb->ev1));
+        pb->dG = pb->gm.host(3);
+        pb->have_solution = true;
+        stats[i] = jobs[i].st;
+    }
+}
+
+void solve(pb_problem *pb, const double *x0, pb_result *out) {
+    std::vector<KrylovStats> st;
+    std::vector<float> ms;
+    solve_many({pb}, {x0}, st, ms);
+    if (out) fill_result(pb, st[0], ms[0], out);
+    if (!(st[0].rel < pb->prm.tol)) fail(PB_ENOCONV, "GMRES reached max_iter before the tolerance");
+}
+
+// Runs `f` with problem i on pool stream i mod (pool size), forked from and
+// joined back to the context stream, so the call stays ordered on it.
+template <typename F>
+void on_pool_streams(pb_ctx *c, const std::vector<pb_problem *> &probs, F &&f) {
+    const size_t np = std::min<size_t>(std::max<size_t>(1, probs.size()), 8);
+    while (c->pool.size() < np) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        PB_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        PB_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        c->pool.push_back(st);
+        c->pool_ev.push_back(ev);
+    }
+    PB_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+    for (size_t k = 0; k < np; ++k) PB_CUDA_TRY(cudaStreamWaitEvent(c->pool[k], c->ev0, 0));
+    for (size_t i = 0; i < probs.size(); ++i) probs[i]->stream = c->pool[i % np];
+    auto restore = [&] {
+        for (size_t k = 0; k < np; ++k) {
+            cudaEventRecord(c->pool_ev[k], c->pool[k]);
+            cudaStreamWaitEvent(c->stream, c->pool_ev[k], 0);
+        }
+        for (pb_problem *pb : probs) pb->stream = c->stream;
+    };
+    try {
+        f();
+    } catch (...) {
+        restore();
+        throw;
+    }
+    restore();
+}
+
+double coulomb(pb_problem *pb) {
+    cudaStream_t s = pb->stream;
+    const int64_t nc = (int64_t)pb->cq.size();
+    if (nc == 0) return 0.0;
+    TmpBuf<double> rowv(nc, s);
+    coulomb_rows(pb->cxyz_d.p, pb->cq_d.p, nc, rowv.p, s);
+    weighted_sum(pb->cq_d.p, rowv.p, nc, 0.5 * kKjPerMol / pb->regions[pb->cregion].eps, pb->energy.p, s);
+    double out = 0.0;
+    PB_CUDA_TRY(cudaMemcpyAsync(&out, pb->energy.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PB_CUDA_TRY(cudaStreamSynchronize(s));
+    return out;
+}
+
+void check_batch(pb_ctx *c, pb_problem *const *probs, int n, std::vector<pb_problem *> &v) {
+    if (n < 0 || (n > 0 && !probs)) fail(PB_EINVAL, "bad problem array");
+    for (int i = 0; i < n; ++i) {
+        if (!probs[i]) fail(PB_EINVAL, "null problem in batch");
+        if (probs[i]->ctx != c) fail(PB_EINVAL, "problem belongs to another context");
+        if (std::find(v.begin(), v.end(), probs[i]) != v.end()) fail(PB_EINVAL, "problem repeated in batch");
+        require_setup(probs[i]);
+        v.push_back(probs[i]);
+    }
 }
 
 }  // namespace
@@ -472,6 +665,11 @@ void pb_ctx_destroy(pb_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    for (size_t k = 0; k < c->pool.size(); ++k) {
+        cudaStreamSynchronize(c->pool[k]);
+        cudaStreamDestroy(c->pool[k]);
+        cudaEventDestroy(c->pool_ev[k]);
+    }
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->stream) cudaStreamDestroy(c->stream);
@@ -484,15 +682,24 @@ void *pb_ctx_stream(pb_ctx *c) { return c ? (void *)c->stream : nullptr; }
 
 int pb_problem_create(pb_ctx *c, pb_problem **out) {
     if (!c || !out) return PB_EINVAL;
-    *out = new pb_problem();
-    (*out)->ctx = c;
+    *out = nullptr;
+    auto pb = std::make_unique<pb_problem>();
+    pb->ctx = c;
+    pb->stream = c->stream;
+    const int rc = guard(c, [&] {
+        set_device(c);
+        PB_CUDA_TRY(cudaEventCreate(&pb->ev0));
+        PB_CUDA_TRY(cudaEventCreate(&pb->ev1));
+    });
+    if (rc != PB_OK) return rc;
+    *out = pb.release();
     return PB_OK;
 }
 
 void pb_problem_destroy(pb_problem *pb) {
     if (!pb) return;
     cudaSetDevice(pb->ctx->device);
-    cudaStreamSynchronize(pb->ctx->stream);
+    cudaStreamSynchronize(pb->stream);
     delete pb;
 }
 
@@ -524,9 +731,9 @@ int pb_add_surface(pb_problem *pb, const double *verts, int64_t nv, const int32_
         SurfIn si;
         si.nv = nv;
         si.nt = nt;
-        si.v.upload(verts, 3 * nv, pb->ctx->stream);
-        si.t.upload(tris, 3 * nt, pb->ctx->stream);
-        PB_CUDA_TRY(cudaStreamSynchronize(pb->ctx->stream));
+        si.v.upload(verts, 3 * nv, pb->stream);
+        si.t.upload(tris, 3 * nt, pb->stream);
+        PB_CUDA_TRY(cudaStreamSynchronize(pb->stream));
         si.inner = inner;
         si.outer = outer;
         pb->sin.push_back(std::move(si));
@@ -546,9 +753,9 @@ int pb_set_charges(pb_problem *pb, const double *xyz, const double *q, int64_t n
         set_device(pb->ctx);
         pb->cxyz.assign(xyz, xyz + 3 * nc);
         pb->cq.assign(q, q + nc);
-        pb->cq_d.upload(q, nc, pb->ctx->stream);
-        pb->cxyz_d.upload(xyz, 3 * nc, pb->ctx->stream);
-        PB_CUDA_TRY(cudaStreamSynchronize(pb->ctx->stream));
+        pb->cq_d.upload(q, nc, pb->stream);
+        pb->cxyz_d.upload(xyz, 3 * nc, pb->stream);
+        PB_CUDA_TRY(cudaStreamSynchronize(pb->stream));
         pb->cregion = region;
         pb->is_setup = false;
     });
@@ -571,7 +778,7 @@ int pb_apply_operator(pb_problem *pb, const double *x, double *y, int device_ptr
     return guard(pb->ctx, [&] {
         require_setup(pb);
         set_device(pb->ctx);
-        cudaStream_t s = pb->ctx->stream;
+        cudaStream_t s = pb->stream;
         const int64_t n2 = 2 * pb->N;
         if (device_ptrs) {
             apply_operator(pb, x, y);
@@ -589,8 +796,8 @@ int pb_rhs(pb_problem *pb, double *bh) {
     if (!pb || !bh) return PB_EINVAL;
     return guard(pb->ctx, [&] {
         require_setup(pb);
-        pb->b.download(bh, 2 * pb->N, pb->ctx->stream);
-        PB_CUDA_TRY(cudaStreamSynchronize(pb->ctx->stream));
+        pb->b.download(bh, 2 * pb->N, pb->stream);
+        PB_CUDA_TRY(cudaStreamSynchronize(pb->stream));
     });
 }
 
@@ -616,7 +823,7 @@ int pb_apply_transpose(pb_problem *pb, const double *x, double *y, int device_pt
     return guard(pb->ctx, [&] {
         require_setup(pb);
         set_device(pb->ctx);
-        cudaStream_t s = pb->ctx->stream;
+        cudaStream_t s = pb->stream;
         const int64_t n2 = 2 * pb->N;
         if (device_ptrs) {
             apply_transpose(pb, x, y);
@@ -635,8 +842,8 @@ int pb_get_solution(pb_problem *pb, double *xh) {
     return guard(pb->ctx, [&] {
         require_setup(pb);
         if (!pb->have_solution) fail(PB_EINVAL, "no solution yet");
-        pb->x.download(xh, 2 * pb->N, pb->ctx->stream);
-        PB_CUDA_TRY(cudaStreamSynchronize(pb->ctx->stream));
+        pb->x.download(xh, 2 * pb->N, pb->stream);
+        PB_CUDA_TRY(cudaStreamSynchronize(pb->stream));
     });
 }
 
@@ -645,7 +852,7 @@ int pb_reaction_potential(pb_problem *pb, const double *xh, double *phi) {
     return guard(pb->ctx, [&] {
         require_setup(pb);
         set_device(pb->ctx);
-        cudaStream_t s = pb->ctx->stream;
+        cudaStream_t s = pb->stream;
         pb->xin.upload(xh, 2 * pb->N, s);
         reaction(pb, pb->xin.p);
         pb->phi_reac.download(phi, pb->cq.size(), s);
@@ -658,14 +865,48 @@ int pb_coulomb_energy(pb_problem *pb, double *out) {
     return guard(pb->ctx, [&] {
         require_setup(pb);
         set_device(pb->ctx);
-        cudaStream_t s = pb->ctx->stream;
-        const int64_t nc = (int64_t)pb->cq.size();
-        if (nc == 0) { *out = 0.0; return; }
-        TmpBuf<double> rowv(nc, s);
-        coulomb_rows(pb->cxyz_d.p, pb->cq_d.p, nc, rowv.p, s);
-        weighted_sum(pb->cq_d.p, rowv.p, nc, 0.5 * kKjPerMol / pb->regions[pb->cregion].eps, pb->energy.p, s);
-        PB_CUDA_TRY(cudaMemcpyAsync(out, pb->energy.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-        PB_CUDA_TRY(cudaStreamSynchronize(s));
+        *out = coulomb(pb);
+    });
+}
+
+int pb_solve_batch(pb_ctx *c, pb_problem *const *probs, int n, pb_result *out) {
+    if (!c) return PB_EINVAL;
+    return guard(c, [&] {
+        set_device(c);
+        std::vector<pb_problem *> v;
+        check_batch(c, probs, n, v);
+        if (v.empty()) return;
+        std::vector<KrylovStats> st;
+        std::vector<float> ms;
+        on_pool_streams(c, v, [&] { solve_many(v, std::vector<const double *>(v.size(), nullptr), st, ms); });
+        bool conv = true;
+        for (size_t i = 0; i < v.size(); ++i) {
+            if (out) fill_result(v[i], st[i], ms[i], out + i);
+            conv = conv && st[i].rel < v[i]->prm.tol;
+        }
+        PB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (!conv) fail(PB_ENOCONV, "GMRES reached max_iter before the tolerance in a batched problem");
+    });
+}
+
+int pb_binding_energy(pb_ctx *c, pb_problem *cx, pb_problem *rec, pb_problem *lig, double *ddG) {
+    if (!c || !ddG) return PB_EINVAL;
+    return guard(c, [&] {
+        set_device(c);
+        pb_problem *arr[3] = {cx, rec, lig};
+        std::vector<pb_problem *> v;
+        check_batch(c, arr, 3, v);
+        std::vector<KrylovStats> st;
+        std::vector<float> ms;
+        double e[3] = {0.0, 0.0, 0.0};
+        on_pool_streams(c, v, [&] {
+            solve_many(v, std::vector<const double *>(3, nullptr), st, ms);
+            for (int i = 0; i < 3; ++i) e[i] = v[i]->dG + coulomb(v[i]);
+        });
+        PB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        for (int i = 0; i < 3; ++i)
+            if (!(st[i].rel < v[i]->prm.tol)) fail(PB_ENOCONV, "GMRES reached max_iter before the tolerance");
+        *ddG = e[0] - e[1] - e[2];
     });
 }
 
@@ -674,7 +915,7 @@ int pb_profile_operator(pb_problem *pb, const double *xh, int reps, double *phas
     return guard(pb->ctx, [&] {
         require_setup(pb);
         set_device(pb->ctx);
-        cudaStream_t s = pb->ctx->stream;
+        cudaStream_t s = pb->stream;
         const int64_t n2 = 2 * pb->N;
         pb->xin.upload(xh, n2, s);
         pb->yout.alloc(n2);
@@ -721,7 +962,7 @@ int pb_tree_export(pb_problem *pb, int surface, uint64_t *keys, int32_t *perm, i
         require_setup(pb);
         if (surface < 0 || surface >= (int)pb->T.size()) fail(PB_EINVAL, "no such surface");
         const Tree &T = pb->T[surface];
-        cudaStream_t s = pb->ctx->stream;
+        cudaStream_t s = pb->stream;
         if (keys) T.keys.download(keys, T.npts, s);
         if (perm) T.perm.download(perm, T.npts, s);
         if (node_level) T.level.download(node_level, T.nnodes, s);
@@ -749,7 +990,7 @@ int pb_lists_export(pb_problem *pb, int target_surface, int source_surface, int6
             if (q.tgt == tg && q.tree == source_surface) P = &q;
         if (!P) fail(PB_EINVAL, "these surfaces do not interact");
         const Targets &G = pb->G[tg];
-        cudaStream_t s = pb->ctx->stream;
+        cudaStream_t s = pb->stream;
         const int64_t m = G.n;
         if (counts) {
             counts[0] = P->n_m2p; counts[1] = P->n_p2p; counts[2] = P->n_near;

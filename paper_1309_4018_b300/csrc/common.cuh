@@ -93,6 +93,32 @@ struct DevBuf {
     }
 };
 
+// Page-locked host scalars (asynchronous device-to-host reads).
+template <typename T>
+struct PinnedBuf {
+    T *p = nullptr;
+    PinnedBuf() = default;
+    PinnedBuf(const PinnedBuf &) = delete;
+    PinnedBuf &operator=(const PinnedBuf &) = delete;
+    PinnedBuf(PinnedBuf &&o) noexcept : p(o.p) { o.p = nullptr; }
+    PinnedBuf &operator=(PinnedBuf &&o) noexcept {
+        if (this != &o) { release(); p = o.p; o.p = nullptr; }
+        return *this;
+    }
+    ~PinnedBuf() { release(); }
+    void release() {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+    }
+    void alloc(size_t count) {
+        release();
+        if (cudaMallocHost(&p, count * sizeof(T)) != cudaSuccess) {
+            p = nullptr;
+            throw Error{PB_ENOMEM, "cudaMallocHost failed"};
+        }
+    }
+};
+
 // Stream-ordered temporary: allocated and freed on the stream that uses it,
 // so its release waits for the kernels queued before it.
 template <typename T>

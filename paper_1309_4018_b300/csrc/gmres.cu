@@ -126,6 +126,10 @@ __global__ void update_x_kernel(const double *__restrict__ V, int64_t ld, int k,
     x[i] = s;
 }
 
+__global__ void set_bnorm_kernel(GmresState *st, double bn) {
+    if (threadIdx.x == 0) st->bnorm = bn;
+}
+
 __global__ void init_cycle_kernel(GmresState *st, const double *__restrict__ beta2) {
     if (threadIdx.x != 0) return;
     const double beta = sqrt(*beta2);
@@ -222,25 +226,28 @@ void Gmres::init(int64_t n_, int m_, cudaStream_t s) {
     h.m = m;
     h.H = H.p; h.cs = cs.p; h.sn = sn.p; h.g = g.p; h.y = y.p;
     h.bnorm = 1.0;
+    hs.alloc(4);
     PB_CUDA_TRY(cudaMemcpyAsync(st.p, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     PB_CUDA_TRY(cudaStreamSynchronize(s));
 }
 
-void Gmres::set_bnorm(double bn, cudaStream_t s) {
-    PB_CUDA_TRY(cudaMemcpyAsync(&st.p->bnorm, &bn, sizeof(double), cudaMemcpyHostToDevice, s));
-    PB_CUDA_TRY(cudaStreamSynchronize(s));
+void Gmres::norm2_async(const double *x, cudaStream_t s) {
+    dot_device(x, 0, 1, x, n, partial.p, scal.p + 2, s);
+    PB_CUDA_TRY(cudaMemcpyAsync(hs.p, scal.p + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
 }
 
-double Gmres::start_cycle(const double *r, cudaStream_t s) {
+void Gmres::set_bnorm(double bn, cudaStream_t s) {
+    set_bnorm_kernel<<<1, 1, 0, s>>>(st.p, bn);
+    PB_LAUNCH_CHECK();
+}
+
+void Gmres::start_cycle(const double *r, cudaStream_t s) {
     dot_device(r, ld, 1, r, n, partial.p, scal.p, s);
     scale_copy_kernel<<<div_up(n, 256), 256, 0, s>>>(r, scal.p, V.p, n);
     PB_LAUNCH_CHECK();
     init_cycle_kernel<<<1, 1, 0, s>>>(st.p, scal.p);
     PB_LAUNCH_CHECK();
-    double b2 = 0.0;
-    PB_CUDA_TRY(cudaMemcpyAsync(&b2, scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-    PB_CUDA_TRY(cudaStreamSynchronize(s));
-    return std::sqrt(b2);
+    PB_CUDA_TRY(cudaMemcpyAsync(hs.p + 1, scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
 }
 
 void Gmres::arnoldi_step(int j, cudaStream_t s) {
@@ -257,13 +264,7 @@ void Gmres::arnoldi_step(int j, cudaStream_t s) {
     PB_LAUNCH_CHECK();
     givens_kernel<<<1, 1, 0, s>>>(st.p, j, hcol.p, scal.p + 1);
     PB_LAUNCH_CHECK();
-}
-
-double Gmres::residual_estimate(cudaStream_t s) {
-    double r = 0.0;
-    PB_CUDA_TRY(cudaMemcpyAsync(&r, &st.p->res_est, sizeof(double), cudaMemcpyDeviceToHost, s));
-    PB_CUDA_TRY(cudaStreamSynchronize(s));
-    return r;
+    PB_CUDA_TRY(cudaMemcpyAsync(hs.p + 2, &st.p->res_est, sizeof(double), cudaMemcpyDeviceToHost, s));
 }
 
 void Gmres::update_solution(int k, double *x, cudaStream_t s) {
@@ -304,14 +305,6 @@ void axpby(double a, const double *x, double b, const double *y, double *out, in
     if (!n) return;
     axpby_kernel<<<div_up(n, 256), 256, 0, s>>>(a, x, b, y, out, n);
     PB_LAUNCH_CHECK();
-}
-
-double norm2_device(const double *x, int64_t n, Gmres &G, cudaStream_t s) {
-    dot_device(x, 0, 1, x, n, G.partial.p, G.scal.p + 2, s);
-    double h = 0.0;
-    PB_CUDA_TRY(cudaMemcpyAsync(&h, G.scal.p + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
-    PB_CUDA_TRY(cudaStreamSynchronize(s));
-    return std::sqrt(h);
 }
 
 void weighted_sum(const double *q, const double *phi, int64_t n, double scale, double *out, cudaStream_t s) {

@@ -15,17 +15,22 @@ struct GmresState {
     double bnorm, beta, hnext, res_est;
 };
 
+// Every step only queues work on the stream; the scalars the host decides on
+// (||b||^2, ||r||^2, the residual estimate) are copied into page-locked host
+// memory and read with host() after the stream has been synchronised.
 struct Gmres {
     int64_t n = 0, ld = 0;
     int m = 0;
     DevBuf<double> V, w, partial, hcol, h2, scal, H, cs, sn, g, y;
     DevBuf<GmresState> st;
+    PinnedBuf<double> hs;                                  // 0: ||b||^2, 1: ||r||^2, 2: residual estimate
     void init(int64_t n, int m, cudaStream_t s);
+    void norm2_async(const double *x, cudaStream_t s);     // hs[0] = ||x||^2
     void set_bnorm(double bn, cudaStream_t s);
-    double start_cycle(const double *r, cudaStream_t s);   // v_0 = r / ||r||; returns ||r||
+    void start_cycle(const double *r, cudaStream_t s);     // v_0 = r / ||r||; hs[1] = ||r||^2
     double *basis(int j) { return V.p + (int64_t)j * ld; }
-    void arnoldi_step(int j, cudaStream_t s);              // needs w = A v_j
-    double residual_estimate(cudaStream_t s);
+    void arnoldi_step(int j, cudaStream_t s);              // needs w = A v_j; hs[2] = residual estimate
+    double host(int i) const { return hs.p[i]; }
     void update_solution(int k, double *x, cudaStream_t s);
 };
 
@@ -40,7 +45,6 @@ void basis_combination(const Gmres &G, int k, double *out, cudaStream_t s);
 
 void add_kernel_launch(double *a, const double *b, int n, cudaStream_t s);
 void axpby(double a, const double *x, double b, const double *y, double *out, int64_t n, cudaStream_t s);
-double norm2_device(const double *x, int64_t n, Gmres &G, cudaStream_t s);
 // *out = scale * sum_k q_k phi_k (device scalar)
 void weighted_sum(const double *q, const double *phi, int64_t n, double scale, double *out, cudaStream_t s);
 // rowv[i] = sum_{j != i} q_j / r_ij

@@ -14,6 +14,8 @@ struct pb_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaStream_t> pool;   // streams of batched solves (created on first use)
+    std::vector<cudaEvent_t> pool_ev;
     std::string err;
 };
 
@@ -40,6 +42,10 @@ struct AdjointState;   // adjoint.cuh
 
 struct pb_problem {
     pb_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;            // the context stream, or a pool stream inside a batch
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaGraphExec_t mv_exec = nullptr;        // captured operator application z1 -> gm.w
+    long long mv_kernels = 0;                 // kernels in that graph
     std::vector<pb::Region> regions;
     std::vector<pb::SurfIn> sin;
     std::vector<double> cxyz, cq;
@@ -64,6 +70,7 @@ struct pb_problem {
     bool have_solution = false;
     double dG = 0.0;                          // energy of the last solve
     std::shared_ptr<pb::AdjointState> adj;   // built by the first gradient after setup
+    ~pb_problem();
 };
 
 namespace pb {
@@ -76,15 +83,34 @@ void apply_operator(pb_problem *pb, const double *xd, double *yd, PhaseEvents *p
 void apply_precond(pb_problem *pb, const double *u, double *z);
 void reaction(pb_problem *pb, const double *xd);
 
-// Restarted, right-preconditioned GMRES on the problem's Krylov state (scratch
+// Restarted, right-preconditioned GMRES on a problem's Krylov state (scratch
 // vectors r, y, z1, z2 of the problem): solves op(x) = b for the 2N-vector x
-// (device), starting from x (x_zero: from 0).  precond may be empty.
+// (device), starting from x (x_zero: from 0).  precond may be empty.  Several
+// jobs advance in lock step, each on its problem's stream: every round queues
+// one unit of work per job (a cycle start or one Arnoldi iteration) and the
+// host synchronises once per round to read the scalars it decides on.
+// graph_op: the Arnoldi operator is the problem's captured graph z1 -> gm.w.
 struct KrylovStats {
     int iters = 0, matvecs = 0;
     double rel = 0.0;
 };
 using DevOp = std::function<void(const double *, double *)>;
+struct KrylovJob {
+    pb_problem *pb = nullptr;
+    DevOp op, precond;
+    const double *b = nullptr;
+    double *x = nullptr;
+    bool x_zero = true;
+    bool graph_op = false;
+    KrylovStats st;
+    // driver state
+    int phase = 0, j = 0, act = 0;
+    double bnorm = 0.0;
+};
+void run_krylov(std::vector<KrylovJob *> &jobs);
 KrylovStats run_gmres(pb_problem *pb, const DevOp &op, const DevOp &precond, const double *b, double *x,
                       bool x_zero);
+// Operator application as a replayable CUDA graph (captured on first use).
+void launch_operator_graph(pb_problem *pb, cudaStream_t s);
 
 }  // namespace pb

@@ -74,6 +74,8 @@ _SIGS = {
     "pb_solve": ([_vp, _vp, ctypes.POINTER(pb_result)], _int),
     "pb_get_solution": ([_vp, _vp], _int),
     "pb_gradient": ([_vp, ctypes.POINTER(pb_grad)], _int),
+    "pb_solve_batch": ([_vp, _vp, _int, _vp], _int),
+    "pb_binding_energy": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_dbl)], _int),
     "pb_apply_transpose": ([_vp, _vp, _vp, _int], _int),
     "pb_reaction_potential": ([_vp, _vp, _vp], _int),
     "pb_coulomb_energy": ([_vp, ctypes.POINTER(_dbl)], _int),
@@ -172,6 +174,29 @@ def make_params(**kw) -> pb_params:
             v = {"fp64": PB_FP64, "mixed": PB_MIXED}[v]
         setattr(p, k, v)
     return p
+
+
+def _result(r) -> "Result":
+    return Result(r.dG_solv, r.residual, r.iterations, bool(r.converged), r.matvecs, r.setup_ms,
+                  r.solve_ms, r.p2p_pairs, r.m2p_pairs, r.near_pairs, r.near_excluded)
+
+
+def solve_batch(ctx: "Context", problems, check=True):
+    """Solve set-up problems of one context together (pb_solve_batch); one Result each."""
+    n = len(problems)
+    handles = (ctypes.c_void_p * max(1, n))(*[p._h for p in problems])
+    res = (pb_result * max(1, n))()
+    rc = _lib.pb_solve_batch(ctx.handle, handles, n, res)
+    if check or rc not in (PB_OK, PB_ENOCONV):
+        ctx.check(rc)
+    return [_result(res[i]) for i in range(n)]
+
+
+def binding_energy(ctx: "Context", cx, rec, lig) -> float:
+    """ddG = E_complex - E_receptor - E_ligand (solvation + Coulomb), kJ/mol (pb_binding_energy)."""
+    out = _dbl()
+    ctx.check(_lib.pb_binding_energy(ctx.handle, cx._h, rec._h, lig._h, ctypes.byref(out)))
+    return out.value
 
 
 class Problem:
@@ -279,8 +304,7 @@ class Problem:
         rc = _lib.pb_solve(self._h, _ptr(xx), ctypes.byref(r))
         if check or rc not in (PB_OK, PB_ENOCONV):
             self.ctx.check(rc)
-        return Result(r.dG_solv, r.residual, r.iterations, bool(r.converged), r.matvecs, r.setup_ms,
-                      r.solve_ms, r.p2p_pairs, r.m2p_pairs, r.near_pairs, r.near_excluded)
+        return _result(r)
 
     def solution(self):
         x = np.empty(self.n_unknowns)

@@ -122,3 +122,67 @@ def multisurface_problem(n_atoms=2000, seed=3, spacing=PROTEIN_SPACING,
 
 def panel_count(problem):
     return sum(int(np.asarray(s["tris"]).shape[0]) for s in problem["surfaces"])
+
+
+def _ball_radius(n_atoms):
+    return 20.0 * (n_atoms / 2000.0) ** (1.0 / 3.0)
+
+
+def place_ligand(rec_xyz, lig_xyz, gap=3.0, direction=(1.0, 0.0, 0.0)):
+    """Translate the ligand along `direction` until its closest atom centre is `gap` A from the receptor's."""
+    from scipy.spatial import cKDTree
+    tree = cKDTree(rec_xyz)
+    u = np.asarray(direction, dtype=np.float64)
+    u = u / np.linalg.norm(u)
+    lo, hi = 0.0, float(np.ptp(rec_xyz, axis=0).max() + np.ptp(lig_xyz, axis=0).max() + 2 * gap)
+
+    def dmin(t):
+        return float(tree.query(lig_xyz + t * u)[0].min())
+
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if dmin(mid) < gap:
+            lo = mid
+        else:
+            hi = mid
+    return lig_xyz + hi * u
+
+
+def _molecule_problem(xyz, radius, q, spacing):
+    v, t = gaussian_surface(xyz, radius, spacing)
+    return {
+        "regions": [{"eps": EPS_IN, "kappa": 0.0}, {"eps": EPS_OUT, "kappa": KAPPA}],
+        "surfaces": [{"verts": v, "tris": t, "inner": 0, "outer": 1}],
+        "charges": {"xyz": np.array(xyz, dtype=np.float64), "q": np.array(q, dtype=np.float64), "region": 0},
+    }
+
+
+def binding_triplet(n_rec=8000, n_lig=1500, seed=4, spacing=PROTEIN_SPACING, gap=3.0):
+    """Receptor, ligand and complex of a synthetic binding pair (Eq. bind_energy).
+
+    Receptor and ligand atoms are drawn like protein_atoms (ball radius
+    20 (N/2000)^(1/3) A, seeds `seed` and `seed` + 1); the ligand is moved
+    along +x until its closest atom centre is `gap` A from the receptor's.
+    The complex is the union of both atom sets (its own Gaussian surface).
+    Returns (complex, receptor, ligand) problem dicts.
+    """
+    rec = synthetic_atoms(n_rec, _ball_radius(n_rec), seed)
+    lig = synthetic_atoms(n_lig, _ball_radius(n_lig), seed + 1)
+    lxyz = place_ligand(rec["xyz"], lig["xyz"], gap)
+    cx_xyz = np.vstack([rec["xyz"], lxyz])
+    cx_r = np.concatenate([rec["radius"], lig["radius"]])
+    cx_q = np.concatenate([rec["q"], lig["q"]])
+    return (_molecule_problem(cx_xyz, cx_r, cx_q, spacing),
+            _molecule_problem(rec["xyz"], rec["radius"], rec["q"], spacing),
+            _molecule_problem(lxyz, lig["radius"], lig["q"], spacing))
+
+
+def ligand_fleet(count=64, n_min=300, n_max=3000, seed=4, spacing=PROTEIN_SPACING):
+    """`count` synthetic ligands with atom counts log-uniform in [n_min, n_max] (seed + 1 + i each)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = np.exp(rng.uniform(np.log(n_min), np.log(n_max), size=count)).astype(int)
+    out = []
+    for i, n in enumerate(sizes):
+        at = synthetic_atoms(int(n), _ball_radius(int(n)), seed + 1 + i)
+        out.append(_molecule_problem(at["xyz"], at["radius"], at["q"], spacing))
+    return out

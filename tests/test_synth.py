@@ -32,3 +32,16 @@ def test_protein_surface():
             + np.einsum("ij,ij->i", c, a) * lb
         w = 2 * np.arctan2(num, den).sum() / (4 * np.pi)
         assert abs(w - 1.0) < 1e-6
+
+
+def test_binding_triplet_geometry():
+    from scipy.spatial import cKDTree
+    from synth.configs import binding_triplet
+    cx, rec, lig = binding_triplet(n_rec=80, n_lig=30, spacing=2.0)
+    for d in (cx, rec, lig):
+        t = d["surfaces"][0]["tris"]
+        assert closed_and_oriented(t)
+        assert signed_volume(d["surfaces"][0]["verts"], t) > 0
+    dmin = cKDTree(rec["charges"]["xyz"]).query(lig["charges"]["xyz"])[0].min()
+    assert abs(dmin - 3.0) < 1e-6
+    assert cx["charges"]["q"].size == rec["charges"]["q"].size + lig["charges"]["q"].size
