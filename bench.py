@@ -177,6 +177,33 @@ def _problem():
     return protein_problem()
 
 
+FLEET = 64          # ligands of the batched-solve measurement
+TRIPLET = (8000, 1500)
+
+
+def _fleet_member(args):
+    from synth.configs import fleet_ligand
+    i, n = args
+    return fleet_ligand(i, n)
+
+
+def _triplet_member(which):
+    from synth.configs import binding_triplet
+    return binding_triplet(*TRIPLET)[which]
+
+
+def _batch_inputs():
+    """The ligand fleet and the binding triplet, generated in a spawned process pool."""
+    import multiprocessing as mp
+    from synth.configs import fleet_sizes
+    sizes = fleet_sizes(FLEET)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        tri = pool.map_async(_triplet_member, [0, 1, 2])
+        fleet = pool.map(_fleet_member, list(enumerate(sizes)))
+        triplet = tri.get()
+    return fleet, triplet
+
+
 # ---------------------------------------------------------------- reference arm (CPU oracle)
 def run_reference(args):
     ws, rank = _dist()
@@ -233,6 +260,7 @@ def cpu_baseline(d):
 
 # ---------------------------------------------------------------- GPU arm
 def run_gpu(args):
+    fleet, triplet = _batch_inputs() if args.extras else (None, None)
     import torch
     ws, rank = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -329,6 +357,10 @@ def run_gpu(args):
     r64 = p64.solve()
     rel_err = abs(r.dG_solv - r64.dG_solv) / abs(r64.dG_solv)
 
+    extras = {}
+    if args.extras:
+        extras = _extras(pbbem, ctx, pb, r, d, fleet, triplet)
+
     if rank == 0:
         cpu = cpu_baseline(d)
         line = {
@@ -354,10 +386,54 @@ def run_gpu(args):
                     "d2h_bytes_per_step": int(d2h), "seconds_per_step": float(np.mean(e2e_t))},
             "gpu_launches": int(launches), "clocks": clocks,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _extras(pbbem, ctx, pb, r, d, fleet, triplet):
+    """Adjoint gradient of the bench problem, a batched fleet solve and a binding energy."""
+    t0 = time.perf_counter()
+    g1 = pb.gradient()
+    first = time.perf_counter() - t0
+    g = pb.gradient()
+    q = d["charges"]["q"]
+    grad = {"workload": WORKLOAD, "grad_ms": g["grad_ms"], "first_call_ms": 1e3 * first,
+            "solve_ms": r.solve_ms + r.setup_ms, "adjoint_iterations": g["iterations"],
+            "q_dq_over_2E": float(q @ g["dq"]) / (2 * r.dG_solv),
+            "dE_deps": g["deps"].tolist(), "dE_dkappa": g["dkappa"].tolist()}
+    probs = [pbbem.Problem.from_dict(ctx, f) for f in fleet]
+    for p in probs:
+        p.setup(precision="mixed", **PARAMS)
+    pbbem.solve_batch(ctx, probs)
+    ts = time.perf_counter()
+    seq = [p.solve() for p in probs]
+    t_seq = time.perf_counter() - ts
+    ts = time.perf_counter()
+    bat = pbbem.solve_batch(ctx, probs)
+    t_bat = time.perf_counter() - ts
+    pairs = sum(x.p2p_pairs * x.matvecs for x in bat)
+    panels = [int(f["surfaces"][0]["tris"].shape[0]) for f in fleet]
+    batch = {"workload": f"{FLEET} synthetic ligands, 300-3000 atoms, {min(panels)}-{max(panels)} panels",
+             "panels_total": int(sum(panels)), "sequential_s": t_seq, "batch_s": t_bat,
+             "speedup_batch_vs_sequential": t_seq / t_bat, "ginteractions_per_s": pairs / t_bat / 1e9,
+             "same_energies": all(a.dG_solv == b.dG_solv for a, b in zip(seq, bat))}
+    for p in probs:
+        p.close()
+    tri = [pbbem.Problem.from_dict(ctx, t) for t in triplet]
+    ts = time.perf_counter()
+    for p in tri:
+        p.setup(precision="mixed", **PARAMS)
+    ddG = pbbem.binding_energy(ctx, *tri)
+    t_bind = time.perf_counter() - ts
+    binding = {"workload": f"receptor {TRIPLET[0]} atoms, ligand {TRIPLET[1]} atoms, complex",
+               "panels": [int(t["surfaces"][0]["tris"].shape[0]) for t in triplet], "ddG_kJ_mol": ddG,
+               "setup_and_solve_s": t_bind}
+    for p in tri:
+        p.close()
+    return {"gradient": grad, "batch": batch, "binding": binding}
 
 
 def main():
@@ -366,6 +442,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the gradient, batched-fleet and binding-energy measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

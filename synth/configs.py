@@ -177,12 +177,18 @@ def binding_triplet(n_rec=8000, n_lig=1500, seed=4, spacing=PROTEIN_SPACING, gap
             _molecule_problem(lxyz, lig["radius"], lig["q"], spacing))
 
 
+def fleet_sizes(count=64, n_min=300, n_max=3000, seed=4):
+    """Atom counts of a ligand fleet: log-uniform in [n_min, n_max]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [int(n) for n in np.exp(rng.uniform(np.log(n_min), np.log(n_max), size=count)).astype(int)]
+
+
+def fleet_ligand(i, n_atoms, seed=4, spacing=PROTEIN_SPACING):
+    """Ligand i of a fleet: n_atoms atoms drawn with seed + 1 + i."""
+    at = synthetic_atoms(int(n_atoms), _ball_radius(int(n_atoms)), seed + 1 + i)
+    return _molecule_problem(at["xyz"], at["radius"], at["q"], spacing)
+
+
 def ligand_fleet(count=64, n_min=300, n_max=3000, seed=4, spacing=PROTEIN_SPACING):
     """`count` synthetic ligands with atom counts log-uniform in [n_min, n_max] (seed + 1 + i each)."""
-    rng = np.random.Generator(np.random.PCG64(seed))
-    sizes = np.exp(rng.uniform(np.log(n_min), np.log(n_max), size=count)).astype(int)
-    out = []
-    for i, n in enumerate(sizes):
-        at = synthetic_atoms(int(n), _ball_radius(int(n)), seed + 1 + i)
-        out.append(_molecule_problem(at["xyz"], at["radius"], at["q"], spacing))
-    return out
+    return [fleet_ligand(i, n, seed, spacing) for i, n in enumerate(fleet_sizes(count, n_min, n_max, seed))]

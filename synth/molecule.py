@@ -229,12 +229,13 @@ def gaussian_surface(xyz, radius, spacing: float, radius_offset: float = 0.0,
     rho = _density_grid(xyz, r, lo, spacing, shape, beta=beta)
     v, t = marching_tetrahedra(rho, lo, spacing)
     v, t = outer_component(v, t)
-    if smooth_iters:
-        v = smooth_on_level_set(v, t, xyz, r, beta=beta, iters=smooth_iters)
-        # smoothing must not fold a triangle over: outward normals still point down the density
-        a, b, c = v[t[:, 0]], v[t[:, 1]], v[t[:, 2]]
+    # smoothing must not fold a triangle over (outward normals still point down
+    # the density); where it would, fewer rounds are used, down to none
+    for it in range(smooth_iters, 0, -1):
+        vs = smooth_on_level_set(v, t, xyz, r, beta=beta, iters=it)
+        a, b, c = vs[t[:, 0]], vs[t[:, 1]], vs[t[:, 2]]
         nrm = np.cross(b - a, c - a)
         _, g = density_and_gradient((a + b + c) / 3.0, xyz, r, beta)
-        if np.any(np.einsum("ij,ij->i", nrm, g) >= 0.0):
-            raise RuntimeError("surface smoothing inverted a triangle; use a finer grid")
+        if not np.any(np.einsum("ij,ij->i", nrm, g) >= 0.0):
+            return vs, t.astype(np.int32)
     return v, t.astype(np.int32)
