@@ -1227,7 +1227,7 @@ void apply_tpairs(pb_problem *pb, std::vector<TPair> &list, const double *u, dou
                 if (mixed) launch_m2pT_typed<float>(prm.P, yuk, tp, G, n64, n32, Tr, tp.mom32.p, k, tp.L.m2p_part32.p, s);
                 else launch_m2pT_typed<double>(prm.P, yuk, tp, G, n64, n32, Tr, tp.mom64.p, k, tp.L.m2p_part64.p, s);
             }
-        launch_gather(tp.L, G, mixed, false, u0, u0, s);
+        launch_gather(tp.L, G, mixed, false, u0, u0, nullptr, s);
     }
     for (int t = 0; t < ns; ++t) {
         TComb tc{};

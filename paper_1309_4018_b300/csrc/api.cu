@@ -81,10 +81,21 @@ Params resolve(const pb_params *p) {
     return r;
 }
 
-int find_pair(std::vector<Pair> &v, int tgt, int tree) {
+// Index of the (tgt, tree) pair in v, appending it if new; a pair of the
+// previous setup with the same surfaces (in `old`) is reused with its buffers.
+int find_pair(std::vector<Pair> &v, std::vector<Pair> &old, int tgt, int tree) {
     for (size_t i = 0; i < v.size(); ++i)
         if (v[i].tgt == tgt && v[i].tree == tree) return (int)i;
-    v.emplace_back();
+    bool reused = false;
+    for (auto &o : old)
+        if (o.tgt == tgt && o.tree == tree) {
+            v.push_back(std::move(o));
+            o.tgt = -1;
+            v.back().kappas.clear();
+            reused = true;
+            break;
+        }
+    if (!reused) v.emplace_back();
     v.back().tgt = tgt;
     v.back().tree = tree;
     return (int)v.size() - 1;
@@ -114,9 +125,15 @@ void setup_problem(pb_problem *pb) {
     }
     upload_rules();
     upload_term_tables();
-    pb->S.clear(); pb->T.clear(); pb->G.clear(); pb->pairs.clear(); pb->cpairs.clear();
-    pb->S.resize(ns);
-    pb->T.resize(ns);
+    // geometry, trees and pairs of a previous setup keep their device buffers
+    if (pb->S.size() != (size_t)ns) {
+        pb->S.clear(); pb->T.clear(); pb->G.clear();
+        pb->S.resize(ns);
+        pb->T.resize(ns);
+    }
+    std::vector<Pair> old_pairs = std::move(pb->pairs), old_cpairs = std::move(pb->cpairs);
+    pb->pairs.clear();
+    pb->cpairs.clear();
     pb->off.assign(ns + 1, 0);
     for (int t = 0; t < ns; ++t) {
         SurfDev &S = pb->S[t];
@@ -151,7 +168,7 @@ void setup_problem(pb_problem *pb) {
                 if (!in && !out) continue;
                 const double sigma = in ? 1.0 : -1.0;
                 const double cc = in ? 1.0 : eps(pb->S[t].inner) / eps(R);
-                const int pi = find_pair(pb->pairs, sf, t);
+                const int pi = find_pair(pb->pairs, old_pairs, sf, t);
                 const int ki = kernel_slot(pb->pairs[pi], pb->regions[R].kappa);
                 pb->rows[2 * sf + side].push_back(Term{pi, ki, sigma, -sigma * cc, R});
             }
@@ -166,7 +183,7 @@ void setup_problem(pb_problem *pb) {
             if (!in && !out) continue;
             const double sigma = in ? 1.0 : -1.0;
             const double cc = in ? 1.0 : eps(pb->S[t].inner) / eps(Rc);
-            const int pi = find_pair(pb->cpairs, ns, t);
+            const int pi = find_pair(pb->cpairs, old_cpairs, ns, t);
             const int ki = kernel_slot(pb->cpairs[pi], pb->regions[Rc].kappa);
             pb->reac.push_back(Term{pi, ki, -sigma, sigma * cc, Rc});
         }
@@ -251,7 +268,11 @@ void setup_problem(pb_problem *pb) {
         if (!sa[0] || !sa[1]) fail(PB_EINVAL, "internal: missing self block");
         block_jacobi_inverse(pb->S[sf].n, cv[0], sa[0], cv[1], sa[1], pb->minv.p + 4 * pb->off[sf], s);
     }
-    // moments for every tree with a far field, so that no operator application allocates
+    // moments for every tree with a far field, and the FP32 densities, so that no
+    // operator application allocates (it may be captured into a CUDA graph)
+    for (int t = 0; t < ns; ++t) {
+        if (prm.precision == PB_MIXED) pb->T[t].phf.alloc(pb->S[t].n);
+    }
     for (int t = 0; t < ns; ++t)
         if (pb->need_far[t]) {
             const size_t nm = (size_t)pb->T[t].nnodes * 2 * nterms(prm.P);
@@ -293,7 +314,7 @@ void apply_operator(pb_problem *pb, const double *xd, double *yd, PhaseEvents *p
     mark(3);
     for (auto &P : pb->pairs) {
         const double *phi = xd + 2 * pb->off[P.tree];
-        launch_gather(P, pb->G[P.tgt], mixed, P.tgt == P.tree, phi, phi + pb->S[P.tree].n, s);
+        launch_gather(P, pb->G[P.tgt], mixed, P.tgt == P.tree, phi, phi + pb->S[P.tree].n, pb->T[P.tree].phf.p, s);
     }
     mark(4);
     for (int sf = 0; sf < ns; ++sf) {
@@ -338,7 +359,7 @@ void reaction(pb_problem *pb, const double *xd) {
         const double *phi = xd + 2 * pb->off[P.tree];
         launch_p2p(P, G, Tr, false, mixed, s);
         launch_m2p(P, G, Tr, prm.P, mixed, s);
-        launch_gather(P, G, mixed, false, phi, phi + pb->S[P.tree].n, s);
+        launch_gather(P, G, mixed, false, phi, phi + pb->S[P.tree].n, pb->T[P.tree].phf.p, s);
     }
     CombineRow row{};
     row.nterm = (int)pb->reac.size();
@@ -653,6 +674,12 @@ int pb_ctx_create(int device, pb_ctx **out) {
         if (device < 0 || device >= nd) fail(PB_EINVAL, "no such CUDA device");
         set_device(c.get());
         PB_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        // stream-ordered temporaries come back from the device's pool without
+        // returning memory to the driver at every synchronisation
+        cudaMemPool_t mp = nullptr;
+        PB_CUDA_TRY(cudaDeviceGetDefaultMemPool(&mp, device));
+        uint64_t keep = UINT64_MAX;
+        PB_CUDA_TRY(cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep));
         PB_CUDA_TRY(cudaEventCreate(&c->ev0));
         PB_CUDA_TRY(cudaEventCreate(&c->ev1));
     });

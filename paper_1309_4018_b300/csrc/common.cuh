@@ -52,16 +52,18 @@ extern std::atomic<long long> g_launches;
 inline void fail(int code, const std::string &m) { throw Error{code, m}; }
 
 // ---------------------------------------------------------------- device buffer
+// Device array owned by the library.  alloc() keeps the existing allocation
+// when it is large enough (a re-setup of the same geometry allocates nothing).
 template <typename T>
 struct DevBuf {
     T *p = nullptr;
-    size_t n = 0;
+    size_t n = 0, cap = 0;
     DevBuf() = default;
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
-    DevBuf(DevBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DevBuf(DevBuf &&o) noexcept : p(o.p), n(o.n), cap(o.cap) { o.p = nullptr; o.n = 0; o.cap = 0; }
     DevBuf &operator=(DevBuf &&o) noexcept {
-        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        if (this != &o) { release(); p = o.p; n = o.n; cap = o.cap; o.p = nullptr; o.n = 0; o.cap = 0; }
         return *this;
     }
     ~DevBuf() { release(); }
@@ -69,9 +71,13 @@ struct DevBuf {
         if (p) cudaFree(p);
         p = nullptr;
         n = 0;
+        cap = 0;
     }
     void alloc(size_t count) {
-        if (count == n && p) return;
+        if (p && count <= cap && count > 0) {
+            n = count;
+            return;
+        }
         release();
         if (count == 0) return;
         cudaError_t e = cudaMalloc(&p, count * sizeof(T));
@@ -80,6 +86,7 @@ struct DevBuf {
             throw Error{PB_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed"};
         }
         n = count;
+        cap = count;
     }
     void zero(cudaStream_t s) {
         if (n) PB_CUDA_TRY(cudaMemsetAsync(p, 0, n * sizeof(T), s));
@@ -97,25 +104,29 @@ struct DevBuf {
 template <typename T>
 struct PinnedBuf {
     T *p = nullptr;
+    size_t cap = 0;
     PinnedBuf() = default;
     PinnedBuf(const PinnedBuf &) = delete;
     PinnedBuf &operator=(const PinnedBuf &) = delete;
-    PinnedBuf(PinnedBuf &&o) noexcept : p(o.p) { o.p = nullptr; }
+    PinnedBuf(PinnedBuf &&o) noexcept : p(o.p), cap(o.cap) { o.p = nullptr; o.cap = 0; }
     PinnedBuf &operator=(PinnedBuf &&o) noexcept {
-        if (this != &o) { release(); p = o.p; o.p = nullptr; }
+        if (this != &o) { release(); p = o.p; cap = o.cap; o.p = nullptr; o.cap = 0; }
         return *this;
     }
     ~PinnedBuf() { release(); }
     void release() {
         if (p) cudaFreeHost(p);
         p = nullptr;
+        cap = 0;
     }
     void alloc(size_t count) {
+        if (p && count <= cap) return;
         release();
         if (cudaMallocHost(&p, count * sizeof(T)) != cudaSuccess) {
             p = nullptr;
             throw Error{PB_ENOMEM, "cudaMallocHost failed"};
         }
+        cap = count;
     }
 };
 

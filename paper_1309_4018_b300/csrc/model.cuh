@@ -56,6 +56,7 @@ struct Tree {
     // per-evaluation source strengths
     DevBuf<double> src64;            // npts * 8: x, y, z, s, dx, dy, dz, pid
     DevBuf<float4> srcA32, srcB32;   // (x, y, z, s) and (dx, dy, dz, pid bits)
+    DevBuf<float2> phf;              // (phi, dphi) per panel in FP32 (mixed path)
     DevBuf<double> mom64;            // nnodes * 2 * nterms: M then D
     DevBuf<float> mom32;
 };
@@ -64,6 +65,7 @@ struct Tree {
 struct Targets {
     int64_t n = 0;
     int surface = -1;                // -1: charges
+    DevBuf<uint64_t> keys;           // sorted Morton keys of the positions
     DevBuf<double> xs;               // sorted positions n * 3
     DevBuf<int32_t> order;           // sorted position -> input index
     DevBuf<int32_t> rank;            // input index -> sorted position

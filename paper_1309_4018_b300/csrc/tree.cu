@@ -277,19 +277,19 @@ __global__ void inv_fill_kernel(int64_t nent, const int32_t *__restrict__ owner,
     pos[e] = (int32_t)p;
 }
 
-__global__ void item_count_kernel(int nkeys, const int64_t *__restrict__ off, int32_t *__restrict__ nitems) {
+__global__ void item_count_kernel(int nkeys, const int64_t *__restrict__ off, int per, int32_t *__restrict__ nitems) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nkeys) return;
-    nitems[k] = (int)((off[k + 1] - off[k] + 31) / 32);
+    nitems[k] = (int)((off[k + 1] - off[k] + per - 1) / per);
 }
 
-__global__ void item_fill_kernel(int nkeys, const int64_t *__restrict__ off, const int64_t *__restrict__ ioff,
+__global__ void item_fill_kernel(int nkeys, const int64_t *__restrict__ off, const int64_t *__restrict__ ioff, int per,
                                  int4 *__restrict__ items) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nkeys) return;
     const int64_t c = off[k + 1] - off[k];
-    for (int64_t w = 0; 32 * w < c; ++w)
-        items[ioff[k] + w] = make_int4(k, (int)(off[k] + 32 * w), (int)(c - 32 * w < 32 ? c - 32 * w : 32), 0);
+    for (int64_t w = 0; per * w < c; ++w)
+        items[ioff[k] + w] = make_int4(k, (int)(off[k] + per * w), (int)(c - per * w < per ? c - per * w : per), 0);
 }
 
 // ---------------------------------------------------------------- near-singular lists
@@ -637,8 +637,7 @@ void build_targets(Targets &G, const double *d_x, int64_t n, int surface, cudaSt
     G.n = n;
     G.surface = surface;
     double corner[3], side;
-    DevBuf<uint64_t> keys;
-    morton_sort(d_x, n, s, corner, side, keys, G.order);
+    morton_sort(d_x, n, s, corner, side, G.keys, G.order);
     G.xs.alloc(3 * n);
     G.self_panel.alloc(n);
     G.rank.alloc(n);
@@ -652,11 +651,11 @@ void build_targets(Targets &G, const double *d_x, int64_t n, int surface, cudaSt
 
 void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
                  cudaStream_t s) {
-    build_far_lists(Pr, G, T, prm, s);
+    build_far_lists(Pr, G, T, prm, s, 32);
     build_near_lists(Pr, G, T, src, prm, use_self, s);
 }
 
-void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &prm, cudaStream_t s) {
+void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &prm, cudaStream_t s, int p2p_per_item) {
     const int64_t m = G.n;
     TmpBuf<int32_t> mc(m, s), pc(m, s), err(1, s);
     PB_CUDA_TRY(cudaMemsetAsync(err.p, 0, 4, s));
@@ -702,7 +701,7 @@ void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &pr
         Pr.p2p_pairs = (int64_t)h;
     }
     // entry-major grouping of the lists
-    auto group = [&](const int64_t *ptr, const int32_t *ent, const int32_t *remap, int nkeys, int64_t nent,
+    auto group = [&](const int64_t *ptr, const int32_t *ent, const int32_t *remap, int nkeys, int64_t nent, int per,
                      DevBuf<int32_t> &inv, DevBuf<int32_t> &pos, DevBuf<int4> &items, int64_t &nitems) {
         TmpBuf<int32_t> cnt(std::max(1, nkeys), s), cursor(std::max(1, nkeys), s), nit(std::max(1, nkeys), s);
         TmpBuf<int64_t> off(nkeys + 1, s), ioff(nkeys + 1, s);
@@ -722,17 +721,18 @@ void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &pr
             inv_fill_kernel<<<div_up(nent, 256), 256, 0, s>>>(nent, owner.p, ent, remap, off.p, cursor.p, inv.p, pos.p);
             PB_LAUNCH_CHECK();
         }
-        item_count_kernel<<<div_up(nkeys, 128), 128, 0, s>>>(nkeys, off.p, nit.p);
+        item_count_kernel<<<div_up(nkeys, 128), 128, 0, s>>>(nkeys, off.p, per, nit.p);
         PB_LAUNCH_CHECK();
         exclusive_scan_i32_to_i64(nit.p, ioff.p, nkeys, s);
         nitems = read_i64(ioff.p + nkeys, s);
         items.alloc(std::max<int64_t>(1, nitems));
-        item_fill_kernel<<<div_up(nkeys, 128), 128, 0, s>>>(nkeys, off.p, ioff.p, items.p);
+        item_fill_kernel<<<div_up(nkeys, 128), 128, 0, s>>>(nkeys, off.p, ioff.p, per, items.p);
         PB_LAUNCH_CHECK();
     };
-    group(Pr.p2p_ptr.p, Pr.p2p_node.p, T.node_leaf.p, T.nleaves, Pr.n_p2p, Pr.p2p_inv, Pr.p2p_pos, Pr.p2p_items,
+    group(Pr.p2p_ptr.p, Pr.p2p_node.p, T.node_leaf.p, T.nleaves, Pr.n_p2p, p2p_per_item, Pr.p2p_inv, Pr.p2p_pos,
+          Pr.p2p_items,
           Pr.n_p2p_items);
-    group(Pr.m2p_ptr.p, Pr.m2p_node.p, nullptr, T.nnodes, Pr.n_m2p, Pr.m2p_inv, Pr.m2p_pos, Pr.m2p_items,
+    group(Pr.m2p_ptr.p, Pr.m2p_node.p, nullptr, T.nnodes, Pr.n_m2p, 32, Pr.m2p_inv, Pr.m2p_pos, Pr.m2p_items,
           Pr.n_m2p_items);
 }
 

@@ -21,8 +21,10 @@ void build_targets(Targets &G, const double *d_x, int64_t n, int surface, cudaSt
 // the panels of the tree's own surface, so each skips its own panel.
 void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
                  cudaStream_t s);
-// The traversal (M2P / P2P lists, direct-sum pair count, entry-major items) alone.
-void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &prm, cudaStream_t s);
+// The traversal (M2P / P2P lists, direct-sum pair count, entry-major items) alone;
+// P2P items hold up to p2p_per_item (32 or 64) (target, leaf) pairs, M2P items 32.
+void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &prm, cudaStream_t s,
+                     int p2p_per_item = 32);
 // The near-singular lists of targets G against the panels of src (after build_far_lists).
 void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
                       cudaStream_t s);

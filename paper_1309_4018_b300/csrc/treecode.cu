@@ -70,6 +70,14 @@ __global__ void strengths32_kernel(int64_t n, const float4 *__restrict__ pos, co
                        __int_as_float(j));
 }
 
+// FP32 copies of (phi, dphi) per panel, read by the mixed-precision gather's
+// near-field terms (one conversion per panel instead of one per near entry).
+__global__ void phi32_kernel(int64_t n, const double *__restrict__ phi, const double *__restrict__ dphi,
+                             float2 *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2((float)phi[i], (float)dphi[i]);
+}
+
 // ---------------------------------------------------------------- P2M (leaves)
 template <typename T>
 struct SrcView;
@@ -98,18 +106,36 @@ struct SrcView<float> {
 
 constexpr int kP2MChunk = 128;
 
-// One block per leaf: each thread computes the powers of one source's offset
-// from the leaf centre (128 sources per chunk), then each thread owns up to 4
-// moment terms and sums over the chunk's sources in order (deterministic).
+// Four consecutive shared-memory values as one (float) or two (double) 16-byte loads.
 template <typename T>
-__global__ void __launch_bounds__(128) p2m_kernel(int nleaves, const int32_t *__restrict__ leaf_node,
+struct Quad {
+    T x, y, z, w;
+};
+__device__ __forceinline__ Quad<float> ld4(const float *p) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Quad<double> ld4(const double *p) {
+    const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+    return {a.x, a.y, b.x, b.y};
+}
+
+// One block per leaf.  Each chunk of sources is staged in shared memory as
+// the powers of its offsets from the leaf centre (zero-padded to a multiple
+// of 4); every thread owns a moment term and a group of 4-source quads
+// (G groups when the terms are few, so all threads work), reads 4 sources per
+// 16-byte load, and the groups' partial sums are added in group order at the
+// end (deterministic).
+template <typename T>
+__global__ void __launch_bounds__(256) p2m_kernel(int nleaves, const int32_t *__restrict__ leaf_node,
                                                   const int64_t *__restrict__ start, const int64_t *__restrict__ count,
                                                   const double *__restrict__ centre, double ox, double oy, double oz,
                                                   SrcView<T> sv, int P, int NT, T *__restrict__ mom) {
     constexpr int CH = sizeof(T) == 4 ? kP2MChunk : kP2MChunk / 2;   // FP64 tiles stay under 48 KB
-    __shared__ T pw[3][kMaxP + 1][CH];
-    __shared__ T sd[4][CH];
+    __shared__ __align__(16) T pw[3][kMaxP + 1][CH];
+    __shared__ __align__(16) T sd[4][CH];
     __shared__ int sterm[3 * 455];
+    __shared__ T part[2][2][128];
     const int node = leaf_node[blockIdx.x];
     const int64_t s0 = start[node], cnt = count[node];
     T c[3];
@@ -119,46 +145,81 @@ __global__ void __launch_bounds__(128) p2m_kernel(int nleaves, const int32_t *__
         c[0] = (T)(centre[3 * node] - ox); c[1] = (T)(centre[3 * node + 1] - oy); c[2] = (T)(centre[3 * node + 2] - oz);
     }
     for (int i = threadIdx.x; i < 3 * NT; i += blockDim.x) sterm[i] = c_terms[i];
-    T accM[4] = {0, 0, 0, 0}, accD[4] = {0, 0, 0, 0};
+    const int G = NT <= 85 ? 3 : NT <= 128 ? 2 : 1;
+    const int g = G > 1 ? threadIdx.x / NT : 0;
+    int kk[2] = {G > 1 ? threadIdx.x % NT : threadIdx.x, threadIdx.x + 256};
+    const int nk = G > 1 ? (g < G ? 1 : 0) : (kk[1] < NT ? 2 : (kk[0] < NT ? 1 : 0));
+    T accM[2] = {0, 0}, accD[2] = {0, 0};
     for (int64_t c0 = 0; c0 < cnt; c0 += CH) {
         const int m = (int)(cnt - c0 < CH ? cnt - c0 : CH);
+        const int m4 = (m + 3) >> 2;
         __syncthreads();
-        if (threadIdx.x < m) {
-            T x, y, z, s, dx, dy, dz;
-            sv.get(s0 + c0 + threadIdx.x, c, x, y, z, s, dx, dy, dz);
+        if (threadIdx.x < 4 * m4) {
+            const int j = threadIdx.x;
+            T x = 0, y = 0, z = 0, st = 0, dx = 0, dy = 0, dz = 0;
+            if (j < m) sv.get(s0 + c0 + j, c, x, y, z, st, dx, dy, dz);
             T px = 1, py = 1, pz = 1;
             for (int e = 0; e <= P; ++e) {
-                pw[0][e][threadIdx.x] = px; pw[1][e][threadIdx.x] = py; pw[2][e][threadIdx.x] = pz;
+                pw[0][e][j] = px; pw[1][e][j] = py; pw[2][e][j] = pz;
                 px *= x; py *= y; pz *= z;
             }
-            sd[0][threadIdx.x] = s; sd[1][threadIdx.x] = dx; sd[2][threadIdx.x] = dy; sd[3][threadIdx.x] = dz;
+            sd[0][j] = st; sd[1][j] = dx; sd[2][j] = dy; sd[3][j] = dz;
         }
         __syncthreads();
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int k = threadIdx.x + 128 * r;
-            if (k >= NT) break;
+        for (int r = 0; r < nk; ++r) {
+            const int k = kk[r];
             const int k1 = sterm[3 * k], k2 = sterm[3 * k + 1], k3 = sterm[3 * k + 2];
             T aM = accM[r], aD = accD[r];
-            for (int j = 0; j < m; ++j) {
-                const T p1 = pw[0][k1][j], p2 = pw[1][k2][j], p3 = pw[2][k3][j];
-                aM += sd[0][j] * (p1 * p2 * p3);
-                T dsum = 0;
-                if (k1) dsum += sd[1][j] * (T)k1 * pw[0][k1 - 1][j] * p2 * p3;
-                if (k2) dsum += sd[2][j] * (T)k2 * p1 * pw[1][k2 - 1][j] * p3;
-                if (k3) dsum += sd[3][j] * (T)k3 * p1 * p2 * pw[2][k3 - 1][j];
-                aD += dsum;
+            for (int q = g; q < m4; q += G) {
+                const int j = 4 * q;
+                const Quad<T> p1 = ld4(&pw[0][k1][j]), p2 = ld4(&pw[1][k2][j]), p3 = ld4(&pw[2][k3][j]);
+                const Quad<T> s = ld4(&sd[0][j]);
+                const Quad<T> m12 = {p1.x * p2.x, p1.y * p2.y, p1.z * p2.z, p1.w * p2.w};
+                aM += s.x * (m12.x * p3.x) + s.y * (m12.y * p3.y) + s.z * (m12.z * p3.z) + s.w * (m12.w * p3.w);
+                if (k1) {
+                    const Quad<T> q1 = ld4(&pw[0][k1 - 1][j]), d = ld4(&sd[1][j]);
+                    const T f = (T)k1;
+                    aD += f * (d.x * q1.x * p2.x * p3.x + d.y * q1.y * p2.y * p3.y + d.z * q1.z * p2.z * p3.z +
+                               d.w * q1.w * p2.w * p3.w);
+                }
+                if (k2) {
+                    const Quad<T> q2 = ld4(&pw[1][k2 - 1][j]), d = ld4(&sd[2][j]);
+                    const T f = (T)k2;
+                    aD += f * (d.x * p1.x * q2.x * p3.x + d.y * p1.y * q2.y * p3.y + d.z * p1.z * q2.z * p3.z +
+                               d.w * p1.w * q2.w * p3.w);
+                }
+                if (k3) {
+                    const Quad<T> q3 = ld4(&pw[2][k3 - 1][j]), d = ld4(&sd[3][j]);
+                    const T f = (T)k3;
+                    aD += f * (d.x * m12.x * q3.x + d.y * m12.y * q3.y + d.z * m12.z * q3.z + d.w * m12.w * q3.w);
+                }
             }
             accM[r] = aM;
             accD[r] = aD;
         }
     }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int k = threadIdx.x + 128 * r;
-        if (k >= NT) break;
-        mom[(int64_t)node * 2 * NT + k] = accM[r];
-        mom[(int64_t)node * 2 * NT + NT + k] = accD[r];
+    if (G > 1) {
+        // groups 1.. hand their sums to group 0, which adds them in order
+        __syncthreads();
+        if (nk && g > 0) {
+            part[g - 1][0][kk[0]] = accM[0];
+            part[g - 1][1][kk[0]] = accD[0];
+        }
+        __syncthreads();
+        if (nk && g == 0) {
+            T aM = accM[0], aD = accD[0];
+            for (int h = 1; h < G; ++h) {
+                aM += part[h - 1][0][kk[0]];
+                aD += part[h - 1][1][kk[0]];
+            }
+            mom[(int64_t)node * 2 * NT + kk[0]] = aM;
+            mom[(int64_t)node * 2 * NT + NT + kk[0]] = aD;
+        }
+    } else {
+        for (int r = 0; r < nk; ++r) {
+            mom[(int64_t)node * 2 * NT + kk[r]] = accM[r];
+            mom[(int64_t)node * 2 * NT + NT + kk[r]] = accD[r];
+        }
     }
 }
 
@@ -631,7 +692,8 @@ struct NearArgs32 {
     const double *selfV[2];
     const int32_t *selfp;
     int use_self;
-    const double *phi, *dphi;
+    const float2 *phf;      // (phi, dphi) of the source surface in FP32
+    const double *dphi;     // FP64 dphi for the self term
 };
 
 template <typename TM, int NK>
@@ -730,7 +792,8 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
         }
     for (int64_t e = nr.ptr[t] + lane; e < nr.ptr[t + 1]; e += 32) {
         const int j = nr.panel[e];
-        const float ph = (float)nr.phi[j], dph = (float)nr.dphi[j];
+        const float2 pd = nr.phf[j];
+        const float ph = pd.x, dph = pd.y;
 #pragma unroll
         for (int a = 0; a < NK; ++a) {
             two_add(nh[2 * a], nl[2 * a], nr.dV[a][e] * dph);
@@ -841,6 +904,9 @@ void compute_strengths(Tree &Tr, const SurfDev &S, const double *phi, const doub
     const int64_t n = Tr.npts;
     if (!n) return;
     if (mixed) {
+        Tr.phf.alloc(S.n);
+        phi32_kernel<<<div_up(S.n, 256), 256, 0, s>>>(S.n, phi, dphi, Tr.phf.p);
+        PB_LAUNCH_CHECK();
         strengths32_kernel<<<div_up(n, 256), 256, 0, s>>>(n, Tr.pos32.p, Tr.was.p, Tr.pids.p, S.nrm.p, phi, dphi,
                                                           Tr.srcA32.p, Tr.srcB32.p);
     } else {
@@ -855,12 +921,12 @@ void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s) {
     if (mixed) {
         Tr.mom32.alloc((size_t)Tr.nnodes * 2 * NT);
         SrcView<float> sv{Tr.srcA32.p, Tr.srcB32.p};
-        p2m_kernel<float><<<Tr.nleaves, 128, 0, s>>>(Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p,
+        p2m_kernel<float><<<Tr.nleaves, 256, 0, s>>>(Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p,
                                                      Tr.origin[0], Tr.origin[1], Tr.origin[2], sv, P, NT, Tr.mom32.p);
     } else {
         Tr.mom64.alloc((size_t)Tr.nnodes * 2 * NT);
         SrcView<double> sv{Tr.src64.p};
-        p2m_kernel<double><<<Tr.nleaves, 128, 0, s>>>(Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p,
+        p2m_kernel<double><<<Tr.nleaves, 256, 0, s>>>(Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p,
                                                       Tr.origin[0], Tr.origin[1], Tr.origin[2], sv, P, NT, Tr.mom64.p);
     }
     PB_LAUNCH_CHECK();
@@ -953,7 +1019,7 @@ void launch_m2p(const Pair &Pr, const Targets &G, const Tree &Tr, int P, bool mi
 }
 
 void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, const double *phi,
-                   const double *dphi, cudaStream_t s) {
+                   const double *dphi, const float2 *phf, cudaStream_t s) {
     const int64_t ntg = G.n;
     if (!ntg) return;
     const int nk = (int)Pr.kappas.size();
@@ -971,8 +1037,9 @@ void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, 
         }
         nr.selfp = G.self_panel.p;
         nr.use_self = use_self ? 1 : 0;
-        nr.phi = phi;
+        nr.phf = phf;
         nr.dphi = dphi;
+        if (Pr.n_near > 0 && !phf) fail(PB_EINVAL, "internal: FP32 densities missing");
         const float *mp = far ? Pr.m2p_part32.p : nullptr;
         if (nk == 1)
             gather32_kernel<1><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_pos.p, Pr.p2p_part32.p, Pr.m2p_ptr.p,

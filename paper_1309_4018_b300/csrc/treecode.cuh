@@ -30,8 +30,10 @@ void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self,
 void launch_m2p(const Pair &Pr, const Targets &G, const Tree &Tr, int P, bool mixed, cudaStream_t s);
 // Pr.VK = each target's partials, plus its near-singular corrections and (use_self)
 // its own panel's semi-analytical term, with phi, dphi of the source surface (overwrites).
+// phf: FP32 (phi, dphi) of the source surface (the tree's phf after
+// compute_strengths), read on the mixed path; may be null without near entries.
 void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, const double *phi,
-                   const double *dphi, cudaStream_t s);
+                   const double *dphi, const float2 *phf, cudaStream_t s);
 // y[i] = half * phi_s[i] (0 if phi_s is null) + sum_terms (cK K + cV V)[rank[i]] for i < n.
 // FP32 target positions relative to the tree origin (mixed path).
 void targets_to_float(Pair &Pr, const Targets &G, const Tree &Tr, cudaStream_t s);
