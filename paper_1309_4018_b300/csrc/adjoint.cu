@@ -205,6 +205,18 @@ struct TKSet {
     float kap[2];
 };
 
+// Single-instruction PTX approximations (flush-to-zero), as in the forward P2P.
+__device__ __forceinline__ float tfast_rsqrt(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float tfast_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ void tcomp_add(float &hi, float &lo, float v) {
     const float t = hi + v;
     lo += (fabsf(hi) >= fabsf(v)) ? ((hi - t) + v) : ((v - t) + hi);
@@ -213,7 +225,8 @@ __device__ __forceinline__ void tcomp_add(float &hi, float &lo, float v) {
 
 template <int NK, bool Y0, bool Y1>
 __global__ void __launch_bounds__(128) p2pT32_kernel(int64_t nitems, const int4 *__restrict__ items,
-                                                     const int32_t *__restrict__ inv, const float4 *__restrict__ x32,
+                                                     const int32_t *__restrict__ inv,
+                                                     const int32_t *__restrict__ sent, const float4 *__restrict__ x32,
                                                      const float4 *__restrict__ n32, const int32_t *__restrict__ selfp,
                                                      int use_self, const int32_t *__restrict__ leaf_node,
                                                      const int64_t *__restrict__ start,
@@ -259,7 +272,7 @@ __global__ void __launch_bounds__(128) p2pT32_kernel(int64_t nitems, const int4 
                 const float4 b = sB[warp][j];
                 const float dx = a.x - tx, dy = a.y - ty, dz = a.z - tz;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float iv = (__float_as_int(b.w) == me) ? 0.f : rsqrtf(r2);
+                const float iv = (__float_as_int(b.w) == me) ? 0.f : tfast_rsqrt(r2);
                 const float rn = fmaf(dx, nx, fmaf(dy, ny, dz * nz));
                 const float i3 = iv * iv * iv;
                 if (!Y0) {
@@ -267,7 +280,7 @@ __global__ void __launch_bounds__(128) p2pT32_kernel(int64_t nitems, const int4 
                     p[1] = fmaf(b.x * rn, i3, p[1]);
                 } else {
                     const float rho = r2 * iv;
-                    const float ex = exp2f(l2e0 * rho);
+                    const float ex = tfast_ex2(l2e0 * rho);
                     p[0] = fmaf(a.w * iv, ex, p[0]);
                     p[1] = fmaf(b.x * rn * i3 * ex, fmaf(k0, rho, 1.f), p[1]);
                 }
@@ -277,7 +290,7 @@ __global__ void __launch_bounds__(128) p2pT32_kernel(int64_t nitems, const int4 
                         p[3] = fmaf(b.z * rn, i3, p[3]);
                     } else {
                         const float rho = r2 * iv;
-                        const float ex = exp2f(l2e1 * rho);
+                        const float ex = tfast_ex2(l2e1 * rho);
                         p[2] = fmaf(b.y * iv, ex, p[2]);
                         p[3] = fmaf(b.z * rn * i3 * ex, fmaf(k1, rho, 1.f), p[3]);
                     }
@@ -289,7 +302,7 @@ __global__ void __launch_bounds__(128) p2pT32_kernel(int64_t nitems, const int4 
         __syncwarp();
     }
     if (valid) {
-        float2 *rec = reinterpret_cast<float2 *>(part + (int64_t)2 * NK * slot);
+        float2 *rec = reinterpret_cast<float2 *>(part + (int64_t)2 * NK * sent[slot]);
 #pragma unroll
         for (int a = 0; a < NK; ++a) rec[a] = make_float2(hi[2 * a] + lo[2 * a], hi[2 * a + 1] + lo[2 * a + 1]);
     }
@@ -297,7 +310,8 @@ __global__ void __launch_bounds__(128) p2pT32_kernel(int64_t nitems, const int4 
 
 template <int NK, bool Y0, bool Y1>
 __global__ void __launch_bounds__(128) p2pT64_kernel(int64_t nitems, const int4 *__restrict__ items,
-                                                     const int32_t *__restrict__ inv, const double *__restrict__ xs,
+                                                     const int32_t *__restrict__ inv,
+                                                     const int32_t *__restrict__ sent, const double *__restrict__ xs,
                                                      const double *__restrict__ n64, const int32_t *__restrict__ selfp,
                                                      int use_self, const int32_t *__restrict__ leaf_node,
                                                      const int64_t *__restrict__ start,
@@ -364,7 +378,7 @@ __global__ void __launch_bounds__(128) p2pT64_kernel(int64_t nitems, const int4 
         __syncwarp();
     }
     if (valid) {
-        double2 *rec = reinterpret_cast<double2 *>(part + (int64_t)2 * NK * slot);
+        double2 *rec = reinterpret_cast<double2 *>(part + (int64_t)2 * NK * sent[slot]);
 #pragma unroll
         for (int a = 0; a < NK; ++a) rec[a] = make_double2(acc[2 * a], acc[2 * a + 1]);
     }
@@ -1109,7 +1123,7 @@ void launch_p2pT(const TPair &tp, const Targets &G, const double *n64, const flo
     if (mixed) {
         TKSet ks{{(float)k0, (float)k1}};
 #define PB_P2PT32(NK, A_, B_)                                                                                   \
-    p2pT32_kernel<NK, A_, B_><<<grid, 128, 0, s>>>(ni, Pr.p2p_items.p, Pr.p2p_inv.p, Pr.x32.p, n32,            \
+    p2pT32_kernel<NK, A_, B_><<<grid, 128, 0, s>>>(ni, Pr.p2p_items.p, Pr.p2p_inv.p, Pr.p2p_ent.p, Pr.x32.p, n32, \
                                                    G.self_panel.p, us, Tr.leaf_node.p, Tr.start.p, Tr.count.p, \
                                                    tp.srcA32.p, tp.srcB32.p, ks, Pr.p2p_part32.p)
         if (nk == 1) { if (y0) PB_P2PT32(1, true, false); else PB_P2PT32(1, false, false); }
@@ -1120,7 +1134,8 @@ void launch_p2pT(const TPair &tp, const Targets &G, const double *n64, const flo
 #undef PB_P2PT32
     } else {
 #define PB_P2PT64(NK, A_, B_)                                                                                    \
-    p2pT64_kernel<NK, A_, B_><<<grid, 128, 0, s>>>(ni, Pr.p2p_items.p, Pr.p2p_inv.p, G.xs.p, n64, G.self_panel.p, \
+    p2pT64_kernel<NK, A_, B_><<<grid, 128, 0, s>>>(ni, Pr.p2p_items.p, Pr.p2p_inv.p, Pr.p2p_ent.p, G.xs.p, n64,    \
+                                                   G.self_panel.p,                                                \
                                                    us, Tr.leaf_node.p, Tr.start.p, Tr.count.p, tp.src64.p, k0,   \
                                                    k1, Pr.p2p_part.p)
         if (nk == 1) { if (y0) PB_P2PT64(1, true, false); else PB_P2PT64(1, false, false); }

@@ -265,16 +265,21 @@ __global__ void inv_count_kernel(int64_t nent, const int32_t *__restrict__ ent, 
 }
 
 // The order of the pairs inside one key's group does not matter: every pair
-// writes its own partial, and the gather reads them back in list order.
+// writes its own partial record, and the gather reads them back in list
+// order.  by_entry: the record of grouped position p goes to its list entry
+// (map[p] = entry; the gather then reads each target's records contiguously);
+// otherwise it stays at p and map[entry] = p tells the gather where.
 __global__ void inv_fill_kernel(int64_t nent, const int32_t *__restrict__ owner, const int32_t *__restrict__ ent,
                                 const int32_t *__restrict__ remap, const int64_t *__restrict__ off,
-                                int32_t *__restrict__ cursor, int32_t *__restrict__ inv, int32_t *__restrict__ pos) {
+                                int32_t *__restrict__ cursor, int by_entry, int32_t *__restrict__ inv,
+                                int32_t *__restrict__ map) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nent) return;
     const int key = remap ? remap[ent[e]] : ent[e];
     const int64_t p = off[key] + atomicAdd(&cursor[key], 1);
     inv[p] = owner[e];
-    pos[e] = (int32_t)p;
+    if (by_entry) map[p] = (int32_t)e;
+    else map[e] = (int32_t)p;
 }
 
 __global__ void item_count_kernel(int nkeys, const int64_t *__restrict__ off, int per, int32_t *__restrict__ nitems) {
@@ -702,6 +707,7 @@ void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &pr
     }
     // entry-major grouping of the lists
     auto group = [&](const int64_t *ptr, const int32_t *ent, const int32_t *remap, int nkeys, int64_t nent, int per,
+                     int by_entry,
                      DevBuf<int32_t> &inv, DevBuf<int32_t> &pos, DevBuf<int4> &items, int64_t &nitems) {
         TmpBuf<int32_t> cnt(std::max(1, nkeys), s), cursor(std::max(1, nkeys), s), nit(std::max(1, nkeys), s);
         TmpBuf<int64_t> off(nkeys + 1, s), ioff(nkeys + 1, s);
@@ -718,7 +724,8 @@ void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &pr
         }
         exclusive_scan_i32_to_i64(cnt.p, off.p, nkeys, s);
         if (m && nent) {
-            inv_fill_kernel<<<div_up(nent, 256), 256, 0, s>>>(nent, owner.p, ent, remap, off.p, cursor.p, inv.p, pos.p);
+            inv_fill_kernel<<<div_up(nent, 256), 256, 0, s>>>(nent, owner.p, ent, remap, off.p, cursor.p, by_entry,
+                                                              inv.p, pos.p);
             PB_LAUNCH_CHECK();
         }
         item_count_kernel<<<div_up(nkeys, 128), 128, 0, s>>>(nkeys, off.p, per, nit.p);
@@ -729,10 +736,10 @@ void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &pr
         item_fill_kernel<<<div_up(nkeys, 128), 128, 0, s>>>(nkeys, off.p, ioff.p, per, items.p);
         PB_LAUNCH_CHECK();
     };
-    group(Pr.p2p_ptr.p, Pr.p2p_node.p, T.node_leaf.p, T.nleaves, Pr.n_p2p, p2p_per_item, Pr.p2p_inv, Pr.p2p_pos,
+    group(Pr.p2p_ptr.p, Pr.p2p_node.p, T.node_leaf.p, T.nleaves, Pr.n_p2p, p2p_per_item, 1, Pr.p2p_inv, Pr.p2p_ent,
           Pr.p2p_items,
           Pr.n_p2p_items);
-    group(Pr.m2p_ptr.p, Pr.m2p_node.p, nullptr, T.nnodes, Pr.n_m2p, 32, Pr.m2p_inv, Pr.m2p_pos, Pr.m2p_items,
+    group(Pr.m2p_ptr.p, Pr.m2p_node.p, nullptr, T.nnodes, Pr.n_m2p, 32, 0, Pr.m2p_inv, Pr.m2p_pos, Pr.m2p_items,
           Pr.n_m2p_items);
 }
 

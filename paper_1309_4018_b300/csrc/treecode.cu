@@ -23,6 +23,7 @@
 // recurrence of Duan & Krasny, with kappa > 0 the screened-Coulomb form of
 // Li, Johnston & Krasny that the paper cites.
 #include <algorithm>
+#include <type_traits>
 
 #include "treecode.cuh"
 
@@ -302,6 +303,20 @@ struct KSet {
     float kap[2];
 };
 
+// Single-instruction special-function unit approximations (PTX rsqrt.approx,
+// ex2.approx, flush-to-zero): relative error ~2^-22, below the FP32 rounding
+// of the sums they feed.
+__device__ __forceinline__ float fast_rsqrt(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float fast_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ void comp_add(float &hi, float &lo, float v) {
     const float t = hi + v;
     lo += (fabsf(hi) >= fabsf(v)) ? ((hi - t) + v) : ((v - t) + hi);
@@ -315,7 +330,8 @@ __device__ __forceinline__ void comp_add(float &hi, float &lo, float v) {
 // stored in FP64 at its grouped position.
 template <int NK, bool Y0, bool Y1>
 __global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, const int4 *__restrict__ items,
-                                                    const int32_t *__restrict__ inv, int64_t npart,
+                                                    const int32_t *__restrict__ inv,
+                                                    const int32_t *__restrict__ sent,
                                                     const float4 *__restrict__ x32,
                                                     const int32_t *__restrict__ selfp, int use_self,
                                                     const int32_t *__restrict__ leaf_node,
@@ -362,7 +378,7 @@ __global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, const int4 *
                 const float4 b = sB[warp][j];
                 const float dx = tx - a.x, dy = ty - a.y, dz = tz - a.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float inv = (__float_as_int(b.w) == me) ? 0.f : rsqrtf(r2);
+                const float inv = (__float_as_int(b.w) == me) ? 0.f : fast_rsqrt(r2);
                 const float sv = a.w * inv;
                 const float rd = fmaf(dx, b.x, fmaf(dy, b.y, dz * b.z));
                 const float kv = rd * (inv * inv * inv);
@@ -371,7 +387,7 @@ __global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, const int4 *
                     p[1] += kv;
                 } else {
                     const float rho = r2 * inv;
-                    const float ex = exp2f(l2e0 * rho);
+                    const float ex = fast_ex2(l2e0 * rho);
                     p[0] = fmaf(sv, ex, p[0]);
                     p[1] = fmaf(kv * ex, fmaf(k0, rho, 1.f), p[1]);
                 }
@@ -381,7 +397,7 @@ __global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, const int4 *
                         p[3] += kv;
                     } else {
                         const float rho = r2 * inv;
-                        const float ex = exp2f(l2e1 * rho);
+                        const float ex = fast_ex2(l2e1 * rho);
                         p[2] = fmaf(sv, ex, p[2]);
                         p[3] = fmaf(kv * ex, fmaf(k1, rho, 1.f), p[3]);
                     }
@@ -394,7 +410,7 @@ __global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, const int4 *
     }
     if (valid) {
         // interleaved record of the entry: (V0, K0[, V1, K1]), the compensated pair rounded once
-        float2 *rec = reinterpret_cast<float2 *>(part + (int64_t)2 * NK * slot);
+        float2 *rec = reinterpret_cast<float2 *>(part + (int64_t)2 * NK * sent[slot]);
 #pragma unroll
         for (int a = 0; a < NK; ++a) rec[a] = make_float2(hi[2 * a] + lo[2 * a], hi[2 * a + 1] + lo[2 * a + 1]);
     }
@@ -403,7 +419,8 @@ __global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, const int4 *
 // ---------------------------------------------------------------- P2P, FP64
 template <int NK, bool Y0, bool Y1>
 __global__ void __launch_bounds__(128) p2p64_kernel(int64_t nitems, const int4 *__restrict__ items,
-                                                    const int32_t *__restrict__ inv, int64_t npart,
+                                                    const int32_t *__restrict__ inv,
+                                                    const int32_t *__restrict__ sent,
                                                     const double *__restrict__ xs, const int32_t *__restrict__ selfp,
                                                     int use_self, const int32_t *__restrict__ leaf_node,
                                                     const int64_t *__restrict__ start, const int64_t *__restrict__ count,
@@ -470,7 +487,7 @@ __global__ void __launch_bounds__(128) p2p64_kernel(int64_t nitems, const int4 *
         __syncwarp();
     }
     if (valid) {
-        double2 *rec = reinterpret_cast<double2 *>(part + (int64_t)2 * NK * slot);
+        double2 *rec = reinterpret_cast<double2 *>(part + (int64_t)2 * NK * sent[slot]);
 #pragma unroll
         for (int a = 0; a < NK; ++a) rec[a] = make_double2(acc[2 * a], acc[2 * a + 1]);
     }
@@ -614,7 +631,7 @@ __device__ void m2p_eval_rt(int P, T ux, T uy, T uz, T kappa, const T *__restric
 // stores (V, K) at the pair's grouped position.
 template <int P, bool YUK, typename T>
 __global__ void __launch_bounds__(128) m2p_kernel(int64_t nitems, const int4 *__restrict__ items,
-                                                  const int32_t *__restrict__ inv, int64_t npart, int Prt,
+                                                  const int32_t *__restrict__ inv, int Prt,
                                                   const double *__restrict__ xs, const float4 *__restrict__ x32,
                                                   const double *__restrict__ centre, const float4 *__restrict__ cen32,
                                                   const T *__restrict__ mom, double kappa, int kslot, int nk,
@@ -698,7 +715,6 @@ struct NearArgs32 {
 
 template <typename TM, int NK>
 __global__ void __launch_bounds__(128) gather_kernel(int64_t ntg, const int64_t *__restrict__ p2p_ptr,
-                                                     const int32_t *__restrict__ p2p_pos,
                                                      const double *__restrict__ p2p_part,
                                                      const int64_t *__restrict__ m2p_ptr,
                                                      const int32_t *__restrict__ m2p_pos,
@@ -711,7 +727,7 @@ __global__ void __launch_bounds__(128) gather_kernel(int64_t ntg, const int64_t 
 #pragma unroll
     for (int a = 0; a < 2 * NK; ++a) { acc[a] = 0.0; far[a] = 0.0; }
     for (int64_t e = p2p_ptr[t] + lane; e < p2p_ptr[t + 1]; e += 32) {
-        const double2 *rec = reinterpret_cast<const double2 *>(p2p_part + (int64_t)2 * NK * p2p_pos[e]);
+        const double2 *rec = reinterpret_cast<const double2 *>(p2p_part + (int64_t)2 * NK * e);
 #pragma unroll
         for (int a = 0; a < NK; ++a) {
             const double2 v = rec[a];
@@ -767,7 +783,6 @@ __device__ __forceinline__ void two_add(float &hi, float &lo, float v) {
 
 template <int NK>
 __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_t *__restrict__ p2p_ptr,
-                                                       const int32_t *__restrict__ p2p_pos,
                                                        const float *__restrict__ p2p_part,
                                                        const int64_t *__restrict__ m2p_ptr,
                                                        const int32_t *__restrict__ m2p_pos,
@@ -779,17 +794,45 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
     float hi[2 * NK], lo[2 * NK], nh[2 * NK], nl[2 * NK];
 #pragma unroll
     for (int a = 0; a < 2 * NK; ++a) { hi[a] = 0.f; lo[a] = 0.f; nh[a] = 0.f; nl[a] = 0.f; }
-    for (int64_t e = p2p_ptr[t] + lane; e < p2p_ptr[t + 1]; e += 32) {
-        const float *rec = p2p_part + (int64_t)2 * NK * p2p_pos[e];
-#pragma unroll
-        for (int a = 0; a < 2 * NK; ++a) two_add(hi[a], lo[a], rec[a]);
-    }
-    if (m2p_part)
-        for (int64_t e = m2p_ptr[t] + lane; e < m2p_ptr[t + 1]; e += 32) {
-            const float *rec = m2p_part + (int64_t)2 * NK * m2p_pos[e];
-#pragma unroll
-            for (int a = 0; a < 2 * NK; ++a) two_add(hi[a], lo[a], rec[a]);
+    // records as one 16-byte (two kernels) or 8-byte load each; four per lane in flight
+    using Rec = typename std::conditional<NK == 2, float4, float2>::type;
+    auto add_rec = [&](const Rec &r) {
+        two_add(hi[0], lo[0], r.x);
+        two_add(hi[1], lo[1], r.y);
+        if constexpr (NK == 2) {
+            two_add(hi[2 % (2 * NK)], lo[2 % (2 * NK)], r.z);
+            two_add(hi[3 % (2 * NK)], lo[3 % (2 * NK)], r.w);
         }
+    };
+    {
+        const Rec *pr = reinterpret_cast<const Rec *>(p2p_part);
+        const int64_t e1 = p2p_ptr[t + 1];
+        for (int64_t e = p2p_ptr[t] + lane; e < e1; e += 128) {
+            Rec r[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e + 32 * u < e1) r[u] = pr[e + 32 * u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e + 32 * u < e1) add_rec(r[u]);
+        }
+    }
+    if (m2p_part) {
+        const Rec *pr = reinterpret_cast<const Rec *>(m2p_part);
+        const int64_t e1 = m2p_ptr[t + 1];
+        for (int64_t e = m2p_ptr[t] + lane; e < e1; e += 128) {
+            int q[4];
+            Rec r[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) q[u] = e + 32 * u < e1 ? m2p_pos[e + 32 * u] : -1;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (q[u] >= 0) r[u] = pr[q[u]];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (q[u] >= 0) add_rec(r[u]);
+        }
+    }
     for (int64_t e = nr.ptr[t] + lane; e < nr.ptr[t + 1]; e += 32) {
         const int j = nr.panel[e];
         const float2 pd = nr.phf[j];
@@ -849,9 +892,8 @@ void launch_m2p_typed(int P, bool yuk, const Pair &Pr, const double *xs, const d
                       const T *mom, double kappa, int kslot, int nk, T *part, cudaStream_t s) {
     const int64_t ni = Pr.n_m2p_items;
     const unsigned grid = (unsigned)((ni + 3) / 4);
-    const int64_t np = Pr.n_m2p;
 #define PB_M2P_ARGS \
-    ni, Pr.m2p_items.p, Pr.m2p_inv.p, np, P, xs, Pr.x32.p, Tr.centre.p, Tr.cen32.p, mom, kappa, kslot, nk, part
+    ni, Pr.m2p_items.p, Pr.m2p_inv.p, P, xs, Pr.x32.p, Tr.centre.p, Tr.cen32.p, mom, kappa, kslot, nk, part
 #define PB_M2P_CASE(PP)                                                                                  \
     case PP:                                                                                             \
         if (yuk) m2p_kernel<PP, true, T><<<grid, 128, 0, s>>>(PB_M2P_ARGS);                              \
@@ -957,11 +999,10 @@ void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self,
     const bool y0 = k0 != 0.0, y1 = k1 != 0.0;
     const int32_t *sp = G.self_panel.p;
     const int us = use_self ? 1 : 0;
-    const int64_t np = Pr.n_p2p;
     if (mixed) {
         KSet ks{{(float)k0, (float)k1}};
 #define PB_P2P32(NK, A, B)                                                                                      \
-    p2p32_kernel<NK, A, B><<<grid, 128, 0, s>>>(ni, Pr.p2p_items.p, Pr.p2p_inv.p, np, Pr.x32.p, sp, us,          \
+    p2p32_kernel<NK, A, B><<<grid, 128, 0, s>>>(ni, Pr.p2p_items.p, Pr.p2p_inv.p, Pr.p2p_ent.p, Pr.x32.p, sp, us, \
                                                 Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.srcA32.p, Tr.srcB32.p, ks, \
                                                 Pr.p2p_part32.p)
         if (nk == 1) { if (y0) PB_P2P32(1, true, false); else PB_P2P32(1, false, false); }
@@ -972,7 +1013,7 @@ void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self,
 #undef PB_P2P32
     } else {
 #define PB_P2P64(NK, A, B)                                                                                       \
-    p2p64_kernel<NK, A, B><<<grid, 128, 0, s>>>(ni, Pr.p2p_items.p, Pr.p2p_inv.p, np, G.xs.p, sp, us,             \
+    p2p64_kernel<NK, A, B><<<grid, 128, 0, s>>>(ni, Pr.p2p_items.p, Pr.p2p_inv.p, Pr.p2p_ent.p, G.xs.p, sp, us,   \
                                                 Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.src64.p, k0, k1,      \
                                                 Pr.p2p_part.p)
         if (nk == 1) { if (y0) PB_P2P64(1, true, false); else PB_P2P64(1, false, false); }
@@ -1042,11 +1083,11 @@ void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, 
         if (Pr.n_near > 0 && !phf) fail(PB_EINVAL, "internal: FP32 densities missing");
         const float *mp = far ? Pr.m2p_part32.p : nullptr;
         if (nk == 1)
-            gather32_kernel<1><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_pos.p, Pr.p2p_part32.p, Pr.m2p_ptr.p,
-                                                    Pr.m2p_pos.p, mp, nr, V0, V1);
+            gather32_kernel<1><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_part32.p, Pr.m2p_ptr.p, Pr.m2p_pos.p, mp, nr,
+                                                    V0, V1);
         else
-            gather32_kernel<2><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_pos.p, Pr.p2p_part32.p, Pr.m2p_ptr.p,
-                                                    Pr.m2p_pos.p, mp, nr, V0, V1);
+            gather32_kernel<2><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_part32.p, Pr.m2p_ptr.p, Pr.m2p_pos.p, mp, nr,
+                                                    V0, V1);
     } else {
         NearArgs nr{};
         nr.ptr = Pr.near_ptr.p;
@@ -1062,11 +1103,11 @@ void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, 
         nr.dphi = dphi;
         const double *mp = far ? Pr.m2p_part64.p : nullptr;
         if (nk == 1)
-            gather_kernel<double, 1><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_pos.p, Pr.p2p_part.p, Pr.m2p_ptr.p,
-                                                          Pr.m2p_pos.p, mp, nr, V0, V1);
+            gather_kernel<double, 1><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_part.p, Pr.m2p_ptr.p, Pr.m2p_pos.p, mp,
+                                                          nr, V0, V1);
         else
-            gather_kernel<double, 2><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_pos.p, Pr.p2p_part.p, Pr.m2p_ptr.p,
-                                                          Pr.m2p_pos.p, mp, nr, V0, V1);
+            gather_kernel<double, 2><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_part.p, Pr.m2p_ptr.p, Pr.m2p_pos.p, mp,
+                                                          nr, V0, V1);
     }
     PB_LAUNCH_CHECK();
 }
