@@ -515,8 +515,9 @@ __device__ __forceinline__ void m2p_eval(T ux, T uy, T uz, T kappa, const T *__r
     K = a[0] * mom[NT];
 #pragma unroll
     for (int n = 1; n <= P; ++n) {
-        const T c1 = (T)(2 * n - 1) / (T)n, c2 = (T)(n - 1) / (T)n;
-        const T kn = kappa / (T)n;
+        // the order's constants folded with -1/r^2
+        const T C1 = -(T)(2 * n - 1) / (T)n * ir2, C2 = -(T)(n - 1) / (T)n * ir2;
+        const T kn = kappa / (T)n, KN = -kn * ir2;
 #pragma unroll
         for (int k1 = n; k1 >= 0; --k1) {
 #pragma unroll
@@ -530,9 +531,9 @@ __device__ __forceinline__ void m2p_eval(T ux, T uy, T uz, T kappa, const T *__r
                 if (k1 >= 2) { s2 += a[term_index(k1 - 2, k2, k3)]; if (YUK) t2 += b[term_index(k1 - 2, k2, k3)]; }
                 if (k2 >= 2) { s2 += a[term_index(k1, k2 - 2, k3)]; if (YUK) t2 += b[term_index(k1, k2 - 2, k3)]; }
                 if (k3 >= 2) { s2 += a[term_index(k1, k2, k3 - 2)]; if (YUK) t2 += b[term_index(k1, k2, k3 - 2)]; }
-                T ai = c1 * s1 + c2 * s2;
-                if (YUK) ai += kn * (t1 + t2);
-                a[i] = -ai * ir2;
+                T ai = C1 * s1 + C2 * s2;
+                if (YUK) ai += KN * (t1 + t2);
+                a[i] = ai;
                 if (YUK) b[i] = -kn * (s1 + s2);
                 V += a[i] * mom[i];
                 K += a[i] * mom[NT + i];
@@ -564,8 +565,9 @@ __device__ __forceinline__ void m2p_eval_ly(T ux, T uy, T uz, T kappa, const T *
     }
 #pragma unroll
     for (int n = 1; n <= P; ++n) {
-        const T c1 = (T)(2 * n - 1) / (T)n, c2 = (T)(n - 1) / (T)n;
-        const T kn = kappa / (T)n;
+        // the order's constants folded with -1/r^2
+        const T C1 = -(T)(2 * n - 1) / (T)n * ir2, C2 = -(T)(n - 1) / (T)n * ir2;
+        const T kn = kappa / (T)n, KN = -kn * ir2;
 #pragma unroll
         for (int k1 = n; k1 >= 0; --k1) {
 #pragma unroll
@@ -579,8 +581,8 @@ __device__ __forceinline__ void m2p_eval_ly(T ux, T uy, T uz, T kappa, const T *
                 if (k1 >= 2) { const int j = term_index(k1 - 2, k2, k3); s2 += a[j]; y2 += ay[j]; t2 += b[j]; }
                 if (k2 >= 2) { const int j = term_index(k1, k2 - 2, k3); s2 += a[j]; y2 += ay[j]; t2 += b[j]; }
                 if (k3 >= 2) { const int j = term_index(k1, k2, k3 - 2); s2 += a[j]; y2 += ay[j]; t2 += b[j]; }
-                a[i] = -(c1 * s1 + c2 * s2) * ir2;
-                ay[i] = -(c1 * y1 + c2 * y2 + kn * (t1 + t2)) * ir2;
+                a[i] = C1 * s1 + C2 * s2;
+                ay[i] = C1 * y1 + C2 * y2 + KN * (t1 + t2);
                 b[i] = -kn * (y1 + y2);
                 const T m = mom[i], d = mom[NT + i];
                 VL += a[i] * m;
