@@ -21,8 +21,9 @@
 // monopole moments M^k = sum_i mu_i (x_i - x_c)^k is sum_k a^k(u) M^k with
 // u = x_c - y and the coefficients a^k of the forward treecode, and its
 // target-normal derivative is
-//   n . grad_y phi = -sum_{1 <= |m| <= P+1} a^m sum_l n_l m_l N^(m - e_l),
-// which needs the coefficients up to order P + 1.  The near-singular and
+//   n . grad_y phi = -sum_{1 <= |m| <= P} a^m sum_l n_l m_l N^(m - e_l),
+// truncated like the forward double layer (whose dipole moments pair order-P
+// coefficients with order-(P-1) source monomials).  The near-singular and
 // self corrections of the forward operator enter transposed.
 //
 // Kernel derivatives (r = x - y, rho = |r|, e = exp(-kappa rho), all / 4 pi):
@@ -385,13 +386,12 @@ __global__ void __launch_bounds__(128) p2pT64_kernel(int64_t nitems, const int4 
 }
 
 // ---------------------------------------------------------------- transposed M2P
-// V = sum_{|k| <= P} a^k M^k and K = -sum_{1 <= |m| <= P+1} a^m sum_l n_l m_l N^(m - e_l)
-// with the forward recurrences for a^k (and b^k, the coefficients of
-// exp(-kappa r)) carried one order further.
+// V = sum_{|k| <= P} a^k M^k and K = -sum_{1 <= |m| <= P} a^m sum_l n_l m_l N^(m - e_l)
+// with the forward recurrences for a^k (and b^k, the coefficients of exp(-kappa r)).
 template <int P, bool YUK, typename T>
 __device__ __forceinline__ void m2pT_eval(T ux, T uy, T uz, T nx, T ny, T nz, T kappa, const T *__restrict__ mM,
                                           const T *__restrict__ mN, T &V, T &K) {
-    constexpr int NT1 = (P + 2) * (P + 3) * (P + 4) / 6;
+    constexpr int NT1 = (P + 1) * (P + 2) * (P + 3) / 6;
     T a[NT1];
     T b[YUK ? NT1 : 1];
     const T r2 = ux * ux + uy * uy + uz * uz;
@@ -407,7 +407,7 @@ __device__ __forceinline__ void m2pT_eval(T ux, T uy, T uz, T nx, T ny, T nz, T 
     V = a[0] * mM[0];
     K = 0;
 #pragma unroll
-    for (int n = 1; n <= P + 1; ++n) {
+    for (int n = 1; n <= P; ++n) {
         const T c1 = (T)(2 * n - 1) / (T)n, c2 = (T)(n - 1) / (T)n;
         const T kn = kappa / (T)n;
 #pragma unroll
@@ -427,7 +427,7 @@ __device__ __forceinline__ void m2pT_eval(T ux, T uy, T uz, T nx, T ny, T nz, T 
                 if (YUK) ai += kn * (t1 + t2);
                 a[i] = -ai * ir2;
                 if (YUK) b[i] = -kn * (s1 + s2);
-                if (n <= P) V += a[i] * mM[i];
+                V += a[i] * mM[i];
                 T g = 0;
                 if (k1 >= 1) g += nx * (T)k1 * mN[tindex(k1 - 1, k2, k3)];
                 if (k2 >= 1) g += ny * (T)k2 * mN[tindex(k1, k2 - 1, k3)];
@@ -441,9 +441,9 @@ __device__ __forceinline__ void m2pT_eval(T ux, T uy, T uz, T nx, T ny, T nz, T 
 template <bool YUK, typename T>
 __device__ void m2pT_eval_rt(int P, T ux, T uy, T uz, T nx, T ny, T nz, T kappa, const T *__restrict__ mM,
                              const T *__restrict__ mN, T &V, T &K) {
-    const int NT1 = (P + 2) * (P + 3) * (P + 4) / 6;
-    T a[kMaxTerms1];
-    T b[YUK ? kMaxTerms1 : 1];
+    const int NT1 = (P + 1) * (P + 2) * (P + 3) / 6;
+    T a[455];
+    T b[YUK ? 455 : 1];
     const T r2 = ux * ux + uy * uy + uz * uz;
     const T r = sqrt(r2);
     const T ir2 = (T)1 / r2;
@@ -466,7 +466,7 @@ __device__ void m2pT_eval_rt(int P, T ux, T uy, T uz, T nx, T ny, T nz, T kappa,
         if (YUK) ai += kappa / (T)n * (t1 + t2);
         a[i] = -ai * ir2;
         if (YUK) b[i] = -kappa / (T)n * (s1 + s2);
-        if (n <= P) V += a[i] * mM[i];
+        V += a[i] * mM[i];
         T g = 0;
         if (k1 >= 1) g += nx * (T)k1 * mN[tindex(k1 - 1, k2, k3)];
         if (k2 >= 1) g += ny * (T)k2 * mN[tindex(k1, k2 - 1, k3)];
@@ -784,9 +784,9 @@ __global__ void assemble_charges_kernel(int64_t nc, double c0, double inv_eps, c
 // from da^0 = -exp(-kappa r), db^0 = -r exp(-kappa r).
 #define PB_DK_STEP(I, K1, K2, K3, NN)                                                                         \
     {                                                                                                         \
-        const double c1 = (double)(2 * (NN) - 1) / (NN), c2 = (double)((NN) - 1) / (NN), kn = kappa / (NN),    \
-                     in = 1.0 / (NN);                                                                         \
-        double s1 = 0, s2 = 0, t1 = 0, t2 = 0, ds1 = 0, ds2 = 0, dt1 = 0, dt2 = 0;                            \
+        const T c1 = (T)(2 * (NN) - 1) / (T)(NN), c2 = (T)((NN) - 1) / (T)(NN), kn = kappa / (T)(NN),          \
+                in = (T)1 / (T)(NN);                                                                          \
+        T s1 = 0, s2 = 0, t1 = 0, t2 = 0, ds1 = 0, ds2 = 0, dt1 = 0, dt2 = 0;                                 \
         if ((K1) >= 1) { const int j = tindex((K1) - 1, K2, K3); s1 += ux * a[j]; t1 += ux * b[j]; ds1 += ux * da[j]; dt1 += ux * db[j]; } \
         if ((K2) >= 1) { const int j = tindex(K1, (K2) - 1, K3); s1 += uy * a[j]; t1 += uy * b[j]; ds1 += uy * da[j]; dt1 += uy * db[j]; } \
         if ((K3) >= 1) { const int j = tindex(K1, K2, (K3) - 1); s1 += uz * a[j]; t1 += uz * b[j]; ds1 += uz * da[j]; dt1 += uz * db[j]; } \
@@ -801,16 +801,15 @@ __global__ void assemble_charges_kernel(int64_t nc, double c0, double inv_eps, c
         dK += da[I] * mD[I];                                                                                  \
     }
 
-template <int P>
-__device__ __forceinline__ void m2p_dkappa_eval(double ux, double uy, double uz, double kappa,
-                                                const double *__restrict__ mM, const double *__restrict__ mD,
-                                                double &dV, double &dK) {
+template <int P, typename T>
+__device__ __forceinline__ void m2p_dkappa_eval(T ux, T uy, T uz, T kappa, const T *__restrict__ mM,
+                                                const T *__restrict__ mD, T &dV, T &dK) {
     constexpr int NT = (P + 1) * (P + 2) * (P + 3) / 6;
-    double a[NT], b[NT], da[NT], db[NT];
-    const double r2 = ux * ux + uy * uy + uz * uz;
-    const double r = sqrt(r2);
-    const double ir2 = 1.0 / r2;
-    const double e0 = exp(-kappa * r);
+    T a[NT], b[NT], da[NT], db[NT];
+    const T r2 = ux * ux + uy * uy + uz * uz;
+    const T r = sqrt(r2);
+    const T ir2 = (T)1 / r2;
+    const T e0 = exp(-kappa * r);
     a[0] = e0 / r;
     b[0] = e0;
     da[0] = -e0;
@@ -827,6 +826,7 @@ __device__ __forceinline__ void m2p_dkappa_eval(double ux, double uy, double uz,
 
 __device__ void m2p_dkappa_eval_rt(int P, double ux, double uy, double uz, double kappa, const double *__restrict__ mM,
                                    const double *__restrict__ mD, double &dV, double &dK) {
+    using T = double;
     const int NT = (P + 1) * (P + 2) * (P + 3) / 6;
     double a[455], b[455], da[455], db[455];
     const double r2 = ux * ux + uy * uy + uz * uz;
@@ -919,7 +919,7 @@ __global__ void __launch_bounds__(128) dkappa_kernel(DkArgs g, double *__restric
         const double *mM = g.mom + (int64_t)b * 2 * g.NT;
         double dv, dk;
         const double ux = g.centre[3 * b] - x[0], uy = g.centre[3 * b + 1] - x[1], uz = g.centre[3 * b + 2] - x[2];
-        if constexpr (P >= 0) m2p_dkappa_eval<(P >= 0 ? P : 0)>(ux, uy, uz, kap, mM, mM + g.NT, dv, dk);
+        if constexpr (P >= 0) m2p_dkappa_eval<(P >= 0 ? P : 0), double>(ux, uy, uz, kap, mM, mM + g.NT, dv, dk);
         else m2p_dkappa_eval_rt(g.Prt, ux, uy, uz, kap, mM, mM + g.NT, dv, dk);
         fV += dv;
         fK += dk;
@@ -943,6 +943,249 @@ __global__ void __launch_bounds__(128) dkappa_kernel(DkArgs g, double *__restric
         if (g.use_self) V += g.dself[me] * g.dphi[me];
         outV[t] = V;
         outK[t] = Kv;
+    }
+}
+
+// FP32 form of the same (mixed path): the forward FP32 sources (x, y, z, s),
+// (d, pid) and moments of the current solution, targets relative to the tree
+// origin; each lane's FP32 sums are combined in FP64.  The near-singular
+// corrections use panel-relative FP32 coordinates.
+struct Dk32Args {
+    int64_t ntg;
+    const float4 *x32;
+    const int32_t *selfp;
+    int use_self;
+    const int64_t *p2p_ptr;
+    const int32_t *p2p_node;
+    const int64_t *start, *count;
+    const float4 *A, *B;
+    const int64_t *m2p_ptr;
+    const int32_t *m2p_node;
+    const float4 *cen32;
+    const float *mom;
+    int NT;
+    const int64_t *near_ptr;
+    const int32_t *near_panel;
+    const double *xs, *verts;
+    const int32_t *tris;
+    const double *nrm, *area;
+    int slotK, slotF;
+    float kappa;
+    const double *phi, *dphi, *dself;
+};
+
+__device__ void panel_rule_dkappa32(const float xr[3], const float e1[3], const float e2[3], const float n[3],
+                                    float area, const TriRule &R, float kappa, float &dV, float &dK) {
+    float sv = 0.f, sk = 0.f;
+    for (int k = 0; k < R.n; ++k) {
+        const float l1 = (float)R.l[k][1], l2 = (float)R.l[k][2];
+        const float rx = xr[0] - (l1 * e1[0] + l2 * e2[0]);
+        const float ry = xr[1] - (l1 * e1[1] + l2 * e2[1]);
+        const float rz = xr[2] - (l1 * e1[2] + l2 * e2[2]);
+        const float rho = sqrtf(rx * rx + ry * ry + rz * rz);
+        const float rn = rx * n[0] + ry * n[1] + rz * n[2];
+        const float e = __expf(-kappa * rho);
+        const float w = (float)R.w[k] * area;
+        sv -= w * e;
+        sk -= w * kappa * rn * e / rho;
+    }
+    dV = sv * (float)kInv4Pi;
+    dK = sk * (float)kInv4Pi;
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) dkappa32_kernel(Dk32Args g, double *__restrict__ outV,
+                                                       double *__restrict__ outK) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * 4 + warp;
+    if (t >= g.ntg) return;
+    const float4 xt = g.x32[t];
+    const int me = g.use_self ? g.selfp[t] : -1;
+    const float kap = g.kappa;
+    const float l2e = -kap * 1.4426950408889634f;
+    double fV = 0.0, fK = 0.0, nV = 0.0, nK = 0.0;
+    for (int64_t e = g.p2p_ptr[t]; e < g.p2p_ptr[t + 1]; ++e) {
+        const int node = g.p2p_node[e];
+        const int64_t q0 = g.start[node], q1 = q0 + g.count[node];
+        float pv = 0.f, pk = 0.f;
+        for (int64_t q = q0 + lane; q < q1; q += 32) {
+            const float4 a = g.A[q], b = g.B[q];
+            if (__float_as_int(b.w) == me) continue;
+            const float rx = xt.x - a.x, ry = xt.y - a.y, rz = xt.z - a.z;
+            const float r2 = rx * rx + ry * ry + rz * rz;
+            const float iv = rsqrtf(r2);
+            const float ex = exp2f(l2e * r2 * iv);
+            pv -= a.w * ex;
+            pk -= kap * (rx * b.x + ry * b.y + rz * b.z) * ex * iv;
+        }
+        fV += pv;
+        fK += pk;
+    }
+    for (int64_t e = g.m2p_ptr[t] + lane; e < g.m2p_ptr[t + 1]; e += 32) {
+        const int b = g.m2p_node[e];
+        const float4 c = g.cen32[b];
+        const float *mM = g.mom + (int64_t)b * 2 * g.NT;
+        float dv, dk;
+        m2p_dkappa_eval<P, float>(c.x - xt.x, c.y - xt.y, c.z - xt.z, kap, mM, mM + g.NT, dv, dk);
+        fV += dv;
+        fK += dk;
+    }
+    for (int64_t e = g.near_ptr[t] + lane; e < g.near_ptr[t + 1]; e += 32) {
+        const int j = g.near_panel[e];
+        const int a = g.tris[3 * j], b = g.tris[3 * j + 1], c = g.tris[3 * j + 2];
+        float xr[3], e1[3], e2[3], n[3];
+        for (int d = 0; d < 3; ++d) {
+            xr[d] = (float)(g.xs[3 * t + d] - g.verts[3 * a + d]);
+            e1[d] = (float)(g.verts[3 * b + d] - g.verts[3 * a + d]);
+            e2[d] = (float)(g.verts[3 * c + d] - g.verts[3 * a + d]);
+            n[d] = (float)g.nrm[3 * j + d];
+        }
+        float vf, kf, vk, kk;
+        panel_rule_dkappa32(xr, e1, e2, n, (float)g.area[j], c_arules[g.slotF], kap, vf, kf);
+        panel_rule_dkappa32(xr, e1, e2, n, (float)g.area[j], c_arules[g.slotK], kap, vk, kk);
+        nV += (double)(vf - vk) * g.dphi[j];
+        nK += (double)(kf - kk) * g.phi[j];
+    }
+    double V = fV * kInv4Pi + nV, Kv = fK * kInv4Pi + nK;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        V += __shfl_xor_sync(0xffffffffu, V, o);
+        Kv += __shfl_xor_sync(0xffffffffu, Kv, o);
+    }
+    if (lane == 0) {
+        if (g.use_self) V += g.dself[me] * g.dphi[me];
+        outV[t] = V;
+        outK[t] = Kv;
+    }
+}
+
+// FP32 forms of the charge-site sums (mixed path), coordinates relative to an
+// origin near the molecule; every chunk's FP32 sum is combined in FP64.
+// Panel data: (centroid - o, (thres L)^2 padded) and the unit normal; Gauss
+// points (y - o, w A) in input order.
+__global__ void pack_panels32_kernel(int64_t n, int K, const double *__restrict__ cen, const double *__restrict__ L,
+                                     const double *__restrict__ nrm, const double *__restrict__ gy,
+                                     const double *__restrict__ gwa, double thres, double ox, double oy, double oz,
+                                     float4 *__restrict__ pc, float4 *__restrict__ pn, float4 *__restrict__ gp) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double tl = thres * L[j];
+    pc[j] = make_float4((float)(cen[3 * j] - ox), (float)(cen[3 * j + 1] - oy), (float)(cen[3 * j + 2] - oz),
+                        (float)(tl * tl * (1.0 + 1e-3) + 1e-3));
+    pn[j] = make_float4((float)nrm[3 * j], (float)nrm[3 * j + 1], (float)nrm[3 * j + 2], 0.f);
+    for (int q = 0; q < K; ++q) {
+        const int64_t p = j * K + q;
+        gp[p] = make_float4((float)(gy[3 * p] - ox), (float)(gy[3 * p + 1] - oy), (float)(gy[3 * p + 2] - oz),
+                            (float)gwa[p]);
+    }
+}
+
+__device__ __forceinline__ void field_point32(const float r[3], const float4 &y, const float4 &n, float wv, float wk,
+                                              float F[3]) {
+    const float dx = r[0] - y.x, dy = r[1] - y.y, dz = r[2] - y.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float iv = rsqrtf(r2);
+    const float i3 = iv * iv * iv;
+    const float rn = dx * n.x + dy * n.y + dz * n.z;
+    const float c3 = 3.f * rn * i3 * iv * iv;
+    F[0] += -wv * dx * i3 + wk * (n.x * i3 - c3 * dx);
+    F[1] += -wv * dy * i3 + wk * (n.y * i3 - c3 * dy);
+    F[2] += -wv * dz * i3 + wk * (n.z * i3 - c3 * dz);
+}
+
+__global__ void __launch_bounds__(128) reac_field32_kernel(int64_t nc, const double *__restrict__ xyz, double ox,
+                                                           double oy, double oz, int64_t npan, int K, int slotF,
+                                                           const float4 *__restrict__ pc,
+                                                           const float4 *__restrict__ pn,
+                                                           const float4 *__restrict__ gp, const double *__restrict__ cen,
+                                                           const double *__restrict__ L,
+                                                           const double *__restrict__ area,
+                                                           const double *__restrict__ verts,
+                                                           const int32_t *__restrict__ tris, double thres, float cK,
+                                                           float cV, const float2 *__restrict__ phf, int64_t chunk,
+                                                           double *__restrict__ part) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nc) return;
+    const int64_t j0 = (int64_t)blockIdx.y * chunk, j1 = min(npan, j0 + chunk);
+    const double rd[3] = {xyz[3 * k], xyz[3 * k + 1], xyz[3 * k + 2]};
+    const float r[3] = {(float)(rd[0] - ox), (float)(rd[1] - oy), (float)(rd[2] - oz)};
+    float F[3] = {0.f, 0.f, 0.f};
+    for (int64_t j = j0; j < j1; ++j) {
+        const float4 c = pc[j];
+        const float4 n = pn[j];
+        const float2 pd = phf[j];
+        const float sv = cV * pd.y, sk = cK * pd.x;
+        const float dx = r[0] - c.x, dy = r[1] - c.y, dz = r[2] - c.z;
+        bool near = false;
+        if (dx * dx + dy * dy + dz * dz < c.w) {
+            const double ex = rd[0] - cen[3 * j], ey = rd[1] - cen[3 * j + 1], ez = rd[2] - cen[3 * j + 2];
+            const double tl = thres * L[j];
+            near = ex * ex + ey * ey + ez * ez < tl * tl;
+        }
+        if (near) {
+            const TriRule &R = c_arules[slotF];
+            const int a = tris[3 * j], b = tris[3 * j + 1], cc = tris[3 * j + 2];
+            for (int q = 0; q < R.n; ++q) {
+                float4 y;
+                y.x = (float)(R.l[q][0] * verts[3 * a] + R.l[q][1] * verts[3 * b] + R.l[q][2] * verts[3 * cc] - ox);
+                y.y = (float)(R.l[q][0] * verts[3 * a + 1] + R.l[q][1] * verts[3 * b + 1] + R.l[q][2] * verts[3 * cc + 1] -
+                              oy);
+                y.z = (float)(R.l[q][0] * verts[3 * a + 2] + R.l[q][1] * verts[3 * b + 2] + R.l[q][2] * verts[3 * cc + 2] -
+                              oz);
+                const float w = (float)(R.w[q] * area[j]);
+                field_point32(r, y, n, w * sv, w * sk, F);
+            }
+        } else {
+            for (int q = 0; q < K; ++q) {
+                const float4 y = gp[j * K + q];
+                field_point32(r, y, n, y.w * sv, y.w * sk, F);
+            }
+        }
+    }
+    double *o = part + (int64_t)blockIdx.y * 3 * nc;
+    o[k] = F[0]; o[nc + k] = F[1]; o[2 * nc + k] = F[2];
+}
+
+__global__ void pack_colloc32_kernel(int64_t n, const double *__restrict__ cen, const double *__restrict__ w, double ox,
+                                     double oy, double oz, float4 *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = make_float4((float)(cen[3 * i] - ox), (float)(cen[3 * i + 1] - oy), (float)(cen[3 * i + 2] - oz),
+                         (float)w[i]);
+}
+
+__global__ void __launch_bounds__(128) colloc32_kernel(int64_t nc, const double *__restrict__ xyz, double ox,
+                                                       double oy, double oz, int64_t m,
+                                                       const float4 *__restrict__ src, float kappa, int64_t chunk,
+                                                       double *__restrict__ part) {
+    __shared__ float4 tile[128];
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t b0 = (int64_t)blockIdx.y * chunk, b1 = min(m, b0 + chunk);
+    float rx = 0.f, ry = 0.f, rz = 0.f;
+    if (k < nc) { rx = (float)(xyz[3 * k] - ox); ry = (float)(xyz[3 * k + 1] - oy); rz = (float)(xyz[3 * k + 2] - oz); }
+    float P = 0.f, Fx = 0.f, Fy = 0.f, Fz = 0.f, D = 0.f;
+    for (int64_t c0 = b0; c0 < b1; c0 += 128) {
+        __syncthreads();
+        if (c0 + threadIdx.x < b1) tile[threadIdx.x] = src[c0 + threadIdx.x];
+        __syncthreads();
+        const int cnt = (int)min((int64_t)128, b1 - c0);
+        if (k < nc)
+            for (int j = 0; j < cnt; ++j) {
+                const float4 s = tile[j];
+                const float dx = s.x - rx, dy = s.y - ry, dz = s.z - rz;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const float iv = rsqrtf(r2);
+                const float e = kappa == 0.f ? 1.f : __expf(-kappa * r2 * iv);
+                const float g = s.w * e * iv;
+                P += g;
+                const float f = g * (1.f + kappa * r2 * iv) * iv * iv;
+                Fx += f * dx; Fy += f * dy; Fz += f * dz;
+                D -= s.w * e;
+            }
+    }
+    if (k < nc) {
+        double *o = part + (int64_t)blockIdx.y * 5 * nc;
+        o[k] = P; o[nc + k] = Fx; o[2 * nc + k] = Fy; o[3 * nc + k] = Fz; o[4 * nc + k] = D;
     }
 }
 
@@ -1067,6 +1310,22 @@ void prepare_adjoint(pb_problem *pb) {
         PB_LAUNCH_CHECK();
     }
     if (nc > 0) build_tree_points(A->TQ, pb->cxyz_d.p, nullptr, nc, 1, ncritT, s);
+    if (prm.precision == PB_MIXED) {
+        A->pc32.resize(ns);
+        A->pn32.resize(ns);
+        A->gp32.resize(ns);
+        for (int t = 0; t < ns; ++t) {
+            const SurfDev &S = pb->S[t];
+            const double *o = pb->T[t].origin;
+            A->pc32[t].alloc(S.n);
+            A->pn32[t].alloc(S.n);
+            A->gp32[t].alloc(S.n * prm.K);
+            pack_panels32_kernel<<<div_up(S.n, 256), 256, 0, s>>>(S.n, prm.K, S.cen.p, S.L.p, S.nrm.p, S.gy.p, S.gwa.p,
+                                                                  prm.thres, o[0], o[1], o[2], A->pc32[t].p,
+                                                                  A->pn32[t].p, A->gp32[t].p);
+            PB_LAUNCH_CHECK();
+        }
+    }
     for (size_t pi = 0; pi < pb->pairs.size(); ++pi) {
         const Pair &F = pb->pairs[pi];
         A->tp.emplace_back();
@@ -1344,6 +1603,56 @@ void launch_dkappa(pb_problem *pb, const Pair &P, const Targets &G, int kidx, bo
     PB_LAUNCH_CHECK();
 }
 
+void launch_dkappa32(pb_problem *pb, const Pair &P, const Targets &G, int kidx, bool use_self, const double *phi,
+                     const double *dphi, const double *dself, double *outV, double *outK, cudaStream_t s) {
+    const Params &prm = pb->prm;
+    const Tree &Tr = pb->T[P.tree];
+    const SurfDev &S = pb->S[P.tree];
+    Dk32Args g{};
+    g.ntg = G.n;
+    g.x32 = P.x32.p;
+    g.selfp = G.self_panel.p;
+    g.use_self = use_self ? 1 : 0;
+    g.p2p_ptr = P.p2p_ptr.p;
+    g.p2p_node = P.p2p_node.p;
+    g.start = Tr.start.p;
+    g.count = Tr.count.p;
+    g.A = Tr.srcA32.p;
+    g.B = Tr.srcB32.p;
+    g.m2p_ptr = P.m2p_ptr.p;
+    g.m2p_node = P.m2p_node.p;
+    g.cen32 = Tr.cen32.p;
+    g.mom = P.n_m2p > 0 ? Tr.mom32.p : nullptr;
+    g.NT = nterms(prm.P);
+    g.near_ptr = P.near_ptr.p;
+    g.near_panel = P.near_panel.p;
+    g.xs = G.xs.p;
+    g.verts = S.verts.p;
+    g.tris = S.tris.p;
+    g.nrm = S.nrm.p;
+    g.area = S.area.p;
+    g.slotK = rule_slot(prm.K);
+    g.slotF = rule_slot(prm.K_fine);
+    g.kappa = (float)P.kappas[kidx];
+    g.phi = phi;
+    g.dphi = dphi;
+    g.dself = dself;
+    if (!G.n) return;
+    const unsigned grid = (unsigned)div_up(G.n, 4);
+    switch (prm.P) {
+        case 0: dkappa32_kernel<0><<<grid, 128, 0, s>>>(g, outV, outK); break;
+        case 1: dkappa32_kernel<1><<<grid, 128, 0, s>>>(g, outV, outK); break;
+        case 2: dkappa32_kernel<2><<<grid, 128, 0, s>>>(g, outV, outK); break;
+        case 3: dkappa32_kernel<3><<<grid, 128, 0, s>>>(g, outV, outK); break;
+        case 4: dkappa32_kernel<4><<<grid, 128, 0, s>>>(g, outV, outK); break;
+        case 5: dkappa32_kernel<5><<<grid, 128, 0, s>>>(g, outV, outK); break;
+        case 6: dkappa32_kernel<6><<<grid, 128, 0, s>>>(g, outV, outK); break;
+        case 7: dkappa32_kernel<7><<<grid, 128, 0, s>>>(g, outV, outK); break;
+        default: dkappa32_kernel<8><<<grid, 128, 0, s>>>(g, outV, outK); break;
+    }
+    PB_LAUNCH_CHECK();
+}
+
 }  // namespace
 
 void apply_transpose(pb_problem *pb, const double *lam, double *out) {
@@ -1401,12 +1710,15 @@ void energy_gradient(pb_problem *pb, pb_grad *out) {
         }
     }
     rank_dot(A, 2 * pb->N, lam, nullptr, pb->b.p, 1.0, nullptr, 0.0, -1.0 / eps_c, geps + Rc, s);
-    // kappa: derivative kernels of every block, FP64 sums
-    for (int t = 0; t < ns; ++t) {
-        const double *phi = x + 2 * pb->off[t];
-        compute_strengths(pb->T[t], pb->S[t], phi, phi + pb->S[t].n, false, s);
-        if (pb->need_far[t]) upward_pass(pb->T[t], prm.P, false, s);
-    }
+    // kappa: derivative kernels of every block; on the mixed path (P <= 8) in
+    // FP32 on the sources and moments the forward product above left for x
+    const bool dk32 = prm.precision == PB_MIXED && prm.P <= 8;
+    if (!dk32)
+        for (int t = 0; t < ns; ++t) {
+            const double *phi = x + 2 * pb->off[t];
+            compute_strengths(pb->T[t], pb->S[t], phi, phi + pb->S[t].n, false, s);
+            if (pb->need_far[t]) upward_pass(pb->T[t], prm.P, false, s);
+        }
     auto dk_pair = [&](const Pair &P, int pi, bool charges) {
         const Targets &G = pb->G[P.tgt];
         const bool use_self = !charges && P.tgt == P.tree;
@@ -1415,7 +1727,8 @@ void energy_gradient(pb_problem *pb, pb_grad *out) {
         TmpBuf<double> dvk(2 * std::max<int64_t>(1, G.n), s), dself(std::max<int64_t>(1, pb->S[P.tree].n), s);
         for (size_t k = 0; k < P.kappas.size(); ++k) {
             if (use_self) self_integrals_dkappa(pb->S[P.tree], prm.N_k, P.kappas[k], dself.p, s);
-            launch_dkappa(pb, P, G, (int)k, use_self, phi, dphi, dself.p, dvk.p, dvk.p + G.n, s);
+            if (dk32) launch_dkappa32(pb, P, G, (int)k, use_self, phi, dphi, dself.p, dvk.p, dvk.p + G.n, s);
+            else launch_dkappa(pb, P, G, (int)k, use_self, phi, dphi, dself.p, dvk.p, dvk.p + G.n, s);
             if (!charges) {
                 const int sf = P.tgt;
                 for (int side = 0; side < 2; ++side) {
@@ -1440,14 +1753,22 @@ void energy_gradient(pb_problem *pb, pb_grad *out) {
         for (int side = 0; side < 2; ++side)
             if ((side == 0 ? pb->S[sf].inner : pb->S[sf].outer) == Rc) m += pb->S[sf].n;
     TmpBuf<dvec4> csrc(std::max<int64_t>(1, m), s);
+    TmpBuf<float4> csrc32(std::max<int64_t>(1, m), s);
+    const bool mixed = prm.precision == PB_MIXED;
+    const double *co = pb->T[0].origin;
     {
         int64_t o = 0;
         for (int sf = 0; sf < ns; ++sf)
             for (int side = 0; side < 2; ++side)
                 if ((side == 0 ? pb->S[sf].inner : pb->S[sf].outer) == Rc) {
                     const int64_t n = pb->S[sf].n;
-                    pack_colloc_kernel<<<div_up(n, 256), 256, 0, s>>>(n, pb->S[sf].cen.p,
-                                                                      lam + 2 * pb->off[sf] + side * n, csrc.p + o);
+                    if (mixed)
+                        pack_colloc32_kernel<<<div_up(n, 256), 256, 0, s>>>(n, pb->S[sf].cen.p,
+                                                                            lam + 2 * pb->off[sf] + side * n, co[0],
+                                                                            co[1], co[2], csrc32.p + o);
+                    else
+                        pack_colloc_kernel<<<div_up(n, 256), 256, 0, s>>>(n, pb->S[sf].cen.p,
+                                                                          lam + 2 * pb->off[sf] + side * n, csrc.p + o);
                     PB_LAUNCH_CHECK();
                     o += n;
                 }
@@ -1457,8 +1778,12 @@ void energy_gradient(pb_problem *pb, pb_grad *out) {
     TmpBuf<double> part((size_t)nparts * 5 * nc, s), col(5 * nc, s), fld(3 * nc, s);
     {
         const int64_t chunk = std::max<int64_t>(1, (m + nparts - 1) / nparts);
-        colloc_kernel<<<dim3(gx, nparts), 128, 0, s>>>(nc, pb->cxyz_d.p, m, csrc.p, pb->regions[Rc].kappa, chunk,
-                                                       part.p);
+        if (mixed)
+            colloc32_kernel<<<dim3(gx, nparts), 128, 0, s>>>(nc, pb->cxyz_d.p, co[0], co[1], co[2], m, csrc32.p,
+                                                             (float)pb->regions[Rc].kappa, chunk, part.p);
+        else
+            colloc_kernel<<<dim3(gx, nparts), 128, 0, s>>>(nc, pb->cxyz_d.p, m, csrc.p, pb->regions[Rc].kappa, chunk,
+                                                           part.p);
         PB_LAUNCH_CHECK();
         sum_parts_kernel<<<div_up(5 * nc, 256), 256, 0, s>>>(nc, 5, nparts, part.p, kInv4Pi, 0, col.p);
         PB_LAUNCH_CHECK();
@@ -1470,10 +1795,18 @@ void energy_gradient(pb_problem *pb, pb_grad *out) {
         const SurfDev &S = pb->S[t];
         const double *phi = x + 2 * pb->off[t];
         const int64_t chunk = std::max<int64_t>(1, (S.n + nparts - 1) / nparts);
-        reac_field_kernel<<<dim3(gx, nparts), 128, 0, s>>>(nc, pb->cxyz_d.p, S.n, prm.K, rule_slot(prm.K_fine), S.gy.p,
-                                                           S.gwa.p, S.cen.p, S.nrm.p, S.L.p, S.area.p, S.verts.p,
-                                                           S.tris.p, prm.thres, tm.cK, tm.cV, phi, phi + S.n, chunk,
-                                                           part.p);
+        if (mixed) {
+            const double *o = pb->T[t].origin;
+            reac_field32_kernel<<<dim3(gx, nparts), 128, 0, s>>>(
+                nc, pb->cxyz_d.p, o[0], o[1], o[2], S.n, prm.K, rule_slot(prm.K_fine), A.pc32[t].p, A.pn32[t].p,
+                A.gp32[t].p, S.cen.p, S.L.p, S.area.p, S.verts.p, S.tris.p, prm.thres, (float)tm.cK, (float)tm.cV,
+                pb->T[t].phf.p, chunk, part.p);
+        } else {
+            reac_field_kernel<<<dim3(gx, nparts), 128, 0, s>>>(nc, pb->cxyz_d.p, S.n, prm.K, rule_slot(prm.K_fine),
+                                                               S.gy.p, S.gwa.p, S.cen.p, S.nrm.p, S.L.p, S.area.p,
+                                                               S.verts.p, S.tris.p, prm.thres, tm.cK, tm.cV, phi,
+                                                               phi + S.n, chunk, part.p);
+        }
         PB_LAUNCH_CHECK();
         sum_parts_kernel<<<div_up(3 * nc, 256), 256, 0, s>>>(nc, 3, nparts, part.p, kInv4Pi, 1, fld.p);
         PB_LAUNCH_CHECK();

@@ -36,6 +36,8 @@ struct AdjointState {
     std::vector<DevBuf<double>> gn64;   // sorted target normals, 3 per target
     std::vector<DevBuf<float4>> gn32;
     std::vector<TPair> tp, tq;     // transposed surface pairs, transposed charge pairs
+    // FP32 panel data per surface (mixed path of the charge-site sums), relative to the surface's tree origin
+    std::vector<DevBuf<float4>> pc32, pn32, gp32;
     DevBuf<double> lam, f, minvT, gacc, dq_d, dxyz_d, part;
 };
 

@@ -48,7 +48,7 @@ def test_transpose_direct_matches_dense(name):
         assert rel_l2(pb.apply_transpose(y), A.T @ y) <= 1e-12
 
 
-@pytest.mark.parametrize("params,P,tol", [(TREE64, 6, 1e-4), (TREE64, 10, 1e-6), (TREE32, 6, 1e-4)])
+@pytest.mark.parametrize("params,P,tol", [(TREE64, 6, 1e-4), (TREE64, 10, 3e-6), (TREE32, 6, 1e-4)])
 def test_transpose_treecode(params, P, tol):
     d = sphere_problem(level=4, charges="both")
     pb = problem(d, **dict(params, P=P))
