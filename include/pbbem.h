@@ -71,6 +71,8 @@ typedef struct {
     int precision;     /* PB_FP64 or PB_MIXED [PB_FP64] */
     int no_precond;    /* 1: plain GMRES; 0: right-preconditioned by the inverse of every
                           panel's 2x2 self block (not in the paper; same solution) [0] */
+    int ncrit_adjoint; /* a box of the transposed treecode (pb_gradient, pb_apply_transpose)
+                          with >= ncrit_adjoint collocation points is split [ncrit] */
 } pb_params;
 
 typedef struct {

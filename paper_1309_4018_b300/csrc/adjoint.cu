@@ -1293,7 +1293,7 @@ void prepare_adjoint(pb_problem *pb) {
     const int64_t nc = (int64_t)pb->cq.size();
     auto A = std::make_shared<AdjointState>();
     upload_adjoint_tables();
-    const int ncritT = std::max(1, prm.ncrit / prm.K);
+    const int ncritT = prm.ncrit_adjoint > 0 ? prm.ncrit_adjoint : prm.ncrit;
     A->TC.resize(ns);
     A->GP.resize(ns);
     A->gn64.resize(ns);

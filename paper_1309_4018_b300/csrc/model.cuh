@@ -16,6 +16,7 @@ struct Params {
     int restart = 50, max_iter = 1000;
     int precision = PB_FP64;
     bool precond = true;
+    int ncrit_adjoint = 0;   // 0: ncrit
 };
 
 struct Region {

@@ -31,7 +31,8 @@ class pb_params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("K_fine", ctypes.c_int), ("N_k", ctypes.c_int),
                 ("thres", ctypes.c_double), ("P", ctypes.c_int), ("theta", ctypes.c_double),
                 ("ncrit", ctypes.c_int), ("gmres_tol", ctypes.c_double), ("restart", ctypes.c_int),
-                ("max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("no_precond", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("no_precond", ctypes.c_int),
+                ("ncrit_adjoint", ctypes.c_int)]
 
 
 class pb_result(ctypes.Structure):
