@@ -211,10 +211,16 @@ __global__ void gather_targets_kernel(int64_t n, const int32_t *__restrict__ ord
 // ---------------------------------------------------------------- traversal (Eq. MAC)
 constexpr int kStack = 192;
 
+// The MAC decision is the exact FP64 test below.  An FP32 estimate decides
+// first when it is clearly on one side: with coordinates relative to the tree
+// origin, |f32 - f| <= 8 eps32 R theta / r_b * (theta^2 d^2 + r_b^2) for
+// f = theta^2 d^2 - r_b^2 and R the largest coordinate, so for theta <= 1 and
+// r_b > R / 1024 a margin of 1e-3 (theta^2 d^2 + r_b^2) can never flip it.
 template <bool FILL>
 __global__ void traverse_kernel(int64_t ntg, const double *__restrict__ xs, const double *__restrict__ centre,
-                                const double *__restrict__ rb2, const int32_t *__restrict__ first_child,
-                                const int32_t *__restrict__ nchild, double theta2, int direct,
+                                const double *__restrict__ rb2, const float4 *__restrict__ cen32,
+                                const int32_t *__restrict__ first_child, const int32_t *__restrict__ nchild,
+                                double theta2, int direct, double ox, double oy, double oz,
                                 int32_t *__restrict__ m2p_cnt, int32_t *__restrict__ p2p_cnt,
                                 const int64_t *__restrict__ m2p_ptr, const int64_t *__restrict__ p2p_ptr,
                                 int32_t *__restrict__ m2p_node, int32_t *__restrict__ p2p_node,
@@ -222,6 +228,10 @@ __global__ void traverse_kernel(int64_t ntg, const double *__restrict__ xs, cons
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ntg) return;
     const double x = xs[3 * i], y = xs[3 * i + 1], z = xs[3 * i + 2];
+    const float fx = (float)(x - ox), fy = (float)(y - oy), fz = (float)(z - oz);
+    const float th2f = (float)theta2;
+    const bool pref = theta2 <= 1.0;
+    const float tmax = fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz)));
     int stack[kStack];
     int sp = 0;
     stack[sp++] = 0;
@@ -229,11 +239,31 @@ __global__ void traverse_kernel(int64_t ntg, const double *__restrict__ xs, cons
     int64_t mo = FILL ? m2p_ptr[i] : 0, po = FILL ? p2p_ptr[i] : 0;
     while (sp > 0) {
         const int b = stack[--sp];
-        const double dx = __dsub_rn(x, centre[3 * b]);
-        const double dy = __dsub_rn(y, centre[3 * b + 1]);
-        const double dz = __dsub_rn(z, centre[3 * b + 2]);
-        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-        if (!direct && rb2[b] < __dmul_rn(theta2, d2)) {
+        bool accept = false;
+        if (!direct) {
+            int dec = -1;
+            if (pref) {
+                const float4 c = cen32[b];
+                const float R = fmaxf(tmax, fmaxf(fabsf(c.x), fmaxf(fabsf(c.y), fabsf(c.z))));
+                if (c.w > R * R * 9.5367431640625e-7f) {   // r_b > R / 1024
+                    const float dx = fx - c.x, dy = fy - c.y, dz = fz - c.z;
+                    const float rhs = th2f * (dx * dx + dy * dy + dz * dz);
+                    const float marg = 1e-3f * (rhs + c.w);
+                    if (rhs - c.w > marg) dec = 1;
+                    else if (c.w - rhs > marg) dec = 0;
+                }
+            }
+            if (dec < 0) {
+                const double dx = __dsub_rn(x, centre[3 * b]);
+                const double dy = __dsub_rn(y, centre[3 * b + 1]);
+                const double dz = __dsub_rn(z, centre[3 * b + 2]);
+                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                accept = rb2[b] < __dmul_rn(theta2, d2);
+            } else {
+                accept = dec == 1;
+            }
+        }
+        if (accept) {
             if (FILL) m2p_node[mo + nm] = b;
             ++nm;
         } else if (nchild[b] == 0) {
@@ -256,12 +286,18 @@ __global__ void owner_kernel(int64_t m, const int64_t *__restrict__ ptr, int32_t
     for (int64_t e = ptr[t]; e < ptr[t + 1]; ++e) owner[e] = (int32_t)t;
 }
 
+// Lanes holding the same key (neighbouring Morton-sorted targets share most
+// boxes) add once per group: one atomic per distinct key per warp.
 __global__ void inv_count_kernel(int64_t nent, const int32_t *__restrict__ ent, const int32_t *__restrict__ remap,
                                  int32_t *__restrict__ cnt) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nent) return;
+    const bool valid = e < nent;
+    const unsigned act = __ballot_sync(0xffffffffu, valid);
+    if (!valid) return;
     const int key = remap ? remap[ent[e]] : ent[e];
-    atomicAdd(&cnt[key], 1);
+    const unsigned grp = __match_any_sync(act, key);
+    const int lane = threadIdx.x & 31;
+    if (lane == __ffs(grp) - 1) atomicAdd(&cnt[key], __popc(grp));
 }
 
 // The order of the pairs inside one key's group does not matter: every pair
@@ -274,9 +310,17 @@ __global__ void inv_fill_kernel(int64_t nent, const int32_t *__restrict__ owner,
                                 int32_t *__restrict__ cursor, int by_entry, int32_t *__restrict__ inv,
                                 int32_t *__restrict__ map) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nent) return;
+    const bool valid = e < nent;
+    const unsigned act = __ballot_sync(0xffffffffu, valid);
+    if (!valid) return;
     const int key = remap ? remap[ent[e]] : ent[e];
-    const int64_t p = off[key] + atomicAdd(&cursor[key], 1);
+    const unsigned grp = __match_any_sync(act, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&cursor[key], __popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    const int64_t p = off[key] + base + __popc(grp & ((1u << lane) - 1u));
     inv[p] = owner[e];
     if (by_entry) map[p] = (int32_t)e;
     else map[e] = (int32_t)p;
@@ -669,8 +713,9 @@ void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &pr
     Pr.m2p_ptr.alloc(m + 1);
     Pr.p2p_ptr.alloc(m + 1);
     if (m) {
-        traverse_kernel<false><<<div_up(m, 128), 128, 0, s>>>(m, G.xs.p, T.centre.p, T.rb2.p, T.first_child.p,
-                                                              T.nchild.p, theta2, direct, mc.p, pc.p, nullptr, nullptr,
+        traverse_kernel<false><<<div_up(m, 128), 128, 0, s>>>(m, G.xs.p, T.centre.p, T.rb2.p, T.cen32.p,
+                                                              T.first_child.p, T.nchild.p, theta2, direct, T.origin[0],
+                                                              T.origin[1], T.origin[2], mc.p, pc.p, nullptr, nullptr,
                                                               nullptr, nullptr, err.p);
         PB_LAUNCH_CHECK();
     }
@@ -681,8 +726,9 @@ void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &pr
     Pr.m2p_node.alloc(std::max<int64_t>(1, Pr.n_m2p));
     Pr.p2p_node.alloc(std::max<int64_t>(1, Pr.n_p2p));
     if (m) {
-        traverse_kernel<true><<<div_up(m, 128), 128, 0, s>>>(m, G.xs.p, T.centre.p, T.rb2.p, T.first_child.p,
-                                                             T.nchild.p, theta2, direct, nullptr, nullptr,
+        traverse_kernel<true><<<div_up(m, 128), 128, 0, s>>>(m, G.xs.p, T.centre.p, T.rb2.p, T.cen32.p,
+                                                             T.first_child.p, T.nchild.p, theta2, direct, T.origin[0],
+                                                             T.origin[1], T.origin[2], nullptr, nullptr,
                                                              Pr.m2p_ptr.p, Pr.p2p_ptr.p, Pr.m2p_node.p, Pr.p2p_node.p,
                                                              err.p);
         PB_LAUNCH_CHECK();
