@@ -1,0 +1,113 @@
+// Caching allocator of the library's device and page-locked host blocks.
+#include <map>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace pb {
+
+namespace {
+
+constexpr size_t kDeviceCacheBytes = size_t(16) << 30;   // per device
+constexpr size_t kHostCacheBytes = size_t(64) << 20;
+constexpr int kMaxDevices = 64;
+
+struct Pool {
+    std::multimap<size_t, void *> free;   // size -> block
+    size_t held = 0;
+};
+
+std::mutex g_mu;
+Pool g_dev[kMaxDevices];
+Pool g_host;
+
+// Smallest cached block of at least `bytes` and at most twice that.
+void *take(Pool &pl, size_t bytes, size_t *got) {
+    auto it = pl.free.lower_bound(bytes);
+    if (it == pl.free.end() || it->first > 2 * bytes) return nullptr;
+    void *p = it->second;
+    *got = it->first;
+    pl.held -= it->first;
+    pl.free.erase(it);
+    return p;
+}
+
+size_t round_up(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+
+void *cached_device_alloc(size_t bytes, size_t *got) {
+    int dev = 0;
+    PB_CUDA_TRY(cudaGetDevice(&dev));
+    bytes = round_up(bytes);
+    if (dev >= 0 && dev < kMaxDevices) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (void *p = take(g_dev[dev], bytes, got)) return p;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        // give the cached blocks back to the driver and try once more
+        cudaGetLastError();
+        if (dev >= 0 && dev < kMaxDevices) {
+            std::lock_guard<std::mutex> lk(g_mu);
+            for (auto &kv : g_dev[dev].free) cudaFree(kv.second);
+            g_dev[dev].free.clear();
+            g_dev[dev].held = 0;
+        }
+        e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{PB_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed"};
+        }
+    }
+    *got = bytes;
+    return p;
+}
+
+void cached_device_free(void *p, size_t bytes) {
+    if (!p) return;
+    int dev = -1;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) == cudaSuccess) dev = at.device;
+    else cudaGetLastError();
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (dev >= 0 && dev < kMaxDevices && g_dev[dev].held + bytes <= kDeviceCacheBytes) {
+            g_dev[dev].free.emplace(bytes, p);
+            g_dev[dev].held += bytes;
+            return;
+        }
+    }
+    cudaFree(p);
+}
+
+void *cached_host_alloc(size_t bytes, size_t *got) {
+    bytes = round_up(bytes);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (void *p = take(g_host, bytes, got)) return p;
+    }
+    void *p = nullptr;
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{PB_ENOMEM, "cudaMallocHost failed"};
+    }
+    *got = bytes;
+    return p;
+}
+
+void cached_host_free(void *p, size_t bytes) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (g_host.held + bytes <= kHostCacheBytes) {
+            g_host.free.emplace(bytes, p);
+            g_host.held += bytes;
+            return;
+        }
+    }
+    cudaFreeHost(p);
+}
+
+}  // namespace pb

@@ -51,6 +51,18 @@ extern std::atomic<long long> g_launches;
 
 inline void fail(int code, const std::string &m) { throw Error{code, m}; }
 
+// ---------------------------------------------------------------- caching allocator
+// Library-owned device and page-locked host blocks are recycled: a released
+// block goes to a per-device free list (bounded; beyond the bound it is freed)
+// and a later request of at most its size takes it back, so a problem built
+// again (or a new one of similar size) allocates nothing from the driver.
+// Blocks are only released when no queued work uses them: every entry point
+// synchronises its stream before returning.  *got receives the block's size.
+void *cached_device_alloc(size_t bytes, size_t *got);
+void cached_device_free(void *p, size_t bytes);
+void *cached_host_alloc(size_t bytes, size_t *got);
+void cached_host_free(void *p, size_t bytes);
+
 // ---------------------------------------------------------------- device buffer
 // Device array owned by the library.  alloc() keeps the existing allocation
 // when it is large enough (a re-setup of the same geometry allocates nothing).
@@ -68,7 +80,7 @@ struct DevBuf {
     }
     ~DevBuf() { release(); }
     void release() {
-        if (p) cudaFree(p);
+        if (p) cached_device_free(p, cap * sizeof(T));
         p = nullptr;
         n = 0;
         cap = 0;
@@ -80,13 +92,10 @@ struct DevBuf {
         }
         release();
         if (count == 0) return;
-        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-        if (e != cudaSuccess) {
-            p = nullptr;
-            throw Error{PB_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed"};
-        }
+        size_t got = 0;
+        p = static_cast<T *>(cached_device_alloc(count * sizeof(T), &got));
         n = count;
-        cap = count;
+        cap = got / sizeof(T);
     }
     void zero(cudaStream_t s) {
         if (n) PB_CUDA_TRY(cudaMemsetAsync(p, 0, n * sizeof(T), s));
@@ -115,18 +124,16 @@ struct PinnedBuf {
     }
     ~PinnedBuf() { release(); }
     void release() {
-        if (p) cudaFreeHost(p);
+        if (p) cached_host_free(p, cap * sizeof(T));
         p = nullptr;
         cap = 0;
     }
     void alloc(size_t count) {
         if (p && count <= cap) return;
         release();
-        if (cudaMallocHost(&p, count * sizeof(T)) != cudaSuccess) {
-            p = nullptr;
-            throw Error{PB_ENOMEM, "cudaMallocHost failed"};
-        }
-        cap = count;
+        size_t got = 0;
+        p = static_cast<T *>(cached_host_alloc(count * sizeof(T), &got));
+        cap = got / sizeof(T);
     }
 };
 

@@ -365,7 +365,12 @@ __device__ __forceinline__ bool is_near(double x, double y, double z, const doub
 // leaves.  An FP32 distance test with a safety margin only prefilters; the
 // decision is the exact FP64 test above.  The fill pass writes the accepted
 // panels in any order and then sorts them ascending (deterministic result).
-template <bool FILL>
+constexpr int kNearCap = 256;   // row capacity of the one-pass mode
+
+// MODE 0: counts; 1: fills the CSR list (after the counts' scan); 2: counts
+// and writes the panels to a row of kNearCap entries per target (compacted
+// and sorted by near_compact_kernel; a longer row sets *overflow).
+template <int MODE>
 __global__ void __launch_bounds__(128) near_kernel(
     int64_t ntg, int K, const double *__restrict__ xs, const int32_t *__restrict__ selfp, int use_self,
     const int64_t *__restrict__ p2p_ptr, const int32_t *__restrict__ p2p_leafidx, const int32_t *__restrict__ leaf_node,
@@ -374,7 +379,9 @@ __global__ void __launch_bounds__(128) near_kernel(
     const double *__restrict__ L, const float4 *__restrict__ pan32, double ox, double oy, double oz, double thres,
     int32_t *__restrict__ ncount, int32_t *__restrict__ excl, int32_t *__restrict__ self_excl,
     const int64_t *__restrict__ near_ptr, int32_t *__restrict__ near_panel, const int64_t *__restrict__ m2p_ptr,
-    const int32_t *__restrict__ m2p_node, const float4 *__restrict__ cen32, double reach) {
+    const int32_t *__restrict__ m2p_node, const float4 *__restrict__ cen32, double reach, int32_t *__restrict__ rows,
+    int32_t *__restrict__ overflow) {
+    constexpr bool FILL = MODE == 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float freach = (float)reach;
     const int64_t i = (int64_t)blockIdx.x * 4 + warp;
@@ -422,6 +429,10 @@ __global__ void __launch_bounds__(128) near_kernel(
             }
             const uint32_t ba = __ballot_sync(0xffffffffu, acc);
             if (FILL && acc) near_panel[o + cnt + __popc(ba & ((1u << lane) - 1u))] = j;
+            if (MODE == 2 && acc) {
+                const int at = cnt + __popc(ba & ((1u << lane) - 1u));
+                if (at < kNearCap) rows[i * kNearCap + at] = j;
+            }
             cnt += __popc(ba);
             ex += __popc(__ballot_sync(0xffffffffu, exc));
         }
@@ -479,6 +490,7 @@ __global__ void __launch_bounds__(128) near_kernel(
     if (lane == 0) {
         ncount[i] = cnt;
         excl[i] = ex;
+        if (MODE == 2 && cnt > kNearCap) atomicExch(overflow, 1);
         int se = 0;
         if (me >= 0)
             for (int kk = 0; kk < K; ++kk)
@@ -515,6 +527,22 @@ __global__ void reach_kernel(int64_t n, const double *__restrict__ v, const int3
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m * (1.0 + 1e-12) + 1e-12));
+}
+
+// Copies every target's row into the CSR list in ascending order (insertion sort).
+__global__ void near_compact_kernel(int64_t ntg, const int32_t *__restrict__ rows, const int64_t *__restrict__ ptr,
+                                    int32_t *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntg) return;
+    const int32_t *row = rows + i * kNearCap;
+    int32_t *a = out + ptr[i];
+    const int n = (int)(ptr[i + 1] - ptr[i]);
+    for (int u = 0; u < n; ++u) {
+        const int v = row[u];
+        int w = u - 1;
+        while (w >= 0 && a[w] > v) { a[w + 1] = a[w]; --w; }
+        a[w + 1] = v;
+    }
 }
 
 __global__ void node_to_leaf_kernel(int64_t n, const int32_t *__restrict__ nodes, const int32_t *__restrict__ node_leaf,
@@ -815,27 +843,45 @@ void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &
     double reach = 0.0;
     std::memcpy(&reach, &rbits, sizeof(reach));
     Pr.near_ptr.alloc(m + 1);
+    bool done = false;
     if (m) {
-        near_kernel<false><<<div_up(m, 4), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
-                                                        pleaf.p, T.leaf_node.p, T.start.p, T.count.p, T.perm.p,
-                                                        T.pids.p, T.point_leaf.p, src.cen.p, src.L.p, pan32.p,
-                                                        T.origin[0], T.origin[1], T.origin[2], prm.thres, nc.p, ex.p,
-                                                        se.p, nullptr, nullptr, Pr.m2p_ptr.p, Pr.m2p_node.p,
-                                                        T.cen32.p, reach);
+        // one pass: counts and a row of panels per target
+        TmpBuf<int32_t> rows((size_t)m * kNearCap, s), ovf(1, s);
+        PB_CUDA_TRY(cudaMemsetAsync(ovf.p, 0, 4, s));
+        near_kernel<2><<<div_up(m, 4), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
+                                                    pleaf.p, T.leaf_node.p, T.start.p, T.count.p, T.perm.p, T.pids.p,
+                                                    T.point_leaf.p, src.cen.p, src.L.p, pan32.p, T.origin[0],
+                                                    T.origin[1], T.origin[2], prm.thres, nc.p, ex.p, se.p, nullptr,
+                                                    nullptr, Pr.m2p_ptr.p, Pr.m2p_node.p, T.cen32.p, reach, rows.p,
+                                                    ovf.p);
         PB_LAUNCH_CHECK();
+        int hov = 0;
+        PB_CUDA_TRY(cudaMemcpyAsync(&hov, ovf.p, 4, cudaMemcpyDeviceToHost, s));
+        PB_CUDA_TRY(cudaStreamSynchronize(s));
+        exclusive_scan_i32_to_i64(nc.p, Pr.near_ptr.p, m, s);
+        Pr.n_near = read_i64(Pr.near_ptr.p + m, s);
+        Pr.near_panel.alloc(std::max<int64_t>(1, Pr.n_near));
+        if (!hov) {
+            near_compact_kernel<<<div_up(m, 128), 128, 0, s>>>(m, rows.p, Pr.near_ptr.p, Pr.near_panel.p);
+            PB_LAUNCH_CHECK();
+            done = true;
+        }
+    } else {
+        exclusive_scan_i32_to_i64(nc.p, Pr.near_ptr.p, m, s);
+        Pr.n_near = 0;
+        Pr.near_panel.alloc(1);
+        done = true;
     }
-    exclusive_scan_i32_to_i64(nc.p, Pr.near_ptr.p, m, s);
-    Pr.n_near = read_i64(Pr.near_ptr.p + m, s);
     Pr.near_excl = device_sum_i32(ex.p, m, s);
     Pr.self_excl = device_sum_i32(se.p, m, s);
-    Pr.near_panel.alloc(std::max<int64_t>(1, Pr.n_near));
-    if (m) {
-        near_kernel<true><<<div_up(m, 4), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
-                                                       pleaf.p, T.leaf_node.p, T.start.p, T.count.p, T.perm.p,
-                                                       T.pids.p, T.point_leaf.p, src.cen.p, src.L.p, pan32.p,
-                                                       T.origin[0], T.origin[1], T.origin[2], prm.thres, nullptr,
-                                                       nullptr, nullptr, Pr.near_ptr.p, Pr.near_panel.p, Pr.m2p_ptr.p,
-                                                       Pr.m2p_node.p, T.cen32.p, reach);
+    if (!done) {
+        // some target has more than kNearCap near panels: fill the CSR list in a second pass
+        near_kernel<1><<<div_up(m, 4), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
+                                                    pleaf.p, T.leaf_node.p, T.start.p, T.count.p, T.perm.p, T.pids.p,
+                                                    T.point_leaf.p, src.cen.p, src.L.p, pan32.p, T.origin[0],
+                                                    T.origin[1], T.origin[2], prm.thres, nullptr, nullptr, nullptr,
+                                                    Pr.near_ptr.p, Pr.near_panel.p, Pr.m2p_ptr.p, Pr.m2p_node.p,
+                                                    T.cen32.p, reach, nullptr, nullptr);
         PB_LAUNCH_CHECK();
     }
     PB_CUDA_TRY(cudaStreamSynchronize(s));
