@@ -274,6 +274,8 @@ void setup_problem(pb_problem *pb) {
     // operator application allocates (it may be captured into a CUDA graph)
     for (int t = 0; t < ns; ++t) {
         if (prm.precision == PB_MIXED) pb->T[t].phf.alloc(pb->S[t].n);
+        pb->T[t].ucnt.alloc(pb->T[t].nnodes);
+        pb->T[t].ucnt.zero(s);
     }
     for (int t = 0; t < ns; ++t)
         if (pb->need_far[t]) {

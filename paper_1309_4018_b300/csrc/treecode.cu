@@ -121,109 +121,6 @@ __device__ __forceinline__ Quad<double> ld4(const double *p) {
     return {a.x, a.y, b.x, b.y};
 }
 
-// One block per leaf.  Each chunk of sources is staged in shared memory as
-// the powers of its offsets from the leaf centre (zero-padded to a multiple
-// of 4); every thread owns a moment term and a group of 4-source quads
-// (G groups when the terms are few, so all threads work), reads 4 sources per
-// 16-byte load, and the groups' partial sums are added in group order at the
-// end (deterministic).
-template <typename T>
-__global__ void __launch_bounds__(256) p2m_kernel(int nleaves, const int32_t *__restrict__ leaf_node,
-                                                  const int64_t *__restrict__ start, const int64_t *__restrict__ count,
-                                                  const double *__restrict__ centre, double ox, double oy, double oz,
-                                                  SrcView<T> sv, int P, int NT, T *__restrict__ mom) {
-    constexpr int CH = sizeof(T) == 4 ? kP2MChunk : kP2MChunk / 2;   // FP64 tiles stay under 48 KB
-    __shared__ __align__(16) T pw[3][kMaxP + 1][CH];
-    __shared__ __align__(16) T sd[4][CH];
-    __shared__ int sterm[3 * 455];
-    __shared__ T part[2][2][128];
-    const int node = leaf_node[blockIdx.x];
-    const int64_t s0 = start[node], cnt = count[node];
-    T c[3];
-    if (sizeof(T) == 8) {
-        c[0] = (T)centre[3 * node]; c[1] = (T)centre[3 * node + 1]; c[2] = (T)centre[3 * node + 2];
-    } else {
-        c[0] = (T)(centre[3 * node] - ox); c[1] = (T)(centre[3 * node + 1] - oy); c[2] = (T)(centre[3 * node + 2] - oz);
-    }
-    for (int i = threadIdx.x; i < 3 * NT; i += blockDim.x) sterm[i] = c_terms[i];
-    const int G = NT <= 85 ? 3 : NT <= 128 ? 2 : 1;
-    const int g = G > 1 ? threadIdx.x / NT : 0;
-    int kk[2] = {G > 1 ? threadIdx.x % NT : threadIdx.x, threadIdx.x + 256};
-    const int nk = G > 1 ? (g < G ? 1 : 0) : (kk[1] < NT ? 2 : (kk[0] < NT ? 1 : 0));
-    T accM[2] = {0, 0}, accD[2] = {0, 0};
-    for (int64_t c0 = 0; c0 < cnt; c0 += CH) {
-        const int m = (int)(cnt - c0 < CH ? cnt - c0 : CH);
-        const int m4 = (m + 3) >> 2;
-        __syncthreads();
-        if (threadIdx.x < 4 * m4) {
-            const int j = threadIdx.x;
-            T x = 0, y = 0, z = 0, st = 0, dx = 0, dy = 0, dz = 0;
-            if (j < m) sv.get(s0 + c0 + j, c, x, y, z, st, dx, dy, dz);
-            T px = 1, py = 1, pz = 1;
-            for (int e = 0; e <= P; ++e) {
-                pw[0][e][j] = px; pw[1][e][j] = py; pw[2][e][j] = pz;
-                px *= x; py *= y; pz *= z;
-            }
-            sd[0][j] = st; sd[1][j] = dx; sd[2][j] = dy; sd[3][j] = dz;
-        }
-        __syncthreads();
-        for (int r = 0; r < nk; ++r) {
-            const int k = kk[r];
-            const int k1 = sterm[3 * k], k2 = sterm[3 * k + 1], k3 = sterm[3 * k + 2];
-            T aM = accM[r], aD = accD[r];
-            for (int q = g; q < m4; q += G) {
-                const int j = 4 * q;
-                const Quad<T> p1 = ld4(&pw[0][k1][j]), p2 = ld4(&pw[1][k2][j]), p3 = ld4(&pw[2][k3][j]);
-                const Quad<T> s = ld4(&sd[0][j]);
-                const Quad<T> m12 = {p1.x * p2.x, p1.y * p2.y, p1.z * p2.z, p1.w * p2.w};
-                aM += s.x * (m12.x * p3.x) + s.y * (m12.y * p3.y) + s.z * (m12.z * p3.z) + s.w * (m12.w * p3.w);
-                if (k1) {
-                    const Quad<T> q1 = ld4(&pw[0][k1 - 1][j]), d = ld4(&sd[1][j]);
-                    const T f = (T)k1;
-                    aD += f * (d.x * q1.x * p2.x * p3.x + d.y * q1.y * p2.y * p3.y + d.z * q1.z * p2.z * p3.z +
-                               d.w * q1.w * p2.w * p3.w);
-                }
-                if (k2) {
-                    const Quad<T> q2 = ld4(&pw[1][k2 - 1][j]), d = ld4(&sd[2][j]);
-                    const T f = (T)k2;
-                    aD += f * (d.x * p1.x * q2.x * p3.x + d.y * p1.y * q2.y * p3.y + d.z * p1.z * q2.z * p3.z +
-                               d.w * p1.w * q2.w * p3.w);
-                }
-                if (k3) {
-                    const Quad<T> q3 = ld4(&pw[2][k3 - 1][j]), d = ld4(&sd[3][j]);
-                    const T f = (T)k3;
-                    aD += f * (d.x * m12.x * q3.x + d.y * m12.y * q3.y + d.z * m12.z * q3.z + d.w * m12.w * q3.w);
-                }
-            }
-            accM[r] = aM;
-            accD[r] = aD;
-        }
-    }
-    if (G > 1) {
-        // groups 1.. hand their sums to group 0, which adds them in order
-        __syncthreads();
-        if (nk && g > 0) {
-            part[g - 1][0][kk[0]] = accM[0];
-            part[g - 1][1][kk[0]] = accD[0];
-        }
-        __syncthreads();
-        if (nk && g == 0) {
-            T aM = accM[0], aD = accD[0];
-            for (int h = 1; h < G; ++h) {
-                aM += part[h - 1][0][kk[0]];
-                aD += part[h - 1][1][kk[0]];
-            }
-            mom[(int64_t)node * 2 * NT + kk[0]] = aM;
-            mom[(int64_t)node * 2 * NT + NT + kk[0]] = aD;
-        }
-    } else {
-        for (int r = 0; r < nk; ++r) {
-            mom[(int64_t)node * 2 * NT + kk[r]] = accM[r];
-            mom[(int64_t)node * 2 * NT + NT + kk[r]] = accD[r];
-        }
-    }
-}
-
 // ---------------------------------------------------------------- M2M (one level, bottom-up)
 // M_parent^k = sum_children sum_{l <= k} C(k, l) (y_child - y_parent)^(k-l) M_child^l;
 // the dipole moments D shift with the same rule.  The shift factorises by
@@ -920,9 +817,197 @@ void launch_m2p_typed(int P, bool yuk, const Pair &Pr, const double *xs, const d
     PB_LAUNCH_CHECK();
 }
 
+// ---------------------------------------------------------------- fused upward pass
+// P2M and every M2M level in one launch: one block per leaf computes the
+// leaf's moments; then the block that finishes last among a node's children
+// (an atomic count per node, each child announcing itself after a memory
+// fence) shifts the children into the parent, and so on to the root.  No
+// block waits for another; each node is computed exactly once, from its
+// children in child order, so the moments equal the level-by-level ones.
+template <typename T>
+__device__ __forceinline__ T ld_cg(const T *p) { return __ldcg(p); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) upward_kernel(int nleaves, const int32_t *__restrict__ leaf_node,
+                                                     const int64_t *__restrict__ start,
+                                                     const int64_t *__restrict__ count,
+                                                     const double *__restrict__ centre, double ox, double oy,
+                                                     double oz, SrcView<T> sv, int P, int NT,
+                                                     const int32_t *__restrict__ first_child,
+                                                     const int32_t *__restrict__ nchild,
+                                                     const int32_t *__restrict__ parent, int32_t *__restrict__ ucnt,
+                                                     T *__restrict__ mom) {
+    constexpr int CH = sizeof(T) == 4 ? kP2MChunk : kP2MChunk / 2;
+    extern __shared__ __align__(16) unsigned char up_smem[];
+    int *sterm = reinterpret_cast<int *>(up_smem);
+    T *region = reinterpret_cast<T *>(up_smem + ((3 * 455 * sizeof(int) + 31) / 32) * 32);
+    __shared__ T hp[8][3][kMaxP + 1];
+    __shared__ T sbin[kMaxP + 1][kMaxP + 1];
+    __shared__ int s_next;
+    for (int i = threadIdx.x; i < 3 * NT; i += blockDim.x) sterm[i] = c_terms[i];
+    for (int i = threadIdx.x; i < (P + 1) * (P + 1); i += blockDim.x) {
+        const int n = i / (P + 1), k = i - n * (P + 1);
+        sbin[n][k] = (T)c_binom[n][k];
+    }
+    // ---- P2M of this block's leaf (the 4-source quad scheme of p2m_kernel)
+    T(*pw)[kMaxP + 1][CH] = reinterpret_cast<T(*)[kMaxP + 1][CH]>(region);
+    T(*sd)[CH] = reinterpret_cast<T(*)[CH]>(region + 3 * (kMaxP + 1) * CH);
+    T(*part)[2][128] = reinterpret_cast<T(*)[2][128]>(region + 3 * (kMaxP + 1) * CH + 4 * CH);
+    int node = leaf_node[blockIdx.x];
+    {
+        const int64_t s0 = start[node], cnt = count[node];
+        T c[3];
+        if (sizeof(T) == 8) {
+            c[0] = (T)centre[3 * node]; c[1] = (T)centre[3 * node + 1]; c[2] = (T)centre[3 * node + 2];
+        } else {
+            c[0] = (T)(centre[3 * node] - ox); c[1] = (T)(centre[3 * node + 1] - oy);
+            c[2] = (T)(centre[3 * node + 2] - oz);
+        }
+        const int G = NT <= 85 ? 3 : NT <= 128 ? 2 : 1;
+        const int g = G > 1 ? threadIdx.x / NT : 0;
+        int kk[2] = {G > 1 ? (int)(threadIdx.x % NT) : (int)threadIdx.x, (int)threadIdx.x + 256};
+        const int nk = G > 1 ? (g < G ? 1 : 0) : (kk[1] < NT ? 2 : (kk[0] < NT ? 1 : 0));
+        T accM[2] = {0, 0}, accD[2] = {0, 0};
+        for (int64_t c0 = 0; c0 < cnt; c0 += CH) {
+            const int m = (int)(cnt - c0 < CH ? cnt - c0 : CH);
+            const int m4 = (m + 3) >> 2;
+            __syncthreads();
+            if (threadIdx.x < 4 * m4) {
+                const int j = threadIdx.x;
+                T x = 0, y = 0, z = 0, st = 0, dx = 0, dy = 0, dz = 0;
+                if (j < m) sv.get(s0 + c0 + j, c, x, y, z, st, dx, dy, dz);
+                T px = 1, py = 1, pz = 1;
+                for (int e = 0; e <= P; ++e) {
+                    pw[0][e][j] = px; pw[1][e][j] = py; pw[2][e][j] = pz;
+                    px *= x; py *= y; pz *= z;
+                }
+                sd[0][j] = st; sd[1][j] = dx; sd[2][j] = dy; sd[3][j] = dz;
+            }
+            __syncthreads();
+            for (int r = 0; r < nk; ++r) {
+                const int k = kk[r];
+                const int k1 = sterm[3 * k], k2 = sterm[3 * k + 1], k3 = sterm[3 * k + 2];
+                T aM = accM[r], aD = accD[r];
+                for (int q = g; q < m4; q += G) {
+                    const int j = 4 * q;
+                    const Quad<T> p1 = ld4(&pw[0][k1][j]), p2 = ld4(&pw[1][k2][j]), p3 = ld4(&pw[2][k3][j]);
+                    const Quad<T> sq = ld4(&sd[0][j]);
+                    const Quad<T> m12 = {p1.x * p2.x, p1.y * p2.y, p1.z * p2.z, p1.w * p2.w};
+                    aM += sq.x * (m12.x * p3.x) + sq.y * (m12.y * p3.y) + sq.z * (m12.z * p3.z) + sq.w * (m12.w * p3.w);
+                    if (k1) {
+                        const Quad<T> q1 = ld4(&pw[0][k1 - 1][j]), d = ld4(&sd[1][j]);
+                        aD += (T)k1 * (d.x * q1.x * p2.x * p3.x + d.y * q1.y * p2.y * p3.y + d.z * q1.z * p2.z * p3.z +
+                                       d.w * q1.w * p2.w * p3.w);
+                    }
+                    if (k2) {
+                        const Quad<T> q2 = ld4(&pw[1][k2 - 1][j]), d = ld4(&sd[2][j]);
+                        aD += (T)k2 * (d.x * p1.x * q2.x * p3.x + d.y * p1.y * q2.y * p3.y + d.z * p1.z * q2.z * p3.z +
+                                       d.w * p1.w * q2.w * p3.w);
+                    }
+                    if (k3) {
+                        const Quad<T> q3 = ld4(&pw[2][k3 - 1][j]), d = ld4(&sd[3][j]);
+                        aD += (T)k3 * (d.x * m12.x * q3.x + d.y * m12.y * q3.y + d.z * m12.z * q3.z +
+                                       d.w * m12.w * q3.w);
+                    }
+                }
+                accM[r] = aM;
+                accD[r] = aD;
+            }
+        }
+        if (G > 1) {
+            __syncthreads();
+            if (nk && g > 0) {
+                part[g - 1][0][kk[0]] = accM[0];
+                part[g - 1][1][kk[0]] = accD[0];
+            }
+            __syncthreads();
+            if (nk && g == 0) {
+                T aM = accM[0], aD = accD[0];
+                for (int h = 1; h < G; ++h) {
+                    aM += part[h - 1][0][kk[0]];
+                    aD += part[h - 1][1][kk[0]];
+                }
+                mom[(int64_t)node * 2 * NT + kk[0]] = aM;
+                mom[(int64_t)node * 2 * NT + NT + kk[0]] = aD;
+            }
+        } else {
+            for (int r = 0; r < nk; ++r) {
+                mom[(int64_t)node * 2 * NT + kk[r]] = accM[r];
+                mom[(int64_t)node * 2 * NT + NT + kk[r]] = accD[r];
+            }
+        }
+    }
+    // ---- climb: the last child to finish computes the parent
+    T *buf0 = region, *buf1 = region + 8 * 2 * NT;
+    while (true) {
+        __threadfence();   // every thread's moment stores before the announcement
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int par = parent[node];
+            int next = -1;
+            if (par >= 0 && atomicAdd(&ucnt[par], 1) == nchild[par] - 1) {
+                next = par;
+                ucnt[par] = 0;
+            }
+            s_next = next;
+        }
+        __syncthreads();
+        const int b = s_next;
+        if (b < 0) return;
+        __threadfence();
+        const int nc = nchild[b], fc = first_child[b];
+        for (int i = threadIdx.x; i < nc * 2 * NT; i += blockDim.x) {
+            const int c = i / (2 * NT), r = i - c * 2 * NT;
+            buf0[i] = ld_cg(mom + (int64_t)(fc + c) * 2 * NT + r);
+        }
+        for (int i = threadIdx.x; i < nc * 3; i += blockDim.x) {
+            const int c = i / 3, ax = i - 3 * c;
+            const T h = (T)(centre[3 * (fc + c) + ax] - centre[3 * b + ax]);
+            T v = 1;
+            for (int e = 0; e <= P; ++e) { hp[c][ax][e] = v; v *= h; }
+        }
+        __syncthreads();
+        T *src = buf0, *dst = buf1;
+        for (int ax = 2; ax >= 0; --ax) {
+            for (int idx = threadIdx.x; idx < nc * 2 * NT; idx += blockDim.x) {
+                const int c = idx / (2 * NT), r = idx - c * 2 * NT;
+                const int half = r >= NT ? NT : 0, k = r - half;
+                int kx[3] = {sterm[3 * k], sterm[3 * k + 1], sterm[3 * k + 2]};
+                const int kax = kx[ax];
+                const T *sc = src + c * 2 * NT + half;
+                T acc = 0;
+                for (int l = 0; l <= kax; ++l) {
+                    kx[ax] = l;
+                    acc += sbin[kax][l] * hp[c][ax][kax - l] * sc[term_index(kx[0], kx[1], kx[2])];
+                }
+                dst[idx] = acc;
+            }
+            __syncthreads();
+            T *tmp = src; src = dst; dst = tmp;
+        }
+        for (int r = threadIdx.x; r < 2 * NT; r += blockDim.x) {
+            T acc = 0;
+            for (int c = 0; c < nc; ++c) acc += src[c * 2 * NT + r];
+            mom[(int64_t)b * 2 * NT + r] = acc;
+        }
+        node = b;
+    }
+}
+
+size_t upward_smem(int NT, size_t elem) {
+    const size_t CH = elem == 4 ? kP2MChunk : kP2MChunk / 2;
+    const size_t p2m = (3 * (kMaxP + 1) * CH + 4 * CH + 2 * 2 * 128) * elem;
+    const size_t m2m = (size_t)2 * 8 * 2 * NT * elem;
+    return (3 * 455 * sizeof(int) + 31) / 32 * 32 + std::max(p2m, m2m);
+}
+
 }  // namespace
 
 void upload_term_tables() {
+    PB_CUDA_TRY(cudaFuncSetAttribute(upward_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)upward_smem(455, 8)));
+    PB_CUDA_TRY(cudaFuncSetAttribute(upward_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)upward_smem(455, 4)));
     PB_CUDA_TRY(cudaFuncSetAttribute(m2m_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kM2MMaxShared));
     PB_CUDA_TRY(cudaFuncSetAttribute(m2m_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kM2MMaxShared));
     int terms[3 * kMaxTerms1];
@@ -962,19 +1047,24 @@ void compute_strengths(Tree &Tr, const SurfDev &S, const double *phi, const doub
 
 void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s) {
     const int NT = nterms(P);
+    if (Tr.ucnt.n != (size_t)Tr.nnodes) {
+        Tr.ucnt.alloc(Tr.nnodes);
+        Tr.ucnt.zero(s);
+    }
     if (mixed) {
         Tr.mom32.alloc((size_t)Tr.nnodes * 2 * NT);
         SrcView<float> sv{Tr.srcA32.p, Tr.srcB32.p};
-        p2m_kernel<float><<<Tr.nleaves, 256, 0, s>>>(Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p,
-                                                     Tr.origin[0], Tr.origin[1], Tr.origin[2], sv, P, NT, Tr.mom32.p);
+        upward_kernel<float><<<Tr.nleaves, 256, upward_smem(NT, 4), s>>>(
+            Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p, Tr.origin[0], Tr.origin[1], Tr.origin[2],
+            sv, P, NT, Tr.first_child.p, Tr.nchild.p, Tr.parent.p, Tr.ucnt.p, Tr.mom32.p);
     } else {
         Tr.mom64.alloc((size_t)Tr.nnodes * 2 * NT);
         SrcView<double> sv{Tr.src64.p};
-        p2m_kernel<double><<<Tr.nleaves, 256, 0, s>>>(Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p,
-                                                      Tr.origin[0], Tr.origin[1], Tr.origin[2], sv, P, NT, Tr.mom64.p);
+        upward_kernel<double><<<Tr.nleaves, 256, upward_smem(NT, 8), s>>>(
+            Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p, Tr.origin[0], Tr.origin[1], Tr.origin[2],
+            sv, P, NT, Tr.first_child.p, Tr.nchild.p, Tr.parent.p, Tr.ucnt.p, Tr.mom64.p);
     }
     PB_LAUNCH_CHECK();
-    m2m_pass(Tr, P, mixed, mixed ? (void *)Tr.mom32.p : (void *)Tr.mom64.p, 2 * NT, 0, s);
 }
 
 void m2m_pass(const Tree &Tr, int P, bool mixed, void *mom, int stride, int base, cudaStream_t s) {
