@@ -753,22 +753,21 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
             two_add(nh[a], nl[a], ph);
             nl[a] += pl;
         }
-    if (lane == 0) {
-        double out[2 * NK];
+    // FP64 epilogue: lane a finishes value a (V0, K0[, V1, K1]) - the B300 FP64
+    // pipe is narrow, so one lane doing all of them dominated the kernel
+    float vh = hi[0], vl = lo[0], wh = nh[0], wl = nl[0];
 #pragma unroll
-        for (int a = 0; a < 2 * NK; ++a)
-            out[a] = ((double)hi[a] + (double)lo[a]) * kInv4Pi + (double)nh[a] + (double)nl[a];
-        if (nr.use_self) {
+    for (int a = 1; a < 2 * NK; ++a)
+        if (lane == a) { vh = hi[a]; vl = lo[a]; wh = nh[a]; wl = nl[a]; }
+    if (lane < 2 * NK) {
+        double out = ((double)vh + (double)vl) * kInv4Pi + ((double)wh + (double)wl);
+        const int a = lane;
+        if (nr.use_self && (a & 1) == 0) {
             const int me = nr.selfp[t];
-#pragma unroll
-            for (int a = 0; a < NK; ++a) out[2 * a] += nr.selfV[a][me] * nr.dphi[me];
+            out += nr.selfV[a >> 1][me] * nr.dphi[me];
         }
-        VK0[t] = out[0];
-        VK0[ntg + t] = out[1];
-        if (NK == 2) {
-            VK1[t] = out[2 % (2 * NK)];
-            VK1[ntg + t] = out[3 % (2 * NK)];
-        }
+        double *dst = (a >> 1) == 0 ? VK0 : VK1;
+        dst[(a & 1) ? ntg + t : t] = out;
     }
 }
 
@@ -850,9 +849,12 @@ __global__ void __launch_bounds__(256) upward_kernel(int nleaves, const int32_t 
         sbin[n][k] = (T)c_binom[n][k];
     }
     // ---- P2M of this block's leaf (the 4-source quad scheme of p2m_kernel)
-    T(*pw)[kMaxP + 1][CH] = reinterpret_cast<T(*)[kMaxP + 1][CH]>(region);
-    T(*sd)[CH] = reinterpret_cast<T(*)[CH]>(region + 3 * (kMaxP + 1) * CH);
-    T(*part)[2][128] = reinterpret_cast<T(*)[2][128]>(region + 3 * (kMaxP + 1) * CH + 4 * CH);
+    // power rows padded by 4 values: threads owning different terms read
+    // different rows at the same column without bank conflicts
+    constexpr int CP = CH + 4;
+    T(*pw)[kMaxP + 1][CP] = reinterpret_cast<T(*)[kMaxP + 1][CP]>(region);
+    T(*sd)[CH] = reinterpret_cast<T(*)[CH]>(region + 3 * (kMaxP + 1) * CP);
+    T(*part)[2][128] = reinterpret_cast<T(*)[2][128]>(region + 3 * (kMaxP + 1) * CP + 4 * CH);
     int node = leaf_node[blockIdx.x];
     {
         const int64_t s0 = start[node], cnt = count[node];
@@ -996,7 +998,7 @@ __global__ void __launch_bounds__(256) upward_kernel(int nleaves, const int32_t 
 
 size_t upward_smem(int NT, size_t elem) {
     const size_t CH = elem == 4 ? kP2MChunk : kP2MChunk / 2;
-    const size_t p2m = (3 * (kMaxP + 1) * CH + 4 * CH + 2 * 2 * 128) * elem;
+    const size_t p2m = (3 * (kMaxP + 1) * (CH + 4) + 4 * CH + 2 * 2 * 128) * elem;
     const size_t m2m = (size_t)2 * 8 * 2 * NT * elem;
     return (3 * 455 * sizeof(int) + 31) / 32 * 32 + std::max(p2m, m2m);
 }
