@@ -66,16 +66,6 @@ __global__ void mdot_finish_kernel(const double *__restrict__ partial, int nv, d
     if (threadIdx.x == 0) out[v] = accumulate ? out[v] + s : s;
 }
 
-// w -= sum_v V[v] h[v]
-__global__ void project_out_kernel(const double *__restrict__ V, int64_t ld, int nv, const double *__restrict__ h,
-                                   double *__restrict__ w, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double s = w[i];
-    for (int v = 0; v < nv; ++v) s -= V[v * ld + i] * h[v];
-    w[i] = s;
-}
-
 __global__ void scale_copy_kernel(const double *__restrict__ src, const double *__restrict__ num_sq,
                                   double *__restrict__ dst, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -88,37 +78,6 @@ __global__ void axpby_kernel(double a, const double *__restrict__ x, double b, c
                              double *__restrict__ out, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = a * x[i] + b * y[i];
-}
-
-__global__ void add_kernel(double *a, const double *b, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) a[i] += b[i];
-}
-
-// Arnoldi column j: H[0..j][j] in hcol; nrm2 = ||w||^2.  Applies the previous
-// rotations, forms the new one, updates g and the residual estimate.
-__global__ void givens_kernel(GmresState *st, int j, const double *__restrict__ hcol, const double *__restrict__ nrm2) {
-    if (threadIdx.x != 0) return;
-    const int m = st->m;
-    double *col = st->H + (int64_t)j * (m + 1);   // column-major (m + 1) x m
-    for (int i = 0; i <= j; ++i) col[i] = hcol[i];
-    const double hn = sqrt(*nrm2);
-    col[j + 1] = hn;
-    st->hnext = hn;
-    for (int i = 0; i < j; ++i) {
-        const double t = st->cs[i] * col[i] + st->sn[i] * col[i + 1];
-        col[i + 1] = -st->sn[i] * col[i] + st->cs[i] * col[i + 1];
-        col[i] = t;
-    }
-    const double den = hypot(col[j], col[j + 1]);
-    const double c = den > 0.0 ? col[j] / den : 1.0, s = den > 0.0 ? col[j + 1] / den : 0.0;
-    st->cs[j] = c;
-    st->sn[j] = s;
-    col[j] = den;
-    col[j + 1] = 0.0;
-    st->g[j + 1] = -s * st->g[j];
-    st->g[j] = c * st->g[j];
-    st->res_est = fabs(st->g[j + 1]) / st->bnorm;
 }
 
 // y = H[0..k)^-1 g (back substitution) into st->y.
@@ -223,6 +182,153 @@ void dot_device(const double *V, int64_t ld, int nv, const double *w, int64_t n,
     PB_LAUNCH_CHECK();
 }
 
+// ---------------------------------------------------------------- fused Arnoldi step
+// One CGS2 step in four launches.  Every block owns a fixed slice of the
+// vector; its partial dot products go to `partial`, and the block that
+// arrives last (an atomic count, each block announcing itself after a fence)
+// adds the partials in block order, so the sums are deterministic.
+struct ArnoldiArgs {
+    const double *V;
+    int64_t ld, n;
+    int nv;                 // j + 1 basis vectors
+    double *w;
+    double *h1, *h2, *nrm2; // device scalars
+    double *partial;        // kDotGroup-blocked partials
+    unsigned *count;        // zero between launches
+    GmresState *st;
+    int j;
+};
+
+__device__ __forceinline__ bool arrive_last(unsigned *count) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(count, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// Block partials of V[v] . w over the block's slice, for v < nv.
+__device__ void slice_dots(const ArnoldiArgs &a, int64_t lo, int64_t hi) {
+    __shared__ double sm[kDotGroup][kRedThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int v0 = 0; v0 < a.nv; v0 += kDotGroup) {
+        const int nb = min(kDotGroup, a.nv - v0);
+        double acc[kDotGroup];
+#pragma unroll
+        for (int b = 0; b < kDotGroup; ++b) acc[b] = 0.0;
+        for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) {
+            const double wi = a.w[i];
+#pragma unroll
+            for (int b = 0; b < kDotGroup; ++b)
+                if (b < nb) acc[b] += a.V[(int64_t)(v0 + b) * a.ld + i] * wi;
+        }
+#pragma unroll
+        for (int b = 0; b < kDotGroup; ++b) {
+            double t = acc[b];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) sm[b][wid] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < nb) {
+            double t = 0.0;
+            for (int k = 0; k < kRedThreads / 32; ++k) t += sm[threadIdx.x][k];
+            a.partial[(v0 + threadIdx.x) * kRedBlocks + blockIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+__device__ void finish_dots(const ArnoldiArgs &a, int nv, double *out) {
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+        double t = 0.0;
+        for (int b = 0; b < kRedBlocks; ++b) t += __ldcg(a.partial + v * kRedBlocks + b);
+        out[v] = t;
+    }
+}
+
+// h1 = V^T w
+__global__ void __launch_bounds__(kRedThreads) arnoldi_dots_kernel(ArnoldiArgs a) {
+    const int64_t per = (a.n + kRedBlocks - 1) / kRedBlocks;
+    const int64_t lo = blockIdx.x * per, hi = min(a.n, lo + per);
+    slice_dots(a, lo, hi);
+    if (arrive_last(a.count)) {
+        finish_dots(a, a.nv, a.h1);
+        if (threadIdx.x == 0) *a.count = 0;
+    }
+}
+
+// w -= V h1, then h2 = V^T w (the block projects its own slice first)
+__global__ void __launch_bounds__(kRedThreads) arnoldi_project_dots_kernel(ArnoldiArgs a) {
+    const int64_t per = (a.n + kRedBlocks - 1) / kRedBlocks;
+    const int64_t lo = blockIdx.x * per, hi = min(a.n, lo + per);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) {
+        double t = a.w[i];
+        for (int v = 0; v < a.nv; ++v) t -= a.V[(int64_t)v * a.ld + i] * a.h1[v];
+        a.w[i] = t;
+    }
+    __syncthreads();
+    slice_dots(a, lo, hi);
+    if (arrive_last(a.count)) {
+        finish_dots(a, a.nv, a.h2);
+        if (threadIdx.x == 0) *a.count = 0;
+    }
+}
+
+// w -= V h2; nrm2 = w . w; the last block also forms the Hessenberg column
+// h1 + h2 and applies the Givens rotations (residual estimate in st).
+__global__ void __launch_bounds__(kRedThreads) arnoldi_project_norm_kernel(ArnoldiArgs a) {
+    __shared__ double sm[kRedThreads / 32];
+    const int64_t per = (a.n + kRedBlocks - 1) / kRedBlocks;
+    const int64_t lo = blockIdx.x * per, hi = min(a.n, lo + per);
+    double s2 = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) {
+        double t = a.w[i];
+        for (int v = 0; v < a.nv; ++v) t -= a.V[(int64_t)v * a.ld + i] * a.h2[v];
+        a.w[i] = t;
+        s2 += t * t;
+    }
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kRedThreads / 32; ++k) t += sm[k];
+        a.partial[blockIdx.x] = t;
+    }
+    if (arrive_last(a.count)) {
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int b = 0; b < kRedBlocks; ++b) t += __ldcg(a.partial + b);
+            *a.nrm2 = t;
+            *a.count = 0;
+            // Hessenberg column j = h1 + h2 with the new subdiagonal ||w||
+            GmresState *st = a.st;
+            const int m = st->m, j = a.j;
+            double *col = st->H + (int64_t)j * (m + 1);
+            for (int i = 0; i <= j; ++i) col[i] = a.h1[i] + a.h2[i];
+            const double hn = sqrt(t);
+            col[j + 1] = hn;
+            st->hnext = hn;
+            for (int i = 0; i < j; ++i) {
+                const double u = st->cs[i] * col[i] + st->sn[i] * col[i + 1];
+                col[i + 1] = -st->sn[i] * col[i] + st->cs[i] * col[i + 1];
+                col[i] = u;
+            }
+            const double den = hypot(col[j], col[j + 1]);
+            const double c = den > 0.0 ? col[j] / den : 1.0, sn = den > 0.0 ? col[j + 1] / den : 0.0;
+            st->cs[j] = c;
+            st->sn[j] = sn;
+            col[j] = den;
+            col[j + 1] = 0.0;
+            st->g[j + 1] = -sn * st->g[j];
+            st->g[j] = c * st->g[j];
+            st->res_est = fabs(st->g[j + 1]) / st->bnorm;
+        }
+    }
+}
+
 }  // namespace
 
 void Gmres::init(int64_t n_, int m_, cudaStream_t s) {
@@ -238,6 +344,8 @@ void Gmres::init(int64_t n_, int m_, cudaStream_t s) {
     H.alloc((size_t)(m + 1) * m);
     cs.alloc(m); sn.alloc(m); g.alloc(m + 1); y.alloc(m);
     st.alloc(1);
+    count.alloc(1);
+    count.zero(s);
     GmresState h{};
     h.m = m;
     h.H = H.p; h.cs = cs.p; h.sn = sn.p; h.g = g.p; h.y = y.p;
@@ -267,18 +375,26 @@ void Gmres::start_cycle(const double *r, cudaStream_t s) {
 }
 
 void Gmres::arnoldi_step(int j, cudaStream_t s) {
-    const int nv = j + 1;
-    dot_device(V.p, ld, nv, w.p, n, partial.p, hcol.p, s);
-    project_out_kernel<<<div_up(n, 256), 256, 0, s>>>(V.p, ld, nv, hcol.p, w.p, n);
+    ArnoldiArgs a;
+    a.V = V.p;
+    a.ld = ld;
+    a.n = n;
+    a.nv = j + 1;
+    a.w = w.p;
+    a.h1 = hcol.p;
+    a.h2 = h2.p;
+    a.nrm2 = scal.p + 1;
+    a.partial = partial.p;
+    a.count = count.p;
+    a.st = st.p;
+    a.j = j;
+    arnoldi_dots_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(a);
     PB_LAUNCH_CHECK();
-    dot_device(V.p, ld, nv, w.p, n, partial.p, h2.p, s);
-    project_out_kernel<<<div_up(n, 256), 256, 0, s>>>(V.p, ld, nv, h2.p, w.p, n);
+    arnoldi_project_dots_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(a);
     PB_LAUNCH_CHECK();
-    add_kernel_launch(hcol.p, h2.p, nv, s);
-    dot_device(w.p, ld, 1, w.p, n, partial.p, scal.p + 1, s);
+    arnoldi_project_norm_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(a);
+    PB_LAUNCH_CHECK();
     scale_copy_kernel<<<div_up(n, 256), 256, 0, s>>>(w.p, scal.p + 1, V.p + (int64_t)(j + 1) * ld, n);
-    PB_LAUNCH_CHECK();
-    givens_kernel<<<1, 1, 0, s>>>(st.p, j, hcol.p, scal.p + 1);
     PB_LAUNCH_CHECK();
     PB_CUDA_TRY(cudaMemcpyAsync(hs.p + 2, &st.p->res_est, sizeof(double), cudaMemcpyDeviceToHost, s));
 }
@@ -309,11 +425,6 @@ void basis_combination(const Gmres &G, int k, double *out, cudaStream_t s) {
     back_solve_kernel<<<1, 1, 0, s>>>(G.st.p, k);
     PB_LAUNCH_CHECK();
     combination_kernel<<<div_up(G.n, 256), 256, 0, s>>>(G.V.p, G.ld, k, G.st.p, out, G.n);
-    PB_LAUNCH_CHECK();
-}
-
-void add_kernel_launch(double *a, const double *b, int n, cudaStream_t s) {
-    add_kernel<<<div_up(n, 256), 256, 0, s>>>(a, b, n);
     PB_LAUNCH_CHECK();
 }
 

@@ -23,6 +23,7 @@ struct Gmres {
     int m = 0;
     DevBuf<double> V, w, partial, hcol, h2, scal, H, cs, sn, g, y;
     DevBuf<GmresState> st;
+    DevBuf<unsigned> count;                                // arrival count of the fused reductions (0 between launches)
     PinnedBuf<double> hs;                                  // 0: ||b||^2, 1: ||r||^2, 2: residual estimate
     void init(int64_t n, int m, cudaStream_t s);
     void norm2_async(const double *x, cudaStream_t s);     // hs[0] = ||x||^2
@@ -43,7 +44,6 @@ void block_jacobi_apply(int64_t n, const double *minv, const double *u_in, const
 // x = sum_c V[c] y[c] (k basis vectors) written into out.
 void basis_combination(const Gmres &G, int k, double *out, cudaStream_t s);
 
-void add_kernel_launch(double *a, const double *b, int n, cudaStream_t s);
 void axpby(double a, const double *x, double b, const double *y, double *out, int64_t n, cudaStream_t s);
 // *out = scale * sum_k q_k phi_k (device scalar)
 void weighted_sum(const double *q, const double *phi, int64_t n, double scale, double *out, cudaStream_t s);
