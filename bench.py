@@ -433,7 +433,15 @@ def _extras(pbbem, ctx, pb, r, d, fleet, triplet):
                "setup_and_solve_s": t_bind}
     for p in tri:
         p.close()
-    return {"gradient": grad, "batch": batch, "binding": binding}
+    from paper_1309_4018_b300.richardson import study
+    from synth.configs import sphere_problem
+    spheres = [sphere_problem(level=l, charges="both") for l in (3, 4, 5)]
+    st = study(spheres, 4.0, ctx, precision="fp64", theta=0.4, P=10, ncrit=100, gmres_tol=1e-10)
+    rich = {"workload": "Kirkwood sphere r=4 A, charges at 0 and 2 A, 512/2048/8192 panels, FP64 treecode "
+                        "(the tests compare the extrapolation with the closed form)",
+            "energies": st.energies, "observed_order": st.order, "extrapolated": st.extrapolated,
+            "solve_s": st.solve_s}
+    return {"gradient": grad, "batch": batch, "binding": binding, "richardson": rich}
 
 
 def main():

@@ -192,3 +192,19 @@ def fleet_ligand(i, n_atoms, seed=4, spacing=PROTEIN_SPACING):
 def ligand_fleet(count=64, n_min=300, n_max=3000, seed=4, spacing=PROTEIN_SPACING):
     """`count` synthetic ligands with atom counts log-uniform in [n_min, n_max] (seed + 1 + i each)."""
     return [fleet_ligand(i, n, seed, spacing) for i, n in enumerate(fleet_sizes(count, n_min, n_max, seed))]
+
+
+def protein_refinements(levels=2, spacing=2.0 * PROTEIN_SPACING, n_atoms=2000, seed=2):
+    """The synthetic protein on nested meshes: its surface at `spacing`, then
+    `levels` refinements that split every panel into four on the same level set
+    (panel area / 4 per level).  Returns problem dicts, coarsest first."""
+    from .molecule import refine_on_level_set
+    at = protein_atoms(n_atoms, seed)
+    base = protein_problem(n_atoms, seed, spacing)
+    s = base["surfaces"][0]
+    out = [base]
+    for v, t in refine_on_level_set(s["verts"], s["tris"], at["xyz"], at["radius"], levels):
+        d = dict(base)
+        d["surfaces"] = [dict(s, verts=v, tris=t)]
+        out.append(d)
+    return out

@@ -239,3 +239,48 @@ def gaussian_surface(xyz, radius, spacing: float, radius_offset: float = 0.0,
         if not np.any(np.einsum("ij,ij->i", nrm, g) >= 0.0):
             return vs, t.astype(np.int32)
     return v, t.astype(np.int32)
+
+
+def _split4(verts, tris):
+    """Split every triangle into four at its edge midpoints (shared midpoints, winding kept)."""
+    v = np.asarray(verts, dtype=np.float64)
+    t = np.asarray(tris, dtype=np.int64)
+    e = np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]])
+    key = np.minimum(e[:, 0], e[:, 1]) * v.shape[0] + np.maximum(e[:, 0], e[:, 1])
+    uk, inv = np.unique(key, return_inverse=True)
+    a, b = uk // v.shape[0], uk % v.shape[0]
+    mid = 0.5 * (v[a] + v[b])
+    m = v.shape[0] + inv.reshape(3, -1).T          # midpoint index of edges (01, 12, 20) per triangle
+    nv = np.vstack([v, mid])
+    t0, t1, t2 = t[:, 0], t[:, 1], t[:, 2]
+    m01, m12, m20 = m[:, 0], m[:, 1], m[:, 2]
+    nt = np.concatenate([np.stack([t0, m01, m20], 1), np.stack([t1, m12, m01], 1),
+                         np.stack([t2, m20, m12], 1), np.stack([m01, m12, m20], 1)])
+    return nv, nt
+
+
+def refine_on_level_set(verts, tris, xyz, radius, levels=1, radius_offset=0.0, beta=BETA, level=1.0):
+    """Nested refinements of a level-set mesh: each level splits every triangle
+    into four and moves the new vertices onto rho = level (Newton steps along
+    grad rho), so the panel area shrinks by 4 per level on the same surface.
+    Returns [(verts, tris int32)] for levels 1..levels.
+    """
+    r = np.asarray(radius, dtype=np.float64) + radius_offset
+    tree = cKDTree(xyz)
+    out = []
+    v, t = np.asarray(verts, dtype=np.float64), np.asarray(tris, dtype=np.int64)
+    for _ in range(levels):
+        n_old = v.shape[0]
+        v, t = _split4(v, t)
+        p = v[n_old:]
+        for _ in range(6):
+            f, g = density_and_gradient(p, xyz, r, beta, tree=tree)
+            g2 = (g * g).sum(1)
+            step = np.where(g2 > 1e-12, (f - level) / np.maximum(g2, 1e-12), 0.0)
+            dv = step[:, None] * g
+            n = np.sqrt((dv * dv).sum(1))
+            dv *= np.minimum(1.0, 0.3 / np.maximum(n, 1e-30))[:, None]
+            p = p - dv
+        v = np.vstack([v[:n_old], p])
+        out.append((v.copy(), t.astype(np.int32)))
+    return out
