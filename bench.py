@@ -192,16 +192,23 @@ def _triplet_member(which):
     return binding_triplet(*TRIPLET)[which]
 
 
+def _variants(_):
+    from synth.configs import model_variants
+    return model_variants()
+
+
 def _batch_inputs():
     """The ligand fleet and the binding triplet, generated in a spawned process pool."""
     import multiprocessing as mp
     from synth.configs import fleet_sizes
     sizes = fleet_sizes(FLEET)
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        var = pool.map_async(_variants, [0])
         tri = pool.map_async(_triplet_member, [0, 1, 2])
         fleet = pool.map(_fleet_member, list(enumerate(sizes)))
         triplet = tri.get()
-    return fleet, triplet
+        variants = var.get()[0]
+    return fleet, triplet, variants
 
 
 # ---------------------------------------------------------------- reference arm (CPU oracle)
@@ -260,7 +267,7 @@ def cpu_baseline(d):
 
 # ---------------------------------------------------------------- GPU arm
 def run_gpu(args):
-    fleet, triplet = _batch_inputs() if args.extras else (None, None)
+    fleet, triplet, variants = _batch_inputs() if args.extras else (None, None, None)
     import torch
     ws, rank = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -359,7 +366,7 @@ def run_gpu(args):
 
     extras = {}
     if args.extras:
-        extras = _extras(pbbem, ctx, pb, r, d, fleet, triplet)
+        extras = _extras(pbbem, ctx, pb, r, d, fleet, triplet, variants)
 
     if rank == 0:
         cpu = cpu_baseline(d)
@@ -393,7 +400,7 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def _extras(pbbem, ctx, pb, r, d, fleet, triplet):
+def _extras(pbbem, ctx, pb, r, d, fleet, triplet, variants):
     """Adjoint gradient of the bench problem, a batched fleet solve and a binding energy."""
     t0 = time.perf_counter()
     g1 = pb.gradient()
@@ -441,7 +448,21 @@ def _extras(pbbem, ctx, pb, r, d, fleet, triplet):
                         "(the tests compare the extrapolation with the closed form)",
             "energies": st.energies, "observed_order": st.order, "extrapolated": st.extrapolated,
             "solve_s": st.solve_s}
-    return {"gradient": grad, "batch": batch, "binding": binding, "richardson": rich}
+    names = list(variants)
+    vp = [pbbem.Problem.from_dict(ctx, variants[k]) for k in names]
+    ts = time.perf_counter()
+    for p in vp:
+        p.setup(precision="mixed", **PARAMS)
+    vr = pbbem.solve_batch(ctx, vp)
+    t_var = time.perf_counter() - ts
+    models = {"workload": "2000-atom molecule with two 3 A solvent cavities and a 2 A Stern layer "
+                          "(Single / Cavity / Stern / Full models)",
+              "panels": {k: int(sum(s["tris"].shape[0] for s in variants[k]["surfaces"])) for k in names},
+              "dG_kJ_mol": {k: x.dG_solv for k, x in zip(names, vr)},
+              "iterations": {k: x.iterations for k, x in zip(names, vr)}, "setup_and_batch_solve_s": t_var}
+    for p in vp:
+        p.close()
+    return {"gradient": grad, "batch": batch, "binding": binding, "richardson": rich, "model_variants": models}
 
 
 def main():

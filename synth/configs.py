@@ -208,3 +208,26 @@ def protein_refinements(levels=2, spacing=2.0 * PROTEIN_SPACING, n_atoms=2000, s
         d["surfaces"] = [dict(s, verts=v, tris=t)]
         out.append(d)
     return out
+
+
+def model_variants(n_atoms=2000, seed=3, spacing=PROTEIN_SPACING, stern_spacing=STERN_SPACING, cavity_level=3):
+    """The four solvent models of the multi-surface molecule (the paper's Single /
+    Cavity / Stern / Full comparison) on the same atoms and meshes:
+    single: molecular surface only; cavity: + the two solvent-filled cavities;
+    stern: + the Stern layer; full: all four surfaces (= multisurface_problem)."""
+    full = multisurface_problem(n_atoms, seed, spacing, stern_spacing, cavity_level)
+    c1, c2, ses, stern = full["surfaces"]
+    ch = full["charges"]
+    ew, eo, kap = EPS_OUT, EPS_IN, KAPPA
+
+    def mk(regions, surfaces, creg):
+        return {"regions": regions, "surfaces": surfaces, "charges": dict(ch, region=creg)}
+
+    single = mk([{"eps": eo, "kappa": 0.0}, {"eps": ew, "kappa": kap}],
+                [dict(ses, inner=0, outer=1)], 0)
+    cavity = mk([{"eps": ew, "kappa": 0.0}, {"eps": ew, "kappa": 0.0}, {"eps": eo, "kappa": 0.0},
+                 {"eps": ew, "kappa": kap}],
+                [dict(c1, inner=0, outer=2), dict(c2, inner=1, outer=2), dict(ses, inner=2, outer=3)], 2)
+    stern_m = mk([{"eps": eo, "kappa": 0.0}, {"eps": ew, "kappa": 0.0}, {"eps": ew, "kappa": kap}],
+                 [dict(ses, inner=0, outer=1), dict(stern, inner=1, outer=2)], 0)
+    return {"single": single, "cavity": cavity, "stern": stern_m, "full": full}
