@@ -462,7 +462,30 @@ def _extras(pbbem, ctx, pb, r, d, fleet, triplet, variants):
               "iterations": {k: x.iterations for k, x in zip(names, vr)}, "setup_and_batch_solve_s": t_var}
     for p in vp:
         p.close()
-    return {"gradient": grad, "batch": batch, "binding": binding, "richardson": rich, "model_variants": models}
+    from paper_1309_4018_b300.pareto import pareto_front, sweep
+    # reference: every knob at its most accurate setting on the same mesh
+    best = dict(PARAMS, precision="mixed", K=7, K_fine=19, thres=4.0, theta=0.3, P=10, gmres_tol=1e-7)
+    ref_pb = pbbem.Problem.from_dict(ctx, d)
+    ref_pb.setup(**best)
+    ref = ref_pb.solve().dG_solv
+    ref_pb.close()
+    grid = []
+    for theta, P in ((0.7, 3), (0.6, 4), (0.5, 6), (0.4, 8)):
+        for tol in (1e-3, 1e-4, 1e-6):
+            grid.append((f"theta={theta} P={P} tol={tol:g}", d,
+                         dict(PARAMS, precision="mixed", theta=theta, P=P, gmres_tol=tol)))
+    for k, v in (("K", 1), ("K", 7), ("K_fine", 3), ("K_fine", 7), ("thres", 0.5), ("thres", 1.0),
+                 ("thres", 4.0), ("no_precond", 1)):
+        grid.append((f"theta=0.5 P=6 tol=0.0001 {k}={v}", d, dict(PARAMS, precision="mixed", **{k: v})))
+    res = sweep(grid, ref, ctx)
+    pareto = {"workload": WORKLOAD.split(",")[0] + ", same mesh; base K=3 K_fine=19 thres=2; reference: "
+                                                   "K=7 K_fine=19 thres=4 theta=0.3 P=10 tol 1e-7",
+              "reference_dG_kJ_mol": ref,
+              "cases": [{"label": c.label, "time_s": c.time_s, "rel_error": c.rel_error,
+                         "iterations": c.iterations} for c in res],
+              "front": [c.label for c in pareto_front(res)]}
+    return {"gradient": grad, "batch": batch, "binding": binding, "richardson": rich, "model_variants": models,
+            "pareto": pareto}
 
 
 def main():

@@ -17,11 +17,13 @@ pytestmark = pytest.mark.gpu
 DIRECT = dict(theta=-1.0, precision="fp64", ncrit=64)
 
 
-@pytest.mark.parametrize("level,K", [(3, 3), (4, 3), (3, 1), (2, 7)])
-def test_direct_matvec_matches_dense(level, K):
+@pytest.mark.parametrize("level,K,K_fine,thres", [(3, 3, 19, 2.0), (4, 3, 19, 2.0), (3, 1, 19, 2.0), (2, 7, 19, 2.0),
+                                                   (3, 3, 7, 0.5), (3, 3, 3, 4.0), (3, 7, 7, 1.0)])
+def test_direct_matvec_matches_dense(level, K, K_fine, thres):
+    # the quadrature knobs the accuracy/time sweeps vary: K, K_fine and the near-singular radius thres
     d = sphere_problem(level=level, charges="both")
-    pb = problem(d, K=K, **DIRECT)
-    A = OD.operator_matrix(d, dict(K=K))
+    pb = problem(d, K=K, K_fine=K_fine, thres=thres, **DIRECT)
+    A = OD.operator_matrix(d, dict(K=K, K_fine=K_fine, thres=thres))
     rng = np.random.default_rng(level)
     for _ in range(2):
         x = rng.normal(size=A.shape[0])
