@@ -110,6 +110,56 @@ int pb_add_region(pb_problem *pb, double eps, double kappa, int *region_id);
  * a zero-area triangle. */
 int pb_add_surface(pb_problem *pb, const double *verts, int64_t nv, const int32_t *tris,
                    int64_t nt, int inner, int outer, int *surface_id);
+/* Molecular surface generated on the device from atoms.  The paper meshes the
+ * solvent-excluded surface with MSMS (Sec. 2.2, Sec. 3); this builds instead
+ * the level set rho = level of the Gaussian density
+ *   rho(x) = sum_a [|x - x_a| <= cutoff R_a] exp(-beta (|x - x_a|^2 / R_a^2 - 1)),
+ * R_a = radius[a] + radius_offset, on the nodes lo + spacing (i, j, k) of a grid
+ * reaching margin + max R_a beyond the atoms; the triangles are those of
+ * marching tetrahedra on the six-tetrahedron (Kuhn) split of every grid cube,
+ * with a vertex at the linear zero of rho - level on every crossing edge (edge
+ * parameter clamped to [tclamp, 1 - tclamp]); only the connected component of
+ * the crossing of largest grid x index (the outer surface) is kept, oriented
+ * towards rho < level; then up to smooth_iters rounds move every vertex a
+ * fraction relax towards the mean of its neighbours and project it
+ * newton_steps times onto the level set along grad rho (steps capped at
+ * max_step), using the largest round count that leaves no triangle facing up
+ * grad rho.  A zero field takes the default in brackets. */
+typedef struct {
+    double spacing;        /* grid spacing in A; required, > 0 */
+    double beta;           /* density decay [0.5] */
+    double cutoff;         /* an atom contributes within cutoff * R_a [2.7] */
+    double radius_offset;  /* added to every radius (a Stern layer: 2) [0] */
+    double margin;         /* grid padding in A beyond the largest radius [4] */
+    double level;          /* iso level [1] */
+    double tclamp;         /* edge parameter clamp, < 0.5 [0.02]; negative: no clamp */
+    double relax;          /* umbrella step fraction, (0, 1] [0.5] */
+    double max_step;       /* length cap of a projection step in A [0.3] */
+    int smooth_iters;      /* smoothing rounds, <= 64 [5]; negative: none */
+    int newton_steps;      /* projections per round, <= 64 [3]; negative: none */
+} pb_surf_params;
+/* Adds the generated surface between regions inner and outer, exactly as
+ * pb_add_surface would add its mesh.  xyz: na x 3 doubles, radius: na doubles
+ * (host; copied).  PB_EINVAL on bad parameters or atoms, a grid of more than
+ * 4096 nodes per axis or 2^31 nodes, or a density with no crossing on the
+ * grid; PB_ETIMEOUT if the device component labelling ran out of its bounded
+ * step budget.  Synchronises the context stream. */
+int pb_add_gaussian_surface(pb_problem *pb, const double *xyz, const double *radius, int64_t na,
+                            const pb_surf_params *sp, int inner, int outer, int *surface_id);
+/* Sizes of a surface and, for a generated one, how it was made. */
+typedef struct {
+    int64_t nv, nt;          /* vertices, triangles */
+    int generated;           /* 1: made by pb_add_gaussian_surface */
+    int grid[3];             /* density grid nodes per axis */
+    int rounds;              /* smoothing rounds used */
+    int pad_;
+    int64_t components;      /* connected components of the level set on the grid */
+    int64_t raw_nv, raw_nt;  /* vertices, triangles before the outer component was taken */
+    double gen_ms;           /* device time of the generation (CUDA events) */
+} pb_surface_info;
+int pb_surface_info_get(pb_problem *pb, int surface, pb_surface_info *out);
+/* Copies a surface's mesh to host arrays of nv x 3 doubles and nt x 3 ints (either may be NULL). */
+int pb_surface_export(pb_problem *pb, int surface, double *verts, int32_t *tris);
 /* Point charges (Eq. pde) inside region `region` (which must have kappa = 0). */
 int pb_set_charges(pb_problem *pb, const double *xyz, const double *q, int64_t nc, int region);
 

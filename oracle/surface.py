@@ -125,10 +125,15 @@ def node_coords(lo, h, shape):
     return np.stack([X, Y, Z], -1)
 
 
-def density(points, xyz, r_eff, beta, cutoff, chunk=4096):
+def _chunk(na):
+    return max(16, 2_000_000 // max(int(na), 1))
+
+
+def density(points, xyz, r_eff, beta, cutoff):
     """rho at `points` [m, 3] by its definition (sum over every atom)."""
     points = np.asarray(points, dtype=np.float64).reshape(-1, 3)
     xyz = np.asarray(xyz, dtype=np.float64)
+    chunk = _chunk(xyz.shape[0])
     R = np.asarray(r_eff, dtype=np.float64)
     out = np.zeros(points.shape[0])
     for s in range(0, points.shape[0], chunk):
@@ -142,10 +147,11 @@ def density(points, xyz, r_eff, beta, cutoff, chunk=4096):
     return out
 
 
-def density_gradient(points, xyz, r_eff, beta, cutoff, chunk=2048):
+def density_gradient(points, xyz, r_eff, beta, cutoff):
     """rho and grad rho at `points` [m, 3]: d/dx of every term is -2 beta (x - x_a) / R_a^2 times it."""
     points = np.asarray(points, dtype=np.float64).reshape(-1, 3)
     xyz = np.asarray(xyz, dtype=np.float64)
+    chunk = _chunk(xyz.shape[0])
     R = np.asarray(r_eff, dtype=np.float64)
     rho = np.zeros(points.shape[0])
     grad = np.zeros((points.shape[0], 3))

@@ -12,6 +12,7 @@
 #include "gmres.cuh"
 #include "model.cuh"
 #include "problem.cuh"
+#include "surface.cuh"
 #include "tree.cuh"
 #include "treecode.cuh"
 
@@ -770,6 +771,68 @@ int pb_add_surface(pb_problem *pb, const double *verts, int64_t nv, const int32_
         pb->sin.push_back(std::move(si));
         pb->is_setup = false;
         if (surface_id) *surface_id = (int)pb->sin.size() - 1;
+    });
+}
+
+int pb_add_gaussian_surface(pb_problem *pb, const double *xyz, const double *radius, int64_t na,
+                            const pb_surf_params *sp, int inner, int outer, int *surface_id) {
+    if (!pb) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        if (!sp) fail(PB_EINVAL, "surface parameters missing");
+        if (inner < 0 || outer < 0 || inner >= (int)pb->regions.size() || outer >= (int)pb->regions.size() ||
+            inner == outer)
+            fail(PB_EINVAL, "surface references an unknown region");
+        SurfGenParams gp;
+        gp.spacing = sp->spacing;
+        if (sp->beta != 0.0) gp.beta = sp->beta;
+        if (sp->cutoff != 0.0) gp.cutoff = sp->cutoff;
+        gp.radius_offset = sp->radius_offset;
+        if (sp->margin != 0.0) gp.margin = sp->margin;
+        if (sp->level != 0.0) gp.level = sp->level;
+        if (sp->tclamp != 0.0) gp.tclamp = sp->tclamp < 0.0 ? 0.0 : sp->tclamp;
+        if (sp->relax != 0.0) gp.relax = sp->relax;
+        if (sp->max_step != 0.0) gp.max_step = sp->max_step;
+        if (sp->smooth_iters != 0) gp.smooth_iters = sp->smooth_iters < 0 ? 0 : sp->smooth_iters;
+        if (sp->newton_steps != 0) gp.newton_steps = sp->newton_steps < 0 ? 0 : sp->newton_steps;
+        set_device(pb->ctx);
+        SurfIn si;
+        gaussian_surface(xyz, radius, na, gp, pb->stream, si);
+        if (si.nt > ((int64_t)1 << 29) / 19) fail(PB_EINVAL, "too many triangles");
+        si.inner = inner;
+        si.outer = outer;
+        pb->sin.push_back(std::move(si));
+        pb->is_setup = false;
+        if (surface_id) *surface_id = (int)pb->sin.size() - 1;
+    });
+}
+
+int pb_surface_info_get(pb_problem *pb, int surface, pb_surface_info *out) {
+    if (!pb) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        if (!out || surface < 0 || surface >= (int)pb->sin.size()) fail(PB_EINVAL, "unknown surface");
+        const SurfIn &si = pb->sin[surface];
+        std::memset(out, 0, sizeof(*out));
+        out->nv = si.nv;
+        out->nt = si.nt;
+        out->generated = si.generated ? 1 : 0;
+        for (int d = 0; d < 3; ++d) out->grid[d] = si.gen.shape[d];
+        out->rounds = si.gen.rounds;
+        out->components = si.gen.components;
+        out->raw_nv = si.gen.raw_nv;
+        out->raw_nt = si.gen.raw_nt;
+        out->gen_ms = si.gen.ms;
+    });
+}
+
+int pb_surface_export(pb_problem *pb, int surface, double *verts, int32_t *tris) {
+    if (!pb) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        if (surface < 0 || surface >= (int)pb->sin.size()) fail(PB_EINVAL, "unknown surface");
+        set_device(pb->ctx);
+        const SurfIn &si = pb->sin[surface];
+        if (verts) si.v.download(verts, 3 * si.nv, pb->stream);
+        if (tris) si.t.download(tris, 3 * si.nt, pb->stream);
+        PB_CUDA_TRY(cudaStreamSynchronize(pb->stream));
     });
 }
 

@@ -21,11 +21,21 @@ struct pb_ctx {
 
 namespace pb {
 
+// Record of a surface built on the device from atoms (surface.cu).
+struct SurfGenInfo {
+    int shape[3] = {0, 0, 0};    // density grid nodes per axis
+    int rounds = 0;              // smoothing rounds used
+    int64_t components = 0, raw_nv = 0, raw_nt = 0;
+    float ms = 0.0f;
+};
+
 struct SurfIn {
     int64_t nv = 0, nt = 0;
-    DevBuf<double> v;      // device copy made when the surface is added
+    DevBuf<double> v;      // device copy made when the surface is added (or the generated mesh)
     DevBuf<int32_t> t;
     int inner = -1, outer = -1;
+    bool generated = false;
+    SurfGenInfo gen;
 };
 
 // One (pair, kernel) contribution cK * K + cV * V of region `region` to a row

@@ -49,6 +49,20 @@ class pb_grad(ctypes.Structure):
                 ("iterations", ctypes.c_int), ("matvecs", ctypes.c_int), ("grad_ms", ctypes.c_double)]
 
 
+class pb_surf_params(ctypes.Structure):
+    _fields_ = [("spacing", ctypes.c_double), ("beta", ctypes.c_double), ("cutoff", ctypes.c_double),
+                ("radius_offset", ctypes.c_double), ("margin", ctypes.c_double), ("level", ctypes.c_double),
+                ("tclamp", ctypes.c_double), ("relax", ctypes.c_double), ("max_step", ctypes.c_double),
+                ("smooth_iters", ctypes.c_int), ("newton_steps", ctypes.c_int)]
+
+
+class pb_surface_info(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int64), ("nt", ctypes.c_int64), ("generated", ctypes.c_int),
+                ("grid", ctypes.c_int * 3), ("rounds", ctypes.c_int), ("pad_", ctypes.c_int),
+                ("components", ctypes.c_int64), ("raw_nv", ctypes.c_int64), ("raw_nt", ctypes.c_int64),
+                ("gen_ms", ctypes.c_double)]
+
+
 class pb_tree_info(ctypes.Structure):
     _fields_ = [("n_points", ctypes.c_int64), ("n_nodes", ctypes.c_int32), ("n_leaves", ctypes.c_int32),
                 ("corner", ctypes.c_double * 3), ("side", ctypes.c_double)]
@@ -68,6 +82,10 @@ _SIGS = {
     "pb_add_region": ([_vp, _dbl, _dbl, ctypes.POINTER(_int)], _int),
     "pb_add_surface": ([_vp, _vp, _i64, _vp, _i64, _int, _int, ctypes.POINTER(_int)], _int),
     "pb_set_charges": ([_vp, _vp, _vp, _i64, _int], _int),
+    "pb_add_gaussian_surface": ([_vp, _vp, _vp, _i64, ctypes.POINTER(pb_surf_params), _int, _int,
+                                 ctypes.POINTER(_int)], _int),
+    "pb_surface_info_get": ([_vp, _int, ctypes.POINTER(pb_surface_info)], _int),
+    "pb_surface_export": ([_vp, _int, _vp, _vp], _int),
     "pb_setup": ([_vp, ctypes.POINTER(pb_params)], _int),
     "pb_num_unknowns": ([_vp], _i64),
     "pb_apply_operator": ([_vp, _vp, _vp, _int], _int),
@@ -218,7 +236,11 @@ class Problem:
         for r in d["regions"]:
             pb.add_region(r["eps"], r["kappa"])
         for s in d["surfaces"]:
-            pb.add_surface(s["verts"], s["tris"], s["inner"], s["outer"])
+            if "atoms" in s:      # generated on the device: {"xyz", "radius"} plus pb_surf_params fields
+                pb.add_gaussian_surface(s["atoms"]["xyz"], s["atoms"]["radius"], s["inner"], s["outer"],
+                                        **s.get("surf_params", {}))
+            else:
+                pb.add_surface(s["verts"], s["tris"], s["inner"], s["outer"])
         ch = d.get("charges")
         if ch is not None:
             pb.set_charges(ch["xyz"], ch["q"], ch["region"])
@@ -237,6 +259,35 @@ class Problem:
         self.ctx.check(_lib.pb_add_surface(self._h, _ptr(v), v.shape[0], _ptr(t), t.shape[0], int(inner),
                                            int(outer), ctypes.byref(sid)))
         return sid.value
+
+    def add_gaussian_surface(self, xyz, radius, inner, outer, **params) -> int:
+        """Surface generated on the device from atoms (pb_add_gaussian_surface); params are
+        pb_surf_params fields (spacing required)."""
+        x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        r = np.ascontiguousarray(radius, dtype=np.float64).ravel()
+        sp = pb_surf_params()
+        for k, v in params.items():
+            if not hasattr(sp, k):
+                raise TypeError(f"unknown surface parameter {k}")
+            setattr(sp, k, v)
+        sid = _int()
+        self.ctx.check(_lib.pb_add_gaussian_surface(self._h, _ptr(x), _ptr(r), r.size, ctypes.byref(sp), int(inner),
+                                                    int(outer), ctypes.byref(sid)))
+        return sid.value
+
+    def surface_info(self, surface: int) -> dict:
+        inf = pb_surface_info()
+        self.ctx.check(_lib.pb_surface_info_get(self._h, int(surface), ctypes.byref(inf)))
+        return dict(nv=inf.nv, nt=inf.nt, generated=bool(inf.generated), grid=tuple(inf.grid), rounds=inf.rounds,
+                    components=inf.components, raw_nv=inf.raw_nv, raw_nt=inf.raw_nt, gen_ms=inf.gen_ms)
+
+    def surface_mesh(self, surface: int):
+        """(verts [nv, 3] float64, tris [nt, 3] int32) of a surface, copied from the device."""
+        inf = self.surface_info(surface)
+        v = np.empty((inf["nv"], 3))
+        t = np.empty((inf["nt"], 3), dtype=np.int32)
+        self.ctx.check(_lib.pb_surface_export(self._h, int(surface), _ptr(v), _ptr(t)))
+        return v, t
 
     def set_charges(self, xyz, q, region):
         x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
