@@ -6,8 +6,8 @@
 //   rho(x) = sum_a [|x - x_a| <= cutoff R_a] exp(-beta (|x - x_a|^2 / R_a^2 - 1)),
 //
 // R_a the atomic radius plus an offset (+2 A for a Stern layer):
-//   1. density at the nodes lo + h (i, j, k) of a grid around the atoms, each
-//      node summing the atoms of the 27 atom cells around it;
+//   1. density at the nodes lo + h (i, j, k) of a grid around the atoms, one
+//      warp per node summing the atoms of the 27 atom cells around it;
 //   2. one vertex on every node edge of the Kuhn split (7 positive directions)
 //      whose two ends differ in the test rho >= level, at the zero of the
 //      linear interpolant of rho - level (parameter clamped to
@@ -21,7 +21,7 @@
 //      crossing of largest x index) is the outer surface and is kept;
 //   5. smoothing rounds (umbrella step, then Newton projections onto the
 //      level set along grad rho); the largest round count that folds no
-//      triangle against grad rho is used.
+//      triangle against grad rho is used (checked from the last round down).
 // Every decision that picks an integer (inside test, crossings, components)
 // is taken on FP64 values; there are two host synchronisations (the raw
 // vertex and triangle counts, then the final counts).
@@ -43,7 +43,9 @@ struct Grid {
 struct Cells {
     double c0[3], cs;
     int nc[3];
-    const dvec4 *atoms;       // sorted by cell: x, y, z, R
+    const dvec4 *atoms;       // sorted by cell: x, y, z, 1 / R^2
+    const double *rc2;        // same order: (cutoff R)^2
+    const float4 *atoms32;    // same order: x - c0, y - c0, z - c0, rejection bound on d^2 (FP32)
     const int64_t *start;     // first atom of every cell; ncell + 1 entries
 };
 
@@ -72,40 +74,98 @@ __device__ __forceinline__ int cell_of(double x, double c0, double cs, int n) {
     return (int)u;
 }
 
-// rho (and grad rho) at p: every atom within its cutoff, atoms of the 27 cells around p.
+// rho (and grad rho) at p, by one warp: every atom within its cutoff, atoms of
+// the 27 cells around p.  The lanes first sweep the candidates with an FP32
+// distance test and append the survivors to a per-warp list (buf, kSurvCap
+// entries); its bound exceeds (cutoff R)^2 by more than the FP32 rounding of
+// the coordinates can move d^2, so the list holds every atom the FP64 test
+// keeps.  The lanes then take the listed atoms 32 at a time through the FP64
+// test and exponential, so that the FP64 work runs with all lanes busy.  The
+// survivors' order is fixed and the butterfly reduction leaves the same bits
+// in every lane.
+constexpr int kSurvCap = 96;
+
 template <bool GRAD>
-__device__ void density_at(const Cells &C, const Shape &S, double px, double py, double pz, double &rho,
-                           double *g) {
+__device__ __forceinline__ void eval_survivors(const Cells &C, const Shape &S, double px, double py, double pz,
+                                               const int *buf, int n, int lane, double &acc, double &g0, double &g1,
+                                               double &g2) {
+    const double m2b = -2.0 * S.beta;
+    for (int i = lane; i < n; i += 32) {
+        const int a = buf[i];
+        const dvec4 A = C.atoms[a];
+        const double gx = __dsub_rn(px, A.x), gy = __dsub_rn(py, A.y), gz = __dsub_rn(pz, A.z);
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(gx, gx), __dmul_rn(gy, gy)), __dmul_rn(gz, gz));
+        if (d2 > C.rc2[a]) continue;
+        const double e = exp(__dmul_rn(-S.beta, __dsub_rn(__dmul_rn(d2, A.w), 1.0)));
+        acc = __dadd_rn(acc, e);
+        if (GRAD) {
+            const double c = e * m2b * A.w;      // d/dx of the term is c (x - x_a)
+            g0 = fma(c, gx, g0);
+            g1 = fma(c, gy, g1);
+            g2 = fma(c, gz, g2);
+        }
+    }
+}
+
+template <bool GRAD>
+__device__ void density_warp(const Cells &C, const Shape &S, double px, double py, double pz, int lane, int *buf,
+                             double &rho, double *g) {
     const int q0 = cell_of(px, C.c0[0], C.cs, C.nc[0]);
     const int q1 = cell_of(py, C.c0[1], C.cs, C.nc[1]);
     const int q2 = cell_of(pz, C.c0[2], C.cs, C.nc[2]);
     const int z0 = max(q2 - 1, 0), z1 = min(q2 + 1, C.nc[2] - 1);
-    rho = 0.0;
-    if (GRAD) g[0] = g[1] = g[2] = 0.0;
-    if (z0 > z1) return;
-    const double m2b = -2.0 * S.beta;
-    for (int ix = max(q0 - 1, 0); ix <= min(q0 + 1, C.nc[0] - 1); ++ix)
-        for (int iy = max(q1 - 1, 0); iy <= min(q1 + 1, C.nc[1] - 1); ++iy) {
-            const int64_t row = ((int64_t)ix * C.nc[1] + iy) * C.nc[2];
-            const int64_t a1 = C.start[row + z1 + 1];
-            for (int64_t a = C.start[row + z0]; a < a1; ++a) {
-                const dvec4 A = C.atoms[a];
-                const double gx = __dsub_rn(px, A.x), gy = __dsub_rn(py, A.y), gz = __dsub_rn(pz, A.z);
-                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(gx, gx), __dmul_rn(gy, gy)), __dmul_rn(gz, gz));
-                const double rc = __dmul_rn(S.cutoff, A.w);
-                if (d2 > __dmul_rn(rc, rc)) continue;
-                const double R2 = __dmul_rn(A.w, A.w);
-                const double e = exp(__dmul_rn(-S.beta, __dsub_rn(__ddiv_rn(d2, R2), 1.0)));
-                rho = __dadd_rn(rho, e);
-                if (GRAD) {
-                    const double em = __dmul_rn(e, m2b);
-                    g[0] = __dadd_rn(g[0], __ddiv_rn(__dmul_rn(em, gx), R2));
-                    g[1] = __dadd_rn(g[1], __ddiv_rn(__dmul_rn(em, gy), R2));
-                    g[2] = __dadd_rn(g[2], __ddiv_rn(__dmul_rn(em, gz), R2));
+    const float fx = (float)(px - C.c0[0]), fy = (float)(py - C.c0[1]), fz = (float)(pz - C.c0[2]);
+    double acc = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    int n = 0;
+    if (z0 <= z1)
+        for (int ix = max(q0 - 1, 0); ix <= min(q0 + 1, C.nc[0] - 1); ++ix)
+            for (int iy = max(q1 - 1, 0); iy <= min(q1 + 1, C.nc[1] - 1); ++iy) {
+                const int64_t row = ((int64_t)ix * C.nc[1] + iy) * C.nc[2];
+                const int64_t a1 = C.start[row + z1 + 1];
+                for (int64_t base = C.start[row + z0]; base < a1; base += 32) {
+                    const int64_t a = base + lane;
+                    bool keep = false;
+                    if (a < a1) {
+                        const float4 F = C.atoms32[a];
+                        const float dx = fx - F.x, dy = fy - F.y, dz = fz - F.z;
+                        keep = dx * dx + dy * dy + dz * dz <= F.w;
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, keep);
+                    if (keep) buf[n + __popc(m & ((1u << lane) - 1u))] = (int)a;
+                    n += __popc(m);
+                    if (n > kSurvCap - 32) {
+                        __syncwarp();
+                        eval_survivors<GRAD>(C, S, px, py, pz, buf, n, lane, acc, g0, g1, g2);
+                        __syncwarp();
+                        n = 0;
+                    }
                 }
             }
+    __syncwarp();
+    eval_survivors<GRAD>(C, S, px, py, pz, buf, n, lane, acc, g0, g1, g2);
+    __syncwarp();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+        if (GRAD) {
+            g0 = __dadd_rn(g0, __shfl_xor_sync(0xffffffffu, g0, o));
+            g1 = __dadd_rn(g1, __shfl_xor_sync(0xffffffffu, g1, o));
+            g2 = __dadd_rn(g2, __shfl_xor_sync(0xffffffffu, g2, o));
         }
+    }
+    rho = acc;
+    if (GRAD) {
+        g[0] = g0;
+        g[1] = g1;
+        g[2] = g2;
+    }
 }
+
+// 256-thread blocks, one warp per point; each warp's survivor list in shared memory
+constexpr int kWarpsPerBlock = 8;
+#define PB_SURV_BUF(name) \
+    __shared__ int name##_all[kWarpsPerBlock][kSurvCap]; \
+    int *name = name##_all[threadIdx.x >> 5]
 
 // ------------------------------------------------------------------ atoms into cells
 __global__ void pack_atoms_kernel(int64_t na, const double *__restrict__ xyz, const double *__restrict__ r,
@@ -127,23 +187,38 @@ __global__ void cell_count_kernel(int64_t na, const uint64_t *__restrict__ key, 
     if (a < na) atomicAdd(cnt + key[a], 1);
 }
 
+// Sorted FP64 atoms (position, 1 / R^2), their cutoff (cutoff R)^2 and their
+// FP32 prefilter records.  ecoord bounds the
+// FP32 rounding error of a coordinate relative to c0 (query or atom), so
+// |d^2_FP32 - d^2| stays below the bound's excess over (cutoff R)^2.
 __global__ void gather_atoms_kernel(int64_t na, const int32_t *__restrict__ idx, const dvec4 *__restrict__ in,
-                                    dvec4 *__restrict__ out) {
+                                    Cells C, double cutoff, double ecoord, dvec4 *__restrict__ out,
+                                    double *__restrict__ rc2, float4 *__restrict__ out32) {
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (a < na) out[a] = in[idx[a]];
+    if (a >= na) return;
+    const dvec4 A = in[idx[a]];
+    out[a] = dvec4{A.x, A.y, A.z, 1.0 / __dmul_rn(A.w, A.w)};
+    const double rc = __dmul_rn(cutoff, A.w);
+    rc2[a] = __dmul_rn(rc, rc);
+    const double rp = rc + 8.0 * ecoord;
+    out32[a] = make_float4((float)(A.x - C.c0[0]), (float)(A.y - C.c0[1]), (float)(A.z - C.c0[2]),
+                           (float)(rp * rp * (1.0 + 1e-5)));
 }
 
 // ------------------------------------------------------------------ grid
+// One warp per node.
 __global__ void density_kernel(Grid g, Cells C, Shape S, double *__restrict__ rho) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (p >= g.nn) return;
     const int k = (int)(p % g.n[2]);
     const int64_t ij = p / g.n[2];
     const int j = (int)(ij % g.n[1]), i = (int)(ij / g.n[1]);
+    PB_SURV_BUF(buf);
     double r;
-    density_at<false>(C, S, node_coord(g.lo[0], g.h, i), node_coord(g.lo[1], g.h, j), node_coord(g.lo[2], g.h, k), r,
-                      nullptr);
-    rho[p] = r;
+    density_warp<false>(C, S, node_coord(g.lo[0], g.h, i), node_coord(g.lo[1], g.h, j), node_coord(g.lo[2], g.h, k),
+                        lane, buf, r, nullptr);
+    if (lane == 0) rho[p] = r;
 }
 
 // Crossing flags of the 7 edges leaving every node, and their count.
@@ -402,7 +477,8 @@ __global__ void sort_neighbours_kernel(const int64_t *__restrict__ nvk, const in
 __global__ void smooth_kernel(const int64_t *__restrict__ nvk, const int64_t *__restrict__ nstart,
                               const int32_t *__restrict__ nbr, const int32_t *__restrict__ udeg, Cells C, Shape S,
                               const double *__restrict__ vin, double *__restrict__ vout) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (v >= *nvk) return;
     const int64_t s = nstart[v];
     const int n = udeg[v];
@@ -416,9 +492,10 @@ __global__ void smooth_kernel(const int64_t *__restrict__ nvk, const int64_t *__
         const double o = vin[3 * v + a];
         x[a] = n > 0 ? __dadd_rn(o, __dmul_rn(S.relax, __dsub_rn(__ddiv_rn(sum[a], (double)n), o))) : o;
     }
+    PB_SURV_BUF(buf);
     for (int it = 0; it < S.newton_steps; ++it) {
         double rho, g[3];
-        density_at<true>(C, S, x[0], x[1], x[2], rho, g);
+        density_warp<true>(C, S, x[0], x[1], x[2], lane, buf, rho, g);
         const double g2 = __dadd_rn(__dadd_rn(__dmul_rn(g[0], g[0]), __dmul_rn(g[1], g[1])), __dmul_rn(g[2], g[2]));
         const double st = g2 > 1e-12 ? __ddiv_rn(__dsub_rn(rho, S.level), g2) : 0.0;
         double dv[3] = {__dmul_rn(st, g[0]), __dmul_rn(st, g[1]), __dmul_rn(st, g[2])};
@@ -427,14 +504,20 @@ __global__ void smooth_kernel(const int64_t *__restrict__ nvk, const int64_t *__
         const double sc = fmin(1.0, __ddiv_rn(S.max_step, fmax(len, 1e-30)));
         for (int a = 0; a < 3; ++a) x[a] = __dsub_rn(x[a], __dmul_rn(dv[a], sc));
     }
-    for (int a = 0; a < 3; ++a) vout[3 * v + a] = x[a];
+    if (lane < 3) vout[3 * v + lane] = x[lane];
 }
 
-// Triangles whose normal has a non-negative component along grad rho at the centroid.
+// Triangles of round r whose normal has a non-negative component along grad
+// rho at the centroid, counted into folds[r].  Rounds are checked from the
+// last down; a round is skipped once a later round is known to fold nothing.
 __global__ void fold_kernel(const int64_t *__restrict__ ntk, const int32_t *__restrict__ tris,
-                            const double *__restrict__ v, Cells C, Shape S, unsigned long long *__restrict__ folds) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                            const double *__restrict__ v, Cells C, Shape S, unsigned long long *__restrict__ folds,
+                            int r, int R) {
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (t >= *ntk) return;
+    for (int q = r + 1; q <= R; ++q)
+        if (folds[q] == 0) return;
     const double *A = v + 3 * (int64_t)tris[3 * t], *B = v + 3 * (int64_t)tris[3 * t + 1],
                  *Cc = v + 3 * (int64_t)tris[3 * t + 2];
     const double e1[3] = {__dsub_rn(B[0], A[0]), __dsub_rn(B[1], A[1]), __dsub_rn(B[2], A[2])};
@@ -444,10 +527,11 @@ __global__ void fold_kernel(const int64_t *__restrict__ ntk, const int32_t *__re
                          __dsub_rn(__dmul_rn(e1[0], e2[1]), __dmul_rn(e1[1], e2[0]))};
     double c[3];
     for (int a = 0; a < 3; ++a) c[a] = __ddiv_rn(__dadd_rn(__dadd_rn(A[a], B[a]), Cc[a]), 3.0);
+    PB_SURV_BUF(buf);
     double rho, g[3];
-    density_at<true>(C, S, c[0], c[1], c[2], rho, g);
+    density_warp<true>(C, S, c[0], c[1], c[2], lane, buf, rho, g);
     const double dot = __dadd_rn(__dadd_rn(__dmul_rn(n[0], g[0]), __dmul_rn(n[1], g[1])), __dmul_rn(n[2], g[2]));
-    if (dot >= 0.0) atomicAdd(folds, 1ull);
+    if (lane == 0 && dot >= 0.0) atomicAdd(folds + r, 1ull);
 }
 
 __device__ __forceinline__ int rounds_used(const unsigned long long *folds, int R) {
@@ -523,6 +607,12 @@ void gaussian_surface(const double *xyz, const double *radius, int64_t na, const
         ncell *= C.nc[d];
     }
     Shape S{p.beta, p.cutoff, p.level, p.tclamp, p.relax, p.max_step, p.newton_steps};
+    // largest |coordinate - c0| of any atom or query point (grid nodes, vertices, centroids), and
+    // the FP32 rounding bound of such a coordinate (two roundings)
+    double reach = 0.0;
+    for (int d = 0; d < 3; ++d)
+        reach = std::max(reach, std::fabs(g.lo[d] - C.c0[d]) + g.h * (g.n[d] - 1) + p.spacing);
+    const double ecoord = (reach + 1.0) * std::ldexp(1.0, -22);
 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     PB_CUDA_TRY(cudaEventCreate(&e0));
@@ -538,6 +628,8 @@ void gaussian_surface(const double *xyz, const double *radius, int64_t na, const
     PB_CUDA_TRY(cudaMemcpyAsync(axyz.p, xyz, 3 * na * sizeof(double), cudaMemcpyHostToDevice, s));
     PB_CUDA_TRY(cudaMemcpyAsync(arad.p, radius, na * sizeof(double), cudaMemcpyHostToDevice, s));
     TmpBuf<dvec4> packed(na, s), sorted(na, s);
+    TmpBuf<float4> sorted32(na, s);
+    TmpBuf<double> rc2(na, s);
     TmpBuf<uint64_t> key(na, s);
     TmpBuf<int32_t> idx(na, s), ccount(ncell, s);
     TmpBuf<int64_t> cstart(ncell + 1, s);
@@ -548,12 +640,15 @@ void gaussian_surface(const double *xyz, const double *radius, int64_t na, const
     cell_count_kernel<<<div_up(na, 256), 256, 0, s>>>(na, key.p, ccount.p);
     PB_LAUNCH_CHECK();
     exclusive_scan_i32_to_i64(ccount.p, cstart.p, ncell, s);
-    gather_atoms_kernel<<<div_up(na, 256), 256, 0, s>>>(na, idx.p, packed.p, sorted.p);
+    gather_atoms_kernel<<<div_up(na, 256), 256, 0, s>>>(na, idx.p, packed.p, C, p.cutoff, ecoord, sorted.p, rc2.p,
+                                                         sorted32.p);
     PB_LAUNCH_CHECK();
     C.atoms = sorted.p;
+    C.rc2 = rc2.p;
+    C.atoms32 = sorted32.p;
     C.start = cstart.p;
     TmpBuf<double> rho(g.nn, s);
-    density_kernel<<<div_up(g.nn, 128), 128, 0, s>>>(g, C, S, rho.p);
+    density_kernel<<<div_up(g.nn * 32, 256), 256, 0, s>>>(g, C, S, rho.p);
     PB_LAUNCH_CHECK();
 
     // 2-3. crossings, vertices, triangles
@@ -625,10 +720,12 @@ void gaussian_surface(const double *xyz, const double *radius, int64_t na, const
         sort_neighbours_kernel<<<div_up(nv, 256), 256, 0, s>>>(nvk, nstart.p, nbr.p, udeg.p);
         PB_LAUNCH_CHECK();
         for (int r = 1; r <= R; ++r) {
-            smooth_kernel<<<div_up(nv, 128), 128, 0, s>>>(nvk, nstart.p, nbr.p, udeg.p, C, S, snaps.p + (r - 1) * stride,
-                                                          snaps.p + r * stride);
+            smooth_kernel<<<div_up(nv * 32, 256), 256, 0, s>>>(nvk, nstart.p, nbr.p, udeg.p, C, S,
+                                                              snaps.p + (r - 1) * stride, snaps.p + r * stride);
             PB_LAUNCH_CHECK();
-            fold_kernel<<<div_up(nt, 128), 128, 0, s>>>(ntk, out.t.p, snaps.p + r * stride, C, S, folds + r);
+        }
+        for (int r = R; r >= 1; --r) {
+            fold_kernel<<<div_up(nt * 32, 256), 256, 0, s>>>(ntk, out.t.p, snaps.p + r * stride, C, S, folds, r, R);
             PB_LAUNCH_CHECK();
         }
     }
