@@ -182,9 +182,13 @@ TRIPLET = (8000, 1500)
 
 
 def _fleet_member(args):
-    from synth.configs import fleet_ligand
+    """Ligand i: its atoms, its CPU-meshed problem and the single-core meshing time."""
+    from synth.configs import fleet_atoms, molecule_problem
     i, n = args
-    return fleet_ligand(i, n)
+    at = fleet_atoms(i, n)
+    t0 = time.perf_counter()
+    d = molecule_problem(at["xyz"], at["radius"], at["q"])
+    return d, at, time.perf_counter() - t0
 
 
 def _triplet_member(which):
@@ -400,8 +404,10 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def _extras(pbbem, ctx, pb, r, d, fleet, triplet, variants):
-    """Adjoint gradient of the bench problem, a batched fleet solve and a binding energy."""
+def _extras(pbbem, ctx, pb, r, d, fleet_members, triplet, variants):
+    """Adjoint gradient of the bench problem, a batched fleet solve, a binding energy, a
+    Richardson study, the model variants, an accuracy/time sweep and device surface generation."""
+    fleet = [f[0] for f in fleet_members]
     t0 = time.perf_counter()
     g1 = pb.gradient()
     first = time.perf_counter() - t0
@@ -484,8 +490,66 @@ def _extras(pbbem, ctx, pb, r, d, fleet, triplet, variants):
               "cases": [{"label": c.label, "time_s": c.time_s, "rel_error": c.rel_error,
                          "iterations": c.iterations} for c in res],
               "front": [c.label for c in pareto_front(res)]}
+    surface = _surface_extra(pbbem, ctx, fleet_members)
     return {"gradient": grad, "batch": batch, "binding": binding, "richardson": rich, "model_variants": models,
-            "pareto": pareto}
+            "pareto": pareto, "surface": surface}
+
+
+def _surface_extra(pbbem, ctx, fleet_members):
+    """Device surface generation: the protein's mesh on the GPU against the CPU mesher, and the
+    ligand fleet's pipeline from atoms (GPU meshes, setup, batched solve) against the same
+    pipeline fed with CPU meshes."""
+    from synth.configs import PROTEIN_SPACING, protein_atoms
+    from synth.molecule import gaussian_surface
+    at = protein_atoms(2000, 2)
+    t0 = time.perf_counter()
+    _, t_cpu = gaussian_surface(at["xyz"], at["radius"], PROTEIN_SPACING)
+    t_cpu_mesh = time.perf_counter() - t0
+    gen = []
+    for _ in range(5):
+        p = pbbem.Problem(ctx)
+        p.add_region(4.0, 0.0)
+        p.add_region(80.0, 0.125)
+        sid = p.add_gaussian_surface(at["xyz"], at["radius"], 0, 1, spacing=PROTEIN_SPACING)
+        info = p.surface_info(sid)
+        gen.append(info["gen_ms"])
+        p.close()
+    prot = {"workload": f"2,000-atom synthetic protein, {PROTEIN_SPACING} A grid", "panels_gpu": info["nt"],
+            "panels_cpu_mesher": int(t_cpu.shape[0]), "gpu_ms_median": float(np.median(gen)),
+            "cpu_mesher_s_one_core": t_cpu_mesh, "speedup": t_cpu_mesh / (float(np.median(gen)) / 1e3),
+            "grid": list(info["grid"]), "rounds": info["rounds"]}
+
+    def pipeline(from_atoms):
+        probs = []
+        ts = time.perf_counter()
+        for dd, a, _ in fleet_members:
+            if from_atoms:
+                p = pbbem.Problem(ctx)
+                for reg in dd["regions"]:
+                    p.add_region(reg["eps"], reg["kappa"])
+                p.add_gaussian_surface(a["xyz"], a["radius"], 0, 1, spacing=PROTEIN_SPACING)
+                p.set_charges(a["xyz"], a["q"], 0)
+            else:
+                p = pbbem.Problem.from_dict(ctx, dd)
+            p.setup(precision="mixed", **PARAMS)
+            probs.append(p)
+        res = pbbem.solve_batch(ctx, probs)
+        t = time.perf_counter() - ts
+        for p in probs:
+            p.close()
+        return t, [x.dG_solv for x in res]
+
+    pipeline(True)
+    t_gpu, e_gpu = pipeline(True)
+    t_up, e_up = pipeline(False)
+    mesh_core = float(sum(m[2] for m in fleet_members))
+    fleet_out = {"workload": f"{len(fleet_members)} synthetic ligands from atoms, {PROTEIN_SPACING} A grid",
+                 "gpu_pipeline_s": t_gpu, "uploaded_cpu_meshes_pipeline_s": t_up,
+                 "cpu_mesher_s_one_core_total": mesh_core,
+                 "cpu_pipeline_s_one_core": mesh_core + t_up,
+                 "speedup_vs_cpu_meshing_one_core": (mesh_core + t_up) / t_gpu,
+                 "max_rel_dG_diff_gpu_vs_cpu_meshes": float(max(abs(a - b) / abs(b) for a, b in zip(e_gpu, e_up)))}
+    return {"protein": prot, "fleet": fleet_out}
 
 
 def main():

@@ -46,10 +46,12 @@ The steps, written here in their plainest form:
 6. Smoothing (rounds r = 1 .. R).  Each round moves every vertex a fraction
    relax towards the mean of its edge neighbours, then takes newton_steps
    projections onto rho = level along grad rho (step (rho - level) / |grad|^2,
-   zero where |grad|^2 <= 1e-12, capped at max_step in length).  A round count
-   is acceptable when no triangle's normal has a non-negative dot product with
-   grad rho at its centroid (a folded triangle); the largest acceptable count
-   <= R is used, none when no count is.
+   zero where |grad|^2 <= 1e-12, capped at max_step in length).  A triangle is
+   folded when its normal has a non-negative dot product with grad rho at its
+   centroid; a round count is acceptable when it leaves no more folded
+   triangles than the unsmoothed mesh has (marching tetrahedra itself can fold
+   a few where a quadrilateral is cut along the diagonal the grid fixes).  The
+   largest acceptable count <= R is used, none when no count is.
 
 Parity status: pinned (tests/test_oracle_surface.py): the triangles of a random
 cube lie on the piecewise-linear level set computed by Freudenthal's formula,
@@ -268,9 +270,11 @@ def gaussian_surface(xyz, radius, spacing, **params):
         for _ in range(p["smooth_iters"]):
             snaps.append(smooth_round(snaps[-1], e, xyz, r_eff, p))
     rounds = 0
-    for r in range(len(snaps) - 1, 0, -1):
-        if folded(snaps[r], t, xyz, r_eff, p) == 0:
-            rounds = r
-            break
+    if len(snaps) > 1:
+        f0 = folded(snaps[0], t, xyz, r_eff, p)
+        for r in range(len(snaps) - 1, 0, -1):
+            if folded(snaps[r], t, xyz, r_eff, p) <= f0:
+                rounds = r
+                break
     return {"verts": snaps[rounds], "tris": t, "shape": shape, "lo": lo, "rounds": rounds,
             "components": ncomp, "raw_verts": raw_v, "raw_tris": raw_t, "rho": rho}

@@ -21,7 +21,7 @@
 //      crossing of largest x index) is the outer surface and is kept;
 //   5. smoothing rounds (umbrella step, then Newton projections onto the
 //      level set along grad rho); the largest round count that folds no
-//      triangle against grad rho is used (checked from the last round down).
+//      more triangles against grad rho than the unsmoothed mesh is used.
 // Every decision that picks an integer (inside test, crossings, components)
 // is taken on FP64 values; there are two host synchronisations (the raw
 // vertex and triangle counts, then the final counts).
@@ -507,17 +507,22 @@ __global__ void smooth_kernel(const int64_t *__restrict__ nvk, const int64_t *__
     if (lane < 3) vout[3 * v + lane] = x[lane];
 }
 
-// Triangles of round r whose normal has a non-negative component along grad
-// rho at the centroid, counted into folds[r].  Rounds are checked from the
-// last down; a round is skipped once a later round is known to fold nothing.
+// Triangles of round r (0: unsmoothed) whose normal has a non-negative
+// component along grad rho at the centroid, counted into folds[r].  A round
+// is acceptable when it folds no more triangles than round 0.  Launch order
+// R, 0, R - 1, ..., 1: round 0 is skipped when round R folds nothing (then
+// R is taken and folds[0] stays 0), a round r < R once a later round is
+// acceptable.
 __global__ void fold_kernel(const int64_t *__restrict__ ntk, const int32_t *__restrict__ tris,
                             const double *__restrict__ v, Cells C, Shape S, unsigned long long *__restrict__ folds,
                             int r, int R) {
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (t >= *ntk) return;
-    for (int q = r + 1; q <= R; ++q)
-        if (folds[q] == 0) return;
+    if (r == 0 && folds[R] == 0) return;
+    if (r > 0)
+        for (int q = r + 1; q <= R; ++q)
+            if (folds[q] <= folds[0]) return;
     const double *A = v + 3 * (int64_t)tris[3 * t], *B = v + 3 * (int64_t)tris[3 * t + 1],
                  *Cc = v + 3 * (int64_t)tris[3 * t + 2];
     const double e1[3] = {__dsub_rn(B[0], A[0]), __dsub_rn(B[1], A[1]), __dsub_rn(B[2], A[2])};
@@ -536,7 +541,7 @@ __global__ void fold_kernel(const int64_t *__restrict__ ntk, const int32_t *__re
 
 __device__ __forceinline__ int rounds_used(const unsigned long long *folds, int R) {
     for (int r = R; r >= 1; --r)
-        if (folds[r] == 0) return r;
+        if (folds[r] <= folds[0]) return r;
     return 0;
 }
 
@@ -724,7 +729,8 @@ void gaussian_surface(const double *xyz, const double *radius, int64_t na, const
                                                               snaps.p + (r - 1) * stride, snaps.p + r * stride);
             PB_LAUNCH_CHECK();
         }
-        for (int r = R; r >= 1; --r) {
+        for (int k = 0; k <= R; ++k) {
+            const int r = k == 0 ? R : k == 1 ? 0 : R + 1 - k;     // R, 0, R - 1, ..., 1
             fold_kernel<<<div_up(nt * 32, 256), 256, 0, s>>>(ntk, out.t.p, snaps.p + r * stride, C, S, folds, r, R);
             PB_LAUNCH_CHECK();
         }

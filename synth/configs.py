@@ -183,9 +183,19 @@ def fleet_sizes(count=64, n_min=300, n_max=3000, seed=4):
     return [int(n) for n in np.exp(rng.uniform(np.log(n_min), np.log(n_max), size=count)).astype(int)]
 
 
+def fleet_atoms(i, n_atoms, seed=4):
+    """Atoms of ligand i of a fleet: n_atoms atoms drawn with seed + 1 + i."""
+    return synthetic_atoms(int(n_atoms), _ball_radius(int(n_atoms)), seed + 1 + i)
+
+
+def molecule_problem(xyz, radius, q, spacing=PROTEIN_SPACING):
+    """One molecule (charges in eps 4, solvent eps 80 / kappa 0.125) meshed on the CPU."""
+    return _molecule_problem(xyz, radius, q, spacing)
+
+
 def fleet_ligand(i, n_atoms, seed=4, spacing=PROTEIN_SPACING):
     """Ligand i of a fleet: n_atoms atoms drawn with seed + 1 + i."""
-    at = synthetic_atoms(int(n_atoms), _ball_radius(int(n_atoms)), seed + 1 + i)
+    at = fleet_atoms(i, n_atoms, seed)
     return _molecule_problem(at["xyz"], at["radius"], at["q"], spacing)
 
 

@@ -73,15 +73,27 @@ def test_smoothed_mesh_matches_oracle(name):
 
 
 def test_fold_fallback_uses_fewer_rounds():
-    # with a sharper density some triangle faces up grad rho after every round:
-    # both sides fall back to the unsmoothed mesh
+    # a sharper density, full umbrella steps and tiny projections: the fifth round
+    # folds more triangles than the unsmoothed mesh, so both sides keep four rounds
     at = synthetic_atoms(200, 9.0, seed=11)
-    params = dict(spacing=1.4, beta=0.8)
+    params = dict(spacing=1.6, beta=1.2, relax=1.0, newton_steps=1, max_step=0.02)
     ref = OS.gaussian_surface(at["xyz"], at["radius"], **params)
-    assert ref["rounds"] == 0
+    assert ref["rounds"] == 4
     v, t, info = _gpu_surface(at["xyz"], at["radius"], **params)
-    assert info["rounds"] == 0
-    assert np.array_equal(t, ref["tris"]) and np.abs(v - ref["verts"]).max() <= 1e-9
+    assert info["rounds"] == 4
+    assert np.array_equal(t, ref["tris"]) and np.abs(v - ref["verts"]).max() <= 1e-8
+
+
+def test_smoothing_kept_when_the_unsmoothed_mesh_already_folds():
+    # ligand 60 of the 64-ligand fleet: marching tetrahedra folds 3 triangles, every
+    # smoothing round leaves 1, so all five rounds are kept
+    from synth.configs import PROTEIN_SPACING, fleet_atoms, fleet_sizes
+    at = fleet_atoms(60, fleet_sizes(64)[60])
+    ref = OS.gaussian_surface(at["xyz"], at["radius"], PROTEIN_SPACING)
+    assert ref["rounds"] == 5
+    v, t, info = _gpu_surface(at["xyz"], at["radius"], spacing=PROTEIN_SPACING)
+    assert info["rounds"] == 5
+    assert np.array_equal(t, ref["tris"]) and np.abs(v - ref["verts"]).max() <= 1e-8
 
 
 def _ring(nbrs, c, depth):
