@@ -187,3 +187,15 @@ def test_sphere_problem_from_device_surface_matches_kirkwood():
     ex = kirkwood_energy(4.0, 4.0, 80.0, 0.125, ch["xyz"], ch["q"])
     assert abs(r.dG_solv - ex) < 1e-2 * abs(ex)
     pb.close()
+
+
+def test_mesh_tool_writes_the_device_mesh(tmp_path, capsys):
+    from paper_1309_4018_b300 import mesh as M
+    at = synthetic_atoms(60, 6.0, seed=5)
+    p = tmp_path / "a.xyzr"
+    np.savetxt(p, np.hstack([at["xyz"], at["radius"][:, None]]))
+    M.main([str(p), "--spacing", "1.0", "--out", str(tmp_path / "m.npz")])
+    z = np.load(tmp_path / "m.npz")
+    ref = OS.gaussian_surface(*M.read_xyzr(str(p)), 1.0)
+    assert np.array_equal(z["tris"], ref["tris"]) and np.abs(z["verts"] - ref["verts"]).max() <= 1e-8
+    assert '"generated": true' in capsys.readouterr().out
