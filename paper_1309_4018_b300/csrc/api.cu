@@ -201,7 +201,10 @@ void setup_problem(pb_problem *pb) {
         build_lists(P, G, Tr, src, prm, use_self, s);
         if (P.n_m2p > 0) pb->need_far[P.tree] = true;
         const size_t nk = P.kappas.size();
-        P.VK.resize(nk); P.dV.resize(nk); P.dK.resize(nk); P.selfV.resize(nk);
+        P.VK.resize(nk); P.dV.resize(nk); P.dK.resize(nk); P.selfV.resize(nk); P.selfV32.resize(nk);
+        // the FP32 direct sum keeps a panel's own points when none sits at its centroid (K = 3);
+        // the self value then carries the correction
+        P.p2p_self_in = prm.precision == PB_MIXED && use_self && prm.K == 3;
         if (prm.precision == PB_MIXED) P.p2p_part32.alloc(2 * nk * std::max<int64_t>(1, P.n_p2p));
         else P.p2p_part.alloc(2 * nk * std::max<int64_t>(1, P.n_p2p));
         if (P.n_m2p > 0) {
@@ -226,6 +229,10 @@ void setup_problem(pb_problem *pb) {
             if (use_self) {
                 P.selfV[k].alloc(src.n);
                 self_integrals(src, prm.N_k, P.kappas[k], P.selfV[k].p, s);
+            }
+            if (P.p2p_self_in) {
+                P.selfV32[k].alloc(src.n);
+                self_minus_kpoint(src, prm.K, P.kappas[k], P.selfV[k].p, P.selfV32[k].p, s);
             }
         }
     };

@@ -417,6 +417,30 @@ void near_values32(const Pair &Pr, const Targets &G, const SurfDev &src, int K, 
     PB_LAUNCH_CHECK();
 }
 
+namespace {
+// out_i = selfv_i - (1/4pi) sum_k w_k A_i G(|c_i - y_ik|): the self value less the
+// share of panel i's own K points in the direct sum at its centroid (FP64).
+__global__ void self_minus_kpoint_kernel(int64_t n, int K, const double *__restrict__ cen,
+                                         const double *__restrict__ gy, const double *__restrict__ gwa, double kappa,
+                                         const double *__restrict__ selfv, double *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double sum = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const int64_t q = i * K + k;
+        const double dx = cen[3 * i] - gy[3 * q], dy = cen[3 * i + 1] - gy[3 * q + 1], dz = cen[3 * i + 2] - gy[3 * q + 2];
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        sum += gwa[q] * (kappa == 0.0 ? 1.0 / r : exp(-kappa * r) / r);
+    }
+    out[i] = selfv[i] - kInv4Pi * sum;
+}
+}  // namespace
+
+void self_minus_kpoint(const SurfDev &S, int K, double kappa, const double *selfv, double *out, cudaStream_t s) {
+    self_minus_kpoint_kernel<<<div_up(S.n, 128), 128, 0, s>>>(S.n, K, S.cen.p, S.gy.p, S.gwa.p, kappa, selfv, out);
+    PB_LAUNCH_CHECK();
+}
+
 void self_integrals(const SurfDev &S, int N_k, double kappa, double *out, cudaStream_t s) {
     if (N_k < 1 || N_k > 32) fail(PB_EINVAL, "N_k must be in 1..32");
     GL gl = gauss_legendre(N_k);

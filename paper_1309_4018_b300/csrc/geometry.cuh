@@ -26,6 +26,9 @@ void near_values32(const Pair &Pr, const Targets &G, const SurfDev &src, int K, 
                    float *dK, cudaStream_t s);
 // Semi-analytical V_ii of every panel of S (input order).
 void self_integrals(const SurfDev &S, int N_k, double kappa, double *out, cudaStream_t s);
+// out = selfv - the own panel's K-point share of the direct sum at the centroid (1/4pi included);
+// valid for rules without a point at the centroid.
+void self_minus_kpoint(const SurfDev &S, int K, double kappa, const double *selfv, double *out, cudaStream_t s);
 // Its kappa derivative by the same rule.
 void self_integrals_dkappa(const SurfDev &S, int N_k, double kappa, double *out, cudaStream_t s);
 // b_i = sum_k q_k G(c_i, r_k) / eps for the panels of S (input order); FP64,

@@ -100,6 +100,10 @@ struct Pair {
     DevBuf<float4> x32;                   // sorted targets relative to the tree origin, FP32
     // near-singular corrections per kernel: dV, dK per near entry; self V per panel
     std::vector<DevBuf<double>> dV, dK, selfV;
+    // FP32 path with the own panel's points left in the direct sum (rules without a centroid point):
+    // self value minus the K-point own-panel share, per kernel
+    bool p2p_self_in = false;
+    std::vector<DevBuf<double>> selfV32;
     // outputs per kernel: V then K per sorted target (2 * n)
     std::vector<DevBuf<double>> VK;
 };

@@ -341,6 +341,32 @@ __global__ void item_fill_kernel(int nkeys, const int64_t *__restrict__ off, con
         items[ioff[k] + w] = make_int4(k, (int)(off[k] + per * w), (int)(c - per * w < per ? c - per * w : per), 0);
 }
 
+// P2P items in descending order of cost (sources of the leaf x targets), by
+// buckets of width `step`: the expensive items start first and the cheap
+// ones fill the last wave.  Only the launch order changes; every item writes
+// its own records, so results do not depend on it.
+__global__ void item_bucket_kernel(int64_t n, const int4 *__restrict__ items, const int32_t *__restrict__ leaf_node,
+                                   const int64_t *__restrict__ count, int nb, int step, int32_t *__restrict__ bucket,
+                                   int32_t *__restrict__ bcnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int4 it = items[i];
+    const int64_t cost = count[leaf_node[it.x]] * it.z;
+    const int64_t q = cost / step;
+    const int b = nb - 1 - (int)(q < nb - 1 ? q : nb - 1);
+    bucket[i] = b;
+    atomicAdd(bcnt + b, 1);
+}
+
+__global__ void item_scatter_kernel(int64_t n, const int4 *__restrict__ in, const int32_t *__restrict__ bucket,
+                                    const int64_t *__restrict__ boff, int32_t *__restrict__ cursor,
+                                    int4 *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = bucket[i];
+    out[boff[b] + atomicAdd(cursor + b, 1)] = in[i];
+}
+
 // ---------------------------------------------------------------- near-singular lists
 __device__ __forceinline__ bool in_sorted(const int32_t *__restrict__ a, int64_t n, int v) {
     int64_t lo = 0, hi = n;
@@ -813,6 +839,23 @@ void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &pr
     group(Pr.p2p_ptr.p, Pr.p2p_node.p, T.node_leaf.p, T.nleaves, Pr.n_p2p, p2p_per_item, 1, Pr.p2p_inv, Pr.p2p_ent,
           Pr.p2p_items,
           Pr.n_p2p_items);
+    if (Pr.n_p2p_items > 1) {
+        constexpr int nb = 64;
+        const int step = std::max(1, prm.ncrit * p2p_per_item / nb);
+        const int64_t ni = Pr.n_p2p_items;
+        TmpBuf<int32_t> bucket(ni, s), bcnt(nb, s), cursor(nb, s);
+        TmpBuf<int64_t> boff(nb + 1, s);
+        TmpBuf<int4> sorted(ni, s);
+        PB_CUDA_TRY(cudaMemsetAsync(bcnt.p, 0, nb * sizeof(int32_t), s));
+        PB_CUDA_TRY(cudaMemsetAsync(cursor.p, 0, nb * sizeof(int32_t), s));
+        item_bucket_kernel<<<div_up(ni, 256), 256, 0, s>>>(ni, Pr.p2p_items.p, T.leaf_node.p, T.count.p, nb, step,
+                                                           bucket.p, bcnt.p);
+        PB_LAUNCH_CHECK();
+        exclusive_scan_i32_to_i64(bcnt.p, boff.p, nb, s);
+        item_scatter_kernel<<<div_up(ni, 256), 256, 0, s>>>(ni, Pr.p2p_items.p, bucket.p, boff.p, cursor.p, sorted.p);
+        PB_LAUNCH_CHECK();
+        PB_CUDA_TRY(cudaMemcpyAsync(Pr.p2p_items.p, sorted.p, ni * sizeof(int4), cudaMemcpyDeviceToDevice, s));
+    }
     group(Pr.m2p_ptr.p, Pr.m2p_node.p, nullptr, T.nnodes, Pr.n_m2p, 32, 0, Pr.m2p_inv, Pr.m2p_pos, Pr.m2p_items,
           Pr.n_m2p_items);
 }

@@ -225,7 +225,9 @@ __device__ __forceinline__ void comp_add(float &hi, float &lo, float v) {
 // shared memory and broadcast; every lane owns one target.  FP32 partial sums
 // per 32-source chunk go into compensated (hi, lo) pairs; the pair's result is
 // stored in FP64 at its grouped position.
-template <int NK, bool Y0, bool Y1>
+// MASK: skip the target's own panel (needed when a rule point sits at the
+// centroid); without it the own points stay in and the self value is corrected.
+template <int NK, bool Y0, bool Y1, bool MASK>
 __global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, const int4 *__restrict__ items,
                                                     const int32_t *__restrict__ inv,
                                                     const int32_t *__restrict__ sent,
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, const int4 *
         tx = x.x;
         ty = x.y;
         tz = x.z;
-        if (use_self) me = selfp[t];
+        if (MASK && use_self) me = selfp[t];
     }
     const float k0 = ks.kap[0], k1 = ks.kap[1];
     const float l2e0 = -k0 * 1.4426950408889634f, l2e1 = -k1 * 1.4426950408889634f;
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, const int4 *
                 const float4 b = sB[warp][j];
                 const float dx = tx - a.x, dy = ty - a.y, dz = tz - a.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float inv = (__float_as_int(b.w) == me) ? 0.f : fast_rsqrt(r2);
+                const float inv = (MASK && __float_as_int(b.w) == me) ? 0.f : fast_rsqrt(r2);
                 const float sv = a.w * inv;
                 const float rd = fmaf(dx, b.x, fmaf(dy, b.y, dz * b.z));
                 const float kv = rd * (inv * inv * inv);
@@ -1095,16 +1097,19 @@ void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self,
     const int us = use_self ? 1 : 0;
     if (mixed) {
         KSet ks{{(float)k0, (float)k1}};
-#define PB_P2P32(NK, A, B)                                                                                      \
-    p2p32_kernel<NK, A, B><<<grid, 128, 0, s>>>(ni, Pr.p2p_items.p, Pr.p2p_inv.p, Pr.p2p_ent.p, Pr.x32.p, sp, us, \
-                                                Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.srcA32.p, Tr.srcB32.p, ks, \
-                                                Pr.p2p_part32.p)
+        const bool mask = use_self && !Pr.p2p_self_in;
+#define PB_P2P32M(NK, A, B, M)                                                                                    \
+    p2p32_kernel<NK, A, B, M><<<grid, 128, 0, s>>>(ni, Pr.p2p_items.p, Pr.p2p_inv.p, Pr.p2p_ent.p, Pr.x32.p, sp, us, \
+                                                   Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.srcA32.p, Tr.srcB32.p,  \
+                                                   ks, Pr.p2p_part32.p)
+#define PB_P2P32(NK, A, B) do { if (mask) PB_P2P32M(NK, A, B, true); else PB_P2P32M(NK, A, B, false); } while (0)
         if (nk == 1) { if (y0) PB_P2P32(1, true, false); else PB_P2P32(1, false, false); }
         else if (!y0 && y1) PB_P2P32(2, false, true);
         else if (y0 && !y1) PB_P2P32(2, true, false);
         else if (y0 && y1) PB_P2P32(2, true, true);
         else PB_P2P32(2, false, false);
 #undef PB_P2P32
+#undef PB_P2P32M
     } else {
 #define PB_P2P64(NK, A, B)                                                                                       \
     p2p64_kernel<NK, A, B><<<grid, 128, 0, s>>>(ni, Pr.p2p_items.p, Pr.p2p_inv.p, Pr.p2p_ent.p, G.xs.p, sp, us,   \
@@ -1168,7 +1173,7 @@ void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, 
         for (int k = 0; k < nk; ++k) {
             nr.dV[k] = Pr.dV32.p + (int64_t)k * Pr.n_near;
             nr.dK[k] = Pr.dK32.p + (int64_t)k * Pr.n_near;
-            nr.selfV[k] = use_self ? Pr.selfV[k].p : nullptr;
+            nr.selfV[k] = use_self ? (Pr.p2p_self_in ? Pr.selfV32[k].p : Pr.selfV[k].p) : nullptr;
         }
         nr.selfp = G.self_panel.p;
         nr.use_self = use_self ? 1 : 0;
