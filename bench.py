@@ -491,8 +491,25 @@ def _extras(pbbem, ctx, pb, r, d, fleet_members, triplet, variants):
                          "iterations": c.iterations} for c in res],
               "front": [c.label for c in pareto_front(res)]}
     surface = _surface_extra(pbbem, ctx, fleet_members)
+    from synth.configs import large_protein_problem
+    dl = large_protein_problem()
+    ts = time.perf_counter()
+    pl = pbbem.Problem.from_dict(ctx, dl)
+    info = pl.surface_info(0)
+    pl.setup(precision="mixed", **PARAMS)
+    rl = pl.solve()
+    gl = pl.gradient()
+    t_large = time.perf_counter() - ts
+    ql = dl["charges"]["q"]
+    large = {"workload": "30,000-atom synthetic globule, surface meshed on the device at 0.8 A "
+                         "(the tests check 32 sampled coordinates and eps/kappa against central differences)",
+             "panels": info["nt"], "mesh_ms": info["gen_ms"], "setup_ms": rl.setup_ms, "solve_ms": rl.solve_ms,
+             "iterations": rl.iterations, "dG_kJ_mol": rl.dG_solv, "grad_ms": gl["grad_ms"],
+             "adjoint_iterations": gl["iterations"], "q_dq_over_2E": float(ql @ gl["dq"]) / (2 * rl.dG_solv),
+             "wall_s": t_large}
+    pl.close()
     return {"gradient": grad, "batch": batch, "binding": binding, "richardson": rich, "model_variants": models,
-            "pareto": pareto, "surface": surface}
+            "pareto": pareto, "surface": surface, "large_gradient": large}
 
 
 def _surface_extra(pbbem, ctx, fleet_members):

@@ -241,3 +241,17 @@ def model_variants(n_atoms=2000, seed=3, spacing=PROTEIN_SPACING, stern_spacing=
     stern_m = mk([{"eps": eo, "kappa": 0.0}, {"eps": ew, "kappa": 0.0}, {"eps": ew, "kappa": kap}],
                  [dict(ses, inner=0, outer=1), dict(stern, inner=1, outer=2)], 0)
     return {"single": single, "cavity": cavity, "stern": stern_m, "full": full}
+
+
+
+def large_protein_problem(n_atoms=30000, seed=2, spacing=0.8):
+    """A 30,000-atom seeded globule (drawn like protein_atoms: ball radius
+    20 (N/2000)^(1/3) = 49 A) whose surface the device mesher builds from the
+    atoms (~480k panels at 0.8 A)."""
+    at = protein_atoms(n_atoms, seed)
+    return {
+        "regions": [{"eps": EPS_IN, "kappa": 0.0}, {"eps": EPS_OUT, "kappa": KAPPA}],
+        "surfaces": [{"atoms": {"xyz": at["xyz"], "radius": at["radius"]}, "surf_params": {"spacing": spacing},
+                      "inner": 0, "outer": 1}],
+        "charges": {"xyz": at["xyz"].copy(), "q": at["q"].copy(), "region": 0},
+    }
