@@ -435,6 +435,7 @@ def _extras(pbbem, ctx, pb, r, d, fleet_members, triplet, variants):
              "same_energies": all(a.dG_solv == b.dG_solv for a, b in zip(seq, bat))}
     for p in probs:
         p.close()
+    batch["autotuned"] = _autotuned_fleet(pbbem, ctx, fleet, bat)
     tri = [pbbem.Problem.from_dict(ctx, t) for t in triplet]
     ts = time.perf_counter()
     for p in tri:
@@ -510,6 +511,38 @@ def _extras(pbbem, ctx, pb, r, d, fleet_members, triplet, variants):
     pl.close()
     return {"gradient": grad, "batch": batch, "binding": binding, "richardson": rich, "model_variants": models,
             "pareto": pareto, "surface": surface, "large_gradient": large}
+
+
+def _autotuned_fleet(pbbem, ctx, fleet, default_results):
+    """The fleet with (theta, P, ncrit) from the autotuner's per-size-class schedule, against the
+    configuration's fixed setting: setup + batched solve wall time and the energies."""
+    from paper_1309_4018_b300.autotune import Schedule
+    base = {k: v for k, v in PARAMS.items() if k not in ("theta", "P", "ncrit")}
+    base["precision"] = "mixed"
+    t0 = time.perf_counter()
+    sched = Schedule.build(ctx, fleet, target=1e-4, base=base)
+    t_tune = time.perf_counter() - t0
+
+    def run(tuned):
+        probs = [pbbem.Problem.from_dict(ctx, f) for f in fleet]
+        ts = time.perf_counter()
+        for p, f in zip(probs, fleet):
+            p.setup(**(dict(base, **sched.params_for(f)) if tuned else dict(PARAMS, precision="mixed")))
+        res = pbbem.solve_batch(ctx, probs)
+        t = time.perf_counter() - ts
+        for p in probs:
+            p.close()
+        return t, res
+
+    run(True)
+    t_tuned, res = run(True)
+    t_def, _ = run(False)
+    return {"schedule": {str(k): dict(c.params(), rel_error=c.rel_error, time_s=c.time_s)
+                         for k, c in sched.choices.items()},
+            "tuning_s": t_tune, "setup_and_batch_s_tuned": t_tuned, "setup_and_batch_s_default": t_def,
+            "speedup": t_def / t_tuned,
+            "max_rel_dG_diff_vs_default": float(max(abs(a.dG_solv - b.dG_solv) / abs(b.dG_solv)
+                                                    for a, b in zip(res, default_results)))}
 
 
 def _surface_extra(pbbem, ctx, fleet_members):
