@@ -45,34 +45,38 @@ FP32_LANES_PER_SM = 128
 
 # ---------------------------------------------------------------- arithmetic counts
 def p2p_ops_per_pair(kernels):
-    """FP32 arithmetic instructions of one P2P pair in the mixed kernel (MUFU not counted).
+    """FP32 and MUFU instructions (each one issue slot) of one P2P pair in the mixed kernel.
 
-    Shared part: 3 differences, r^2 (3), self-mask select (1), s*inv (1),
-    d.(x-y) (3), kv = rd * inv^3 (3) = 14.  Per Laplace kernel: 2 adds.  Per
-    Yukawa kernel: rho, exponent scale, s*e fma, kv*e, 1+kappa*rho, fma = 6.
+    Shared part: 3 differences, r^2 (3), rsqrt (1 MUFU), s*inv (1), d.(x-y) (3),
+    kv = rd * inv^3 (3) = 14.  Per Laplace kernel: 2 adds.  Per Yukawa kernel:
+    rho, exponent scale, ex2 (1 MUFU), s*e fma, kv*e, 1+kappa*rho, fma = 7.
     """
-    return 14 + sum(2 if k == 0.0 else 6 for k in kernels)
+    return 14 + sum(2 if k == 0.0 else 7 for k in kernels)
 
 
-def m2p_ops_per_box(P, yukawa):
-    """FP32 arithmetic instructions of one (target, box) M2P evaluation at order P.
+def radial_terms(P):
+    return sum(((P - a) // 2 + 1) * (a + 1) * (a + 2) // 2 for a in range(P + 1))
 
-    Mirrors the fully unrolled recurrence: per term with c1 nonzero indices and
-    c2 indices >= 2: s1 (c1), s2 (c2 - 1), a = -(c1' s1 + c2' s2) / r^2 (2-3),
-    contraction with M and D (2); Yukawa adds t1, t2 and the b recurrence.
-    Per box: u (3), r^2 (3), 1/r^2 (1), a0, b0 and the first contraction (4-6).
+
+def m2p_ops_per_box(P):
+    """FP32 and MUFU instructions of one (target, box) evaluation of the fused
+    Laplace + Yukawa M2P in radial form at order P (mirrors the kernel).
+
+    u (3), r^2 (3), rsqrt (1), 1/r^2 (1); Laplace radial functions (2 per
+    order); rho, exponent and ex2 (3); Yukawa F_0, F_1, kappa^2 (5) and 3 per
+    further order; coordinate powers (3 (P - 1)); monomials (one multiply per
+    nontrivial factor); two fmas per radial moment (M and D); four fmas per
+    order for (V, K) of both kernels.  Loads of the radial moments not counted.
     """
-    ops = 3 + 3 + 1 + 1 + 2 + (3 if yukawa else 0)
-    for n in range(1, P + 1):
-        for k1 in range(n, -1, -1):
-            for k2 in range(n - k1, -1, -1):
-                k = (k1, k2, n - k1 - k2)
-                c1 = sum(1 for x in k if x >= 1)
-                c2 = sum(1 for x in k if x >= 2)
-                ops += c1 + max(c2 - 1, 0) + (2 if c2 else 1) + 1 + 2
-                if yukawa:
-                    ops += c1 + max(c2 - 1, 0) + (2 if c2 else 1) + (2 if c2 else 1)
-    return ops
+    if P == 0:
+        return 3 + 3 + 1 + 1 + 3 + 1 + 2 + 4
+    mono = 0
+    for a1 in range(P + 1):
+        for a2 in range(P + 1 - a1):
+            mono += 1 if (a1 and a2) else 0
+            mono += sum(1 for a3 in range(P + 1 - a1 - a2) if a3)
+    return (3 + 3 + 1 + 1 + 2 * P + 3 + 5 + 3 * (P - 1) + 3 * (P - 1) + mono + 2 * radial_terms(P)
+            + 4 * (P + 1))
 
 
 # ---------------------------------------------------------------- clocks
@@ -334,7 +338,7 @@ def run_gpu(args):
     alu_peak = nsm * FP32_LANES_PER_SM * fmax / 1e12      # FP32 Tinstr/s
     kernels = [d["regions"][0]["kappa"], d["regions"][1]["kappa"]]
     p2p_ops = r.p2p_pairs * p2p_ops_per_pair(kernels)
-    m2p_ops = (r.m2p_pairs // 2) * (m2p_ops_per_box(PARAMS["P"], False) + m2p_ops_per_box(PARAMS["P"], True))
+    m2p_ops = (r.m2p_pairs // 2) * m2p_ops_per_box(PARAMS["P"])
     cand = {"p2p32": (prof["p2p"], p2p_ops), "m2p32": (prof["m2p"], m2p_ops)}
     dom = max(cand, key=lambda k: cand[k][0])
     dom_ms, dom_ops = cand[dom]

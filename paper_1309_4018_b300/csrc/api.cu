@@ -289,6 +289,8 @@ void setup_problem(pb_problem *pb) {
         if (pb->need_far[t]) {
             const size_t nm = (size_t)pb->T[t].nnodes * 2 * nterms(prm.P);
             if (prm.precision == PB_MIXED) pb->T[t].mom32.alloc(nm); else pb->T[t].mom64.alloc(nm);
+            if (prm.precision == PB_MIXED && prm.P <= kRadialMaxP)
+                pb->T[t].rmom32.alloc((size_t)pb->T[t].nnodes * radial_floats(prm.P));
         }
     PB_CUDA_TRY(cudaEventRecord(pb->ev1, s));
     PB_CUDA_TRY(cudaEventSynchronize(pb->ev1));

@@ -18,6 +18,7 @@ constexpr double kInv4Pi = 1.0 / (4.0 * kPi);
 constexpr double kKjPerMol = 1389.3545764;
 constexpr int kMaxLevel = 21;
 constexpr int kMaxP = 12;
+constexpr int kRadialMaxP = 8;      // the FP32 M2P uses the radial form up to this order
 constexpr int kMaxTerms1 = (kMaxP + 2) * (kMaxP + 3) * (kMaxP + 4) / 6;   // terms up to order kMaxP + 1
 
 // Four doubles, 32-byte aligned (one vector load).

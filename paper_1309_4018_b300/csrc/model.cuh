@@ -61,6 +61,7 @@ struct Tree {
     DevBuf<int32_t> ucnt;            // per node: children finished in the fused upward pass (0 between passes)
     DevBuf<double> mom64;            // nnodes * 2 * nterms: M then D
     DevBuf<float> mom32;
+    DevBuf<float> rmom32;            // moments in radial form (FP32 M2P, P <= kRadialMaxP)
 };
 
 // Evaluation points: panel centroids of one surface, or the charges.

@@ -441,58 +441,6 @@ __device__ __forceinline__ void m2p_eval(T ux, T uy, T uz, T kappa, const T *__r
     }
 }
 
-// Laplace and Yukawa coefficients for the same (target, box) in one pass: the
-// moments of each term are loaded once and contracted with both.
-template <int P, typename T>
-__device__ __forceinline__ void m2p_eval_ly(T ux, T uy, T uz, T kappa, const T *__restrict__ mom, T &VL, T &KL,
-                                            T &VY, T &KY) {
-    constexpr int NT = (P + 1) * (P + 2) * (P + 3) / 6;
-    T a[NT], ay[NT], b[NT];
-    const T r2 = ux * ux + uy * uy + uz * uz;
-    T rinv;
-    if constexpr (sizeof(T) == 4) rinv = rsqrtf(r2); else rinv = rsqrt(r2);
-    const T ir2 = rinv * rinv;
-    T e0;
-    if constexpr (sizeof(T) == 4) e0 = __expf(-kappa * r2 * rinv); else e0 = exp(-kappa * r2 * rinv);
-    a[0] = rinv;
-    ay[0] = e0 * rinv;
-    b[0] = e0;
-    {
-        const T m = mom[0], d = mom[NT];
-        VL = a[0] * m; KL = a[0] * d;
-        VY = ay[0] * m; KY = ay[0] * d;
-    }
-#pragma unroll
-    for (int n = 1; n <= P; ++n) {
-        // the order's constants folded with -1/r^2
-        const T C1 = -(T)(2 * n - 1) / (T)n * ir2, C2 = -(T)(n - 1) / (T)n * ir2;
-        const T kn = kappa / (T)n, KN = -kn * ir2;
-#pragma unroll
-        for (int k1 = n; k1 >= 0; --k1) {
-#pragma unroll
-            for (int k2 = n - k1; k2 >= 0; --k2) {
-                const int k3 = n - k1 - k2;
-                const int i = term_index(k1, k2, k3);
-                T s1 = 0, s2 = 0, y1 = 0, y2 = 0, t1 = 0, t2 = 0;
-                if (k1 >= 1) { const int j = term_index(k1 - 1, k2, k3); s1 += ux * a[j]; y1 += ux * ay[j]; t1 += ux * b[j]; }
-                if (k2 >= 1) { const int j = term_index(k1, k2 - 1, k3); s1 += uy * a[j]; y1 += uy * ay[j]; t1 += uy * b[j]; }
-                if (k3 >= 1) { const int j = term_index(k1, k2, k3 - 1); s1 += uz * a[j]; y1 += uz * ay[j]; t1 += uz * b[j]; }
-                if (k1 >= 2) { const int j = term_index(k1 - 2, k2, k3); s2 += a[j]; y2 += ay[j]; t2 += b[j]; }
-                if (k2 >= 2) { const int j = term_index(k1, k2 - 2, k3); s2 += a[j]; y2 += ay[j]; t2 += b[j]; }
-                if (k3 >= 2) { const int j = term_index(k1, k2, k3 - 2); s2 += a[j]; y2 += ay[j]; t2 += b[j]; }
-                a[i] = C1 * s1 + C2 * s2;
-                ay[i] = C1 * y1 + C2 * y2 + KN * (t1 + t2);
-                b[i] = -kn * (y1 + y2);
-                const T m = mom[i], d = mom[NT + i];
-                VL += a[i] * m;
-                KL += a[i] * d;
-                VY += ay[i] * m;
-                KY += ay[i] * d;
-            }
-        }
-    }
-}
-
 // Runtime-order variant for orders without a compiled specialisation (local arrays).
 template <bool YUK, typename T>
 __device__ void m2p_eval_rt(int P, T ux, T uy, T uz, T kappa, const T *__restrict__ mom, T &V, T &K) {
@@ -568,14 +516,112 @@ __global__ void __launch_bounds__(128) m2p_kernel(int64_t nitems, const int4 *__
     rec[1] = K;
 }
 
+// ---------------------------------------------------------------- M2P in radial form (FP32)
+// The kernels are radial, G = F(|u|), u = y_c - x, and the Taylor coefficient
+// of order k is (1/k!) d^k F(u), with (one axis at a time, since d_i F_m = u_i F_{m+1})
+//   d^k F(u) = sum_j prod_i k_i! / (2^j_i j_i! (k_i - 2 j_i)!) u^(k - 2j) F_{|k| - |j|}(|u|),
+//   F_m = ((1/r) d/dr)^m F.
+// Grouping the expansion sum_{|k| <= P} (1/k!) d^k F(u) M^k by (alpha = k - 2j, n = |k| - |j|):
+//   sum_{alpha, n} u^alpha F_n(|u|) N_{alpha,n},
+//   N_{alpha,n} = sum_{|j| = n - |alpha|, |alpha| + 2|j| <= P} prod_i 1 / (2^j_i j_i! alpha_i!) M^(alpha + 2j).
+// N depends only on the box's moments, so it is formed once per box for M and
+// for D and serves the Laplace and the Yukawa kernel alike; per (target, box)
+// there remain the monomials u^alpha, the radial functions
+//   Laplace F = 1/r:        F_{n+1} = -(2n + 1) F_n / r^2,
+//   Yukawa  F = e^{-kr}/r:  F_1 = -(kr + 1) e^{-kr} / r^3,  F_{n+1} = (k^2 F_{n-1} - (2n + 1) F_n) / r^2
+// (the second from r^2 F_{n+1} + (2n + 1) F_n - k^2 F_{n-1} = 0, which
+// (1/r d/dr)^n of the Yukawa equation gives), and two dot products.
+// The sum equals the Taylor sum exactly; only the rounding differs.
+__host__ __device__ constexpr int radial_terms(int P) {
+    int n = 0;
+    for (int a = 0; a <= P; ++a) n += ((P - a) / 2 + 1) * (a + 1) * (a + 2) / 2;
+    return n;
+}
+// floats per node in the radial moment array (N^M, N^D interleaved), padded to 16 bytes
+__host__ __device__ constexpr int radial_stride(int P) { return (2 * radial_terms(P) + 3) / 4 * 4; }
+
+__host__ __device__ constexpr int radial_table_terms(int P) {
+    int q = 0;
+    for (int a = 0; a <= P; ++a)
+        for (int m = 0; a + 2 * m <= P; ++m) q += (a + 1) * (a + 2) / 2 * (m + 1) * (m + 2) / 2;
+    return q;
+}
+
+// The transform N = T M as a sparse table, built at compile time: for output
+// r = (alpha, n) in the order alpha_1, alpha_2, alpha_3 ascending (nested),
+// then n ascending, the terms start[r] .. start[r + 1] - 1 are
+// (moment index of alpha + 2j, weight prod_i 1 / (2^j_i j_i! alpha_i!)).
+template <int P>
+struct RadialTable {
+    int16_t start[radial_terms(P) + 1];
+    int16_t k[radial_table_terms(P)];
+    float w[radial_table_terms(P)];
+};
+
+__host__ __device__ constexpr double fact_d(int n) {
+    double f = 1.0;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+}
+
+template <int P>
+constexpr RadialTable<P> make_radial_table() {
+    RadialTable<P> t{};
+    int r = 0, q = 0;
+    for (int a1 = 0; a1 <= P; ++a1)
+        for (int a2 = 0; a2 <= P - a1; ++a2)
+            for (int a3 = 0; a3 <= P - a1 - a2; ++a3) {
+                const int a = a1 + a2 + a3;
+                for (int n = a; 2 * n <= a + P; ++n) {
+                    const int m = n - a;
+                    t.start[r++] = (int16_t)q;
+                    for (int j1 = 0; j1 <= m; ++j1)
+                        for (int j2 = 0; j2 <= m - j1; ++j2) {
+                            const int j3 = m - j1 - j2;
+                            t.k[q] = (int16_t)term_index(a1 + 2 * j1, a2 + 2 * j2, a3 + 2 * j3);
+                            t.w[q] = (float)(1.0 / ((double)(1 << m) * fact_d(j1) * fact_d(j2) * fact_d(j3) *
+                                                    fact_d(a1) * fact_d(a2) * fact_d(a3)));
+                            ++q;
+                        }
+                }
+            }
+    t.start[r] = (int16_t)q;
+    return t;
+}
+
+template <int P>
+__device__ const RadialTable<P> g_radial = make_radial_table<P>();
+
+// One thread per (node, output pair): (N^M_r, N^D_r) of the node; the padding pairs are zeroed.
+template <int P>
+__global__ void radial_moments_kernel(int nnodes, const float *__restrict__ mom, float *__restrict__ rmom) {
+    constexpr int NT = (P + 1) * (P + 2) * (P + 3) / 6, NR = radial_terms(P), NP = radial_stride(P) / 2;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nnodes * NP) return;
+    const int64_t b = t / NP;
+    const int r = (int)(t % NP);
+    float sm = 0.f, sd = 0.f;
+    if (r < NR) {
+        const RadialTable<P> &T = g_radial<P>;
+        const float *M = mom + b * 2 * NT, *D = M + NT;
+        for (int q = T.start[r]; q < T.start[r + 1]; ++q) {
+            const float w = T.w[q];
+            const int k = T.k[q];
+            sm = fmaf(w, M[k], sm);
+            sd = fmaf(w, D[k], sd);
+        }
+    }
+    reinterpret_cast<float2 *>(rmom)[b * NP + r] = make_float2(sm, sd);
+}
+
 // Box-major M2P for a pair whose two kernels are Laplace (slot 0) and Yukawa
-// (slot 1): both recurrences in one pass, one record (VL, KL, VY, KY) per pair.
+// (slot 1): one warp per (box, up to 32 targets) item, the box's radial
+// moments read as uniform 16-byte loads, one record (VL, KL, VY, KY) per pair.
 template <int P>
 __global__ void __launch_bounds__(128) m2p_ly32_kernel(int64_t nitems, const int4 *__restrict__ items,
                                                        const int32_t *__restrict__ inv, const float4 *__restrict__ x32,
-                                                       const float4 *__restrict__ cen32, const float *__restrict__ mom,
+                                                       const float4 *__restrict__ cen32, const float *__restrict__ rmom,
                                                        float kappa, float4 *__restrict__ part) {
-    constexpr int NT = (P + 1) * (P + 2) * (P + 3) / 6;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * 4 + warp;
     if (item >= nitems) return;
@@ -585,8 +631,58 @@ __global__ void __launch_bounds__(128) m2p_ly32_kernel(int64_t nitems, const int
     const int b = it.x;
     const float4 c = cen32[b];
     const float4 x = x32[inv[slot]];
-    float VL, KL, VY, KY;
-    m2p_eval_ly<P, float>(c.x - x.x, c.y - x.y, c.z - x.z, kappa, mom + (int64_t)b * 2 * NT, VL, KL, VY, KY);
+    const float ux = c.x - x.x, uy = c.y - x.y, uz = c.z - x.z;
+    const float r2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+    const float rinv = rsqrtf(r2), ir2 = rinv * rinv;
+    float FL[P + 1], FY[P + 1];
+    FL[0] = rinv;
+#pragma unroll
+    for (int n = 0; n < P; ++n) FL[n + 1] = (-(float)(2 * n + 1) * ir2) * FL[n];
+    const float rho = r2 * rinv;
+    const float e = __expf(-kappa * rho);
+    FY[0] = e * rinv;
+    if (P >= 1) FY[1] = -fmaf(kappa, rho, 1.f) * FY[0] * ir2;
+    const float k2 = kappa * kappa;
+#pragma unroll
+    for (int n = 1; n < P; ++n) FY[n + 1] = fmaf(k2, FY[n - 1], -(float)(2 * n + 1) * FY[n]) * ir2;
+    float px[P + 1], py[P + 1], pz[P + 1];
+    px[0] = py[0] = pz[0] = 1.f;
+#pragma unroll
+    for (int i = 1; i <= P; ++i) { px[i] = px[i - 1] * ux; py[i] = py[i - 1] * uy; pz[i] = pz[i - 1] * uz; }
+    float SM[P + 1], SD[P + 1];
+#pragma unroll
+    for (int n = 0; n <= P; ++n) { SM[n] = 0.f; SD[n] = 0.f; }
+    const float4 *R = reinterpret_cast<const float4 *>(rmom + (int64_t)b * radial_stride(P));
+    float4 cur = make_float4(0.f, 0.f, 0.f, 0.f);
+    int o = 0;
+#pragma unroll
+    for (int a1 = 0; a1 <= P; ++a1)
+#pragma unroll
+        for (int a2 = 0; a2 <= P - a1; ++a2) {
+            const float base = px[a1] * py[a2];
+#pragma unroll
+            for (int a3 = 0; a3 <= P - a1 - a2; ++a3) {
+                const float mono = base * pz[a3];
+                const int a = a1 + a2 + a3;
+#pragma unroll
+                for (int n = a; 2 * n <= a + P; ++n) {
+                    if ((o & 3) == 0) cur = __ldg(R + (o >> 2));
+                    const float nm = (o & 3) == 0 ? cur.x : cur.z;
+                    const float nd = (o & 3) == 0 ? cur.y : cur.w;
+                    SM[n] = fmaf(mono, nm, SM[n]);
+                    SD[n] = fmaf(mono, nd, SD[n]);
+                    o += 2;
+                }
+            }
+        }
+    float VL = 0.f, KL = 0.f, VY = 0.f, KY = 0.f;
+#pragma unroll
+    for (int n = 0; n <= P; ++n) {
+        VL = fmaf(FL[n], SM[n], VL);
+        KL = fmaf(FL[n], SD[n], KL);
+        VY = fmaf(FY[n], SM[n], VY);
+        KY = fmaf(FY[n], SD[n], KY);
+    }
     part[slot] = make_float4(VL, KL, VY, KY);
 }
 
@@ -1049,6 +1145,8 @@ void compute_strengths(Tree &Tr, const SurfDev &S, const double *phi, const doub
     PB_LAUNCH_CHECK();
 }
 
+size_t radial_floats(int P) { return (size_t)radial_stride(P); }
+
 void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s) {
     const int NT = nterms(P);
     if (Tr.ucnt.n != (size_t)Tr.nnodes) {
@@ -1061,6 +1159,15 @@ void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s) {
         upward_kernel<float><<<Tr.nleaves, 256, upward_smem(NT, 4), s>>>(
             Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p, Tr.origin[0], Tr.origin[1], Tr.origin[2],
             sv, P, NT, Tr.first_child.p, Tr.nchild.p, Tr.parent.p, Tr.ucnt.p, Tr.mom32.p);
+        if (P <= kRadialMaxP) {
+            PB_LAUNCH_CHECK();
+            Tr.rmom32.alloc((size_t)Tr.nnodes * radial_stride(P));
+            const unsigned g = (unsigned)div_up((int64_t)Tr.nnodes * (radial_stride(P) / 2), 128);
+#define PB_RAD(PP) \
+    case PP: radial_moments_kernel<PP><<<g, 128, 0, s>>>(Tr.nnodes, Tr.mom32.p, Tr.rmom32.p); break;
+            switch (P) { PB_RAD(0) PB_RAD(1) PB_RAD(2) PB_RAD(3) PB_RAD(4) PB_RAD(5) PB_RAD(6) PB_RAD(7) PB_RAD(8) }
+#undef PB_RAD
+        }
     } else {
         Tr.mom64.alloc((size_t)Tr.nnodes * 2 * NT);
         SrcView<double> sv{Tr.src64.p};
@@ -1127,15 +1234,15 @@ void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self,
 
 void launch_m2p(const Pair &Pr, const Targets &G, const Tree &Tr, int P, bool mixed, cudaStream_t s) {
     if (Pr.n_m2p_items == 0) return;
-    if (mixed && Pr.kappas.size() == 2 && Pr.kappas[0] == 0.0 && Pr.kappas[1] != 0.0 && P <= 8) {
+    if (mixed && Pr.kappas.size() == 2 && Pr.kappas[0] == 0.0 && Pr.kappas[1] != 0.0 && P <= kRadialMaxP) {
         const int64_t ni = Pr.n_m2p_items;
         const unsigned grid = (unsigned)((ni + 3) / 4);
         float4 *part = reinterpret_cast<float4 *>(Pr.m2p_part32.p);
         const float kap = (float)Pr.kappas[1];
 #define PB_LY(PP)                                                                                              \
     case PP:                                                                                                   \
-        m2p_ly32_kernel<PP><<<grid, 128, 0, s>>>(ni, Pr.m2p_items.p, Pr.m2p_inv.p, Pr.x32.p, Tr.cen32.p, Tr.mom32.p, \
-                                                 kap, part);                                                   \
+        m2p_ly32_kernel<PP><<<grid, 128, 0, s>>>(ni, Pr.m2p_items.p, Pr.m2p_inv.p, Pr.x32.p, Tr.cen32.p,          \
+                                                 Tr.rmom32.p, kap, part);                                      \
         break;
         switch (P) {
             PB_LY(0) PB_LY(1) PB_LY(2) PB_LY(3) PB_LY(4) PB_LY(5) PB_LY(6) PB_LY(7) PB_LY(8)

@@ -21,6 +21,8 @@ void upload_term_tables();
 void compute_strengths(Tree &Tr, const SurfDev &S, const double *phi, const double *dphi, bool mixed, cudaStream_t s);
 // P2M at the leaves, then M2M level by level to the root.
 void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s);
+// floats per node of the radial-form moments of order P (FP32 M2P)
+size_t radial_floats(int P);
 // M2M level by level over moments `mom` (float if mixed, else double) holding
 // `stride` values per node; shifts the 2 nterms(P) values at offset `base`.
 void m2m_pass(const Tree &Tr, int P, bool mixed, void *mom, int stride, int base, cudaStream_t s);
