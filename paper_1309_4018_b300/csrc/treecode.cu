@@ -615,20 +615,29 @@ __global__ void radial_moments_kernel(int nnodes, const float *__restrict__ mom,
 }
 
 // Box-major M2P for a pair whose two kernels are Laplace (slot 0) and Yukawa
-// (slot 1): one warp per (box, up to 32 targets) item, the box's radial
-// moments read as uniform 16-byte loads, one record (VL, KL, VY, KY) per pair.
+// (slot 1): one warp per (box, up to 32 targets) item; the warp stages the
+// box's radial moments in shared memory with coalesced loads and every lane
+// reads them as broadcasts; one record (VL, KL, VY, KY) per pair.
 template <int P>
 __global__ void __launch_bounds__(128) m2p_ly32_kernel(int64_t nitems, const int4 *__restrict__ items,
                                                        const int32_t *__restrict__ inv, const float4 *__restrict__ x32,
                                                        const float4 *__restrict__ cen32, const float *__restrict__ rmom,
                                                        float kappa, float4 *__restrict__ part) {
+    constexpr int NQ = radial_stride(P) / 4;     // float4 per box
+    __shared__ float4 sR[4][NQ];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * 4 + warp;
     if (item >= nitems) return;
     const int4 it = items[item];
+    const int b = it.x;
+    // the box's radial moments staged by the whole warp (coalesced), then read as broadcasts
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(rmom + (int64_t)b * radial_stride(P));
+        for (int q = lane; q < NQ; q += 32) sR[warp][q] = src[q];
+        __syncwarp();
+    }
     if (lane >= it.z) return;
     const int64_t slot = (int64_t)it.y + lane;
-    const int b = it.x;
     const float4 c = cen32[b];
     const float4 x = x32[inv[slot]];
     const float ux = c.x - x.x, uy = c.y - x.y, uz = c.z - x.z;
@@ -652,7 +661,7 @@ __global__ void __launch_bounds__(128) m2p_ly32_kernel(int64_t nitems, const int
     float SM[P + 1], SD[P + 1];
 #pragma unroll
     for (int n = 0; n <= P; ++n) { SM[n] = 0.f; SD[n] = 0.f; }
-    const float4 *R = reinterpret_cast<const float4 *>(rmom + (int64_t)b * radial_stride(P));
+    const float4 *R = sR[warp];
     float4 cur = make_float4(0.f, 0.f, 0.f, 0.f);
     int o = 0;
 #pragma unroll
@@ -666,7 +675,7 @@ __global__ void __launch_bounds__(128) m2p_ly32_kernel(int64_t nitems, const int
                 const int a = a1 + a2 + a3;
 #pragma unroll
                 for (int n = a; 2 * n <= a + P; ++n) {
-                    if ((o & 3) == 0) cur = __ldg(R + (o >> 2));
+                    if ((o & 3) == 0) cur = R[o >> 2];
                     const float nm = (o & 3) == 0 ? cur.x : cur.z;
                     const float nd = (o & 3) == 0 ? cur.y : cur.w;
                     SM[n] = fmaf(mono, nm, SM[n]);
