@@ -39,6 +39,7 @@
 #include "geometry.cuh"
 #include "tree.cuh"
 #include "treecode.cuh"
+#include "radial.cuh"
 
 namespace pb {
 
@@ -515,6 +516,146 @@ __global__ void __launch_bounds__(128) m2pT_kernel(int64_t nitems, const int4 *_
     T *rec = part + (int64_t)2 * nk * slot + 2 * kslot;
     rec[0] = V;
     rec[1] = K;
+}
+
+bool radial_pair(const TPair &tp, const Params &prm);
+size_t radialT_floats_per_node(int P);
+
+// ---------------------------------------------------------------- transposed M2P in radial form (FP32)
+// For a pair whose kernels are Laplace (slot 0) and Yukawa (slot 1), both
+// transposed sums in one pass.  With u = y_c - x and the radial expansion
+// of radial.cuh, the monopole potential of the box is
+//   Phi_mu(x) = sum_{alpha, n} u^alpha F_n N^mu_{alpha,n}          (order P),
+// and the target-normal field of the nu monopoles (expansion of order P - 1) is
+//   n . grad_x Phi_nu = -sum_{alpha, m} N^nu_{alpha,m} [ (n . grad u^alpha) F_m + (n . u) u^alpha F_{m+1} ],
+// since grad_x u^alpha = -grad_u u^alpha and grad_x F_m(|u|) = -u F_{m+1}.
+// Per node the radial moments are [mu_0 (order P), nu_0 (order P - 1),
+// mu_1 (order P), nu_1 (order P - 1)], padded to 16 bytes.
+__host__ __device__ constexpr int radialT_floats(int P) { return 2 * (radial_terms(P) + radial_terms(P - 1)); }
+__host__ __device__ constexpr int radialT_stride(int P) { return (radialT_floats(P) + 3) / 4 * 4; }
+
+template <int Q>
+__device__ __forceinline__ float radial_apply(int r, const float *__restrict__ M) {
+    const RadialTable<Q> &T = g_radial<Q>;
+    float v = 0.f;
+    for (int q = T.start[r]; q < T.start[r + 1]; ++q) v = fmaf(T.w[q], M[T.k[q]], v);
+    return v;
+}
+
+// One thread per (node, output).  mom: per node 4 monopole sets of NT(P) terms (mu_0, nu_0, mu_1, nu_1).
+template <int P>
+__global__ void radialT_moments_kernel(int nnodes, const float *__restrict__ mom, float *__restrict__ rmom) {
+    constexpr int NT = (P + 1) * (P + 2) * (P + 3) / 6, A = radial_terms(P), B = radial_terms(P - 1);
+    constexpr int ST = radialT_stride(P);
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nnodes * ST) return;
+    const int64_t b = t / ST;
+    const int r = (int)(t % ST);
+    const float *M = mom + b * 4 * NT;
+    float v = 0.f;
+    if (r < A) v = radial_apply<P>(r, M);
+    else if (r < A + B) v = radial_apply<P - 1>(r - A, M + NT);
+    else if (r < 2 * A + B) v = radial_apply<P>(r - A - B, M + 2 * NT);
+    else if (r < 2 * A + 2 * B) v = radial_apply<P - 1>(r - 2 * A - B, M + 3 * NT);
+    rmom[t] = v;
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) m2pT_ly32_kernel(int64_t nitems, const int4 *__restrict__ items,
+                                                        const int32_t *__restrict__ inv, const float4 *__restrict__ x32,
+                                                        const float4 *__restrict__ n32, const float4 *__restrict__ cen32,
+                                                        const float *__restrict__ rmom, float kappa,
+                                                        float4 *__restrict__ part) {
+    constexpr int A = radial_terms(P), B = radial_terms(P - 1), NQ = radialT_stride(P) / 4;
+    __shared__ float4 sR[4][NQ];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * 4 + warp;
+    if (item >= nitems) return;
+    const int4 it = items[item];
+    const int b = it.x;
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(rmom + (int64_t)b * radialT_stride(P));
+        for (int q = lane; q < NQ; q += 32) sR[warp][q] = src[q];
+        __syncwarp();
+    }
+    if (lane >= it.z) return;
+    const int64_t slot = (int64_t)it.y + lane;
+    const int t = inv[slot];
+    const float4 c = cen32[b], x = x32[t], nn = n32[t];
+    const float ux = c.x - x.x, uy = c.y - x.y, uz = c.z - x.z;
+    const float r2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+    const float rinv = rsqrtf(r2), ir2 = rinv * rinv;
+    float FL[P + 1], FY[P + 1];
+    FL[0] = rinv;
+#pragma unroll
+    for (int n = 0; n < P; ++n) FL[n + 1] = (-(float)(2 * n + 1) * ir2) * FL[n];
+    const float rho = r2 * rinv;
+    const float e = __expf(-kappa * rho);
+    FY[0] = e * rinv;
+    FY[1] = -fmaf(kappa, rho, 1.f) * FY[0] * ir2;
+    const float k2 = kappa * kappa;
+#pragma unroll
+    for (int n = 1; n < P; ++n) FY[n + 1] = fmaf(k2, FY[n - 1], -(float)(2 * n + 1) * FY[n]) * ir2;
+    float px[P + 1], py[P + 1], pz[P + 1], dx[P + 1], dy[P + 1], dz[P + 1];
+    px[0] = py[0] = pz[0] = 1.f;
+    dx[0] = dy[0] = dz[0] = 0.f;
+#pragma unroll
+    for (int i = 1; i <= P; ++i) {
+        dx[i] = (float)i * nn.x * px[i - 1];
+        dy[i] = (float)i * nn.y * py[i - 1];
+        dz[i] = (float)i * nn.z * pz[i - 1];
+        px[i] = px[i - 1] * ux;
+        py[i] = py[i - 1] * uy;
+        pz[i] = pz[i - 1] * uz;
+    }
+    float SL[P + 1], SY[P + 1], GL[P], HL[P], GY[P], HY[P];
+#pragma unroll
+    for (int n = 0; n <= P; ++n) { SL[n] = 0.f; SY[n] = 0.f; }
+#pragma unroll
+    for (int n = 0; n < P; ++n) { GL[n] = 0.f; HL[n] = 0.f; GY[n] = 0.f; HY[n] = 0.f; }
+    const float *R = reinterpret_cast<const float *>(sR[warp]);
+    int om = 0, on = 0;
+#pragma unroll
+    for (int a1 = 0; a1 <= P; ++a1)
+#pragma unroll
+        for (int a2 = 0; a2 <= P - a1; ++a2) {
+            const float base = px[a1] * py[a2];
+            const float dbase = fmaf(dx[a1], py[a2], px[a1] * dy[a2]);
+#pragma unroll
+            for (int a3 = 0; a3 <= P - a1 - a2; ++a3) {
+                const int a = a1 + a2 + a3;
+                const float mono = base * pz[a3];
+#pragma unroll
+                for (int n = a; 2 * n <= a + P; ++n, ++om) {
+                    SL[n] = fmaf(mono, R[om], SL[n]);
+                    SY[n] = fmaf(mono, R[A + B + om], SY[n]);
+                }
+                if (a <= P - 1) {
+                    const float dmono = fmaf(dbase, pz[a3], base * dz[a3]);
+#pragma unroll
+                    for (int m = a; 2 * m <= a + P - 1; ++m, ++on) {
+                        const float wl = R[A + on], wy = R[2 * A + B + on];
+                        GL[m] = fmaf(dmono, wl, GL[m]);
+                        HL[m] = fmaf(mono, wl, HL[m]);
+                        GY[m] = fmaf(dmono, wy, GY[m]);
+                        HY[m] = fmaf(mono, wy, HY[m]);
+                    }
+                }
+            }
+        }
+    const float nu = fmaf(nn.x, ux, fmaf(nn.y, uy, nn.z * uz));
+    float VL = 0.f, VY = 0.f, KL = 0.f, KY = 0.f;
+#pragma unroll
+    for (int n = 0; n <= P; ++n) {
+        VL = fmaf(FL[n], SL[n], VL);
+        VY = fmaf(FY[n], SY[n], VY);
+    }
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+        KL = fmaf(FL[m], GL[m], fmaf(nu * FL[m + 1], HL[m], KL));
+        KY = fmaf(FY[m], GY[m], fmaf(nu * FY[m + 1], HY[m], KY));
+    }
+    part[slot] = make_float4(VL, -KL, VY, -KY);
 }
 
 // ---------------------------------------------------------------- transposed near list
@@ -1263,6 +1404,7 @@ void init_tpair(pb_problem *pb, AdjointState &A, TPair &tp, const Tree &Tr) {
     if (L.n_m2p > 0) {
         const size_t nm = (size_t)Tr.nnodes * 2 * nk * nterms(prm.P);
         if (mixed) tp.mom32.alloc(nm); else tp.mom64.alloc(nm);
+        if (radial_pair(tp, prm)) tp.rmom32.alloc((size_t)Tr.nnodes * radialT_floats_per_node(prm.P));
     }
     // transposed near list: forward entries grouped by panel of the target surface
     const int64_t npan = pb->S[tp.tgt].n, nn = F.n_near;
@@ -1442,6 +1584,33 @@ void launch_m2pT_typed(int P, bool yuk, const TPair &tp, const Targets &G, const
     PB_LAUNCH_CHECK();
 }
 
+// A mixed-precision pair of a Laplace (slot 0) and a Yukawa (slot 1) kernel takes the radial-form kernel.
+bool radial_pair(const TPair &tp, const Params &prm) {
+    return prm.precision == PB_MIXED && tp.nk == 2 && tp.L.kappas[0] == 0.0 && tp.L.kappas[1] != 0.0 &&
+           prm.P >= 1 && prm.P <= kRadialMaxP;
+}
+
+size_t radialT_floats_per_node(int P) { return (size_t)radialT_stride(P); }
+
+void launch_m2pT_radial(int P, TPair &tp, const Targets &G, const float4 *n32, const Tree &Tr, cudaStream_t s) {
+    const Pair &Pr = tp.L;
+    const int64_t ni = Pr.n_m2p_items;
+    const unsigned grid = (unsigned)((ni + 3) / 4);
+    const unsigned gt = (unsigned)div_up((int64_t)Tr.nnodes * radialT_stride(P), 128);
+    float4 *part = reinterpret_cast<float4 *>(Pr.m2p_part32.p);
+    const float kap = (float)Pr.kappas[1];
+#define PB_RT(PP)                                                                                               \
+    case PP:                                                                                                    \
+        radialT_moments_kernel<PP><<<gt, 128, 0, s>>>(Tr.nnodes, tp.mom32.p, tp.rmom32.p);                      \
+        PB_LAUNCH_CHECK();                                                                                      \
+        m2pT_ly32_kernel<PP><<<grid, 128, 0, s>>>(ni, Pr.m2p_items.p, Pr.m2p_inv.p, Pr.x32.p, n32, Tr.cen32.p,  \
+                                                  tp.rmom32.p, kap, part);                                      \
+        break;
+    switch (P) { PB_RT(1) PB_RT(2) PB_RT(3) PB_RT(4) PB_RT(5) PB_RT(6) PB_RT(7) PB_RT(8) default: break; }
+#undef PB_RT
+    PB_LAUNCH_CHECK();
+}
+
 // Transposed products of the listed pairs: sources folded from u (rows of each
 // pair's source surface, or the charges), their sums at the Gauss points, and
 // the per-panel combination into out (unknown order).  half: add the 1/2 phi
@@ -1495,12 +1664,15 @@ void apply_tpairs(pb_problem *pb, std::vector<TPair> &list, const double *u, dou
         const double *n64 = A.gn64[tp.tgt].p;
         const float4 *n32 = A.gn32[tp.tgt].p;
         launch_p2pT(tp, G, n64, n32, Tr, mixed, s);
-        if (tp.L.n_m2p_items > 0)
+        if (tp.L.n_m2p_items > 0 && radial_pair(tp, prm)) {
+            launch_m2pT_radial(prm.P, tp, G, n32, Tr, s);
+        } else if (tp.L.n_m2p_items > 0) {
             for (int k = 0; k < tp.nk; ++k) {
                 const bool yuk = tp.L.kappas[k] != 0.0;
                 if (mixed) launch_m2pT_typed<float>(prm.P, yuk, tp, G, n64, n32, Tr, tp.mom32.p, k, tp.L.m2p_part32.p, s);
                 else launch_m2pT_typed<double>(prm.P, yuk, tp, G, n64, n32, Tr, tp.mom64.p, k, tp.L.m2p_part64.p, s);
             }
+        }
         launch_gather(tp.L, G, mixed, false, u0, u0, nullptr, s);
     }
     for (int t = 0; t < ns; ++t) {

@@ -25,6 +25,7 @@ struct TPair {
     DevBuf<float4> srcA32, srcB32;   // (x, y, z, mu0), (nu0, mu1, nu1, owner bits)
     DevBuf<double> mom64;      // per node 2 nk nterms(P): mu0, nu0, mu1, nu1 moments
     DevBuf<float> mom32;
+    DevBuf<float> rmom32;      // radial-form moments (mixed Laplace + Yukawa pairs)
     DevBuf<int64_t> nt_ptr;    // transposed near list: per target panel its forward entries
     DevBuf<int32_t> nt_ent, nt_src;
 };
