@@ -209,9 +209,15 @@ __device__ __forceinline__ bool arrive_last(unsigned *count) {
     return last;
 }
 
-// Block partials of V[v] . w over the block's slice, for v < nv.
+// Block partials of V[v] . w over the block's slice, for v < nv.  The FP64
+// pipe is narrow on this part, so the block reduction is arranged to issue
+// few FP64 instructions: every thread's partials go to shared memory, each
+// (vector, 8-thread chunk) is summed by one thread, and one warp per vector
+// adds the 32 chunk sums by a butterfly (96 FP64 warp instructions per
+// group of 8 vectors instead of a butterfly per vector in every warp).
 __device__ void slice_dots(const ArnoldiArgs &a, int64_t lo, int64_t hi) {
-    __shared__ double sm[kDotGroup][kRedThreads / 32];
+    static_assert(kRedThreads == 256 && kDotGroup == 8, "the reduction layout assumes 256 threads, 8 vectors");
+    __shared__ double red[kDotGroup][kRedThreads + 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int v0 = 0; v0 < a.nv; v0 += kDotGroup) {
         const int nb = min(kDotGroup, a.nv - v0);
@@ -225,16 +231,15 @@ __device__ void slice_dots(const ArnoldiArgs &a, int64_t lo, int64_t hi) {
                 if (b < nb) acc[b] += a.V[(int64_t)(v0 + b) * a.ld + i] * wi;
         }
 #pragma unroll
-        for (int b = 0; b < kDotGroup; ++b) {
-            double t = acc[b];
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) sm[b][wid] = t;
-        }
+        for (int b = 0; b < kDotGroup; ++b) red[b][threadIdx.x] = acc[b];
         __syncthreads();
-        if (threadIdx.x < nb) {
-            double t = 0.0;
-            for (int k = 0; k < kRedThreads / 32; ++k) t += sm[threadIdx.x][k];
-            a.partial[(v0 + threadIdx.x) * kRedBlocks + blockIdx.x] = t;
+        // thread (vector wid, chunk lane) sums the partials of threads 8 lane .. 8 lane + 7
+        double t = 0.0;
+        if (wid < nb) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) t += red[wid][8 * lane + k];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) a.partial[(v0 + wid) * kRedBlocks + blockIdx.x] = t;
         }
         __syncthreads();
     }
