@@ -66,12 +66,18 @@ __global__ void mdot_finish_kernel(const double *__restrict__ partial, int nv, d
     if (threadIdx.x == 0) out[v] = accumulate ? out[v] + s : s;
 }
 
+// dst = src / sqrt(*num_sq): the reciprocal is formed once per block (FP64
+// division and square root are long sequences on the narrow FP64 pipe).
 __global__ void scale_copy_kernel(const double *__restrict__ src, const double *__restrict__ num_sq,
                                   double *__restrict__ dst, int64_t n) {
+    __shared__ double inv;
+    if (threadIdx.x == 0) {
+        const double d = sqrt(*num_sq);
+        inv = d > 0.0 ? 1.0 / d : 0.0;
+    }
+    __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double d = sqrt(*num_sq);
-    dst[i] = d > 0.0 ? src[i] / d : 0.0;
+    if (i < n) dst[i] = src[i] * inv;
 }
 
 __global__ void axpby_kernel(double a, const double *__restrict__ x, double b, const double *__restrict__ y,
@@ -245,11 +251,14 @@ __device__ void slice_dots(const ArnoldiArgs &a, int64_t lo, int64_t hi) {
     }
 }
 
+// One warp per vector: lanes take the block partials in a fixed stride, then a butterfly.
 __device__ void finish_dots(const ArnoldiArgs &a, int nv, double *out) {
-    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int v = wid; v < nv; v += kRedThreads / 32) {
         double t = 0.0;
-        for (int b = 0; b < kRedBlocks; ++b) t += __ldcg(a.partial + v * kRedBlocks + b);
-        out[v] = t;
+        for (int b = lane; b < kRedBlocks; b += 32) t += __ldcg(a.partial + v * kRedBlocks + b);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) out[v] = t;
     }
 }
 
@@ -303,9 +312,15 @@ __global__ void __launch_bounds__(kRedThreads) arnoldi_project_norm_kernel(Arnol
         a.partial[blockIdx.x] = t;
     }
     if (arrive_last(a.count)) {
+        // ||w||^2 from the block partials: a fixed tree over the whole block
+        double p = 0.0;
+        for (int b = threadIdx.x; b < kRedBlocks; b += kRedThreads) p += __ldcg(a.partial + b);
+        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = p;
+        __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
-            for (int b = 0; b < kRedBlocks; ++b) t += __ldcg(a.partial + b);
+            for (int k = 0; k < kRedThreads / 32; ++k) t += sm[k];
             *a.nrm2 = t;
             *a.count = 0;
             // Hessenberg column j = h1 + h2 with the new subdiagonal ||w||
