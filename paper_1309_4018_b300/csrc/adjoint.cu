@@ -1658,8 +1658,11 @@ void apply_tpairs(pb_problem *pb, std::vector<TPair> &list, const double *u, dou
                                                                    Tr.origin[2], sv, prm.P, NT, NS, tp.mom64.p);
             }
             PB_LAUNCH_CHECK();
-            for (int k = 0; k < tp.nk; ++k)
-                m2m_pass(Tr, prm.P, mixed, mixed ? (void *)tp.mom32.p : (void *)tp.mom64.p, NS * NT, 2 * k * NT, s);
+            void *mom = mixed ? (void *)tp.mom32.p : (void *)tp.mom64.p;
+            if (climb_fits(NS * NT, mixed))
+                m2m_climb(const_cast<Tree &>(Tr), prm.P, mixed, mom, NS * NT, s);
+            else
+                for (int k = 0; k < tp.nk; ++k) m2m_pass(Tr, prm.P, mixed, mom, NS * NT, 2 * k * NT, s);
         }
         const double *n64 = A.gn64[tp.tgt].p;
         const float4 *n32 = A.gn32[tp.tgt].p;

@@ -130,6 +130,7 @@ __device__ __forceinline__ Quad<double> ld4(const double *p) {
 // reads terms with |l| <= |k|, so the truncated set is closed under the
 // passes.  One block per node of the level; the children (contiguous node
 // ids) are shifted in parallel in shared memory and added in child order.
+constexpr size_t kClimbMaxShared = 220 * 1024;   // dynamic shared memory of the one-launch M2M (227 KB less the static arrays)
 constexpr int kM2MMaxShared = 2 * 8 * 2 * 455 * 8 + 3 * 455 * 4;
 
 // Each node holds `stride` values; one launch shifts the 2 NT values at
@@ -861,6 +862,98 @@ void launch_m2p_typed(int P, bool yuk, const Pair &Pr, const double *xs, const d
 template <typename T>
 __device__ __forceinline__ T ld_cg(const T *p) { return __ldcg(p); }
 
+// Climb from `node` (whose moments are complete) towards the root: after each
+// node the block announces it to the parent (a fence, then an atomic count);
+// the block that brings a parent's count to its number of children shifts the
+// children's moments into it (three one-axis passes in shared memory, children
+// added in child order) and continues from there.  Every node holds `nval`
+// values: nval / NT sets of NT moments, each shifted by the same rule.  No
+// block waits for another.  buf0, buf1: 8 * nval values each.
+template <typename T>
+__device__ void climb_m2m(int node, int P, int NT, int nval, const double *__restrict__ centre,
+                          const int32_t *__restrict__ first_child, const int32_t *__restrict__ nchild,
+                          const int32_t *__restrict__ parent, int32_t *__restrict__ ucnt, T *__restrict__ mom,
+                          T *buf0, T *buf1, T (*hp)[3][kMaxP + 1], T (*sbin)[kMaxP + 1], const int *sterm,
+                          int &s_next) {
+    while (true) {
+        __threadfence();   // every thread's moment stores before the announcement
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int par = parent[node];
+            int next = -1;
+            if (par >= 0 && atomicAdd(&ucnt[par], 1) == nchild[par] - 1) {
+                next = par;
+                ucnt[par] = 0;
+            }
+            s_next = next;
+        }
+        __syncthreads();
+        const int b = s_next;
+        if (b < 0) return;
+        __threadfence();
+        const int nc = nchild[b], fc = first_child[b];
+        for (int i = threadIdx.x; i < nc * nval; i += blockDim.x) {
+            const int c = i / nval, r = i - c * nval;
+            buf0[i] = ld_cg(mom + (int64_t)(fc + c) * nval + r);
+        }
+        for (int i = threadIdx.x; i < nc * 3; i += blockDim.x) {
+            const int c = i / 3, ax = i - 3 * c;
+            const T h = (T)(centre[3 * (fc + c) + ax] - centre[3 * b + ax]);
+            T v = 1;
+            for (int e = 0; e <= P; ++e) { hp[c][ax][e] = v; v *= h; }
+        }
+        __syncthreads();
+        T *src = buf0, *dst = buf1;
+        for (int ax = 2; ax >= 0; --ax) {
+            for (int idx = threadIdx.x; idx < nc * nval; idx += blockDim.x) {
+                const int c = idx / nval, r = idx - c * nval;
+                const int set = r / NT, k = r - set * NT;
+                int kx[3] = {sterm[3 * k], sterm[3 * k + 1], sterm[3 * k + 2]};
+                const int kax = kx[ax];
+                const T *sc = src + c * nval + set * NT;
+                T acc = 0;
+                for (int l = 0; l <= kax; ++l) {
+                    kx[ax] = l;
+                    acc += sbin[kax][l] * hp[c][ax][kax - l] * sc[term_index(kx[0], kx[1], kx[2])];
+                }
+                dst[idx] = acc;
+            }
+            __syncthreads();
+            T *tmp = src; src = dst; dst = tmp;
+        }
+        for (int r = threadIdx.x; r < nval; r += blockDim.x) {
+            T acc = 0;
+            for (int c = 0; c < nc; ++c) acc += src[c * nval + r];
+            mom[(int64_t)b * nval + r] = acc;
+        }
+        node = b;
+    }
+}
+
+// M2M of every internal node by the climb alone (the leaves' moments already
+// computed): one block per leaf, nval values per node.
+template <typename T>
+__global__ void __launch_bounds__(256) climb_kernel(int nleaves, const int32_t *__restrict__ leaf_node,
+                                                    const double *__restrict__ centre, int P, int NT, int nval,
+                                                    const int32_t *__restrict__ first_child,
+                                                    const int32_t *__restrict__ nchild,
+                                                    const int32_t *__restrict__ parent, int32_t *__restrict__ ucnt,
+                                                    T *__restrict__ mom) {
+    extern __shared__ __align__(16) unsigned char up_smem[];
+    int *sterm = reinterpret_cast<int *>(up_smem);
+    T *region = reinterpret_cast<T *>(up_smem + ((3 * 455 * sizeof(int) + 31) / 32) * 32);
+    __shared__ T hp[8][3][kMaxP + 1];
+    __shared__ T sbin[kMaxP + 1][kMaxP + 1];
+    __shared__ int s_next;
+    for (int i = threadIdx.x; i < 3 * NT; i += blockDim.x) sterm[i] = c_terms[i];
+    for (int i = threadIdx.x; i < (P + 1) * (P + 1); i += blockDim.x) {
+        const int n = i / (P + 1), k = i - n * (P + 1);
+        sbin[n][k] = (T)c_binom[n][k];
+    }
+    climb_m2m<T>(leaf_node[blockIdx.x], P, NT, nval, centre, first_child, nchild, parent, ucnt, mom, region,
+                 region + 8 * nval, hp, sbin, sterm, s_next);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) upward_kernel(int nleaves, const int32_t *__restrict__ leaf_node,
                                                      const int64_t *__restrict__ start,
@@ -975,60 +1068,8 @@ __global__ void __launch_bounds__(256) upward_kernel(int nleaves, const int32_t 
         }
     }
     // ---- climb: the last child to finish computes the parent
-    T *buf0 = region, *buf1 = region + 8 * 2 * NT;
-    while (true) {
-        __threadfence();   // every thread's moment stores before the announcement
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int par = parent[node];
-            int next = -1;
-            if (par >= 0 && atomicAdd(&ucnt[par], 1) == nchild[par] - 1) {
-                next = par;
-                ucnt[par] = 0;
-            }
-            s_next = next;
-        }
-        __syncthreads();
-        const int b = s_next;
-        if (b < 0) return;
-        __threadfence();
-        const int nc = nchild[b], fc = first_child[b];
-        for (int i = threadIdx.x; i < nc * 2 * NT; i += blockDim.x) {
-            const int c = i / (2 * NT), r = i - c * 2 * NT;
-            buf0[i] = ld_cg(mom + (int64_t)(fc + c) * 2 * NT + r);
-        }
-        for (int i = threadIdx.x; i < nc * 3; i += blockDim.x) {
-            const int c = i / 3, ax = i - 3 * c;
-            const T h = (T)(centre[3 * (fc + c) + ax] - centre[3 * b + ax]);
-            T v = 1;
-            for (int e = 0; e <= P; ++e) { hp[c][ax][e] = v; v *= h; }
-        }
-        __syncthreads();
-        T *src = buf0, *dst = buf1;
-        for (int ax = 2; ax >= 0; --ax) {
-            for (int idx = threadIdx.x; idx < nc * 2 * NT; idx += blockDim.x) {
-                const int c = idx / (2 * NT), r = idx - c * 2 * NT;
-                const int half = r >= NT ? NT : 0, k = r - half;
-                int kx[3] = {sterm[3 * k], sterm[3 * k + 1], sterm[3 * k + 2]};
-                const int kax = kx[ax];
-                const T *sc = src + c * 2 * NT + half;
-                T acc = 0;
-                for (int l = 0; l <= kax; ++l) {
-                    kx[ax] = l;
-                    acc += sbin[kax][l] * hp[c][ax][kax - l] * sc[term_index(kx[0], kx[1], kx[2])];
-                }
-                dst[idx] = acc;
-            }
-            __syncthreads();
-            T *tmp = src; src = dst; dst = tmp;
-        }
-        for (int r = threadIdx.x; r < 2 * NT; r += blockDim.x) {
-            T acc = 0;
-            for (int c = 0; c < nc; ++c) acc += src[c * 2 * NT + r];
-            mom[(int64_t)b * 2 * NT + r] = acc;
-        }
-        node = b;
-    }
+    climb_m2m<T>(node, P, NT, 2 * NT, centre, first_child, nchild, parent, ucnt, mom, region, region + 8 * 2 * NT,
+                 hp, sbin, sterm, s_next);
 }
 
 size_t upward_smem(int NT, size_t elem) {
@@ -1045,6 +1086,10 @@ void upload_term_tables() {
                                      (int)upward_smem(455, 8)));
     PB_CUDA_TRY(cudaFuncSetAttribute(upward_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)upward_smem(455, 4)));
+    PB_CUDA_TRY(cudaFuncSetAttribute(climb_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kClimbMaxShared));
+    PB_CUDA_TRY(cudaFuncSetAttribute(climb_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kClimbMaxShared));
     PB_CUDA_TRY(cudaFuncSetAttribute(m2m_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kM2MMaxShared));
     PB_CUDA_TRY(cudaFuncSetAttribute(m2m_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kM2MMaxShared));
     int terms[3 * kMaxTerms1];
@@ -1112,6 +1157,31 @@ void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s) {
             Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p, Tr.origin[0], Tr.origin[1], Tr.origin[2],
             sv, P, NT, Tr.first_child.p, Tr.nchild.p, Tr.parent.p, Tr.ucnt.p, Tr.mom64.p);
     }
+    PB_LAUNCH_CHECK();
+}
+
+size_t climb_smem(int nval, bool mixed) {
+    return (3 * 455 * sizeof(int) + 31) / 32 * 32 + (size_t)2 * 8 * nval * (mixed ? sizeof(float) : sizeof(double));
+}
+
+bool climb_fits(int nval, bool mixed) { return climb_smem(nval, mixed) <= kClimbMaxShared; }
+
+void m2m_climb(Tree &Tr, int P, bool mixed, void *mom, int nval, cudaStream_t s) {
+    const int NT = nterms(P);
+    if (Tr.ucnt.n != (size_t)Tr.nnodes) {
+        Tr.ucnt.alloc(Tr.nnodes);
+        Tr.ucnt.zero(s);
+    }
+    const size_t shm = climb_smem(nval, mixed);
+    if (shm > kClimbMaxShared) fail(PB_EINVAL, "internal: moment sets too large for the one-launch M2M");
+    if (mixed)
+        climb_kernel<float><<<Tr.nleaves, 256, shm, s>>>(Tr.nleaves, Tr.leaf_node.p, Tr.centre.p, P, NT, nval,
+                                                         Tr.first_child.p, Tr.nchild.p, Tr.parent.p, Tr.ucnt.p,
+                                                         (float *)mom);
+    else
+        climb_kernel<double><<<Tr.nleaves, 256, shm, s>>>(Tr.nleaves, Tr.leaf_node.p, Tr.centre.p, P, NT, nval,
+                                                          Tr.first_child.p, Tr.nchild.p, Tr.parent.p, Tr.ucnt.p,
+                                                          (double *)mom);
     PB_LAUNCH_CHECK();
 }
 

@@ -25,6 +25,11 @@ void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s);
 size_t radial_floats(int P);
 // M2M level by level over moments `mom` (float if mixed, else double) holding
 // `stride` values per node; shifts the 2 nterms(P) values at offset `base`.
+// M2M of every internal node in one launch (the leaves' moments complete): nval values per node,
+// nval / NT moment sets shifted by the same rule.  Needs Tr.ucnt zeroed (the kernel leaves it zeroed).
+void m2m_climb(Tree &Tr, int P, bool mixed, void *mom, int nval, cudaStream_t s);
+// whether nval values per node fit the one-launch M2M's shared memory
+bool climb_fits(int nval, bool mixed);
 void m2m_pass(const Tree &Tr, int P, bool mixed, void *mom, int stride, int base, cudaStream_t s);
 // Direct-sum partials of every (target, leaf) list entry.
 void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self, bool mixed, cudaStream_t s);
