@@ -26,6 +26,9 @@ pb_problem::~pb_problem() {
     if (mv_exec) cudaGraphExecDestroy(mv_exec);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
+    if (evf) cudaEventDestroy(evf);
+    if (evj) cudaEventDestroy(evj);
+    if (side) cudaStreamDestroy(side);
 }
 
 namespace {
@@ -315,16 +318,30 @@ void apply_operator(pb_problem *pb, const double *xd, double *yd, PhaseEvents *p
         if (ph) PB_CUDA_TRY(cudaEventRecord(ph->ev[k], s));
     };
     mark(0);
+    // Without phase marks the direct sums (which need only the source
+    // strengths) run on the side stream while the upward pass and the
+    // expansions run here; the gather waits for both.
+    const bool fork = !ph && pb->side;
     for (int t = 0; t < ns; ++t) {
         const double *phi = xd + 2 * pb->off[t];
         const double *dphi = phi + pb->S[t].n;
         compute_strengths(pb->T[t], pb->S[t], phi, dphi, mixed, s);
+    }
+    if (fork) PB_CUDA_TRY(cudaEventRecord(pb->evf, s));
+    // the upward pass is enqueued first: its blocks (one per leaf) start before the direct sums fill the GPU
+    for (int t = 0; t < ns; ++t)
         if (pb->need_far[t]) upward_pass(pb->T[t], prm.P, mixed, s);
+    if (fork) {
+        PB_CUDA_TRY(cudaStreamWaitEvent(pb->side, pb->evf, 0));
+        for (auto &P : pb->pairs) launch_p2p(P, pb->G[P.tgt], pb->T[P.tree], P.tgt == P.tree, mixed, pb->side);
+        PB_CUDA_TRY(cudaEventRecord(pb->evj, pb->side));
     }
     mark(1);
-    for (auto &P : pb->pairs) launch_p2p(P, pb->G[P.tgt], pb->T[P.tree], P.tgt == P.tree, mixed, s);
+    if (!fork)
+        for (auto &P : pb->pairs) launch_p2p(P, pb->G[P.tgt], pb->T[P.tree], P.tgt == P.tree, mixed, s);
     mark(2);
     for (auto &P : pb->pairs) launch_m2p(P, pb->G[P.tgt], pb->T[P.tree], prm.P, mixed, s);
+    if (fork) PB_CUDA_TRY(cudaStreamWaitEvent(s, pb->evj, 0));
     mark(3);
     for (auto &P : pb->pairs) {
         const double *phi = xd + 2 * pb->off[P.tree];
@@ -731,6 +748,9 @@ int pb_problem_create(pb_ctx *c, pb_problem **out) {
         set_device(c);
         PB_CUDA_TRY(cudaEventCreate(&pb->ev0));
         PB_CUDA_TRY(cudaEventCreate(&pb->ev1));
+        PB_CUDA_TRY(cudaStreamCreateWithFlags(&pb->side, cudaStreamNonBlocking));
+        PB_CUDA_TRY(cudaEventCreateWithFlags(&pb->evf, cudaEventDisableTiming));
+        PB_CUDA_TRY(cudaEventCreateWithFlags(&pb->evj, cudaEventDisableTiming));
     });
     if (rc != PB_OK) return rc;
     *out = pb.release();

@@ -54,6 +54,8 @@ struct pb_problem {
     pb_ctx *ctx = nullptr;
     cudaStream_t stream = nullptr;            // the context stream, or a pool stream inside a batch
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaStream_t side = nullptr;              // the operator's direct sums run here beside the upward pass
+    cudaEvent_t evf = nullptr, evj = nullptr; // fork and join of the side stream
     cudaGraphExec_t mv_exec = nullptr;        // captured operator application z1 -> gm.w
     long long mv_kernels = 0;                 // kernels in that graph
     std::vector<pb::Region> regions;
