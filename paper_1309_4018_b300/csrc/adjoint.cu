@@ -1507,6 +1507,15 @@ void prepare_adjoint(pb_problem *pb) {
     A->f.alloc(2 * pb->N);
     A->gacc.alloc(2 * pb->regions.size());
     A->part.alloc(kDotBlocks);
+    // counters of the one-launch M2M (the transposed operator is captured into a graph: nothing allocates there)
+    auto counters = [&](Tree &T) {
+        if (T.nnodes > 0) {
+            T.ucnt.alloc(T.nnodes);
+            T.ucnt.zero(s);
+        }
+    };
+    for (Tree &T : A->TC) counters(T);
+    counters(A->TQ);
     PB_CUDA_TRY(cudaStreamSynchronize(s));
     pb->adj = A;
 }
@@ -1644,6 +1653,11 @@ void apply_tpairs(pb_problem *pb, std::vector<TPair> &list, const double *u, dou
                                                                     tp.src64.p);
             PB_LAUNCH_CHECK();
         }
+        // the direct sums need only the strengths: they run on the side stream beside the expansions
+        const double *n64 = A.gn64[tp.tgt].p;
+        const float4 *n32 = A.gn32[tp.tgt].p;
+        const bool fork = pb->side != nullptr;
+        if (fork) PB_CUDA_TRY(cudaEventRecord(pb->evf, s));
         if (tp.L.n_m2p > 0) {
             const int NS = 2 * tp.nk;
             if (mixed) {
@@ -1664,9 +1678,13 @@ void apply_tpairs(pb_problem *pb, std::vector<TPair> &list, const double *u, dou
             else
                 for (int k = 0; k < tp.nk; ++k) m2m_pass(Tr, prm.P, mixed, mom, NS * NT, 2 * k * NT, s);
         }
-        const double *n64 = A.gn64[tp.tgt].p;
-        const float4 *n32 = A.gn32[tp.tgt].p;
-        launch_p2pT(tp, G, n64, n32, Tr, mixed, s);
+        if (fork) {
+            PB_CUDA_TRY(cudaStreamWaitEvent(pb->side, pb->evf, 0));
+            launch_p2pT(tp, G, n64, n32, Tr, mixed, pb->side);
+            PB_CUDA_TRY(cudaEventRecord(pb->evj, pb->side));
+        } else {
+            launch_p2pT(tp, G, n64, n32, Tr, mixed, s);
+        }
         if (tp.L.n_m2p_items > 0 && radial_pair(tp, prm)) {
             launch_m2pT_radial(prm.P, tp, G, n32, Tr, s);
         } else if (tp.L.n_m2p_items > 0) {
@@ -1676,6 +1694,7 @@ void apply_tpairs(pb_problem *pb, std::vector<TPair> &list, const double *u, dou
                 else launch_m2pT_typed<double>(prm.P, yuk, tp, G, n64, n32, Tr, tp.mom64.p, k, tp.L.m2p_part64.p, s);
             }
         }
+        if (fork) PB_CUDA_TRY(cudaStreamWaitEvent(s, pb->evj, 0));
         launch_gather(tp.L, G, mixed, false, u0, u0, nullptr, s);
     }
     for (int t = 0; t < ns; ++t) {
@@ -1853,7 +1872,21 @@ void energy_gradient(pb_problem *pb, pb_grad *out) {
     DevOp op = [pb](const double *u, double *v) { apply_transpose(pb, u, v); };
     DevOp pc;
     if (prm.precond) pc = [pb](const double *u, double *z) { apply_precond_T(pb, u, z); };
-    const KrylovStats st = run_gmres(pb, op, pc, A.f.p, A.lam.p, true);
+    KrylovJob jb;
+    jb.pb = pb;
+    jb.op = op;
+    jb.precond = pc;
+    jb.b = A.f.p;
+    jb.x = A.lam.p;
+    jb.x_zero = true;
+    // every Arnoldi step replays the transposed operator as one captured graph
+    jb.graph = [pb](cudaStream_t gs) {
+        launch_captured(pb, pb->adj_exec, pb->adj_kernels,
+                        [pb] { apply_tpairs(pb, pb->adj->tp, pb->z1.p, pb->gm.w.p, true); }, gs);
+    };
+    std::vector<KrylovJob *> jobs{&jb};
+    run_krylov(jobs);
+    const KrylovStats st = jb.st;
     const double *lam = A.lam.p;
     // forward block sums at the solution
     reaction(pb, x);

@@ -24,6 +24,7 @@ std::atomic<long long> g_launches{0};
 
 pb_problem::~pb_problem() {
     if (mv_exec) cudaGraphExecDestroy(mv_exec);
+    if (adj_exec) cudaGraphExecDestroy(adj_exec);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     if (evf) cudaEventDestroy(evf);
@@ -128,6 +129,10 @@ void setup_problem(pb_problem *pb) {
     if (pb->mv_exec) {
         cudaGraphExecDestroy(pb->mv_exec);
         pb->mv_exec = nullptr;
+    }
+    if (pb->adj_exec) {
+        cudaGraphExecDestroy(pb->adj_exec);
+        pb->adj_exec = nullptr;
     }
     upload_rules();
     upload_term_tables();
@@ -411,28 +416,33 @@ void apply_precond(pb_problem *pb, const double *u, double *z) {
     }
 }
 
-void launch_operator_graph(pb_problem *pb, cudaStream_t s) {
-    if (!pb->mv_exec) {
+void launch_captured(pb_problem *pb, cudaGraphExec_t &exec, long long &nk, const std::function<void()> &body,
+                     cudaStream_t s) {
+    if (!exec) {
         cudaStream_t cs = pb->stream;
         const long long k0 = g_launches.load();
         PB_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         cudaGraph_t graph = nullptr;
         try {
-            apply_operator(pb, pb->z1.p, pb->gm.w.p);
+            body();
         } catch (...) {
             cudaStreamEndCapture(cs, &graph);
             if (graph) cudaGraphDestroy(graph);
             throw;
         }
         PB_CUDA_TRY(cudaStreamEndCapture(cs, &graph));
-        const cudaError_t e = cudaGraphInstantiate(&pb->mv_exec, graph, 0);
+        const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         PB_CUDA_TRY(e);
-        pb->mv_kernels = g_launches.load() - k0;
-        g_launches.fetch_sub(pb->mv_kernels);   // captured, not executed
+        nk = g_launches.load() - k0;
+        g_launches.fetch_sub(nk);   // captured, not executed
     }
-    PB_CUDA_TRY(cudaGraphLaunch(pb->mv_exec, s));
-    g_launches.fetch_add(pb->mv_kernels);
+    PB_CUDA_TRY(cudaGraphLaunch(exec, s));
+    g_launches.fetch_add(nk);
+}
+
+void launch_operator_graph(pb_problem *pb, cudaStream_t s) {
+    launch_captured(pb, pb->mv_exec, pb->mv_kernels, [pb] { apply_operator(pb, pb->z1.p, pb->gm.w.p); }, s);
 }
 
 namespace {
@@ -490,11 +500,11 @@ void run_krylov(std::vector<KrylovJob *> &jobs) {
                 gm.start_cycle(pb->r.p, s);
                 jb->act = 1;
             } else if (jb->phase == 2) {
-                if (jb->graph_op) {
+                if (jb->graph) {
                     if (jb->precond) jb->precond(gm.basis(jb->j), pb->z1.p);
                     else PB_CUDA_TRY(cudaMemcpyAsync(pb->z1.p, gm.basis(jb->j), n2 * sizeof(double),
                                                      cudaMemcpyDeviceToDevice, s));
-                    launch_operator_graph(pb, s);
+                    jb->graph(s);
                 } else if (jb->precond) {
                     jb->precond(gm.basis(jb->j), pb->z1.p);
                     jb->op(pb->z1.p, gm.w.p);
@@ -603,7 +613,7 @@ void solve_many(const std::vector<pb_problem *> &probs, const std::vector<const 
         jb.b = pb->b.p;
         jb.x = pb->x.p;
         jb.x_zero = x0s[i] == nullptr;
-        jb.graph_op = true;
+        jb.graph = [pb](cudaStream_t gs) { launch_operator_graph(pb, gs); };
         jp[i] = &jb;
     }
     run_krylov(jp);

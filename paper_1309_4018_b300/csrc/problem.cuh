@@ -58,6 +58,8 @@ struct pb_problem {
     cudaEvent_t evf = nullptr, evj = nullptr; // fork and join of the side stream
     cudaGraphExec_t mv_exec = nullptr;        // captured operator application z1 -> gm.w
     long long mv_kernels = 0;                 // kernels in that graph
+    cudaGraphExec_t adj_exec = nullptr;       // captured transposed operator z1 -> gm.w (gradient)
+    long long adj_kernels = 0;
     std::vector<pb::Region> regions;
     std::vector<pb::SurfIn> sin;
     std::vector<double> cxyz, cq;
@@ -101,7 +103,8 @@ void reaction(pb_problem *pb, const double *xd);
 // jobs advance in lock step, each on its problem's stream: every round queues
 // one unit of work per job (a cycle start or one Arnoldi iteration) and the
 // host synchronises once per round to read the scalars it decides on.
-// graph_op: the Arnoldi operator is the problem's captured graph z1 -> gm.w.
+// graph: when set, the Arnoldi operator is a captured graph z1 -> gm.w launched
+// on the given stream (the preconditioned basis vector is first written to z1).
 struct KrylovStats {
     int iters = 0, matvecs = 0;
     double rel = 0.0;
@@ -113,7 +116,7 @@ struct KrylovJob {
     const double *b = nullptr;
     double *x = nullptr;
     bool x_zero = true;
-    bool graph_op = false;
+    std::function<void(cudaStream_t)> graph;
     KrylovStats st;
     // driver state
     int phase = 0, j = 0, act = 0;
@@ -124,5 +127,8 @@ KrylovStats run_gmres(pb_problem *pb, const DevOp &op, const DevOp &precond, con
                       bool x_zero);
 // Operator application as a replayable CUDA graph (captured on first use).
 void launch_operator_graph(pb_problem *pb, cudaStream_t s);
+// Captures `body` (work on pb->stream) into `exec` on first use, then launches it on s; nk counts its kernels.
+void launch_captured(pb_problem *pb, cudaGraphExec_t &exec, long long &nk, const std::function<void()> &body,
+                     cudaStream_t s);
 
 }  // namespace pb
