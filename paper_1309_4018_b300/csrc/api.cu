@@ -224,25 +224,28 @@ void setup_problem(pb_problem *pb) {
             P.dV32.alloc(std::max<int64_t>(1, (int64_t)nk * P.n_near));
             P.dK32.alloc(std::max<int64_t>(1, (int64_t)nk * P.n_near));
         }
+        if (mixed) near_values32(P, G, src, prm.K, prm.K_fine, P.dV32.p, P.dK32.p, s);
         for (size_t k = 0; k < nk; ++k) {
             P.VK[k].alloc(2 * std::max<int64_t>(1, G.n));
-            if (mixed) {
-                near_values32(P, G, src, prm.K, prm.K_fine, P.kappas[k], P.dV32.p + (int64_t)k * P.n_near,
-                              P.dK32.p + (int64_t)k * P.n_near, s);
-            } else {
+            if (!mixed) {
                 P.dV[k].alloc(std::max<int64_t>(1, P.n_near));
                 P.dK[k].alloc(std::max<int64_t>(1, P.n_near));
                 near_values(P, G, src, prm.K, prm.K_fine, P.kappas[k], P.dV[k].p, P.dK[k].p, s);
             }
             if (use_self) {
                 P.selfV[k].alloc(src.n);
-                self_integrals(src, prm.N_k, P.kappas[k], P.selfV[k].p, s);
+                if (nk == 2 && k == 1) {
+                    self_integrals2(src, prm.N_k, P.kappas[0], P.kappas[1], P.selfV[0].p, P.selfV[1].p, s);
+                } else if (nk == 1) {
+                    self_integrals(src, prm.N_k, P.kappas[k], P.selfV[k].p, s);
+                }
             }
-            if (P.p2p_self_in) {
+        }
+        if (P.p2p_self_in)
+            for (size_t k = 0; k < nk; ++k) {
                 P.selfV32[k].alloc(src.n);
                 self_minus_kpoint(src, prm.K, P.kappas[k], P.selfV[k].p, P.selfV32[k].p, s);
             }
-        }
     };
     for (auto &P : pb->pairs) prepare(P, false);
     for (auto &P : pb->cpairs) prepare(P, true);

@@ -140,11 +140,23 @@ __global__ void near_values_kernel(int64_t ntg, int64_t nnear, const double *__r
 
 // Mixed path: the same corrections in FP32, with positions taken relative to
 // the panel's first vertex (differences of nearby points stay exact enough).
+// FP32 copies of the rules (the FP64 constants converted once, not per point).
+struct TriRule32 {
+    int n;
+    float l1[19], l2[19], w[19];
+};
+__constant__ TriRule32 c_rules32[4];
+
+// V and K of one panel at xr (relative to its first vertex) for NK kernels at once:
+// the geometry of every rule point is shared by the kernels.
+template <int NK>
 __device__ void panel_rule_sums32(const float xr[3], const float e1[3], const float e2[3], const float nrm[3],
-                                  float area, const TriRule &R, float kappa, float &V, float &K) {
-    float sv = 0.f, sk = 0.f;
+                                  float area, const TriRule32 &R, const float *kappa, float *V, float *K) {
+    float sv[NK], sk[NK];
+#pragma unroll
+    for (int a = 0; a < NK; ++a) { sv[a] = 0.f; sk[a] = 0.f; }
     for (int k = 0; k < R.n; ++k) {
-        const float l1 = (float)R.l[k][1], l2 = (float)R.l[k][2];
+        const float l1 = R.l1[k], l2 = R.l2[k];
         const float rx = xr[0] - (l1 * e1[0] + l2 * e2[0]);
         const float ry = xr[1] - (l1 * e1[1] + l2 * e2[1]);
         const float rz = xr[2] - (l1 * e1[2] + l2 * e2[2]);
@@ -152,20 +164,29 @@ __device__ void panel_rule_sums32(const float xr[3], const float e1[3], const fl
         const float inv = rsqrtf(r2);
         const float rho = r2 * inv;
         const float rn = rx * nrm[0] + ry * nrm[1] + rz * nrm[2];
-        const float e = kappa == 0.f ? 1.f : __expf(-kappa * rho);
-        const float wa = (float)R.w[k] * area;
-        sv += wa * e * inv;
-        sk += wa * rn * (1.f + kappa * rho) * e * inv * inv * inv;
+        const float wa = R.w[k] * area;
+        const float wi = wa * inv, wk = wa * rn * inv * inv * inv;
+#pragma unroll
+        for (int a = 0; a < NK; ++a) {
+            const float e = kappa[a] == 0.f ? 1.f : __expf(-kappa[a] * rho);
+            sv[a] += wi * e;
+            sk[a] += wk * (1.f + kappa[a] * rho) * e;
+        }
     }
-    V = sv * (float)kInv4Pi;
-    K = sk * (float)kInv4Pi;
+#pragma unroll
+    for (int a = 0; a < NK; ++a) {
+        V[a] = sv[a] * (float)kInv4Pi;
+        K[a] = sk[a] * (float)kInv4Pi;
+    }
 }
 
+template <int NK>
 __global__ void near_values32_kernel(int64_t ntg, int64_t nnear, const double *__restrict__ xs,
                                      const int64_t *__restrict__ ptr, const int32_t *__restrict__ pan,
                                      const double *__restrict__ v, const int32_t *__restrict__ t,
                                      const double *__restrict__ nrm, const double *__restrict__ area, int slotK,
-                                     int slotF, float kappa, float *__restrict__ dV, float *__restrict__ dK) {
+                                     int slotF, float kap0, float kap1, float *__restrict__ dV,
+                                     float *__restrict__ dK) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nnear) return;
     int64_t lo = 0, hi = ntg;  // last i with ptr[i] <= e
@@ -183,11 +204,15 @@ __global__ void near_values32_kernel(int64_t ntg, int64_t nnear, const double *_
         e2[d] = (float)(v[3 * c + d] - v[3 * a + d]);
         nj[d] = (float)nrm[3 * j + d];
     }
-    float vf, kf, vk, kk;
-    panel_rule_sums32(xr, e1, e2, nj, (float)area[j], c_rules[slotF], kappa, vf, kf);
-    panel_rule_sums32(xr, e1, e2, nj, (float)area[j], c_rules[slotK], kappa, vk, kk);
-    dV[e] = vf - vk;
-    dK[e] = kf - kk;
+    const float kap[2] = {kap0, kap1};
+    float vf[NK], kf[NK], vk[NK], kk[NK];
+    panel_rule_sums32<NK>(xr, e1, e2, nj, (float)area[j], c_rules32[slotF], kap, vf, kf);
+    panel_rule_sums32<NK>(xr, e1, e2, nj, (float)area[j], c_rules32[slotK], kap, vk, kk);
+#pragma unroll
+    for (int a = 0; a < NK; ++a) {
+        dV[a * nnear + e] = vf[a] - vk[a];
+        dK[a * nnear + e] = kf[a] - kk[a];
+    }
 }
 
 // Semi-analytical single-layer self integral at the centroid (Zhu et al.
@@ -202,13 +227,19 @@ struct GL {
     double x[32], w[32];
 };
 
+// NK kernels at once (kappa[a], out[a]): the edge geometry and the hyperbolic
+// substitution are shared, only the radial function differs.
+template <int NK>
 __global__ void self_integral_kernel(int64_t n, const double *__restrict__ v, const int32_t *__restrict__ t,
-                                     const double *__restrict__ cen, GL gl, double kappa, double *__restrict__ out) {
+                                     const double *__restrict__ cen, GL gl, double kappa0, double kappa1,
+                                     double *__restrict__ out0, double *__restrict__ out1) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int idx[3] = {t[3 * i], t[3 * i + 1], t[3 * i + 2]};
     const double c[3] = {cen[3 * i], cen[3 * i + 1], cen[3 * i + 2]};
-    double total = 0.0;
+    const double kap[2] = {kappa0, kappa1};
+    double tot[NK];
+    for (int a = 0; a < NK; ++a) tot[a] = 0.0;
     for (int e = 0; e < 3; ++e) {
         const double *va = v + 3 * idx[e];
         const double *vb = v + 3 * idx[(e + 1) % 3];
@@ -228,11 +259,15 @@ __global__ void self_integral_kernel(int64_t n, const double *__restrict__ v, co
         for (int q = 0; q < gl.n; ++q) {
             const double ch = cosh(mid + half * gl.x[q]);
             const double rho = h * ch;
-            const double F = kappa == 0.0 ? rho : -expm1(-kappa * rho) / kappa;
-            total += gl.w[q] * half * F / ch;
+#pragma unroll
+            for (int a = 0; a < NK; ++a) {
+                const double F = kap[a] == 0.0 ? rho : -expm1(-kap[a] * rho) / kap[a];
+                tot[a] += gl.w[q] * half * F / ch;
+            }
         }
     }
-    out[i] = total * kInv4Pi;
+    out0[i] = tot[0] * kInv4Pi;
+    if (NK > 1) out1[i] = tot[NK - 1] * kInv4Pi;
 }
 
 // d V_ii / d kappa by the same rule: the radial integral of -exp(-kappa r) r dr
@@ -377,6 +412,16 @@ GL gauss_legendre(int n) {
 void upload_rules() {
     TriRule r[4] = {make_rule(1), make_rule(3), make_rule(7), make_rule(19)};
     PB_CUDA_TRY(cudaMemcpyToSymbol(c_rules, r, sizeof(r)));
+    TriRule32 r32[4] = {};
+    for (int q = 0; q < 4; ++q) {
+        r32[q].n = r[q].n;
+        for (int k = 0; k < r[q].n; ++k) {
+            r32[q].l1[k] = (float)r[q].l[k][1];
+            r32[q].l2[k] = (float)r[q].l[k][2];
+            r32[q].w[k] = (float)r[q].w[k];
+        }
+    }
+    PB_CUDA_TRY(cudaMemcpyToSymbol(c_rules32, r32, sizeof(r32)));
 }
 
 bool valid_rule(int K) { return K == 1 || K == 3 || K == 7 || K == 19; }
@@ -407,13 +452,19 @@ void near_values(const Pair &Pr, const Targets &G, const SurfDev &src, int K, in
     PB_LAUNCH_CHECK();
 }
 
-void near_values32(const Pair &Pr, const Targets &G, const SurfDev &src, int K, int K_fine, double kappa, float *dV,
-                   float *dK, cudaStream_t s) {
+void near_values32(const Pair &Pr, const Targets &G, const SurfDev &src, int K, int K_fine, float *dV, float *dK,
+                   cudaStream_t s) {
     if (G.n == 0 || Pr.n_near == 0) return;
-    near_values32_kernel<<<div_up(Pr.n_near, 128), 128, 0, s>>>(G.n, Pr.n_near, G.xs.p, Pr.near_ptr.p,
-                                                                 Pr.near_panel.p, src.verts.p, src.tris.p, src.nrm.p,
-                                                                 src.area.p, rule_slot(K), rule_slot(K_fine),
-                                                                 (float)kappa, dV, dK);
+    const int nk = (int)Pr.kappas.size();
+    const float k0 = (float)Pr.kappas[0], k1 = nk > 1 ? (float)Pr.kappas[1] : 0.f;
+    if (nk == 1)
+        near_values32_kernel<1><<<div_up(Pr.n_near, 128), 128, 0, s>>>(
+            G.n, Pr.n_near, G.xs.p, Pr.near_ptr.p, Pr.near_panel.p, src.verts.p, src.tris.p, src.nrm.p, src.area.p,
+            rule_slot(K), rule_slot(K_fine), k0, k1, dV, dK);
+    else
+        near_values32_kernel<2><<<div_up(Pr.n_near, 128), 128, 0, s>>>(
+            G.n, Pr.n_near, G.xs.p, Pr.near_ptr.p, Pr.near_panel.p, src.verts.p, src.tris.p, src.nrm.p, src.area.p,
+            rule_slot(K), rule_slot(K_fine), k0, k1, dV, dK);
     PB_LAUNCH_CHECK();
 }
 
@@ -444,7 +495,17 @@ void self_minus_kpoint(const SurfDev &S, int K, double kappa, const double *self
 void self_integrals(const SurfDev &S, int N_k, double kappa, double *out, cudaStream_t s) {
     if (N_k < 1 || N_k > 32) fail(PB_EINVAL, "N_k must be in 1..32");
     GL gl = gauss_legendre(N_k);
-    self_integral_kernel<<<div_up(S.n, 128), 128, 0, s>>>(S.n, S.verts.p, S.tris.p, S.cen.p, gl, kappa, out);
+    self_integral_kernel<1><<<div_up(S.n, 128), 128, 0, s>>>(S.n, S.verts.p, S.tris.p, S.cen.p, gl, kappa, 0.0, out,
+                                                             nullptr);
+    PB_LAUNCH_CHECK();
+}
+
+void self_integrals2(const SurfDev &S, int N_k, double kappa0, double kappa1, double *out0, double *out1,
+                     cudaStream_t s) {
+    if (N_k < 1 || N_k > 32) fail(PB_EINVAL, "N_k must be in 1..32");
+    GL gl = gauss_legendre(N_k);
+    self_integral_kernel<2><<<div_up(S.n, 128), 128, 0, s>>>(S.n, S.verts.p, S.tris.p, S.cen.p, gl, kappa0, kappa1,
+                                                             out0, out1);
     PB_LAUNCH_CHECK();
 }
 

@@ -22,10 +22,14 @@ void surface_geometry(SurfDev &S, int K, cudaStream_t s);
 void near_values(const Pair &Pr, const Targets &G, const SurfDev &src, int K, int K_fine, double kappa, double *dV,
                  double *dK, cudaStream_t s);
 // The same corrections evaluated in FP32 (mixed path).
-void near_values32(const Pair &Pr, const Targets &G, const SurfDev &src, int K, int K_fine, double kappa, float *dV,
-                   float *dK, cudaStream_t s);
+// FP32 near-singular corrections of every kernel of the pair (kernel k at offset k * n_near).
+void near_values32(const Pair &Pr, const Targets &G, const SurfDev &src, int K, int K_fine, float *dV, float *dK,
+                   cudaStream_t s);
 // Semi-analytical V_ii of every panel of S (input order).
 void self_integrals(const SurfDev &S, int N_k, double kappa, double *out, cudaStream_t s);
+// The same for two kernels in one pass (shared geometry).
+void self_integrals2(const SurfDev &S, int N_k, double kappa0, double kappa1, double *out0, double *out1,
+                     cudaStream_t s);
 // out = selfv - the own panel's K-point share of the direct sum at the centroid (1/4pi included);
 // valid for rules without a point at the centroid.
 void self_minus_kpoint(const SurfDev &S, int K, double kappa, const double *selfv, double *out, cudaStream_t s);

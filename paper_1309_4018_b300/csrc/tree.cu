@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(128) near_kernel(
     const int64_t *__restrict__ p2p_ptr, const int32_t *__restrict__ p2p_leafidx, const int32_t *__restrict__ leaf_node,
     const int64_t *__restrict__ start, const int64_t *__restrict__ count, const int32_t *__restrict__ perm,
     const int32_t *__restrict__ pids, const int32_t *__restrict__ point_leaf, const double *__restrict__ cen,
-    const double *__restrict__ L, const float4 *__restrict__ pan32, double ox, double oy, double oz, double thres,
+    const double *__restrict__ L, const float4 *__restrict__ ppan32, double ox, double oy, double oz, double thres,
     int32_t *__restrict__ ncount, int32_t *__restrict__ excl, int32_t *__restrict__ self_excl,
     const int64_t *__restrict__ near_ptr, int32_t *__restrict__ near_panel, const int64_t *__restrict__ m2p_ptr,
     const int32_t *__restrict__ m2p_node, const float4 *__restrict__ cen32, double reach, int32_t *__restrict__ rows,
@@ -433,11 +433,12 @@ __global__ void __launch_bounds__(128) near_kernel(
             bool acc = false, exc = false;
             int j = -1;
             if (q < q1) {
-                j = pids[q];
-                const float4 pc = pan32[j];
+                // the point's panel (centroid, near radius) in point order: one coalesced load
+                const float4 pc = ppan32[q];
                 const float dx = fx - pc.x, dy = fy - pc.y, dz = fz - pc.z;
                 const float d2 = dx * dx + dy * dy + dz * dz;
-                if (j != me && d2 < pc.w && is_near(x, y, z, cen, L, thres, j)) {
+                if (d2 < pc.w) j = pids[q];
+                if (d2 < pc.w && j != me && is_near(x, y, z, cen, L, thres, j)) {
                     const int k = perm[q] - j * K;
                     // handle panel j once, at its lowest-numbered point inside the direct leaves
                     bool first = true;
@@ -499,11 +500,10 @@ __global__ void __launch_bounds__(128) near_kernel(
                 const int64_t q = qb + lane;
                 bool exc = false;
                 if (q < q1) {
-                    const int j = pids[q];
-                    const float4 pc = pan32[j];
+                    const float4 pc = ppan32[q];
                     const float dx = fx - pc.x, dy = fy - pc.y, dz = fz - pc.z;
-                    if (perm[q] == j * K && j != me && dx * dx + dy * dy + dz * dz < pc.w &&
-                        is_near(x, y, z, cen, L, thres, j)) {
+                    const int j = dx * dx + dy * dy + dz * dz < pc.w ? pids[q] : -1;
+                    if (j >= 0 && perm[q] == j * K && j != me && is_near(x, y, z, cen, L, thres, j)) {
                         bool any = false;
                         for (int kk = 0; kk < K && !any; ++kk) any = in_sorted(lst, nl, point_leaf[j * K + kk]);
                         exc = !any;
@@ -534,6 +534,13 @@ __global__ void pan32_kernel(int64_t n, const double *__restrict__ cen, const do
     const double tl = thres * L[j];
     pan32[j] = make_float4((float)(cen[3 * j] - ox), (float)(cen[3 * j + 1] - oy), (float)(cen[3 * j + 2] - oz),
                            (float)(tl * tl * (1.0 + 1e-3) + 1e-3));
+}
+
+// The panel record of every source point, in the tree's point order.
+__global__ void point_pan32_kernel(int64_t npts, const int32_t *__restrict__ pids, const float4 *__restrict__ pan32,
+                                   float4 *__restrict__ ppan32) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < npts) ppan32[q] = pan32[pids[q]];
 }
 
 // max_j (thres L_j + max_v |v - c_j|) over the panels of a surface; the
@@ -882,6 +889,11 @@ void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &
     pan32_kernel<<<div_up(src.n, 256), 256, 0, s>>>(src.n, src.cen.p, src.L.p, prm.thres, T.origin[0], T.origin[1],
                                                      T.origin[2], pan32.p);
     PB_LAUNCH_CHECK();
+    TmpBuf<float4> ppan32(std::max<int64_t>(1, T.npts), s);
+    if (T.npts) {
+        point_pan32_kernel<<<div_up(T.npts, 256), 256, 0, s>>>(T.npts, T.pids.p, pan32.p, ppan32.p);
+        PB_LAUNCH_CHECK();
+    }
     PB_CUDA_TRY(cudaStreamSynchronize(s));
     double reach = 0.0;
     std::memcpy(&reach, &rbits, sizeof(reach));
@@ -893,7 +905,7 @@ void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &
         PB_CUDA_TRY(cudaMemsetAsync(ovf.p, 0, 4, s));
         near_kernel<2><<<div_up(m, 4), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
                                                     pleaf.p, T.leaf_node.p, T.start.p, T.count.p, T.perm.p, T.pids.p,
-                                                    T.point_leaf.p, src.cen.p, src.L.p, pan32.p, T.origin[0],
+                                                    T.point_leaf.p, src.cen.p, src.L.p, ppan32.p, T.origin[0],
                                                     T.origin[1], T.origin[2], prm.thres, nc.p, ex.p, se.p, nullptr,
                                                     nullptr, Pr.m2p_ptr.p, Pr.m2p_node.p, T.cen32.p, reach, rows.p,
                                                     ovf.p);
@@ -921,7 +933,7 @@ void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &
         // some target has more than kNearCap near panels: fill the CSR list in a second pass
         near_kernel<1><<<div_up(m, 4), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
                                                     pleaf.p, T.leaf_node.p, T.start.p, T.count.p, T.perm.p, T.pids.p,
-                                                    T.point_leaf.p, src.cen.p, src.L.p, pan32.p, T.origin[0],
+                                                    T.point_leaf.p, src.cen.p, src.L.p, ppan32.p, T.origin[0],
                                                     T.origin[1], T.origin[2], prm.thres, nullptr, nullptr, nullptr,
                                                     Pr.near_ptr.p, Pr.near_panel.p, Pr.m2p_ptr.p, Pr.m2p_node.p,
                                                     T.cen32.p, reach, nullptr, nullptr);
