@@ -72,3 +72,30 @@ def test_mixed_rhs_close_to_oracle():
     ref = OD._green(sd[0].cen[rows], np.asarray(d["charges"]["xyz"]), 0.0) @ d["charges"]["q"] / 4.0
     assert rel_l2(b[rows], ref) <= 1e-5
     assert np.all(b[n:] == 0.0)
+
+
+@pytest.mark.parametrize("P", [1, 3, 6, 8, 9])
+def test_mixed_treecode_matches_fp64_treecode(P):
+    # same tree, same lists, same truncation: the FP32 path (radial-form M2P for
+    # P <= 8, recurrences above) differs from the FP64 treecode only by FP32
+    # rounding (measured 2.3e-7 .. 2.7e-7; FP32 unit roundoff 6e-8 times a few
+    # for the sums' cancellation); bound 2e-6.
+    d = layered_sphere_problem(level=3, charges="both")
+    kw = dict(theta=0.5, P=P, ncrit=40)
+    x = np.random.default_rng(P).normal(size=2 * sum(s["tris"].shape[0] for s in d["surfaces"]))
+    y64 = problem(d, precision="fp64", **kw).apply(x)
+    y32 = problem(d, precision="mixed", **kw).apply(x)
+    assert rel_l2(y32, y64) <= 2e-6
+
+
+def test_mixed_protein_operator_matches_fp64_treecode():
+    # the 40k-panel protein of the benchmark, its default settings: measured
+    # 2.9e-6 (coordinates relative to the root centre reach 30 A, panels 0.6 A:
+    # the FP32 differences of the near terms lose more); bound 2e-5
+    from synth.configs import protein_problem
+    d = protein_problem()
+    kw = dict(theta=0.5, P=6, ncrit=300)
+    x = np.random.default_rng(0).normal(size=2 * d["surfaces"][0]["tris"].shape[0])
+    y64 = problem(d, precision="fp64", **kw).apply(x)
+    y32 = problem(d, precision="mixed", **kw).apply(x)
+    assert rel_l2(y32, y64) <= 2e-5
