@@ -102,3 +102,16 @@ def test_gradient_identities_protein():
     assert abs(q @ g["dq"] - 2 * r.dG_solv) <= 1e-4 * abs(r.dG_solv)
     assert abs(eps @ g["deps"] + r.dG_solv) <= 1e-4 * abs(r.dG_solv)
     assert np.all(np.isfinite(g["dxyz"])) and np.all(np.isfinite(g["dkappa"]))
+
+
+@pytest.mark.parametrize("P", [2, 6, 8])
+def test_mixed_transpose_matches_fp64_transpose(P):
+    # same trees and lists in both precisions: the FP32 transposed operator
+    # (radial-form M2P of the Laplace + Yukawa pairs) differs from the FP64 one
+    # by rounding only; bound 2e-6 as for the forward operator
+    d = layered_sphere_problem(level=3, charges="both")
+    kw = dict(theta=0.5, P=P, ncrit=40)
+    x = np.random.default_rng(P).normal(size=2 * sum(s["tris"].shape[0] for s in d["surfaces"]))
+    y64 = problem(d, precision="fp64", **kw).apply_transpose(x)
+    y32 = problem(d, precision="mixed", **kw).apply_transpose(x)
+    assert rel_l2(y32, y64) <= 2e-6
