@@ -1884,6 +1884,10 @@ void energy_gradient(pb_problem *pb, pb_grad *out) {
         launch_captured(pb, pb->adj_exec, pb->adj_kernels,
                         [pb] { apply_tpairs(pb, pb->adj->tp, pb->z1.p, pb->gm.w.p, true); }, gs);
     };
+    // a whole cycle's Arnoldi steps as one graph, the loop ended on the device
+    jb.cycle_op = [pb] { apply_tpairs(pb, pb->adj->tp, pb->z1.p, pb->gm.w.p, true); };
+    jb.cycle_exec = &pb->adj_cyc_exec;
+    jb.cycle_kernels = &pb->adj_cyc_kernels;
     std::vector<KrylovJob *> jobs{&jb};
     run_krylov(jobs);
     const KrylovStats st = jb.st;

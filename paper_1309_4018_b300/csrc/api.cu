@@ -25,6 +25,8 @@ std::atomic<long long> g_launches{0};
 pb_problem::~pb_problem() {
     if (mv_exec) cudaGraphExecDestroy(mv_exec);
     if (adj_exec) cudaGraphExecDestroy(adj_exec);
+    if (cyc_exec) cudaGraphExecDestroy(cyc_exec);
+    if (adj_cyc_exec) cudaGraphExecDestroy(adj_cyc_exec);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     if (evf) cudaEventDestroy(evf);
@@ -134,6 +136,11 @@ void setup_problem(pb_problem *pb) {
         cudaGraphExecDestroy(pb->adj_exec);
         pb->adj_exec = nullptr;
     }
+    for (cudaGraphExec_t *e : {&pb->cyc_exec, &pb->adj_cyc_exec})
+        if (*e) {
+            cudaGraphExecDestroy(*e);
+            *e = nullptr;
+        }
     upload_rules();
     upload_term_tables();
     // geometry, trees and pairs of a previous setup keep their device buffers
@@ -463,6 +470,50 @@ void sync_streams(const std::vector<KrylovJob *> &jobs, bool only_active) {
 
 }  // namespace
 
+// One GMRES cycle's Arnoldi loop as a graph: a WHILE node whose body takes
+// v_j (column j in the device state), applies the preconditioner and the
+// operator, runs the Arnoldi step and lets the control kernel end the loop.
+void build_cycle_graph(KrylovJob *jb) {
+    pb_problem *pb = jb->pb;
+    cudaStream_t cs = pb->stream;
+    Gmres &gm = pb->gm;
+    cudaGraph_t g = nullptr;
+    PB_CUDA_TRY(cudaGraphCreate(&g, 0));
+    struct GraphGuard {
+        cudaGraph_t &g;
+        ~GraphGuard() { if (g) cudaGraphDestroy(g); }
+    } guard{g};
+    cudaGraphConditionalHandle h;
+    PB_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    PB_CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    const long long k0 = g_launches.load();
+    PB_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+        if (jb->precond) {
+            gm.copy_basis(pb->z2.p, cs);
+            jb->precond(pb->z2.p, pb->z1.p);
+        } else {
+            gm.copy_basis(pb->z1.p, cs);
+        }
+        jb->cycle_op();
+        gm.arnoldi_step_dev(h, pb->prm.tol, cs);
+    } catch (...) {
+        cudaStreamEndCapture(cs, &body);
+        throw;
+    }
+    PB_CUDA_TRY(cudaStreamEndCapture(cs, &body));
+    *jb->cycle_kernels = g_launches.load() - k0;
+    g_launches.fetch_sub(*jb->cycle_kernels);   // captured, counted per executed step
+    PB_CUDA_TRY(cudaGraphInstantiate(jb->cycle_exec, g, 0));
+}
+
 void run_krylov(std::vector<KrylovJob *> &jobs) {
     for (KrylovJob *jb : jobs) {
         pb_problem *pb = jb->pb;
@@ -502,6 +553,12 @@ void run_krylov(std::vector<KrylovJob *> &jobs) {
                 jb->x_zero = false;
                 gm.start_cycle(pb->r.p, s);
                 jb->act = 1;
+            } else if (jb->phase == 2 && jb->cycle_exec) {
+                gm.set_cycle(pb->prm.max_iter - jb->st.iters, s);
+                if (!*jb->cycle_exec) build_cycle_graph(jb);
+                PB_CUDA_TRY(cudaGraphLaunch(*jb->cycle_exec, s));
+                gm.read_cycle_async(s);
+                jb->act = 3;
             } else if (jb->phase == 2) {
                 if (jb->graph) {
                     if (jb->precond) jb->precond(gm.basis(jb->j), pb->z1.p);
@@ -535,6 +592,22 @@ void run_krylov(std::vector<KrylovJob *> &jobs) {
                     jb->phase = 2;
                     jb->j = 0;
                 }
+            } else if (jb->act == 3) {
+                // the device ran the cycle's steps; the solution update follows
+                const int steps = (int)gm.host(3);
+                jb->st.iters += steps;
+                jb->st.matvecs += steps;
+                g_launches.fetch_add(*jb->cycle_kernels * steps);
+                if (steps > 0) {
+                    if (jb->precond) {
+                        basis_combination(gm, steps, pb->z1.p, s);
+                        jb->precond(pb->z1.p, pb->z2.p);
+                        axpby(1.0, jb->x, 1.0, pb->z2.p, jb->x, 2 * pb->N, s);
+                    } else {
+                        gm.update_solution(steps, jb->x, s);
+                    }
+                }
+                jb->phase = 1;
             } else if (jb->act == 2) {
                 ++jb->st.iters;
                 const int k = jb->j + 1;
@@ -617,6 +690,9 @@ void solve_many(const std::vector<pb_problem *> &probs, const std::vector<const 
         jb.x = pb->x.p;
         jb.x_zero = x0s[i] == nullptr;
         jb.graph = [pb](cudaStream_t gs) { launch_operator_graph(pb, gs); };
+        jb.cycle_op = [pb] { apply_operator(pb, pb->z1.p, pb->gm.w.p); };
+        jb.cycle_exec = &pb->cyc_exec;
+        jb.cycle_kernels = &pb->cyc_kernels;
         jp[i] = &jb;
     }
     run_krylov(jp);

@@ -111,6 +111,42 @@ __global__ void set_bnorm_kernel(GmresState *st, double bn) {
     if (threadIdx.x == 0) st->bnorm = bn;
 }
 
+__global__ void set_cycle_kernel(GmresState *st, int maxit) {
+    if (threadIdx.x != 0) return;
+    st->j = 0;
+    st->maxit = maxit;
+    st->steps = 0.0;
+}
+
+__global__ void copy_basis_kernel(const double *__restrict__ V, int64_t ld, const GmresState *st,
+                                  double *__restrict__ dst, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = V[(int64_t)st->j * ld + i];
+}
+
+// v_{j+1} = w / ||w|| for the device column j (one reciprocal per block).
+__global__ void scale_copy_next_kernel(const double *__restrict__ src, const double *__restrict__ num_sq,
+                                       double *__restrict__ V, int64_t ld, const GmresState *st, int64_t n) {
+    __shared__ double inv;
+    if (threadIdx.x == 0) {
+        const double d = sqrt(*num_sq);
+        inv = d > 0.0 ? 1.0 / d : 0.0;
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) V[(int64_t)(st->j + 1) * ld + i] = src[i] * inv;
+}
+
+// After step j: record the steps and either advance to column j + 1 or end the loop.
+__global__ void arnoldi_control_kernel(GmresState *st, cudaGraphConditionalHandle h, double tol) {
+    if (threadIdx.x != 0) return;
+    const int steps = st->j + 1;
+    st->steps = (double)steps;
+    const bool stop = !(st->res_est >= tol) || steps >= st->maxit || steps >= st->m;
+    if (!stop) st->j = steps;
+    cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
 __global__ void init_cycle_kernel(GmresState *st, const double *__restrict__ beta2) {
     if (threadIdx.x != 0) return;
     const double beta = sqrt(*beta2);
@@ -215,6 +251,15 @@ __device__ __forceinline__ bool arrive_last(unsigned *count) {
     return last;
 }
 
+// a.j < 0: the column is the device state's (device-driven loop).
+__device__ __forceinline__ ArnoldiArgs device_column(ArnoldiArgs a) {
+    if (a.j < 0) {
+        a.j = a.st->j;
+        a.nv = a.j + 1;
+    }
+    return a;
+}
+
 // Block partials of V[v] . w over the block's slice, for v < nv.  The FP64
 // pipe is narrow on this part, so the block reduction is arranged to issue
 // few FP64 instructions: every thread's partials go to shared memory, each
@@ -263,7 +308,8 @@ __device__ void finish_dots(const ArnoldiArgs &a, int nv, double *out) {
 }
 
 // h1 = V^T w
-__global__ void __launch_bounds__(kRedThreads) arnoldi_dots_kernel(ArnoldiArgs a) {
+__global__ void __launch_bounds__(kRedThreads) arnoldi_dots_kernel(ArnoldiArgs a0) {
+    const ArnoldiArgs a = device_column(a0);
     const int64_t per = (a.n + kRedBlocks - 1) / kRedBlocks;
     const int64_t lo = blockIdx.x * per, hi = min(a.n, lo + per);
     slice_dots(a, lo, hi);
@@ -274,7 +320,8 @@ __global__ void __launch_bounds__(kRedThreads) arnoldi_dots_kernel(ArnoldiArgs a
 }
 
 // w -= V h1, then h2 = V^T w (the block projects its own slice first)
-__global__ void __launch_bounds__(kRedThreads) arnoldi_project_dots_kernel(ArnoldiArgs a) {
+__global__ void __launch_bounds__(kRedThreads) arnoldi_project_dots_kernel(ArnoldiArgs a0) {
+    const ArnoldiArgs a = device_column(a0);
     const int64_t per = (a.n + kRedBlocks - 1) / kRedBlocks;
     const int64_t lo = blockIdx.x * per, hi = min(a.n, lo + per);
     for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) {
@@ -292,7 +339,8 @@ __global__ void __launch_bounds__(kRedThreads) arnoldi_project_dots_kernel(Arnol
 
 // w -= V h2; nrm2 = w . w; the last block also forms the Hessenberg column
 // h1 + h2 and applies the Givens rotations (residual estimate in st).
-__global__ void __launch_bounds__(kRedThreads) arnoldi_project_norm_kernel(ArnoldiArgs a) {
+__global__ void __launch_bounds__(kRedThreads) arnoldi_project_norm_kernel(ArnoldiArgs a0) {
+    const ArnoldiArgs a = device_column(a0);
     __shared__ double sm[kRedThreads / 32];
     const int64_t per = (a.n + kRedBlocks - 1) / kRedBlocks;
     const int64_t lo = blockIdx.x * per, hi = min(a.n, lo + per);
@@ -417,6 +465,46 @@ void Gmres::arnoldi_step(int j, cudaStream_t s) {
     scale_copy_kernel<<<div_up(n, 256), 256, 0, s>>>(w.p, scal.p + 1, V.p + (int64_t)(j + 1) * ld, n);
     PB_LAUNCH_CHECK();
     PB_CUDA_TRY(cudaMemcpyAsync(hs.p + 2, &st.p->res_est, sizeof(double), cudaMemcpyDeviceToHost, s));
+}
+
+void Gmres::set_cycle(int maxit, cudaStream_t s) {
+    set_cycle_kernel<<<1, 1, 0, s>>>(st.p, maxit);
+    PB_LAUNCH_CHECK();
+}
+
+void Gmres::copy_basis(double *dst, cudaStream_t s) {
+    copy_basis_kernel<<<div_up(n, 256), 256, 0, s>>>(V.p, ld, st.p, dst, n);
+    PB_LAUNCH_CHECK();
+}
+
+void Gmres::arnoldi_step_dev(cudaGraphConditionalHandle h, double tol, cudaStream_t s) {
+    ArnoldiArgs a;
+    a.V = V.p;
+    a.ld = ld;
+    a.n = n;
+    a.nv = 0;
+    a.w = w.p;
+    a.h1 = hcol.p;
+    a.h2 = h2.p;
+    a.nrm2 = scal.p + 1;
+    a.partial = partial.p;
+    a.count = count.p;
+    a.st = st.p;
+    a.j = -1;
+    arnoldi_dots_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(a);
+    PB_LAUNCH_CHECK();
+    arnoldi_project_dots_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(a);
+    PB_LAUNCH_CHECK();
+    arnoldi_project_norm_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(a);
+    PB_LAUNCH_CHECK();
+    scale_copy_next_kernel<<<div_up(n, 256), 256, 0, s>>>(w.p, scal.p + 1, V.p, ld, st.p, n);
+    PB_LAUNCH_CHECK();
+    arnoldi_control_kernel<<<1, 1, 0, s>>>(st.p, h, tol);
+    PB_LAUNCH_CHECK();
+}
+
+void Gmres::read_cycle_async(cudaStream_t s) {
+    PB_CUDA_TRY(cudaMemcpyAsync(hs.p + 2, &st.p->res_est, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
 }
 
 void Gmres::update_solution(int k, double *x, cudaStream_t s) {

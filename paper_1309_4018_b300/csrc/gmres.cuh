@@ -13,6 +13,8 @@ struct GmresState {
     int pad_;
     double *H, *cs, *sn, *g, *y;
     double bnorm, beta, hnext, res_est;
+    double steps;       // Arnoldi steps of the current cycle (device loop; next to res_est for one copy)
+    int j, maxit;       // device loop: current column, step limit of the cycle
 };
 
 // Every step only queues work on the stream; the scalars the host decides on
@@ -33,6 +35,16 @@ struct Gmres {
     void arnoldi_step(int j, cudaStream_t s);              // needs w = A v_j; hs[2] = residual estimate
     double host(int i) const { return hs.p[i]; }
     void update_solution(int k, double *x, cudaStream_t s);
+    // Device-driven Arnoldi loop (one GMRES cycle as a graph WHILE node): the
+    // column j lives in the device state.  set_cycle: j = 0, at most maxit
+    // steps.  copy_basis: dst = v_j.  arnoldi_step_dev: the step for w = A z
+    // (z from v_j), then the loop condition: continue while the residual
+    // estimate is >= tol, fewer than maxit steps and j + 1 < m.
+    void set_cycle(int maxit, cudaStream_t s);
+    void copy_basis(double *dst, cudaStream_t s);
+    void arnoldi_step_dev(cudaGraphConditionalHandle h, double tol, cudaStream_t s);
+    // hs[2] = residual estimate, hs[3] = steps of the cycle (copy queued after the loop)
+    void read_cycle_async(cudaStream_t s);
 };
 
 // Inverse 2x2 self blocks of one surface's panels: minv = 4 n doubles (m11, m12, m21, m22 per panel).

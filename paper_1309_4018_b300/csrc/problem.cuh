@@ -60,6 +60,10 @@ struct pb_problem {
     long long mv_kernels = 0;                 // kernels in that graph
     cudaGraphExec_t adj_exec = nullptr;       // captured transposed operator z1 -> gm.w (gradient)
     long long adj_kernels = 0;
+    cudaGraphExec_t cyc_exec = nullptr;       // one GMRES cycle's Arnoldi loop as a graph WHILE node (solve)
+    long long cyc_kernels = 0;                // kernels per step of that loop
+    cudaGraphExec_t adj_cyc_exec = nullptr;   // the same for the adjoint solve
+    long long adj_cyc_kernels = 0;
     std::vector<pb::Region> regions;
     std::vector<pb::SurfIn> sin;
     std::vector<double> cxyz, cq;
@@ -117,6 +121,12 @@ struct KrylovJob {
     double *x = nullptr;
     bool x_zero = true;
     std::function<void(cudaStream_t)> graph;
+    // cycle: when set, a whole cycle's Arnoldi steps run as one captured graph
+    // whose WHILE node the device ends (no host round trip per step); cycle_op
+    // enqueues the operator z1 -> gm.w on pb->stream for the capture.
+    std::function<void()> cycle_op;
+    cudaGraphExec_t *cycle_exec = nullptr;
+    long long *cycle_kernels = nullptr;
     KrylovStats st;
     // driver state
     int phase = 0, j = 0, act = 0;
