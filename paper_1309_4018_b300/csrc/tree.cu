@@ -326,6 +326,58 @@ __global__ void inv_fill_kernel(int64_t nent, const int32_t *__restrict__ owner,
     else map[e] = (int32_t)p;
 }
 
+// The same grouping with per-block histograms in shared memory (few keys):
+// every block counts its contiguous chunk of entries by key with shared
+// atomics, a per-key pass turns the block counts into each block's starting
+// offset, and every block then places its entries from those offsets.  The
+// global atomics of the kernels above, up to one per entry on a few thousand
+// popular keys, become shared ones.
+constexpr int kHistKeys = 12000;   // keys per shared-memory histogram (48 KB)
+
+__global__ void hist_count_kernel(int64_t nent, int64_t chunk, const int32_t *__restrict__ ent,
+                                  const int32_t *__restrict__ remap, int nkeys, int32_t *__restrict__ hb) {
+    extern __shared__ int32_t hist[];
+    for (int k = threadIdx.x; k < nkeys; k += blockDim.x) hist[k] = 0;
+    __syncthreads();
+    const int64_t e0 = (int64_t)blockIdx.x * chunk, e1 = min(nent, e0 + chunk);
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int key = remap ? remap[ent[e]] : ent[e];
+        atomicAdd(&hist[key], 1);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nkeys; k += blockDim.x) hb[(int64_t)blockIdx.x * nkeys + k] = hist[k];
+}
+
+// hb[b][k] <- sum_{b' < b} hb[b'][k] (each block's start within key k); cnt[k] = the total.
+__global__ void hist_scan_kernel(int nkeys, int nb, int32_t *__restrict__ hb, int32_t *__restrict__ cnt) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nkeys) return;
+    int32_t run = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int32_t c = hb[(int64_t)b * nkeys + k];
+        hb[(int64_t)b * nkeys + k] = run;
+        run += c;
+    }
+    cnt[k] = run;
+}
+
+__global__ void hist_fill_kernel(int64_t nent, int64_t chunk, const int32_t *__restrict__ owner,
+                                 const int32_t *__restrict__ ent, const int32_t *__restrict__ remap,
+                                 const int64_t *__restrict__ off, const int32_t *__restrict__ hb, int nkeys,
+                                 int by_entry, int32_t *__restrict__ inv, int32_t *__restrict__ map) {
+    extern __shared__ int32_t cur[];
+    for (int k = threadIdx.x; k < nkeys; k += blockDim.x) cur[k] = hb[(int64_t)blockIdx.x * nkeys + k];
+    __syncthreads();
+    const int64_t e0 = (int64_t)blockIdx.x * chunk, e1 = min(nent, e0 + chunk);
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int key = remap ? remap[ent[e]] : ent[e];
+        const int64_t p = off[key] + atomicAdd(&cur[key], 1);
+        inv[p] = owner[e];
+        if (by_entry) map[p] = (int32_t)e;
+        else map[e] = (int32_t)p;
+    }
+}
+
 __global__ void item_count_kernel(int nkeys, const int64_t *__restrict__ off, int per, int32_t *__restrict__ nitems) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nkeys) return;
@@ -823,16 +875,32 @@ void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &pr
         inv.alloc(std::max<int64_t>(1, nent));
         pos.alloc(std::max<int64_t>(1, nent));
         TmpBuf<int32_t> owner(std::max<int64_t>(1, nent), s);
+        const bool hist = nkeys <= kHistKeys && nent > 0;
+        const int nb = hist ? (int)std::min<int64_t>(296, div_up(nent, 2048)) : 0;
+        const int64_t chunk = hist ? (nent + nb - 1) / nb : 0;
+        TmpBuf<int32_t> hb(hist ? (size_t)nb * nkeys : 0, s);
+        const size_t hshm = (size_t)nkeys * sizeof(int32_t);
         if (m && nent) {
             owner_kernel<<<div_up(m, 128), 128, 0, s>>>(m, ptr, owner.p);
             PB_LAUNCH_CHECK();
-            inv_count_kernel<<<div_up(nent, 256), 256, 0, s>>>(nent, ent, remap, cnt.p);
-            PB_LAUNCH_CHECK();
+            if (hist) {
+                hist_count_kernel<<<nb, 256, hshm, s>>>(nent, chunk, ent, remap, nkeys, hb.p);
+                PB_LAUNCH_CHECK();
+                hist_scan_kernel<<<div_up(nkeys, 128), 128, 0, s>>>(nkeys, nb, hb.p, cnt.p);
+                PB_LAUNCH_CHECK();
+            } else {
+                inv_count_kernel<<<div_up(nent, 256), 256, 0, s>>>(nent, ent, remap, cnt.p);
+                PB_LAUNCH_CHECK();
+            }
         }
         exclusive_scan_i32_to_i64(cnt.p, off.p, nkeys, s);
         if (m && nent) {
-            inv_fill_kernel<<<div_up(nent, 256), 256, 0, s>>>(nent, owner.p, ent, remap, off.p, cursor.p, by_entry,
-                                                              inv.p, pos.p);
+            if (hist)
+                hist_fill_kernel<<<nb, 256, hshm, s>>>(nent, chunk, owner.p, ent, remap, off.p, hb.p, nkeys, by_entry,
+                                                       inv.p, pos.p);
+            else
+                inv_fill_kernel<<<div_up(nent, 256), 256, 0, s>>>(nent, owner.p, ent, remap, off.p, cursor.p, by_entry,
+                                                                  inv.p, pos.p);
             PB_LAUNCH_CHECK();
         }
         item_count_kernel<<<div_up(nkeys, 128), 128, 0, s>>>(nkeys, off.p, per, nit.p);
