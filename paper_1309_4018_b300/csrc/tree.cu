@@ -224,9 +224,15 @@ __global__ void traverse_kernel(int64_t ntg, const double *__restrict__ xs, cons
                                 int32_t *__restrict__ m2p_cnt, int32_t *__restrict__ p2p_cnt,
                                 const int64_t *__restrict__ m2p_ptr, const int64_t *__restrict__ p2p_ptr,
                                 int32_t *__restrict__ m2p_node, int32_t *__restrict__ p2p_node,
-                                int32_t *__restrict__ err) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ntg) return;
+                                int32_t *__restrict__ err, int nsplit) {
+    // nsplit > 1: thread (i, c) traverses only the subtree of the root's child c
+    // (the root itself, when accepted or a leaf, belongs to c = 0); counts and
+    // offsets are per (i, c), and a target's list is their concatenation in c
+    // order, which is its depth-first pre-order.
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= ntg * nsplit) return;
+    const int64_t i = tid / nsplit;
+    const int csub = nsplit > 1 ? (int)(tid % nsplit) : -1;
     const double x = xs[3 * i], y = xs[3 * i + 1], z = xs[3 * i + 2];
     const float fx = (float)(x - ox), fy = (float)(y - oy), fz = (float)(z - oz);
     const float th2f = (float)theta2;
@@ -236,7 +242,7 @@ __global__ void traverse_kernel(int64_t ntg, const double *__restrict__ xs, cons
     int sp = 0;
     stack[sp++] = 0;
     int nm = 0, np = 0;
-    int64_t mo = FILL ? m2p_ptr[i] : 0, po = FILL ? p2p_ptr[i] : 0;
+    int64_t mo = FILL ? m2p_ptr[tid] : 0, po = FILL ? p2p_ptr[tid] : 0;
     while (sp > 0) {
         const int b = stack[--sp];
         bool accept = false;
@@ -263,19 +269,32 @@ __global__ void traverse_kernel(int64_t ntg, const double *__restrict__ xs, cons
                 accept = dec == 1;
             }
         }
+        const bool mine = b != 0 || csub <= 0;   // the root's own entry goes to c = 0
         if (accept) {
-            if (FILL) m2p_node[mo + nm] = b;
-            ++nm;
+            if (mine) {
+                if (FILL) m2p_node[mo + nm] = b;
+                ++nm;
+            }
         } else if (nchild[b] == 0) {
-            if (FILL) p2p_node[po + np] = b;
-            ++np;
+            if (mine) {
+                if (FILL) p2p_node[po + np] = b;
+                ++np;
+            }
+        } else if (b == 0 && csub >= 0) {
+            if (csub < nchild[0]) stack[sp++] = first_child[0] + csub;
         } else {
             const int fc = first_child[b], nc = nchild[b];
             if (sp + nc > kStack) { atomicExch(err, 1); return; }
             for (int c = fc + nc - 1; c >= fc; --c) stack[sp++] = c;
         }
     }
-    if (!FILL) { m2p_cnt[i] = nm; p2p_cnt[i] = np; }
+    if (!FILL) { m2p_cnt[tid] = nm; p2p_cnt[tid] = np; }
+}
+
+// ptr[i] = off[i * nsplit], i = 0 .. m (per-target offsets from per-(target, subtree) ones).
+__global__ void take_every_kernel(int64_t m, int nsplit, const int64_t *__restrict__ off, int64_t *__restrict__ ptr) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= m) ptr[i] = off[i * nsplit];
 }
 
 // ---------------------------------------------------------------- entry-major grouping
@@ -819,31 +838,46 @@ void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, 
 
 void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &prm, cudaStream_t s, int p2p_per_item) {
     const int64_t m = G.n;
-    TmpBuf<int32_t> mc(m, s), pc(m, s), err(1, s);
+    // small target sets (the charges) traverse the root's eight subtrees in parallel
+    const int nsplit = m < 8192 ? 8 : 1;
+    const int64_t ms = m * nsplit;
+    TmpBuf<int32_t> mc(ms, s), pc(ms, s), err(1, s);
+    TmpBuf<int64_t> mo(nsplit > 1 ? ms + 1 : 0, s), po(nsplit > 1 ? ms + 1 : 0, s);
     PB_CUDA_TRY(cudaMemsetAsync(err.p, 0, 4, s));
     const double theta2 = prm.theta * prm.theta;
     const int direct = prm.theta <= 0.0;
     Pr.m2p_ptr.alloc(m + 1);
     Pr.p2p_ptr.alloc(m + 1);
     if (m) {
-        traverse_kernel<false><<<div_up(m, 128), 128, 0, s>>>(m, G.xs.p, T.centre.p, T.rb2.p, T.cen32.p,
-                                                              T.first_child.p, T.nchild.p, theta2, direct, T.origin[0],
-                                                              T.origin[1], T.origin[2], mc.p, pc.p, nullptr, nullptr,
-                                                              nullptr, nullptr, err.p);
+        traverse_kernel<false><<<div_up(ms, 128), 128, 0, s>>>(m, G.xs.p, T.centre.p, T.rb2.p, T.cen32.p,
+                                                               T.first_child.p, T.nchild.p, theta2, direct, T.origin[0],
+                                                               T.origin[1], T.origin[2], mc.p, pc.p, nullptr, nullptr,
+                                                               nullptr, nullptr, err.p, nsplit);
         PB_LAUNCH_CHECK();
     }
-    exclusive_scan_i32_to_i64(mc.p, Pr.m2p_ptr.p, m, s);
-    exclusive_scan_i32_to_i64(pc.p, Pr.p2p_ptr.p, m, s);
+    int64_t *moff = Pr.m2p_ptr.p, *poff = Pr.p2p_ptr.p;
+    if (nsplit > 1) {
+        exclusive_scan_i32_to_i64(mc.p, mo.p, ms, s);
+        exclusive_scan_i32_to_i64(pc.p, po.p, ms, s);
+        take_every_kernel<<<div_up(m + 1, 256), 256, 0, s>>>(m, nsplit, mo.p, Pr.m2p_ptr.p);
+        PB_LAUNCH_CHECK();
+        take_every_kernel<<<div_up(m + 1, 256), 256, 0, s>>>(m, nsplit, po.p, Pr.p2p_ptr.p);
+        PB_LAUNCH_CHECK();
+        moff = mo.p;
+        poff = po.p;
+    } else {
+        exclusive_scan_i32_to_i64(mc.p, Pr.m2p_ptr.p, m, s);
+        exclusive_scan_i32_to_i64(pc.p, Pr.p2p_ptr.p, m, s);
+    }
     Pr.n_m2p = read_i64(Pr.m2p_ptr.p + m, s);
     Pr.n_p2p = read_i64(Pr.p2p_ptr.p + m, s);
     Pr.m2p_node.alloc(std::max<int64_t>(1, Pr.n_m2p));
     Pr.p2p_node.alloc(std::max<int64_t>(1, Pr.n_p2p));
     if (m) {
-        traverse_kernel<true><<<div_up(m, 128), 128, 0, s>>>(m, G.xs.p, T.centre.p, T.rb2.p, T.cen32.p,
-                                                             T.first_child.p, T.nchild.p, theta2, direct, T.origin[0],
-                                                             T.origin[1], T.origin[2], nullptr, nullptr,
-                                                             Pr.m2p_ptr.p, Pr.p2p_ptr.p, Pr.m2p_node.p, Pr.p2p_node.p,
-                                                             err.p);
+        traverse_kernel<true><<<div_up(ms, 128), 128, 0, s>>>(m, G.xs.p, T.centre.p, T.rb2.p, T.cen32.p,
+                                                              T.first_child.p, T.nchild.p, theta2, direct, T.origin[0],
+                                                              T.origin[1], T.origin[2], nullptr, nullptr, moff, poff,
+                                                              Pr.m2p_node.p, Pr.p2p_node.p, err.p, nsplit);
         PB_LAUNCH_CHECK();
     }
     int herr = 0;
