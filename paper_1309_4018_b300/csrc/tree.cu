@@ -838,8 +838,9 @@ void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, 
 
 void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &prm, cudaStream_t s, int p2p_per_item) {
     const int64_t m = G.n;
-    // small target sets (the charges) traverse the root's eight subtrees in parallel
-    const int nsplit = m < 8192 ? 8 : 1;
+    // every target traverses the root's eight subtrees as eight threads (eight times
+    // the parallelism for the charges, shorter serial walks for the panels)
+    const int nsplit = 8;
     const int64_t ms = m * nsplit;
     TmpBuf<int32_t> mc(ms, s), pc(ms, s), err(1, s);
     TmpBuf<int64_t> mo(nsplit > 1 ? ms + 1 : 0, s), po(nsplit > 1 ? ms + 1 : 0, s);
