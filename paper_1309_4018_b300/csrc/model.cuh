@@ -58,6 +58,7 @@ struct Tree {
     DevBuf<double> src64;            // npts * 8: x, y, z, s, dx, dy, dz, pid
     DevBuf<float4> srcA32, srcB32;   // (x, y, z, s) and (dx, dy, dz, pid bits)
     DevBuf<float2> phf;              // (phi, dphi) per panel in FP32 (mixed path)
+    DevBuf<int4> link;               // per node: (parent, parent's first child, parent's child count, 0)
     DevBuf<int32_t> ucnt;            // per node: children finished in the fused upward pass (0 between passes)
     DevBuf<double> mom64;            // nnodes * 2 * nterms: M then D
     DevBuf<float> mom32;

@@ -154,6 +154,16 @@ __global__ void node_geom_kernel(int nnodes, const int32_t *__restrict__ level, 
     rb2[b] = __dmul_rn(__dmul_rn(sl, sl), 0.75);
 }
 
+// Per node: (parent, the parent's first child, the parent's child count, 0);
+// (-1, 0, 0, 0) at the root.  One record per level of the upward climb.
+__global__ void link_kernel(int nnodes, const int32_t *__restrict__ parent, const int32_t *__restrict__ first_child,
+                            const int32_t *__restrict__ nchild, int4 *__restrict__ link) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nnodes) return;
+    const int p = parent[i];
+    link[i] = p >= 0 ? make_int4(p, first_child[p], nchild[p], 0) : make_int4(-1, 0, 0, 0);
+}
+
 __global__ void centre32_kernel(int nnodes, const double *__restrict__ centre, const double *__restrict__ rb2,
                                 double ox, double oy, double oz, float4 *__restrict__ cen32) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -787,6 +797,9 @@ void build_tree_points(Tree &T, const double *pts, const double *wts, int64_t n,
     T.rb2.alloc(T.nnodes);
     node_geom_kernel<<<div_up(T.nnodes, 128), 128, 0, s>>>(T.nnodes, T.level.p, ijk.p, T.corner[0], T.corner[1],
                                                            T.corner[2], T.side, T.centre.p, T.rb2.p);
+    PB_LAUNCH_CHECK();
+    T.link.alloc(T.nnodes);
+    link_kernel<<<div_up(T.nnodes, 128), 128, 0, s>>>(T.nnodes, T.parent.p, T.first_child.p, T.nchild.p, T.link.p);
     PB_LAUNCH_CHECK();
     T.cen32.alloc(T.nnodes);
     centre32_kernel<<<div_up(T.nnodes, 128), 128, 0, s>>>(T.nnodes, T.centre.p, T.rb2.p, T.origin[0], T.origin[1],

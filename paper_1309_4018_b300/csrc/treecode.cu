@@ -35,6 +35,7 @@ namespace {
 __constant__ int c_terms[3 * kMaxTerms1];   // (k1, k2, k3) of every term up to order kMaxP + 1, graded order
 __constant__ double c_binom[13][13];
 
+
 __host__ __device__ constexpr int term_index(int k1, int k2, int k3) {
     // graded by n = |k|, then k1 descending, then k2 descending
     return (k1 + k2 + k3) * (k1 + k2 + k3 + 1) * (k1 + k2 + k3 + 2) / 6 + (k2 + k3) * (k2 + k3 + 1) / 2 + k3;
@@ -133,6 +134,70 @@ __device__ __forceinline__ Quad<double> ld4(const double *p) {
 constexpr size_t kClimbMaxShared = 220 * 1024;   // dynamic shared memory of the one-launch M2M (227 KB less the static arrays)
 constexpr int kM2MMaxShared = 2 * 8 * 2 * 455 * 8 + 3 * 455 * 4;
 
+// Shift the children's moments (src: 8 x nval, child-major, nval = sets x NT;
+// the rows of absent children zero) to the parent's centre and add them in
+// child order into out[0, nval).  hs[c][ax] = (child c - parent)_ax, sbin =
+// binomials.  Each thread owns outputs r (one term k of one set) and, per
+// pass, walks the inputs of k along the axis once for all eight children:
+// e = 0 .. k_ax with l = k_ax - e, coefficient C(k_ax, l) h^e, the power
+// h^e carried in a register (1, h, h h, ... as a running product) and the
+// input's index stepped down from k by additions.  No per-child branch, so
+// the eight loads of an input are issued together; the last pass adds the
+// children's shifted values and stores the sum.  Two barriers; src and dst
+// are overwritten.
+template <typename T>
+__device__ __forceinline__ void shift_children(int NT, int nval, const int *__restrict__ sterm,
+                                               const T (*sbin)[kMaxP + 1], const T (*hs)[3], T *src, T *dst,
+                                               T *__restrict__ out) {
+#pragma unroll
+    for (int ax = 2; ax >= 0; --ax) {
+        T hh[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) hh[c] = hs[c][ax];
+        for (int r = threadIdx.x; r < nval; r += blockDim.x) {
+            const int set = r / NT, k = r - set * NT;
+            const int k1 = sterm[3 * k], k2 = sterm[3 * k + 1], k3 = sterm[3 * k + 2];
+            const int kax = ax == 0 ? k1 : ax == 1 ? k2 : k3;
+            // index of k with k_ax = l: T3(n0 + l) + T2(m0 + dm l) + c0 + dc l
+            // (T3(n) = n(n+1)(n+2)/6, T2(m) = m(m+1)/2), equal to k at l = k_ax
+            const int n = k1 + k2 + k3, n0 = n - kax, m = k2 + k3;
+            const int dm = ax == 0 ? 0 : 1, dc = ax == 2 ? 1 : 0;
+            int t3 = n * (n + 1) * (n + 2) / 6, w3 = n * (n + 1) / 2;
+            int t2 = m * (m + 1) / 2, w2 = m, cc = k3;
+            const T *sc = src + set * NT;
+            T acc[8], v[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) { acc[c] = 0; v[c] = 1; }
+            for (int e = 0; e <= kax; ++e) {
+                const int l = kax - e;
+                const int li = t3 + t2 + cc;
+                t3 -= w3; w3 -= n0 + l;
+                t2 -= dm * w2; w2 -= dm;
+                cc -= dc;
+                const T b = sbin[kax][l];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    acc[c] += b * v[c] * sc[c * nval + li];
+                    v[c] *= hh[c];
+                }
+            }
+            if (ax > 0) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) dst[c * nval + r] = acc[c];
+            } else {
+                T sum = 0;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) sum += acc[c];
+                out[r] = sum;
+            }
+        }
+        if (ax > 0) {
+            __syncthreads();
+            T *tmp = src; src = dst; dst = tmp;
+        }
+    }
+}
+
 // Each node holds `stride` values; one launch shifts the 2 NT values at
 // offset `base` (one (M, D) or two monopole sets).
 template <typename T>
@@ -144,51 +209,27 @@ __global__ void __launch_bounds__(256) m2m_kernel(int nodes_begin, const int32_t
     T *buf0 = reinterpret_cast<T *>(m2m_smem);          // nc x 2NT
     T *buf1 = buf0 + 8 * 2 * NT;                        // nc x 2NT
     int *sterm = reinterpret_cast<int *>(buf1 + 8 * 2 * NT);
-    __shared__ T hp[8][3][kMaxP + 1];
+    __shared__ T hs[8][3];
     __shared__ T sbin[kMaxP + 1][kMaxP + 1];
     const int b = nodes_begin + blockIdx.x;
     const int nc = nchild[b];
     if (nc == 0) return;
     const int fc = first_child[b];
-    for (int i = threadIdx.x; i < nc * 2 * NT; i += blockDim.x) {
+    for (int i = threadIdx.x; i < 8 * 2 * NT; i += blockDim.x) {
         const int c = i / (2 * NT), r = i - c * 2 * NT;
-        buf0[i] = mom[(int64_t)(fc + c) * stride + base + r];
+        buf0[i] = c < nc ? mom[(int64_t)(fc + c) * stride + base + r] : T(0);
     }
     for (int i = threadIdx.x; i < 3 * NT; i += blockDim.x) sterm[i] = c_terms[i];
-    for (int i = threadIdx.x; i < nc * 3; i += blockDim.x) {
+    for (int i = threadIdx.x; i < 8 * 3; i += blockDim.x) {
         const int c = i / 3, ax = i - 3 * c;
-        const T h = (T)(centre[3 * (fc + c) + ax] - centre[3 * b + ax]);
-        T v = 1;
-        for (int e = 0; e <= P; ++e) { hp[c][ax][e] = v; v *= h; }
+        hs[c][ax] = c < nc ? (T)(centre[3 * (fc + c) + ax] - centre[3 * b + ax]) : T(0);
     }
     for (int i = threadIdx.x; i < (P + 1) * (P + 1); i += blockDim.x) {
         const int n = i / (P + 1), k = i - n * (P + 1);
         sbin[n][k] = (T)c_binom[n][k];
     }
     __syncthreads();
-    T *src = buf0, *dst = buf1;
-    for (int ax = 2; ax >= 0; --ax) {
-        for (int idx = threadIdx.x; idx < nc * 2 * NT; idx += blockDim.x) {
-            const int c = idx / (2 * NT), r = idx - c * 2 * NT;
-            const int half = r >= NT ? NT : 0, k = r - half;
-            int kk[3] = {sterm[3 * k], sterm[3 * k + 1], sterm[3 * k + 2]};
-            const int kax = kk[ax];
-            const T *sc = src + c * 2 * NT + half;
-            T acc = 0;
-            for (int l = 0; l <= kax; ++l) {
-                kk[ax] = l;
-                acc += sbin[kax][l] * hp[c][ax][kax - l] * sc[term_index(kk[0], kk[1], kk[2])];
-            }
-            dst[idx] = acc;
-        }
-        __syncthreads();
-        T *tmp = src; src = dst; dst = tmp;
-    }
-    for (int r = threadIdx.x; r < 2 * NT; r += blockDim.x) {
-        T acc = 0;
-        for (int c = 0; c < nc; ++c) acc += src[c * 2 * NT + r];
-        mom[(int64_t)b * stride + base + r] = acc;
-    }
+    shift_children<T>(NT, 2 * NT, sterm, sbin, hs, buf0, buf1, mom + (int64_t)b * stride + base);
 }
 
 // ---------------------------------------------------------------- P2P, FP32 (mixed precision)
@@ -862,71 +903,66 @@ void launch_m2p_typed(int P, bool yuk, const Pair &Pr, const double *xs, const d
 template <typename T>
 __device__ __forceinline__ T ld_cg(const T *p) { return __ldcg(p); }
 
-// Climb from `node` (whose moments are complete) towards the root: after each
-// node the block announces it to the parent (a fence, then an atomic count);
-// the block that brings a parent's count to its number of children shifts the
-// children's moments into it (three one-axis passes in shared memory, children
-// added in child order) and continues from there.  Every node holds `nval`
-// values: nval / NT sets of NT moments, each shifted by the same rule.  No
-// block waits for another.  buf0, buf1: 8 * nval values each.
+// Climb from a node whose moments are complete towards the root: after each
+// node the block announces it to the parent (a barrier, a fence by thread 0,
+// then an atomic count); the block that brings a parent's count to its number
+// of children shifts the children's moments into it (three one-axis passes in
+// shared memory, children added in child order) and continues from there.
+// Every node holds `nval` values: nval / NT sets of NT moments, each shifted
+// by the same rule.  No block waits for another.  link[i] = (parent, the
+// parent's first child, the parent's child count, 0), (-1, 0, 0, 0) at the
+// root; `up` = the starting node's record, read by thread 0 ahead of time (as is each next
+// level's record), so a level costs the fence, the atomic and one round of
+// loads.  buf0, buf1: 8 * nval values each.
 template <typename T>
-__device__ void climb_m2m(int node, int P, int NT, int nval, const double *__restrict__ centre,
-                          const int32_t *__restrict__ first_child, const int32_t *__restrict__ nchild,
-                          const int32_t *__restrict__ parent, int32_t *__restrict__ ucnt, T *__restrict__ mom,
-                          T *buf0, T *buf1, T (*hp)[3][kMaxP + 1], T (*sbin)[kMaxP + 1], const int *sterm,
-                          int &s_next) {
+__device__ void climb_m2m(int4 up, int NT, int nval, const double *__restrict__ centre,
+                          const int4 *__restrict__ link, int32_t *__restrict__ ucnt, T *__restrict__ mom, T *buf0,
+                          T *buf1, T (*hs)[3], T (*sbin)[kMaxP + 1], const int *sterm, int4 &s_next) {
     while (true) {
-        __threadfence();   // every thread's moment stores before the announcement
-        __syncthreads();
+        __syncthreads();   // the block's moment stores of `node` are issued
         if (threadIdx.x == 0) {
-            const int par = parent[node];
-            int next = -1;
-            if (par >= 0 && atomicAdd(&ucnt[par], 1) == nchild[par] - 1) {
-                next = par;
-                ucnt[par] = 0;
-            }
-            s_next = next;
-        }
-        __syncthreads();
-        const int b = s_next;
-        if (b < 0) return;
-        __threadfence();
-        const int nc = nchild[b], fc = first_child[b];
-        for (int i = threadIdx.x; i < nc * nval; i += blockDim.x) {
-            const int c = i / nval, r = i - c * nval;
-            buf0[i] = ld_cg(mom + (int64_t)(fc + c) * nval + r);
-        }
-        for (int i = threadIdx.x; i < nc * 3; i += blockDim.x) {
-            const int c = i / 3, ax = i - 3 * c;
-            const T h = (T)(centre[3 * (fc + c) + ax] - centre[3 * b + ax]);
-            T v = 1;
-            for (int e = 0; e <= P; ++e) { hp[c][ax][e] = v; v *= h; }
-        }
-        __syncthreads();
-        T *src = buf0, *dst = buf1;
-        for (int ax = 2; ax >= 0; --ax) {
-            for (int idx = threadIdx.x; idx < nc * nval; idx += blockDim.x) {
-                const int c = idx / nval, r = idx - c * nval;
-                const int set = r / NT, k = r - set * NT;
-                int kx[3] = {sterm[3 * k], sterm[3 * k + 1], sterm[3 * k + 2]};
-                const int kax = kx[ax];
-                const T *sc = src + c * nval + set * NT;
-                T acc = 0;
-                for (int l = 0; l <= kax; ++l) {
-                    kx[ax] = l;
-                    acc += sbin[kax][l] * hp[c][ax][kax - l] * sc[term_index(kx[0], kx[1], kx[2])];
+            int4 nx = make_int4(-1, 0, 0, 0);
+            if (up.x >= 0) {
+                __threadfence();   // cumulative over the barrier: the block's stores before the announcement
+                if (atomicAdd(&ucnt[up.x], 1) == up.z - 1) {
+                    ucnt[up.x] = 0;
+                    __threadfence();   // the siblings' stores before this block's reads
+                    nx = up;
+                    up = link[up.x];   // consumed one level up
                 }
-                dst[idx] = acc;
             }
-            __syncthreads();
-            T *tmp = src; src = dst; dst = tmp;
+            s_next = nx;
         }
-        for (int r = threadIdx.x; r < nval; r += blockDim.x) {
-            T acc = 0;
-            for (int c = 0; c < nc; ++c) acc += src[c * nval + r];
-            mom[(int64_t)b * nval + r] = acc;
+        __syncthreads();
+        const int4 nx = s_next;
+        const int b = nx.x;
+        if (b < 0) return;
+        const int fc = nx.y, nc = nx.z;
+        // the centre offsets are loaded first so that their latency overlaps the moments'
+        T h = 0;
+        const int hc = threadIdx.x / 3, hax = threadIdx.x - 3 * hc;
+        if (threadIdx.x < 3 * nc) h = (T)(centre[3 * (fc + hc) + hax] - centre[3 * b + hax]);
+        // absent children: zero rows (and zero offsets)
+        for (int i = nc * nval + threadIdx.x; i < 8 * nval; i += blockDim.x) buf0[i] = 0;
+        // the children are consecutive nodes; eight loads per thread in flight at once
+        const T *cm = mom + (int64_t)fc * nval;
+        const int tot = nc * nval;
+        for (int i0 = threadIdx.x; i0 < tot; i0 += 8 * blockDim.x) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * blockDim.x;
+                v[u] = i < tot ? ld_cg(cm + i) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * blockDim.x;
+                if (i < tot) buf0[i] = v[u];
+            }
         }
-        node = b;
+        if (threadIdx.x < 24) hs[hc][hax] = h;
+        __syncthreads();
+        shift_children<T>(NT, nval, sterm, sbin, hs, buf0, buf1, mom + (int64_t)b * nval);
     }
 }
 
@@ -935,23 +971,23 @@ __device__ void climb_m2m(int node, int P, int NT, int nval, const double *__res
 template <typename T>
 __global__ void __launch_bounds__(256) climb_kernel(int nleaves, const int32_t *__restrict__ leaf_node,
                                                     const double *__restrict__ centre, int P, int NT, int nval,
-                                                    const int32_t *__restrict__ first_child,
-                                                    const int32_t *__restrict__ nchild,
-                                                    const int32_t *__restrict__ parent, int32_t *__restrict__ ucnt,
+                                                    const int4 *__restrict__ link, int32_t *__restrict__ ucnt,
                                                     T *__restrict__ mom) {
     extern __shared__ __align__(16) unsigned char up_smem[];
     int *sterm = reinterpret_cast<int *>(up_smem);
     T *region = reinterpret_cast<T *>(up_smem + ((3 * 455 * sizeof(int) + 31) / 32) * 32);
-    __shared__ T hp[8][3][kMaxP + 1];
+    __shared__ T hs[8][3];
     __shared__ T sbin[kMaxP + 1][kMaxP + 1];
-    __shared__ int s_next;
+    __shared__ int4 s_next;
+    const int node = leaf_node[blockIdx.x];
+    int4 up = make_int4(-1, 0, 0, 0);
+    if (threadIdx.x == 0) up = link[node];
     for (int i = threadIdx.x; i < 3 * NT; i += blockDim.x) sterm[i] = c_terms[i];
     for (int i = threadIdx.x; i < (P + 1) * (P + 1); i += blockDim.x) {
         const int n = i / (P + 1), k = i - n * (P + 1);
         sbin[n][k] = (T)c_binom[n][k];
     }
-    climb_m2m<T>(leaf_node[blockIdx.x], P, NT, nval, centre, first_child, nchild, parent, ucnt, mom, region,
-                 region + 8 * nval, hp, sbin, sterm, s_next);
+    climb_m2m<T>(up, NT, nval, centre, link, ucnt, mom, region, region + 8 * nval, hs, sbin, sterm, s_next);
 }
 
 template <typename T>
@@ -960,17 +996,15 @@ __global__ void __launch_bounds__(256) upward_kernel(int nleaves, const int32_t 
                                                      const int64_t *__restrict__ count,
                                                      const double *__restrict__ centre, double ox, double oy,
                                                      double oz, SrcView<T> sv, int P, int NT,
-                                                     const int32_t *__restrict__ first_child,
-                                                     const int32_t *__restrict__ nchild,
-                                                     const int32_t *__restrict__ parent, int32_t *__restrict__ ucnt,
+                                                     const int4 *__restrict__ link, int32_t *__restrict__ ucnt,
                                                      T *__restrict__ mom) {
     constexpr int CH = sizeof(T) == 4 ? kP2MChunk : kP2MChunk / 2;
     extern __shared__ __align__(16) unsigned char up_smem[];
     int *sterm = reinterpret_cast<int *>(up_smem);
     T *region = reinterpret_cast<T *>(up_smem + ((3 * 455 * sizeof(int) + 31) / 32) * 32);
-    __shared__ T hp[8][3][kMaxP + 1];
+    __shared__ T hs[8][3];
     __shared__ T sbin[kMaxP + 1][kMaxP + 1];
-    __shared__ int s_next;
+    __shared__ int4 s_next;
     for (int i = threadIdx.x; i < 3 * NT; i += blockDim.x) sterm[i] = c_terms[i];
     for (int i = threadIdx.x; i < (P + 1) * (P + 1); i += blockDim.x) {
         const int n = i / (P + 1), k = i - n * (P + 1);
@@ -983,7 +1017,9 @@ __global__ void __launch_bounds__(256) upward_kernel(int nleaves, const int32_t 
     T(*pw)[kMaxP + 1][CP] = reinterpret_cast<T(*)[kMaxP + 1][CP]>(region);
     T(*sd)[CH] = reinterpret_cast<T(*)[CH]>(region + 3 * (kMaxP + 1) * CP);
     T(*part)[2][128] = reinterpret_cast<T(*)[2][128]>(region + 3 * (kMaxP + 1) * CP + 4 * CH);
-    int node = leaf_node[blockIdx.x];
+    const int node = leaf_node[blockIdx.x];
+    int4 up = make_int4(-1, 0, 0, 0);
+    if (threadIdx.x == 0) up = link[node];   // used after the P2M
     {
         const int64_t s0 = start[node], cnt = count[node];
         T c[3];
@@ -1068,8 +1104,8 @@ __global__ void __launch_bounds__(256) upward_kernel(int nleaves, const int32_t 
         }
     }
     // ---- climb: the last child to finish computes the parent
-    climb_m2m<T>(node, P, NT, 2 * NT, centre, first_child, nchild, parent, ucnt, mom, region, region + 8 * 2 * NT,
-                 hp, sbin, sterm, s_next);
+    climb_m2m<T>(up, NT, 2 * NT, centre, link, ucnt, mom, region, region + 8 * 2 * NT, hs, sbin, sterm,
+                 s_next);
 }
 
 size_t upward_smem(int NT, size_t elem) {
@@ -1140,7 +1176,7 @@ void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s) {
         SrcView<float> sv{Tr.srcA32.p, Tr.srcB32.p};
         upward_kernel<float><<<Tr.nleaves, 256, upward_smem(NT, 4), s>>>(
             Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p, Tr.origin[0], Tr.origin[1], Tr.origin[2],
-            sv, P, NT, Tr.first_child.p, Tr.nchild.p, Tr.parent.p, Tr.ucnt.p, Tr.mom32.p);
+            sv, P, NT, Tr.link.p, Tr.ucnt.p, Tr.mom32.p);
         if (P <= kRadialMaxP) {
             PB_LAUNCH_CHECK();
             Tr.rmom32.alloc((size_t)Tr.nnodes * radial_stride(P));
@@ -1155,7 +1191,7 @@ void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s) {
         SrcView<double> sv{Tr.src64.p};
         upward_kernel<double><<<Tr.nleaves, 256, upward_smem(NT, 8), s>>>(
             Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p, Tr.origin[0], Tr.origin[1], Tr.origin[2],
-            sv, P, NT, Tr.first_child.p, Tr.nchild.p, Tr.parent.p, Tr.ucnt.p, Tr.mom64.p);
+            sv, P, NT, Tr.link.p, Tr.ucnt.p, Tr.mom64.p);
     }
     PB_LAUNCH_CHECK();
 }
@@ -1176,12 +1212,10 @@ void m2m_climb(Tree &Tr, int P, bool mixed, void *mom, int nval, cudaStream_t s)
     if (shm > kClimbMaxShared) fail(PB_EINVAL, "internal: moment sets too large for the one-launch M2M");
     if (mixed)
         climb_kernel<float><<<Tr.nleaves, 256, shm, s>>>(Tr.nleaves, Tr.leaf_node.p, Tr.centre.p, P, NT, nval,
-                                                         Tr.first_child.p, Tr.nchild.p, Tr.parent.p, Tr.ucnt.p,
-                                                         (float *)mom);
+                                                         Tr.link.p, Tr.ucnt.p, (float *)mom);
     else
         climb_kernel<double><<<Tr.nleaves, 256, shm, s>>>(Tr.nleaves, Tr.leaf_node.p, Tr.centre.p, P, NT, nval,
-                                                          Tr.first_child.p, Tr.nchild.p, Tr.parent.p, Tr.ucnt.p,
-                                                          (double *)mom);
+                                                          Tr.link.p, Tr.ucnt.p, (double *)mom);
     PB_LAUNCH_CHECK();
 }
 
