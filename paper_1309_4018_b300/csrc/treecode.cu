@@ -770,7 +770,12 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
     float hi[2 * NK], lo[2 * NK], nh[2 * NK], nl[2 * NK];
 #pragma unroll
     for (int a = 0; a < 2 * NK; ++a) { hi[a] = 0.f; lo[a] = 0.f; nh[a] = 0.f; nl[a] = 0.f; }
-    // records as one 16-byte (two kernels) or 8-byte load each; four per lane in flight
+    // records as one 16-byte (two kernels) or 8-byte load each.  The list
+    // bounds, then the first four P2P records, four M2P positions and two
+    // near entries of every lane, then the M2P records and the densities they
+    // point to, are each issued as one round of independent loads (three
+    // dependent rounds in all); longer lists continue in loops.  Every lane
+    // adds its P2P, then M2P, then near values, each in list order.
     using Rec = typename std::conditional<NK == 2, float4, float2>::type;
     auto add_rec = [&](const Rec &r) {
         two_add(hi[0], lo[0], r.x);
@@ -780,43 +785,90 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
             two_add(hi[3 % (2 * NK)], lo[3 % (2 * NK)], r.w);
         }
     };
-    {
-        const Rec *pr = reinterpret_cast<const Rec *>(p2p_part);
-        const int64_t e1 = p2p_ptr[t + 1];
-        for (int64_t e = p2p_ptr[t] + lane; e < e1; e += 128) {
-            Rec r[4];
+    const Rec *pp = reinterpret_cast<const Rec *>(p2p_part);
+    const Rec *mp = reinterpret_cast<const Rec *>(m2p_part);
+    const int64_t pb = p2p_ptr[t] + lane, pe = p2p_ptr[t + 1];
+    const int64_t mb = m2p_part ? m2p_ptr[t] + lane : 0, me = m2p_part ? m2p_ptr[t + 1] : 0;
+    const int64_t nb = nr.ptr[t] + lane, ne = nr.ptr[t + 1];
+    const int sp = nr.use_self && lane < 2 * NK ? nr.selfp[t] : 0;
+    // round 1
+    Rec rp[4], rm[4];
+    int q[4], jn[2];
+    float dv[2][NK], dk[2][NK];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (e + 32 * u < e1) r[u] = pr[e + 32 * u];
+    for (int u = 0; u < 4; ++u)
+        if (pb + 32 * u < pe) rp[u] = pp[pb + 32 * u];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (e + 32 * u < e1) add_rec(r[u]);
-        }
-    }
-    if (m2p_part) {
-        const Rec *pr = reinterpret_cast<const Rec *>(m2p_part);
-        const int64_t e1 = m2p_ptr[t + 1];
-        for (int64_t e = m2p_ptr[t] + lane; e < e1; e += 128) {
-            int q[4];
-            Rec r[4];
+    for (int u = 0; u < 4; ++u) q[u] = mb + 32 * u < me ? m2p_pos[mb + 32 * u] : -1;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) q[u] = e + 32 * u < e1 ? m2p_pos[e + 32 * u] : -1;
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (q[u] >= 0) r[u] = pr[q[u]];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (q[u] >= 0) add_rec(r[u]);
-        }
-    }
-    for (int64_t e = nr.ptr[t] + lane; e < nr.ptr[t + 1]; e += 32) {
-        const int j = nr.panel[e];
-        const float2 pd = nr.phf[j];
-        const float ph = pd.x, dph = pd.y;
+    for (int u = 0; u < 2; ++u) {
+        const int64_t e = nb + 32 * u;
+        jn[u] = e < ne ? nr.panel[e] : -1;
 #pragma unroll
         for (int a = 0; a < NK; ++a) {
-            two_add(nh[2 * a], nl[2 * a], nr.dV[a][e] * dph);
-            two_add(nh[2 * a + 1], nl[2 * a + 1], nr.dK[a][e] * ph);
+            dv[u][a] = e < ne ? nr.dV[a][e] : 0.f;
+            dk[u][a] = e < ne ? nr.dK[a][e] : 0.f;
+        }
+    }
+    // the P2P records arrive with the positions that round 2 needs
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (pb + 32 * u < pe) add_rec(rp[u]);
+    // round 2
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (q[u] >= 0) rm[u] = mp[q[u]];
+    float2 pd[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) pd[u] = jn[u] >= 0 ? nr.phf[jn[u]] : make_float2(0.f, 0.f);
+    double sv = 0.0, sd = 0.0;
+    if (nr.use_self && lane < 2 * NK && (lane & 1) == 0) {
+        sv = nr.selfV[lane >> 1][sp];
+        sd = nr.dphi[sp];
+    }
+    // P2P beyond four entries per lane
+    for (int64_t e = pb + 128; e < pe; e += 128) {
+        Rec r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (e + 32 * u < pe) r[u] = pp[e + 32 * u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (e + 32 * u < pe) add_rec(r[u]);
+    }
+    // M2P
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (q[u] >= 0) add_rec(rm[u]);
+    for (int64_t e = mb + 128; e < me; e += 128) {
+        int qq[4];
+        Rec r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) qq[u] = e + 32 * u < me ? m2p_pos[e + 32 * u] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (qq[u] >= 0) r[u] = mp[qq[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (qq[u] >= 0) add_rec(r[u]);
+    }
+    // near-singular corrections
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+        if (jn[u] >= 0) {
+#pragma unroll
+            for (int a = 0; a < NK; ++a) {
+                two_add(nh[2 * a], nl[2 * a], dv[u][a] * pd[u].y);
+                two_add(nh[2 * a + 1], nl[2 * a + 1], dk[u][a] * pd[u].x);
+            }
+        }
+    for (int64_t e = nb + 64; e < ne; e += 32) {
+        const int j = nr.panel[e];
+        const float2 pdj = nr.phf[j];
+#pragma unroll
+        for (int a = 0; a < NK; ++a) {
+            two_add(nh[2 * a], nl[2 * a], nr.dV[a][e] * pdj.y);
+            two_add(nh[2 * a + 1], nl[2 * a + 1], nr.dK[a][e] * pdj.x);
         }
     }
 #pragma unroll
@@ -839,10 +891,7 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
     if (lane < 2 * NK) {
         double out = ((double)vh + (double)vl) * kInv4Pi + ((double)wh + (double)wl);
         const int a = lane;
-        if (nr.use_self && (a & 1) == 0) {
-            const int me = nr.selfp[t];
-            out += nr.selfV[a >> 1][me] * nr.dphi[me];
-        }
+        if (nr.use_self && (a & 1) == 0) out += sv * sd;
         double *dst = (a >> 1) == 0 ? VK0 : VK1;
         dst[(a & 1) ? ntg + t : t] = out;
     }
