@@ -378,16 +378,32 @@ __global__ void hist_count_kernel(int64_t nent, int64_t chunk, const int32_t *__
 }
 
 // hb[b][k] <- sum_{b' < b} hb[b'][k] (each block's start within key k); cnt[k] = the total.
+// One warp per key: 64 blocks' counts loaded at once, scanned with shuffles.
+__device__ __forceinline__ int32_t warp_inclusive_scan(int32_t x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
 __global__ void hist_scan_kernel(int nkeys, int nb, int32_t *__restrict__ hb, int32_t *__restrict__ cnt) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (k >= nkeys) return;
     int32_t run = 0;
-    for (int b = 0; b < nb; ++b) {
-        const int32_t c = hb[(int64_t)b * nkeys + k];
-        hb[(int64_t)b * nkeys + k] = run;
-        run += c;
+    for (int b0 = 0; b0 < nb; b0 += 64) {
+        const int ba = b0 + lane, bb = b0 + 32 + lane;
+        const int32_t ca = ba < nb ? hb[(int64_t)ba * nkeys + k] : 0;
+        const int32_t cb = bb < nb ? hb[(int64_t)bb * nkeys + k] : 0;
+        const int32_t xa = warp_inclusive_scan(ca, lane), xb = warp_inclusive_scan(cb, lane);
+        const int32_t ta = __shfl_sync(0xffffffffu, xa, 31), tb = __shfl_sync(0xffffffffu, xb, 31);
+        if (ba < nb) hb[(int64_t)ba * nkeys + k] = run + xa - ca;
+        if (bb < nb) hb[(int64_t)bb * nkeys + k] = run + ta + xb - cb;
+        run += ta + tb;
     }
-    cnt[k] = run;
+    if (lane == 0) cnt[k] = run;
 }
 
 __global__ void hist_fill_kernel(int64_t nent, int64_t chunk, const int32_t *__restrict__ owner,
@@ -934,7 +950,7 @@ void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &pr
             if (hist) {
                 hist_count_kernel<<<nb, 256, hshm, s>>>(nent, chunk, ent, remap, nkeys, hb.p);
                 PB_LAUNCH_CHECK();
-                hist_scan_kernel<<<div_up(nkeys, 128), 128, 0, s>>>(nkeys, nb, hb.p, cnt.p);
+                hist_scan_kernel<<<div_up(nkeys, 4), 128, 0, s>>>(nkeys, nb, hb.p, cnt.p);
                 PB_LAUNCH_CHECK();
             } else {
                 inv_count_kernel<<<div_up(nent, 256), 256, 0, s>>>(nent, ent, remap, cnt.p);

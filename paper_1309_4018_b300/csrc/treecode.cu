@@ -58,11 +58,14 @@ __global__ void strengths64_kernel(int64_t n, const double *__restrict__ ys, con
     o[7] = (double)j;
 }
 
+// Also the FP32 copy (phi, dphi) of the ns panel densities (threads q < ns).
 __global__ void strengths32_kernel(int64_t n, const float4 *__restrict__ pos, const double *__restrict__ was,
                                    const int32_t *__restrict__ pids, const double *__restrict__ nrm,
                                    const double *__restrict__ phi, const double *__restrict__ dphi,
-                                   float4 *__restrict__ A, float4 *__restrict__ B) {
+                                   float4 *__restrict__ A, float4 *__restrict__ B, int64_t ns,
+                                   float2 *__restrict__ phf) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < ns) phf[q] = make_float2((float)phi[q], (float)dphi[q]);
     if (q >= n) return;
     const int j = pids[q];
     const double w = was[q];
@@ -75,12 +78,6 @@ __global__ void strengths32_kernel(int64_t n, const float4 *__restrict__ pos, co
 
 // FP32 copies of (phi, dphi) per panel, read by the mixed-precision gather's
 // near-field terms (one conversion per panel instead of one per near entry).
-__global__ void phi32_kernel(int64_t n, const double *__restrict__ phi, const double *__restrict__ dphi,
-                             float2 *__restrict__ out) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = make_float2((float)phi[i], (float)dphi[i]);
-}
-
 // ---------------------------------------------------------------- P2M (leaves)
 template <typename T>
 struct SrcView;
@@ -1201,10 +1198,8 @@ void compute_strengths(Tree &Tr, const SurfDev &S, const double *phi, const doub
     if (!n) return;
     if (mixed) {
         Tr.phf.alloc(S.n);
-        phi32_kernel<<<div_up(S.n, 256), 256, 0, s>>>(S.n, phi, dphi, Tr.phf.p);
-        PB_LAUNCH_CHECK();
-        strengths32_kernel<<<div_up(n, 256), 256, 0, s>>>(n, Tr.pos32.p, Tr.was.p, Tr.pids.p, S.nrm.p, phi, dphi,
-                                                          Tr.srcA32.p, Tr.srcB32.p);
+        strengths32_kernel<<<div_up(std::max<int64_t>(n, S.n), 256), 256, 0, s>>>(
+            n, Tr.pos32.p, Tr.was.p, Tr.pids.p, S.nrm.p, phi, dphi, Tr.srcA32.p, Tr.srcB32.p, S.n, Tr.phf.p);
     } else {
         strengths64_kernel<<<div_up(n, 256), 256, 0, s>>>(n, Tr.ys.p, Tr.was.p, Tr.pids.p, S.nrm.p, phi, dphi,
                                                           Tr.src64.p);
