@@ -21,6 +21,8 @@ constexpr int kRedThreads = 256;
 // Vectors are taken 8 at a time: each thread keeps 8 running sums, so w is
 // read once per group and the block synchronises once per group.
 constexpr int kDotGroup = 8;
+constexpr int kSliceGroup = 16;     // basis vectors per pass of the fused Arnoldi dots
+constexpr int kMaxRestart = 200;    // the largest restart length (checked when the parameters are set)
 
 __global__ void __launch_bounds__(kRedThreads) mdot_kernel(const double *__restrict__ V, int64_t ld, int nv,
                                                            const double *__restrict__ w, int64_t n,
@@ -260,40 +262,72 @@ __device__ __forceinline__ ArnoldiArgs device_column(ArnoldiArgs a) {
     return a;
 }
 
-// Block partials of V[v] . w over the block's slice, for v < nv.  The FP64
-// pipe is narrow on this part, so the block reduction is arranged to issue
-// few FP64 instructions: every thread's partials go to shared memory, each
-// (vector, 8-thread chunk) is summed by one thread, and one warp per vector
-// adds the 32 chunk sums by a butterfly (96 FP64 warp instructions per
-// group of 8 vectors instead of a butterfly per vector in every warp).
+// Block partials of V[v] . w over the block's slice, for v < nv, 16 vectors
+// per pass (16 independent loads per element in flight).  The FP64 pipe is
+// narrow on this part, so the block reduction is arranged to issue few FP64
+// instructions: every thread's partials go to shared memory, each (vector,
+// 8-thread chunk) is summed by one thread, and one warp per vector adds the
+// 32 chunk sums by a butterfly (each warp takes two vectors of the pass).
 __device__ void slice_dots(const ArnoldiArgs &a, int64_t lo, int64_t hi) {
-    static_assert(kRedThreads == 256 && kDotGroup == 8, "the reduction layout assumes 256 threads, 8 vectors");
-    __shared__ double red[kDotGroup][kRedThreads + 1];
+    constexpr int G = kSliceGroup;
+    static_assert(kRedThreads == 256 && G == 16, "the reduction layout assumes 256 threads, 16 vectors");
+    __shared__ double red[G][kRedThreads + 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int v0 = 0; v0 < a.nv; v0 += kDotGroup) {
-        const int nb = min(kDotGroup, a.nv - v0);
-        double acc[kDotGroup];
+    for (int v0 = 0; v0 < a.nv; v0 += G) {
+        const int nb = min(G, a.nv - v0);
+        double acc[G];
 #pragma unroll
-        for (int b = 0; b < kDotGroup; ++b) acc[b] = 0.0;
+        for (int b = 0; b < G; ++b) acc[b] = 0.0;
         for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) {
             const double wi = a.w[i];
+            // unconditional loads (the index clamped to the last vector; the
+            // extra sums are never stored), so the 16 are issued together
+            double x[G];
 #pragma unroll
-            for (int b = 0; b < kDotGroup; ++b)
-                if (b < nb) acc[b] += a.V[(int64_t)(v0 + b) * a.ld + i] * wi;
+            for (int b = 0; b < G; ++b) x[b] = a.V[(int64_t)(v0 + min(b, nb - 1)) * a.ld + i];
+#pragma unroll
+            for (int b = 0; b < G; ++b) acc[b] += x[b] * wi;
         }
 #pragma unroll
-        for (int b = 0; b < kDotGroup; ++b) red[b][threadIdx.x] = acc[b];
+        for (int b = 0; b < G; ++b) red[b][threadIdx.x] = acc[b];
         __syncthreads();
-        // thread (vector wid, chunk lane) sums the partials of threads 8 lane .. 8 lane + 7
-        double t = 0.0;
-        if (wid < nb) {
+        // warp wid sums vectors wid and wid + 8: lane adds the partials of threads 8 lane .. 8 lane + 7
 #pragma unroll
-            for (int k = 0; k < 8; ++k) t += red[wid][8 * lane + k];
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) a.partial[(v0 + wid) * kRedBlocks + blockIdx.x] = t;
+        for (int h = 0; h < 2; ++h) {
+            const int vb = wid + 8 * h;
+            if (vb < nb) {
+                double t = 0.0;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) t += red[vb][8 * lane + k];
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                if (lane == 0) a.partial[(v0 + vb) * kRedBlocks + blockIdx.x] = t;
+            }
         }
         __syncthreads();
     }
+}
+
+// w[i] - sum_v V[v][i] h[v], subtracted in v order, eight basis loads in flight
+// per step.  sh holds h padded with zeros to a multiple of eight and the
+// padding steps load the last vector (finite), so they subtract zero.
+__device__ __forceinline__ double project_elem(const ArnoldiArgs &a, const double *__restrict__ sh, int64_t i,
+                                               double t) {
+    const int nv8 = (a.nv + 7) & ~7;
+    for (int v = 0; v < nv8; v += 8) {
+        double x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = a.V[(int64_t)min(v + u, a.nv - 1) * a.ld + i];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t -= x[u] * sh[v + u];
+    }
+    return t;
+}
+
+// h[0 .. nv) into shared memory, zero up to the next multiple of eight.
+__device__ __forceinline__ void stage_h(double *sh, const double *__restrict__ h, int nv) {
+    const int nv8 = (nv + 7) & ~7;
+    for (int v = threadIdx.x; v < nv8; v += kRedThreads) sh[v] = v < nv ? h[v] : 0.0;
+    __syncthreads();
 }
 
 // One warp per vector: lanes take the block partials in a fixed stride, then a butterfly.
@@ -301,6 +335,7 @@ __device__ void finish_dots(const ArnoldiArgs &a, int nv, double *out) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int v = wid; v < nv; v += kRedThreads / 32) {
         double t = 0.0;
+#pragma unroll
         for (int b = lane; b < kRedBlocks; b += 32) t += __ldcg(a.partial + v * kRedBlocks + b);
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (lane == 0) out[v] = t;
@@ -324,11 +359,9 @@ __global__ void __launch_bounds__(kRedThreads) arnoldi_project_dots_kernel(Arnol
     const ArnoldiArgs a = device_column(a0);
     const int64_t per = (a.n + kRedBlocks - 1) / kRedBlocks;
     const int64_t lo = blockIdx.x * per, hi = min(a.n, lo + per);
-    for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) {
-        double t = a.w[i];
-        for (int v = 0; v < a.nv; ++v) t -= a.V[(int64_t)v * a.ld + i] * a.h1[v];
-        a.w[i] = t;
-    }
+    __shared__ double sh[kMaxRestart + 8];
+    stage_h(sh, a.h1, a.nv);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) a.w[i] = project_elem(a, sh, i, a.w[i]);
     __syncthreads();
     slice_dots(a, lo, hi);
     if (arrive_last(a.count)) {
@@ -344,10 +377,11 @@ __global__ void __launch_bounds__(kRedThreads) arnoldi_project_norm_kernel(Arnol
     __shared__ double sm[kRedThreads / 32];
     const int64_t per = (a.n + kRedBlocks - 1) / kRedBlocks;
     const int64_t lo = blockIdx.x * per, hi = min(a.n, lo + per);
+    __shared__ double sh[kMaxRestart + 8];
+    stage_h(sh, a.h2, a.nv);
     double s2 = 0.0;
     for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) {
-        double t = a.w[i];
-        for (int v = 0; v < a.nv; ++v) t -= a.V[(int64_t)v * a.ld + i] * a.h2[v];
+        const double t = project_elem(a, sh, i, a.w[i]);
         a.w[i] = t;
         s2 += t * t;
     }
@@ -366,22 +400,30 @@ __global__ void __launch_bounds__(kRedThreads) arnoldi_project_norm_kernel(Arnol
         for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
         if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = p;
         __syncthreads();
+        // Hessenberg column j = h1 + h2 and the earlier rotations, staged in
+        // shared memory by the whole block; thread 0 applies the rotations
+        // there (no global round trip per step), then the block writes it back
+        __shared__ double scol[kMaxRestart + 2], scs[kMaxRestart], ssn[kMaxRestart];
+        GmresState *st = a.st;
+        const int m = st->m, j = a.j;
+        for (int i = threadIdx.x; i <= j; i += kRedThreads) scol[i] = a.h1[i] + a.h2[i];
+        for (int i = threadIdx.x; i < j; i += kRedThreads) {
+            scs[i] = st->cs[i];
+            ssn[i] = st->sn[i];
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
             for (int k = 0; k < kRedThreads / 32; ++k) t += sm[k];
             *a.nrm2 = t;
             *a.count = 0;
-            // Hessenberg column j = h1 + h2 with the new subdiagonal ||w||
-            GmresState *st = a.st;
-            const int m = st->m, j = a.j;
-            double *col = st->H + (int64_t)j * (m + 1);
-            for (int i = 0; i <= j; ++i) col[i] = a.h1[i] + a.h2[i];
+            double *col = scol;
             const double hn = sqrt(t);
             col[j + 1] = hn;
             st->hnext = hn;
             for (int i = 0; i < j; ++i) {
-                const double u = st->cs[i] * col[i] + st->sn[i] * col[i + 1];
-                col[i + 1] = -st->sn[i] * col[i] + st->cs[i] * col[i + 1];
+                const double u = scs[i] * col[i] + ssn[i] * col[i + 1];
+                col[i + 1] = -ssn[i] * col[i] + scs[i] * col[i + 1];
                 col[i] = u;
             }
             const double den = hypot(col[j], col[j + 1]);
@@ -390,10 +432,14 @@ __global__ void __launch_bounds__(kRedThreads) arnoldi_project_norm_kernel(Arnol
             st->sn[j] = sn;
             col[j] = den;
             col[j + 1] = 0.0;
-            st->g[j + 1] = -sn * st->g[j];
-            st->g[j] = c * st->g[j];
-            st->res_est = fabs(st->g[j + 1]) / st->bnorm;
+            const double gj = st->g[j];
+            st->g[j + 1] = -sn * gj;
+            st->g[j] = c * gj;
+            st->res_est = fabs(-sn * gj) / st->bnorm;
         }
+        __syncthreads();
+        double *col = st->H + (int64_t)j * (m + 1);
+        for (int i = threadIdx.x; i <= j + 1; i += kRedThreads) col[i] = scol[i];
     }
 }
 
