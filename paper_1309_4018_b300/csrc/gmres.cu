@@ -14,7 +14,7 @@ namespace pb {
 
 namespace {
 
-constexpr int kRedBlocks = 296;   // 2 x 148 SMs
+constexpr int kRedBlocks = 148;   // one per SM: two elements per thread halve the FP64 block reductions
 constexpr int kRedThreads = 256;
 
 // partial[v * kRedBlocks + block] = sum over the block's slice of V[v] . w.
