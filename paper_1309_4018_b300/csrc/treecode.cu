@@ -581,85 +581,150 @@ __global__ void radial_moments_kernel(int nnodes, const float *__restrict__ mom,
     reinterpret_cast<float2 *>(rmom)[b * NP + r] = make_float2(sm, sd);
 }
 
-// Box-major M2P for a pair whose two kernels are Laplace (slot 0) and Yukawa
-// (slot 1): one warp per (box, up to 32 targets) item; the warp stages the
-// box's radial moments in shared memory with coalesced loads and every lane
-// reads them as broadcasts; one record (VL, KL, VY, KY) per pair.
-template <int P>
-__global__ void __launch_bounds__(128) m2p_ly32_kernel(int64_t nitems, const int4 *__restrict__ items,
-                                                       const int32_t *__restrict__ inv, const float4 *__restrict__ x32,
-                                                       const float4 *__restrict__ cen32, const float *__restrict__ rmom,
-                                                       float kappa, float4 *__restrict__ part) {
-    constexpr int NQ = radial_stride(P) / 4;     // float4 per box
-    __shared__ float4 sR[4][NQ];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t item = (int64_t)blockIdx.x * 4 + warp;
-    if (item >= nitems) return;
-    const int4 it = items[item];
-    const int b = it.x;
-    // the box's radial moments staged by the whole warp (coalesced), then read as broadcasts
-    {
-        const float4 *src = reinterpret_cast<const float4 *>(rmom + (int64_t)b * radial_stride(P));
-        for (int q = lane; q < NQ; q += 32) sR[warp][q] = src[q];
-        __syncwarp();
+// The radial-form M2P sums of NTG targets against one box's staged radial
+// moments R: every moment pair is read from shared memory once for all NTG
+// targets.  u = box centre - target; out = (VL, KL, VY, KY) per target.  The
+// arithmetic per target is that of the one-target form, in the same order.
+template <int P, int NTG>
+__device__ __forceinline__ void m2p_ly_eval(const float4 *R, const float (&ux)[NTG], const float (&uy)[NTG],
+                                            const float (&uz)[NTG], float kappa, float4 (&out)[NTG]) {
+    float px[NTG][P + 1], py[NTG][P + 1], pz[NTG][P + 1], SM[NTG][P + 1], SD[NTG][P + 1];
+#pragma unroll
+    for (int t = 0; t < NTG; ++t) {
+        px[t][0] = py[t][0] = pz[t][0] = 1.f;
+#pragma unroll
+        for (int i = 1; i <= P; ++i) {
+            px[t][i] = px[t][i - 1] * ux[t];
+            py[t][i] = py[t][i - 1] * uy[t];
+            pz[t][i] = pz[t][i - 1] * uz[t];
+        }
+#pragma unroll
+        for (int n = 0; n <= P; ++n) { SM[t][n] = 0.f; SD[t][n] = 0.f; }
     }
-    if (lane >= it.z) return;
-    const int64_t slot = (int64_t)it.y + lane;
-    const float4 c = cen32[b];
-    const float4 x = x32[inv[slot]];
-    const float ux = c.x - x.x, uy = c.y - x.y, uz = c.z - x.z;
-    const float r2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-    const float rinv = rsqrtf(r2), ir2 = rinv * rinv;
-    float FL[P + 1], FY[P + 1];
-    FL[0] = rinv;
-#pragma unroll
-    for (int n = 0; n < P; ++n) FL[n + 1] = (-(float)(2 * n + 1) * ir2) * FL[n];
-    const float rho = r2 * rinv;
-    const float e = __expf(-kappa * rho);
-    FY[0] = e * rinv;
-    if (P >= 1) FY[1] = -fmaf(kappa, rho, 1.f) * FY[0] * ir2;
-    const float k2 = kappa * kappa;
-#pragma unroll
-    for (int n = 1; n < P; ++n) FY[n + 1] = fmaf(k2, FY[n - 1], -(float)(2 * n + 1) * FY[n]) * ir2;
-    float px[P + 1], py[P + 1], pz[P + 1];
-    px[0] = py[0] = pz[0] = 1.f;
-#pragma unroll
-    for (int i = 1; i <= P; ++i) { px[i] = px[i - 1] * ux; py[i] = py[i - 1] * uy; pz[i] = pz[i - 1] * uz; }
-    float SM[P + 1], SD[P + 1];
-#pragma unroll
-    for (int n = 0; n <= P; ++n) { SM[n] = 0.f; SD[n] = 0.f; }
-    const float4 *R = sR[warp];
     float4 cur = make_float4(0.f, 0.f, 0.f, 0.f);
     int o = 0;
 #pragma unroll
     for (int a1 = 0; a1 <= P; ++a1)
 #pragma unroll
         for (int a2 = 0; a2 <= P - a1; ++a2) {
-            const float base = px[a1] * py[a2];
+            float base[NTG];
+#pragma unroll
+            for (int t = 0; t < NTG; ++t) base[t] = px[t][a1] * py[t][a2];
 #pragma unroll
             for (int a3 = 0; a3 <= P - a1 - a2; ++a3) {
-                const float mono = base * pz[a3];
+                float mono[NTG];
+#pragma unroll
+                for (int t = 0; t < NTG; ++t) mono[t] = base[t] * pz[t][a3];
                 const int a = a1 + a2 + a3;
 #pragma unroll
                 for (int n = a; 2 * n <= a + P; ++n) {
                     if ((o & 3) == 0) cur = R[o >> 2];
                     const float nm = (o & 3) == 0 ? cur.x : cur.z;
                     const float nd = (o & 3) == 0 ? cur.y : cur.w;
-                    SM[n] = fmaf(mono, nm, SM[n]);
-                    SD[n] = fmaf(mono, nd, SD[n]);
+#pragma unroll
+                    for (int t = 0; t < NTG; ++t) {
+                        SM[t][n] = fmaf(mono[t], nm, SM[t][n]);
+                        SD[t][n] = fmaf(mono[t], nd, SD[t][n]);
+                    }
                     o += 2;
                 }
             }
         }
-    float VL = 0.f, KL = 0.f, VY = 0.f, KY = 0.f;
 #pragma unroll
-    for (int n = 0; n <= P; ++n) {
-        VL = fmaf(FL[n], SM[n], VL);
-        KL = fmaf(FL[n], SD[n], KL);
-        VY = fmaf(FY[n], SM[n], VY);
-        KY = fmaf(FY[n], SD[n], KY);
+    for (int t = 0; t < NTG; ++t) {
+        const float r2 = fmaf(ux[t], ux[t], fmaf(uy[t], uy[t], uz[t] * uz[t]));
+        const float rinv = rsqrtf(r2), ir2 = rinv * rinv;
+        float FL[P + 1], FY[P + 1];
+        FL[0] = rinv;
+#pragma unroll
+        for (int n = 0; n < P; ++n) FL[n + 1] = (-(float)(2 * n + 1) * ir2) * FL[n];
+        const float rho = r2 * rinv;
+        const float e = __expf(-kappa * rho);
+        FY[0] = e * rinv;
+        if (P >= 1) FY[1] = -fmaf(kappa, rho, 1.f) * FY[0] * ir2;
+        const float k2 = kappa * kappa;
+#pragma unroll
+        for (int n = 1; n < P; ++n) FY[n + 1] = fmaf(k2, FY[n - 1], -(float)(2 * n + 1) * FY[n]) * ir2;
+        float VL = 0.f, KL = 0.f, VY = 0.f, KY = 0.f;
+#pragma unroll
+        for (int n = 0; n <= P; ++n) {
+            VL = fmaf(FL[n], SM[t][n], VL);
+            KL = fmaf(FL[n], SD[t][n], KL);
+            VY = fmaf(FY[n], SM[t][n], VY);
+            KY = fmaf(FY[n], SD[t][n], KY);
+        }
+        out[t] = make_float4(VL, KL, VY, KY);
     }
-    part[slot] = make_float4(VL, KL, VY, KY);
+}
+
+// Box-major M2P for a pair whose two kernels are Laplace (slot 0) and Yukawa
+// (slot 1), one record (VL, KL, VY, KY) per (target, box).  A warp takes NI
+// consecutive (box, up to 32 targets) items and stages the box's radial
+// moments in shared memory with coalesced loads; every lane reads them as
+// broadcasts.  When the NI items are all the same box's groups of targets
+// (the usual case: a box's items are consecutive and all but the last hold
+// 32 targets), every lane evaluates one target of each, so each moment pair
+// is read once for NI targets; otherwise the items are evaluated one after
+// the other.  Lanes past the last item's count evaluate their first target
+// again and store it once.
+template <int P, int NI>
+__global__ void __launch_bounds__(128) m2p_ly32x_kernel(int64_t nitems, const int4 *__restrict__ items,
+                                                        const int32_t *__restrict__ inv,
+                                                        const float4 *__restrict__ x32,
+                                                        const float4 *__restrict__ cen32,
+                                                        const float *__restrict__ rmom, float kappa,
+                                                        float4 *__restrict__ part) {
+    constexpr int NQ = radial_stride(P) / 4;     // float4 per box
+    __shared__ float4 sR[4][NQ];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i0 = ((int64_t)blockIdx.x * 4 + warp) * NI;
+    if (i0 >= nitems) return;
+    int4 it[NI];
+    bool same = true;
+#pragma unroll
+    for (int k = 0; k < NI; ++k) {
+        it[k] = i0 + k < nitems ? items[i0 + k] : make_int4(-1, 0, 0, 0);
+        same = same && it[k].x == it[0].x;
+    }
+    const float4 *R = sR[warp];
+    auto stage = [&](int b) {
+        const float4 *src = reinterpret_cast<const float4 *>(rmom + (int64_t)b * radial_stride(P));
+        __syncwarp();
+        for (int q = lane; q < NQ; q += 32) sR[warp][q] = src[q];
+        __syncwarp();
+    };
+    stage(it[0].x);
+    if (same) {
+        const float4 c = cen32[it[0].x];
+        int64_t sl[NI];
+        float ux[NI], uy[NI], uz[NI];
+#pragma unroll
+        for (int k = 0; k < NI; ++k) {
+            sl[k] = lane < it[k].z ? (int64_t)it[k].y + lane : (int64_t)it[0].y + lane;
+            const float4 x = x32[inv[sl[k]]];
+            ux[k] = c.x - x.x; uy[k] = c.y - x.y; uz[k] = c.z - x.z;
+        }
+        float4 out[NI];
+        m2p_ly_eval<P, NI>(R, ux, uy, uz, kappa, out);
+#pragma unroll
+        for (int k = 0; k < NI; ++k)
+            if (lane < it[k].z) part[sl[k]] = out[k];
+    } else {
+#pragma unroll 1
+        for (int k = 0; k < NI; ++k) {
+            if (it[k].x < 0) break;
+            if (k > 0) stage(it[k].x);
+            if (lane < it[k].z) {
+                const int64_t slot = (int64_t)it[k].y + lane;
+                const float4 c = cen32[it[k].x];
+                const float4 x = x32[inv[slot]];
+                const float ux[1] = {c.x - x.x}, uy[1] = {c.y - x.y}, uz[1] = {c.z - x.z};
+                float4 out[1];
+                m2p_ly_eval<P, 1>(R, ux, uy, uz, kappa, out);
+                part[slot] = out[0];
+            }
+        }
+    }
 }
 
 // One warp per target: V and K of every kernel = its P2P and M2P partials
@@ -1321,13 +1386,14 @@ void launch_m2p(const Pair &Pr, const Targets &G, const Tree &Tr, int P, bool mi
     if (Pr.n_m2p_items == 0) return;
     if (mixed && Pr.kappas.size() == 2 && Pr.kappas[0] == 0.0 && Pr.kappas[1] != 0.0 && P <= kRadialMaxP) {
         const int64_t ni = Pr.n_m2p_items;
-        const unsigned grid = (unsigned)((ni + 3) / 4);
+        constexpr int NI = 2;   // items per warp (three or four: 99 us against 90 at P = 6, fewer warps per SM)
+        const unsigned grid = (unsigned)((ni + 4 * NI - 1) / (4 * NI));
         float4 *part = reinterpret_cast<float4 *>(Pr.m2p_part32.p);
         const float kap = (float)Pr.kappas[1];
 #define PB_LY(PP)                                                                                              \
     case PP:                                                                                                   \
-        m2p_ly32_kernel<PP><<<grid, 128, 0, s>>>(ni, Pr.m2p_items.p, Pr.m2p_inv.p, Pr.x32.p, Tr.cen32.p,          \
-                                                 Tr.rmom32.p, kap, part);                                      \
+        m2p_ly32x_kernel<PP, NI><<<grid, 128, 0, s>>>(ni, Pr.m2p_items.p, Pr.m2p_inv.p, Pr.x32.p, Tr.cen32.p,    \
+                                                      Tr.rmom32.p, kap, part);                                 \
         break;
         switch (P) {
             PB_LY(0) PB_LY(1) PB_LY(2) PB_LY(3) PB_LY(4) PB_LY(5) PB_LY(6) PB_LY(7) PB_LY(8)
