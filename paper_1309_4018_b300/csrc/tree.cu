@@ -84,32 +84,44 @@ __global__ void morton_kernel(const double *__restrict__ p, int64_t n, double cx
 }
 
 // For every node of one level: count the non-empty octants of the nodes that split.
+// Eight threads per node (consecutive lanes), thread o (1..8) finding the first
+// position of the node's keys whose octant digit is >= o by binary search; the
+// node's child count is the number of non-empty octants (a ballot over the
+// eight lanes).  Nodes of fewer than ncrit points, or at the deepest level,
+// do not split.
 __global__ void split_count_kernel(int lvl, int nb, int nodes_begin, const int64_t *__restrict__ start,
                                    const int64_t *__restrict__ count, const uint64_t *__restrict__ keys, int ncrit,
                                    int32_t *__restrict__ nchild, int32_t *__restrict__ child_bounds /*nodes*9*/) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nb) return;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int t = (int)(gt >> 3), o = (int)(gt & 7) + 1;
+    const bool act = t < nb;
     const int b = nodes_begin + t;
-    const int64_t s = start[b], c = count[b];
-    int nc = 0;
-    if (c >= ncrit && lvl < kMaxLevel) {
-        const int sh = 3 * (kMaxLevel - 1 - lvl);
-        int64_t prev = 0;
-        child_bounds[9 * t] = 0;
-        for (int o = 1; o <= 8; ++o) {
-            // first position in [s, s + c) whose octant digit is >= o
-            int64_t lo = 0, hi = c;
+    int64_t c = 0, lo = 0;
+    bool split = false;
+    if (act) {
+        c = count[b];
+        split = c >= ncrit && lvl < kMaxLevel;
+        if (split) {
+            const int64_t s = start[b];
+            const int sh = 3 * (kMaxLevel - 1 - lvl);
+            int64_t hi = c;
             while (lo < hi) {
-                int64_t mid = (lo + hi) >> 1;
-                int d = (int)((keys[s + mid] >> sh) & 7ull);
+                const int64_t mid = (lo + hi) >> 1;
+                const int d = (int)((keys[s + mid] >> sh) & 7ull);
                 if (d < o) lo = mid + 1; else hi = mid;
             }
-            child_bounds[9 * t + o] = (int32_t)lo;
-            if (lo > prev) ++nc;
-            prev = lo;
         }
     }
-    nchild[b] = nc;
+    const int64_t up = __shfl_up_sync(0xffffffffu, lo, 1);
+    const int64_t prev = o == 1 ? 0 : up;
+    const unsigned nonempty = __ballot_sync(0xffffffffu, split && lo > prev);
+    if (!act) return;
+    if (split) {
+        child_bounds[9 * t + o] = (int32_t)lo;
+        if (o == 1) child_bounds[9 * t] = 0;
+    }
+    if (o == 1) nchild[b] = split ? __popc((nonempty >> (lane & ~7)) & 0xffu) : 0;
 }
 
 __global__ void split_write_kernel(int lvl, int nb, int nodes_begin, int nodes_end, const int64_t *__restrict__ cscan,
@@ -793,8 +805,8 @@ void build_tree_points(Tree &T, const double *pts, const double *wts, int64_t n,
         const int nb = le - lb;
         TmpBuf<int32_t> bounds((size_t)nb * 9, s);
         TmpBuf<int64_t> cscan(nb + 1, s);
-        split_count_kernel<<<div_up(nb, 128), 128, 0, s>>>(lvl, nb, lb, T.start.p, T.count.p, T.keys.p, ncrit,
-                                                           T.nchild.p, bounds.p);
+        split_count_kernel<<<div_up((int64_t)nb * 8, 128), 128, 0, s>>>(lvl, nb, lb, T.start.p, T.count.p, T.keys.p,
+                                                                         ncrit, T.nchild.p, bounds.p);
         PB_LAUNCH_CHECK();
         exclusive_scan_i32_to_i64(T.nchild.p + lb, cscan.p, nb, s);
         const int64_t nnew = read_i64(cscan.p + nb, s);
