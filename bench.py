@@ -354,8 +354,8 @@ def run_gpu(args):
 
     # end to end through the public API with host buffers (H2D inside the timed region)
     e2e_t = []
-    # the first new problem fills the allocator's cache (a second problem's buffers); untimed like the warm-up steps
-    for i in range(max(1, min(args.warmup, 2))):
+    # untimed new problems first, as many as the device warm-up steps (the first fills the allocator's cache)
+    for i in range(max(1, args.warmup)):
         p2 = make_problem()
         step(p2)
         p2.close()
