@@ -141,8 +141,6 @@ void setup_problem(pb_problem *pb) {
             cudaGraphExecDestroy(*e);
             *e = nullptr;
         }
-    upload_rules();
-    upload_term_tables();
     // geometry, trees and pairs of a previous setup keep their device buffers
     if (pb->S.size() != (size_t)ns) {
         pb->S.clear(); pb->T.clear(); pb->G.clear();
@@ -802,6 +800,10 @@ int pb_ctx_create(int device, pb_ctx **out) {
         PB_CUDA_TRY(cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep));
         PB_CUDA_TRY(cudaEventCreate(&c->ev0));
         PB_CUDA_TRY(cudaEventCreate(&c->ev1));
+        // constant tables (quadrature rules, Taylor term indices, binomials) and
+        // kernel attributes, once per context instead of at every setup
+        upload_rules();
+        upload_term_tables();
     });
     if (rc != PB_OK) return rc;
     *out = c.release();

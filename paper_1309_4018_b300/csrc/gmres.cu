@@ -465,8 +465,11 @@ void Gmres::init(int64_t n_, int m_, cudaStream_t s) {
     h.H = H.p; h.cs = cs.p; h.sn = sn.p; h.g = g.p; h.y = y.p;
     h.bnorm = 1.0;
     hs.alloc(4);
-    PB_CUDA_TRY(cudaMemcpyAsync(st.p, &h, sizeof(h), cudaMemcpyHostToDevice, s));
-    PB_CUDA_TRY(cudaStreamSynchronize(s));
+    // page-locked source that outlives the copy: no host wait here (a later
+    // init runs after the setup's final synchronisation)
+    hst.alloc(1);
+    *hst.p = h;
+    PB_CUDA_TRY(cudaMemcpyAsync(st.p, hst.p, sizeof(h), cudaMemcpyHostToDevice, s));
 }
 
 void Gmres::norm2_async(const double *x, cudaStream_t s) {

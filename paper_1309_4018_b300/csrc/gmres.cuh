@@ -27,6 +27,7 @@ struct Gmres {
     DevBuf<GmresState> st;
     DevBuf<unsigned> count;                                // arrival count of the fused reductions (0 between launches)
     PinnedBuf<double> hs;                                  // 0: ||b||^2, 1: ||r||^2, 2: residual estimate
+    PinnedBuf<GmresState> hst;                             // the initial state, copied without a host wait
     void init(int64_t n, int m, cudaStream_t s);
     void norm2_async(const double *x, cudaStream_t s);     // hs[0] = ||x||^2
     void set_bnorm(double bn, cudaStream_t s);
