@@ -854,7 +854,7 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
     const int64_t mb = m2p_part ? m2p_ptr[t] + lane : 0, me = m2p_part ? m2p_ptr[t + 1] : 0;
     const int64_t nb = nr.ptr[t] + lane, ne = nr.ptr[t + 1];
     const int sp = nr.use_self && lane < 2 * NK ? nr.selfp[t] : 0;
-    // round 1
+    // first load round
     Rec rp[4], rm[4];
     int q[4], jn[2];
     float dv[2][NK], dk[2][NK];
@@ -873,11 +873,11 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
             dk[u][a] = e < ne ? nr.dK[a][e] : 0.f;
         }
     }
-    // the P2P records arrive with the positions that round 2 needs
+    // the P2P records arrive with the positions that the second load round needs
 #pragma unroll
     for (int u = 0; u < 4; ++u)
         if (pb + 32 * u < pe) add_rec(rp[u]);
-    // round 2
+    // second load round
 #pragma unroll
     for (int u = 0; u < 4; ++u)
         if (q[u] >= 0) rm[u] = mp[q[u]];
