@@ -258,7 +258,11 @@ long long pb_launch_count(void);
  * that array, so calls whose work overlaps on the GPU (other streams, other
  * threads) race; each call rewrites all the entries it reads.  The first call
  * on a device resolves the array's device address, so make it before any
- * stream capture.  *err (optional) receives a static message on failure. */
+ * stream capture.  That address is cached for the life of the process: after
+ * cudaDeviceReset (or any other reset of the device's primary context) it no
+ * longer belongs to the array, so do not call this function on that device
+ * again in the same process.  *err (optional) receives a static message on
+ * failure. */
 int pb_coulomb_energy_noalloc(int device, const double *xyz, const double *q, int64_t nc, double eps,
                               double *energy, void *stream, const char **err);
 

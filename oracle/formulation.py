@@ -8,7 +8,7 @@ dphi_1/dn at the panel centroids and the 2N x 2N system is
     [ 1/2 I + K_L      -V_L          ] [ phi   ]   [ Q ]
     [ 1/2 I - K_Y   (eps1/eps2) V_Y  ] [ dphi  ] = [ 0 ].
 
-Readings where the paper is garbled or silent (all listed in the design doc):
+Readings where the paper is garbled or silent (Sec. 2.1 Eqs. nBEM, reac_integral; Sec. 2.2 Eqs. nBEM_disc, matrix, matel):
   * The ratio on V_Y is eps1/eps2 (Eqs. nBEM_disc and matrix); the eps2/eps1
     printed in Eq. nBEM contradicts flux continuity and is read as a typo.
   * Every kernel, Q and phi_reac keep the 1/(4 pi) of Eqs. nBEM/nBEM_disc

@@ -264,7 +264,8 @@ __device__ __forceinline__ void comp_add(float &hi, float &lo, float v) {
 // pairs that sum over it.  The leaf's sources are staged 32 at a time in
 // shared memory and broadcast; every lane owns one target.  FP32 partial sums
 // per 32-source chunk go into compensated (hi, lo) pairs; the pair's result is
-// stored in FP64 at its grouped position.
+// the FP32 sum hi + lo, rounded once into an FP32 float2 record (one value per
+// row kernel) at its grouped position.
 // MASK: skip the target's own panel (needed when a rule point sits at the
 // centroid); without it the own points stay in and the self value is corrected.
 template <int NK, bool Y0, bool Y1, bool MASK>

@@ -55,9 +55,12 @@ def layered_sphere_problem(level=3, a=4.0, b=6.0, stern_level=None, eps=(4.0, 80
     }
 
 
-def cavity_sphere_problem(level=3, eps_cav=80.0):
-    """Cavity r < 1.5 | protein shell to 4 | Stern to 6 | solvent, charge at 2.5 A."""
-    vc, tc = octasphere(max(level - 1, 1), 1.5)
+def cavity_sphere_problem(level=3, eps_cav=80.0, cavity_coarsening=1):
+    """Cavity r < 1.5 | protein shell to 4 | Stern to 6 | solvent, charge at 2.5 A.
+
+    The cavity sphere is meshed `cavity_coarsening` octasphere levels below the
+    two outer spheres (0: the same level, as a refinement study needs)."""
+    vc, tc = octasphere(max(level - cavity_coarsening, 1), 1.5)
     v1, t1 = octasphere(level, 4.0)
     v2, t2 = octasphere(level, 6.0)
     return {

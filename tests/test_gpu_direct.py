@@ -61,8 +61,33 @@ def test_direct_solve_energy_multisurface():
     r = pb.solve()
     ref = OD.solve_dense(d)
     assert abs(r.dG_solv - ref["dG"]) <= 1e-6 * abs(ref["dG"])
-    ex = layered_sphere_energy([4.0, 6.0], [4, 80, 80], [0, 0, 0.125], 0, d["charges"]["xyz"], d["charges"]["q"])
-    assert abs(r.dG_solv - ex) <= 2.5e-2 * abs(ex)
+
+
+@pytest.mark.parametrize("eps_s,kap_s,kap_o", [(80.0, 0.0, 0.125), (20.0, 0.0, 0.125), (80.0, 0.05, 0.25)])
+def test_direct_stern_layer_richardson(eps_s, kap_s, kap_o):
+    # the oracle's Stern-layer pin through the CUDA path: three meshes, observed
+    # order ~1 (Eq. observed_order), Richardson value (Eq. rich_extr) within 2e-4
+    # of the layered-sphere series (a wrong Stern kappa or eps is >= 2.5e-3 away)
+    eps, kap = (4.0, eps_s, 80.0), (0.0, kap_s, kap_o)
+    f = []
+    for lv in (2, 3, 4):
+        d = layered_sphere_problem(level=lv, eps=eps, kappa=kap, charges="both")
+        f.append(problem(d, gmres_tol=1e-10, **DIRECT).solve().dG_solv)
+    p = np.log((f[0] - f[1]) / (f[1] - f[2])) / np.log(4.0)
+    rich = f[2] + (f[2] - f[1]) / (4.0 ** p - 1.0)
+    ex = layered_sphere_energy([4.0, 6.0], eps, kap, 0, d["charges"]["xyz"], d["charges"]["q"])
+    assert 0.9 < p < 1.1
+    assert abs(rich - ex) <= 2e-4 * abs(ex)
+
+
+def test_direct_cavity_richardson():
+    f = [problem(cavity_sphere_problem(level=lv, cavity_coarsening=0), gmres_tol=1e-10, **DIRECT).solve().dG_solv
+         for lv in (2, 3, 4)]
+    p = np.log((f[0] - f[1]) / (f[1] - f[2])) / np.log(4.0)
+    rich = f[2] + (f[2] - f[1]) / (4.0 ** p - 1.0)
+    ex = layered_sphere_energy([1.5, 4.0, 6.0], [80, 4, 80, 80], [0, 0, 0, 0.125], 1, [[2.5, 0, 0]], [1.0])
+    assert 0.9 < p < 1.2
+    assert abs(rich - ex) <= 5e-4 * abs(ex)
 
 
 def test_coulomb_energy():

@@ -11,6 +11,7 @@ from scipy import integrate
 
 from oracle import formulation as F
 from oracle.cdense import DenseOperator
+from oracle.cdense import solve as cdense_solve
 from oracle.closed_forms import kirkwood_energy, layered_sphere_energy
 from oracle.dense import (KJ_PER_MOL, SurfaceData, coulomb_energy, kernel_matrices,
                           operator_matrix, rhs, solve_dense)
@@ -116,20 +117,95 @@ def test_superposition():
     assert np.allclose(ra["x"] + rb["x"], rab["x"], rtol=0, atol=1e-13 * np.abs(rab["x"]).max())
 
 
-def test_stern_layer_vs_layered_closed_form():
-    pr = layered_sphere_problem(level=3, charges="both")
-    r = solve_dense(pr)
-    ex = layered_sphere_energy([4.0, 6.0], [4, 80, 80], [0, 0, 0.125], 0, pr["charges"]["xyz"],
-                               pr["charges"]["q"])
-    assert abs(r["dG"] - ex) < 2.5e-2 * abs(ex)
+def _refinement_study(make, levels=(2, 3, 4)):
+    """Energies on three meshes (panel area / 4 per level), the observed order
+    (Eq. observed_order) and the Richardson value (Eq. rich_extr)."""
+    f = [cdense_solve(make(lv), tol=1e-10)["dG"] for lv in levels]
+    p = np.log((f[0] - f[1]) / (f[1] - f[2])) / np.log(4.0)
+    return f, p, f[2] + (f[2] - f[1]) / (4.0 ** p - 1.0)
 
 
-def test_cavity_vs_layered_closed_form():
-    pr = cavity_sphere_problem(level=3)
-    r = solve_dense(pr)
-    ex = layered_sphere_energy([1.5, 4.0, 6.0], [80, 4, 80, 80], [0, 0, 0, 0.125], 1,
-                               [[2.5, 0, 0]], [1.0])
-    assert abs(r["dG"] - ex) < 3e-2 * abs(ex)
+XY2 = [[0.0, 0.0, 0.0], [2.0, 0.0, 0.0]]
+# (Stern eps, Stern kappa, solvent kappa): the configuration's Stern layer
+# (eps_solvent, kappa 0, Sec. 2.2 "Multi-surface problems"), a high-contrast one
+# (eps 20) and a screened one (Yukawa kernels on both sides of the Stern surface)
+STERN_CASES = [(80.0, 0.0, 0.125), (20.0, 0.0, 0.125), (80.0, 0.05, 0.25)]
+STERN_TOL = 2e-4
+
+
+@pytest.mark.parametrize("eps_s,kap_s,kap_o", STERN_CASES)
+def test_stern_layer_richardson_vs_layered_closed_form(eps_s, kap_s, kap_o):
+    # the extrapolated energy must land on the layered-sphere series well inside
+    # the gap to what a wrong kernel choice for the Stern blocks would give
+    eps, kap = (4.0, eps_s, 80.0), (0.0, kap_s, kap_o)
+    ex = layered_sphere_energy([4.0, 6.0], eps, kap, 0, XY2, [1.0, 1.0])
+    wrong = [layered_sphere_energy([4.0, 6.0], eps, (0.0, kap_o, kap_o), 0, XY2, [1.0, 1.0]),
+             layered_sphere_energy([4.0, 6.0], (4.0, 80.0, 80.0), kap, 0, XY2, [1.0, 1.0]),
+             kirkwood_energy(4.0, 4.0, 80.0, kap_o, XY2, [1.0, 1.0])]
+    gaps = [abs(w - ex) / abs(ex) for w in wrong if w != ex]
+    assert min(gaps) > 5 * STERN_TOL
+    f, p, rich = _refinement_study(lambda lv: layered_sphere_problem(level=lv, eps=eps, kappa=kap, charges="both"))
+    assert 0.9 < p < 1.1
+    assert abs(rich - ex) < STERN_TOL * abs(ex)
+
+
+def _planted(monkeypatch, kappa_from=None, eps_from=None):
+    """Plant a mistake in the oracle's multi-surface rule: the Stern region (1)
+    takes the solvent's (2) kappa in its kernels, or its eps in the c factors."""
+    if kappa_from is not None:
+        orig_blocks = F.blocks
+
+        def blocks(problem):
+            return [F.Block(b.s, kappa_from if b.R == 1 else b.R, b.row_side, b.t, b.sigma, b.c)
+                    for b in orig_blocks(problem)]
+        monkeypatch.setattr(F, "blocks", blocks)
+    if eps_from is not None:
+        orig_sc = F.sigma_c
+
+        def sigma_c(problem, R, t):
+            sg, c = orig_sc(problem, R, t)
+            if R == 1 and sg < 0:
+                eps = [r["eps"] for r in problem["regions"]]
+                c = eps[problem["surfaces"][t]["inner"]] / eps[eps_from]
+            return sg, c
+        monkeypatch.setattr(F, "sigma_c", sigma_c)
+
+
+@pytest.mark.parametrize("mistake", ["stern_kappa", "stern_eps"])
+def test_stern_pin_catches_a_planted_mistake(monkeypatch, mistake):
+    # the same study with the Stern blocks given the solvent's kappa (configuration
+    # case) or eps (high-contrast case) misses the closed form by far more than the bound
+    eps_s = 80.0 if mistake == "stern_kappa" else 20.0
+    eps, kap = (4.0, eps_s, 80.0), (0.0, 0.0, 0.125)
+    ex = layered_sphere_energy([4.0, 6.0], eps, kap, 0, XY2, [1.0, 1.0])
+    _planted(monkeypatch, kappa_from=2 if mistake == "stern_kappa" else None,
+             eps_from=2 if mistake == "stern_eps" else None)
+    f, p, rich = _refinement_study(lambda lv: layered_sphere_problem(level=lv, eps=eps, kappa=kap, charges="both"))
+    assert abs(rich - ex) > 5 * STERN_TOL * abs(ex)
+
+
+def test_layered_closed_form_centred_charge():
+    # a centred charge sees only the n = 0 term: phi_reac(0) = sum over interfaces
+    # of (1/eps_outer - 1/eps_inner)/a, with 1/(eps (1 + kappa a)) for a screened outer region
+    for eps_s in (80.0, 20.0):
+        ex = layered_sphere_energy([4.0, 6.0], [4.0, eps_s, 80.0], [0.0, 0.0, 0.125], 0, [[0, 0, 0]], [1.0])
+        phi = (1 / eps_s - 1 / 4.0) / 4.0 + (1 / (80.0 * (1 + 0.125 * 6.0)) - 1 / eps_s) / 6.0
+        assert abs(ex - 0.5 * KJ_PER_MOL * phi) < 1e-12 * abs(ex)
+    # a Stern layer with the solvent's eps and kappa reduces to Kirkwood exactly
+    for x in ([[0, 0, 0]], XY2):
+        q = np.ones(len(x))
+        a = layered_sphere_energy([4.0, 6.0], [4, 80, 80], [0, 0.125, 0.125], 0, x, q)
+        assert abs(a - kirkwood_energy(4, 4, 80, 0.125, x, q)) < 1e-11 * abs(a)
+
+
+def test_cavity_richardson_vs_layered_closed_form():
+    # cavity r < 1.5 (eps 80) inside the protein shell, Stern layer to 6 A; the
+    # charge sits 1 A from the cavity, so three levels reach order ~1.1 and the
+    # extrapolation ~2e-4; an absent cavity (eps_cav = eps_protein) is 18% away
+    ex = layered_sphere_energy([1.5, 4.0, 6.0], [80, 4, 80, 80], [0, 0, 0, 0.125], 1, [[2.5, 0, 0]], [1.0])
+    f, p, rich = _refinement_study(lambda lv: cavity_sphere_problem(level=lv, cavity_coarsening=0))
+    assert 0.9 < p < 1.2
+    assert abs(rich - ex) < 5e-4 * abs(ex)
 
 
 def test_invisible_interfaces():
