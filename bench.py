@@ -181,6 +181,17 @@ def _problem():
     return protein_problem()
 
 
+def _oracle_golden(d):
+    """The oracle's stored energy of the benchmark protein (tests/golden/protein40k.json),
+    if the file is there and was made on the same mesh."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "protein40k.json")) as f:
+            g = json.load(f)
+    except OSError:
+        return None
+    return g if g["mesh"][0]["n_panels"] == int(d["surfaces"][0]["tris"].shape[0]) else None
+
+
 FLEET = 64          # ligands of the batched-solve measurement
 TRIPLET = (8000, 1500)
 
@@ -267,10 +278,52 @@ def cpu_baseline(d):
     t0 = time.perf_counter()
     op.apply(x, {0: sample})
     t = time.perf_counter() - t0
-    return {"value": sample.size * ns / t / 1e9, "unit": "Ginteractions/s",
-            "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-            "sample": f"dense FP64 matrix-free operator: {sample.size} of {n} target rows against all {ns} "
-                      f"Gauss points, Laplace and Yukawa kernels ({t:.1f} s)"}
+    value = sample.size * ns / t / 1e9
+    out = {"value": value, "unit": "Ginteractions/s",
+           "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+           "sample": f"dense FP64 matrix-free operator: {sample.size} of {n} target rows against all {ns} "
+                     f"Gauss points, Laplace and Yukawa kernels ({t:.1f} s)"}
+    out["one_core"] = _oracle_one_core(512)
+    g = _oracle_golden(d)
+    if g:
+        # one operator application per GMRES iteration plus one per cycle start
+        applications = g["iterations"] + (g["iterations"] + PARAMS["restart"] - 1) // PARAMS["restart"] + 1
+        out["full_solve"] = {
+            "recorded_s": g["seconds"], "recorded_cores": g["host_cores"], "gmres_tol": g["gmres_tol"],
+            "iterations": g["iterations"],
+            "estimated_s_on_these_cores": applications * n * ns / (value * 1e9),
+            "note": "setup + GMRES + energy of the dense oracle; recorded when tests/golden/protein40k.json "
+                    "was written, estimated here from the sampled all-core rate"}
+    return out
+
+
+_ONE_CORE = r"""
+import sys, time
+import numpy as np
+sys.path.insert(0, {root!r})
+from oracle.cdense import DenseOperator
+from synth.configs import protein_problem
+op = DenseOperator(protein_problem(), {params!r})
+n = op.sd[0].n
+rows = np.linspace(0, n - 1, {m}).astype(np.int64)
+x = np.random.default_rng(0).normal(size=op.n)
+op.apply(x, {{0: rows[:4]}})
+t0 = time.perf_counter()
+op.apply(x, {{0: rows}})
+print(rows.size * n * {K} / (time.perf_counter() - t0) / 1e9)
+"""
+
+
+def _oracle_one_core(m):
+    """The oracle's sampled operator rate on one host core (OMP_NUM_THREADS=1, child process)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    code = _ONE_CORE.format(root=ROOT, params=PARAMS, m=m, K=PARAMS["K"])
+    try:
+        p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        return {"value": float(p.stdout.strip().splitlines()[-1]), "unit": "Ginteractions/s", "cores": 1,
+                "sample": f"{m} target rows against all Gauss points"}
+    except (subprocess.SubprocessError, ValueError, IndexError) as e:
+        return {"value": None, "error": str(e)[:200]}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -371,11 +424,28 @@ def run_gpu(args):
     d2h = 8 * (2 + cycles + r2.iterations)
     e2e_val = ws * r2.p2p_pairs * r2.matvecs / float(np.mean(e2e_t)) / 1e9
 
-    # FP64 treecode on the same GPU and the energy error of the mixed form
+    # The metric's second half: the plain FP64 treecode on the same GPU at the
+    # same tolerance (1e-4, equal energy error: the same tree, lists and
+    # truncation), timed like the mixed steps; the oracle's energy decides
+    # whether both meet the 1e-4 bar.  The FP64 solve at tol 1e-8 is kept as a
+    # separately labelled extra.
+    mixed_s = t_total / args.steps
     p64 = make_problem()
+    step64 = lambda: (p64.setup(precision="fp64", **PARAMS), p64.solve())[1]
+    step64()
+    t64 = []
+    for _ in range(3):
+        flush.zero_()
+        torch.cuda.synchronize()
+        r64 = step64()
+        t64.append((r64.setup_ms + r64.solve_ms) / 1e3)
     p64.setup(precision="fp64", **dict(PARAMS, gmres_tol=1e-8))
-    r64 = p64.solve()
-    rel_err = abs(r.dG_solv - r64.dG_solv) / abs(r64.dG_solv)
+    r64t = p64.solve()
+    p64.close()
+    rel_err = abs(r.dG_solv - r64t.dG_solv) / abs(r64t.dG_solv)
+    golden = _oracle_golden(d)
+    dG_or = golden["dG"] if golden else None
+    rel_or = (lambda e: abs(e - dG_or) / abs(dG_or)) if golden else (lambda e: None)
 
     extras = {}
     if args.extras:
@@ -393,14 +463,23 @@ def run_gpu(args):
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "solve_time_s": r.solve_ms / 1e3 + r.setup_ms / 1e3,
             "setup_ms": r.setup_ms, "gmres_ms": r.solve_ms, "iterations": r.iterations, "matvecs": r.matvecs,
-            "dG_kJ_mol": r.dG_solv, "dG_rel_err_vs_fp64": rel_err,
+            "dG_kJ_mol": r.dG_solv, "dG_rel_err_vs_fp64": rel_err, "dG_rel_err_vs_oracle": rel_or(r.dG_solv),
+            "oracle": {"dG_kJ_mol": dG_or, "gmres_tol": golden["gmres_tol"] if golden else None,
+                       "source": "tests/golden/protein40k.json (dense FP64 oracle, GMRES, written by "
+                                 "tests/golden/make_golden.py)" if golden else "missing"},
             "p2p_pairs_per_matvec": r.p2p_pairs, "m2p_evals_per_matvec": r.m2p_pairs,
             "matvec_phase_ms": prof,
             "matvec_gint_per_s": r.p2p_pairs / (prof["total"] / 1e3) / 1e9,
             "dense_equivalent_gint_per_s": surf["tris"].shape[0] * nsrc / (prof["total"] / 1e3) / 1e9,
-            "fp64": {"solve_time_s": (r64.solve_ms + r64.setup_ms) / 1e3, "iterations": r64.iterations,
-                     "gmres_tol": 1e-8, "dG_kJ_mol": r64.dG_solv,
-                     "speedup_mixed_vs_fp64": (r64.solve_ms + r64.setup_ms) / (r.solve_ms + r.setup_ms)},
+            "fp64": {"solve_time_s": float(np.mean(t64)), "iterations": r64.iterations,
+                     "gmres_tol": PARAMS["gmres_tol"], "dG_kJ_mol": r64.dG_solv,
+                     "dG_rel_err_vs_oracle": rel_or(r64.dG_solv), "mixed_solve_time_s": mixed_s,
+                     "speedup_mixed_vs_fp64": float(np.mean(t64)) / mixed_s,
+                     "meets_1e-4_vs_oracle": {"mixed": rel_or(r.dG_solv) is not None and rel_or(r.dG_solv) <= 1e-4,
+                                              "fp64": rel_or(r64.dG_solv) is not None and rel_or(r64.dG_solv) <= 1e-4},
+                     "extra_tol_1e-8": {"solve_time_s": (r64t.solve_ms + r64t.setup_ms) / 1e3,
+                                        "iterations": r64t.iterations, "dG_kJ_mol": r64t.dG_solv,
+                                        "dG_rel_err_vs_oracle": rel_or(r64t.dG_solv)}},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "Ginteractions/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "seconds_per_step": float(np.mean(e2e_t))},
@@ -445,6 +524,7 @@ def _extras(pbbem, ctx, pb, r, d, fleet_members, triplet, variants):
     for p in probs:
         p.close()
     batch["autotuned"] = _autotuned_fleet(pbbem, ctx, fleet, bat)
+    batch["mixed_vs_fp64"] = _batched_fp64(pbbem, ctx, fleet[:16])
     tri = [pbbem.Problem.from_dict(ctx, t) for t in triplet]
     ts = time.perf_counter()
     for p in tri:
@@ -520,6 +600,34 @@ def _extras(pbbem, ctx, pb, r, d, fleet_members, triplet, variants):
     pl.close()
     return {"gradient": grad, "batch": batch, "binding": binding, "richardson": rich, "model_variants": models,
             "pareto": pareto, "surface": surface, "large_gradient": large}
+
+
+def _batched_fp64(pbbem, ctx, ligands):
+    """Batched solve time to the 1e-4 energy bar: setup + pb_solve_batch of the same
+    ligands in FP32-mixed and in plain FP64 at the same tolerance, tree and lists
+    (so the same truncation error), wall time after one untimed round each."""
+    def run(prec):
+        t = None
+        for _ in range(2):
+            probs = [pbbem.Problem.from_dict(ctx, f) for f in ligands]
+            ts = time.perf_counter()
+            for p in probs:
+                p.setup(precision=prec, **PARAMS)
+            res = pbbem.solve_batch(ctx, probs)
+            t = time.perf_counter() - ts
+            for p in probs:
+                p.close()
+        return t, res
+
+    tm, rm = run("mixed")
+    t64, r64 = run("fp64")
+    return {"workload": f"the first {len(ligands)} ligands of the fleet "
+                        f"({sum(int(f['surfaces'][0]['tris'].shape[0]) for f in ligands)} panels)",
+            "gmres_tol": PARAMS["gmres_tol"], "mixed_setup_and_batch_s": tm, "fp64_setup_and_batch_s": t64,
+            "speedup_mixed_vs_fp64": t64 / tm,
+            "iterations_mixed": [x.iterations for x in rm], "iterations_fp64": [x.iterations for x in r64],
+            "max_rel_dG_diff_mixed_vs_fp64": float(max(abs(a.dG_solv - b.dG_solv) / abs(b.dG_solv)
+                                                       for a, b in zip(rm, r64)))}
 
 
 def _autotuned_fleet(pbbem, ctx, fleet, default_results):

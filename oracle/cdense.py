@@ -122,12 +122,25 @@ class DenseOperator:
         return out
 
 
-def solve(problem, params=None, tol=None):
-    """GMRES solve with the dense matrix-free operator; returns dict(x, dG, iters, resid)."""
+def solve(problem, params=None, tol=None, precond=False, log=None):
+    """GMRES solve with the dense matrix-free operator; returns dict(x, dG, iters, resid).
+
+    precond: right block-Jacobi preconditioner from the panels' 2x2 self blocks
+    (oracle.formulation.block_jacobi); it changes the iteration count, not the
+    solution, and keeps the stopping test on the true residual.
+    log: optional callable(str) told of every operator application."""
     op = DenseOperator(problem, params)
     b = rhs(problem, op.p, op.sd)
-    x, it, res, _ = gmres(op, b, tol=tol if tol is not None else op.p["gmres_tol"],
-                          restart=op.p["restart"], max_iter=op.p["max_iter"])
+    M = F.block_jacobi(problem, lambda s, k: op.sd[s].self_V(k, op.p["N_k"])) if precond else None
+    count = [0]
+
+    def apply(v):
+        count[0] += 1
+        if log is not None:
+            log(f"operator application {count[0]}")
+        return op(v)
+    x, it, res, _ = gmres(apply, b, tol=tol if tol is not None else op.p["gmres_tol"],
+                          restart=op.p["restart"], max_iter=op.p["max_iter"], M_inv=M)
     phr = op.phi_reac(x)
     dG = 0.5 * KJ_PER_MOL * float(np.dot(problem["charges"]["q"], FOUR_PI * phr))
     return dict(x=x, dG=dG, iters=it, resid=res, phi_reac=phr)

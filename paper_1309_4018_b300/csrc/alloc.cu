@@ -1,4 +1,6 @@
 // Caching allocator of the library's device and page-locked host blocks.
+#include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
 
@@ -34,9 +36,23 @@ void *take(Pool &pl, size_t bytes, size_t *got) {
 
 size_t round_up(size_t b) { return (b + 255) / 256 * 256; }
 
+// Host-side fault injection for tests of the error paths: with the environment
+// variable PB_FAULT=alloc:N set when the library is loaded, the N-th device
+// allocation request (counted from 1 over the whole process) fails with
+// PB_ENOMEM as if cudaMalloc had run out of memory.  Nothing reaches the GPU.
+long long fault_alloc_at() {
+    const char *e = std::getenv("PB_FAULT");
+    if (!e || std::strncmp(e, "alloc:", 6) != 0) return 0;
+    return std::atoll(e + 6);
+}
+const long long g_fault_at = fault_alloc_at();
+std::atomic<long long> g_alloc_requests{0};
+
 }  // namespace
 
 void *cached_device_alloc(size_t bytes, size_t *got) {
+    if (g_fault_at > 0 && g_alloc_requests.fetch_add(1) + 1 == g_fault_at)
+        throw Error{PB_ENOMEM, "injected allocation failure (PB_FAULT=alloc:" + std::to_string(g_fault_at) + ")"};
     int dev = 0;
     PB_CUDA_TRY(cudaGetDevice(&dev));
     bytes = round_up(bytes);

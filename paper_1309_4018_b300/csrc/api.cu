@@ -11,6 +11,7 @@
 #include "geometry.cuh"
 #include "gmres.cuh"
 #include "model.cuh"
+#include "validate.cuh"
 #include "problem.cuh"
 #include "surface.cuh"
 #include "tree.cuh"
@@ -172,6 +173,32 @@ void setup_problem(pb_problem *pb) {
     for (int t = 0; t < ns; ++t) build_targets(pb->G[t], pb->S[t].cen.p, pb->S[t].n, t, s);
     const int64_t nc = (int64_t)pb->cq.size();
     build_targets(pb->G[ns], pb->cxyz_d.p, nc, -1, s);
+    // the charges must lie in their region: inside every surface that has it as
+    // inner region, outside every surface that has it as outer region
+    int n_wind = 0;
+    if (nc > 0) {
+        std::vector<int32_t> expect;
+        std::vector<int> wsurf;
+        for (int t = 0; t < ns; ++t)
+            if (pb->S[t].inner == pb->cregion || pb->S[t].outer == pb->cregion) {
+                wsurf.push_back(t);
+                expect.push_back(pb->S[t].inner == pb->cregion ? 1 : 0);
+            }
+        n_wind = (int)wsurf.size();
+        if (n_wind > 8) fail(PB_EINVAL, "the charged region is bounded by more than 8 surfaces");
+        if (n_wind > 0) {
+            pb->wind.alloc(n_wind * nc);
+            pb->wind.zero(s);
+            for (int k = 0; k < n_wind; ++k)
+                winding_numbers(pb->S[wsurf[k]].verts.p, pb->S[wsurf[k]].tris.p, pb->S[wsurf[k]].n, pb->cxyz_d.p,
+                                nc, pb->wind.p + k * nc, s);
+            pb->wind_bad.alloc(3);
+            pb->wind_bad_h.alloc(3);
+            winding_mismatch(pb->wind.p, nc, n_wind, expect.data(), pb->wind_bad.p, s);
+            PB_CUDA_TRY(cudaMemcpyAsync(pb->wind_bad_h.p, pb->wind_bad.p, 3 * sizeof(int32_t),
+                                        cudaMemcpyDeviceToHost, s));
+        }
+    }
     // block structure (multi-surface rule): row (s, R) gets sigma (K - c V) of every t in dR
     pb->rows.assign(2 * ns, {});
     auto eps = [&](int R) { return pb->regions[R].eps; };
@@ -310,6 +337,12 @@ void setup_problem(pb_problem *pb) {
         }
     PB_CUDA_TRY(cudaEventRecord(pb->ev1, s));
     PB_CUDA_TRY(cudaEventSynchronize(pb->ev1));
+    if (n_wind > 0 && pb->wind_bad_h.p[0] > 0) {
+        const int32_t *bad = pb->wind_bad_h.p;
+        fail(PB_EINVAL, std::to_string(bad[0]) + " charge(s) lie outside their region (first: charge " +
+                            std::to_string(bad[1]) + ", against surface " +
+                            std::to_string(bad[2] < n_wind ? bad[2] : -1) + " of the region's boundary)");
+    }
     float ms = 0.f;
     PB_CUDA_TRY(cudaEventElapsedTime(&ms, pb->ev0, pb->ev1));
     pb->setup_ms = ms;
@@ -879,6 +912,7 @@ int pb_add_surface(pb_problem *pb, const double *verts, int64_t nv, const int32_
             if (!std::isfinite(verts[i])) fail(PB_EINVAL, "non-finite vertex coordinate");
         for (int64_t i = 0; i < 3 * nt; ++i)
             if (tris[i] < 0 || tris[i] >= nv) fail(PB_EINVAL, "triangle vertex index out of range");
+        check_closed_mesh(verts, nv, tris, nt);
         set_device(pb->ctx);
         SurfIn si;
         si.nv = nv;

@@ -83,6 +83,8 @@ struct pb_problem {
     int64_t N = 0;
     pb::DevBuf<double> b, x, y, r, xin, yout, z1, z2, minv;
     pb::DevBuf<double> cq_d, cxyz_d, phi_reac, energy;
+    pb::DevBuf<int32_t> wind, wind_bad;      // charge-region check: winding numbers, mismatch record
+    pb::PinnedBuf<int32_t> wind_bad_h;
     pb::Gmres gm;
     double setup_ms = 0.0;
     bool have_solution = false;

@@ -8,6 +8,7 @@ there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import functools
 import os
 from dataclasses import dataclass
 
@@ -420,15 +421,18 @@ class Problem:
         self.close()
 
 
+@functools.lru_cache(maxsize=1)
 def _energy_autograd():
     import torch
 
     class Energy(torch.autograd.Function):
         """Solvation energy (kJ/mol) as a differentiable function of (q, xyz, eps, kappa).
 
-        forward(problem_dict, q [nc], xyz [nc,3], eps [n_regions], kappa [n_regions], ctx=None, **params)
-        builds the problem with these values, sets it up, solves it and keeps the
-        adjoint gradient (pb_gradient) for backward.  The mesh is held fixed.
+        forward(problem_dict, q [nc], xyz [nc,3], eps [n_regions], kappa [n_regions], context=None, params=None)
+        builds the problem with these values, sets it up and solves it (Eq. solv).
+        When an input needs a gradient the set-up problem is kept, and backward
+        runs the adjoint solve (pb_gradient) once, on its first call; a forward
+        that no backward follows costs one solve.  The mesh is held fixed.
         """
 
         @staticmethod
@@ -442,16 +446,21 @@ def _energy_autograd():
             pb = Problem.from_dict(c, d)
             pb.setup(**(params or {}))
             r = pb.solve()
-            g = pb.gradient()
-            pb.close()
-            fctx.save_for_backward(*[torch.as_tensor(g[k], dtype=q.dtype, device=q.device)
-                                     for k in ("dq", "dxyz", "deps", "dkappa")])
+            if any(fctx.needs_input_grad[1:5]):
+                fctx.pb = pb
+            else:
+                pb.close()
+            fctx.like = (q.dtype, q.device)
             return torch.as_tensor(r.dG_solv, dtype=q.dtype, device=q.device)
 
         @staticmethod
         def backward(fctx, gout):
-            dq, dxyz, deps, dkap = fctx.saved_tensors
-            return None, gout * dq, gout * dxyz, gout * deps, gout * dkap, None, None
+            g = fctx.pb.gradient()
+            fctx.pb.close()
+            fctx.pb = None
+            dt, dev = fctx.like
+            out = [gout * torch.as_tensor(g[k], dtype=dt, device=dev) for k in ("dq", "dxyz", "deps", "dkappa")]
+            return (None, *out, None, None)
 
     return Energy
 

@@ -80,11 +80,15 @@ STERN_SPACING = 1.16        # ~60k panels for the +2 A Stern surface of the seed
 
 
 @functools.lru_cache(maxsize=8)
-def protein_atoms(n_atoms=2000, seed=2, cavities=False):
+def protein_atoms(n_atoms=2000, seed=2, cavities=False, cavity_x=7.0, cavity_r=3.0):
+    """Atoms of a synthetic protein; with `cavities`, atom centres keep
+    cavity_r + 2.0 + 1.4 A away from (+-cavity_x, 0, 0) to leave room for two
+    solvent-filled cavities of radius cavity_r."""
     radius = 20.0 * (n_atoms / 2000.0) ** (1.0 / 3.0)
     exclude = ()
     if cavities:
-        exclude = (((7.0, 0.0, 0.0), 3.0 + 2.0 + 1.4), ((-7.0, 0.0, 0.0), 3.0 + 2.0 + 1.4))
+        gap = cavity_r + 2.0 + 1.4
+        exclude = (((cavity_x, 0.0, 0.0), gap), ((-cavity_x, 0.0, 0.0), gap))
     return synthetic_atoms(n_atoms, radius, seed, exclude=exclude)
 
 
@@ -100,17 +104,18 @@ def protein_problem(n_atoms=2000, seed=2, spacing=PROTEIN_SPACING):
 
 
 def multisurface_problem(n_atoms=2000, seed=3, spacing=PROTEIN_SPACING,
-                         stern_spacing=STERN_SPACING, cavity_level=3):
-    """Protein SES + Stern surface (+2 A) + two 3 A solvent-filled cavities.
+                         stern_spacing=STERN_SPACING, cavity_level=3, cavity_x=7.0, cavity_r=3.0):
+    """Protein SES + Stern surface (+2 A) + two solvent-filled cavities of
+    radius cavity_r at (+-cavity_x, 0, 0) (3 A at +-7 A for the 2,000-atom molecule).
 
     Regions: 0 cav1, 1 cav2, 2 protein (charged), 3 Stern (eps_out, kappa 0),
     4 solvent (eps_out, kappa).  Surfaces: C1, C2, SES, Stern.
     """
-    at = protein_atoms(n_atoms, seed, cavities=True)
+    at = protein_atoms(n_atoms, seed, cavities=True, cavity_x=cavity_x, cavity_r=cavity_r)
     vs, ts = gaussian_surface(at["xyz"], at["radius"], spacing)
     vt, tt = gaussian_surface(at["xyz"], at["radius"], stern_spacing, radius_offset=2.0)
-    c1v, c1t = icosphere(cavity_level, 3.0, (7.0, 0.0, 0.0))
-    c2v, c2t = icosphere(cavity_level, 3.0, (-7.0, 0.0, 0.0))
+    c1v, c1t = icosphere(cavity_level, cavity_r, (cavity_x, 0.0, 0.0))
+    c2v, c2t = icosphere(cavity_level, cavity_r, (-cavity_x, 0.0, 0.0))
     return {
         "regions": [{"eps": EPS_OUT, "kappa": 0.0}, {"eps": EPS_OUT, "kappa": 0.0},
                     {"eps": EPS_IN, "kappa": 0.0}, {"eps": EPS_OUT, "kappa": 0.0},
@@ -223,12 +228,13 @@ def protein_refinements(levels=2, spacing=2.0 * PROTEIN_SPACING, n_atoms=2000, s
     return out
 
 
-def model_variants(n_atoms=2000, seed=3, spacing=PROTEIN_SPACING, stern_spacing=STERN_SPACING, cavity_level=3):
+def model_variants(n_atoms=2000, seed=3, spacing=PROTEIN_SPACING, stern_spacing=STERN_SPACING, cavity_level=3,
+                   cavity_x=7.0, cavity_r=3.0):
     """The four solvent models of the multi-surface molecule (the paper's Single /
     Cavity / Stern / Full comparison) on the same atoms and meshes:
     single: molecular surface only; cavity: + the two solvent-filled cavities;
     stern: + the Stern layer; full: all four surfaces (= multisurface_problem)."""
-    full = multisurface_problem(n_atoms, seed, spacing, stern_spacing, cavity_level)
+    full = multisurface_problem(n_atoms, seed, spacing, stern_spacing, cavity_level, cavity_x, cavity_r)
     c1, c2, ses, stern = full["surfaces"]
     ch = full["charges"]
     ew, eo, kap = EPS_OUT, EPS_IN, KAPPA
@@ -245,6 +251,18 @@ def model_variants(n_atoms=2000, seed=3, spacing=PROTEIN_SPACING, stern_spacing=
                  [dict(ses, inner=0, outer=1), dict(stern, inner=1, outer=2)], 0)
     return {"single": single, "cavity": cavity, "stern": stern_m, "full": full}
 
+
+
+# Reduced multi-surface molecule, small enough for the dense oracle to solve
+# its four model variants on host cores in minutes: 400 atoms (ball radius
+# 11.7 A), two 2 A cavities at (+-4.5, 0, 0) meshed as 320-panel icospheres,
+# SES and Stern surface on a 1.4 A grid (10,324 + 19,568 + 2 x 320 panels).
+REDUCED_MULTISURFACE = dict(n_atoms=400, seed=3, spacing=1.4, stern_spacing=1.4, cavity_level=2,
+                            cavity_x=4.5, cavity_r=2.0)
+
+
+def reduced_model_variants():
+    return model_variants(**REDUCED_MULTISURFACE)
 
 
 def large_protein_problem(n_atoms=30000, seed=2, spacing=0.8):
