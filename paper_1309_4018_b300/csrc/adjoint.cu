@@ -479,7 +479,8 @@ __device__ void m2pT_eval_rt(int P, T ux, T uy, T uz, T nx, T ny, T nz, T kappa,
 // Box-major: one warp per (box, up to 32 targets) item.
 template <int P, bool YUK, typename T>
 __global__ void __launch_bounds__(128) m2pT_kernel(int64_t nitems, const int4 *__restrict__ items,
-                                                   const int32_t *__restrict__ inv, int Prt,
+                                                   const int32_t *__restrict__ inv,
+                                                   const int32_t *__restrict__ ent, int Prt,
                                                    const double *__restrict__ xs, const float4 *__restrict__ x32,
                                                    const double *__restrict__ n64, const float4 *__restrict__ n32,
                                                    const double *__restrict__ centre,
@@ -513,7 +514,7 @@ __global__ void __launch_bounds__(128) m2pT_kernel(int64_t nitems, const int4 *_
     T V, K;
     if constexpr (P >= 0) m2pT_eval<(P >= 0 ? P : 0), YUK, T>(ux, uy, uz, nx, ny, nz, (T)kappa, mM, mM + NT, V, K);
     else m2pT_eval_rt<YUK, T>(Prt, ux, uy, uz, nx, ny, nz, (T)kappa, mM, mM + NT, V, K);
-    T *rec = part + (int64_t)2 * nk * slot + 2 * kslot;
+    T *rec = part + (int64_t)2 * nk * ent[slot] + 2 * kslot;
     rec[0] = V;
     rec[1] = K;
 }
@@ -562,7 +563,8 @@ __global__ void radialT_moments_kernel(int nnodes, const float *__restrict__ mom
 
 template <int P>
 __global__ void __launch_bounds__(128) m2pT_ly32_kernel(int64_t nitems, const int4 *__restrict__ items,
-                                                        const int32_t *__restrict__ inv, const float4 *__restrict__ x32,
+                                                        const int32_t *__restrict__ inv,
+                                                        const int32_t *__restrict__ ent, const float4 *__restrict__ x32,
                                                         const float4 *__restrict__ n32, const float4 *__restrict__ cen32,
                                                         const float *__restrict__ rmom, float kappa,
                                                         float4 *__restrict__ part) {
@@ -655,7 +657,7 @@ __global__ void __launch_bounds__(128) m2pT_ly32_kernel(int64_t nitems, const in
         KL = fmaf(FL[m], GL[m], fmaf(nu * FL[m + 1], HL[m], KL));
         KY = fmaf(FY[m], GY[m], fmaf(nu * FY[m + 1], HY[m], KY));
     }
-    part[slot] = make_float4(VL, -KL, VY, -KY);
+    part[ent[slot]] = make_float4(VL, -KL, VY, -KY);
 }
 
 // ---------------------------------------------------------------- transposed near list
@@ -1567,7 +1569,8 @@ void launch_m2pT_typed(int P, bool yuk, const TPair &tp, const Targets &G, const
     const int64_t stride = (int64_t)2 * tp.nk * nterms(P);
     const double kap = Pr.kappas[kslot];
 #define PB_M2PT_ARGS \
-    ni, Pr.m2p_items.p, Pr.m2p_inv.p, P, G.xs.p, Pr.x32.p, n64, n32, Tr.centre.p, Tr.cen32.p, mom, stride, kap, kslot, \
+    ni, Pr.m2p_items.p, Pr.m2p_inv.p, Pr.m2p_ent.p, P, G.xs.p, Pr.x32.p, n64, n32, Tr.centre.p, Tr.cen32.p, mom,   \
+        stride, kap, kslot, \
         tp.nk, part
 #define PB_M2PT_CASE(PP)                                                      \
     case PP:                                                                  \
@@ -1612,7 +1615,8 @@ void launch_m2pT_radial(int P, TPair &tp, const Targets &G, const float4 *n32, c
     case PP:                                                                                                    \
         radialT_moments_kernel<PP><<<gt, 128, 0, s>>>(Tr.nnodes, tp.mom32.p, tp.rmom32.p);                      \
         PB_LAUNCH_CHECK();                                                                                      \
-        m2pT_ly32_kernel<PP><<<grid, 128, 0, s>>>(ni, Pr.m2p_items.p, Pr.m2p_inv.p, Pr.x32.p, n32, Tr.cen32.p,  \
+        m2pT_ly32_kernel<PP><<<grid, 128, 0, s>>>(ni, Pr.m2p_items.p, Pr.m2p_inv.p, Pr.m2p_ent.p, Pr.x32.p, n32, \
+                                                  Tr.cen32.p,                                                    \
                                                   tp.rmom32.p, kap, part);                                      \
         break;
     switch (P) { PB_RT(1) PB_RT(2) PB_RT(3) PB_RT(4) PB_RT(5) PB_RT(6) PB_RT(7) PB_RT(8) default: break; }

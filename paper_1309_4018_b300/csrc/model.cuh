@@ -89,13 +89,12 @@ struct Pair {
     // work item (one warp); every pair writes one partial sum, and a gather
     // adds each target's partials in its own list order.
     DevBuf<int32_t> p2p_inv, m2p_inv;     // target of every grouped (target, entry) pair
-    DevBuf<int32_t> p2p_ent;              // P2P: grouped position -> CSR entry (where its record goes)
-    DevBuf<int32_t> m2p_pos;              // M2P: CSR entry -> grouped position (where its record is)
+    DevBuf<int32_t> p2p_ent, m2p_ent;     // grouped position -> CSR entry (where its record goes)
     DevBuf<int4> p2p_items, m2p_items;    // (leaf | box, grouped start, count <= 32, 0)
     int64_t n_p2p_items = 0, n_m2p_items = 0;
     // partial records, interleaved per entry: (V, K) of every kernel (2 nk
-    // values); P2P records at their CSR entries (each target's contiguous),
-    // M2P records at their grouped positions (the box-major writes stay coalesced)
+    // values), P2P and M2P records at their CSR entries: each target's records
+    // are contiguous, so the gather reads them with coalesced loads and no index
     DevBuf<double> p2p_part, m2p_part64;
     DevBuf<float> p2p_part32, m2p_part32;
     DevBuf<float> dV32, dK32;             // mixed path: near corrections in FP32, kernel-major

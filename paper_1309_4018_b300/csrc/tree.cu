@@ -1007,7 +1007,7 @@ void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &pr
         PB_LAUNCH_CHECK();
         PB_CUDA_TRY(cudaMemcpyAsync(Pr.p2p_items.p, sorted.p, ni * sizeof(int4), cudaMemcpyDeviceToDevice, s));
     }
-    group(Pr.m2p_ptr.p, Pr.m2p_node.p, nullptr, T.nnodes, Pr.n_m2p, 32, 0, Pr.m2p_inv, Pr.m2p_pos, Pr.m2p_items,
+    group(Pr.m2p_ptr.p, Pr.m2p_node.p, nullptr, T.nnodes, Pr.n_m2p, 32, 1, Pr.m2p_inv, Pr.m2p_ent, Pr.m2p_items,
           Pr.n_m2p_items);
 }
 

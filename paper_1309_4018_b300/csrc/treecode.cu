@@ -518,10 +518,11 @@ __device__ void m2p_eval_rt(int P, T ux, T uy, T uz, T kappa, const T *__restric
 // Box-major: one warp per work item = one accepted box and up to 32
 // (target, entry) pairs that use it; the box's moments and centre are the
 // same for every lane, each lane runs the recurrences for its own target and
-// stores (V, K) at the pair's grouped position.
+// stores (V, K) at the pair's list entry.
 template <int P, bool YUK, typename T>
 __global__ void __launch_bounds__(128) m2p_kernel(int64_t nitems, const int4 *__restrict__ items,
-                                                  const int32_t *__restrict__ inv, int Prt,
+                                                  const int32_t *__restrict__ inv,
+                                                  const int32_t *__restrict__ ent, int Prt,
                                                   const double *__restrict__ xs, const float4 *__restrict__ x32,
                                                   const double *__restrict__ centre, const float4 *__restrict__ cen32,
                                                   const T *__restrict__ mom, double kappa, int kslot, int nk,
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__(128) m2p_kernel(int64_t nitems, const int4 *__
     if constexpr (P >= 0) m2p_eval<(P >= 0 ? P : 0), YUK, T>(ux, uy, uz, (T)kappa, mom + (int64_t)b * 2 * NT, V, K);
     else m2p_eval_rt<YUK, T>(Prt, ux, uy, uz, (T)kappa, mom + (int64_t)b * 2 * NT, V, K);
     // interleaved record of the entry: (V, K) of every kernel
-    T *rec = part + (int64_t)2 * nk * slot + 2 * kslot;
+    T *rec = part + (int64_t)2 * nk * ent[slot] + 2 * kslot;
     rec[0] = V;
     rec[1] = K;
 }
@@ -672,6 +673,7 @@ __device__ __forceinline__ void m2p_ly_eval(const float4 *R, const float (&ux)[N
 template <int P, int NI>
 __global__ void __launch_bounds__(128, 7) m2p_ly32x_kernel(int64_t nitems, const int4 *__restrict__ items,
                                                         const int32_t *__restrict__ inv,
+                                                        const int32_t *__restrict__ ent,
                                                         const float4 *__restrict__ x32,
                                                         const float4 *__restrict__ cen32,
                                                         const float *__restrict__ rmom, float kappa,
@@ -710,7 +712,7 @@ __global__ void __launch_bounds__(128, 7) m2p_ly32x_kernel(int64_t nitems, const
         m2p_ly_eval<P, NI>(R, ux, uy, uz, kappa, out);
 #pragma unroll
         for (int k = 0; k < NI; ++k)
-            if (lane < it[k].z) part[sl[k]] = out[k];
+            if (lane < it[k].z) part[ent[sl[k]]] = out[k];
     } else {
 #pragma unroll 1
         for (int k = 0; k < NI; ++k) {
@@ -723,7 +725,7 @@ __global__ void __launch_bounds__(128, 7) m2p_ly32x_kernel(int64_t nitems, const
                 const float ux[1] = {c.x - x.x}, uy[1] = {c.y - x.y}, uz[1] = {c.z - x.z};
                 float4 out[1];
                 m2p_ly_eval<P, 1>(R, ux, uy, uz, kappa, out);
-                part[slot] = out[0];
+                part[ent[slot]] = out[0];
             }
         }
     }
@@ -757,7 +759,6 @@ template <typename TM, int NK>
 __global__ void __launch_bounds__(128) gather_kernel(int64_t ntg, const int64_t *__restrict__ p2p_ptr,
                                                      const double *__restrict__ p2p_part,
                                                      const int64_t *__restrict__ m2p_ptr,
-                                                     const int32_t *__restrict__ m2p_pos,
                                                      const TM *__restrict__ m2p_part, NearArgs nr,
                                                      double *__restrict__ VK0, double *__restrict__ VK1) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -777,7 +778,7 @@ __global__ void __launch_bounds__(128) gather_kernel(int64_t ntg, const int64_t 
     }
     if (m2p_part)
         for (int64_t e = m2p_ptr[t] + lane; e < m2p_ptr[t + 1]; e += 32) {
-            const TM *rec = m2p_part + (int64_t)2 * NK * m2p_pos[e];
+            const TM *rec = m2p_part + (int64_t)2 * NK * e;
 #pragma unroll
             for (int a = 0; a < 2 * NK; ++a) far[a] += (double)rec[a];
         }
@@ -825,7 +826,6 @@ template <int NK>
 __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_t *__restrict__ p2p_ptr,
                                                        const float *__restrict__ p2p_part,
                                                        const int64_t *__restrict__ m2p_ptr,
-                                                       const int32_t *__restrict__ m2p_pos,
                                                        const float *__restrict__ m2p_part, NearArgs32 nr,
                                                        double *__restrict__ VK0, double *__restrict__ VK1) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -834,12 +834,13 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
     float hi[2 * NK], lo[2 * NK], nh[2 * NK], nl[2 * NK];
 #pragma unroll
     for (int a = 0; a < 2 * NK; ++a) { hi[a] = 0.f; lo[a] = 0.f; nh[a] = 0.f; nl[a] = 0.f; }
-    // records as one 16-byte (two kernels) or 8-byte load each.  The list
-    // bounds, then the first four P2P records, four M2P positions and two
-    // near entries of every lane, then the M2P records and the densities they
-    // point to, are each issued as one round of independent loads (three
-    // dependent rounds in all); longer lists continue in loops.  Every lane
-    // adds its P2P, then M2P, then near values, each in list order.
+    // records as one 16-byte (two kernels) or 8-byte load each, every
+    // target's P2P and M2P records contiguous (written at their list entries).
+    // The list bounds, then the first four P2P and four M2P records and two
+    // near entries of every lane, then the densities of those near panels,
+    // are each issued as one round of independent loads (three dependent
+    // rounds in all); longer lists continue in loops.  Every lane adds its
+    // P2P, then M2P, then near values, each in list order.
     using Rec = typename std::conditional<NK == 2, float4, float2>::type;
     auto add_rec = [&](const Rec &r) {
         two_add(hi[0], lo[0], r.x);
@@ -857,13 +858,14 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
     const int sp = nr.use_self && lane < 2 * NK ? nr.selfp[t] : 0;
     // first load round
     Rec rp[4], rm[4];
-    int q[4], jn[2];
+    int jn[2];
     float dv[2][NK], dk[2][NK];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
         if (pb + 32 * u < pe) rp[u] = pp[pb + 32 * u];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) q[u] = mb + 32 * u < me ? m2p_pos[mb + 32 * u] : -1;
+    for (int u = 0; u < 4; ++u)
+        if (mb + 32 * u < me) rm[u] = mp[mb + 32 * u];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         const int64_t e = nb + 32 * u;
@@ -874,14 +876,10 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
             dk[u][a] = e < ne ? nr.dK[a][e] : 0.f;
         }
     }
-    // the P2P records arrive with the positions that the second load round needs
 #pragma unroll
     for (int u = 0; u < 4; ++u)
         if (pb + 32 * u < pe) add_rec(rp[u]);
-    // second load round
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-        if (q[u] >= 0) rm[u] = mp[q[u]];
+    // second load round: the densities of the near panels
     float2 pd[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) pd[u] = jn[u] >= 0 ? nr.phf[jn[u]] : make_float2(0.f, 0.f);
@@ -903,18 +901,15 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
     // M2P
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-        if (q[u] >= 0) add_rec(rm[u]);
+        if (mb + 32 * u < me) add_rec(rm[u]);
     for (int64_t e = mb + 128; e < me; e += 128) {
-        int qq[4];
         Rec r[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) qq[u] = e + 32 * u < me ? m2p_pos[e + 32 * u] : -1;
+        for (int u = 0; u < 4; ++u)
+            if (e + 32 * u < me) r[u] = mp[e + 32 * u];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (qq[u] >= 0) r[u] = mp[qq[u]];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (qq[u] >= 0) add_rec(r[u]);
+            if (e + 32 * u < me) add_rec(r[u]);
     }
     // near-singular corrections
 #pragma unroll
@@ -981,7 +976,8 @@ void launch_m2p_typed(int P, bool yuk, const Pair &Pr, const double *xs, const d
     const int64_t ni = Pr.n_m2p_items;
     const unsigned grid = (unsigned)((ni + 3) / 4);
 #define PB_M2P_ARGS \
-    ni, Pr.m2p_items.p, Pr.m2p_inv.p, P, xs, Pr.x32.p, Tr.centre.p, Tr.cen32.p, mom, kappa, kslot, nk, part
+    ni, Pr.m2p_items.p, Pr.m2p_inv.p, Pr.m2p_ent.p, P, xs, Pr.x32.p, Tr.centre.p, Tr.cen32.p, mom, kappa, kslot, nk, \
+        part
 #define PB_M2P_CASE(PP)                                                                                  \
     case PP:                                                                                             \
         if (yuk) m2p_kernel<PP, true, T><<<grid, 128, 0, s>>>(PB_M2P_ARGS);                              \
@@ -1394,7 +1390,8 @@ void launch_m2p(const Pair &Pr, const Targets &G, const Tree &Tr, int P, bool mi
         const float kap = (float)Pr.kappas[1];
 #define PB_LY(PP)                                                                                              \
     case PP:                                                                                                   \
-        m2p_ly32x_kernel<PP, NI><<<grid, 128, 0, s>>>(ni, Pr.m2p_items.p, Pr.m2p_inv.p, Pr.x32.p, Tr.cen32.p,    \
+        m2p_ly32x_kernel<PP, NI><<<grid, 128, 0, s>>>(ni, Pr.m2p_items.p, Pr.m2p_inv.p, Pr.m2p_ent.p, Pr.x32.p,  \
+                                                      Tr.cen32.p,                                              \
                                                       Tr.rmom32.p, kap, part);                                 \
         break;
         switch (P) {
@@ -1442,10 +1439,10 @@ void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, 
         if (Pr.n_near > 0 && !phf) fail(PB_EINVAL, "internal: FP32 densities missing");
         const float *mp = far ? Pr.m2p_part32.p : nullptr;
         if (nk == 1)
-            gather32_kernel<1><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_part32.p, Pr.m2p_ptr.p, Pr.m2p_pos.p, mp, nr,
+            gather32_kernel<1><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_part32.p, Pr.m2p_ptr.p, mp, nr,
                                                     V0, V1);
         else
-            gather32_kernel<2><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_part32.p, Pr.m2p_ptr.p, Pr.m2p_pos.p, mp, nr,
+            gather32_kernel<2><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_part32.p, Pr.m2p_ptr.p, mp, nr,
                                                     V0, V1);
     } else {
         NearArgs nr{};
@@ -1462,10 +1459,10 @@ void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, 
         nr.dphi = dphi;
         const double *mp = far ? Pr.m2p_part64.p : nullptr;
         if (nk == 1)
-            gather_kernel<double, 1><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_part.p, Pr.m2p_ptr.p, Pr.m2p_pos.p, mp,
+            gather_kernel<double, 1><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_part.p, Pr.m2p_ptr.p, mp,
                                                           nr, V0, V1);
         else
-            gather_kernel<double, 2><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_part.p, Pr.m2p_ptr.p, Pr.m2p_pos.p, mp,
+            gather_kernel<double, 2><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_part.p, Pr.m2p_ptr.p, mp,
                                                           nr, V0, V1);
     }
     PB_LAUNCH_CHECK();

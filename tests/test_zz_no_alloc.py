@@ -20,7 +20,8 @@ pytestmark = pytest.mark.gpu
 
 
 def _reference(xyz, q):
-    d = sphere_problem(level=1)
+    # the regular entry point needs a problem whose surface encloses the charges
+    d = sphere_problem(level=1, radius=60.0)
     d["charges"] = {"xyz": xyz, "q": q, "region": 0}
     return problem(d, theta=-1.0, precision="fp64").coulomb_energy()
 
