@@ -176,6 +176,7 @@ void setup_problem(pb_problem *pb) {
     // the charges must lie in their region: inside every surface that has it as
     // inner region, outside every surface that has it as outer region
     int n_wind = 0;
+    bool wind_join = false;
     if (nc > 0) {
         std::vector<int32_t> expect;
         std::vector<int> wsurf;
@@ -187,16 +188,24 @@ void setup_problem(pb_problem *pb) {
         n_wind = (int)wsurf.size();
         if (n_wind > 8) fail(PB_EINVAL, "the charged region is bounded by more than 8 surfaces");
         if (n_wind > 0) {
+            // on the side stream, beside the latency-bound list construction below
+            cudaStream_t ws = pb->side ? pb->side : s;
+            if (ws != s) {
+                PB_CUDA_TRY(cudaEventRecord(pb->evf, s));
+                PB_CUDA_TRY(cudaStreamWaitEvent(ws, pb->evf, 0));
+            }
             pb->wind.alloc(n_wind * nc);
-            pb->wind.zero(s);
+            pb->wind.zero(ws);
             for (int k = 0; k < n_wind; ++k)
                 winding_numbers(pb->S[wsurf[k]].verts.p, pb->S[wsurf[k]].tris.p, pb->S[wsurf[k]].n, pb->cxyz_d.p,
-                                nc, pb->wind.p + k * nc, s);
+                                nc, pb->wind.p + k * nc, ws);
             pb->wind_bad.alloc(3);
             pb->wind_bad_h.alloc(3);
-            winding_mismatch(pb->wind.p, nc, n_wind, expect.data(), pb->wind_bad.p, s);
+            winding_mismatch(pb->wind.p, nc, n_wind, expect.data(), pb->wind_bad.p, ws);
             PB_CUDA_TRY(cudaMemcpyAsync(pb->wind_bad_h.p, pb->wind_bad.p, 3 * sizeof(int32_t),
-                                        cudaMemcpyDeviceToHost, s));
+                                        cudaMemcpyDeviceToHost, ws));
+            if (ws != s) PB_CUDA_TRY(cudaEventRecord(pb->evj, ws));
+            wind_join = ws != s;
         }
     }
     // block structure (multi-surface rule): row (s, R) gets sigma (K - c V) of every t in dR
@@ -335,6 +344,7 @@ void setup_problem(pb_problem *pb) {
             if (prm.precision == PB_MIXED && prm.P <= kRadialMaxP)
                 pb->T[t].rmom32.alloc((size_t)pb->T[t].nnodes * radial_floats(prm.P));
         }
+    if (wind_join) PB_CUDA_TRY(cudaStreamWaitEvent(s, pb->evj, 0));
     PB_CUDA_TRY(cudaEventRecord(pb->ev1, s));
     PB_CUDA_TRY(cudaEventSynchronize(pb->ev1));
     if (n_wind > 0 && pb->wind_bad_h.p[0] > 0) {
@@ -912,14 +922,16 @@ int pb_add_surface(pb_problem *pb, const double *verts, int64_t nv, const int32_
             if (!std::isfinite(verts[i])) fail(PB_EINVAL, "non-finite vertex coordinate");
         for (int64_t i = 0; i < 3 * nt; ++i)
             if (tris[i] < 0 || tris[i] >= nv) fail(PB_EINVAL, "triangle vertex index out of range");
-        check_closed_mesh(verts, nv, tris, nt);
         set_device(pb->ctx);
         SurfIn si;
         si.nv = nv;
         si.nt = nt;
         si.v.upload(verts, 3 * nv, pb->stream);
         si.t.upload(tris, 3 * nt, pb->stream);
+        pb->mesh_chk_h.alloc(1);
+        check_mesh_async(si.v.p, nv, si.t.p, nt, pb->mesh_chk_h.p, pb->stream);
         PB_CUDA_TRY(cudaStreamSynchronize(pb->stream));
+        mesh_check_result(*pb->mesh_chk_h.p);
         si.inner = inner;
         si.outer = outer;
         pb->sin.push_back(std::move(si));

@@ -9,6 +9,7 @@
 
 #include "gmres.cuh"
 #include "model.cuh"
+#include "validate.cuh"
 
 struct pb_ctx {
     int device = 0;
@@ -85,6 +86,7 @@ struct pb_problem {
     pb::DevBuf<double> cq_d, cxyz_d, phi_reac, energy;
     pb::DevBuf<int32_t> wind, wind_bad;      // charge-region check: winding numbers, mismatch record
     pb::PinnedBuf<int32_t> wind_bad_h;
+    pb::PinnedBuf<pb::MeshCheck> mesh_chk_h;  // outcome of the last pb_add_surface's mesh check
     pb::Gmres gm;
     double setup_ms = 0.0;
     bool have_solution = false;

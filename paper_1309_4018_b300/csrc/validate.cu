@@ -8,54 +8,143 @@
 
 namespace pb {
 
-// ---------------------------------------------------------------- meshes (host)
+// ---------------------------------------------------------------- meshes (device)
 
-void check_closed_mesh(const double *verts, int64_t nv, const int32_t *tris, int64_t nt) {
-    // directed edges bucketed by their lower vertex (counting sort); each
-    // undirected edge must occur exactly twice, once in each direction
-    std::vector<int64_t> start(nv + 1, 0);
-    for (int64_t i = 0; i < nt; ++i) {
-        const int32_t *t = tris + 3 * i;
-        if (t[0] == t[1] || t[1] == t[2] || t[2] == t[0])
-            fail(PB_EINVAL, "triangle " + std::to_string(i) + " repeats a vertex");
-        for (int k = 0; k < 3; ++k) ++start[std::min(t[k], t[(k + 1) % 3]) + 1];
-    }
-    for (int64_t v = 0; v < nv; ++v) start[v + 1] += start[v];
-    std::vector<int64_t> fill(start.begin(), start.end() - 1);
-    std::vector<int32_t> other(3 * nt);
-    std::vector<int8_t> dir(3 * nt);
-    for (int64_t i = 0; i < nt; ++i) {
-        const int32_t *t = tris + 3 * i;
-        for (int k = 0; k < 3; ++k) {
-            const int32_t a = t[k], b = t[(k + 1) % 3];
-            const int64_t slot = fill[std::min(a, b)]++;
-            other[slot] = std::max(a, b);
-            dir[slot] = a < b ? 1 : -1;
+namespace {
+
+// error codes of a mesh check, lowest first reported
+constexpr unsigned long long kRepeat = 1, kOpen = 2, kFlip = 3;
+
+__global__ void corner_count_kernel(int64_t n3, const int32_t *__restrict__ tris, int32_t *__restrict__ cnt) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n3) atomicAdd(&cnt[tris[c]], 1);
+}
+
+__global__ void corner_fill_kernel(int64_t n3, const int32_t *__restrict__ tris, const int64_t *__restrict__ off,
+                                   int32_t *__restrict__ cur, int32_t *__restrict__ adj) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n3) return;
+    const int32_t v = tris[c];
+    adj[off[v] + atomicAdd(&cur[v], 1)] = (int32_t)(c / 3);
+}
+
+// One thread per directed edge a -> b of triangle i: every other triangle at a
+// is searched for b -> a (its partner) and a -> b (a duplicate).  A closed,
+// consistently oriented 2-manifold has exactly one partner and no duplicate.
+__global__ void edge_check_kernel(int64_t n3, const int32_t *__restrict__ tris, const int64_t *__restrict__ off,
+                                  const int32_t *__restrict__ adj, unsigned long long *__restrict__ bad) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n3) return;
+    const int64_t i = c / 3;
+    const int k = (int)(c - 3 * i);
+    const int32_t a = tris[c], b = tris[3 * i + (k == 2 ? 0 : k + 1)];
+    unsigned long long code = 0;
+    int uses = 1, rev = 0;
+    if (a == b) {
+        code = kRepeat;
+    } else {
+        for (int64_t q = off[a]; q < off[a + 1]; ++q) {
+            const int32_t j = adj[q];
+            if (j == i) continue;
+            const int32_t t0 = tris[3 * (int64_t)j], t1 = tris[3 * (int64_t)j + 1], t2 = tris[3 * (int64_t)j + 2];
+            const int32_t e[3][2] = {{t0, t1}, {t1, t2}, {t2, t0}};
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                if (e[m][0] == b && e[m][1] == a) { ++uses; ++rev; }
+                if (e[m][0] == a && e[m][1] == b) ++uses;
+            }
         }
+        if (uses != 2) code = kOpen;
+        else if (rev != 1) code = kFlip;
     }
-    for (int64_t v = 0; v < nv; ++v)
-        for (int64_t i = start[v]; i < start[v + 1]; ++i) {
-            int uses = 0, net = 0;
-            for (int64_t j = start[v]; j < start[v + 1]; ++j)
-                if (other[j] == other[i]) { ++uses; net += dir[j]; }
-            const std::string e = "edge (" + std::to_string(v) + ", " + std::to_string(other[i]) + ")";
-            if (uses != 2)
-                fail(PB_EINVAL, "surface is not a closed 2-manifold: " + e + " belongs to " +
-                                    std::to_string(uses) + " triangle(s), not 2");
-            if (net != 0)
-                fail(PB_EINVAL, "surface is not consistently oriented: " + e +
-                                    " is traversed twice in the same direction");
-        }
-    double vol6 = 0.0;
-    for (int64_t i = 0; i < nt; ++i) {
-        const double *a = verts + 3 * (int64_t)tris[3 * i], *b = verts + 3 * (int64_t)tris[3 * i + 1],
-                     *c = verts + 3 * (int64_t)tris[3 * i + 2];
-        vol6 += a[0] * (b[1] * c[2] - b[2] * c[1]) + a[1] * (b[2] * c[0] - b[0] * c[2]) +
-                a[2] * (b[0] * c[1] - b[1] * c[0]);
+    if (code) {
+        // code, then the number of triangles on the edge (open case), then the corner
+        const unsigned long long rec = (code << 60) | ((unsigned long long)min(uses, 255) << 52) |
+                                       (unsigned long long)(c & ((1ull << 52) - 1));
+        atomicMin(bad, rec);
     }
-    if (!(vol6 > 0.0)) {
+}
+
+// Six times the signed volume, sum of a . (b x c): per-block sums in a fixed
+// order, then one block adds them (the same result on every run).
+constexpr int kVolBlocks = 256, kVolThreads = 256;
+
+__global__ void __launch_bounds__(kVolThreads) volume_partial_kernel(int64_t nt, const double *__restrict__ v,
+                                                                     const int32_t *__restrict__ t,
+                                                                     double *__restrict__ part) {
+    __shared__ double sh[kVolThreads];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kVolThreads + threadIdx.x; i < nt; i += (int64_t)kVolBlocks * kVolThreads) {
+        const double *a = v + 3 * (int64_t)t[3 * i], *b = v + 3 * (int64_t)t[3 * i + 1], *c = v + 3 * (int64_t)t[3 * i + 2];
+        acc += a[0] * (b[1] * c[2] - b[2] * c[1]) + a[1] * (b[2] * c[0] - b[0] * c[2]) +
+               a[2] * (b[0] * c[1] - b[1] * c[0]);
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kVolThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(kVolBlocks) volume_final_kernel(const double *__restrict__ part,
+                                                                  MeshCheck *__restrict__ out,
+                                                                  const unsigned long long *__restrict__ bad) {
+    __shared__ double sh[kVolBlocks];
+    sh[threadIdx.x] = part[threadIdx.x];
+    __syncthreads();
+    for (int w = kVolBlocks / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out->vol6 = sh[0];
+        out->bad = *bad;
+    }
+}
+
+}  // namespace
+
+void check_mesh_async(const double *verts, int64_t nv, const int32_t *tris, int64_t nt, MeshCheck *out,
+                      cudaStream_t s) {
+    const int64_t n3 = 3 * nt;
+    TmpBuf<int32_t> cnt(nv, s), cur(nv, s), adj(n3, s);
+    TmpBuf<int64_t> off(nv + 1, s);
+    TmpBuf<unsigned long long> bad(1, s);
+    TmpBuf<double> part(kVolBlocks, s);
+    TmpBuf<MeshCheck> res(1, s);
+    PB_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, nv * sizeof(int32_t), s));
+    PB_CUDA_TRY(cudaMemsetAsync(cur.p, 0, nv * sizeof(int32_t), s));
+    PB_CUDA_TRY(cudaMemsetAsync(bad.p, 0xff, sizeof(unsigned long long), s));
+    corner_count_kernel<<<div_up(n3, 256), 256, 0, s>>>(n3, tris, cnt.p);
+    PB_LAUNCH_CHECK();
+    exclusive_scan_i32_to_i64(cnt.p, off.p, nv, s);
+    corner_fill_kernel<<<div_up(n3, 256), 256, 0, s>>>(n3, tris, off.p, cur.p, adj.p);
+    PB_LAUNCH_CHECK();
+    edge_check_kernel<<<div_up(n3, 256), 256, 0, s>>>(n3, tris, off.p, adj.p, bad.p);
+    PB_LAUNCH_CHECK();
+    volume_partial_kernel<<<kVolBlocks, kVolThreads, 0, s>>>(nt, verts, tris, part.p);
+    PB_LAUNCH_CHECK();
+    volume_final_kernel<<<1, kVolBlocks, 0, s>>>(part.p, res.p, bad.p);
+    PB_LAUNCH_CHECK();
+    PB_CUDA_TRY(cudaMemcpyAsync(out, res.p, sizeof(MeshCheck), cudaMemcpyDeviceToHost, s));
+}
+
+void mesh_check_result(const MeshCheck &r) {
+    if (r.bad != ~0ull) {
+        const unsigned long long code = r.bad >> 60, uses = (r.bad >> 52) & 255, c = r.bad & ((1ull << 52) - 1);
+        const std::string where = "triangle " + std::to_string(c / 3) + ", corner " + std::to_string(c % 3);
+        if (code == kRepeat) fail(PB_EINVAL, "a triangle repeats a vertex (" + where + ")");
+        if (code == kOpen)
+            fail(PB_EINVAL, "surface is not a closed 2-manifold: an edge belongs to " + std::to_string(uses) +
+                                " triangle(s), not 2 (" + where + ")");
+        fail(PB_EINVAL, "surface is not consistently oriented: an edge is traversed twice in the same direction (" +
+                            where + ")");
+    }
+    if (!(r.vol6 > 0.0)) {
         char buf[96];
-        std::snprintf(buf, sizeof buf, "%.6g", vol6 / 6.0);
+        std::snprintf(buf, sizeof buf, "%.6g", r.vol6 / 6.0);
         fail(PB_EINVAL, std::string("surface encloses its outer region (signed volume ") + buf +
                             " <= 0): triangles must wind counter-clockwise seen from the outer region");
     }

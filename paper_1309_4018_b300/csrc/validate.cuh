@@ -11,13 +11,23 @@
 
 namespace pb {
 
-// PB_EINVAL unless every edge of the mesh is shared by exactly two triangles
+// Mesh check: every edge of the mesh must be shared by exactly two triangles
 // that traverse it in opposite directions (a closed, consistently oriented
-// 2-manifold), no triangle repeats a vertex index, and the signed volume
-// (1/6) sum v0 . (v1 x v2) is positive: the triangles wind counter-clockwise
-// seen from the outer region, so the surface encloses its inner region.
-// Host arrays; O(nt) work.
-void check_closed_mesh(const double *verts, int64_t nv, const int32_t *tris, int64_t nt);
+// 2-manifold), no triangle may repeat a vertex index, and the signed volume
+// (1/6) sum v0 . (v1 x v2) must be positive: the triangles wind
+// counter-clockwise seen from the outer region, so the surface encloses its
+// inner region.  check_mesh_async queues the check of a device mesh on s and
+// copies its outcome to *out (page-locked host memory, valid once s has been
+// synchronised); mesh_check_result then fails with PB_EINVAL and a message
+// when the mesh is refused.  Work: one thread per directed edge searching
+// the triangles at its first vertex.
+struct MeshCheck {
+    unsigned long long bad;   // all ones: no edge fault; else (code << 60) | (uses << 52) | corner
+    double vol6;              // six times the signed volume
+};
+void check_mesh_async(const double *verts, int64_t nv, const int32_t *tris, int64_t nt, MeshCheck *out,
+                      cudaStream_t s);
+void mesh_check_result(const MeshCheck &r);
 
 // Queues on s the winding number of the closed surface (device verts, tris)
 // about each of nc points xyz (device): the signed count of the surface's
