@@ -96,6 +96,12 @@ void pb_ctx_destroy(pb_ctx *ctx);
 const char *pb_last_error(pb_ctx *ctx);
 /* The cudaStream_t all work of this context is issued on (for event timing). */
 void *pb_ctx_stream(pb_ctx *ctx);
+/* Context options (not in the paper).  PB_OPT_BATCH_PERSISTENT (1, the
+ * default, or 0): whether pb_solve_batch runs the operator applications of
+ * an eligible batch as one persistent launch per GMRES step (see
+ * pb_solve_batch).  PB_EINVAL for an unknown option or value. */
+#define PB_OPT_BATCH_PERSISTENT 1
+int pb_ctx_set_option(pb_ctx *ctx, int option, long long value);
 
 /* Problem: regions, surfaces and charges (Sec. 2.1, Eq. pde; Sec. 2.2). */
 int pb_problem_create(pb_ctx *ctx, pb_problem **out);
@@ -179,11 +185,22 @@ int pb_rhs(pb_problem *pb, double *b);
  * x0: optional initial guess (2 N host doubles) or NULL for zero. */
 int pb_solve(pb_problem *pb, const double *x0, pb_result *out);
 /* Solve n set-up problems of this context together (the binding triplet, a
- * fleet of ligands): every problem runs its own GMRES on one of up to 8 pool
- * streams, all advancing in lock step with one host synchronisation per
- * iteration round, so small problems overlap on the GPU.  The call is ordered
- * on the context stream.  out: n results (may be NULL).  PB_ENOCONV if any
- * problem reached max_iter (every result is still written). */
+ * fleet of ligands; the batching pattern of the production workload, applied
+ * to Eq. bind_energy's three solves): every problem runs its own GMRES on one
+ * of up to 8 pool streams.  An eligible batch (two or more problems, all
+ * PB_MIXED with the same P <= 8, every surface between a kappa = 0 region
+ * and a kappa > 0 region with K = 3: single-surface molecules) advances its
+ * Arnoldi steps in lock step, one host synchronisation per step for the
+ * whole batch, and each step's direct sums, far-field sums and per-target
+ * gathers of all problems run as ONE persistent launch over a device queue
+ * of (problem, phase, tile) entries; a problem's gathers wait, with a bounded
+ * number of polls, for its direct and far-field entries, and a wait that runs
+ * out ends the call with PB_ETIMEOUT (the context stays usable).  Other
+ * batches (or PB_OPT_BATCH_PERSISTENT = 0) run each problem's GMRES cycle as
+ * a device-driven graph, one host synchronisation per cycle round.  Either
+ * way the energies equal those of single pb_solve calls bit for bit.  The
+ * call is ordered on the context stream.  out: n results (may be NULL).
+ * PB_ENOCONV if any problem reached max_iter (every result is still written). */
 int pb_solve_batch(pb_ctx *ctx, pb_problem *const *probs, int n, pb_result *out);
 /* Binding energy (Eq. bind_energy): solves complex, receptor and ligand as one
  * batch and returns ddG = E_cx - E_rec - E_lig with E = dG_solv + the Coulomb

@@ -364,6 +364,25 @@ void setup_problem(pb_problem *pb) {
 
 namespace pb {
 
+namespace {
+
+void strengths_all(pb_problem *pb, const double *xd, cudaStream_t s) {
+    const bool mixed = pb->prm.precision == PB_MIXED;
+    for (size_t t = 0; t < pb->S.size(); ++t) {
+        const double *phi = xd + 2 * pb->off[t];
+        const double *dphi = phi + pb->S[t].n;
+        compute_strengths(pb->T[t], pb->S[t], phi, dphi, mixed, s);
+    }
+}
+
+void upward_all(pb_problem *pb, cudaStream_t s) {
+    const bool mixed = pb->prm.precision == PB_MIXED;
+    for (size_t t = 0; t < pb->S.size(); ++t)
+        if (pb->need_far[t]) upward_pass(pb->T[t], pb->prm.P, mixed, s);
+}
+
+}  // namespace
+
 // y = A x, both device pointers of 2N doubles; optional event marks between the phases.
 void apply_operator(pb_problem *pb, const double *xd, double *yd, PhaseEvents *ph) {
     cudaStream_t s = pb->stream;
@@ -378,15 +397,10 @@ void apply_operator(pb_problem *pb, const double *xd, double *yd, PhaseEvents *p
     // strengths) run on the side stream while the upward pass and the
     // expansions run here; the gather waits for both.
     const bool fork = !ph && pb->side;
-    for (int t = 0; t < ns; ++t) {
-        const double *phi = xd + 2 * pb->off[t];
-        const double *dphi = phi + pb->S[t].n;
-        compute_strengths(pb->T[t], pb->S[t], phi, dphi, mixed, s);
-    }
+    strengths_all(pb, xd, s);
     if (fork) PB_CUDA_TRY(cudaEventRecord(pb->evf, s));
     // the upward pass is enqueued first: its blocks (one per leaf) start before the direct sums fill the GPU
-    for (int t = 0; t < ns; ++t)
-        if (pb->need_far[t]) upward_pass(pb->T[t], prm.P, mixed, s);
+    upward_all(pb, s);
     if (fork) {
         PB_CUDA_TRY(cudaStreamWaitEvent(pb->side, pb->evf, 0));
         for (auto &P : pb->pairs) launch_p2p(P, pb->G[P.tgt], pb->T[P.tree], P.tgt == P.tree, mixed, pb->side);
@@ -404,6 +418,17 @@ void apply_operator(pb_problem *pb, const double *xd, double *yd, PhaseEvents *p
         launch_gather(P, pb->G[P.tgt], mixed, P.tgt == P.tree, phi, phi + pb->S[P.tree].n, pb->T[P.tree].phf.p, s);
     }
     mark(4);
+    operator_post(pb, xd, yd, s);
+    mark(5);
+}
+
+void operator_pre(pb_problem *pb, const double *xd, cudaStream_t s) {
+    strengths_all(pb, xd, s);
+    upward_all(pb, s);
+}
+
+void operator_post(pb_problem *pb, const double *xd, double *yd, cudaStream_t s) {
+    const int ns = (int)pb->S.size();
     for (int sf = 0; sf < ns; ++sf) {
         for (int side = 0; side < 2; ++side) {
             CombineRow row{};
@@ -417,7 +442,6 @@ void apply_operator(pb_problem *pb, const double *xd, double *yd, PhaseEvents *p
                            yd + 2 * pb->off[sf] + side * pb->S[sf].n, s);
         }
     }
-    mark(5);
 }
 
 // phi_reac at the charges (input order) for the unknowns x (device); then
@@ -555,7 +579,7 @@ void build_cycle_graph(KrylovJob *jb) {
     PB_CUDA_TRY(cudaGraphInstantiate(jb->cycle_exec, g, 0));
 }
 
-void run_krylov(std::vector<KrylovJob *> &jobs) {
+void run_krylov(std::vector<KrylovJob *> &jobs, BatchPlan *plan) {
     for (KrylovJob *jb : jobs) {
         pb_problem *pb = jb->pb;
         jb->st = KrylovStats{};
@@ -594,6 +618,14 @@ void run_krylov(std::vector<KrylovJob *> &jobs) {
                 jb->x_zero = false;
                 gm.start_cycle(pb->r.p, s);
                 jb->act = 1;
+            } else if (jb->phase == 2 && plan) {
+                // the step's operator input, then the ends of the operator that stay per problem
+                if (jb->precond) jb->precond(gm.basis(jb->j), pb->z1.p);
+                else PB_CUDA_TRY(cudaMemcpyAsync(pb->z1.p, gm.basis(jb->j), n2 * sizeof(double),
+                                                 cudaMemcpyDeviceToDevice, s));
+                operator_pre(pb, pb->z1.p, s);
+                PB_CUDA_TRY(cudaEventRecord(pb->evf, s));
+                jb->act = 2;
             } else if (jb->phase == 2 && jb->cycle_exec) {
                 gm.set_cycle(pb->prm.max_iter - jb->st.iters, s);
                 if (!*jb->cycle_exec) build_cycle_graph(jb);
@@ -618,8 +650,39 @@ void run_krylov(std::vector<KrylovJob *> &jobs) {
             }
             any = any || jb->act != 0;
         }
+        if (plan && any) {
+            // one persistent launch for the direct sums, far field and gathers of every
+            // problem taking an Arnoldi step, then each problem's combine and step
+            cudaStream_t bs = jobs[0]->pb->ctx->stream;
+            bool stepping = false;
+            for (size_t i = 0; i < jobs.size(); ++i) {
+                const bool on = jobs[i]->act == 2;
+                plan->active_h.p[i] = on ? 1 : 0;
+                if (on) {
+                    PB_CUDA_TRY(cudaStreamWaitEvent(bs, jobs[i]->pb->evf, 0));
+                    stepping = true;
+                }
+            }
+            if (stepping) {
+                batch_operator_launch(*plan, bs);
+                PB_CUDA_TRY(cudaEventRecord(plan->ev, bs));
+                for (KrylovJob *jb : jobs) {
+                    if (jb->act != 2) continue;
+                    pb_problem *pb = jb->pb;
+                    PB_CUDA_TRY(cudaStreamWaitEvent(pb->stream, plan->ev, 0));
+                    operator_post(pb, pb->z1.p, pb->gm.w.p, pb->stream);
+                    ++jb->st.matvecs;
+                    pb->gm.arnoldi_step(jb->j, pb->stream);
+                }
+            }
+        }
         if (!any) break;
         sync_streams(jobs, true);
+        if (plan && plan->status_h.p[0] != PB_OK) {
+            PB_CUDA_TRY(cudaStreamSynchronize(jobs[0]->pb->ctx->stream));
+            fail(PB_ETIMEOUT, "batched operator: a gather's bounded wait for its pair's direct and far-field "
+                              "sums ran out");
+        }
         for (KrylovJob *jb : jobs) {
             pb_problem *pb = jb->pb;
             const Params &prm = pb->prm;
@@ -709,6 +772,20 @@ void fill_result(pb_problem *pb, const KrylovStats &st, float ms, pb_result *out
     }
 }
 
+// Whether a batch takes the persistent batched operator: two or more
+// problems, all FP32-mixed with the same expansion order in the radial form,
+// and every pair of each one a Laplace-inside / Yukawa-outside pair
+// (single-surface molecules: binding triplets, ligand fleets).
+bool batch_persistent_eligible(const std::vector<pb_problem *> &probs) {
+    if (probs.size() < 2 || !probs[0]->ctx->batch_persistent) return false;
+    for (pb_problem *pb : probs) {
+        if (pb->prm.precision != PB_MIXED || pb->prm.P != probs[0]->prm.P) return false;
+        for (const Pair &P : pb->pairs)
+            if (!batch_pair_eligible(P, pb->prm, P.tgt == P.tree)) return false;
+    }
+    return true;
+}
+
 // Solve every problem of `probs` (set up, distinct) by lock-step GMRES, each on
 // its current stream, then its reaction potential and energy.
 void solve_many(const std::vector<pb_problem *> &probs, const std::vector<const double *> &x0s,
@@ -736,7 +813,19 @@ void solve_many(const std::vector<pb_problem *> &probs, const std::vector<const 
         jb.cycle_kernels = &pb->cyc_kernels;
         jp[i] = &jb;
     }
-    run_krylov(jp);
+    std::unique_ptr<BatchPlan> plan;
+    if (batch_persistent_eligible(probs)) {
+        plan = std::make_unique<BatchPlan>();
+        std::vector<BatchPairRef> refs;
+        for (size_t i = 0; i < n; ++i) {
+            pb_problem *pb = probs[i];
+            for (const Pair &P : pb->pairs)
+                refs.push_back(BatchPairRef{&P, &pb->G[P.tgt], &pb->T[P.tree], P.tgt == P.tree,
+                                            pb->z1.p + 2 * pb->off[P.tree] + pb->S[P.tree].n, (int)i});
+        }
+        batch_plan_build(*plan, refs, (int)n, probs[0]->prm.P, probs[0]->ctx->stream);
+    }
+    run_krylov(jp, plan.get());
     for (size_t i = 0; i < n; ++i) {
         pb_problem *pb = probs[i];
         reaction(pb, pb->x.p);
@@ -869,6 +958,18 @@ void pb_ctx_destroy(pb_ctx *c) {
 }
 
 const char *pb_last_error(pb_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int pb_ctx_set_option(pb_ctx *c, int option, long long value) {
+    if (!c) return PB_EINVAL;
+    return guard(c, [&] {
+        if (option == PB_OPT_BATCH_PERSISTENT) {
+            if (value != 0 && value != 1) fail(PB_EINVAL, "PB_OPT_BATCH_PERSISTENT takes 0 or 1");
+            c->batch_persistent = (int)value;
+        } else {
+            fail(PB_EINVAL, "unknown option");
+        }
+    });
+}
 
 void *pb_ctx_stream(pb_ctx *c) { return c ? (void *)c->stream : nullptr; }
 

@@ -9,6 +9,7 @@
 
 #include "gmres.cuh"
 #include "model.cuh"
+#include "treecode.cuh"
 #include "validate.cuh"
 
 struct pb_ctx {
@@ -17,6 +18,7 @@ struct pb_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaStream_t> pool;   // streams of batched solves (created on first use)
     std::vector<cudaEvent_t> pool_ev;
+    int batch_persistent = 1;         // pb_solve_batch: one persistent launch per step for eligible batches
     std::string err;
 };
 
@@ -136,7 +138,14 @@ struct KrylovJob {
     int phase = 0, j = 0, act = 0;
     double bnorm = 0.0;
 };
-void run_krylov(std::vector<KrylovJob *> &jobs);
+// plan: when set, the Arnoldi steps of all jobs advance in lock step and their
+// operator applications z1 -> gm.w (every job's pb->z1) run as one batched
+// persistent launch per step (the plan's pairs, built for those inputs).
+void run_krylov(std::vector<KrylovJob *> &jobs, BatchPlan *plan = nullptr);
+// The two ends of one operator application around the pairs' sums: source
+// strengths and upward passes (pre); block combination into y (post).
+void operator_pre(pb_problem *pb, const double *xd, cudaStream_t s);
+void operator_post(pb_problem *pb, const double *xd, double *yd, cudaStream_t s);
 KrylovStats run_gmres(pb_problem *pb, const DevOp &op, const DevOp &precond, const double *b, double *x,
                       bool x_zero);
 // Operator application as a replayable CUDA graph (captured on first use).

@@ -23,6 +23,9 @@
 // recurrence of Duan & Krasny, with kappa > 0 the screened-Coulomb form of
 // Li, Johnston & Krasny that the paper cites.
 #include <algorithm>
+#include <climits>
+#include <cstdlib>
+#include <cstring>
 #include <type_traits>
 
 #include "treecode.cuh"
@@ -230,12 +233,10 @@ __global__ void __launch_bounds__(256) m2m_kernel(int nodes_begin, const int32_t
 }
 
 // ---------------------------------------------------------------- P2P, FP32 (mixed precision)
-// One warp per group of 32 consecutive sorted targets.  The warp walks the
-// union of its targets' direct-sum leaves; each leaf's sources are staged 32 at
-// a time in shared memory and broadcast to all lanes, and a lane accumulates
-// only the leaves in its own list (lane mask).  FP32 partial sums of each
-// 32-source chunk are added into (hi, lo) FP32 pairs with Neumaier's
-// compensated summation.
+// Leaf-major work items (below): every leaf's sources are staged 32 at a time
+// in shared memory and broadcast to the lanes of a warp, each lane owning one
+// target that sums over the leaf.  FP32 partial sums of each 32-source chunk
+// are added into (hi, lo) FP32 pairs with Neumaier's compensated summation.
 struct KSet {
     float kap[2];
 };
@@ -265,57 +266,59 @@ __device__ __forceinline__ void comp_add(float &hi, float &lo, float v) {
 // shared memory and broadcast; every lane owns one target.  FP32 partial sums
 // per 32-source chunk go into compensated (hi, lo) pairs; the pair's result is
 // the FP32 sum hi + lo, rounded once into an FP32 float2 record (one value per
-// row kernel) at its grouped position.
+// row kernel) at its list entry.
 // MASK: skip the target's own panel (needed when a rule point sits at the
 // centroid); without it the own points stay in and the self value is corrected.
+struct P2PArgs32 {
+    const int4 *items;                     // (leaf, grouped start, count <= 32, 0)
+    const int32_t *inv, *sent;             // grouped pair -> sorted target, list entry
+    const float4 *x32;                     // sorted targets (FP32, tree-origin relative)
+    const int32_t *selfp;
+    int use_self;
+    const int32_t *leaf_node;
+    const int64_t *start, *count;
+    const float4 *A, *B;                   // sorted sources (x, y, z, s) and (d, panel)
+    KSet ks;
+    float *part;                           // records, 2 NK floats per list entry
+};
+
+// The work item `item` on the calling warp; sA, sB: the warp's 32-source staging.
 template <int NK, bool Y0, bool Y1, bool MASK>
-__global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, const int4 *__restrict__ items,
-                                                    const int32_t *__restrict__ inv,
-                                                    const int32_t *__restrict__ sent,
-                                                    const float4 *__restrict__ x32,
-                                                    const int32_t *__restrict__ selfp, int use_self,
-                                                    const int32_t *__restrict__ leaf_node,
-                                                    const int64_t *__restrict__ start, const int64_t *__restrict__ count,
-                                                    const float4 *__restrict__ A, const float4 *__restrict__ B,
-                                                    KSet ks, float *__restrict__ part) {
-    __shared__ float4 sA[4][32], sB[4][32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t item = (int64_t)blockIdx.x * 4 + warp;
-    if (item >= nitems) return;
-    const int4 it = items[item];
+__device__ __forceinline__ void p2p32_item(const P2PArgs32 &g, int64_t item, int lane, float4 *sA, float4 *sB) {
+    const int4 it = g.items[item];
     const bool valid = lane < it.z;
     const int64_t slot = (int64_t)it.y + lane;
     float tx = 0.f, ty = 0.f, tz = 0.f;
     int me = -1;
     if (valid) {
-        const int t = inv[slot];
-        const float4 x = x32[t];
+        const int t = g.inv[slot];
+        const float4 x = g.x32[t];
         tx = x.x;
         ty = x.y;
         tz = x.z;
-        if (MASK && use_self) me = selfp[t];
+        if (MASK && g.use_self) me = g.selfp[t];
     }
-    const float k0 = ks.kap[0], k1 = ks.kap[1];
+    const float k0 = g.ks.kap[0], k1 = g.ks.kap[1];
     const float l2e0 = -k0 * 1.4426950408889634f, l2e1 = -k1 * 1.4426950408889634f;
     float hi[2 * NK], lo[2 * NK];
 #pragma unroll
     for (int a = 0; a < 2 * NK; ++a) { hi[a] = 0.f; lo[a] = 0.f; }
-    const int node = leaf_node[it.x];
-    const int64_t s0 = start[node];
-    const int cnt = (int)count[node];
+    const int node = g.leaf_node[it.x];
+    const int64_t s0 = g.start[node];
+    const int cnt = (int)g.count[node];
     for (int c0 = 0; c0 < cnt; c0 += 32) {
         const int m = min(32, cnt - c0);
         if (lane < m) {
-            sA[warp][lane] = A[s0 + c0 + lane];
-            sB[warp][lane] = B[s0 + c0 + lane];
+            sA[lane] = g.A[s0 + c0 + lane];
+            sB[lane] = g.B[s0 + c0 + lane];
         }
         __syncwarp();
         if (valid) {
             float p[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 4
             for (int j = 0; j < m; ++j) {
-                const float4 a = sA[warp][j];
-                const float4 b = sB[warp][j];
+                const float4 a = sA[j];
+                const float4 b = sB[j];
                 const float dx = tx - a.x, dy = ty - a.y, dz = tz - a.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 const float inv = (MASK && __float_as_int(b.w) == me) ? 0.f : fast_rsqrt(r2);
@@ -350,10 +353,19 @@ __global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, const int4 *
     }
     if (valid) {
         // interleaved record of the entry: (V0, K0[, V1, K1]), the compensated pair rounded once
-        float2 *rec = reinterpret_cast<float2 *>(part + (int64_t)2 * NK * sent[slot]);
+        float2 *rec = reinterpret_cast<float2 *>(g.part + (int64_t)2 * NK * g.sent[slot]);
 #pragma unroll
         for (int a = 0; a < NK; ++a) rec[a] = make_float2(hi[2 * a] + lo[2 * a], hi[2 * a + 1] + lo[2 * a + 1]);
     }
+}
+
+template <int NK, bool Y0, bool Y1, bool MASK>
+__global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, P2PArgs32 g) {
+    __shared__ float4 sA[4][32], sB[4][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * 4 + warp;
+    if (item >= nitems) return;
+    p2p32_item<NK, Y0, Y1, MASK>(g, item, lane, sA[warp], sB[warp]);
 }
 
 // ---------------------------------------------------------------- P2P, FP64
@@ -670,49 +682,49 @@ __device__ __forceinline__ void m2p_ly_eval(const float4 *R, const float (&ux)[N
 // the other.  Lanes past the last item's count evaluate their first target
 // again and store it once.  Seven blocks per SM (72 registers, no spills):
 // 90 -> 86 us at P = 6 against the unbounded 80 registers and six blocks.
+struct M2PArgs32 {
+    const int4 *items;                     // (box, grouped start, count <= 32, 0)
+    const int32_t *inv, *ent;              // grouped pair -> sorted target, list entry
+    const float4 *x32, *cen32;             // targets, box centres (FP32, tree-origin relative)
+    const float *rmom;                     // radial moments, radial_stride(P) floats per node
+    float kappa;                           // Yukawa kernel (slot 1)
+    float4 *part;                          // records (VL, KL, VY, KY) per list entry
+};
+
+// The NI items i0.. on the calling warp; sR: the warp's staging of one box's radial moments.
 template <int P, int NI>
-__global__ void __launch_bounds__(128, 7) m2p_ly32x_kernel(int64_t nitems, const int4 *__restrict__ items,
-                                                        const int32_t *__restrict__ inv,
-                                                        const int32_t *__restrict__ ent,
-                                                        const float4 *__restrict__ x32,
-                                                        const float4 *__restrict__ cen32,
-                                                        const float *__restrict__ rmom, float kappa,
-                                                        float4 *__restrict__ part) {
+__device__ __forceinline__ void m2p_ly32x_task(const M2PArgs32 &g, int64_t nitems, int64_t i0, int lane, float4 *sR) {
     constexpr int NQ = radial_stride(P) / 4;     // float4 per box
-    __shared__ float4 sR[4][NQ];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i0 = ((int64_t)blockIdx.x * 4 + warp) * NI;
-    if (i0 >= nitems) return;
     int4 it[NI];
     bool same = true;
 #pragma unroll
     for (int k = 0; k < NI; ++k) {
-        it[k] = i0 + k < nitems ? items[i0 + k] : make_int4(-1, 0, 0, 0);
+        it[k] = i0 + k < nitems ? g.items[i0 + k] : make_int4(-1, 0, 0, 0);
         same = same && it[k].x == it[0].x;
     }
-    const float4 *R = sR[warp];
+    const float4 *R = sR;
     auto stage = [&](int b) {
-        const float4 *src = reinterpret_cast<const float4 *>(rmom + (int64_t)b * radial_stride(P));
+        const float4 *src = reinterpret_cast<const float4 *>(g.rmom + (int64_t)b * radial_stride(P));
         __syncwarp();
-        for (int q = lane; q < NQ; q += 32) sR[warp][q] = src[q];
+        for (int q = lane; q < NQ; q += 32) sR[q] = src[q];
         __syncwarp();
     };
     stage(it[0].x);
     if (same) {
-        const float4 c = cen32[it[0].x];
+        const float4 c = g.cen32[it[0].x];
         int64_t sl[NI];
         float ux[NI], uy[NI], uz[NI];
 #pragma unroll
         for (int k = 0; k < NI; ++k) {
             sl[k] = lane < it[k].z ? (int64_t)it[k].y + lane : (int64_t)it[0].y + lane;
-            const float4 x = x32[inv[sl[k]]];
+            const float4 x = g.x32[g.inv[sl[k]]];
             ux[k] = c.x - x.x; uy[k] = c.y - x.y; uz[k] = c.z - x.z;
         }
         float4 out[NI];
-        m2p_ly_eval<P, NI>(R, ux, uy, uz, kappa, out);
+        m2p_ly_eval<P, NI>(R, ux, uy, uz, g.kappa, out);
 #pragma unroll
         for (int k = 0; k < NI; ++k)
-            if (lane < it[k].z) part[ent[sl[k]]] = out[k];
+            if (lane < it[k].z) g.part[g.ent[sl[k]]] = out[k];
     } else {
 #pragma unroll 1
         for (int k = 0; k < NI; ++k) {
@@ -720,15 +732,25 @@ __global__ void __launch_bounds__(128, 7) m2p_ly32x_kernel(int64_t nitems, const
             if (k > 0) stage(it[k].x);
             if (lane < it[k].z) {
                 const int64_t slot = (int64_t)it[k].y + lane;
-                const float4 c = cen32[it[k].x];
-                const float4 x = x32[inv[slot]];
+                const float4 c = g.cen32[it[k].x];
+                const float4 x = g.x32[g.inv[slot]];
                 const float ux[1] = {c.x - x.x}, uy[1] = {c.y - x.y}, uz[1] = {c.z - x.z};
                 float4 out[1];
-                m2p_ly_eval<P, 1>(R, ux, uy, uz, kappa, out);
-                part[ent[slot]] = out[0];
+                m2p_ly_eval<P, 1>(R, ux, uy, uz, g.kappa, out);
+                g.part[g.ent[slot]] = out[0];
             }
         }
     }
+}
+
+template <int P, int NI>
+__global__ void __launch_bounds__(128, 7) m2p_ly32x_kernel(int64_t nitems, M2PArgs32 g) {
+    constexpr int NQ = radial_stride(P) / 4;
+    __shared__ float4 sR[4][NQ];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i0 = ((int64_t)blockIdx.x * 4 + warp) * NI;
+    if (i0 >= nitems) return;
+    m2p_ly32x_task<P, NI>(g, nitems, i0, lane, sR[warp]);
 }
 
 // One warp per target: V and K of every kernel = its P2P and M2P partials
@@ -822,15 +844,18 @@ __device__ __forceinline__ void two_add(float &hi, float &lo, float v) {
     hi = s;
 }
 
+struct GatherArgs32 {
+    const int64_t *p2p_ptr;                // per sorted target: its P2P list entries
+    const float *p2p_part;                 // P2P records at the list entries
+    const int64_t *m2p_ptr;
+    const float *m2p_part;                 // M2P records at the list entries (null: no far field)
+    NearArgs32 nr;
+    double *VK0, *VK1;                     // outputs of kernel 0 and 1: V at [0, ntg), K at [ntg, 2 ntg)
+};
+
+// Target t on the calling warp.
 template <int NK>
-__global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_t *__restrict__ p2p_ptr,
-                                                       const float *__restrict__ p2p_part,
-                                                       const int64_t *__restrict__ m2p_ptr,
-                                                       const float *__restrict__ m2p_part, NearArgs32 nr,
-                                                       double *__restrict__ VK0, double *__restrict__ VK1) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t t = (int64_t)blockIdx.x * 4 + warp;
-    if (t >= ntg) return;
+__device__ __forceinline__ void gather32_target(const GatherArgs32 &g, int64_t ntg, int64_t t, int lane) {
     float hi[2 * NK], lo[2 * NK], nh[2 * NK], nl[2 * NK];
 #pragma unroll
     for (int a = 0; a < 2 * NK; ++a) { hi[a] = 0.f; lo[a] = 0.f; nh[a] = 0.f; nl[a] = 0.f; }
@@ -850,12 +875,12 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
             two_add(hi[3 % (2 * NK)], lo[3 % (2 * NK)], r.w);
         }
     };
-    const Rec *pp = reinterpret_cast<const Rec *>(p2p_part);
-    const Rec *mp = reinterpret_cast<const Rec *>(m2p_part);
-    const int64_t pb = p2p_ptr[t] + lane, pe = p2p_ptr[t + 1];
-    const int64_t mb = m2p_part ? m2p_ptr[t] + lane : 0, me = m2p_part ? m2p_ptr[t + 1] : 0;
-    const int64_t nb = nr.ptr[t] + lane, ne = nr.ptr[t + 1];
-    const int sp = nr.use_self && lane < 2 * NK ? nr.selfp[t] : 0;
+    const Rec *pp = reinterpret_cast<const Rec *>(g.p2p_part);
+    const Rec *mp = reinterpret_cast<const Rec *>(g.m2p_part);
+    const int64_t pb = g.p2p_ptr[t] + lane, pe = g.p2p_ptr[t + 1];
+    const int64_t mb = g.m2p_part ? g.m2p_ptr[t] + lane : 0, me = g.m2p_part ? g.m2p_ptr[t + 1] : 0;
+    const int64_t nb = g.nr.ptr[t] + lane, ne = g.nr.ptr[t + 1];
+    const int sp = g.nr.use_self && lane < 2 * NK ? g.nr.selfp[t] : 0;
     // first load round
     Rec rp[4], rm[4];
     int jn[2];
@@ -869,11 +894,11 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         const int64_t e = nb + 32 * u;
-        jn[u] = e < ne ? nr.panel[e] : -1;
+        jn[u] = e < ne ? g.nr.panel[e] : -1;
 #pragma unroll
         for (int a = 0; a < NK; ++a) {
-            dv[u][a] = e < ne ? nr.dV[a][e] : 0.f;
-            dk[u][a] = e < ne ? nr.dK[a][e] : 0.f;
+            dv[u][a] = e < ne ? g.nr.dV[a][e] : 0.f;
+            dk[u][a] = e < ne ? g.nr.dK[a][e] : 0.f;
         }
     }
 #pragma unroll
@@ -882,11 +907,11 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
     // second load round: the densities of the near panels
     float2 pd[2];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) pd[u] = jn[u] >= 0 ? nr.phf[jn[u]] : make_float2(0.f, 0.f);
+    for (int u = 0; u < 2; ++u) pd[u] = jn[u] >= 0 ? g.nr.phf[jn[u]] : make_float2(0.f, 0.f);
     double sv = 0.0, sd = 0.0;
-    if (nr.use_self && lane < 2 * NK && (lane & 1) == 0) {
-        sv = nr.selfV[lane >> 1][sp];
-        sd = nr.dphi[sp];
+    if (g.nr.use_self && lane < 2 * NK && (lane & 1) == 0) {
+        sv = g.nr.selfV[lane >> 1][sp];
+        sd = g.nr.dphi[sp];
     }
     // P2P beyond four entries per lane
     for (int64_t e = pb + 128; e < pe; e += 128) {
@@ -922,12 +947,12 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
             }
         }
     for (int64_t e = nb + 64; e < ne; e += 32) {
-        const int j = nr.panel[e];
-        const float2 pdj = nr.phf[j];
+        const int j = g.nr.panel[e];
+        const float2 pdj = g.nr.phf[j];
 #pragma unroll
         for (int a = 0; a < NK; ++a) {
-            two_add(nh[2 * a], nl[2 * a], nr.dV[a][e] * pdj.y);
-            two_add(nh[2 * a + 1], nl[2 * a + 1], nr.dK[a][e] * pdj.x);
+            two_add(nh[2 * a], nl[2 * a], g.nr.dV[a][e] * pdj.y);
+            two_add(nh[2 * a + 1], nl[2 * a + 1], g.nr.dK[a][e] * pdj.x);
         }
     }
 #pragma unroll
@@ -950,10 +975,18 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, const int64_
     if (lane < 2 * NK) {
         double out = ((double)vh + (double)vl) * kInv4Pi + ((double)wh + (double)wl);
         const int a = lane;
-        if (nr.use_self && (a & 1) == 0) out += sv * sd;
-        double *dst = (a >> 1) == 0 ? VK0 : VK1;
+        if (g.nr.use_self && (a & 1) == 0) out += sv * sd;
+        double *dst = (a >> 1) == 0 ? g.VK0 : g.VK1;
         dst[(a & 1) ? ntg + t : t] = out;
     }
+}
+
+template <int NK>
+__global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, GatherArgs32 g) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * 4 + warp;
+    if (t >= ntg) return;
+    gather32_target<NK>(g, ntg, t, lane);
 }
 
 // ---------------------------------------------------------------- near field and combine
@@ -1224,6 +1257,91 @@ size_t upward_smem(int NT, size_t elem) {
     return (3 * 455 * sizeof(int) + 31) / 32 * 32 + std::max(p2m, m2m);
 }
 
+// ---------------------------------------------------------------- batched operator: one persistent launch
+// Several problems' treecode sums in one launch.  A device queue holds
+// (pair, phase, first, count) entries: phase 0 = P2P work items, 1 = M2P
+// tasks (two box items each), 2 = gathers of consecutive sorted targets.
+// Warps take entries in queue order from one counter, so an entry is only
+// ever held by a running warp.  P2P and M2P entries never wait; a gather
+// entry waits until every P2P and M2P entry of its pair is done (the pair's
+// counter reaches `need`).  Those entries come earlier in the queue and are
+// held by warps that finish them without waiting, so every wait ends; the
+// wait is still bounded: after `cap` polls (or once another warp gave up) the
+// warp records PB_ETIMEOUT in status[0], raises the abort flag status[1] and
+// skips the entry.  A pair's records are published by a fence of every lane
+// before the warp counts the entry done; the waiting warp fences after the
+// counter has reached `need`.
+struct BatchPair {
+    P2PArgs32 p2p;
+    M2PArgs32 m2p;
+    GatherArgs32 ga;
+    int64_t n_m2p_items, ntg;
+    int problem;          // index of the problem's active flag
+    unsigned need;        // P2P and M2P entries of the pair
+};
+
+// The pair descriptors travel in the launch's parameter space (up to
+// kMaxBatchPairs pairs per launch): every field is a warp-uniform constant
+// load that the item code can re-read instead of keeping it in a register.
+constexpr int kMaxBatchPairs = 30000 / (int)sizeof(BatchPair);
+struct BatchArgs {
+    BatchPair p[kMaxBatchPairs];
+};
+
+template <int P>
+__global__ void __launch_bounds__(128, 6) batch_operator_kernel(const __grid_constant__ BatchArgs args,
+                                                                const int4 *__restrict__ queue, int64_t nq,
+                                                                const int *__restrict__ active,
+                                                                unsigned *__restrict__ cnt, int *__restrict__ status,
+                                                                long long cap, unsigned extra) {
+    constexpr int NQ = radial_stride(P) / 4;
+    constexpr int W = NQ > 64 ? NQ : 64;
+    __shared__ float4 sh[4][W];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4 *ws = sh[warp];
+    while (true) {
+        unsigned k = 0;
+        if (lane == 0) k = atomicAdd(cnt, 1u);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if ((int64_t)k >= nq) return;
+        const int4 e = queue[k];
+        const BatchPair &bp = args.p[e.x];
+        if (!active[bp.problem]) continue;
+        if (e.y == 2) {
+            int ok = 1;
+            if (lane == 0) {
+                const unsigned want = bp.need + extra;
+                const volatile unsigned *d = cnt + 1 + e.x;
+                const volatile int *abort_flag = status + 1;
+                for (long long it = 0; *d < want; ++it) {
+                    if (*abort_flag || it >= cap) {
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+                if (!ok) {
+                    atomicExch(status, PB_ETIMEOUT);
+                    atomicExch(status + 1, 1);
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) continue;
+            __threadfence();
+            for (int u = 0; u < e.w; ++u) gather32_target<2>(bp.ga, bp.ntg, (int64_t)e.z + u, lane);
+            continue;
+        }
+        if (e.y == 0) {
+            for (int u = 0; u < e.w; ++u) p2p32_item<2, false, true, false>(bp.p2p, (int64_t)e.z + u, lane, ws, ws + 32);
+        } else {
+            for (int u = 0; u < e.w; ++u) m2p_ly32x_task<P, 2>(bp.m2p, bp.n_m2p_items, (int64_t)e.z + 2 * u, lane, ws);
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicAdd(cnt + 1 + e.x, 1u);
+    }
+}
+
 }  // namespace
 
 void upload_term_tables() {
@@ -1341,6 +1459,25 @@ void m2m_pass(const Tree &Tr, int P, bool mixed, void *mom, int stride, int base
     }
 }
 
+P2PArgs32 p2p_args32(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self) {
+    const int nk = (int)Pr.kappas.size();
+    P2PArgs32 a{};
+    a.items = Pr.p2p_items.p;
+    a.inv = Pr.p2p_inv.p;
+    a.sent = Pr.p2p_ent.p;
+    a.x32 = Pr.x32.p;
+    a.selfp = G.self_panel.p;
+    a.use_self = use_self ? 1 : 0;
+    a.leaf_node = Tr.leaf_node.p;
+    a.start = Tr.start.p;
+    a.count = Tr.count.p;
+    a.A = Tr.srcA32.p;
+    a.B = Tr.srcB32.p;
+    a.ks = KSet{{(float)Pr.kappas[0], nk > 1 ? (float)Pr.kappas[1] : 0.f}};
+    a.part = Pr.p2p_part32.p;
+    return a;
+}
+
 void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self, bool mixed, cudaStream_t s) {
     const int64_t ni = Pr.n_p2p_items;
     if (!ni) return;
@@ -1351,12 +1488,9 @@ void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self,
     const int32_t *sp = G.self_panel.p;
     const int us = use_self ? 1 : 0;
     if (mixed) {
-        KSet ks{{(float)k0, (float)k1}};
         const bool mask = use_self && !Pr.p2p_self_in;
-#define PB_P2P32M(NK, A, B, M)                                                                                    \
-    p2p32_kernel<NK, A, B, M><<<grid, 128, 0, s>>>(ni, Pr.p2p_items.p, Pr.p2p_inv.p, Pr.p2p_ent.p, Pr.x32.p, sp, us, \
-                                                   Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.srcA32.p, Tr.srcB32.p,  \
-                                                   ks, Pr.p2p_part32.p)
+        const P2PArgs32 ga = p2p_args32(Pr, G, Tr, use_self);
+#define PB_P2P32M(NK, A, B, M) p2p32_kernel<NK, A, B, M><<<grid, 128, 0, s>>>(ni, ga)
 #define PB_P2P32(NK, A, B) do { if (mask) PB_P2P32M(NK, A, B, true); else PB_P2P32M(NK, A, B, false); } while (0)
         if (nk == 1) { if (y0) PB_P2P32(1, true, false); else PB_P2P32(1, false, false); }
         else if (!y0 && y1) PB_P2P32(2, false, true);
@@ -1380,19 +1514,29 @@ void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self,
     PB_LAUNCH_CHECK();
 }
 
+M2PArgs32 m2p_args32(const Pair &Pr, const Tree &Tr) {
+    M2PArgs32 a{};
+    a.items = Pr.m2p_items.p;
+    a.inv = Pr.m2p_inv.p;
+    a.ent = Pr.m2p_ent.p;
+    a.x32 = Pr.x32.p;
+    a.cen32 = Tr.cen32.p;
+    a.rmom = Tr.rmom32.p;
+    a.kappa = Pr.kappas.size() > 1 ? (float)Pr.kappas[1] : 0.f;
+    a.part = reinterpret_cast<float4 *>(Pr.m2p_part32.p);
+    return a;
+}
+
 void launch_m2p(const Pair &Pr, const Targets &G, const Tree &Tr, int P, bool mixed, cudaStream_t s) {
     if (Pr.n_m2p_items == 0) return;
     if (mixed && Pr.kappas.size() == 2 && Pr.kappas[0] == 0.0 && Pr.kappas[1] != 0.0 && P <= kRadialMaxP) {
         const int64_t ni = Pr.n_m2p_items;
         constexpr int NI = 2;   // items per warp (three or four: 99 us against 90 at P = 6, fewer warps per SM)
         const unsigned grid = (unsigned)((ni + 4 * NI - 1) / (4 * NI));
-        float4 *part = reinterpret_cast<float4 *>(Pr.m2p_part32.p);
-        const float kap = (float)Pr.kappas[1];
-#define PB_LY(PP)                                                                                              \
-    case PP:                                                                                                   \
-        m2p_ly32x_kernel<PP, NI><<<grid, 128, 0, s>>>(ni, Pr.m2p_items.p, Pr.m2p_inv.p, Pr.m2p_ent.p, Pr.x32.p,  \
-                                                      Tr.cen32.p,                                              \
-                                                      Tr.rmom32.p, kap, part);                                 \
+        const M2PArgs32 ga = m2p_args32(Pr, Tr);
+#define PB_LY(PP)                                                            \
+    case PP:                                                                 \
+        m2p_ly32x_kernel<PP, NI><<<grid, 128, 0, s>>>(ni, ga);               \
         break;
         switch (P) {
             PB_LY(0) PB_LY(1) PB_LY(2) PB_LY(3) PB_LY(4) PB_LY(5) PB_LY(6) PB_LY(7) PB_LY(8)
@@ -1415,6 +1559,25 @@ void launch_m2p(const Pair &Pr, const Targets &G, const Tree &Tr, int P, bool mi
     }
 }
 
+GatherArgs32 gather_args32(const Pair &Pr, const Targets &G, bool use_self, const double *dphi, const float2 *phf) {
+    const int nk = (int)Pr.kappas.size();
+    NearArgs32 nr{};
+    nr.ptr = Pr.near_ptr.p;
+    nr.panel = Pr.near_panel.p;
+    for (int k = 0; k < nk; ++k) {
+        nr.dV[k] = Pr.dV32.p + (int64_t)k * Pr.n_near;
+        nr.dK[k] = Pr.dK32.p + (int64_t)k * Pr.n_near;
+        nr.selfV[k] = use_self ? (Pr.p2p_self_in ? Pr.selfV32[k].p : Pr.selfV[k].p) : nullptr;
+    }
+    nr.selfp = G.self_panel.p;
+    nr.use_self = use_self ? 1 : 0;
+    nr.phf = phf;
+    nr.dphi = dphi;
+    if (Pr.n_near > 0 && !phf) fail(PB_EINVAL, "internal: FP32 densities missing");
+    return GatherArgs32{Pr.p2p_ptr.p, Pr.p2p_part32.p, Pr.m2p_ptr.p, Pr.n_m2p_items > 0 ? Pr.m2p_part32.p : nullptr,
+                        nr, Pr.VK[0].p, nk > 1 ? Pr.VK[1].p : nullptr};
+}
+
 void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, const double *phi,
                    const double *dphi, const float2 *phf, cudaStream_t s) {
     const int64_t ntg = G.n;
@@ -1424,26 +1587,9 @@ void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, 
     double *V0 = Pr.VK[0].p, *V1 = nk > 1 ? Pr.VK[1].p : nullptr;
     const unsigned grid = (unsigned)((ntg + 3) / 4);
     if (mixed) {
-        NearArgs32 nr{};
-        nr.ptr = Pr.near_ptr.p;
-        nr.panel = Pr.near_panel.p;
-        for (int k = 0; k < nk; ++k) {
-            nr.dV[k] = Pr.dV32.p + (int64_t)k * Pr.n_near;
-            nr.dK[k] = Pr.dK32.p + (int64_t)k * Pr.n_near;
-            nr.selfV[k] = use_self ? (Pr.p2p_self_in ? Pr.selfV32[k].p : Pr.selfV[k].p) : nullptr;
-        }
-        nr.selfp = G.self_panel.p;
-        nr.use_self = use_self ? 1 : 0;
-        nr.phf = phf;
-        nr.dphi = dphi;
-        if (Pr.n_near > 0 && !phf) fail(PB_EINVAL, "internal: FP32 densities missing");
-        const float *mp = far ? Pr.m2p_part32.p : nullptr;
-        if (nk == 1)
-            gather32_kernel<1><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_part32.p, Pr.m2p_ptr.p, mp, nr,
-                                                    V0, V1);
-        else
-            gather32_kernel<2><<<grid, 128, 0, s>>>(ntg, Pr.p2p_ptr.p, Pr.p2p_part32.p, Pr.m2p_ptr.p, mp, nr,
-                                                    V0, V1);
+        const GatherArgs32 ga = gather_args32(Pr, G, use_self, dphi, phf);
+        if (nk == 1) gather32_kernel<1><<<grid, 128, 0, s>>>(ntg, ga);
+        else gather32_kernel<2><<<grid, 128, 0, s>>>(ntg, ga);
     } else {
         NearArgs nr{};
         nr.ptr = Pr.near_ptr.p;
@@ -1486,6 +1632,129 @@ void launch_combine(int64_t n, const int32_t *rank, const double *phi_s, double 
     if (!n) return;
     combine_kernel<<<div_up(n, 256), 256, 0, s>>>(n, rank, phi_s, half, row, y);
     PB_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------- batched operator (host)
+namespace {
+
+constexpr int kBatchPer = 8;   // work items (P2P), two-item tasks (M2P) or targets (gather) per queue entry
+
+// PB_FAULT=wait (read when the library is loaded): every gather of a batched
+// operator application waits for one entry more than its pair has, so the
+// bounded wait runs out (test of the timeout path; nothing else changes).
+bool fault_wait() {
+    const char *e = std::getenv("PB_FAULT");
+    return e && std::strcmp(e, "wait") == 0;
+}
+const bool g_fault_wait = fault_wait();
+
+template <int P>
+int batch_grid() {
+    int nsm = 0, dev = 0, per = 0;
+    PB_CUDA_TRY(cudaGetDevice(&dev));
+    PB_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    PB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_operator_kernel<P>, 128, 0));
+    return std::max(1, nsm * std::max(1, per));
+}
+
+}  // namespace
+
+BatchPlan::~BatchPlan() {
+    if (ev) cudaEventDestroy(ev);
+}
+
+bool batch_pair_eligible(const Pair &Pr, const Params &prm, bool use_self) {
+    return prm.precision == PB_MIXED && Pr.kappas.size() == 2 && Pr.kappas[0] == 0.0 && Pr.kappas[1] != 0.0 &&
+           prm.P >= 0 && prm.P <= kRadialMaxP && !(use_self && !Pr.p2p_self_in);
+}
+
+void batch_plan_build(BatchPlan &bp, const std::vector<BatchPairRef> &prs, int nproblems, int P, cudaStream_t s) {
+    if (P < 0 || P > kRadialMaxP) fail(PB_EINVAL, "internal: batched operator needs the radial-form M2P");
+    bp.P = P;
+    bp.nproblems = nproblems;
+    bp.npairs = (int)prs.size();
+    bp.seg_args.clear();
+    bp.seg_q.clear();
+    std::vector<int4> q;
+    // segments of at most kMaxBatchPairs pairs, one launch each
+    for (size_t p0 = 0; p0 < prs.size(); p0 += kMaxBatchPairs) {
+        const size_t p1 = std::min(prs.size(), p0 + (size_t)kMaxBatchPairs);
+        std::vector<unsigned char> bytes(sizeof(BatchArgs), 0);
+        BatchArgs &args = *reinterpret_cast<BatchArgs *>(bytes.data());
+        const int64_t q0 = (int64_t)q.size();
+        auto gathers = [&](int k) {
+            const int64_t n = args.p[k].ntg;
+            for (int64_t t = 0; t < n; t += kBatchPer)
+                q.push_back(make_int4(k, 2, (int)t, (int)std::min<int64_t>(kBatchPer, n - t)));
+        };
+        for (size_t k = 0; k < p1 - p0; ++k) {
+            const BatchPairRef &r = prs[p0 + k];
+            const Pair &Pr = *r.P;
+            if (Pr.n_p2p_items >= INT32_MAX || Pr.n_m2p_items >= INT32_MAX || r.G->n >= INT32_MAX)
+                fail(PB_EINVAL, "internal: batched operator pair too large");
+            BatchPair &b = args.p[k];
+            b.p2p = p2p_args32(Pr, *r.G, *r.T, r.use_self);
+            b.m2p = m2p_args32(Pr, *r.T);
+            b.ga = gather_args32(Pr, *r.G, r.use_self, r.dphi, r.T->phf.p);
+            b.n_m2p_items = Pr.n_m2p_items;
+            b.ntg = r.G->n;
+            b.problem = r.problem;
+            const size_t e0 = q.size();
+            for (int64_t i = 0; i < Pr.n_p2p_items; i += kBatchPer)
+                q.push_back(make_int4((int)k, 0, (int)i, (int)std::min<int64_t>(kBatchPer, Pr.n_p2p_items - i)));
+            const int64_t ntask = (Pr.n_m2p_items + 1) / 2;
+            for (int64_t t = 0; t < ntask; t += kBatchPer)
+                q.push_back(make_int4((int)k, 1, (int)(2 * t), (int)std::min<int64_t>(kBatchPer, ntask - t)));
+            b.need = (unsigned)(q.size() - e0);
+            // a pair's gathers follow the next pair's direct and far-field entries
+            if (k > 0) gathers((int)k - 1);
+        }
+        gathers((int)(p1 - p0) - 1);
+        bp.seg_args.push_back(std::move(bytes));
+        bp.seg_q.emplace_back(q0, (int64_t)q.size() - q0);
+    }
+    bp.queue.alloc(std::max<size_t>(1, q.size()));
+    if (!q.empty()) bp.queue.upload(q.data(), q.size(), s);
+    bp.cnt.alloc(std::max<size_t>(1, bp.seg_args.size()) * (1 + kMaxBatchPairs));
+    bp.active.alloc(std::max(1, nproblems));
+    bp.status.alloc(2);
+    bp.active_h.alloc(std::max(1, nproblems));
+    bp.status_h.alloc(2);
+    for (int i = 0; i < nproblems; ++i) bp.active_h.p[i] = 0;
+    bp.status_h.p[0] = PB_OK;
+    bp.status_h.p[1] = 0;
+    bp.extra = g_fault_wait ? 1u : 0u;
+    bp.cap = g_fault_wait ? (1ll << 12) : (1ll << 24);   // polls 128 ns apart: ~0.5 ms / ~2 s
+    if (!bp.ev) PB_CUDA_TRY(cudaEventCreateWithFlags(&bp.ev, cudaEventDisableTiming));
+    switch (P) {
+#define PB_BG(PP) case PP: bp.grid = batch_grid<PP>(); break;
+        PB_BG(0) PB_BG(1) PB_BG(2) PB_BG(3) PB_BG(4) PB_BG(5) PB_BG(6) PB_BG(7) PB_BG(8)
+#undef PB_BG
+    }
+}
+
+void batch_operator_launch(BatchPlan &bp, cudaStream_t s) {
+    PB_CUDA_TRY(cudaMemcpyAsync(bp.active.p, bp.active_h.p, sizeof(int) * std::max(1, bp.nproblems),
+                                cudaMemcpyHostToDevice, s));
+    PB_CUDA_TRY(cudaMemsetAsync(bp.cnt.p, 0, sizeof(unsigned) * bp.cnt.n, s));
+    PB_CUDA_TRY(cudaMemsetAsync(bp.status.p, 0, 2 * sizeof(int), s));
+    for (size_t g = 0; g < bp.seg_args.size(); ++g) {
+        const BatchArgs &args = *reinterpret_cast<const BatchArgs *>(bp.seg_args[g].data());
+        const int4 *queue = bp.queue.p + bp.seg_q[g].first;
+        const int64_t nq = bp.seg_q[g].second;
+        unsigned *cnt = bp.cnt.p + g * (1 + kMaxBatchPairs);
+        switch (bp.P) {
+#define PB_BL(PP)                                                                                                 \
+    case PP:                                                                                                      \
+        batch_operator_kernel<PP><<<bp.grid, 128, 0, s>>>(args, queue, nq, bp.active.p, cnt, bp.status.p,         \
+                                                          bp.cap, bp.extra);                                      \
+        break;
+            PB_BL(0) PB_BL(1) PB_BL(2) PB_BL(3) PB_BL(4) PB_BL(5) PB_BL(6) PB_BL(7) PB_BL(8)
+#undef PB_BL
+        }
+        PB_LAUNCH_CHECK();
+    }
+    PB_CUDA_TRY(cudaMemcpyAsync(bp.status_h.p, bp.status.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
 }
 
 }  // namespace pb

@@ -1,6 +1,9 @@
 // Evaluation-phase entry points of the treecode (treecode.cu).
 #pragma once
 
+#include <utility>
+#include <vector>
+
 #include "model.cuh"
 
 namespace pb {
@@ -46,5 +49,44 @@ void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, 
 void targets_to_float(Pair &Pr, const Targets &G, const Tree &Tr, cudaStream_t s);
 void launch_combine(int64_t n, const int32_t *rank, const double *phi_s, double half, const CombineRow &row, double *y,
                     cudaStream_t s);
+
+// ---------------------------------------------------------------- batched operator
+// The direct sums, far-field sums and gathers of several problems' operator
+// applications in one persistent launch over a device queue of (pair, phase,
+// tile) entries (treecode.cu, batch_operator_kernel); each pair's gathers wait,
+// with a bounded number of polls, until its direct and far-field entries are
+// done.  Serves mixed-precision pairs of one Laplace and one Yukawa kernel
+// with the radial-form M2P whose direct sums keep the own panel's points
+// (K = 3): single-surface molecules such as binding triplets and ligand fleets.
+struct BatchPairRef {
+    const Pair *P;
+    const Targets *G;
+    const Tree *T;           // source tree (its FP32 densities phf feed the near corrections)
+    bool use_self;
+    const double *dphi;      // FP64 dphi of the source surface inside the operator's input vector
+    int problem;             // index of the problem's active flag
+};
+struct BatchPlan {
+    int P = -1, nproblems = 0, npairs = 0, grid = 0;
+    std::vector<std::vector<unsigned char>> seg_args;   // per launch: the pair descriptors (parameter space)
+    std::vector<std::pair<int64_t, int64_t>> seg_q;      // per launch: its queue entries (offset, count)
+    DevBuf<int4> queue;                // (pair within the launch, phase, first, count)
+    DevBuf<unsigned> cnt;              // per launch: [0] next entry, [1 + k] done entries of pair k
+    DevBuf<int> active, status;        // per-problem flags; status[0] code, status[1] abort flag
+    PinnedBuf<int> active_h, status_h; // host copies: set active_h before a launch, read status_h after it
+    long long cap = 0;                 // polls of a waiting gather before it gives up
+    unsigned extra = 0;                // added to every pair's count (PB_FAULT=wait)
+    cudaEvent_t ev = nullptr;
+    BatchPlan() = default;
+    BatchPlan(const BatchPlan &) = delete;
+    BatchPlan &operator=(const BatchPlan &) = delete;
+    ~BatchPlan();
+};
+bool batch_pair_eligible(const Pair &Pr, const Params &prm, bool use_self);
+void batch_plan_build(BatchPlan &bp, const std::vector<BatchPairRef> &pairs, int nproblems, int P, cudaStream_t s);
+// One operator application (P2P, M2P, gather) of every pair whose problem has
+// its active_h flag set, queued on s; status_h[0] is PB_OK or PB_ETIMEOUT once
+// s has been synchronised.
+void batch_operator_launch(BatchPlan &bp, cudaStream_t s);
 
 }  // namespace pb

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libpbbem.so")
 
 PB_OK, PB_EINVAL, PB_ENOMEM, PB_ECUDA, PB_ENOCONV, PB_ETIMEOUT, PB_ENOTSETUP = range(7)
 PB_FP64, PB_MIXED = 0, 1
+PB_OPT_BATCH_PERSISTENT = 1
 _ERRNAMES = {1: "PB_EINVAL", 2: "PB_ENOMEM", 3: "PB_ECUDA", 4: "PB_ENOCONV", 5: "PB_ETIMEOUT",
              6: "PB_ENOTSETUP"}
 
@@ -78,6 +79,7 @@ _SIGS = {
     "pb_ctx_destroy": ([_vp], None),
     "pb_last_error": ([_vp], ctypes.c_char_p),
     "pb_ctx_stream": ([_vp], _vp),
+    "pb_ctx_set_option": ([_vp, _int, ctypes.c_longlong], _int),
     "pb_problem_create": ([_vp, ctypes.POINTER(_vp)], _int),
     "pb_problem_destroy": ([_vp], None),
     "pb_add_region": ([_vp, _dbl, _dbl, ctypes.POINTER(_int)], _int),
@@ -158,6 +160,10 @@ class Context:
     @property
     def stream(self) -> int:
         return _lib.pb_ctx_stream(self._h) or 0
+
+    def set_option(self, option: int, value: int):
+        """pb_ctx_set_option (PB_OPT_BATCH_PERSISTENT: 1 or 0)."""
+        self.check(_lib.pb_ctx_set_option(self._h, int(option), int(value)))
 
     def check(self, rc):
         if rc != PB_OK:

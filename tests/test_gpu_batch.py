@@ -1,10 +1,21 @@
-"""Batched solves (lock-step GMRES on pool streams) and the binding energy (Eq. bind_energy).
+"""Batched solves and the binding energy (Eq. bind_energy).
 
-A batched problem runs exactly the kernels of a single solve on another
-stream, and every reduction has a fixed order, so its energy equals the
-single solve's bit for bit.  The binding energy of a small synthetic complex
-is checked against the dense oracle (LU) and the Coulomb energies.
+A batch of single-surface FP32-mixed molecules runs its operator
+applications as one persistent launch per GMRES step over a queue of
+(problem, phase, tile) entries; other batches run every problem's GMRES
+cycle as a device-driven graph on a pool stream.  Both compute exactly the
+arithmetic of a single solve, and every reduction has a fixed order, so the
+energies equal the single solves' bit for bit.  The binding energy of a small
+synthetic complex is checked against the dense oracle (LU) and the Coulomb
+energies.  The persistent launch's bounded wait is made to run out (a count
+that nothing reaches, PB_FAULT=wait, in a child process): the batch returns
+PB_ETIMEOUT and the context stays usable.
 """
+import json
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -36,12 +47,77 @@ def test_batch_equals_single_direct():
         assert a.dG_solv == b.dG_solv
 
 
-def test_batch_equals_single_treecode_fleet():
-    dicts = ligand_fleet(count=6, n_min=150, n_max=600, spacing=1.4)
-    single, batch = _batch(dicts, MIXED)
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_batch_equals_single_treecode_fleet(persistent):
+    from paper_1309_4018_b300 import pbbem
+    ctx().set_option(pbbem.PB_OPT_BATCH_PERSISTENT, persistent)
+    try:
+        dicts = ligand_fleet(count=6, n_min=150, n_max=600, spacing=1.4)
+        single, batch = _batch(dicts, MIXED)
+    finally:
+        ctx().set_option(pbbem.PB_OPT_BATCH_PERSISTENT, 1)
     for a, b in zip(single, batch):
         assert b.converged and a.iterations == b.iterations
         assert a.dG_solv == b.dG_solv
+
+
+def test_batch_persistent_mixed_triplet_and_theta_variants():
+    # the binding triplet's three molecules, FP32-mixed, at two treecode settings
+    from paper_1309_4018_b300 import pbbem
+    cx, rec, lig = binding_triplet(n_rec=400, n_lig=120, spacing=1.6)
+    for kw in (dict(theta=0.5, P=6, ncrit=100), dict(theta=0.6, P=4, ncrit=60)):
+        single, batch = _batch([cx, rec, lig], dict(MIXED, **kw))
+        for a, b in zip(single, batch):
+            assert b.converged and a.iterations == b.iterations and a.dG_solv == b.dG_solv
+
+
+def test_batch_option_rejects_bad_values():
+    from paper_1309_4018_b300 import pbbem
+    with pytest.raises(pbbem.PBError):
+        ctx().set_option(pbbem.PB_OPT_BATCH_PERSISTENT, 2)
+    with pytest.raises(pbbem.PBError):
+        ctx().set_option(99, 1)
+
+
+_TIMEOUT = r"""
+import json, sys
+sys.path.insert(0, {root!r})
+from paper_1309_4018_b300 import pbbem
+from synth.configs import ligand_fleet
+ctx = pbbem.Context(0)
+dicts = ligand_fleet(count=3, n_min=150, n_max=400, spacing=1.6)
+def probs():
+    out = []
+    for d in dicts:
+        p = pbbem.Problem.from_dict(ctx, d)
+        p.setup(precision="mixed", gmres_tol=1e-5)
+        out.append(p)
+    return out
+out = {{}}
+try:
+    pbbem.solve_batch(ctx, probs())
+    out["batch"] = "ok"
+except pbbem.PBError as e:
+    out["batch"] = [e.code, str(e)]
+# the context is still usable: single solves and the per-problem batch path
+ps = probs()
+out["single"] = [p.solve().dG_solv for p in ps]
+ctx.set_option(pbbem.PB_OPT_BATCH_PERSISTENT, 0)
+out["graphs"] = [r.dG_solv for r in pbbem.solve_batch(ctx, probs())]
+print(json.dumps(out))
+"""
+
+
+def test_persistent_batch_bounded_wait_times_out():
+    from paper_1309_4018_b300 import pbbem
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PB_FAULT="wait")
+    p = subprocess.run([sys.executable, "-c", _TIMEOUT.format(root=root)], env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert p.returncode == 0, p.stderr[-2000:]
+    out = json.loads(p.stdout.strip().splitlines()[-1])
+    assert out["batch"][0] == pbbem.PB_ETIMEOUT and "bounded wait" in out["batch"][1]
+    assert out["graphs"] == out["single"]
 
 
 def test_binding_energy_vs_oracle():
