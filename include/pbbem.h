@@ -96,8 +96,8 @@ void pb_ctx_destroy(pb_ctx *ctx);
 const char *pb_last_error(pb_ctx *ctx);
 /* The cudaStream_t all work of this context is issued on (for event timing). */
 void *pb_ctx_stream(pb_ctx *ctx);
-/* Context options (not in the paper).  PB_OPT_BATCH_PERSISTENT (1, the
- * default, or 0): whether pb_solve_batch runs the operator applications of
+/* Context options (not in the paper).  PB_OPT_BATCH_PERSISTENT (0, the
+ * default, or 1): whether pb_solve_batch runs the operator applications of
  * an eligible batch as one persistent launch per GMRES step (see
  * pb_solve_batch).  PB_EINVAL for an unknown option or value. */
 #define PB_OPT_BATCH_PERSISTENT 1
@@ -186,21 +186,21 @@ int pb_rhs(pb_problem *pb, double *b);
 int pb_solve(pb_problem *pb, const double *x0, pb_result *out);
 /* Solve n set-up problems of this context together (the binding triplet, a
  * fleet of ligands; the batching pattern of the production workload, applied
- * to Eq. bind_energy's three solves): every problem runs its own GMRES on one
- * of up to 8 pool streams.  An eligible batch (two or more problems, all
+ * to Eq. bind_energy's three solves).  By default every problem runs its
+ * GMRES cycles as device-driven graphs on one of up to 8 pool streams, one
+ * host synchronisation per cycle round for the whole batch.  With
+ * PB_OPT_BATCH_PERSISTENT = 1 an eligible batch (two or more problems, all
  * PB_MIXED with the same P <= 8, every surface between a kappa = 0 region
- * and a kappa > 0 region with K = 3: single-surface molecules) advances its
- * Arnoldi steps in lock step, one host synchronisation per step for the
- * whole batch, and each step's direct sums, far-field sums and per-target
- * gathers of all problems run as ONE persistent launch over a device queue
- * of (problem, phase, tile) entries; a problem's gathers wait, with a bounded
- * number of polls, for its direct and far-field entries, and a wait that runs
- * out ends the call with PB_ETIMEOUT (the context stays usable).  Other
- * batches (or PB_OPT_BATCH_PERSISTENT = 0) run each problem's GMRES cycle as
- * a device-driven graph, one host synchronisation per cycle round.  Either
- * way the energies equal those of single pb_solve calls bit for bit.  The
- * call is ordered on the context stream.  out: n results (may be NULL).
- * PB_ENOCONV if any problem reached max_iter (every result is still written). */
+ * and a kappa > 0 region with K = 3: single-surface molecules) instead
+ * advances its Arnoldi steps in lock step, one host synchronisation per step,
+ * and each step's direct sums, far-field sums and per-target gathers of all
+ * problems run as ONE persistent launch over a device queue of (problem,
+ * phase, tile) entries; a problem's gathers wait, with a bounded number of
+ * polls, for its direct and far-field entries, and a wait that runs out ends
+ * the call with PB_ETIMEOUT (the context stays usable).  Either way the
+ * energies equal those of single pb_solve calls bit for bit.  The call is
+ * ordered on the context stream.  out: n results (may be NULL).  PB_ENOCONV
+ * if any problem reached max_iter (every result is still written). */
 int pb_solve_batch(pb_ctx *ctx, pb_problem *const *probs, int n, pb_result *out);
 /* Binding energy (Eq. bind_energy): solves complex, receptor and ligand as one
  * batch and returns ddG = E_cx - E_rec - E_lig with E = dG_solv + the Coulomb

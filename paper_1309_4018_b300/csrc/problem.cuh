@@ -18,7 +18,7 @@ struct pb_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaStream_t> pool;   // streams of batched solves (created on first use)
     std::vector<cudaEvent_t> pool_ev;
-    int batch_persistent = 1;         // pb_solve_batch: one persistent launch per step for eligible batches
+    int batch_persistent = 0;         // pb_solve_batch: one persistent launch per step for eligible batches
     std::string err;
 };
 
