@@ -73,6 +73,9 @@ typedef struct {
                           panel's 2x2 self block (not in the paper; same solution) [0] */
     int ncrit_adjoint; /* a box of the transposed treecode (pb_gradient, pb_apply_transpose)
                           with >= ncrit_adjoint collocation points is split [ncrit] */
+    int p2p_tile;      /* targets per direct-sum (P2P) work item, 1..32: a warp sums one leaf's
+                          sources, staged 32 at a time, for this many targets that list the
+                          leaf (not in the paper; the results do not depend on it) [32] */
 } pb_params;
 
 typedef struct {

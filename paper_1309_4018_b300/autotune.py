@@ -1,16 +1,19 @@
-"""Autotuner of the treecode settings (theta, P, ncrit) for batched solves.
+"""Autotuner of the treecode settings (theta, P, ncrit) and the P2P tile for batched solves.
 
 The treecode's cost splits between the direct sums (P2P, whose source tile is
-a leaf of fewer than ncrit points) and the expansions (M2P, whose work grows
-with P and the number of accepted boxes, i.e. falls as theta grows).  Which
-setting is fastest at a given energy accuracy depends on the molecule's size
-and shape, so the tuner measures it:
+a leaf of fewer than ncrit points, swept by a warp for up to p2p_tile
+targets at a time) and the expansions (M2P, whose work grows with P and the
+number of accepted boxes, i.e. falls as theta grows).  Which setting is
+fastest at a given energy accuracy depends on the molecule's size and shape,
+so the tuner measures it:
 
 * `tune` solves one problem with every candidate setting, times setup +
   solve on the device (the library's CUDA events, best of `repeats`),
   measures the energy's error against an accurate reference (theta = 0.3,
-  P = 10, tight GMRES tolerance), and returns the fastest candidate whose
-  error is at most `target` / `safety`.
+  P = 10, tight GMRES tolerance), and keeps the fastest candidate whose
+  error is at most `target` / `safety`; then it times that setting with
+  every P2P tile (targets per work item: the energy does not depend on it)
+  and keeps the fastest.
 * `Schedule` bins problems by panel count (factor-of-two classes), tunes one
   representative per class (the median problem) and hands every problem the
   setting of its class.
@@ -27,6 +30,7 @@ from . import pbbem
 # (theta, P) pairs of roughly balanced accuracy, times leaf sizes
 THETA_P = ((0.7, 3), (0.6, 4), (0.5, 5), (0.5, 6), (0.4, 7), (0.4, 8))
 NCRIT = (100, 200, 300, 500)
+P2P_TILES = (32, 16, 8)
 REFERENCE = dict(theta=0.3, P=10, gmres_tol=1e-7)
 
 
@@ -37,9 +41,10 @@ class Choice:
     ncrit: int
     time_s: float
     rel_error: float
+    p2p_tile: int = 32
 
     def params(self) -> dict:
-        return dict(theta=self.theta, P=self.P, ncrit=self.ncrit)
+        return dict(theta=self.theta, P=self.P, ncrit=self.ncrit, p2p_tile=self.p2p_tile)
 
 
 def candidates(theta_p=THETA_P, ncrit=NCRIT):
@@ -68,7 +73,8 @@ def pick(measured, target, safety=2.0):
     return min(measured, key=lambda m: m[2])
 
 
-def tune(ctx, d, target=1e-4, base=None, cands=None, repeats=2, safety=2.0, reference=None) -> Choice:
+def tune(ctx, d, target=1e-4, base=None, cands=None, repeats=2, safety=2.0, reference=None,
+         tiles=P2P_TILES) -> Choice:
     """Fastest candidate setting for problem dict `d` within `target` relative energy error.
 
     base: other pb_params fields (precision, gmres_tol, K, ...), mixed precision by default.
@@ -82,7 +88,14 @@ def tune(ctx, d, target=1e-4, base=None, cands=None, repeats=2, safety=2.0, refe
         e, t = _energy_and_time(ctx, d, dict(base, **c), repeats)
         measured.append((c, t, abs(e - reference) / abs(reference)))
     c, t, err = pick(measured, target, safety)
-    return Choice(c["theta"], c["P"], c["ncrit"], t, err)
+    tile = c.get("p2p_tile", 32)
+    for tl in tiles:
+        if tl == tile:
+            continue
+        _, tt = _energy_and_time(ctx, d, dict(base, **dict(c, p2p_tile=tl)), repeats)
+        if tt < t:
+            tile, t = tl, tt
+    return Choice(c["theta"], c["P"], c["ncrit"], t, err, tile)
 
 
 def panel_count(d) -> int:

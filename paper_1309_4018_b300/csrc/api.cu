@@ -75,6 +75,7 @@ Params resolve(const pb_params *p) {
         r.precision = p->precision;
         r.precond = p->no_precond == 0;
         r.ncrit_adjoint = p->ncrit_adjoint;
+        if (p->p2p_tile) r.p2p_tile = p->p2p_tile;
     }
     if (!valid_rule(r.K)) fail(PB_EINVAL, "K must be 1, 3, 7 or 19");
     if (!valid_rule(r.K_fine)) fail(PB_EINVAL, "K_fine must be 1, 3, 7 or 19");
@@ -82,6 +83,7 @@ Params resolve(const pb_params *p) {
     if (r.P < 0 || r.P > kMaxP) fail(PB_EINVAL, "P must be in 0..12");
     if (r.ncrit < 1) fail(PB_EINVAL, "ncrit must be >= 1");
     if (r.ncrit_adjoint < 0) fail(PB_EINVAL, "ncrit_adjoint must be >= 0");
+    if (r.p2p_tile < 1 || r.p2p_tile > 32) fail(PB_EINVAL, "p2p_tile must be in 1..32");
     if (r.restart < 1 || r.restart > 200) fail(PB_EINVAL, "restart must be in 1..200");
     if (r.max_iter < 1) fail(PB_EINVAL, "max_iter must be >= 1");
     if (!(r.tol > 0.0)) fail(PB_EINVAL, "gmres_tol must be > 0");

@@ -17,6 +17,7 @@ struct Params {
     int precision = PB_FP64;
     bool precond = true;
     int ncrit_adjoint = 0;   // 0: ncrit
+    int p2p_tile = 32;       // targets per P2P work item
 };
 
 struct Region {

@@ -873,7 +873,7 @@ void build_targets(Targets &G, const double *d_x, int64_t n, int surface, cudaSt
 
 void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
                  cudaStream_t s) {
-    build_far_lists(Pr, G, T, prm, s, 32);
+    build_far_lists(Pr, G, T, prm, s, prm.p2p_tile);
     build_near_lists(Pr, G, T, src, prm, use_self, s);
 }
 
