@@ -657,7 +657,7 @@ __global__ void point_pan32_kernel(int64_t npts, const int32_t *__restrict__ pid
 __global__ void reach_kernel(int64_t n, const double *__restrict__ v, const int32_t *__restrict__ t,
                              const double *__restrict__ cen, const double *__restrict__ L, double thres,
                              unsigned long long *__restrict__ out) {
-    double m = 0.0;
+    double m = 0.0, h = 0.0;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         double r = 0.0;
         for (int c = 0; c < 3; ++c) {
@@ -666,9 +666,105 @@ __global__ void reach_kernel(int64_t n, const double *__restrict__ v, const int3
             r = fmax(r, sqrt(dx * dx + dy * dy + dz * dz));
         }
         m = fmax(m, thres * L[j] + r);
+        h = fmax(h, thres * L[j]);
     }
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m * (1.0 + 1e-12) + 1e-12));
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        h = fmax(h, __shfl_xor_sync(0xffffffffu, h, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, (unsigned long long)__double_as_longlong(m * (1.0 + 1e-12) + 1e-12));
+        atomicMax(out + 1, (unsigned long long)__double_as_longlong(h * (1.0 + 1e-12) + 1e-12));
+    }
+}
+
+// ---------------------------------------------------------------- near lists through a cell grid
+// Panel centroids binned in a uniform grid of cells at least as wide as the
+// largest near-singular radius thres L_j: every panel near a target lies in
+// one of the 27 cells around the target's cell.  The decision is the same
+// exact FP64 test as in near_kernel, so the lists are the same.
+struct NearGrid {
+    double corner[3];
+    double inv_cell;
+    int n[3];
+};
+
+__device__ __forceinline__ int grid_axis(double v, double c, double inv, int n) {
+    const double f = floor((v - c) * inv);
+    return f < -2.0 ? -2 : (f > (double)(n + 1) ? n + 1 : (int)f);
+}
+
+__global__ void cell_count_kernel(int64_t n, const double *__restrict__ cen, NearGrid g, int32_t *__restrict__ cellof,
+                                  int32_t *__restrict__ cnt) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int c[3];
+    for (int a = 0; a < 3; ++a) c[a] = min(max(grid_axis(cen[3 * j + a], g.corner[a], g.inv_cell, g.n[a]), 0), g.n[a] - 1);
+    const int flat = (c[0] * g.n[1] + c[1]) * g.n[2] + c[2];
+    cellof[j] = flat;
+    atomicAdd(cnt + flat, 1);
+}
+
+__global__ void cell_fill_kernel(int64_t n, const int32_t *__restrict__ cellof, const int64_t *__restrict__ off,
+                                 int32_t *__restrict__ cursor, int32_t *__restrict__ order) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int c = cellof[j];
+    order[off[c] + atomicAdd(cursor + c, 1)] = (int32_t)j;
+}
+
+// One thread per target: the panels of the 27 cells around it; an FP32
+// distance test with a safety margin prefilters, the FP64 is_near decides.
+// Near panels whose points all lie in the target's direct-sum leaves go to
+// its row (any order; near_compact_kernel sorts), the others are counted as
+// excluded.  Outputs as near_kernel<2>.
+__global__ void __launch_bounds__(128) near_grid_kernel(
+    int64_t ntg, int K, const double *__restrict__ xs, const int32_t *__restrict__ selfp, int use_self,
+    const int64_t *__restrict__ p2p_ptr, const int32_t *__restrict__ p2p_leafidx, const int32_t *__restrict__ point_leaf,
+    const double *__restrict__ cen, const double *__restrict__ L, const float4 *__restrict__ pan32, double ox, double oy,
+    double oz, double thres, NearGrid g, const int64_t *__restrict__ off, const int32_t *__restrict__ order,
+    int32_t *__restrict__ ncount, int32_t *__restrict__ excl, int32_t *__restrict__ self_excl,
+    int32_t *__restrict__ rows, int32_t *__restrict__ overflow) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntg) return;
+    const double x = xs[3 * i], y = xs[3 * i + 1], z = xs[3 * i + 2];
+    const float fx = (float)(x - ox), fy = (float)(y - oy), fz = (float)(z - oz);
+    const int me = use_self ? selfp[i] : -1;
+    const int64_t l0 = p2p_ptr[i];
+    const int32_t *lst = p2p_leafidx + l0;
+    const int64_t nl = p2p_ptr[i + 1] - l0;
+    const int cx = grid_axis(x, g.corner[0], g.inv_cell, g.n[0]);
+    const int cy = grid_axis(y, g.corner[1], g.inv_cell, g.n[1]);
+    const int cz = grid_axis(z, g.corner[2], g.inv_cell, g.n[2]);
+    int cnt = 0, ex = 0;
+    int32_t *row = rows + i * kNearCap;
+    for (int ax = max(cx - 1, 0); ax <= min(cx + 1, g.n[0] - 1); ++ax)
+        for (int ay = max(cy - 1, 0); ay <= min(cy + 1, g.n[1] - 1); ++ay)
+            for (int az = max(cz - 1, 0); az <= min(cz + 1, g.n[2] - 1); ++az) {
+                const int c = (ax * g.n[1] + ay) * g.n[2] + az;
+                for (int64_t q = off[c]; q < off[c + 1]; ++q) {
+                    const int j = order[q];
+                    const float4 pc = pan32[j];
+                    const float dx = fx - pc.x, dy = fy - pc.y, dz = fz - pc.z;
+                    if (!(dx * dx + dy * dy + dz * dz < pc.w) || j == me || !is_near(x, y, z, cen, L, thres, j)) continue;
+                    bool all = true;
+                    for (int kk = 0; kk < K && all; ++kk) all = in_sorted(lst, nl, point_leaf[(int64_t)j * K + kk]);
+                    if (all) {
+                        if (cnt < kNearCap) row[cnt] = j;
+                        ++cnt;
+                    } else {
+                        ++ex;
+                    }
+                }
+            }
+    ncount[i] = cnt;
+    excl[i] = ex;
+    if (cnt > kNearCap) atomicExch(overflow, 1);
+    int se = 0;
+    if (me >= 0)
+        for (int kk = 0; kk < K; ++kk)
+            if (!in_sorted(lst, nl, point_leaf[(int64_t)me * K + kk])) se = 1;
+    self_excl[i] = se;
 }
 
 // Copies every target's row into the CSR list in ascending order (insertion sort).
@@ -1022,37 +1118,60 @@ void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &
     }
     // near-singular lists
     TmpBuf<int32_t> nc(m, s), ex(m, s), se(m, s);
-    TmpBuf<unsigned long long> reach_d(1, s);
-    PB_CUDA_TRY(cudaMemsetAsync(reach_d.p, 0, sizeof(unsigned long long), s));
+    TmpBuf<unsigned long long> reach_d(2, s);
+    PB_CUDA_TRY(cudaMemsetAsync(reach_d.p, 0, 2 * sizeof(unsigned long long), s));
     reach_kernel<<<std::min<int64_t>(592, div_up(src.n, 256)), 256, 0, s>>>(src.n, src.verts.p, src.tris.p, src.cen.p,
                                                                            src.L.p, prm.thres, reach_d.p);
     PB_LAUNCH_CHECK();
-    unsigned long long rbits = 0;
-    PB_CUDA_TRY(cudaMemcpyAsync(&rbits, reach_d.p, sizeof(rbits), cudaMemcpyDeviceToHost, s));
+    unsigned long long rbits[2] = {0, 0};
+    PB_CUDA_TRY(cudaMemcpyAsync(rbits, reach_d.p, sizeof(rbits), cudaMemcpyDeviceToHost, s));
     TmpBuf<float4> pan32(std::max<int64_t>(1, src.n), s);
     pan32_kernel<<<div_up(src.n, 256), 256, 0, s>>>(src.n, src.cen.p, src.L.p, prm.thres, T.origin[0], T.origin[1],
                                                      T.origin[2], pan32.p);
     PB_LAUNCH_CHECK();
-    TmpBuf<float4> ppan32(std::max<int64_t>(1, T.npts), s);
-    if (T.npts) {
-        point_pan32_kernel<<<div_up(T.npts, 256), 256, 0, s>>>(T.npts, T.pids.p, pan32.p, ppan32.p);
+    PB_CUDA_TRY(cudaStreamSynchronize(s));
+    double reach = 0.0, hmax = 0.0;
+    std::memcpy(&reach, &rbits[0], sizeof(reach));
+    std::memcpy(&hmax, &rbits[1], sizeof(hmax));
+    // cell grid over the tree's root cube (it holds every centroid): cells at
+    // least as wide as the largest near radius, at most about two per panel
+    NearGrid g{};
+    {
+        const double cmin = hmax * 1.001 + 1e-9;
+        int na = (int)std::max(1.0, std::floor(T.side / cmin));
+        while ((double)na * na * na > 2.0 * (double)src.n + 64.0 && na > 1) --na;
+        const double cell = std::max(cmin, T.side / na);
+        for (int a = 0; a < 3; ++a) {
+            g.corner[a] = T.corner[a];
+            g.n[a] = na;
+        }
+        g.inv_cell = 1.0 / cell;
+    }
+    const int64_t ncell = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    TmpBuf<int32_t> cellof(std::max<int64_t>(1, src.n), s), ccnt(ncell, s), ccur(ncell, s),
+        corder(std::max<int64_t>(1, src.n), s);
+    TmpBuf<int64_t> coff(ncell + 1, s);
+    PB_CUDA_TRY(cudaMemsetAsync(ccnt.p, 0, ncell * sizeof(int32_t), s));
+    PB_CUDA_TRY(cudaMemsetAsync(ccur.p, 0, ncell * sizeof(int32_t), s));
+    if (src.n) {
+        cell_count_kernel<<<div_up(src.n, 256), 256, 0, s>>>(src.n, src.cen.p, g, cellof.p, ccnt.p);
         PB_LAUNCH_CHECK();
     }
-    PB_CUDA_TRY(cudaStreamSynchronize(s));
-    double reach = 0.0;
-    std::memcpy(&reach, &rbits, sizeof(reach));
+    exclusive_scan_i32_to_i64(ccnt.p, coff.p, ncell, s);
+    if (src.n) {
+        cell_fill_kernel<<<div_up(src.n, 256), 256, 0, s>>>(src.n, cellof.p, coff.p, ccur.p, corder.p);
+        PB_LAUNCH_CHECK();
+    }
     Pr.near_ptr.alloc(m + 1);
     bool done = false;
     if (m) {
         // one pass: counts and a row of panels per target
         TmpBuf<int32_t> rows((size_t)m * kNearCap, s), ovf(1, s);
         PB_CUDA_TRY(cudaMemsetAsync(ovf.p, 0, 4, s));
-        near_kernel<2><<<div_up(m, 4), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
-                                                    pleaf.p, T.leaf_node.p, T.start.p, T.count.p, T.perm.p, T.pids.p,
-                                                    T.point_leaf.p, src.cen.p, src.L.p, ppan32.p, T.origin[0],
-                                                    T.origin[1], T.origin[2], prm.thres, nc.p, ex.p, se.p, nullptr,
-                                                    nullptr, Pr.m2p_ptr.p, Pr.m2p_node.p, T.cen32.p, reach, rows.p,
-                                                    ovf.p);
+        near_grid_kernel<<<div_up(m, 128), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
+                                                         pleaf.p, T.point_leaf.p, src.cen.p, src.L.p, pan32.p,
+                                                         T.origin[0], T.origin[1], T.origin[2], prm.thres, g, coff.p,
+                                                         corder.p, nc.p, ex.p, se.p, rows.p, ovf.p);
         PB_LAUNCH_CHECK();
         int hov = 0;
         PB_CUDA_TRY(cudaMemcpyAsync(&hov, ovf.p, 4, cudaMemcpyDeviceToHost, s));
@@ -1075,6 +1194,11 @@ void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &
     Pr.self_excl = device_sum_i32(se.p, m, s);
     if (!done) {
         // some target has more than kNearCap near panels: fill the CSR list in a second pass
+        TmpBuf<float4> ppan32(std::max<int64_t>(1, T.npts), s);
+        if (T.npts) {
+            point_pan32_kernel<<<div_up(T.npts, 256), 256, 0, s>>>(T.npts, T.pids.p, pan32.p, ppan32.p);
+            PB_LAUNCH_CHECK();
+        }
         near_kernel<1><<<div_up(m, 4), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
                                                     pleaf.p, T.leaf_node.p, T.start.p, T.count.p, T.perm.p, T.pids.p,
                                                     T.point_leaf.p, src.cen.p, src.L.p, ppan32.p, T.origin[0],
