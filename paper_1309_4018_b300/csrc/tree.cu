@@ -705,27 +705,32 @@ __global__ void cell_count_kernel(int64_t n, const double *__restrict__ cen, Nea
     atomicAdd(cnt + flat, 1);
 }
 
+// Panel ids and FP32 records (centroid, near radius bound) in cell order.
 __global__ void cell_fill_kernel(int64_t n, const int32_t *__restrict__ cellof, const int64_t *__restrict__ off,
-                                 int32_t *__restrict__ cursor, int32_t *__restrict__ order) {
+                                 int32_t *__restrict__ cursor, const float4 *__restrict__ pan32,
+                                 int32_t *__restrict__ order, float4 *__restrict__ cpan) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const int c = cellof[j];
-    order[off[c] + atomicAdd(cursor + c, 1)] = (int32_t)j;
+    const int64_t q = off[c] + atomicAdd(cursor + c, 1);
+    order[q] = (int32_t)j;
+    cpan[q] = pan32[j];
 }
 
-// One thread per target: the panels of the 27 cells around it; an FP32
-// distance test with a safety margin prefilters, the FP64 is_near decides.
-// Near panels whose points all lie in the target's direct-sum leaves go to
-// its row (any order; near_compact_kernel sorts), the others are counted as
-// excluded.  Outputs as near_kernel<2>.
+// One warp per target: its lanes read the panels of the 27 cells around it
+// in cell order (coalesced); an FP32 distance test with a safety margin
+// prefilters, the FP64 is_near decides.  Near panels whose points all lie in
+// the target's direct-sum leaves go to its row (any order; near_compact_kernel
+// sorts), the others are counted as excluded.  Outputs as near_kernel<2>.
 __global__ void __launch_bounds__(128) near_grid_kernel(
     int64_t ntg, int K, const double *__restrict__ xs, const int32_t *__restrict__ selfp, int use_self,
     const int64_t *__restrict__ p2p_ptr, const int32_t *__restrict__ p2p_leafidx, const int32_t *__restrict__ point_leaf,
-    const double *__restrict__ cen, const double *__restrict__ L, const float4 *__restrict__ pan32, double ox, double oy,
-    double oz, double thres, NearGrid g, const int64_t *__restrict__ off, const int32_t *__restrict__ order,
+    const double *__restrict__ cen, const double *__restrict__ L, double ox, double oy, double oz, double thres,
+    NearGrid g, const int64_t *__restrict__ off, const int32_t *__restrict__ order, const float4 *__restrict__ cpan,
     int32_t *__restrict__ ncount, int32_t *__restrict__ excl, int32_t *__restrict__ self_excl,
     int32_t *__restrict__ rows, int32_t *__restrict__ overflow) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 4 + warp;
     if (i >= ntg) return;
     const double x = xs[3 * i], y = xs[3 * i + 1], z = xs[3 * i + 2];
     const float fx = (float)(x - ox), fy = (float)(y - oy), fz = (float)(z - oz);
@@ -742,29 +747,44 @@ __global__ void __launch_bounds__(128) near_grid_kernel(
         for (int ay = max(cy - 1, 0); ay <= min(cy + 1, g.n[1] - 1); ++ay)
             for (int az = max(cz - 1, 0); az <= min(cz + 1, g.n[2] - 1); ++az) {
                 const int c = (ax * g.n[1] + ay) * g.n[2] + az;
-                for (int64_t q = off[c]; q < off[c + 1]; ++q) {
-                    const int j = order[q];
-                    const float4 pc = pan32[j];
-                    const float dx = fx - pc.x, dy = fy - pc.y, dz = fz - pc.z;
-                    if (!(dx * dx + dy * dy + dz * dz < pc.w) || j == me || !is_near(x, y, z, cen, L, thres, j)) continue;
-                    bool all = true;
-                    for (int kk = 0; kk < K && all; ++kk) all = in_sorted(lst, nl, point_leaf[(int64_t)j * K + kk]);
-                    if (all) {
-                        if (cnt < kNearCap) row[cnt] = j;
-                        ++cnt;
-                    } else {
-                        ++ex;
+                const int64_t q1 = off[c + 1];
+                for (int64_t qb = off[c]; qb < q1; qb += 32) {
+                    const int64_t q = qb + lane;
+                    bool acc = false, exc = false;
+                    int j = -1;
+                    if (q < q1) {
+                        const float4 pc = cpan[q];
+                        const float dx = fx - pc.x, dy = fy - pc.y, dz = fz - pc.z;
+                        if (dx * dx + dy * dy + dz * dz < pc.w) {
+                            j = order[q];
+                            if (j != me && is_near(x, y, z, cen, L, thres, j)) {
+                                bool all = true;
+                                for (int kk = 0; kk < K && all; ++kk)
+                                    all = in_sorted(lst, nl, point_leaf[(int64_t)j * K + kk]);
+                                acc = all;
+                                exc = !all;
+                            }
+                        }
                     }
+                    const uint32_t ba = __ballot_sync(0xffffffffu, acc);
+                    if (acc) {
+                        const int at = cnt + __popc(ba & ((1u << lane) - 1u));
+                        if (at < kNearCap) row[at] = j;
+                    }
+                    cnt += __popc(ba);
+                    ex += __popc(__ballot_sync(0xffffffffu, exc));
                 }
             }
-    ncount[i] = cnt;
-    excl[i] = ex;
-    if (cnt > kNearCap) atomicExch(overflow, 1);
-    int se = 0;
-    if (me >= 0)
-        for (int kk = 0; kk < K; ++kk)
-            if (!in_sorted(lst, nl, point_leaf[(int64_t)me * K + kk])) se = 1;
-    self_excl[i] = se;
+    if (lane == 0) {
+        ncount[i] = cnt;
+        excl[i] = ex;
+        if (cnt > kNearCap) atomicExch(overflow, 1);
+        int se = 0;
+        if (me >= 0)
+            for (int kk = 0; kk < K; ++kk)
+                if (!in_sorted(lst, nl, point_leaf[(int64_t)me * K + kk])) se = 1;
+        self_excl[i] = se;
+    }
 }
 
 // Copies every target's row into the CSR list in ascending order (insertion sort).
@@ -1150,6 +1170,7 @@ void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &
     const int64_t ncell = (int64_t)g.n[0] * g.n[1] * g.n[2];
     TmpBuf<int32_t> cellof(std::max<int64_t>(1, src.n), s), ccnt(ncell, s), ccur(ncell, s),
         corder(std::max<int64_t>(1, src.n), s);
+    TmpBuf<float4> cpan(std::max<int64_t>(1, src.n), s);
     TmpBuf<int64_t> coff(ncell + 1, s);
     PB_CUDA_TRY(cudaMemsetAsync(ccnt.p, 0, ncell * sizeof(int32_t), s));
     PB_CUDA_TRY(cudaMemsetAsync(ccur.p, 0, ncell * sizeof(int32_t), s));
@@ -1159,7 +1180,8 @@ void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &
     }
     exclusive_scan_i32_to_i64(ccnt.p, coff.p, ncell, s);
     if (src.n) {
-        cell_fill_kernel<<<div_up(src.n, 256), 256, 0, s>>>(src.n, cellof.p, coff.p, ccur.p, corder.p);
+        cell_fill_kernel<<<div_up(src.n, 256), 256, 0, s>>>(src.n, cellof.p, coff.p, ccur.p, pan32.p, corder.p,
+                                                            cpan.p);
         PB_LAUNCH_CHECK();
     }
     Pr.near_ptr.alloc(m + 1);
@@ -1168,10 +1190,10 @@ void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &
         // one pass: counts and a row of panels per target
         TmpBuf<int32_t> rows((size_t)m * kNearCap, s), ovf(1, s);
         PB_CUDA_TRY(cudaMemsetAsync(ovf.p, 0, 4, s));
-        near_grid_kernel<<<div_up(m, 128), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
-                                                         pleaf.p, T.point_leaf.p, src.cen.p, src.L.p, pan32.p,
-                                                         T.origin[0], T.origin[1], T.origin[2], prm.thres, g, coff.p,
-                                                         corder.p, nc.p, ex.p, se.p, rows.p, ovf.p);
+        near_grid_kernel<<<div_up(m, 4), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
+                                                       pleaf.p, T.point_leaf.p, src.cen.p, src.L.p, T.origin[0],
+                                                       T.origin[1], T.origin[2], prm.thres, g, coff.p, corder.p,
+                                                       cpan.p, nc.p, ex.p, se.p, rows.p, ovf.p);
         PB_LAUNCH_CHECK();
         int hov = 0;
         PB_CUDA_TRY(cudaMemcpyAsync(&hov, ovf.p, 4, cudaMemcpyDeviceToHost, s));
