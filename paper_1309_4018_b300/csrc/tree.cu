@@ -705,30 +705,52 @@ __global__ void cell_count_kernel(int64_t n, const double *__restrict__ cen, Nea
     atomicAdd(cnt + flat, 1);
 }
 
-// Panel ids and FP32 records (centroid, near radius bound) in cell order.
+// Panel ids, FP32 records (centroid, near radius bound) and FP64 (centroid,
+// L) in cell order.
 __global__ void cell_fill_kernel(int64_t n, const int32_t *__restrict__ cellof, const int64_t *__restrict__ off,
                                  int32_t *__restrict__ cursor, const float4 *__restrict__ pan32,
-                                 int32_t *__restrict__ order, float4 *__restrict__ cpan) {
+                                 const double *__restrict__ cen, const double *__restrict__ L,
+                                 int32_t *__restrict__ order, float4 *__restrict__ cpan, dvec4 *__restrict__ cgeo) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const int c = cellof[j];
     const int64_t q = off[c] + atomicAdd(cursor + c, 1);
     order[q] = (int32_t)j;
     cpan[q] = pan32[j];
+    cgeo[q] = dvec4{cen[3 * j], cen[3 * j + 1], cen[3 * j + 2], L[j]};
 }
 
-// One warp per target: its lanes read the panels of the 27 cells around it
-// in cell order (coalesced); an FP32 distance test with a safety margin
-// prefilters, the FP64 is_near decides.  Near panels whose points all lie in
-// the target's direct-sum leaves go to its row (any order; near_compact_kernel
-// sorts), the others are counted as excluded.  Outputs as near_kernel<2>.
+// One warp per target.  The panels of the 27 cells around the target form one
+// list (the cells' ranges loaded one per lane, their offsets by a warp scan)
+// that the lanes walk 32 entries at a time, whatever the cells' sizes: the
+// FP32 record (prefilter) and the panel id, then the FP64 centroid and L of
+// the exact test, all in cell order; the target's direct-sum leaf list is
+// staged in shared memory for the membership tests of the near panels' points.  The
+// decision is the same FP64 test as is_near.  Near panels whose points all
+// lie in the target's direct-sum leaves go to its row (any order;
+// near_compact_kernel sorts), the others are counted as excluded.  Outputs as
+// near_kernel<2>.
+constexpr int kNearLeafStage = 128;   // direct-sum leaves staged per warp
+
+__device__ __forceinline__ bool in_sorted_shared(const int32_t *a, int n, int v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo < n && a[lo] == v;
+}
+
 __global__ void __launch_bounds__(128) near_grid_kernel(
     int64_t ntg, int K, const double *__restrict__ xs, const int32_t *__restrict__ selfp, int use_self,
     const int64_t *__restrict__ p2p_ptr, const int32_t *__restrict__ p2p_leafidx, const int32_t *__restrict__ point_leaf,
-    const double *__restrict__ cen, const double *__restrict__ L, double ox, double oy, double oz, double thres,
-    NearGrid g, const int64_t *__restrict__ off, const int32_t *__restrict__ order, const float4 *__restrict__ cpan,
+    double ox, double oy, double oz, double thres, NearGrid g, const int64_t *__restrict__ off,
+    const int32_t *__restrict__ order, const float4 *__restrict__ cpan, const dvec4 *__restrict__ cgeo,
     int32_t *__restrict__ ncount, int32_t *__restrict__ excl, int32_t *__restrict__ self_excl,
     int32_t *__restrict__ rows, int32_t *__restrict__ overflow) {
+    __shared__ int32_t sleaf[4][kNearLeafStage];
+    __shared__ int32_t scell[4][27];
+    __shared__ int64_t sbase[4][27];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * 4 + warp;
     if (i >= ntg) return;
@@ -736,45 +758,81 @@ __global__ void __launch_bounds__(128) near_grid_kernel(
     const float fx = (float)(x - ox), fy = (float)(y - oy), fz = (float)(z - oz);
     const int me = use_self ? selfp[i] : -1;
     const int64_t l0 = p2p_ptr[i];
-    const int32_t *lst = p2p_leafidx + l0;
     const int64_t nl = p2p_ptr[i + 1] - l0;
+    const bool staged = nl <= kNearLeafStage;
+    if (staged)
+        for (int u = lane; u < nl; u += 32) sleaf[warp][u] = p2p_leafidx[l0 + u];
+    __syncwarp();
+    auto member = [&](int leaf) {
+        return staged ? in_sorted_shared(sleaf[warp], (int)nl, leaf) : in_sorted(p2p_leafidx + l0, nl, leaf);
+    };
     const int cx = grid_axis(x, g.corner[0], g.inv_cell, g.n[0]);
     const int cy = grid_axis(y, g.corner[1], g.inv_cell, g.n[1]);
     const int cz = grid_axis(z, g.corner[2], g.inv_cell, g.n[2]);
+    // the 27 cells' panels as one list: lane k < 27 holds cell k's range, a
+    // warp scan of the counts gives every cell's first position in the list
+    int64_t cs = 0;
+    int cn = 0;
+    if (lane < 27) {
+        const int ax = cx - 1 + lane / 9, ay = cy - 1 + (lane / 3) % 3, az = cz - 1 + lane % 3;
+        if (ax >= 0 && ax < g.n[0] && ay >= 0 && ay < g.n[1] && az >= 0 && az < g.n[2]) {
+            const int c = (ax * g.n[1] + ay) * g.n[2] + az;
+            cs = off[c];
+            cn = (int)(off[c + 1] - cs);
+        }
+    }
+    int pre = cn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, pre, 31);
+    if (lane < 27) {
+        scell[warp][lane] = pre - cn;   // first list position of cell `lane`
+        sbase[warp][lane] = cs - (pre - cn);
+    }
+    __syncwarp();
+    const double tt = thres;
     int cnt = 0, ex = 0;
     int32_t *row = rows + i * kNearCap;
-    for (int ax = max(cx - 1, 0); ax <= min(cx + 1, g.n[0] - 1); ++ax)
-        for (int ay = max(cy - 1, 0); ay <= min(cy + 1, g.n[1] - 1); ++ay)
-            for (int az = max(cz - 1, 0); az <= min(cz + 1, g.n[2] - 1); ++az) {
-                const int c = (ax * g.n[1] + ay) * g.n[2] + az;
-                const int64_t q1 = off[c + 1];
-                for (int64_t qb = off[c]; qb < q1; qb += 32) {
-                    const int64_t q = qb + lane;
-                    bool acc = false, exc = false;
-                    int j = -1;
-                    if (q < q1) {
-                        const float4 pc = cpan[q];
-                        const float dx = fx - pc.x, dy = fy - pc.y, dz = fz - pc.z;
-                        if (dx * dx + dy * dy + dz * dz < pc.w) {
-                            j = order[q];
-                            if (j != me && is_near(x, y, z, cen, L, thres, j)) {
-                                bool all = true;
-                                for (int kk = 0; kk < K && all; ++kk)
-                                    all = in_sorted(lst, nl, point_leaf[(int64_t)j * K + kk]);
-                                acc = all;
-                                exc = !all;
-                            }
-                        }
-                    }
-                    const uint32_t ba = __ballot_sync(0xffffffffu, acc);
-                    if (acc) {
-                        const int at = cnt + __popc(ba & ((1u << lane) - 1u));
-                        if (at < kNearCap) row[at] = j;
-                    }
-                    cnt += __popc(ba);
-                    ex += __popc(__ballot_sync(0xffffffffu, exc));
+    for (int ub = 0; ub < total; ub += 32) {
+        const int u = ub + lane;
+        bool acc = false, exc = false;
+        int j = -1;
+        if (u < total) {
+            // the last cell whose first position is <= u
+            int lo = 0, hi = 26;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (scell[warp][mid] <= u) lo = mid; else hi = mid - 1;
+            }
+            const int64_t q = sbase[warp][lo] + u;
+            const float4 pc = cpan[q];
+            j = order[q];
+            const float dx = fx - pc.x, dy = fy - pc.y, dz = fz - pc.z;
+            if (dx * dx + dy * dy + dz * dz < pc.w && j != me) {
+                // is_near with the panel's centroid and L from its cell-ordered copy
+                const dvec4 cg = cgeo[q];
+                const double ddx = __dsub_rn(x, cg.x), ddy = __dsub_rn(y, cg.y), ddz = __dsub_rn(z, cg.z);
+                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+                const double tl = __dmul_rn(tt, cg.w);
+                if (d2 < __dmul_rn(tl, tl)) {
+                    bool all = true;
+                    for (int kk = 0; kk < K && all; ++kk) all = member(point_leaf[(int64_t)j * K + kk]);
+                    acc = all;
+                    exc = !all;
                 }
             }
+        }
+        const uint32_t ba = __ballot_sync(0xffffffffu, acc);
+        if (acc) {
+            const int at = cnt + __popc(ba & ((1u << lane) - 1u));
+            if (at < kNearCap) row[at] = j;
+        }
+        cnt += __popc(ba);
+        ex += __popc(__ballot_sync(0xffffffffu, exc));
+    }
     if (lane == 0) {
         ncount[i] = cnt;
         excl[i] = ex;
@@ -782,7 +840,7 @@ __global__ void __launch_bounds__(128) near_grid_kernel(
         int se = 0;
         if (me >= 0)
             for (int kk = 0; kk < K; ++kk)
-                if (!in_sorted(lst, nl, point_leaf[(int64_t)me * K + kk])) se = 1;
+                if (!member(point_leaf[(int64_t)me * K + kk])) se = 1;
         self_excl[i] = se;
     }
 }
@@ -1171,6 +1229,7 @@ void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &
     TmpBuf<int32_t> cellof(std::max<int64_t>(1, src.n), s), ccnt(ncell, s), ccur(ncell, s),
         corder(std::max<int64_t>(1, src.n), s);
     TmpBuf<float4> cpan(std::max<int64_t>(1, src.n), s);
+    TmpBuf<dvec4> cgeo(std::max<int64_t>(1, src.n), s);
     TmpBuf<int64_t> coff(ncell + 1, s);
     PB_CUDA_TRY(cudaMemsetAsync(ccnt.p, 0, ncell * sizeof(int32_t), s));
     PB_CUDA_TRY(cudaMemsetAsync(ccur.p, 0, ncell * sizeof(int32_t), s));
@@ -1180,8 +1239,8 @@ void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &
     }
     exclusive_scan_i32_to_i64(ccnt.p, coff.p, ncell, s);
     if (src.n) {
-        cell_fill_kernel<<<div_up(src.n, 256), 256, 0, s>>>(src.n, cellof.p, coff.p, ccur.p, pan32.p, corder.p,
-                                                            cpan.p);
+        cell_fill_kernel<<<div_up(src.n, 256), 256, 0, s>>>(src.n, cellof.p, coff.p, ccur.p, pan32.p, src.cen.p,
+                                                            src.L.p, corder.p, cpan.p, cgeo.p);
         PB_LAUNCH_CHECK();
     }
     Pr.near_ptr.alloc(m + 1);
@@ -1191,9 +1250,9 @@ void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &
         TmpBuf<int32_t> rows((size_t)m * kNearCap, s), ovf(1, s);
         PB_CUDA_TRY(cudaMemsetAsync(ovf.p, 0, 4, s));
         near_grid_kernel<<<div_up(m, 4), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
-                                                       pleaf.p, T.point_leaf.p, src.cen.p, src.L.p, T.origin[0],
-                                                       T.origin[1], T.origin[2], prm.thres, g, coff.p, corder.p,
-                                                       cpan.p, nc.p, ex.p, se.p, rows.p, ovf.p);
+                                                       pleaf.p, T.point_leaf.p, T.origin[0], T.origin[1],
+                                                       T.origin[2], prm.thres, g, coff.p, corder.p, cpan.p, cgeo.p,
+                                                       nc.p, ex.p, se.p, rows.p, ovf.p);
         PB_LAUNCH_CHECK();
         int hov = 0;
         PB_CUDA_TRY(cudaMemcpyAsync(&hov, ovf.p, 4, cudaMemcpyDeviceToHost, s));
