@@ -492,6 +492,20 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_phases(reps):
+    """One setup and solve of the workload, then `reps` operator applications timed phase by phase."""
+    from paper_1309_4018_b300.build import build
+    build()
+    from paper_1309_4018_b300 import pbbem
+    d = _problem()
+    ctx = pbbem.Context(0)
+    pb = pbbem.Problem.from_dict(ctx, d)
+    pb.setup(precision="mixed", **PARAMS)
+    r = pb.solve()
+    x = np.random.default_rng(0).normal(size=pb.n_unknowns)
+    print(json.dumps({"setup_ms": r.setup_ms, "solve_ms": r.solve_ms, "phases_ms": pb.profile(x, reps=reps)}))
+
+
 def _extras(pbbem, ctx, pb, r, d, fleet_members, triplet, variants):
     """Adjoint gradient of the bench problem, a batched fleet solve, a binding energy, a
     Richardson study, the model variants, an accuracy/time sweep and device surface generation."""
@@ -738,9 +752,14 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip the gradient, batched-fleet and binding-energy measurements")
+    ap.add_argument("--phases", type=int, default=0, metavar="R",
+                    help="only set up and solve the workload once, then time R operator applications phase by "
+                         "phase (pb_profile_operator) and print them: a short run for profilers")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.phases:
+        run_phases(args.phases)
     else:
         run_gpu(args)
 
