@@ -405,6 +405,17 @@ def run_gpu(args):
                 "other": {k: {"ms": v[0], "Tinstr_s": v[1] / (v[0] / 1e3) / 1e12,
                               "frac": v[1] / (v[0] / 1e3) / 1e12 / alu_peak} for k, v in cand.items()}}
 
+    # the M2P contraction on the tensor pipe (pb_params.m2p_variant = 1): phase time and energy
+    ptc = make_problem()
+    ptc.setup(precision="mixed", m2p_variant=1, **PARAMS)
+    rtc = ptc.solve()
+    prof_tc = ptc.profile(x, reps=20)
+    ptc.close()
+    m2p_tc = {"m2p_ms": prof_tc["m2p"], "m2p_ms_fp32_pipe": prof["m2p"], "matvec_ms": prof_tc["total"],
+              "dG_kJ_mol": rtc.dG_solv, "iterations": rtc.iterations,
+              "note": "radial-form contraction as mma.sync m16n8k8 TF32 with split operands (3 products), "
+                      "FP32 accumulation; monomials, radial functions and final sums on the FP32 pipe"}
+
     # end to end through the public API with host buffers (H2D inside the timed region)
     e2e_t = []
     # untimed new problems first, as many as the device warm-up steps (the first fills the allocator's cache)
@@ -446,6 +457,7 @@ def run_gpu(args):
     golden = _oracle_golden(d)
     dG_or = golden["dG"] if golden else None
     rel_or = (lambda e: abs(e - dG_or) / abs(dG_or)) if golden else (lambda e: None)
+    m2p_tc["dG_rel_err_vs_oracle"] = rel_or(rtc.dG_solv)
 
     extras = {}
     if args.extras:
@@ -480,7 +492,7 @@ def run_gpu(args):
                      "extra_tol_1e-8": {"solve_time_s": (r64t.solve_ms + r64t.setup_ms) / 1e3,
                                         "iterations": r64t.iterations, "dG_kJ_mol": r64t.dG_solv,
                                         "dG_rel_err_vs_oracle": rel_or(r64t.dG_solv)}},
-            "roofline": roofline, "cpu_baseline": cpu,
+            "roofline": roofline, "cpu_baseline": cpu, "m2p_tensor_pipe": m2p_tc,
             "e2e": {"value": e2e_val, "unit": "Ginteractions/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "seconds_per_step": float(np.mean(e2e_t))},
             "gpu_launches": int(launches), "clocks": clocks,
@@ -492,7 +504,7 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_phases(reps):
+def run_phases(reps, m2p_variant=0):
     """One setup and solve of the workload, then `reps` operator applications timed phase by phase."""
     from paper_1309_4018_b300.build import build
     build()
@@ -500,7 +512,7 @@ def run_phases(reps):
     d = _problem()
     ctx = pbbem.Context(0)
     pb = pbbem.Problem.from_dict(ctx, d)
-    pb.setup(precision="mixed", **PARAMS)
+    pb.setup(precision="mixed", m2p_variant=m2p_variant, **PARAMS)
     r = pb.solve()
     x = np.random.default_rng(0).normal(size=pb.n_unknowns)
     print(json.dumps({"setup_ms": r.setup_ms, "solve_ms": r.solve_ms, "phases_ms": pb.profile(x, reps=reps)}))
@@ -755,11 +767,12 @@ def main():
     ap.add_argument("--phases", type=int, default=0, metavar="R",
                     help="only set up and solve the workload once, then time R operator applications phase by "
                          "phase (pb_profile_operator) and print them: a short run for profilers")
+    ap.add_argument("--m2p-variant", type=int, default=0, help="with --phases: pb_params.m2p_variant")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.phases:
-        run_phases(args.phases)
+        run_phases(args.phases, args.m2p_variant)
     else:
         run_gpu(args)
 

@@ -76,6 +76,10 @@ typedef struct {
     int p2p_tile;      /* targets per direct-sum (P2P) work item, 1..32: a warp sums one leaf's
                           sources, staged 32 at a time, for this many targets that list the
                           leaf (not in the paper; the results do not depend on it) [32] */
+    int m2p_variant;   /* 1: the PB_MIXED far field of a Laplace/Yukawa pair (P <= 7) forms its
+                          radial-form contraction on the tensor pipe (TF32 instructions, every
+                          operand split in two TF32 parts, FP32 accumulation; rounding differs
+                          from 0, accuracy the same); 0: on the FP32 pipe (not in the paper) [0] */
 } pb_params;
 
 typedef struct {

@@ -76,6 +76,7 @@ Params resolve(const pb_params *p) {
         r.precond = p->no_precond == 0;
         r.ncrit_adjoint = p->ncrit_adjoint;
         if (p->p2p_tile) r.p2p_tile = p->p2p_tile;
+        r.m2p_variant = p->m2p_variant;
     }
     if (!valid_rule(r.K)) fail(PB_EINVAL, "K must be 1, 3, 7 or 19");
     if (!valid_rule(r.K_fine)) fail(PB_EINVAL, "K_fine must be 1, 3, 7 or 19");
@@ -84,6 +85,7 @@ Params resolve(const pb_params *p) {
     if (r.ncrit < 1) fail(PB_EINVAL, "ncrit must be >= 1");
     if (r.ncrit_adjoint < 0) fail(PB_EINVAL, "ncrit_adjoint must be >= 0");
     if (r.p2p_tile < 1 || r.p2p_tile > 32) fail(PB_EINVAL, "p2p_tile must be in 1..32");
+    if (r.m2p_variant != 0 && r.m2p_variant != 1) fail(PB_EINVAL, "m2p_variant must be 0 or 1");
     if (r.restart < 1 || r.restart > 200) fail(PB_EINVAL, "restart must be in 1..200");
     if (r.max_iter < 1) fail(PB_EINVAL, "max_iter must be >= 1");
     if (!(r.tol > 0.0)) fail(PB_EINVAL, "gmres_tol must be > 0");
@@ -412,7 +414,7 @@ void apply_operator(pb_problem *pb, const double *xd, double *yd, PhaseEvents *p
     if (!fork)
         for (auto &P : pb->pairs) launch_p2p(P, pb->G[P.tgt], pb->T[P.tree], P.tgt == P.tree, mixed, s);
     mark(2);
-    for (auto &P : pb->pairs) launch_m2p(P, pb->G[P.tgt], pb->T[P.tree], prm.P, mixed, s);
+    for (auto &P : pb->pairs) launch_m2p(P, pb->G[P.tgt], pb->T[P.tree], prm.P, mixed, s, prm.m2p_variant);
     if (fork) PB_CUDA_TRY(cudaStreamWaitEvent(s, pb->evj, 0));
     mark(3);
     for (auto &P : pb->pairs) {
@@ -471,7 +473,7 @@ void reaction(pb_problem *pb, const double *xd) {
         const Tree &Tr = pb->T[P.tree];
         const double *phi = xd + 2 * pb->off[P.tree];
         launch_p2p(P, G, Tr, false, mixed, s);
-        launch_m2p(P, G, Tr, prm.P, mixed, s);
+        launch_m2p(P, G, Tr, prm.P, mixed, s, prm.m2p_variant);
         launch_gather(P, G, mixed, false, phi, phi + pb->S[P.tree].n, pb->T[P.tree].phf.p, s);
     }
     CombineRow row{};

@@ -18,6 +18,7 @@ struct Params {
     bool precond = true;
     int ncrit_adjoint = 0;   // 0: ncrit
     int p2p_tile = 32;       // targets per P2P work item
+    int m2p_variant = 0;     // 1: FP32 radial M2P with its contraction on the tensor pipe
 };
 
 struct Region {

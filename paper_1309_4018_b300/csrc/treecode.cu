@@ -682,14 +682,6 @@ __device__ __forceinline__ void m2p_ly_eval(const float4 *R, const float (&ux)[N
 // the other.  Lanes past the last item's count evaluate their first target
 // again and store it once.  Seven blocks per SM (72 registers, no spills):
 // 90 -> 86 us at P = 6 against the unbounded 80 registers and six blocks.
-struct M2PArgs32 {
-    const int4 *items;                     // (box, grouped start, count <= 32, 0)
-    const int32_t *inv, *ent;              // grouped pair -> sorted target, list entry
-    const float4 *x32, *cen32;             // targets, box centres (FP32, tree-origin relative)
-    const float *rmom;                     // radial moments, radial_stride(P) floats per node
-    float kappa;                           // Yukawa kernel (slot 1)
-    float4 *part;                          // records (VL, KL, VY, KY) per list entry
-};
 
 // The NI items i0.. on the calling warp; sR: the warp's staging of one box's radial moments.
 template <int P, int NI>
@@ -1355,6 +1347,7 @@ void upload_term_tables() {
                                      (int)kClimbMaxShared));
     PB_CUDA_TRY(cudaFuncSetAttribute(m2m_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kM2MMaxShared));
     PB_CUDA_TRY(cudaFuncSetAttribute(m2m_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kM2MMaxShared));
+    m2p_tc_prepare();
     int terms[3 * kMaxTerms1];
     int i = 0;
     for (int n = 0; n <= kMaxP + 1; ++n)
@@ -1527,8 +1520,12 @@ M2PArgs32 m2p_args32(const Pair &Pr, const Tree &Tr) {
     return a;
 }
 
-void launch_m2p(const Pair &Pr, const Targets &G, const Tree &Tr, int P, bool mixed, cudaStream_t s) {
+void launch_m2p(const Pair &Pr, const Targets &G, const Tree &Tr, int P, bool mixed, cudaStream_t s, int variant) {
     if (Pr.n_m2p_items == 0) return;
+    if (variant == 1 && m2p_tc_eligible(Pr, P, mixed)) {
+        launch_m2p_tc(m2p_args32(Pr, Tr), Pr.n_m2p_items, P, s);
+        return;
+    }
     if (mixed && Pr.kappas.size() == 2 && Pr.kappas[0] == 0.0 && Pr.kappas[1] != 0.0 && P <= kRadialMaxP) {
         const int64_t ni = Pr.n_m2p_items;
         constexpr int NI = 2;   // items per warp (three or four: 99 us against 90 at P = 6, fewer warps per SM)

@@ -37,7 +37,9 @@ void m2m_pass(const Tree &Tr, int P, bool mixed, void *mom, int stride, int base
 // Direct-sum partials of every (target, leaf) list entry.
 void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self, bool mixed, cudaStream_t s);
 // Far-field partials of every (target, box) list entry and kernel.
-void launch_m2p(const Pair &Pr, const Targets &G, const Tree &Tr, int P, bool mixed, cudaStream_t s);
+// variant 1: the FP32 radial form's contraction on the tensor pipe where eligible.
+void launch_m2p(const Pair &Pr, const Targets &G, const Tree &Tr, int P, bool mixed, cudaStream_t s,
+                int variant = 0);
 // Pr.VK = each target's partials, plus its near-singular corrections and (use_self)
 // its own panel's semi-analytical term, with phi, dphi of the source surface (overwrites).
 // phf: FP32 (phi, dphi) of the source surface (the tree's phf after
@@ -49,6 +51,22 @@ void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, 
 void targets_to_float(Pair &Pr, const Targets &G, const Tree &Tr, cudaStream_t s);
 void launch_combine(int64_t n, const int32_t *rank, const double *phi_s, double half, const CombineRow &row, double *y,
                     cudaStream_t s);
+
+// Arguments of the FP32 radial-form M2P of one pair (Laplace slot 0, Yukawa slot 1).
+struct M2PArgs32 {
+    const int4 *items;                     // (box, grouped start, count <= 32, 0)
+    const int32_t *inv, *ent;              // grouped pair -> sorted target, list entry
+    const float4 *x32, *cen32;             // targets, box centres (FP32, tree-origin relative)
+    const float *rmom;                     // radial moments, radial_stride(P) floats per node
+    float kappa;                           // Yukawa kernel (slot 1)
+    float4 *part;                          // records (VL, KL, VY, KY) per list entry
+};
+M2PArgs32 m2p_args32(const Pair &Pr, const Tree &Tr);
+// The radial-form M2P with its contraction on the tensor pipe (m2p_tc.cu):
+// kernel attributes (once per context), eligibility of a pair, launch.
+void m2p_tc_prepare();
+bool m2p_tc_eligible(const Pair &Pr, int P, bool mixed);
+void launch_m2p_tc(const M2PArgs32 &a, int64_t nitems, int P, cudaStream_t s);
 
 // ---------------------------------------------------------------- batched operator
 // The direct sums, far-field sums and gathers of several problems' operator

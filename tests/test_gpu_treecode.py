@@ -99,3 +99,21 @@ def test_mixed_protein_operator_matches_fp64_treecode():
     y64 = problem(d, precision="fp64", **kw).apply(x)
     y32 = problem(d, precision="mixed", **kw).apply(x)
     assert rel_l2(y32, y64) <= 2e-5
+
+
+def test_m2p_tensor_pipe_variant():
+    # the radial contraction on the tensor pipe (split TF32 operands, FP32
+    # accumulation) against the FP32-pipe path and the FP64 treecode on the
+    # 40k-panel protein: rounding differences only
+    from synth.configs import protein_problem
+    d = protein_problem()
+    kw = dict(theta=0.5, P=6, ncrit=300)
+    x = np.random.default_rng(0).normal(size=2 * d["surfaces"][0]["tris"].shape[0])
+    y64 = problem(d, precision="fp64", **kw).apply(x)
+    y32 = problem(d, precision="mixed", **kw).apply(x)
+    ytc = problem(d, precision="mixed", m2p_variant=1, **kw).apply(x)
+    assert rel_l2(ytc, y64) <= 2e-5
+    assert rel_l2(ytc, y32) <= 1e-5
+    e0 = problem(d, precision="mixed", gmres_tol=1e-6, **kw).solve().dG_solv
+    e1 = problem(d, precision="mixed", gmres_tol=1e-6, m2p_variant=1, **kw).solve().dG_solv
+    assert abs(e1 - e0) <= 1e-6 * abs(e0)
