@@ -565,14 +565,16 @@ void build_cycle_graph(KrylovJob *jb) {
     const long long k0 = g_launches.load();
     PB_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     try {
-        if (jb->precond) {
+        if (jb->prep) {
+            jb->prep(cs);
+        } else if (jb->precond) {
             gm.copy_basis(pb->z2.p, cs);
             jb->precond(pb->z2.p, pb->z1.p);
         } else {
             gm.copy_basis(pb->z1.p, cs);
         }
         jb->cycle_op();
-        gm.arnoldi_step_dev(h, pb->prm.tol, cs);
+        gm.arnoldi_step_dev(h, pb->prm.tol, cs, (bool)jb->prep);
     } catch (...) {
         cudaStreamEndCapture(cs, &body);
         throw;
@@ -813,6 +815,11 @@ void solve_many(const std::vector<pb_problem *> &probs, const std::vector<const 
         jb.x_zero = x0s[i] == nullptr;
         jb.graph = [pb](cudaStream_t gs) { launch_operator_graph(pb, gs); };
         jb.cycle_op = [pb] { apply_operator(pb, pb->z1.p, pb->gm.w.p); };
+        jb.prep = [pb](cudaStream_t ps) {
+            std::vector<std::pair<int64_t, int64_t>> sf;
+            for (size_t t = 0; t < pb->S.size(); ++t) sf.emplace_back(pb->off[t], pb->S[t].n);
+            pb->gm.prep_step(pb->prm.precond ? pb->minv.p : nullptr, sf, pb->z1.p, ps);
+        };
         jb.cycle_exec = &pb->cyc_exec;
         jb.cycle_kernels = &pb->cyc_kernels;
         jp[i] = &jb;

@@ -116,8 +116,48 @@ __global__ void set_bnorm_kernel(GmresState *st, double bn) {
 __global__ void set_cycle_kernel(GmresState *st, int maxit) {
     if (threadIdx.x != 0) return;
     st->j = 0;
+    st->pend = 0;
     st->maxit = maxit;
     st->steps = 0.0;
+}
+
+// Fused first kernel of a device-loop step for the panels [off, off + n) of
+// one surface: v = w / ||w|| (pend: the previous step's new vector, stored as
+// column j) or column j; z = M^-1 v with the panels' 2x2 blocks (minv), or
+// z = v without a preconditioner.  Elements off + i and off + n + i form a
+// panel's pair.
+__global__ void prep_step_kernel(int64_t n, int64_t off, const double *__restrict__ minv,
+                                 const GmresState *__restrict__ st, double *__restrict__ V, int64_t ld,
+                                 const double *__restrict__ w, const double *__restrict__ num_sq,
+                                 double *__restrict__ z) {
+    __shared__ double inv;
+    const int pend = st->pend;
+    if (threadIdx.x == 0 && pend) {
+        const double d = sqrt(*num_sq);
+        inv = d > 0.0 ? 1.0 / d : 0.0;
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double *col = V + (int64_t)st->j * ld;
+    const int64_t i1 = off + i, i2 = off + n + i;
+    double a, b;
+    if (pend) {
+        a = w[i1] * inv;
+        b = w[i2] * inv;
+        col[i1] = a;
+        col[i2] = b;
+    } else {
+        a = col[i1];
+        b = col[i2];
+    }
+    if (minv) {
+        z[i1] = minv[4 * i] * a + minv[4 * i + 1] * b;
+        z[i2] = minv[4 * i + 2] * a + minv[4 * i + 3] * b;
+    } else {
+        z[i1] = a;
+        z[i2] = b;
+    }
 }
 
 __global__ void copy_basis_kernel(const double *__restrict__ V, int64_t ld, const GmresState *st,
@@ -241,6 +281,10 @@ struct ArnoldiArgs {
     unsigned *count;        // zero between launches
     GmresState *st;
     int j;
+    // fused device loop: the last block of the norm kernel also ends or advances the loop
+    int control;
+    double tol;
+    cudaGraphConditionalHandle h;
 };
 
 __device__ __forceinline__ bool arrive_last(unsigned *count) {
@@ -436,6 +480,17 @@ __global__ void __launch_bounds__(kRedThreads) arnoldi_project_norm_kernel(Arnol
             st->g[j + 1] = -sn * gj;
             st->g[j] = c * gj;
             st->res_est = fabs(-sn * gj) / st->bnorm;
+            if (a.control) {
+                // every block has read the column index: the loop may advance it now
+                const int steps = j + 1;
+                st->steps = (double)steps;
+                const bool stop = !(st->res_est >= a.tol) || steps >= st->maxit || steps >= m;
+                if (!stop) {
+                    st->j = steps;
+                    st->pend = 1;
+                }
+                cudaGraphSetConditional(a.h, stop ? 0u : 1u);
+            }
         }
         __syncthreads();
         double *col = st->H + (int64_t)j * (m + 1);
@@ -492,7 +547,7 @@ void Gmres::start_cycle(const double *r, cudaStream_t s) {
 }
 
 void Gmres::arnoldi_step(int j, cudaStream_t s) {
-    ArnoldiArgs a;
+    ArnoldiArgs a{};
     a.V = V.p;
     a.ld = ld;
     a.n = n;
@@ -526,8 +581,18 @@ void Gmres::copy_basis(double *dst, cudaStream_t s) {
     PB_LAUNCH_CHECK();
 }
 
-void Gmres::arnoldi_step_dev(cudaGraphConditionalHandle h, double tol, cudaStream_t s) {
-    ArnoldiArgs a;
+void Gmres::prep_step(const double *minv, const std::vector<std::pair<int64_t, int64_t>> &surfaces, double *z,
+                      cudaStream_t s) {
+    for (const auto &sf : surfaces) {
+        if (sf.second == 0) continue;
+        prep_step_kernel<<<div_up(sf.second, 256), 256, 0, s>>>(sf.second, 2 * sf.first, minv ? minv + 4 * sf.first : nullptr,
+                                                                 st.p, V.p, ld, w.p, scal.p + 1, z);
+        PB_LAUNCH_CHECK();
+    }
+}
+
+void Gmres::arnoldi_step_dev(cudaGraphConditionalHandle h, double tol, cudaStream_t s, bool fused) {
+    ArnoldiArgs a{};
     a.V = V.p;
     a.ld = ld;
     a.n = n;
@@ -540,12 +605,16 @@ void Gmres::arnoldi_step_dev(cudaGraphConditionalHandle h, double tol, cudaStrea
     a.count = count.p;
     a.st = st.p;
     a.j = -1;
+    a.control = fused ? 1 : 0;
+    a.tol = tol;
+    a.h = h;
     arnoldi_dots_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(a);
     PB_LAUNCH_CHECK();
     arnoldi_project_dots_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(a);
     PB_LAUNCH_CHECK();
     arnoldi_project_norm_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(a);
     PB_LAUNCH_CHECK();
+    if (fused) return;   // v_{j+1} is formed by the next step's prep_step, the loop control ran above
     scale_copy_next_kernel<<<div_up(n, 256), 256, 0, s>>>(w.p, scal.p + 1, V.p, ld, st.p, n);
     PB_LAUNCH_CHECK();
     arnoldi_control_kernel<<<1, 1, 0, s>>>(st.p, h, tol);

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cmath>
+#include <utility>
+#include <vector>
 
 #include "common.cuh"
 
@@ -10,7 +12,7 @@ namespace pb {
 // Small Krylov state kept on the device (pointers into Gmres buffers).
 struct GmresState {
     int m;
-    int pad_;
+    int pend;           // device loop: v_j is still w / ||w|| of the previous step (written by prep_step)
     double *H, *cs, *sn, *g, *y;
     double bnorm, beta, hnext, res_est;
     double steps;       // Arnoldi steps of the current cycle (device loop; next to res_est for one copy)
@@ -43,7 +45,14 @@ struct Gmres {
     // estimate is >= tol, fewer than maxit steps and j + 1 < m.
     void set_cycle(int maxit, cudaStream_t s);
     void copy_basis(double *dst, cudaStream_t s);
-    void arnoldi_step_dev(cudaGraphConditionalHandle h, double tol, cudaStream_t s);
+    void arnoldi_step_dev(cudaGraphConditionalHandle h, double tol, cudaStream_t s, bool fused = false);
+    // Device loop, fused form: the step's first kernel forms v_j (from w and
+    // ||w|| of the previous step when pend, else the stored column), stores
+    // it and writes z = M^-1 v_j (minv: 2x2 blocks of the surfaces (offset,
+    // panels) given, or null for z = v_j); the loop control then runs in the
+    // last block of the norm kernel (arnoldi_step_dev with fused = true).
+    void prep_step(const double *minv, const std::vector<std::pair<int64_t, int64_t>> &surfaces, double *z,
+                   cudaStream_t s);
     // hs[2] = residual estimate, hs[3] = steps of the cycle (copy queued after the loop)
     void read_cycle_async(cudaStream_t s);
 };

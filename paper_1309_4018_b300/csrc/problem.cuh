@@ -131,6 +131,10 @@ struct KrylovJob {
     // whose WHILE node the device ends (no host round trip per step); cycle_op
     // enqueues the operator z1 -> gm.w on pb->stream for the capture.
     std::function<void()> cycle_op;
+    // prep: when set, the cycle graph's steps start with it (v_j formed, stored
+    // and preconditioned into z1 by one launch per surface) and end their
+    // Arnoldi step with the loop control in the norm kernel (Gmres::prep_step).
+    std::function<void(cudaStream_t)> prep;
     cudaGraphExec_t *cycle_exec = nullptr;
     long long *cycle_kernels = nullptr;
     KrylovStats st;
