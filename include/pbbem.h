@@ -123,6 +123,17 @@ int pb_add_region(pb_problem *pb, double eps, double kappa, int *region_id);
  * a zero-area triangle. */
 int pb_add_surface(pb_problem *pb, const double *verts, int64_t nv, const int32_t *tris,
                    int64_t nt, int inner, int outer, int *surface_id);
+/* pb_add_surface with verts and tris in device (or managed) memory of the
+ * context's device, as a torch CUDA tensor holds them: nv x 3 doubles and
+ * nt x 3 ints, row-major, contiguous; the caller keeps ownership (they are
+ * copied on the context stream, and the call returns once the copy and the
+ * checks are done).  Writes to them on another stream must be complete
+ * before the call.  The checks are those of pb_add_surface (finite
+ * coordinates and indices in range, here run on the device, then the mesh
+ * check); PB_EINVAL also for a pointer that is not device memory of the
+ * context's device. */
+int pb_add_surface_dev(pb_problem *pb, const double *verts, int64_t nv, const int32_t *tris,
+                       int64_t nt, int inner, int outer, int *surface_id);
 /* Molecular surface generated on the device from atoms.  The paper meshes the
  * solvent-excluded surface with MSMS (Sec. 2.2, Sec. 3); this builds instead
  * the level set rho = level of the Gaussian density
@@ -175,6 +186,13 @@ int pb_surface_info_get(pb_problem *pb, int surface, pb_surface_info *out);
 int pb_surface_export(pb_problem *pb, int surface, double *verts, int32_t *tris);
 /* Point charges (Eq. pde) inside region `region` (which must have kappa = 0). */
 int pb_set_charges(pb_problem *pb, const double *xyz, const double *q, int64_t nc, int region);
+/* pb_set_charges with xyz (nc x 3 doubles) and q (nc doubles) in device (or
+ * managed) memory of the context's device; copied on the context stream,
+ * caller keeps ownership, writes on another stream must be complete before
+ * the call.  PB_EINVAL for a pointer that is not device memory of the
+ * context's device, or a non-finite position (found on the device after the
+ * copy; the problem then holds no charges). */
+int pb_set_charges_dev(pb_problem *pb, const double *xyz, const double *q, int64_t nc, int region);
 
 /* Geometry, octrees, interaction lists, near-singular corrections and the
  * right-hand side (Sec. 2.3: built once, reused by every iteration). */
@@ -184,7 +202,8 @@ int64_t pb_num_unknowns(pb_problem *pb);  /* 2 N, or -1 before pb_setup */
 /* y = A x for the assembled operator (one treecode evaluation, Sec. 2.3
  * "Treecode-accelerated BEM").  x, y: 2 N doubles; on the host if
  * device_ptrs == 0, else device pointers of this context's device (the call
- * is ordered on the context stream and returns when y is complete). */
+ * is ordered on the context stream and returns when y is complete; PB_EINVAL
+ * for a pointer that is not device memory of that device). */
 int pb_apply_operator(pb_problem *pb, const double *x, double *y, int device_ptrs);
 /* b of Eq. matrix (2 N host doubles). */
 int pb_rhs(pb_problem *pb, double *b);

@@ -1434,7 +1434,7 @@ void prepare_adjoint(pb_problem *pb) {
     cudaStream_t s = pb->stream;
     const Params &prm = pb->prm;
     const int ns = (int)pb->S.size();
-    const int64_t nc = (int64_t)pb->cq.size();
+    const int64_t nc = pb->nc;
     auto A = std::make_shared<AdjointState>();
     upload_adjoint_tables();
     const int ncritT = prm.ncrit_adjoint > 0 ? prm.ncrit_adjoint : prm.ncrit;
@@ -1862,7 +1862,7 @@ void energy_gradient(pb_problem *pb, pb_grad *out) {
     cudaStream_t s = pb->stream;
     const Params &prm = pb->prm;
     const int ns = (int)pb->S.size();
-    const int64_t nc = (int64_t)pb->cq.size();
+    const int64_t nc = pb->nc;
     const int nreg = (int)pb->regions.size();
     const int Rc = pb->cregion;
     if (!pb->have_solution) fail(PB_EINVAL, "pb_gradient needs a pb_solve since the last pb_setup");

@@ -175,7 +175,7 @@ void setup_problem(pb_problem *pb) {
     pb->N = pb->off[ns];
     pb->G.resize(ns + 1);
     for (int t = 0; t < ns; ++t) build_targets(pb->G[t], pb->S[t].cen.p, pb->S[t].n, t, s);
-    const int64_t nc = (int64_t)pb->cq.size();
+    const int64_t nc = pb->nc;
     build_targets(pb->G[ns], pb->cxyz_d.p, nc, -1, s);
     // the charges must lie in their region: inside every surface that has it as
     // inner region, outside every surface that has it as outer region
@@ -455,7 +455,7 @@ void reaction(pb_problem *pb, const double *xd) {
     const Params &prm = pb->prm;
     const bool mixed = prm.precision == PB_MIXED;
     const int ns = (int)pb->S.size();
-    const int64_t nc = (int64_t)pb->cq.size();
+    const int64_t nc = pb->nc;
     if (nc == 0) {
         pb->energy.zero(s);
         return;
@@ -898,7 +898,7 @@ void on_pool_streams(pb_ctx *c, const std::vector<pb_problem *> &probs, F &&f) {
 
 double coulomb(pb_problem *pb) {
     cudaStream_t s = pb->stream;
-    const int64_t nc = (int64_t)pb->cq.size();
+    const int64_t nc = pb->nc;
     if (nc == 0) return 0.0;
     TmpBuf<double> rowv(nc, s);
     coulomb_rows(pb->cxyz_d.p, pb->cq_d.p, nc, rowv.p, s);
@@ -1021,15 +1021,59 @@ int pb_add_region(pb_problem *pb, double eps, double kappa, int *region_id) {
     });
 }
 
+namespace {
+
+void check_surface_args(pb_problem *pb, const void *verts, int64_t nv, const void *tris, int64_t nt, int inner,
+                        int outer) {
+    if (!verts || !tris || nv < 3 || nt < 1) fail(PB_EINVAL, "empty surface");
+    if (inner < 0 || outer < 0 || inner >= (int)pb->regions.size() || outer >= (int)pb->regions.size() ||
+        inner == outer)
+        fail(PB_EINVAL, "surface references an unknown region");
+    if (nt > ((int64_t)1 << 29) / 19) fail(PB_EINVAL, "too many triangles");
+}
+
+// The mesh check, then the surface joins the problem (si holds the device copy).
+void add_checked_surface(pb_problem *pb, SurfIn &&si, int inner, int outer, int *surface_id) {
+    pb->mesh_chk_h.alloc(1);
+    check_mesh_async(si.v.p, si.nv, si.t.p, si.nt, pb->mesh_chk_h.p, pb->stream);
+    PB_CUDA_TRY(cudaStreamSynchronize(pb->stream));
+    mesh_check_result(*pb->mesh_chk_h.p);
+    si.inner = inner;
+    si.outer = outer;
+    pb->sin.push_back(std::move(si));
+    pb->is_setup = false;
+    if (surface_id) *surface_id = (int)pb->sin.size() - 1;
+}
+
+// p must be device (or managed) memory of the context's device.
+void require_device_ptr(pb_ctx *ctx, const void *p, const char *what) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        fail(PB_EINVAL, std::string(what) + " is not a CUDA pointer");
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        fail(PB_EINVAL, std::string(what) + " is not device memory");
+    if (at.device != ctx->device)
+        fail(PB_EINVAL, std::string(what) + " is memory of device " + std::to_string(at.device) +
+                            ", not of the context's device " + std::to_string(ctx->device));
+}
+
+// Fails with PB_EINVAL naming the first bad element found by check_values_async.
+void value_check_result(const ValueCheck &r, const char *value_what, const char *index_what) {
+    if (r.bad_value != ~0ull)
+        fail(PB_EINVAL, std::string("non-finite ") + value_what + " (element " + std::to_string(r.bad_value) + ")");
+    if (r.bad_index != ~0ull)
+        fail(PB_EINVAL, std::string(index_what) + " out of range (element " + std::to_string(r.bad_index) + ")");
+}
+
+}  // namespace
+
 int pb_add_surface(pb_problem *pb, const double *verts, int64_t nv, const int32_t *tris, int64_t nt, int inner,
                    int outer, int *surface_id) {
     if (!pb) return PB_EINVAL;
     return guard(pb->ctx, [&] {
-        if (!verts || !tris || nv < 3 || nt < 1) fail(PB_EINVAL, "empty surface");
-        if (inner < 0 || outer < 0 || inner >= (int)pb->regions.size() || outer >= (int)pb->regions.size() ||
-            inner == outer)
-            fail(PB_EINVAL, "surface references an unknown region");
-        if (nt > ((int64_t)1 << 29) / 19) fail(PB_EINVAL, "too many triangles");
+        check_surface_args(pb, verts, nv, tris, nt, inner, outer);
         for (int64_t i = 0; i < 3 * nv; ++i)
             if (!std::isfinite(verts[i])) fail(PB_EINVAL, "non-finite vertex coordinate");
         for (int64_t i = 0; i < 3 * nt; ++i)
@@ -1040,15 +1084,31 @@ int pb_add_surface(pb_problem *pb, const double *verts, int64_t nv, const int32_
         si.nt = nt;
         si.v.upload(verts, 3 * nv, pb->stream);
         si.t.upload(tris, 3 * nt, pb->stream);
-        pb->mesh_chk_h.alloc(1);
-        check_mesh_async(si.v.p, nv, si.t.p, nt, pb->mesh_chk_h.p, pb->stream);
-        PB_CUDA_TRY(cudaStreamSynchronize(pb->stream));
-        mesh_check_result(*pb->mesh_chk_h.p);
-        si.inner = inner;
-        si.outer = outer;
-        pb->sin.push_back(std::move(si));
-        pb->is_setup = false;
-        if (surface_id) *surface_id = (int)pb->sin.size() - 1;
+        add_checked_surface(pb, std::move(si), inner, outer, surface_id);
+    });
+}
+
+int pb_add_surface_dev(pb_problem *pb, const double *verts, int64_t nv, const int32_t *tris, int64_t nt, int inner,
+                       int outer, int *surface_id) {
+    if (!pb) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        check_surface_args(pb, verts, nv, tris, nt, inner, outer);
+        set_device(pb->ctx);
+        require_device_ptr(pb->ctx, verts, "verts");
+        require_device_ptr(pb->ctx, tris, "tris");
+        cudaStream_t s = pb->stream;
+        SurfIn si;
+        si.nv = nv;
+        si.nt = nt;
+        si.v.alloc(3 * nv);
+        si.t.alloc(3 * nt);
+        PB_CUDA_TRY(cudaMemcpyAsync(si.v.p, verts, 3 * nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        PB_CUDA_TRY(cudaMemcpyAsync(si.t.p, tris, 3 * nt * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        pb->val_chk_h.alloc(1);
+        check_values_async(si.v.p, 3 * nv, si.t.p, 3 * nt, nv, pb->val_chk_h.p, s);
+        PB_CUDA_TRY(cudaStreamSynchronize(s));
+        value_check_result(*pb->val_chk_h.p, "vertex coordinate", "triangle vertex index");
+        add_checked_surface(pb, std::move(si), inner, outer, surface_id);
     });
 }
 
@@ -1123,13 +1183,41 @@ int pb_set_charges(pb_problem *pb, const double *xyz, const double *q, int64_t n
         for (int64_t i = 0; i < 3 * nc; ++i)
             if (!std::isfinite(xyz[i])) fail(PB_EINVAL, "non-finite charge position");
         set_device(pb->ctx);
-        pb->cxyz.assign(xyz, xyz + 3 * nc);
-        pb->cq.assign(q, q + nc);
         pb->cq_d.upload(q, nc, pb->stream);
         pb->cxyz_d.upload(xyz, 3 * nc, pb->stream);
         PB_CUDA_TRY(cudaStreamSynchronize(pb->stream));
+        pb->nc = nc;
         pb->cregion = region;
         pb->is_setup = false;
+    });
+}
+
+int pb_set_charges_dev(pb_problem *pb, const double *xyz, const double *q, int64_t nc, int region) {
+    if (!pb) return PB_EINVAL;
+    return guard(pb->ctx, [&] {
+        if (nc < 0 || (nc > 0 && (!xyz || !q))) fail(PB_EINVAL, "bad charge arrays");
+        if (region < 0 || region >= (int)pb->regions.size()) fail(PB_EINVAL, "unknown charge region");
+        if (pb->regions[region].kappa != 0.0) fail(PB_EINVAL, "charges must sit in a kappa = 0 region");
+        set_device(pb->ctx);
+        cudaStream_t s = pb->stream;
+        if (nc > 0) {
+            require_device_ptr(pb->ctx, xyz, "xyz");
+            require_device_ptr(pb->ctx, q, "q");
+        }
+        pb->cq_d.alloc(nc);
+        pb->cxyz_d.alloc(3 * nc);
+        if (nc > 0) {
+            PB_CUDA_TRY(cudaMemcpyAsync(pb->cq_d.p, q, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            PB_CUDA_TRY(cudaMemcpyAsync(pb->cxyz_d.p, xyz, 3 * nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
+        pb->val_chk_h.alloc(1);
+        check_values_async(pb->cxyz_d.p, 3 * nc, nullptr, 0, 0, pb->val_chk_h.p, s);
+        PB_CUDA_TRY(cudaStreamSynchronize(s));
+        pb->nc = 0;
+        pb->is_setup = false;
+        value_check_result(*pb->val_chk_h.p, "charge position", "index");
+        pb->nc = nc;
+        pb->cregion = region;
     });
 }
 
@@ -1153,6 +1241,8 @@ int pb_apply_operator(pb_problem *pb, const double *x, double *y, int device_ptr
         cudaStream_t s = pb->stream;
         const int64_t n2 = 2 * pb->N;
         if (device_ptrs) {
+            require_device_ptr(pb->ctx, x, "x");
+            require_device_ptr(pb->ctx, y, "y");
             apply_operator(pb, x, y);
         } else {
             pb->xin.upload(x, n2, s);
@@ -1198,6 +1288,8 @@ int pb_apply_transpose(pb_problem *pb, const double *x, double *y, int device_pt
         cudaStream_t s = pb->stream;
         const int64_t n2 = 2 * pb->N;
         if (device_ptrs) {
+            require_device_ptr(pb->ctx, x, "x");
+            require_device_ptr(pb->ctx, y, "y");
             apply_transpose(pb, x, y);
         } else {
             pb->xin.upload(x, n2, s);
@@ -1227,7 +1319,7 @@ int pb_reaction_potential(pb_problem *pb, const double *xh, double *phi) {
         cudaStream_t s = pb->stream;
         pb->xin.upload(xh, 2 * pb->N, s);
         reaction(pb, pb->xin.p);
-        pb->phi_reac.download(phi, pb->cq.size(), s);
+        pb->phi_reac.download(phi, pb->nc, s);
         PB_CUDA_TRY(cudaStreamSynchronize(s));
     });
 }

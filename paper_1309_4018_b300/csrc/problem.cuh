@@ -69,7 +69,7 @@ struct pb_problem {
     long long adj_cyc_kernels = 0;
     std::vector<pb::Region> regions;
     std::vector<pb::SurfIn> sin;
-    std::vector<double> cxyz, cq;
+    int64_t nc = 0;                         // charges
     int cregion = -1;
     bool is_setup = false;
     pb::Params prm;
@@ -88,7 +88,8 @@ struct pb_problem {
     pb::DevBuf<double> cq_d, cxyz_d, phi_reac, energy;
     pb::DevBuf<int32_t> wind, wind_bad;      // charge-region check: winding numbers, mismatch record
     pb::PinnedBuf<int32_t> wind_bad_h;
-    pb::PinnedBuf<pb::MeshCheck> mesh_chk_h;  // outcome of the last pb_add_surface's mesh check
+    pb::PinnedBuf<pb::MeshCheck> mesh_chk_h;
+    pb::PinnedBuf<pb::ValueCheck> val_chk_h;  // outcome of the last pb_add_surface's mesh check
     pb::Gmres gm;
     double setup_ms = 0.0;
     bool have_solution = false;

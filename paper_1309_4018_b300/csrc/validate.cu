@@ -106,6 +106,29 @@ __global__ void __launch_bounds__(kVolBlocks) volume_final_kernel(const double *
 
 }  // namespace
 
+__global__ void value_check_kernel(const double *__restrict__ x, int64_t nx, const int32_t *__restrict__ idx,
+                                   int64_t ni, int64_t lim, unsigned long long *bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += stride)
+        if (!isfinite(x[i])) atomicMin(bad, (unsigned long long)i);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += stride)
+        if (idx[i] < 0 || idx[i] >= lim) atomicMin(bad + 1, (unsigned long long)i);
+}
+
+void check_values_async(const double *x, int64_t nx, const int32_t *idx, int64_t ni, int64_t lim, ValueCheck *out,
+                        cudaStream_t s) {
+    TmpBuf<unsigned long long> bad(2, s);
+    PB_CUDA_TRY(cudaMemsetAsync(bad.p, 0xff, 2 * sizeof(unsigned long long), s));
+    const int64_t n = nx > ni ? nx : ni;
+    if (n > 0) {
+        const int64_t want = div_up(n, 256);
+        const int blocks = (int)(want < 148 * 8 ? want : 148 * 8);
+        value_check_kernel<<<blocks, 256, 0, s>>>(x, nx, idx, ni, lim, bad.p);
+        PB_LAUNCH_CHECK();
+    }
+    PB_CUDA_TRY(cudaMemcpyAsync(out, bad.p, sizeof(ValueCheck), cudaMemcpyDeviceToHost, s));
+}
+
 void check_mesh_async(const double *verts, int64_t nv, const int32_t *tris, int64_t nt, MeshCheck *out,
                       cudaStream_t s) {
     const int64_t n3 = 3 * nt;

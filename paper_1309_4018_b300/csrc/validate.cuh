@@ -29,6 +29,16 @@ void check_mesh_async(const double *verts, int64_t nv, const int32_t *tris, int6
                       cudaStream_t s);
 void mesh_check_result(const MeshCheck &r);
 
+// Check of arrays given by device pointers: bad_value = the lowest i < nx
+// with a non-finite x[i], bad_index = the lowest i < ni with idx[i] outside
+// [0, lim); all ones where there is none.  Queued on s and copied to *out
+// (page-locked host memory, valid once s has been synchronised).
+struct ValueCheck {
+    unsigned long long bad_value, bad_index;
+};
+void check_values_async(const double *x, int64_t nx, const int32_t *idx, int64_t ni, int64_t lim, ValueCheck *out,
+                        cudaStream_t s);
+
 // Queues on s the winding number of the closed surface (device verts, tris)
 // about each of nc points xyz (device): the signed count of the surface's
 // crossings by a ray from the point, +1 where the surface's normal points

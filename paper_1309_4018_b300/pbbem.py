@@ -85,6 +85,8 @@ _SIGS = {
     "pb_add_region": ([_vp, _dbl, _dbl, ctypes.POINTER(_int)], _int),
     "pb_add_surface": ([_vp, _vp, _i64, _vp, _i64, _int, _int, ctypes.POINTER(_int)], _int),
     "pb_set_charges": ([_vp, _vp, _vp, _i64, _int], _int),
+    "pb_add_surface_dev": ([_vp, _vp, _i64, _vp, _i64, _int, _int, ctypes.POINTER(_int)], _int),
+    "pb_set_charges_dev": ([_vp, _vp, _vp, _i64, _int], _int),
     "pb_add_gaussian_surface": ([_vp, _vp, _vp, _i64, ctypes.POINTER(pb_surf_params), _int, _int,
                                  ctypes.POINTER(_int)], _int),
     "pb_surface_info_get": ([_vp, _int, ctypes.POINTER(pb_surface_info)], _int),
@@ -141,6 +143,26 @@ class PBError(RuntimeError):
 
 def _ptr(a):
     return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _is_cuda_tensor(a) -> bool:
+    return hasattr(a, "data_ptr") and getattr(a, "is_cuda", False)
+
+
+def _cuda_arg(a, dtype: str, cols):
+    """A CUDA torch tensor of the given dtype, contiguous, with `cols` columns
+    (or flat); the current torch stream is synchronised so the library's
+    stream sees its contents."""
+    import torch
+    if not _is_cuda_tensor(a):
+        raise TypeError("device arguments must all be CUDA tensors")
+    want = getattr(torch, dtype)
+    if a.dtype != want:
+        raise TypeError(f"expected a {dtype} tensor, got {a.dtype}")
+    a = a.contiguous()
+    a = a.reshape(-1, cols) if cols else a.reshape(-1)
+    torch.cuda.current_stream(a.device).synchronize()
+    return a
 
 
 class Context:
@@ -218,6 +240,28 @@ def solve_batch(ctx: "Context", problems, check=True):
     return [_result(res[i]) for i in range(n)]
 
 
+def solve(problem: dict, context: "Context | None" = None, return_solution: bool = False, check: bool = True,
+          **params):
+    """One problem in one call: build it from its description (Problem.from_dict),
+    set it up with the pb_params fields given as keywords, solve it, free it.
+
+    Returns the Result, or (Result, x) with the solution x (2 N host doubles)
+    when return_solution is set.  A context made here is closed again.
+    """
+    ctx = context if context is not None else Context(0)
+    try:
+        pb = Problem.from_dict(ctx, problem)
+        try:
+            pb.setup(**params)
+            r = pb.solve(check=check)
+            return (r, pb.solution()) if return_solution else r
+        finally:
+            pb.close()
+    finally:
+        if context is None:
+            ctx.close()
+
+
 def binding_energy(ctx: "Context", cx, rec, lig) -> float:
     """ddG = E_complex - E_receptor - E_ligand (solvation + Coulomb), kJ/mol (pb_binding_energy)."""
     out = _dbl()
@@ -260,6 +304,14 @@ class Problem:
         return rid.value
 
     def add_surface(self, verts, tris, inner, outer) -> int:
+        """verts [nv, 3], tris [nt, 3]: numpy arrays (host), or CUDA torch tensors
+        (float64, int32) handed over by device pointer (pb_add_surface_dev)."""
+        if _is_cuda_tensor(verts) or _is_cuda_tensor(tris):
+            v, t = _cuda_arg(verts, "float64", 3), _cuda_arg(tris, "int32", 3)
+            sid = _int()
+            self.ctx.check(_lib.pb_add_surface_dev(self._h, _vp(v.data_ptr()), v.shape[0], _vp(t.data_ptr()),
+                                                   t.shape[0], int(inner), int(outer), ctypes.byref(sid)))
+            return sid.value
         v = np.ascontiguousarray(verts, dtype=np.float64)
         t = np.ascontiguousarray(tris, dtype=np.int32)
         sid = _int()
@@ -297,6 +349,16 @@ class Problem:
         return v, t
 
     def set_charges(self, xyz, q, region):
+        """xyz [nc, 3], q [nc]: numpy arrays (host), or CUDA torch float64 tensors
+        handed over by device pointer (pb_set_charges_dev)."""
+        if _is_cuda_tensor(xyz) or _is_cuda_tensor(q):
+            x, qq = _cuda_arg(xyz, "float64", 3), _cuda_arg(q, "float64", None)
+            if x.shape[0] != qq.numel():
+                raise ValueError("xyz and q hold different numbers of charges")
+            self.ctx.check(_lib.pb_set_charges_dev(self._h, _vp(x.data_ptr()), _vp(qq.data_ptr()), qq.numel(),
+                                                   int(region)))
+            self.n_charges = qq.numel()
+            return
         x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
         qq = np.ascontiguousarray(q, dtype=np.float64).ravel()
         self.ctx.check(_lib.pb_set_charges(self._h, _ptr(x), _ptr(qq), qq.size, int(region)))
