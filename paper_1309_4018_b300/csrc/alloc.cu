@@ -126,4 +126,38 @@ void cached_host_free(void *p, size_t bytes) {
     cudaFreeHost(p);
 }
 
+namespace {
+
+// Page-locked staging area of a host thread (HostReads), grown on demand.
+struct Staging {
+    unsigned char *p = nullptr;
+    size_t cap = 0, top = 0;
+    ~Staging() {
+        if (p) cached_host_free(p, cap);
+    }
+};
+thread_local Staging t_staging;
+constexpr size_t kStagingBytes = 64 << 10;
+
+}  // namespace
+
+HostReads::HostReads(cudaStream_t s) : s_(s), begin_(t_staging.top), end_(t_staging.top) {}
+
+HostReads::~HostReads() { t_staging.top = begin_; }
+
+void *HostReads::take(size_t bytes) {
+    Staging &st = t_staging;
+    if (!st.p) {
+        size_t got = 0;
+        st.p = static_cast<unsigned char *>(cached_host_alloc(kStagingBytes, &got));
+        st.cap = got;
+    }
+    if (end_ != st.top) fail(PB_EINVAL, "internal: host staging area used out of order");
+    const size_t at = (end_ + 15) / 16 * 16;
+    if (at + bytes > st.cap) fail(PB_EINVAL, "internal: host staging area exhausted");
+    end_ = at + bytes;
+    st.top = end_;
+    return st.p + at;
+}
+
 }  // namespace pb

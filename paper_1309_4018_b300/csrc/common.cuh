@@ -138,6 +138,40 @@ struct PinnedBuf {
     }
 };
 
+// Small device-to-host reads gathered into one stream synchronisation.  The
+// values land in a page-locked staging area of the calling host thread (a
+// copy into pageable memory would wait for the stream inside cudaMemcpyAsync
+// and pass through a driver buffer): add() queues a copy and returns where it
+// will be, valid after wait() and until the HostReads is destroyed.  Objects
+// on one thread must be destroyed in reverse order of creation.
+class HostReads {
+  public:
+    explicit HostReads(cudaStream_t s);
+    ~HostReads();
+    HostReads(const HostReads &) = delete;
+    HostReads &operator=(const HostReads &) = delete;
+    template <typename T>
+    const T *add(const T *d, size_t n = 1) {
+        void *h = take(n * sizeof(T));
+        PB_CUDA_TRY(cudaMemcpyAsync(h, d, n * sizeof(T), cudaMemcpyDeviceToHost, s_));
+        return static_cast<const T *>(h);
+    }
+    void wait() { PB_CUDA_TRY(cudaStreamSynchronize(s_)); }
+
+  private:
+    void *take(size_t bytes);
+    cudaStream_t s_;
+    size_t begin_, end_;
+};
+// One value read from the device (a stream synchronisation).
+template <typename T>
+T read_device(const T *d, cudaStream_t s) {
+    HostReads r(s);
+    const T *h = r.add(d);
+    r.wait();
+    return *h;
+}
+
 // Stream-ordered temporary: allocated and freed on the stream that uses it,
 // so its release waits for the kernels queued before it.
 template <typename T>

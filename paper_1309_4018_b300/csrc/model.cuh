@@ -86,6 +86,7 @@ struct Pair {
     DevBuf<int64_t> m2p_ptr, p2p_ptr, near_ptr;
     DevBuf<int32_t> m2p_node, p2p_node, near_panel;
     int64_t n_m2p = 0, n_p2p = 0, n_near = 0, near_excl = 0, self_excl = 0, p2p_pairs = 0;
+    DevBuf<unsigned long long> stats;   // list-build counters read back with the list sizes
     // Entry-major work: for every leaf (P2P) / box (M2P) the (sorted target,
     // list entry) pairs that use it, grouped by leaf / box and packed 32 per
     // work item (one warp); every pair writes one partial sum, and a gather

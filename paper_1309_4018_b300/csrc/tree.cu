@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <optional>
 
 #include "model.cuh"
 #include "tree.cuh"
@@ -51,7 +52,11 @@ __global__ void bbox_blocks_kernel(const double *__restrict__ p, int64_t n, doub
         }
 }
 
-__global__ void bbox_final_kernel(const double *__restrict__ part, int nb, double *__restrict__ out) {
+// Root cube from the block boxes: cube = (corner x, y, z, side), with
+//   centre = (lo + hi) / 2, side = max extent * (1 + 2^-20) (1 if that is 0 or
+//   not finite), corner = centre - side / 2,
+// each operation rounded on its own (no fused multiply-add).
+__global__ void cube_final_kernel(const double *__restrict__ part, int nb, double *__restrict__ cube) {
     if (threadIdx.x != 0) return;
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int b = 0; b < nb; ++b)
@@ -59,7 +64,23 @@ __global__ void bbox_final_kernel(const double *__restrict__ part, int nb, doubl
             lo[a] = fmin(lo[a], part[6 * b + a]);
             hi[a] = fmax(hi[a], part[6 * b + 3 + a]);
         }
-    for (int a = 0; a < 3; ++a) { out[a] = lo[a]; out[3 + a] = hi[a]; }
+    double centre[3], ext[3];
+    for (int a = 0; a < 3; ++a) {
+        centre[a] = __dmul_rn(__dadd_rn(lo[a], hi[a]), 0.5);
+        ext[a] = __dsub_rn(hi[a], lo[a]);
+    }
+    const double m01 = ext[0] < ext[1] ? ext[1] : ext[0];
+    const double m = m01 < ext[2] ? ext[2] : m01;
+    double side = __dmul_rn(m, 1.0 + 0x1p-20);
+    if (side == 0.0 || !isfinite(side)) side = 1.0;
+    const double half = __dmul_rn(side, 0.5);
+    for (int a = 0; a < 3; ++a) cube[a] = __dsub_rn(centre[a], half);
+    cube[3] = side;
+}
+
+// The tree origin (the root cube's centre) as the host forms it: corner + 0.5 side.
+__device__ __forceinline__ double cube_origin(const double *cube, int a) {
+    return __dadd_rn(cube[a], __dmul_rn(0.5, cube[3]));
 }
 
 __device__ __forceinline__ uint64_t spread3(uint64_t v) {
@@ -68,11 +89,12 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v) {
     return r;
 }
 
-__global__ void morton_kernel(const double *__restrict__ p, int64_t n, double cx, double cy, double cz,
-                              double scale, uint64_t *__restrict__ keys, int32_t *__restrict__ idx) {
+__global__ void morton_kernel(const double *__restrict__ p, int64_t n, const double *__restrict__ cube,
+                              uint64_t *__restrict__ keys, int32_t *__restrict__ idx) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double c[3] = {cx, cy, cz};
+    const double c[3] = {cube[0], cube[1], cube[2]};
+    const double scale = __ddiv_rn(2097152.0, cube[3]);
     uint64_t q[3];
     for (int a = 0; a < 3; ++a) {
         double f = floor(__dmul_rn(__dsub_rn(p[3 * i + a], c[a]), scale));
@@ -83,84 +105,135 @@ __global__ void morton_kernel(const double *__restrict__ p, int64_t n, double cx
     idx[i] = (int32_t)i;
 }
 
-// For every node of one level: count the non-empty octants of the nodes that split.
-// Eight threads per node (consecutive lanes), thread o (1..8) finding the first
-// position of the node's keys whose octant digit is >= o by binary search; the
-// node's child count is the number of non-empty octants (a ballot over the
-// eight lanes).  Nodes of fewer than ncrit points, or at the deepest level,
-// do not split.
-__global__ void split_count_kernel(int lvl, int nb, int nodes_begin, const int64_t *__restrict__ start,
-                                   const int64_t *__restrict__ count, const uint64_t *__restrict__ keys, int ncrit,
-                                   int32_t *__restrict__ nchild, int32_t *__restrict__ child_bounds /*nodes*9*/) {
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const int t = (int)(gt >> 3), o = (int)(gt & 7) + 1;
-    const bool act = t < nb;
-    const int b = nodes_begin + t;
-    int64_t c = 0, lo = 0;
-    bool split = false;
-    if (act) {
-        c = count[b];
-        split = c >= ncrit && lvl < kMaxLevel;
-        if (split) {
-            const int64_t s = start[b];
-            const int sh = 3 * (kMaxLevel - 1 - lvl);
-            int64_t hi = c;
-            while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                const int d = (int)((keys[s + mid] >> sh) & 7ull);
-                if (d < o) lo = mid + 1; else hi = mid;
+// The whole octree below the root in one block, level by level (a host round
+// trip per level cost more than the levels themselves).  Per node of the level
+// (one thread each): a node with >= ncrit points above the deepest level splits
+// into its non-empty octants, the bound of octant o being the first of its
+// sorted keys whose octant digit is >= o (binary search).  The block then
+// numbers the children breadth first (an exclusive scan of the child counts in
+// node order, octants in order within a node) and writes them.  info: [0]
+// nodes, [1] levels, [2] 1 if maxn nodes were not enough, [3 + l] first node
+// of level l (levels + 1 entries).  Writes beyond maxn are skipped.
+constexpr int kLevelThreads = 1024;
+
+__device__ __forceinline__ int octant_bounds(const uint64_t *__restrict__ keys, int64_t s, int64_t c, int lvl,
+                                             int64_t bnd[9]) {
+    const int sh = 3 * (kMaxLevel - 1 - lvl);
+    bnd[0] = 0;
+    int nonempty = 0;
+    for (int o = 1; o <= 8; ++o) {
+        int64_t lo = bnd[o - 1], hi = c;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            const int d = (int)((keys[s + mid] >> sh) & 7ull);
+            if (d < o) lo = mid + 1; else hi = mid;
+        }
+        bnd[o] = lo;
+        nonempty += lo > bnd[o - 1];
+    }
+    return nonempty;
+}
+
+__global__ void __launch_bounds__(kLevelThreads) build_levels_kernel(
+    int64_t n, int ncrit, int maxn, const uint64_t *__restrict__ keys, int64_t *__restrict__ start,
+    int64_t *__restrict__ count, int32_t *__restrict__ level, int32_t *__restrict__ first_child,
+    int32_t *__restrict__ nchild, int32_t *__restrict__ parent, int64_t *__restrict__ ijk, int32_t *__restrict__ info) {
+    __shared__ int wsum[kLevelThreads / 32];
+    __shared__ int s_total;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        start[0] = 0; count[0] = n; level[0] = 0; first_child[0] = -1; nchild[0] = 0; parent[0] = -1;
+        ijk[0] = 0; ijk[1] = 0; ijk[2] = 0;
+        info[3] = 0;
+    }
+    __syncthreads();
+    int lb = 0, le = 1, lvl = 0, err = 0;
+    while (true) {
+        if (tid == 0) info[3 + lvl + 1] = le;
+        // child counts of the level's nodes
+        for (int b = lb + tid; b < le; b += kLevelThreads) {
+            const int64_t c = count[b];
+            int64_t bnd[9];
+            nchild[b] = (c >= ncrit && lvl < kMaxLevel) ? octant_bounds(keys, start[b], c, lvl, bnd) : 0;
+        }
+        __syncthreads();
+        // children, numbered by an exclusive scan of the counts over the level in chunks of the block
+        int carry = 0;
+        for (int c0 = lb; c0 < le; c0 += kLevelThreads) {
+            const int b = c0 + tid;
+            const int nc = b < le ? nchild[b] : 0;
+            int incl = nc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
+            if (lane == 31) wsum[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                int t = wsum[lane];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, t, o);
+                    if (lane >= o) t += y;
+                }
+                wsum[lane] = t;
+                if (lane == 31) s_total = t;
+            }
+            __syncthreads();
+            const int excl = carry + incl - nc + (warp > 0 ? wsum[warp - 1] : 0);
+            if (b < le) {
+                if (nc == 0) {
+                    first_child[b] = -1;
+                } else {
+                    int ch = le + excl;
+                    first_child[b] = ch;
+                    const int64_t s0 = start[b];
+                    int64_t bnd[9];
+                    octant_bounds(keys, s0, count[b], lvl, bnd);
+                    for (int o = 0; o < 8; ++o) {
+                        if (bnd[o + 1] <= bnd[o]) continue;
+                        if (ch < maxn) {
+                            start[ch] = s0 + bnd[o];
+                            count[ch] = bnd[o + 1] - bnd[o];
+                            level[ch] = lvl + 1;
+                            parent[ch] = b;
+                            nchild[ch] = 0;
+                            first_child[ch] = -1;
+                            ijk[3 * ch + 0] = 2 * ijk[3 * b + 0] + ((o >> 2) & 1);
+                            ijk[3 * ch + 1] = 2 * ijk[3 * b + 1] + ((o >> 1) & 1);
+                            ijk[3 * ch + 2] = 2 * ijk[3 * b + 2] + (o & 1);
+                        }
+                        ++ch;
+                    }
+                }
+            }
+            carry += s_total;
+            __syncthreads();
         }
+        if (carry == 0) break;
+        if ((int64_t)le + carry > maxn) {
+            err = 1;
+            break;
+        }
+        lb = le;
+        le += carry;
+        ++lvl;
     }
-    const int64_t up = __shfl_up_sync(0xffffffffu, lo, 1);
-    const int64_t prev = o == 1 ? 0 : up;
-    const unsigned nonempty = __ballot_sync(0xffffffffu, split && lo > prev);
-    if (!act) return;
-    if (split) {
-        child_bounds[9 * t + o] = (int32_t)lo;
-        if (o == 1) child_bounds[9 * t] = 0;
+    if (tid == 0) {
+        info[0] = le;
+        info[1] = lvl + 1;
+        info[2] = err;
     }
-    if (o == 1) nchild[b] = split ? __popc((nonempty >> (lane & ~7)) & 0xffu) : 0;
 }
 
-__global__ void split_write_kernel(int lvl, int nb, int nodes_begin, int nodes_end, const int64_t *__restrict__ cscan,
-                                   const int32_t *__restrict__ child_bounds, int64_t *__restrict__ start,
-                                   int64_t *__restrict__ count, int32_t *__restrict__ level,
-                                   int32_t *__restrict__ first_child, int32_t *__restrict__ nchild,
-                                   int32_t *__restrict__ parent, int64_t *__restrict__ ijk /*nodes*3*/) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nb) return;
-    const int b = nodes_begin + t;
-    const int nc = nchild[b];
-    if (nc == 0) { first_child[b] = -1; return; }
-    int c = nodes_end + (int)cscan[t];
-    first_child[b] = c;
-    const int64_t s = start[b];
-    for (int o = 0; o < 8; ++o) {
-        const int64_t cs = child_bounds[9 * t + o], ce = child_bounds[9 * t + o + 1];
-        if (ce > cs) {
-            start[c] = s + cs;
-            count[c] = ce - cs;
-            level[c] = lvl + 1;
-            parent[c] = b;
-            nchild[c] = 0;
-            first_child[c] = -1;
-            ijk[3 * c + 0] = 2 * ijk[3 * b + 0] + ((o >> 2) & 1);
-            ijk[3 * c + 1] = 2 * ijk[3 * b + 1] + ((o >> 1) & 1);
-            ijk[3 * c + 2] = 2 * ijk[3 * b + 2] + (o & 1);
-            ++c;
-        }
-    }
-}
-
-__global__ void node_geom_kernel(int nnodes, const int32_t *__restrict__ level, const int64_t *__restrict__ ijk,
-                                 double cx, double cy, double cz, double side, double *__restrict__ centre,
-                                 double *__restrict__ rb2) {
+__global__ void node_geom_kernel(const int32_t *__restrict__ info, const int32_t *__restrict__ level,
+                                 const int64_t *__restrict__ ijk, const double *__restrict__ cube,
+                                 double *__restrict__ centre, double *__restrict__ rb2) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nnodes) return;
-    const double sl = ldexp(side, -level[b]);
-    const double c[3] = {cx, cy, cz};
+    if (b >= info[0]) return;
+    const double sl = ldexp(cube[3], -level[b]);
+    const double c[3] = {cube[0], cube[1], cube[2]};
     for (int a = 0; a < 3; ++a)
         centre[3 * b + a] = __dadd_rn(c[a], __dmul_rn(__dadd_rn((double)ijk[3 * b + a], 0.5), sl));
     rb2[b] = __dmul_rn(__dmul_rn(sl, sl), 0.75);
@@ -168,35 +241,39 @@ __global__ void node_geom_kernel(int nnodes, const int32_t *__restrict__ level, 
 
 // Per node: (parent, the parent's first child, the parent's child count, 0);
 // (-1, 0, 0, 0) at the root.  One record per level of the upward climb.
-__global__ void link_kernel(int nnodes, const int32_t *__restrict__ parent, const int32_t *__restrict__ first_child,
-                            const int32_t *__restrict__ nchild, int4 *__restrict__ link) {
+__global__ void link_kernel(const int32_t *__restrict__ info, const int32_t *__restrict__ parent,
+                            const int32_t *__restrict__ first_child, const int32_t *__restrict__ nchild,
+                            int4 *__restrict__ link) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nnodes) return;
+    if (i >= info[0]) return;
     const int p = parent[i];
     link[i] = p >= 0 ? make_int4(p, first_child[p], nchild[p], 0) : make_int4(-1, 0, 0, 0);
 }
 
-__global__ void centre32_kernel(int nnodes, const double *__restrict__ centre, const double *__restrict__ rb2,
-                                double ox, double oy, double oz, float4 *__restrict__ cen32) {
+__global__ void centre32_kernel(const int32_t *__restrict__ info, const double *__restrict__ centre,
+                                const double *__restrict__ rb2, const double *__restrict__ cube,
+                                float4 *__restrict__ cen32) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nnodes) return;
+    if (b >= info[0]) return;
+    const double ox = cube_origin(cube, 0), oy = cube_origin(cube, 1), oz = cube_origin(cube, 2);
     cen32[b] = make_float4((float)(centre[3 * b] - ox), (float)(centre[3 * b + 1] - oy), (float)(centre[3 * b + 2] - oz),
                            (float)rb2[b]);
 }
 
-__global__ void leaf_flag_kernel(int nnodes, const int32_t *__restrict__ nchild, const int64_t *__restrict__ start,
-                                 int32_t *__restrict__ head /*npts*/) {
+__global__ void leaf_flag_kernel(const int32_t *__restrict__ info, const int32_t *__restrict__ nchild,
+                                 const int64_t *__restrict__ start, int32_t *__restrict__ head /*npts*/) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nnodes) return;
+    if (b >= info[0]) return;
     if (nchild[b] == 0) head[start[b]] = 1;
 }
 
-__global__ void leaf_index_kernel(int nnodes, const int32_t *__restrict__ nchild, const int64_t *__restrict__ start,
-                                  const int64_t *__restrict__ count, const int64_t *__restrict__ hscan,
-                                  const int32_t *__restrict__ perm, int32_t *__restrict__ node_leaf,
-                                  int32_t *__restrict__ leaf_node, int32_t *__restrict__ point_leaf) {
+__global__ void leaf_index_kernel(const int32_t *__restrict__ info, const int32_t *__restrict__ nchild,
+                                  const int64_t *__restrict__ start, const int64_t *__restrict__ count,
+                                  const int64_t *__restrict__ hscan, const int32_t *__restrict__ perm,
+                                  int32_t *__restrict__ node_leaf, int32_t *__restrict__ leaf_node,
+                                  int32_t *__restrict__ point_leaf) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nnodes) return;
+    if (b >= info[0]) return;
     if (nchild[b] != 0) { node_leaf[b] = -1; return; }
     const int li = (int)hscan[start[b]];
     node_leaf[b] = li;
@@ -205,11 +282,12 @@ __global__ void leaf_index_kernel(int nnodes, const int32_t *__restrict__ nchild
 }
 
 __global__ void gather_sources_kernel(int64_t n, int K, const int32_t *__restrict__ perm, const double *__restrict__ gy,
-                                      const double *__restrict__ gwa, double ox, double oy, double oz,
+                                      const double *__restrict__ gwa, const double *__restrict__ cube,
                                       double *__restrict__ ys, double *__restrict__ was, int32_t *__restrict__ pids,
                                       float4 *__restrict__ pos32) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
+    const double ox = cube_origin(cube, 0), oy = cube_origin(cube, 1), oz = cube_origin(cube, 2);
     const int p = perm[q];
     const double x = gy[3 * p], y = gy[3 * p + 1], z = gy[3 * p + 2];
     const double w = gwa ? gwa[p] : 1.0;
@@ -246,7 +324,7 @@ __global__ void traverse_kernel(int64_t ntg, const double *__restrict__ xs, cons
                                 int32_t *__restrict__ m2p_cnt, int32_t *__restrict__ p2p_cnt,
                                 const int64_t *__restrict__ m2p_ptr, const int64_t *__restrict__ p2p_ptr,
                                 int32_t *__restrict__ m2p_node, int32_t *__restrict__ p2p_node,
-                                int32_t *__restrict__ err, int nsplit) {
+                                unsigned long long *__restrict__ err, int nsplit) {
     // nsplit > 1: thread (i, c) traverses only the subtree of the root's child c
     // (the root itself, when accepted or a leaf, belongs to c = 0); counts and
     // offsets are per (i, c), and a target's list is their concatenation in c
@@ -306,7 +384,9 @@ __global__ void traverse_kernel(int64_t ntg, const double *__restrict__ xs, cons
             if (csub < nchild[0]) stack[sp++] = first_child[0] + csub;
         } else {
             const int fc = first_child[b], nc = nchild[b];
-            if (sp + nc > kStack) { atomicExch(err, 1); return; }
+            // cannot happen below 22 levels (at most 7 pending siblings per level);
+            // counting and filling stop at the same node, so the lists stay consistent
+            if (sp + nc > kStack) { atomicExch(err, 1ull); break; }
             for (int c = fc + nc - 1; c >= fc; --c) stack[sp++] = c;
         }
     }
@@ -884,63 +964,24 @@ __global__ void p2p_pairs_kernel(int64_t ntg, const int64_t *__restrict__ ptr, c
     if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
 }
 
-int64_t device_sum_i32(const int32_t *a, int64_t n, cudaStream_t s) {
-    TmpBuf<unsigned long long> d(1, s);
-    PB_CUDA_TRY(cudaMemsetAsync(d.p, 0, sizeof(unsigned long long), s));
-    if (n > 0) {
-        sum_i32_kernel<<<std::min<int64_t>(1024, div_up(n, 256)), 256, 0, s>>>(a, n, d.p);
-        PB_LAUNCH_CHECK();
-    }
-    unsigned long long h = 0;
-    PB_CUDA_TRY(cudaMemcpyAsync(&h, d.p, sizeof(h), cudaMemcpyDeviceToHost, s));
-    PB_CUDA_TRY(cudaStreamSynchronize(s));
-    return (int64_t)h;
-}
-
-void root_cube_from(const double *d_points, int64_t n, cudaStream_t s, double corner[3], double &side) {
-    TmpBuf<double> bb(6, s);
+void root_cube_from(const double *d_points, int64_t n, cudaStream_t s, double *cube) {
     const int nb = (int)std::min<int64_t>(256, std::max<int64_t>(1, (n + 4095) / 4096));
     TmpBuf<double> part(6 * nb, s);
     bbox_blocks_kernel<<<nb, 256, 0, s>>>(d_points, n, part.p);
     PB_LAUNCH_CHECK();
-    bbox_final_kernel<<<1, 32, 0, s>>>(part.p, nb, bb.p);
+    cube_final_kernel<<<1, 32, 0, s>>>(part.p, nb, cube);
     PB_LAUNCH_CHECK();
-    double h[6];
-    PB_CUDA_TRY(cudaMemcpyAsync(h, bb.p, sizeof(h), cudaMemcpyDeviceToHost, s));
-    PB_CUDA_TRY(cudaStreamSynchronize(s));
-    // plain IEEE double arithmetic, one operation per statement (the host is
-    // compiled without contraction)
-    double centre[3], ext[3];
-    for (int a = 0; a < 3; ++a) {
-        centre[a] = (h[a] + h[3 + a]) * 0.5;
-        ext[a] = h[3 + a] - h[a];
-    }
-    const double m = std::max(std::max(ext[0], ext[1]), ext[2]);
-    side = m * (1.0 + 0x1p-20);
-    if (side == 0.0 || !std::isfinite(side)) side = 1.0;
-    for (int a = 0; a < 3; ++a) {
-        const double half = side * 0.5;
-        corner[a] = centre[a] - half;
-    }
 }
 
 }  // namespace
 
-int64_t read_i64(const int64_t *d, cudaStream_t s) {
-    int64_t h = 0;
-    PB_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
-    PB_CUDA_TRY(cudaStreamSynchronize(s));
-    return h;
-}
-
-void morton_sort(const double *d_points, int64_t n, cudaStream_t s, double corner[3], double &side,
-                 DevBuf<uint64_t> &keys, DevBuf<int32_t> &perm) {
-    root_cube_from(d_points, n, s, corner, side);
+void morton_sort(const double *d_points, int64_t n, cudaStream_t s, double *cube, DevBuf<uint64_t> &keys,
+                 DevBuf<int32_t> &perm) {
+    root_cube_from(d_points, n, s, cube);
     keys.alloc(n);
     perm.alloc(n);
-    const double scale = 2097152.0 / side;
     if (n) {
-        morton_kernel<<<div_up(n, 256), 256, 0, s>>>(d_points, n, corner[0], corner[1], corner[2], scale, keys.p, perm.p);
+        morton_kernel<<<div_up(n, 256), 256, 0, s>>>(d_points, n, cube, keys.p, perm.p);
         PB_LAUNCH_CHECK();
         sort_key_index(keys.p, perm.p, n, s);
     }
@@ -950,90 +991,82 @@ void build_tree(Tree &T, const SurfDev &S, int K, int ncrit, cudaStream_t s) {
     build_tree_points(T, S.gy.p, S.gwa.p, S.n * K, K, ncrit, s);
 }
 
+// Everything on the device, one host read at the end: the root cube, the
+// sort, the levels (one block), node geometry, leaves and sorted sources are
+// sized by the node bound maxn, and the kernels read the node count from info.
 void build_tree_points(Tree &T, const double *pts, const double *wts, int64_t n, int K, int ncrit, cudaStream_t s) {
     T.npts = n;
-    morton_sort(pts, n, s, T.corner, T.side, T.keys, T.perm);
-    for (int a = 0; a < 3; ++a) T.origin[a] = T.corner[a] + 0.5 * T.side;
-    // level-by-level splitting; capacity bound: every level holds disjoint nodes
+    constexpr int kInfo = 32;
+    TmpBuf<double> cube(4, s);
+    TmpBuf<int32_t> info(kInfo, s);
+    morton_sort(pts, n, s, cube.p, T.keys, T.perm);
+    // node bound: every level holds disjoint nodes, each split node >= ncrit points
     const int64_t maxn = std::min<int64_t>((int64_t)1 + 8LL * (kMaxLevel + 1) * (n / std::max(1, ncrit) + 1),
                                            2 * n + 64);
     T.level.alloc(maxn); T.first_child.alloc(maxn); T.nchild.alloc(maxn); T.parent.alloc(maxn);
     T.start.alloc(maxn); T.count.alloc(maxn);
     TmpBuf<int64_t> ijk(3 * maxn, s);
-    {
-        int32_t l0 = 0, fc = -1, nc = 0, par = -1;
-        int64_t st = 0, ct = n, z3[3] = {0, 0, 0};
-        PB_CUDA_TRY(cudaMemcpyAsync(T.level.p, &l0, 4, cudaMemcpyHostToDevice, s));
-        PB_CUDA_TRY(cudaMemcpyAsync(T.first_child.p, &fc, 4, cudaMemcpyHostToDevice, s));
-        PB_CUDA_TRY(cudaMemcpyAsync(T.nchild.p, &nc, 4, cudaMemcpyHostToDevice, s));
-        PB_CUDA_TRY(cudaMemcpyAsync(T.parent.p, &par, 4, cudaMemcpyHostToDevice, s));
-        PB_CUDA_TRY(cudaMemcpyAsync(T.start.p, &st, 8, cudaMemcpyHostToDevice, s));
-        PB_CUDA_TRY(cudaMemcpyAsync(T.count.p, &ct, 8, cudaMemcpyHostToDevice, s));
-        PB_CUDA_TRY(cudaMemcpyAsync(ijk.p, z3, 24, cudaMemcpyHostToDevice, s));
-        PB_CUDA_TRY(cudaStreamSynchronize(s));
-    }
-    T.level_off.assign(1, 0);
-    int lb = 0, le = 1, lvl = 0;
-    while (true) {
-        T.level_off.push_back(le);
-        const int nb = le - lb;
-        TmpBuf<int32_t> bounds((size_t)nb * 9, s);
-        TmpBuf<int64_t> cscan(nb + 1, s);
-        split_count_kernel<<<div_up((int64_t)nb * 8, 128), 128, 0, s>>>(lvl, nb, lb, T.start.p, T.count.p, T.keys.p,
-                                                                         ncrit, T.nchild.p, bounds.p);
-        PB_LAUNCH_CHECK();
-        exclusive_scan_i32_to_i64(T.nchild.p + lb, cscan.p, nb, s);
-        const int64_t nnew = read_i64(cscan.p + nb, s);
-        if (le + nnew > maxn) fail(PB_ENOMEM, "octree node capacity exceeded");
-        split_write_kernel<<<div_up(nb, 128), 128, 0, s>>>(lvl, nb, lb, le, cscan.p, bounds.p, T.start.p, T.count.p,
-                                                           T.level.p, T.first_child.p, T.nchild.p, T.parent.p, ijk.p);
-        PB_LAUNCH_CHECK();
-        if (nnew == 0) break;
-        lb = le;
-        le = le + (int)nnew;
-        ++lvl;
-    }
-    T.nnodes = le;
-    T.nlevels = lvl + 1;
-    T.centre.alloc(3 * (size_t)T.nnodes);
-    T.rb2.alloc(T.nnodes);
-    node_geom_kernel<<<div_up(T.nnodes, 128), 128, 0, s>>>(T.nnodes, T.level.p, ijk.p, T.corner[0], T.corner[1],
-                                                           T.corner[2], T.side, T.centre.p, T.rb2.p);
+    build_levels_kernel<<<1, kLevelThreads, 0, s>>>(n, ncrit, (int)maxn, T.keys.p, T.start.p, T.count.p, T.level.p,
+                                                     T.first_child.p, T.nchild.p, T.parent.p, ijk.p, info.p);
     PB_LAUNCH_CHECK();
-    T.link.alloc(T.nnodes);
-    link_kernel<<<div_up(T.nnodes, 128), 128, 0, s>>>(T.nnodes, T.parent.p, T.first_child.p, T.nchild.p, T.link.p);
+    const int gn = div_up(maxn, 128);
+    T.centre.alloc(3 * (size_t)maxn);
+    T.rb2.alloc(maxn);
+    node_geom_kernel<<<gn, 128, 0, s>>>(info.p, T.level.p, ijk.p, cube.p, T.centre.p, T.rb2.p);
     PB_LAUNCH_CHECK();
-    T.cen32.alloc(T.nnodes);
-    centre32_kernel<<<div_up(T.nnodes, 128), 128, 0, s>>>(T.nnodes, T.centre.p, T.rb2.p, T.origin[0], T.origin[1],
-                                                          T.origin[2], T.cen32.p);
+    T.link.alloc(maxn);
+    link_kernel<<<gn, 128, 0, s>>>(info.p, T.parent.p, T.first_child.p, T.nchild.p, T.link.p);
+    PB_LAUNCH_CHECK();
+    T.cen32.alloc(maxn);
+    centre32_kernel<<<gn, 128, 0, s>>>(info.p, T.centre.p, T.rb2.p, cube.p, T.cen32.p);
     PB_LAUNCH_CHECK();
     // leaves in Morton order (= depth-first pre-order)
-    TmpBuf<int32_t> head(n, s);
+    TmpBuf<int32_t> head(std::max<int64_t>(1, n), s);
     TmpBuf<int64_t> hscan(n + 1, s);
-    PB_CUDA_TRY(cudaMemsetAsync(head.p, 0, n * sizeof(int32_t), s));
-    leaf_flag_kernel<<<div_up(T.nnodes, 128), 128, 0, s>>>(T.nnodes, T.nchild.p, T.start.p, head.p);
+    if (n) PB_CUDA_TRY(cudaMemsetAsync(head.p, 0, n * sizeof(int32_t), s));
+    leaf_flag_kernel<<<gn, 128, 0, s>>>(info.p, T.nchild.p, T.start.p, head.p);
     PB_LAUNCH_CHECK();
     exclusive_scan_i32_to_i64(head.p, hscan.p, n, s);
-    T.nleaves = (int)read_i64(hscan.p + n, s);
-    T.node_leaf.alloc(T.nnodes);
-    T.leaf_node.alloc(T.nleaves);
-    T.point_leaf.alloc(n);
-    leaf_index_kernel<<<div_up(T.nnodes, 128), 128, 0, s>>>(T.nnodes, T.nchild.p, T.start.p, T.count.p, hscan.p,
-                                                            T.perm.p, T.node_leaf.p, T.leaf_node.p, T.point_leaf.p);
+    T.node_leaf.alloc(maxn);
+    T.leaf_node.alloc(maxn);
+    T.point_leaf.alloc(std::max<int64_t>(1, n));
+    leaf_index_kernel<<<gn, 128, 0, s>>>(info.p, T.nchild.p, T.start.p, T.count.p, hscan.p, T.perm.p, T.node_leaf.p,
+                                         T.leaf_node.p, T.point_leaf.p);
     PB_LAUNCH_CHECK();
     // sorted source geometry
     T.ys.alloc(3 * n); T.was.alloc(n); T.pids.alloc(n); T.pos32.alloc(n);
-    gather_sources_kernel<<<div_up(n, 256), 256, 0, s>>>(n, K, T.perm.p, pts, wts, T.origin[0], T.origin[1],
-                                                         T.origin[2], T.ys.p, T.was.p, T.pids.p, T.pos32.p);
-    PB_LAUNCH_CHECK();
+    if (n) {
+        gather_sources_kernel<<<div_up(n, 256), 256, 0, s>>>(n, K, T.perm.p, pts, wts, cube.p, T.ys.p, T.was.p,
+                                                             T.pids.p, T.pos32.p);
+        PB_LAUNCH_CHECK();
+    }
     T.src64.alloc(8 * n); T.srcA32.alloc(n); T.srcB32.alloc(n);
+    HostReads rd(s);
+    const double *hc = rd.add(cube.p, 4);
+    const int32_t *hi = rd.add(info.p, kInfo);
+    const int64_t *hl = rd.add(hscan.p + n);
+    rd.wait();
+    if (hi[2]) fail(PB_ENOMEM, "octree node capacity exceeded");
+    for (int a = 0; a < 3; ++a) T.corner[a] = hc[a];
+    T.side = hc[3];
+    for (int a = 0; a < 3; ++a) T.origin[a] = T.corner[a] + 0.5 * T.side;
+    T.nnodes = hi[0];
+    T.nlevels = hi[1];
+    T.level_off.assign(hi + 3, hi + 3 + T.nlevels + 1);
+    T.nleaves = (int)*hl;
+    // the arrays keep their bound-sized blocks; their counts become the tree's
+    for (auto *b : {&T.level, &T.first_child, &T.nchild, &T.parent, &T.node_leaf}) b->alloc(T.nnodes);
+    T.start.alloc(T.nnodes); T.count.alloc(T.nnodes);
+    T.centre.alloc(3 * (size_t)T.nnodes); T.rb2.alloc(T.nnodes);
+    T.link.alloc(T.nnodes); T.cen32.alloc(T.nnodes);
+    T.leaf_node.alloc(std::max(1, T.nleaves));
 }
 
 void build_targets(Targets &G, const double *d_x, int64_t n, int surface, cudaStream_t s, int points_per_panel) {
     G.n = n;
     G.surface = surface;
-    double corner[3], side;
-    morton_sort(d_x, n, s, corner, side, G.keys, G.order);
+    TmpBuf<double> cube(4, s);
+    morton_sort(d_x, n, s, cube.p, G.keys, G.order);
     G.xs.alloc(3 * n);
     G.self_panel.alloc(n);
     G.rank.alloc(n);
@@ -1042,175 +1075,174 @@ void build_targets(Targets &G, const double *d_x, int64_t n, int surface, cudaSt
                                                              surface >= 0 ? points_per_panel : 0);
         PB_LAUNCH_CHECK();
     }
-    PB_CUDA_TRY(cudaStreamSynchronize(s));
 }
 
-void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
-                 cudaStream_t s) {
-    build_far_lists(Pr, G, T, prm, s, prm.p2p_tile);
-    build_near_lists(Pr, G, T, src, prm, use_self, s);
+namespace {
+
+// Entry-major grouping of one list kind (P2P or M2P) across the phases of a list build.
+struct Grouping {
+    int nkeys = 0;
+    int per = 32;
+    std::optional<TmpBuf<int64_t>> off, ioff;   // per key: first grouped entry, first item
+};
+
+// inv / pos: the list entries regrouped by key (box or leaf), and the per-key
+// item offsets; the item count is ioff[nkeys] (read by the caller).
+void group_count(int64_t m, const int64_t *ptr, const int32_t *ent, const int32_t *remap, int nkeys, int64_t nent,
+                 int per, int by_entry, DevBuf<int32_t> &inv, DevBuf<int32_t> &pos, Grouping &gr, cudaStream_t s) {
+    gr.nkeys = nkeys;
+    gr.per = per;
+    gr.off.emplace(nkeys + 1, s);
+    gr.ioff.emplace(nkeys + 1, s);
+    TmpBuf<int32_t> cnt(std::max(1, nkeys), s), cursor(std::max(1, nkeys), s), nit(std::max(1, nkeys), s);
+    PB_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * std::max(1, nkeys), s));
+    PB_CUDA_TRY(cudaMemsetAsync(cursor.p, 0, sizeof(int32_t) * std::max(1, nkeys), s));
+    inv.alloc(std::max<int64_t>(1, nent));
+    pos.alloc(std::max<int64_t>(1, nent));
+    TmpBuf<int32_t> owner(std::max<int64_t>(1, nent), s);
+    const bool hist = nkeys <= kHistKeys && nent > 0;
+    const int nb = hist ? (int)std::min<int64_t>(296, div_up(nent, 2048)) : 0;
+    const int64_t chunk = hist ? (nent + nb - 1) / nb : 0;
+    TmpBuf<int32_t> hb(hist ? (size_t)nb * nkeys : 0, s);
+    const size_t hshm = (size_t)nkeys * sizeof(int32_t);
+    if (m && nent) {
+        owner_kernel<<<div_up(m, 128), 128, 0, s>>>(m, ptr, owner.p);
+        PB_LAUNCH_CHECK();
+        if (hist) {
+            hist_count_kernel<<<nb, 256, hshm, s>>>(nent, chunk, ent, remap, nkeys, hb.p);
+            PB_LAUNCH_CHECK();
+            hist_scan_kernel<<<div_up(nkeys, 4), 128, 0, s>>>(nkeys, nb, hb.p, cnt.p);
+            PB_LAUNCH_CHECK();
+        } else {
+            inv_count_kernel<<<div_up(nent, 256), 256, 0, s>>>(nent, ent, remap, cnt.p);
+            PB_LAUNCH_CHECK();
+        }
+    }
+    exclusive_scan_i32_to_i64(cnt.p, gr.off->p, nkeys, s);
+    if (m && nent) {
+        if (hist)
+            hist_fill_kernel<<<nb, 256, hshm, s>>>(nent, chunk, owner.p, ent, remap, gr.off->p, hb.p, nkeys, by_entry,
+                                                   inv.p, pos.p);
+        else
+            inv_fill_kernel<<<div_up(nent, 256), 256, 0, s>>>(nent, owner.p, ent, remap, gr.off->p, cursor.p, by_entry,
+                                                              inv.p, pos.p);
+        PB_LAUNCH_CHECK();
+    }
+    item_count_kernel<<<div_up(nkeys, 128), 128, 0, s>>>(nkeys, gr.off->p, per, nit.p);
+    PB_LAUNCH_CHECK();
+    exclusive_scan_i32_to_i64(nit.p, gr.ioff->p, nkeys, s);
 }
 
-void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &prm, cudaStream_t s, int p2p_per_item) {
-    const int64_t m = G.n;
-    // every target traverses the root's eight subtrees as eight threads (eight times
-    // the parallelism for the charges, shorter serial walks for the panels)
-    const int nsplit = 8;
-    const int64_t ms = m * nsplit;
-    TmpBuf<int32_t> mc(ms, s), pc(ms, s), err(1, s);
-    TmpBuf<int64_t> mo(nsplit > 1 ? ms + 1 : 0, s), po(nsplit > 1 ? ms + 1 : 0, s);
-    PB_CUDA_TRY(cudaMemsetAsync(err.p, 0, 4, s));
-    const double theta2 = prm.theta * prm.theta;
-    const int direct = prm.theta <= 0.0;
+void group_fill(Grouping &gr, int64_t nitems, DevBuf<int4> &items, cudaStream_t s) {
+    items.alloc(std::max<int64_t>(1, nitems));
+    item_fill_kernel<<<div_up(gr.nkeys, 128), 128, 0, s>>>(gr.nkeys, gr.off->p, gr.ioff->p, gr.per, items.p);
+    PB_LAUNCH_CHECK();
+}
+
+// P2P items in buckets of similar source-leaf size (the larger leaves first
+// keep the direct-sum warps of one wave alike), stable within a bucket.
+void bucket_p2p_items(Pair &Pr, const Tree &T, int ncrit, int p2p_per_item, cudaStream_t s) {
+    if (Pr.n_p2p_items <= 1) return;
+    constexpr int nb = 64;
+    const int step = std::max(1, ncrit * p2p_per_item / nb);
+    const int64_t ni = Pr.n_p2p_items;
+    TmpBuf<int32_t> bucket(ni, s), bcnt(nb, s), cursor(nb, s);
+    TmpBuf<int64_t> boff(nb + 1, s);
+    TmpBuf<int4> sorted(ni, s);
+    PB_CUDA_TRY(cudaMemsetAsync(bcnt.p, 0, nb * sizeof(int32_t), s));
+    PB_CUDA_TRY(cudaMemsetAsync(cursor.p, 0, nb * sizeof(int32_t), s));
+    item_bucket_kernel<<<div_up(ni, 256), 256, 0, s>>>(ni, Pr.p2p_items.p, T.leaf_node.p, T.count.p, nb, step,
+                                                       bucket.p, bcnt.p);
+    PB_LAUNCH_CHECK();
+    exclusive_scan_i32_to_i64(bcnt.p, boff.p, nb, s);
+    item_scatter_kernel<<<div_up(ni, 256), 256, 0, s>>>(ni, Pr.p2p_items.p, bucket.p, boff.p, cursor.p, sorted.p);
+    PB_LAUNCH_CHECK();
+    PB_CUDA_TRY(cudaMemcpyAsync(Pr.p2p_items.p, sorted.p, ni * sizeof(int4), cudaMemcpyDeviceToDevice, s));
+}
+
+// State of one pair's list build between its two host reads.
+struct ListBuild {
+    static constexpr int nsplit = 8;   // a target walks the root's eight subtrees as eight threads
+    std::optional<TmpBuf<int64_t>> mo, po;             // per (target, subtree) list offsets
+    std::optional<TmpBuf<unsigned long long>> reach;   // source panels: largest near radius bits, largest h
+    Grouping gp, gm;
+    std::optional<TmpBuf<int32_t>> pleaf, rows, ovf;
+    std::optional<TmpBuf<float4>> pan32;
+};
+
+// Phase 1: list lengths per (target, subtree) and their offsets; the source
+// panels' near-field reach.
+void far_count(Pair &Pr, const Targets &G, const Tree &T, const SurfDev *src, const Params &prm, ListBuild &lb,
+               cudaStream_t s) {
+    const int64_t m = G.n, ms = m * ListBuild::nsplit;
+    Pr.stats.alloc(4);
+    PB_CUDA_TRY(cudaMemsetAsync(Pr.stats.p, 0, 4 * sizeof(unsigned long long), s));
+    TmpBuf<int32_t> mc(ms, s), pc(ms, s);
+    lb.mo.emplace(ms + 1, s);
+    lb.po.emplace(ms + 1, s);
     Pr.m2p_ptr.alloc(m + 1);
     Pr.p2p_ptr.alloc(m + 1);
     if (m) {
-        traverse_kernel<false><<<div_up(ms, 128), 128, 0, s>>>(m, G.xs.p, T.centre.p, T.rb2.p, T.cen32.p,
-                                                               T.first_child.p, T.nchild.p, theta2, direct, T.origin[0],
-                                                               T.origin[1], T.origin[2], mc.p, pc.p, nullptr, nullptr,
-                                                               nullptr, nullptr, err.p, nsplit);
+        traverse_kernel<false><<<div_up(ms, 128), 128, 0, s>>>(
+            m, G.xs.p, T.centre.p, T.rb2.p, T.cen32.p, T.first_child.p, T.nchild.p, prm.theta * prm.theta,
+            prm.theta <= 0.0, T.origin[0], T.origin[1], T.origin[2], mc.p, pc.p, nullptr, nullptr, nullptr, nullptr,
+            Pr.stats.p, ListBuild::nsplit);
         PB_LAUNCH_CHECK();
     }
-    int64_t *moff = Pr.m2p_ptr.p, *poff = Pr.p2p_ptr.p;
-    if (nsplit > 1) {
-        exclusive_scan_i32_to_i64(mc.p, mo.p, ms, s);
-        exclusive_scan_i32_to_i64(pc.p, po.p, ms, s);
-        take_every_kernel<<<div_up(m + 1, 256), 256, 0, s>>>(m, nsplit, mo.p, Pr.m2p_ptr.p);
+    exclusive_scan_i32_to_i64(mc.p, lb.mo->p, ms, s);
+    exclusive_scan_i32_to_i64(pc.p, lb.po->p, ms, s);
+    take_every_kernel<<<div_up(m + 1, 256), 256, 0, s>>>(m, ListBuild::nsplit, lb.mo->p, Pr.m2p_ptr.p);
+    PB_LAUNCH_CHECK();
+    take_every_kernel<<<div_up(m + 1, 256), 256, 0, s>>>(m, ListBuild::nsplit, lb.po->p, Pr.p2p_ptr.p);
+    PB_LAUNCH_CHECK();
+    if (src) {
+        lb.reach.emplace(2, s);
+        PB_CUDA_TRY(cudaMemsetAsync(lb.reach->p, 0, 2 * sizeof(unsigned long long), s));
+        reach_kernel<<<std::min<int64_t>(592, div_up(src->n, 256)), 256, 0, s>>>(
+            src->n, src->verts.p, src->tris.p, src->cen.p, src->L.p, prm.thres, lb.reach->p);
         PB_LAUNCH_CHECK();
-        take_every_kernel<<<div_up(m + 1, 256), 256, 0, s>>>(m, nsplit, po.p, Pr.p2p_ptr.p);
-        PB_LAUNCH_CHECK();
-        moff = mo.p;
-        poff = po.p;
-    } else {
-        exclusive_scan_i32_to_i64(mc.p, Pr.m2p_ptr.p, m, s);
-        exclusive_scan_i32_to_i64(pc.p, Pr.p2p_ptr.p, m, s);
     }
-    Pr.n_m2p = read_i64(Pr.m2p_ptr.p + m, s);
-    Pr.n_p2p = read_i64(Pr.p2p_ptr.p + m, s);
+}
+
+// Phase 2 (Pr.n_m2p, Pr.n_p2p known): the lists, the direct-sum pair count and
+// the first half of both groupings.
+void far_fill(Pair &Pr, const Targets &G, const Tree &T, const Params &prm, int p2p_per_item, ListBuild &lb,
+              cudaStream_t s) {
+    const int64_t m = G.n, ms = m * ListBuild::nsplit;
     Pr.m2p_node.alloc(std::max<int64_t>(1, Pr.n_m2p));
     Pr.p2p_node.alloc(std::max<int64_t>(1, Pr.n_p2p));
     if (m) {
-        traverse_kernel<true><<<div_up(ms, 128), 128, 0, s>>>(m, G.xs.p, T.centre.p, T.rb2.p, T.cen32.p,
-                                                              T.first_child.p, T.nchild.p, theta2, direct, T.origin[0],
-                                                              T.origin[1], T.origin[2], nullptr, nullptr, moff, poff,
-                                                              Pr.m2p_node.p, Pr.p2p_node.p, err.p, nsplit);
+        traverse_kernel<true><<<div_up(ms, 128), 128, 0, s>>>(
+            m, G.xs.p, T.centre.p, T.rb2.p, T.cen32.p, T.first_child.p, T.nchild.p, prm.theta * prm.theta,
+            prm.theta <= 0.0, T.origin[0], T.origin[1], T.origin[2], nullptr, nullptr, lb.mo->p, lb.po->p,
+            Pr.m2p_node.p, Pr.p2p_node.p, Pr.stats.p, ListBuild::nsplit);
+        PB_LAUNCH_CHECK();
+        p2p_pairs_kernel<<<std::min<int64_t>(1024, div_up(m, 256)), 256, 0, s>>>(m, Pr.p2p_ptr.p, Pr.p2p_node.p,
+                                                                                T.count.p, Pr.stats.p + 1);
         PB_LAUNCH_CHECK();
     }
-    int herr = 0;
-    PB_CUDA_TRY(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, s));
-    PB_CUDA_TRY(cudaStreamSynchronize(s));
-    if (herr) fail(PB_EINVAL, "octree traversal stack overflow");
-    // direct-sum pair count
-    {
-        TmpBuf<unsigned long long> d(1, s);
-        PB_CUDA_TRY(cudaMemsetAsync(d.p, 0, 8, s));
-        if (m) {
-            p2p_pairs_kernel<<<std::min<int64_t>(1024, div_up(m, 256)), 256, 0, s>>>(m, Pr.p2p_ptr.p, Pr.p2p_node.p,
-                                                                                    T.count.p, d.p);
-            PB_LAUNCH_CHECK();
-        }
-        unsigned long long h = 0;
-        PB_CUDA_TRY(cudaMemcpyAsync(&h, d.p, 8, cudaMemcpyDeviceToHost, s));
-        PB_CUDA_TRY(cudaStreamSynchronize(s));
-        Pr.p2p_pairs = (int64_t)h;
-    }
-    // entry-major grouping of the lists
-    auto group = [&](const int64_t *ptr, const int32_t *ent, const int32_t *remap, int nkeys, int64_t nent, int per,
-                     int by_entry,
-                     DevBuf<int32_t> &inv, DevBuf<int32_t> &pos, DevBuf<int4> &items, int64_t &nitems) {
-        TmpBuf<int32_t> cnt(std::max(1, nkeys), s), cursor(std::max(1, nkeys), s), nit(std::max(1, nkeys), s);
-        TmpBuf<int64_t> off(nkeys + 1, s), ioff(nkeys + 1, s);
-        PB_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * std::max(1, nkeys), s));
-        PB_CUDA_TRY(cudaMemsetAsync(cursor.p, 0, sizeof(int32_t) * std::max(1, nkeys), s));
-        inv.alloc(std::max<int64_t>(1, nent));
-        pos.alloc(std::max<int64_t>(1, nent));
-        TmpBuf<int32_t> owner(std::max<int64_t>(1, nent), s);
-        const bool hist = nkeys <= kHistKeys && nent > 0;
-        const int nb = hist ? (int)std::min<int64_t>(296, div_up(nent, 2048)) : 0;
-        const int64_t chunk = hist ? (nent + nb - 1) / nb : 0;
-        TmpBuf<int32_t> hb(hist ? (size_t)nb * nkeys : 0, s);
-        const size_t hshm = (size_t)nkeys * sizeof(int32_t);
-        if (m && nent) {
-            owner_kernel<<<div_up(m, 128), 128, 0, s>>>(m, ptr, owner.p);
-            PB_LAUNCH_CHECK();
-            if (hist) {
-                hist_count_kernel<<<nb, 256, hshm, s>>>(nent, chunk, ent, remap, nkeys, hb.p);
-                PB_LAUNCH_CHECK();
-                hist_scan_kernel<<<div_up(nkeys, 4), 128, 0, s>>>(nkeys, nb, hb.p, cnt.p);
-                PB_LAUNCH_CHECK();
-            } else {
-                inv_count_kernel<<<div_up(nent, 256), 256, 0, s>>>(nent, ent, remap, cnt.p);
-                PB_LAUNCH_CHECK();
-            }
-        }
-        exclusive_scan_i32_to_i64(cnt.p, off.p, nkeys, s);
-        if (m && nent) {
-            if (hist)
-                hist_fill_kernel<<<nb, 256, hshm, s>>>(nent, chunk, owner.p, ent, remap, off.p, hb.p, nkeys, by_entry,
-                                                       inv.p, pos.p);
-            else
-                inv_fill_kernel<<<div_up(nent, 256), 256, 0, s>>>(nent, owner.p, ent, remap, off.p, cursor.p, by_entry,
-                                                                  inv.p, pos.p);
-            PB_LAUNCH_CHECK();
-        }
-        item_count_kernel<<<div_up(nkeys, 128), 128, 0, s>>>(nkeys, off.p, per, nit.p);
-        PB_LAUNCH_CHECK();
-        exclusive_scan_i32_to_i64(nit.p, ioff.p, nkeys, s);
-        nitems = read_i64(ioff.p + nkeys, s);
-        items.alloc(std::max<int64_t>(1, nitems));
-        item_fill_kernel<<<div_up(nkeys, 128), 128, 0, s>>>(nkeys, off.p, ioff.p, per, items.p);
-        PB_LAUNCH_CHECK();
-    };
-    group(Pr.p2p_ptr.p, Pr.p2p_node.p, T.node_leaf.p, T.nleaves, Pr.n_p2p, p2p_per_item, 1, Pr.p2p_inv, Pr.p2p_ent,
-          Pr.p2p_items,
-          Pr.n_p2p_items);
-    if (Pr.n_p2p_items > 1) {
-        constexpr int nb = 64;
-        const int step = std::max(1, prm.ncrit * p2p_per_item / nb);
-        const int64_t ni = Pr.n_p2p_items;
-        TmpBuf<int32_t> bucket(ni, s), bcnt(nb, s), cursor(nb, s);
-        TmpBuf<int64_t> boff(nb + 1, s);
-        TmpBuf<int4> sorted(ni, s);
-        PB_CUDA_TRY(cudaMemsetAsync(bcnt.p, 0, nb * sizeof(int32_t), s));
-        PB_CUDA_TRY(cudaMemsetAsync(cursor.p, 0, nb * sizeof(int32_t), s));
-        item_bucket_kernel<<<div_up(ni, 256), 256, 0, s>>>(ni, Pr.p2p_items.p, T.leaf_node.p, T.count.p, nb, step,
-                                                           bucket.p, bcnt.p);
-        PB_LAUNCH_CHECK();
-        exclusive_scan_i32_to_i64(bcnt.p, boff.p, nb, s);
-        item_scatter_kernel<<<div_up(ni, 256), 256, 0, s>>>(ni, Pr.p2p_items.p, bucket.p, boff.p, cursor.p, sorted.p);
-        PB_LAUNCH_CHECK();
-        PB_CUDA_TRY(cudaMemcpyAsync(Pr.p2p_items.p, sorted.p, ni * sizeof(int4), cudaMemcpyDeviceToDevice, s));
-    }
-    group(Pr.m2p_ptr.p, Pr.m2p_node.p, nullptr, T.nnodes, Pr.n_m2p, 32, 1, Pr.m2p_inv, Pr.m2p_ent, Pr.m2p_items,
-          Pr.n_m2p_items);
+    group_count(m, Pr.p2p_ptr.p, Pr.p2p_node.p, T.node_leaf.p, T.nleaves, Pr.n_p2p, p2p_per_item, 1, Pr.p2p_inv,
+                Pr.p2p_ent, lb.gp, s);
+    group_count(m, Pr.m2p_ptr.p, Pr.m2p_node.p, nullptr, T.nnodes, Pr.n_m2p, 32, 1, Pr.m2p_inv, Pr.m2p_ent, lb.gm, s);
 }
 
-void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
-                      cudaStream_t s) {
+// Phase 2, near part (reach known): the cell grid of the source panels and one
+// pass of near_grid_kernel (counts, rows of up to kNearCap panels), the CSR
+// offsets and the excluded-panel counts.
+void near_count(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
+                double hmax, ListBuild &lb, cudaStream_t s) {
     const int64_t m = G.n;
-    // P2P leaf indices per target (ascending = pre-order)
-    TmpBuf<int32_t> pleaf(std::max<int64_t>(1, Pr.n_p2p), s);
+    lb.pleaf.emplace(std::max<int64_t>(1, Pr.n_p2p), s);
     if (Pr.n_p2p) {
-        node_to_leaf_kernel<<<div_up(Pr.n_p2p, 256), 256, 0, s>>>(Pr.n_p2p, Pr.p2p_node.p, T.node_leaf.p, pleaf.p);
+        node_to_leaf_kernel<<<div_up(Pr.n_p2p, 256), 256, 0, s>>>(Pr.n_p2p, Pr.p2p_node.p, T.node_leaf.p,
+                                                                   lb.pleaf->p);
         PB_LAUNCH_CHECK();
     }
-    // near-singular lists
-    TmpBuf<int32_t> nc(m, s), ex(m, s), se(m, s);
-    TmpBuf<unsigned long long> reach_d(2, s);
-    PB_CUDA_TRY(cudaMemsetAsync(reach_d.p, 0, 2 * sizeof(unsigned long long), s));
-    reach_kernel<<<std::min<int64_t>(592, div_up(src.n, 256)), 256, 0, s>>>(src.n, src.verts.p, src.tris.p, src.cen.p,
-                                                                           src.L.p, prm.thres, reach_d.p);
-    PB_LAUNCH_CHECK();
-    unsigned long long rbits[2] = {0, 0};
-    PB_CUDA_TRY(cudaMemcpyAsync(rbits, reach_d.p, sizeof(rbits), cudaMemcpyDeviceToHost, s));
-    TmpBuf<float4> pan32(std::max<int64_t>(1, src.n), s);
+    TmpBuf<int32_t> nc(std::max<int64_t>(1, m), s), ex(std::max<int64_t>(1, m), s), se(std::max<int64_t>(1, m), s);
+    lb.pan32.emplace(std::max<int64_t>(1, src.n), s);
     pan32_kernel<<<div_up(src.n, 256), 256, 0, s>>>(src.n, src.cen.p, src.L.p, prm.thres, T.origin[0], T.origin[1],
-                                                     T.origin[2], pan32.p);
+                                                     T.origin[2], lb.pan32->p);
     PB_LAUNCH_CHECK();
-    PB_CUDA_TRY(cudaStreamSynchronize(s));
-    double reach = 0.0, hmax = 0.0;
-    std::memcpy(&reach, &rbits[0], sizeof(reach));
-    std::memcpy(&hmax, &rbits[1], sizeof(hmax));
     // cell grid over the tree's root cube (it holds every centroid): cells at
     // least as wide as the largest near radius, at most about two per panel
     NearGrid g{};
@@ -1239,56 +1271,124 @@ void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &
     }
     exclusive_scan_i32_to_i64(ccnt.p, coff.p, ncell, s);
     if (src.n) {
-        cell_fill_kernel<<<div_up(src.n, 256), 256, 0, s>>>(src.n, cellof.p, coff.p, ccur.p, pan32.p, src.cen.p,
+        cell_fill_kernel<<<div_up(src.n, 256), 256, 0, s>>>(src.n, cellof.p, coff.p, ccur.p, lb.pan32->p, src.cen.p,
                                                             src.L.p, corder.p, cpan.p, cgeo.p);
         PB_LAUNCH_CHECK();
     }
     Pr.near_ptr.alloc(m + 1);
-    bool done = false;
+    lb.ovf.emplace(1, s);
+    PB_CUDA_TRY(cudaMemsetAsync(lb.ovf->p, 0, 4, s));
     if (m) {
-        // one pass: counts and a row of panels per target
-        TmpBuf<int32_t> rows((size_t)m * kNearCap, s), ovf(1, s);
-        PB_CUDA_TRY(cudaMemsetAsync(ovf.p, 0, 4, s));
+        lb.rows.emplace((size_t)m * kNearCap, s);
         near_grid_kernel<<<div_up(m, 4), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
-                                                       pleaf.p, T.point_leaf.p, T.origin[0], T.origin[1],
+                                                       lb.pleaf->p, T.point_leaf.p, T.origin[0], T.origin[1],
                                                        T.origin[2], prm.thres, g, coff.p, corder.p, cpan.p, cgeo.p,
-                                                       nc.p, ex.p, se.p, rows.p, ovf.p);
+                                                       nc.p, ex.p, se.p, lb.rows->p, lb.ovf->p);
         PB_LAUNCH_CHECK();
-        int hov = 0;
-        PB_CUDA_TRY(cudaMemcpyAsync(&hov, ovf.p, 4, cudaMemcpyDeviceToHost, s));
-        PB_CUDA_TRY(cudaStreamSynchronize(s));
-        exclusive_scan_i32_to_i64(nc.p, Pr.near_ptr.p, m, s);
-        Pr.n_near = read_i64(Pr.near_ptr.p + m, s);
-        Pr.near_panel.alloc(std::max<int64_t>(1, Pr.n_near));
-        if (!hov) {
-            near_compact_kernel<<<div_up(m, 128), 128, 0, s>>>(m, rows.p, Pr.near_ptr.p, Pr.near_panel.p);
-            PB_LAUNCH_CHECK();
-            done = true;
-        }
-    } else {
-        exclusive_scan_i32_to_i64(nc.p, Pr.near_ptr.p, m, s);
-        Pr.n_near = 0;
-        Pr.near_panel.alloc(1);
-        done = true;
-    }
-    Pr.near_excl = device_sum_i32(ex.p, m, s);
-    Pr.self_excl = device_sum_i32(se.p, m, s);
-    if (!done) {
-        // some target has more than kNearCap near panels: fill the CSR list in a second pass
-        TmpBuf<float4> ppan32(std::max<int64_t>(1, T.npts), s);
-        if (T.npts) {
-            point_pan32_kernel<<<div_up(T.npts, 256), 256, 0, s>>>(T.npts, T.pids.p, pan32.p, ppan32.p);
-            PB_LAUNCH_CHECK();
-        }
-        near_kernel<1><<<div_up(m, 4), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
-                                                    pleaf.p, T.leaf_node.p, T.start.p, T.count.p, T.perm.p, T.pids.p,
-                                                    T.point_leaf.p, src.cen.p, src.L.p, ppan32.p, T.origin[0],
-                                                    T.origin[1], T.origin[2], prm.thres, nullptr, nullptr, nullptr,
-                                                    Pr.near_ptr.p, Pr.near_panel.p, Pr.m2p_ptr.p, Pr.m2p_node.p,
-                                                    T.cen32.p, reach, nullptr, nullptr);
+        sum_i32_kernel<<<std::min<int64_t>(1024, div_up(m, 256)), 256, 0, s>>>(ex.p, m, Pr.stats.p + 2);
+        PB_LAUNCH_CHECK();
+        sum_i32_kernel<<<std::min<int64_t>(1024, div_up(m, 256)), 256, 0, s>>>(se.p, m, Pr.stats.p + 3);
         PB_LAUNCH_CHECK();
     }
-    PB_CUDA_TRY(cudaStreamSynchronize(s));
+    exclusive_scan_i32_to_i64(nc.p, Pr.near_ptr.p, m, s);
+}
+
+// Phase 3 (n_near and the row overflow flag known): the near lists in CSR form,
+// compacted from the rows or, where some target has more than kNearCap near
+// panels, filled by a second pass.
+void near_fill(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
+               double reach, bool overflow, ListBuild &lb, cudaStream_t s) {
+    const int64_t m = G.n;
+    Pr.near_panel.alloc(std::max<int64_t>(1, Pr.n_near));
+    if (!m) return;
+    if (!overflow) {
+        near_compact_kernel<<<div_up(m, 128), 128, 0, s>>>(m, lb.rows->p, Pr.near_ptr.p, Pr.near_panel.p);
+        PB_LAUNCH_CHECK();
+        return;
+    }
+    TmpBuf<float4> ppan32(std::max<int64_t>(1, T.npts), s);
+    if (T.npts) {
+        point_pan32_kernel<<<div_up(T.npts, 256), 256, 0, s>>>(T.npts, T.pids.p, lb.pan32->p, ppan32.p);
+        PB_LAUNCH_CHECK();
+    }
+    near_kernel<1><<<div_up(m, 4), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
+                                                lb.pleaf->p, T.leaf_node.p, T.start.p, T.count.p, T.perm.p, T.pids.p,
+                                                T.point_leaf.p, src.cen.p, src.L.p, ppan32.p, T.origin[0],
+                                                T.origin[1], T.origin[2], prm.thres, nullptr, nullptr, nullptr,
+                                                Pr.near_ptr.p, Pr.near_panel.p, Pr.m2p_ptr.p, Pr.m2p_node.p,
+                                                T.cen32.p, reach, nullptr, nullptr);
+    PB_LAUNCH_CHECK();
+}
+
+// stats: [0] traversal stack overflow, [1] direct-sum pairs, [2] near panels
+// excluded (outside the direct-sum leaves), [3] own panels excluded.
+void apply_list_stats(Pair &Pr, const unsigned long long *h) {
+    if (h[0]) fail(PB_EINVAL, "octree traversal stack overflow");
+    Pr.p2p_pairs = (int64_t)h[1];
+    Pr.near_excl = (int64_t)h[2];
+    Pr.self_excl = (int64_t)h[3];
+}
+
+void read_far_counts(Pair &Pr, ListBuild &lb, int64_t m, double *reach, double *hmax, cudaStream_t s) {
+    HostReads rd(s);
+    const int64_t *hm = rd.add(Pr.m2p_ptr.p + m);
+    const int64_t *hp = rd.add(Pr.p2p_ptr.p + m);
+    const unsigned long long *hr = lb.reach ? rd.add(lb.reach->p, 2) : nullptr;
+    rd.wait();
+    Pr.n_m2p = *hm;
+    Pr.n_p2p = *hp;
+    if (hr) {
+        std::memcpy(reach, &hr[0], sizeof(double));
+        std::memcpy(hmax, &hr[1], sizeof(double));
+    }
+}
+
+}  // namespace
+
+void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
+                 cudaStream_t s) {
+    const int64_t m = G.n;
+    ListBuild lb;
+    double reach = 0.0, hmax = 0.0;
+    far_count(Pr, G, T, &src, prm, lb, s);
+    read_far_counts(Pr, lb, m, &reach, &hmax, s);
+    far_fill(Pr, G, T, prm, prm.p2p_tile, lb, s);
+    near_count(Pr, G, T, src, prm, use_self, hmax, lb, s);
+    HostReads rd(s);
+    const int64_t *hpi = rd.add(lb.gp.ioff->p + lb.gp.nkeys);
+    const int64_t *hmi = rd.add(lb.gm.ioff->p + lb.gm.nkeys);
+    const int32_t *hov = rd.add(lb.ovf->p);
+    const int64_t *hnn = rd.add(Pr.near_ptr.p + m);
+    const unsigned long long *hst = rd.add(Pr.stats.p, 4);
+    rd.wait();
+    apply_list_stats(Pr, hst);
+    Pr.n_p2p_items = *hpi;
+    Pr.n_m2p_items = *hmi;
+    Pr.n_near = m ? *hnn : 0;
+    group_fill(lb.gp, Pr.n_p2p_items, Pr.p2p_items, s);
+    bucket_p2p_items(Pr, T, prm.ncrit, prm.p2p_tile, s);
+    group_fill(lb.gm, Pr.n_m2p_items, Pr.m2p_items, s);
+    near_fill(Pr, G, T, src, prm, use_self, reach, *hov != 0, lb, s);
+}
+
+void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &prm, cudaStream_t s, int p2p_per_item) {
+    const int64_t m = G.n;
+    ListBuild lb;
+    double reach = 0.0, hmax = 0.0;
+    far_count(Pr, G, T, nullptr, prm, lb, s);
+    read_far_counts(Pr, lb, m, &reach, &hmax, s);
+    far_fill(Pr, G, T, prm, p2p_per_item, lb, s);
+    HostReads rd(s);
+    const int64_t *hpi = rd.add(lb.gp.ioff->p + lb.gp.nkeys);
+    const int64_t *hmi = rd.add(lb.gm.ioff->p + lb.gm.nkeys);
+    const unsigned long long *hst = rd.add(Pr.stats.p, 4);
+    rd.wait();
+    apply_list_stats(Pr, hst);
+    Pr.n_p2p_items = *hpi;
+    Pr.n_m2p_items = *hmi;
+    group_fill(lb.gp, Pr.n_p2p_items, Pr.p2p_items, s);
+    bucket_p2p_items(Pr, T, prm.ncrit, p2p_per_item, s);
+    group_fill(lb.gm, Pr.n_m2p_items, Pr.m2p_items, s);
 }
 
 }  // namespace pb

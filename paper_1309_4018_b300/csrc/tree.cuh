@@ -5,9 +5,10 @@
 
 namespace pb {
 
-// Root cube of the points, Morton keys and the (key, index) sort.
-void morton_sort(const double *d_points, int64_t n, cudaStream_t s, double corner[3], double &side,
-                 DevBuf<uint64_t> &keys, DevBuf<int32_t> &perm);
+// Root cube of the points (device: corner x, y, z, side), Morton keys and the
+// (key, index) sort, all queued on s.
+void morton_sort(const double *d_points, int64_t n, cudaStream_t s, double *cube, DevBuf<uint64_t> &keys,
+                 DevBuf<int32_t> &perm);
 // Octree over the K Gauss points of every panel of S (point j*K + k).
 void build_tree(Tree &T, const SurfDev &S, int K, int ncrit, cudaStream_t s);
 // Octree over n points (n * 3, input order) with weights wts (null: 1); point p
@@ -28,6 +29,5 @@ void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &pr
 // The near-singular lists of targets G against the panels of src (after build_far_lists).
 void build_near_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
                       cudaStream_t s);
-int64_t read_i64(const int64_t *d, cudaStream_t s);
 
 }  // namespace pb
