@@ -1,4 +1,6 @@
 // Device-wide exclusive scan and key/index sort used by the setup phase.
+#include <utility>
+
 #include "common.cuh"
 
 namespace pb {
@@ -80,32 +82,26 @@ void scan_impl(const TIn *in, int64_t *out, int64_t n, cudaStream_t s) {
     PB_LAUNCH_CHECK();
 }
 
-// ---------------------------------------------------------------- bitonic sort
-__device__ __forceinline__ bool pair_greater(uint64_t ka, int32_t ia, uint64_t kb, int32_t ib) {
-    return ka > kb || (ka == kb && ia > ib);
+// ---------------------------------------------------------------- merge sort
+// (key, idx) pairs in one total order: by key, then by idx.
+__device__ __forceinline__ bool pair_less(uint64_t ka, int32_t ia, uint64_t kb, int32_t ib) {
+    return ka < kb || (ka == kb && ia < ib);
 }
 
-__global__ void bitonic_global_kernel(uint64_t *__restrict__ k, int32_t *__restrict__ v, int64_t half,
-                                      int64_t j, int64_t stage) {
+constexpr int kSortBlock = 2048;   // elements per tile sorted in shared memory (1024 threads)
+constexpr int kMergeItems = 8;     // outputs per thread of a merge round
+
+// Copies n pairs and pads to n2 (a multiple of kSortBlock) with pairs that
+// order after every real one.
+__global__ void pad_kernel(uint64_t *k, int32_t *v, const uint64_t *kin, const int32_t *vin, int64_t n, int64_t n2) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= half) return;
-    const int64_t lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
-    const int64_t hi = lo + j;
-    const bool asc = (lo & stage) == 0;
-    uint64_t ka = k[lo], kb = k[hi];
-    int32_t ia = v[lo], ib = v[hi];
-    if (pair_greater(ka, ia, kb, ib) == asc) {
-        k[lo] = kb; k[hi] = ka;
-        v[lo] = ib; v[hi] = ia;
-    }
+    if (i >= n2) return;
+    if (i < n) { k[i] = kin[i]; v[i] = vin[i]; }
+    else { k[i] = ~0ull; v[i] = 0x7fffffff; }
 }
 
-constexpr int kSortBlock = 2048;  // elements per block in shared memory (1024 threads)
-
-// Runs every step j <= jmax of the given stage (or of all stages up to kSortBlock
-// when stage == 0) inside one block's shared tile.
-__global__ void __launch_bounds__(1024) bitonic_shared_kernel(uint64_t *__restrict__ k, int32_t *__restrict__ v,
-                                                              int64_t stage, int64_t jmax) {
+// Every tile of kSortBlock pairs sorted ascending in shared memory (bitonic network).
+__global__ void __launch_bounds__(1024) tile_sort_kernel(uint64_t *__restrict__ k, int32_t *__restrict__ v) {
     __shared__ uint64_t sk[kSortBlock];
     __shared__ int32_t sv[kSortBlock];
     const int64_t base = (int64_t)blockIdx.x * kSortBlock;
@@ -114,36 +110,54 @@ __global__ void __launch_bounds__(1024) bitonic_shared_kernel(uint64_t *__restri
         sv[t] = v[base + t];
     }
     __syncthreads();
-    auto step = [&](int64_t st, int64_t j) {
-        const int i = threadIdx.x;  // kSortBlock / 2 compare-exchanges
-        const int lo = ((i & ~(int)(j - 1)) << 1) | (i & (int)(j - 1));
-        const int hi = lo + (int)j;
-        const bool asc = ((base + lo) & st) == 0;
-        uint64_t ka = sk[lo], kb = sk[hi];
-        int32_t ia = sv[lo], ib = sv[hi];
-        if (pair_greater(ka, ia, kb, ib) == asc) {
-            sk[lo] = kb; sk[hi] = ka;
-            sv[lo] = ib; sv[hi] = ia;
+    for (int st = 2; st <= kSortBlock; st <<= 1)
+        for (int j = st >> 1; j > 0; j >>= 1) {
+            const int i = threadIdx.x;   // kSortBlock / 2 compare-exchanges
+            const int lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+            const int hi = lo + j;
+            const bool asc = (lo & st) == 0;
+            const uint64_t ka = sk[lo], kb = sk[hi];
+            const int32_t ia = sv[lo], ib = sv[hi];
+            if (pair_less(kb, ib, ka, ia) == asc) {
+                sk[lo] = kb; sk[hi] = ka;
+                sv[lo] = ib; sv[hi] = ia;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-    };
-    if (stage == 0) {
-        for (int64_t st = 2; st <= kSortBlock; st <<= 1)
-            for (int64_t j = st >> 1; j > 0; j >>= 1) step(st, j);
-    } else {
-        for (int64_t j = jmax; j > 0; j >>= 1) step(stage, j);
-    }
     for (int t = threadIdx.x; t < kSortBlock; t += blockDim.x) {
         k[base + t] = sk[t];
         v[base + t] = sv[t];
     }
 }
 
-__global__ void pad_kernel(uint64_t *k, int32_t *v, const uint64_t *kin, const int32_t *vin, int64_t n, int64_t n2) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n2) return;
-    if (i < n) { k[i] = kin[i]; v[i] = vin[i]; }
-    else { k[i] = ~0ull; v[i] = 0x7fffffff; }
+// One merge round: the sorted runs of width w of (ka, va) merged pairwise into
+// (kb, vb); only the first nout outputs are written.  Each thread finds where
+// its first output lies on the merge path of its two runs (binary search),
+// then merges kMergeItems outputs.  Within the total order no two real pairs
+// are equal, so the result is the unique sorted order.
+__global__ void merge_round_kernel(const uint64_t *__restrict__ ka, const int32_t *__restrict__ va,
+                                   uint64_t *__restrict__ kb, int32_t *__restrict__ vb, int64_t n, int64_t nout,
+                                   int64_t w) {
+    const int64_t o0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kMergeItems;
+    if (o0 >= nout) return;
+    const int64_t s = o0 / (2 * w) * (2 * w);
+    const int64_t a0 = s, na = min(w, n - s);
+    const int64_t b0 = s + na, nb = max((int64_t)0, min(w, n - s - na));
+    const int64_t d = o0 - s;
+    int64_t lo = max((int64_t)0, d - nb), hi = min(d, na);
+    while (lo < hi) {   // smallest i with B[d - i - 1] < A[i]
+        const int64_t i = (lo + hi) >> 1;
+        const int64_t j = d - i - 1;
+        if (pair_less(ka[b0 + j], va[b0 + j], ka[a0 + i], va[a0 + i])) hi = i;
+        else lo = i + 1;
+    }
+    int64_t i = lo, j = d - lo;
+    const int64_t end = min(o0 + kMergeItems, min(nout, s + na + nb));
+    for (int64_t o = o0; o < end; ++o) {
+        const bool take_a = j >= nb || (i < na && !pair_less(ka[b0 + j], va[b0 + j], ka[a0 + i], va[a0 + i]));
+        if (take_a) { kb[o] = ka[a0 + i]; vb[o] = va[a0 + i]; ++i; }
+        else { kb[o] = ka[b0 + j]; vb[o] = va[b0 + j]; ++j; }
+    }
 }
 
 }  // namespace
@@ -151,28 +165,33 @@ __global__ void pad_kernel(uint64_t *k, int32_t *v, const uint64_t *kin, const i
 void exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s) { scan_impl<int64_t>(in, out, n, s); }
 void exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s) { scan_impl<int32_t>(in, out, n, s); }
 
+// Tiles of kSortBlock pairs sorted in shared memory, then merge rounds doubling
+// the sorted run width; the last round writes into (keys, idx).
 void sort_key_index(uint64_t *keys, int32_t *idx, int64_t n, cudaStream_t s) {
     if (n <= 1) return;
-    int64_t n2 = kSortBlock;
-    while (n2 < n) n2 <<= 1;
-    TmpBuf<uint64_t> k(n2, s);
-    TmpBuf<int32_t> v(n2, s);
-    pad_kernel<<<div_up(n2, 256), 256, 0, s>>>(k.p, v.p, keys, idx, n, n2);
+    const int64_t n2 = (n + kSortBlock - 1) / kSortBlock * kSortBlock;
+    TmpBuf<uint64_t> k0(n2, s), k1(n2, s);
+    TmpBuf<int32_t> v0(n2, s), v1(n2, s);
+    pad_kernel<<<div_up(n2, 256), 256, 0, s>>>(k0.p, v0.p, keys, idx, n, n2);
     PB_LAUNCH_CHECK();
-    const unsigned nblk = (unsigned)(n2 / kSortBlock);
-    bitonic_shared_kernel<<<nblk, 1024, 0, s>>>(k.p, v.p, 0, 0);
+    tile_sort_kernel<<<(unsigned)(n2 / kSortBlock), 1024, 0, s>>>(k0.p, v0.p);
     PB_LAUNCH_CHECK();
-    for (int64_t stage = 2 * kSortBlock; stage <= n2; stage <<= 1) {
-        int64_t j = stage >> 1;
-        for (; j >= kSortBlock; j >>= 1) {
-            bitonic_global_kernel<<<div_up(n2 / 2, 256), 256, 0, s>>>(k.p, v.p, n2 / 2, j, stage);
-            PB_LAUNCH_CHECK();
-        }
-        bitonic_shared_kernel<<<nblk, 1024, 0, s>>>(k.p, v.p, stage, j);
+    uint64_t *ka = k0.p, *kb = k1.p;
+    int32_t *va = v0.p, *vb = v1.p;
+    for (int64_t w = kSortBlock; w < n2; w <<= 1) {
+        const bool last = 2 * w >= n2;
+        uint64_t *ko = last ? keys : kb;
+        int32_t *vo = last ? idx : vb;
+        const int64_t nout = last ? n : n2;
+        merge_round_kernel<<<div_up(div_up(nout, kMergeItems), 256), 256, 0, s>>>(ka, va, ko, vo, n2, nout, w);
         PB_LAUNCH_CHECK();
+        if (last) return;
+        std::swap(ka, kb);
+        std::swap(va, vb);
     }
-    PB_CUDA_TRY(cudaMemcpyAsync(keys, k.p, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
-    PB_CUDA_TRY(cudaMemcpyAsync(idx, v.p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    // a single tile: copy the sorted pairs back
+    PB_CUDA_TRY(cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    PB_CUDA_TRY(cudaMemcpyAsync(idx, va, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
 }
 
 }  // namespace pb
