@@ -180,7 +180,11 @@ void setup_problem(pb_problem *pb) {
     // the charges must lie in their region: inside every surface that has it as
     // inner region, outside every surface that has it as outer region
     int n_wind = 0;
-    bool wind_join = false;
+    // the near-field values, self integrals and right-hand side go to the side
+    // stream as soon as their inputs exist, beside the next pair's list build
+    // (latency-bound: small kernels and host reads); joined before the
+    // preconditioner
+    cudaStream_t fs = pb->side ? pb->side : s;
     if (nc > 0) {
         std::vector<int32_t> expect;
         std::vector<int> wsurf;
@@ -208,8 +212,6 @@ void setup_problem(pb_problem *pb) {
             winding_mismatch(pb->wind.p, nc, n_wind, expect.data(), pb->wind_bad.p, ws);
             PB_CUDA_TRY(cudaMemcpyAsync(pb->wind_bad_h.p, pb->wind_bad.p, 3 * sizeof(int32_t),
                                         cudaMemcpyDeviceToHost, ws));
-            if (ws != s) PB_CUDA_TRY(cudaEventRecord(pb->evj, ws));
-            wind_join = ws != s;
         }
     }
     // block structure (multi-surface rule): row (s, R) gets sigma (K - c V) of every t in dR
@@ -269,27 +271,31 @@ void setup_problem(pb_problem *pb) {
             P.dV32.alloc(std::max<int64_t>(1, (int64_t)nk * P.n_near));
             P.dK32.alloc(std::max<int64_t>(1, (int64_t)nk * P.n_near));
         }
-        if (mixed) near_values32(P, G, src, prm.K, prm.K_fine, P.dV32.p, P.dK32.p, s);
+        if (fs != s) {
+            PB_CUDA_TRY(cudaEventRecord(pb->evf, s));
+            PB_CUDA_TRY(cudaStreamWaitEvent(fs, pb->evf, 0));
+        }
+        if (mixed) near_values32(P, G, src, prm.K, prm.K_fine, P.dV32.p, P.dK32.p, fs);
         for (size_t k = 0; k < nk; ++k) {
             P.VK[k].alloc(2 * std::max<int64_t>(1, G.n));
             if (!mixed) {
                 P.dV[k].alloc(std::max<int64_t>(1, P.n_near));
                 P.dK[k].alloc(std::max<int64_t>(1, P.n_near));
-                near_values(P, G, src, prm.K, prm.K_fine, P.kappas[k], P.dV[k].p, P.dK[k].p, s);
+                near_values(P, G, src, prm.K, prm.K_fine, P.kappas[k], P.dV[k].p, P.dK[k].p, fs);
             }
             if (use_self) {
                 P.selfV[k].alloc(src.n);
                 if (nk == 2 && k == 1) {
-                    self_integrals2(src, prm.N_k, P.kappas[0], P.kappas[1], P.selfV[0].p, P.selfV[1].p, s);
+                    self_integrals2(src, prm.N_k, P.kappas[0], P.kappas[1], P.selfV[0].p, P.selfV[1].p, fs);
                 } else if (nk == 1) {
-                    self_integrals(src, prm.N_k, P.kappas[k], P.selfV[k].p, s);
+                    self_integrals(src, prm.N_k, P.kappas[k], P.selfV[k].p, fs);
                 }
             }
         }
         if (P.p2p_self_in)
             for (size_t k = 0; k < nk; ++k) {
                 P.selfV32[k].alloc(src.n);
-                self_minus_kpoint(src, prm.K, P.kappas[k], P.selfV[k].p, P.selfV32[k].p, s);
+                self_minus_kpoint(src, prm.K, P.kappas[k], P.selfV[k].p, P.selfV32[k].p, fs);
             }
     };
     for (auto &P : pb->pairs) prepare(P, false);
@@ -300,7 +306,7 @@ void setup_problem(pb_problem *pb) {
     }
     // right-hand side
     pb->b.alloc(2 * pb->N);
-    pb->b.zero(s);
+    pb->b.zero(fs);
     if (nc > 0) {
         const Region &Rg = pb->regions[pb->cregion];
         for (int sf = 0; sf < ns; ++sf) {
@@ -309,8 +315,12 @@ void setup_problem(pb_problem *pb) {
                 if (Rs[side] == pb->cregion)
                     rhs_rows(pb->S[sf], nc, pb->cq_d.p, pb->cxyz_d.p, Rg.kappa, Rg.eps,
                              pb->b.p + 2 * pb->off[sf] + side * pb->S[sf].n,
-                             prm.precision == PB_MIXED ? pb->T[sf].origin : nullptr, s);
+                             prm.precision == PB_MIXED ? pb->T[sf].origin : nullptr, fs);
         }
+    }
+    if (fs != s) {
+        PB_CUDA_TRY(cudaEventRecord(pb->evj, fs));
+        PB_CUDA_TRY(cudaStreamWaitEvent(s, pb->evj, 0));
     }
     pb->x.alloc(2 * pb->N);
     pb->x.zero(s);
@@ -348,7 +358,6 @@ void setup_problem(pb_problem *pb) {
             if (prm.precision == PB_MIXED && prm.P <= kRadialMaxP)
                 pb->T[t].rmom32.alloc((size_t)pb->T[t].nnodes * radial_floats(prm.P));
         }
-    if (wind_join) PB_CUDA_TRY(cudaStreamWaitEvent(s, pb->evj, 0));
     PB_CUDA_TRY(cudaEventRecord(pb->ev1, s));
     PB_CUDA_TRY(cudaEventSynchronize(pb->ev1));
     if (n_wind > 0 && pb->wind_bad_h.p[0] > 0) {

@@ -17,8 +17,12 @@
 #include <cstring>
 #include <optional>
 
+#include <cooperative_groups.h>
+
 #include "model.cuh"
 #include "tree.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pb {
 
@@ -105,125 +109,131 @@ __global__ void morton_kernel(const double *__restrict__ p, int64_t n, const dou
     idx[i] = (int32_t)i;
 }
 
-// The whole octree below the root in one block, level by level (a host round
-// trip per level cost more than the levels themselves).  Per node of the level
-// (one thread each): a node with >= ncrit points above the deepest level splits
-// into its non-empty octants, the bound of octant o being the first of its
-// sorted keys whose octant digit is >= o (binary search).  The block then
-// numbers the children breadth first (an exclusive scan of the child counts in
-// node order, octants in order within a node) and writes them.  info: [0]
-// nodes, [1] levels, [2] 1 if maxn nodes were not enough, [3 + l] first node
-// of level l (levels + 1 entries).  Writes beyond maxn are skipped.
-constexpr int kLevelThreads = 1024;
-
-__device__ __forceinline__ int octant_bounds(const uint64_t *__restrict__ keys, int64_t s, int64_t c, int lvl,
-                                             int64_t bnd[9]) {
-    const int sh = 3 * (kMaxLevel - 1 - lvl);
-    bnd[0] = 0;
-    int nonempty = 0;
-    for (int o = 1; o <= 8; ++o) {
-        int64_t lo = bnd[o - 1], hi = c;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            const int d = (int)((keys[s + mid] >> sh) & 7ull);
-            if (d < o) lo = mid + 1; else hi = mid;
-        }
-        bnd[o] = lo;
-        nonempty += lo > bnd[o - 1];
-    }
-    return nonempty;
-}
+// The whole octree below the root in one cooperative launch, level by level
+// (a host round trip per level cost more than the levels themselves), with a
+// grid-wide barrier between the phases of a level:
+//   A  per (node, octant o = 1..8) of a node with >= ncrit points above the
+//      deepest level: the first of the node's sorted keys whose octant digit
+//      is >= o (binary search), into bnd[9 t + o];
+//   B  (block 0) child counts (non-empty octants) and their exclusive scan in
+//      node order: the children are numbered breadth first, octants in order
+//      within a node;
+//   C  per node: the children written.
+// info: [0] nodes, [1] levels, [2] 1 if maxn nodes were not enough, [3 + l]
+// first node of level l (levels + 1 entries).  Writes beyond maxn are skipped.
+constexpr int kLevelThreads = 256;
 
 __global__ void __launch_bounds__(kLevelThreads) build_levels_kernel(
     int64_t n, int ncrit, int maxn, const uint64_t *__restrict__ keys, int64_t *__restrict__ start,
     int64_t *__restrict__ count, int32_t *__restrict__ level, int32_t *__restrict__ first_child,
-    int32_t *__restrict__ nchild, int32_t *__restrict__ parent, int64_t *__restrict__ ijk, int32_t *__restrict__ info) {
+    int32_t *__restrict__ nchild, int32_t *__restrict__ parent, int64_t *__restrict__ ijk, int32_t *__restrict__ bnd,
+    int32_t *__restrict__ cscan, int32_t *__restrict__ info) {
+    cg::grid_group grid = cg::this_grid();
     __shared__ int wsum[kLevelThreads / 32];
-    __shared__ int s_total;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
+    const int64_t gtid = (int64_t)blockIdx.x * kLevelThreads + tid, gsize = (int64_t)gridDim.x * kLevelThreads;
+    if (gtid == 0) {
         start[0] = 0; count[0] = n; level[0] = 0; first_child[0] = -1; nchild[0] = 0; parent[0] = -1;
         ijk[0] = 0; ijk[1] = 0; ijk[2] = 0;
         info[3] = 0;
+        info[2] = 0;
     }
-    __syncthreads();
-    int lb = 0, le = 1, lvl = 0, err = 0;
+    grid.sync();
+    int lb = 0, le = 1, lvl = 0;
     while (true) {
-        if (tid == 0) info[3 + lvl + 1] = le;
-        // child counts of the level's nodes
-        for (int b = lb + tid; b < le; b += kLevelThreads) {
-            const int64_t c = count[b];
-            int64_t bnd[9];
-            nchild[b] = (c >= ncrit && lvl < kMaxLevel) ? octant_bounds(keys, start[b], c, lvl, bnd) : 0;
-        }
-        __syncthreads();
-        // children, numbered by an exclusive scan of the counts over the level in chunks of the block
-        int carry = 0;
-        for (int c0 = lb; c0 < le; c0 += kLevelThreads) {
-            const int b = c0 + tid;
-            const int nc = b < le ? nchild[b] : 0;
-            int incl = nc;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+        const int nb = le - lb;
+        const int sh = 3 * (kMaxLevel - 1 - lvl);
+        // A: octant bounds of the nodes that split
+        for (int64_t g = gtid; g < (int64_t)nb * 8; g += gsize) {
+            const int t = (int)(g >> 3), o = (int)(g & 7) + 1;
+            const int64_t c = count[lb + t];
+            if (!(c >= ncrit && lvl < kMaxLevel)) continue;
+            const int64_t s0 = start[lb + t];
+            int64_t lo = 0, hi = c;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                const int d = (int)((keys[s0 + mid] >> sh) & 7ull);
+                if (d < o) lo = mid + 1; else hi = mid;
             }
-            if (lane == 31) wsum[warp] = incl;
-            __syncthreads();
-            if (warp == 0) {
-                int t = wsum[lane];
+            bnd[9 * t + o] = (int32_t)lo;
+            if (o == 1) bnd[9 * t] = 0;
+        }
+        grid.sync();
+        // B: child counts and their scan (block 0)
+        if (blockIdx.x == 0) {
+            if (tid == 0) info[3 + lvl + 1] = le;
+            int carry = 0;
+            for (int c0 = 0; c0 < nb; c0 += kLevelThreads) {
+                const int t = c0 + tid;
+                int nc = 0;
+                if (t < nb) {
+                    const int64_t c = count[lb + t];
+                    if (c >= ncrit && lvl < kMaxLevel)
+                        for (int o = 0; o < 8; ++o) nc += bnd[9 * t + o + 1] > bnd[9 * t + o];
+                    nchild[lb + t] = nc;
+                }
+                int incl = nc;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, t, o);
-                    if (lane >= o) t += y;
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
                 }
-                wsum[lane] = t;
-                if (lane == 31) s_total = t;
-            }
-            __syncthreads();
-            const int excl = carry + incl - nc + (warp > 0 ? wsum[warp - 1] : 0);
-            if (b < le) {
-                if (nc == 0) {
-                    first_child[b] = -1;
-                } else {
-                    int ch = le + excl;
-                    first_child[b] = ch;
-                    const int64_t s0 = start[b];
-                    int64_t bnd[9];
-                    octant_bounds(keys, s0, count[b], lvl, bnd);
-                    for (int o = 0; o < 8; ++o) {
-                        if (bnd[o + 1] <= bnd[o]) continue;
-                        if (ch < maxn) {
-                            start[ch] = s0 + bnd[o];
-                            count[ch] = bnd[o + 1] - bnd[o];
-                            level[ch] = lvl + 1;
-                            parent[ch] = b;
-                            nchild[ch] = 0;
-                            first_child[ch] = -1;
-                            ijk[3 * ch + 0] = 2 * ijk[3 * b + 0] + ((o >> 2) & 1);
-                            ijk[3 * ch + 1] = 2 * ijk[3 * b + 1] + ((o >> 1) & 1);
-                            ijk[3 * ch + 2] = 2 * ijk[3 * b + 2] + (o & 1);
-                        }
-                        ++ch;
-                    }
+                if (lane == 31) wsum[warp] = incl;
+                __syncthreads();
+                int before = 0, total = 0;
+                for (int w = 0; w < kLevelThreads / 32; ++w) {
+                    if (w < warp) before += wsum[w];
+                    total += wsum[w];
                 }
+                if (t < nb) cscan[t] = carry + before + incl - nc;
+                carry += total;
+                __syncthreads();
             }
-            carry += s_total;
-            __syncthreads();
+            if (tid == 0) cscan[nb] = carry;
         }
-        if (carry == 0) break;
-        if ((int64_t)le + carry > maxn) {
-            err = 1;
-            break;
+        grid.sync();
+        // C: the children
+        const int nnew = cscan[nb];
+        const bool over = (int64_t)le + nnew > maxn;
+        for (int64_t t = gtid; t < nb; t += gsize) {
+            const int b = lb + (int)t;
+            const int nc = nchild[b];
+            if (nc == 0) {
+                first_child[b] = -1;
+                continue;
+            }
+            int ch = le + cscan[t];
+            first_child[b] = ch;
+            const int64_t s0 = start[b];
+            for (int o = 0; o < 8; ++o) {
+                const int64_t cs = bnd[9 * t + o], ce = bnd[9 * t + o + 1];
+                if (ce <= cs) continue;
+                if (ch < maxn) {
+                    start[ch] = s0 + cs;
+                    count[ch] = ce - cs;
+                    level[ch] = lvl + 1;
+                    parent[ch] = b;
+                    nchild[ch] = 0;
+                    first_child[ch] = -1;
+                    ijk[3 * ch + 0] = 2 * ijk[3 * b + 0] + ((o >> 2) & 1);
+                    ijk[3 * ch + 1] = 2 * ijk[3 * b + 1] + ((o >> 1) & 1);
+                    ijk[3 * ch + 2] = 2 * ijk[3 * b + 2] + (o & 1);
+                }
+                ++ch;
+            }
+        }
+        grid.sync();
+        if (nnew == 0 || over) {
+            if (gtid == 0) {
+                info[0] = le;
+                info[1] = lvl + 1;
+                info[2] = over ? 1 : 0;
+            }
+            return;
         }
         lb = le;
-        le += carry;
+        le += nnew;
         ++lvl;
-    }
-    if (tid == 0) {
-        info[0] = le;
-        info[1] = lvl + 1;
-        info[2] = err;
     }
 }
 
@@ -268,17 +278,21 @@ __global__ void leaf_flag_kernel(const int32_t *__restrict__ info, const int32_t
 }
 
 __global__ void leaf_index_kernel(const int32_t *__restrict__ info, const int32_t *__restrict__ nchild,
-                                  const int64_t *__restrict__ start, const int64_t *__restrict__ count,
-                                  const int64_t *__restrict__ hscan, const int32_t *__restrict__ perm,
-                                  int32_t *__restrict__ node_leaf, int32_t *__restrict__ leaf_node,
-                                  int32_t *__restrict__ point_leaf) {
+                                  const int64_t *__restrict__ start, const int64_t *__restrict__ hscan,
+                                  int32_t *__restrict__ node_leaf, int32_t *__restrict__ leaf_node) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= info[0]) return;
     if (nchild[b] != 0) { node_leaf[b] = -1; return; }
     const int li = (int)hscan[start[b]];
     node_leaf[b] = li;
     leaf_node[li] = b;
-    for (int64_t q = start[b]; q < start[b] + count[b]; ++q) point_leaf[perm[q]] = li;
+}
+
+// The leaf of sorted point q is the number of leaf starts at or before q, less one.
+__global__ void point_leaf_kernel(int64_t n, const int64_t *__restrict__ hscan, const int32_t *__restrict__ perm,
+                                  int32_t *__restrict__ point_leaf) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) point_leaf[perm[q]] = (int32_t)(hscan[q + 1] - 1);
 }
 
 __global__ void gather_sources_kernel(int64_t n, int K, const int32_t *__restrict__ perm, const double *__restrict__ gy,
@@ -1006,9 +1020,26 @@ void build_tree_points(Tree &T, const double *pts, const double *wts, int64_t n,
     T.level.alloc(maxn); T.first_child.alloc(maxn); T.nchild.alloc(maxn); T.parent.alloc(maxn);
     T.start.alloc(maxn); T.count.alloc(maxn);
     TmpBuf<int64_t> ijk(3 * maxn, s);
-    build_levels_kernel<<<1, kLevelThreads, 0, s>>>(n, ncrit, (int)maxn, T.keys.p, T.start.p, T.count.p, T.level.p,
-                                                     T.first_child.p, T.nchild.p, T.parent.p, ijk.p, info.p);
-    PB_LAUNCH_CHECK();
+    {
+        // at most maxn nodes on a level: bounds of 9 per node, scan of maxn + 1
+        TmpBuf<int32_t> bnd(9 * maxn, s), cscan(maxn + 1, s);
+        int per_sm = 0;
+        PB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_levels_kernel, kLevelThreads, 0));
+        int nsm = 0, dev = 0;
+        PB_CUDA_TRY(cudaGetDevice(&dev));
+        PB_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        const int grid = std::max(1, std::min(nsm * std::min(per_sm, 2), div_up(maxn * 8, kLevelThreads)));
+        int64_t a_n = n;
+        int a_ncrit = ncrit, a_maxn = (int)maxn;
+        const uint64_t *a_keys = T.keys.p;
+        int64_t *a_start = T.start.p, *a_count = T.count.p, *a_ijk = ijk.p;
+        int32_t *a_level = T.level.p, *a_fc = T.first_child.p, *a_nch = T.nchild.p, *a_par = T.parent.p,
+                *a_bnd = bnd.p, *a_cs = cscan.p, *a_info = info.p;
+        void *args[] = {&a_n, &a_ncrit, &a_maxn, &a_keys, &a_start, &a_count, &a_level, &a_fc, &a_nch, &a_par,
+                        &a_ijk, &a_bnd, &a_cs, &a_info};
+        PB_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)build_levels_kernel, grid, kLevelThreads, args, 0, s));
+        PB_LAUNCH_CHECK();
+    }
     const int gn = div_up(maxn, 128);
     T.centre.alloc(3 * (size_t)maxn);
     T.rb2.alloc(maxn);
@@ -1030,9 +1061,12 @@ void build_tree_points(Tree &T, const double *pts, const double *wts, int64_t n,
     T.node_leaf.alloc(maxn);
     T.leaf_node.alloc(maxn);
     T.point_leaf.alloc(std::max<int64_t>(1, n));
-    leaf_index_kernel<<<gn, 128, 0, s>>>(info.p, T.nchild.p, T.start.p, T.count.p, hscan.p, T.perm.p, T.node_leaf.p,
-                                         T.leaf_node.p, T.point_leaf.p);
+    leaf_index_kernel<<<gn, 128, 0, s>>>(info.p, T.nchild.p, T.start.p, hscan.p, T.node_leaf.p, T.leaf_node.p);
     PB_LAUNCH_CHECK();
+    if (n) {
+        point_leaf_kernel<<<div_up(n, 256), 256, 0, s>>>(n, hscan.p, T.perm.p, T.point_leaf.p);
+        PB_LAUNCH_CHECK();
+    }
     // sorted source geometry
     T.ys.alloc(3 * n); T.was.alloc(n); T.pids.alloc(n); T.pos32.alloc(n);
     if (n) {
