@@ -1,7 +1,12 @@
 // Device-wide exclusive scan and key/index sort used by the setup phase.
+#include <cooperative_groups.h>
+
+#include <algorithm>
 #include <utility>
 
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pb {
 
@@ -51,13 +56,95 @@ __global__ void scan_tiles_kernel(const TIn *__restrict__ in, int64_t *__restric
     if (threadIdx.x == kScanThreads - 1) tile_sums[blockIdx.x] = excl + run;
 }
 
-__global__ void scan_add_kernel(int64_t *__restrict__ out, const int64_t *__restrict__ tile_off, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] += tile_off[i / kScanTile];
+// Sum of the block's values (every thread gets it).
+__device__ __forceinline__ int64_t block_sum(int64_t v, int64_t *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    int64_t t = 0;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; ++w) t += red[w];
+    return t;
 }
 
-__global__ void write_total_kernel(int64_t *out, const int64_t *tile_off, int64_t ntiles, int64_t n) {
-    out[n] = tile_off[ntiles];
+// The whole scan in one cooperative launch: every block takes a contiguous
+// run of tiles; it sums its run, and after a grid-wide barrier adds the sums
+// of the blocks before it and scans its tiles in order with a running carry.
+// Block 0 writes the total into out[n].  Integer sums: the result does not
+// depend on the grid.
+template <typename TIn>
+__global__ void __launch_bounds__(kScanThreads) scan_coop_kernel(const TIn *__restrict__ in, int64_t *__restrict__ out,
+                                                                 int64_t n, int64_t *__restrict__ block_sums) {
+    cg::grid_group grid = cg::this_grid();
+    __shared__ int64_t warp_tot[kScanThreads / 32];
+    __shared__ int64_t red[kScanThreads / 32];
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * per * kScanTile, b1 = min(n, b0 + per * kScanTile);
+    int64_t local = 0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += kScanThreads) local += (int64_t)in[i];
+    local = block_sum(local, red);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = local;
+    grid.sync();
+    int64_t before = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += kScanThreads) before += block_sums[b];
+    before = block_sum(before, red);
+    if (blockIdx.x == 0) {
+        int64_t all = 0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += kScanThreads) all += block_sums[b];
+        all = block_sum(all, red);
+        if (threadIdx.x == 0) out[n] = all;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t carry = before;
+    for (int64_t t0 = b0; t0 < b1; t0 += kScanTile) {
+        const int64_t base = t0 + threadIdx.x * kScanItems;
+        int64_t v[kScanItems];
+        int64_t run = 0;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            const int64_t x = (base + i < b1) ? (int64_t)in[base + i] : 0;
+            v[i] = run;
+            run += x;
+        }
+        int64_t incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        __syncthreads();
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        int64_t wbefore = 0, tile_total = 0;
+#pragma unroll
+        for (int w = 0; w < kScanThreads / 32; ++w) {
+            if (w < warp) wbefore += warp_tot[w];
+            tile_total += warp_tot[w];
+        }
+        const int64_t excl = carry + wbefore + incl - run;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i)
+            if (base + i < b1) out[base + i] = v[i] + excl;
+        carry += tile_total;
+    }
+}
+
+int scan_grid(int64_t ntiles) {
+    static int cap = 0;
+    if (!cap) {
+        int per_sm = 0, nsm = 0, dev = 0;
+        PB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_coop_kernel<int64_t>, kScanThreads, 0));
+        int per_sm32 = 0;
+        PB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm32, scan_coop_kernel<int32_t>, kScanThreads, 0));
+        PB_CUDA_TRY(cudaGetDevice(&dev));
+        PB_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        cap = std::max(1, nsm * std::min(2, std::min(per_sm, per_sm32)));
+    }
+    return (int)std::min<int64_t>(cap, ntiles);
 }
 
 template <typename TIn>
@@ -71,14 +158,13 @@ void scan_impl(const TIn *in, int64_t *out, int64_t n, cudaStream_t s) {
         PB_LAUNCH_CHECK();
         return;
     }
-    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
-    TmpBuf<int64_t> sums(ntiles, s), offs(ntiles + 1, s);
-    scan_tiles_kernel<TIn><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, out, sums.p, n);
-    PB_LAUNCH_CHECK();
-    scan_impl<int64_t>(sums.p, offs.p, ntiles, s);
-    scan_add_kernel<<<div_up(n, 256), 256, 0, s>>>(out, offs.p, n);
-    PB_LAUNCH_CHECK();
-    write_total_kernel<<<1, 1, 0, s>>>(out, offs.p, ntiles, n);
+    const int grid = scan_grid((n + kScanTile - 1) / kScanTile);
+    TmpBuf<int64_t> sums(grid, s);
+    const TIn *a_in = in;
+    int64_t *a_out = out, *a_sums = sums.p;
+    int64_t a_n = n;
+    void *args[] = {&a_in, &a_out, &a_n, &a_sums};
+    PB_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)scan_coop_kernel<TIn>, grid, kScanThreads, args, 0, s));
     PB_LAUNCH_CHECK();
 }
 

@@ -415,10 +415,12 @@ __global__ void take_every_kernel(int64_t m, int nsplit, const int64_t *__restri
 
 // ---------------------------------------------------------------- entry-major grouping
 // key(e) = leaf index of a P2P entry (remap = node_leaf) or node id of an M2P entry.
+// owner[e] = the target whose list holds entry e (one warp per target).
 __global__ void owner_kernel(int64_t m, const int64_t *__restrict__ ptr, int32_t *__restrict__ owner) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= m) return;
-    for (int64_t e = ptr[t]; e < ptr[t + 1]; ++e) owner[e] = (int32_t)t;
+    const int lane = threadIdx.x & 31;
+    for (int64_t e = ptr[t] + lane; e < ptr[t + 1]; e += 32) owner[e] = (int32_t)t;
 }
 
 // Lanes holding the same key (neighbouring Morton-sorted targets share most
@@ -535,13 +537,15 @@ __global__ void item_count_kernel(int nkeys, const int64_t *__restrict__ off, in
     nitems[k] = (int)((off[k + 1] - off[k] + per - 1) / per);
 }
 
+// The items of key k: (k, first grouped entry, entries <= per, 0), one warp per key.
 __global__ void item_fill_kernel(int nkeys, const int64_t *__restrict__ off, const int64_t *__restrict__ ioff, int per,
                                  int4 *__restrict__ items) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (k >= nkeys) return;
+    const int lane = threadIdx.x & 31;
     const int64_t c = off[k + 1] - off[k];
-    for (int64_t w = 0; per * w < c; ++w)
-        items[ioff[k] + w] = make_int4(k, (int)(off[k] + per * w), (int)(c - per * w < per ? c - per * w : per), 0);
+    for (int64_t w = lane; per * w < c; w += 32)
+        items[ioff[k] + w] = make_int4((int)k, (int)(off[k] + per * w), (int)(c - per * w < per ? c - per * w : per), 0);
 }
 
 // P2P items in descending order of cost (sources of the leaf x targets), by
@@ -803,8 +807,9 @@ __global__ void cell_count_kernel(int64_t n, const double *__restrict__ cen, Nea
 // L) in cell order.
 __global__ void cell_fill_kernel(int64_t n, const int32_t *__restrict__ cellof, const int64_t *__restrict__ off,
                                  int32_t *__restrict__ cursor, const float4 *__restrict__ pan32,
-                                 const double *__restrict__ cen, const double *__restrict__ L,
-                                 int32_t *__restrict__ order, float4 *__restrict__ cpan, dvec4 *__restrict__ cgeo) {
+                                 const double *__restrict__ cen, const double *__restrict__ L, double thres,
+                                 int32_t *__restrict__ order, float4 *__restrict__ cpan, dvec4 *__restrict__ cgeo,
+                                 float *__restrict__ cr2) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const int c = cellof[j];
@@ -812,6 +817,8 @@ __global__ void cell_fill_kernel(int64_t n, const int32_t *__restrict__ cellof, 
     order[q] = (int32_t)j;
     cpan[q] = pan32[j];
     cgeo[q] = dvec4{cen[3 * j], cen[3 * j + 1], cen[3 * j + 2], L[j]};
+    const double tl = __dmul_rn(thres, L[j]);
+    cr2[q] = (float)__dmul_rn(tl, tl);
 }
 
 // One warp per target.  The panels of the 27 cells around the target form one
@@ -840,8 +847,8 @@ __global__ void __launch_bounds__(128) near_grid_kernel(
     const int64_t *__restrict__ p2p_ptr, const int32_t *__restrict__ p2p_leafidx, const int32_t *__restrict__ point_leaf,
     double ox, double oy, double oz, double thres, NearGrid g, const int64_t *__restrict__ off,
     const int32_t *__restrict__ order, const float4 *__restrict__ cpan, const dvec4 *__restrict__ cgeo,
-    int32_t *__restrict__ ncount, int32_t *__restrict__ excl, int32_t *__restrict__ self_excl,
-    int32_t *__restrict__ rows, int32_t *__restrict__ overflow) {
+    const float *__restrict__ cr2, double side, int32_t *__restrict__ ncount, int32_t *__restrict__ excl,
+    int32_t *__restrict__ self_excl, int32_t *__restrict__ rows, int32_t *__restrict__ overflow) {
     __shared__ int32_t sleaf[4][kNearLeafStage];
     __shared__ int32_t scell[4][27];
     __shared__ int64_t sbase[4][27];
@@ -850,6 +857,9 @@ __global__ void __launch_bounds__(128) near_grid_kernel(
     if (i >= ntg) return;
     const double x = xs[3 * i], y = xs[3 * i + 1], z = xs[3 * i + 2];
     const float fx = (float)(x - ox), fy = (float)(y - oy), fz = (float)(z - oz);
+    // bound on the FP32 coordinate differences' error (the panels lie in the
+    // root cube, |c - o| <= side / 2 per axis)
+    const float ecoord = (float)(0x1p-23 * (fmax(fabs(x - ox), fmax(fabs(y - oy), fabs(z - oz))) + side));
     const int me = use_self ? selfp[i] : -1;
     const int64_t l0 = p2p_ptr[i];
     const int64_t nl = p2p_ptr[i + 1] - l0;
@@ -905,13 +915,27 @@ __global__ void __launch_bounds__(128) near_grid_kernel(
             const float4 pc = cpan[q];
             j = order[q];
             const float dx = fx - pc.x, dy = fy - pc.y, dz = fz - pc.z;
-            if (dx * dx + dy * dy + dz * dz < pc.w && j != me) {
-                // is_near with the panel's centroid and L from its cell-ordered copy
-                const dvec4 cg = cgeo[q];
-                const double ddx = __dsub_rn(x, cg.x), ddy = __dsub_rn(y, cg.y), ddz = __dsub_rn(z, cg.z);
-                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
-                const double tl = __dmul_rn(tt, cg.w);
-                if (d2 < __dmul_rn(tl, tl)) {
+            const float d2f = dx * dx + dy * dy + dz * dz;
+            if (d2f < pc.w && j != me) {
+                // is_near: in FP32 where the error bound leaves no doubt (|d2f - d2| and
+                // |r2f - r2| within err), else by the FP64 test with the panel's
+                // centroid and L from its cell-ordered copy
+                const float r2f = cr2[q];
+                const float err = 1e-4f * (d2f + r2f) + ecoord * (4.f * sqrtf(d2f) + 10.f * ecoord);
+                bool nearp;
+                if (d2f + err < r2f) {
+                    nearp = true;
+                } else if (d2f - err > r2f) {
+                    nearp = false;
+                } else {
+                    const dvec4 cg = cgeo[q];
+                    const double ddx = __dsub_rn(x, cg.x), ddy = __dsub_rn(y, cg.y), ddz = __dsub_rn(z, cg.z);
+                    const double d2 =
+                        __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+                    const double tl = __dmul_rn(tt, cg.w);
+                    nearp = d2 < __dmul_rn(tl, tl);
+                }
+                if (nearp) {
                     bool all = true;
                     for (int kk = 0; kk < K && all; ++kk) all = member(point_leaf[(int64_t)j * K + kk]);
                     acc = all;
@@ -1140,7 +1164,7 @@ void group_count(int64_t m, const int64_t *ptr, const int32_t *ent, const int32_
     TmpBuf<int32_t> hb(hist ? (size_t)nb * nkeys : 0, s);
     const size_t hshm = (size_t)nkeys * sizeof(int32_t);
     if (m && nent) {
-        owner_kernel<<<div_up(m, 128), 128, 0, s>>>(m, ptr, owner.p);
+        owner_kernel<<<div_up(m * 32, 256), 256, 0, s>>>(m, ptr, owner.p);
         PB_LAUNCH_CHECK();
         if (hist) {
             hist_count_kernel<<<nb, 256, hshm, s>>>(nent, chunk, ent, remap, nkeys, hb.p);
@@ -1169,7 +1193,8 @@ void group_count(int64_t m, const int64_t *ptr, const int32_t *ent, const int32_
 
 void group_fill(Grouping &gr, int64_t nitems, DevBuf<int4> &items, cudaStream_t s) {
     items.alloc(std::max<int64_t>(1, nitems));
-    item_fill_kernel<<<div_up(gr.nkeys, 128), 128, 0, s>>>(gr.nkeys, gr.off->p, gr.ioff->p, gr.per, items.p);
+    item_fill_kernel<<<div_up((int64_t)gr.nkeys * 32, 256), 256, 0, s>>>(gr.nkeys, gr.off->p, gr.ioff->p, gr.per,
+                                                                         items.p);
     PB_LAUNCH_CHECK();
 }
 
@@ -1296,6 +1321,7 @@ void near_count(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, c
         corder(std::max<int64_t>(1, src.n), s);
     TmpBuf<float4> cpan(std::max<int64_t>(1, src.n), s);
     TmpBuf<dvec4> cgeo(std::max<int64_t>(1, src.n), s);
+    TmpBuf<float> cr2(std::max<int64_t>(1, src.n), s);
     TmpBuf<int64_t> coff(ncell + 1, s);
     PB_CUDA_TRY(cudaMemsetAsync(ccnt.p, 0, ncell * sizeof(int32_t), s));
     PB_CUDA_TRY(cudaMemsetAsync(ccur.p, 0, ncell * sizeof(int32_t), s));
@@ -1306,7 +1332,7 @@ void near_count(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, c
     exclusive_scan_i32_to_i64(ccnt.p, coff.p, ncell, s);
     if (src.n) {
         cell_fill_kernel<<<div_up(src.n, 256), 256, 0, s>>>(src.n, cellof.p, coff.p, ccur.p, lb.pan32->p, src.cen.p,
-                                                            src.L.p, corder.p, cpan.p, cgeo.p);
+                                                            src.L.p, prm.thres, corder.p, cpan.p, cgeo.p, cr2.p);
         PB_LAUNCH_CHECK();
     }
     Pr.near_ptr.alloc(m + 1);
@@ -1317,7 +1343,7 @@ void near_count(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, c
         near_grid_kernel<<<div_up(m, 4), 128, 0, s>>>(m, prm.K, G.xs.p, G.self_panel.p, (int)use_self, Pr.p2p_ptr.p,
                                                        lb.pleaf->p, T.point_leaf.p, T.origin[0], T.origin[1],
                                                        T.origin[2], prm.thres, g, coff.p, corder.p, cpan.p, cgeo.p,
-                                                       nc.p, ex.p, se.p, lb.rows->p, lb.ovf->p);
+                                                       cr2.p, T.side, nc.p, ex.p, se.p, lb.rows->p, lb.ovf->p);
         PB_LAUNCH_CHECK();
         sum_i32_kernel<<<std::min<int64_t>(1024, div_up(m, 256)), 256, 0, s>>>(ex.p, m, Pr.stats.p + 2);
         PB_LAUNCH_CHECK();
