@@ -49,6 +49,7 @@ struct Tree {
     DevBuf<int64_t> start, count;
     DevBuf<double> centre, rb2;      // centre: nnodes * 3
     DevBuf<float4> cen32;            // (centre - origin) in FP32, r_b^2
+    DevBuf<float4> pofs32;           // centre - parent centre, the FP64 difference rounded to FP32 (0 at the root)
     DevBuf<int32_t> leaf_node;       // leaf index (Morton order) -> node
     DevBuf<int32_t> point_leaf;      // point index (input order) -> leaf index
     // sorted source data

@@ -270,6 +270,16 @@ __global__ void centre32_kernel(const int32_t *__restrict__ info, const double *
                            (float)rb2[b]);
 }
 
+__global__ void parent_offset_kernel(const int32_t *__restrict__ info, const int32_t *__restrict__ parent,
+                                     const double *__restrict__ centre, float4 *__restrict__ pofs32) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= info[0]) return;
+    const int p = parent[b];
+    pofs32[b] = p < 0 ? make_float4(0.f, 0.f, 0.f, 0.f)
+                      : make_float4((float)(centre[3 * b] - centre[3 * p]), (float)(centre[3 * b + 1] - centre[3 * p + 1]),
+                                    (float)(centre[3 * b + 2] - centre[3 * p + 2]), 0.f);
+}
+
 __global__ void leaf_flag_kernel(const int32_t *__restrict__ info, const int32_t *__restrict__ nchild,
                                  const int64_t *__restrict__ start, int32_t *__restrict__ head /*npts*/) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1075,6 +1085,9 @@ void build_tree_points(Tree &T, const double *pts, const double *wts, int64_t n,
     T.cen32.alloc(maxn);
     centre32_kernel<<<gn, 128, 0, s>>>(info.p, T.centre.p, T.rb2.p, cube.p, T.cen32.p);
     PB_LAUNCH_CHECK();
+    T.pofs32.alloc(maxn);
+    parent_offset_kernel<<<gn, 128, 0, s>>>(info.p, T.parent.p, T.centre.p, T.pofs32.p);
+    PB_LAUNCH_CHECK();
     // leaves in Morton order (= depth-first pre-order)
     TmpBuf<int32_t> head(std::max<int64_t>(1, n), s);
     TmpBuf<int64_t> hscan(n + 1, s);
@@ -1116,7 +1129,7 @@ void build_tree_points(Tree &T, const double *pts, const double *wts, int64_t n,
     for (auto *b : {&T.level, &T.first_child, &T.nchild, &T.parent, &T.node_leaf}) b->alloc(T.nnodes);
     T.start.alloc(T.nnodes); T.count.alloc(T.nnodes);
     T.centre.alloc(3 * (size_t)T.nnodes); T.rb2.alloc(T.nnodes);
-    T.link.alloc(T.nnodes); T.cen32.alloc(T.nnodes);
+    T.link.alloc(T.nnodes); T.cen32.alloc(T.nnodes); T.pofs32.alloc(T.nnodes);
     T.leaf_node.alloc(std::max(1, T.nleaves));
 }
 

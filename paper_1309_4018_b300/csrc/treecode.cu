@@ -37,6 +37,7 @@ namespace {
 
 __constant__ int c_terms[3 * kMaxTerms1];   // (k1, k2, k3) of every term up to order kMaxP + 1, graded order
 __constant__ double c_binom[13][13];
+__constant__ float c_binom32[13][13];   // the same integers in FP32 (exact)
 
 
 __host__ __device__ constexpr int term_index(int k1, int k2, int k3) {
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(256) m2m_kernel(int nodes_begin, const int32_t
     }
     for (int i = threadIdx.x; i < (P + 1) * (P + 1); i += blockDim.x) {
         const int n = i / (P + 1), k = i - n * (P + 1);
-        sbin[n][k] = (T)c_binom[n][k];
+        sbin[n][k] = sizeof(T) == 4 ? (T)c_binom32[n][k] : (T)c_binom[n][k];
     }
     __syncthreads();
     shift_children<T>(NT, 2 * NT, sterm, sbin, hs, buf0, buf1, mom + (int64_t)b * stride + base);
@@ -1050,6 +1051,7 @@ __device__ __forceinline__ T ld_cg(const T *p) { return __ldcg(p); }
 // loads.  buf0, buf1: 8 * nval values each.
 template <typename T>
 __device__ void climb_m2m(int4 up, int NT, int nval, const double *__restrict__ centre,
+                          const float4 *__restrict__ pofs32,
                           const int4 *__restrict__ link, int32_t *__restrict__ ucnt, T *__restrict__ mom, T *buf0,
                           T *buf1, T (*hs)[3], T (*sbin)[kMaxP + 1], const int *sterm, int4 &s_next) {
     while (true) {
@@ -1075,7 +1077,14 @@ __device__ void climb_m2m(int4 up, int NT, int nval, const double *__restrict__ 
         // the centre offsets are loaded first so that their latency overlaps the moments'
         T h = 0;
         const int hc = threadIdx.x / 3, hax = threadIdx.x - 3 * hc;
-        if (threadIdx.x < 3 * nc) h = (T)(centre[3 * (fc + hc) + hax] - centre[3 * b + hax]);
+        if (threadIdx.x < 3 * nc) {
+            if (sizeof(T) == 4) {   // the FP64 difference rounded to FP32, formed at the tree build
+                const float4 o = pofs32[fc + hc];
+                h = (T)(hax == 0 ? o.x : hax == 1 ? o.y : o.z);
+            } else {
+                h = (T)(centre[3 * (fc + hc) + hax] - centre[3 * b + hax]);
+            }
+        }
         // absent children: zero rows (and zero offsets)
         for (int i = nc * nval + threadIdx.x; i < 8 * nval; i += blockDim.x) buf0[i] = 0;
         // the children are consecutive nodes; eight loads per thread in flight at once
@@ -1104,7 +1113,8 @@ __device__ void climb_m2m(int4 up, int NT, int nval, const double *__restrict__ 
 // computed): one block per leaf, nval values per node.
 template <typename T>
 __global__ void __launch_bounds__(256) climb_kernel(int nleaves, const int32_t *__restrict__ leaf_node,
-                                                    const double *__restrict__ centre, int P, int NT, int nval,
+                                                    const double *__restrict__ centre,
+                                                    const float4 *__restrict__ pofs32, int P, int NT, int nval,
                                                     const int4 *__restrict__ link, int32_t *__restrict__ ucnt,
                                                     T *__restrict__ mom) {
     extern __shared__ __align__(16) unsigned char up_smem[];
@@ -1119,16 +1129,17 @@ __global__ void __launch_bounds__(256) climb_kernel(int nleaves, const int32_t *
     for (int i = threadIdx.x; i < 3 * NT; i += blockDim.x) sterm[i] = c_terms[i];
     for (int i = threadIdx.x; i < (P + 1) * (P + 1); i += blockDim.x) {
         const int n = i / (P + 1), k = i - n * (P + 1);
-        sbin[n][k] = (T)c_binom[n][k];
+        sbin[n][k] = sizeof(T) == 4 ? (T)c_binom32[n][k] : (T)c_binom[n][k];
     }
-    climb_m2m<T>(up, NT, nval, centre, link, ucnt, mom, region, region + 8 * nval, hs, sbin, sterm, s_next);
+    climb_m2m<T>(up, NT, nval, centre, pofs32, link, ucnt, mom, region, region + 8 * nval, hs, sbin, sterm, s_next);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) upward_kernel(int nleaves, const int32_t *__restrict__ leaf_node,
                                                      const int64_t *__restrict__ start,
                                                      const int64_t *__restrict__ count,
-                                                     const double *__restrict__ centre, double ox, double oy,
+                                                     const double *__restrict__ centre,
+                                                     const float4 *__restrict__ pofs32, double ox, double oy,
                                                      double oz, SrcView<T> sv, int P, int NT,
                                                      const int4 *__restrict__ link, int32_t *__restrict__ ucnt,
                                                      T *__restrict__ mom) {
@@ -1142,7 +1153,7 @@ __global__ void __launch_bounds__(256) upward_kernel(int nleaves, const int32_t 
     for (int i = threadIdx.x; i < 3 * NT; i += blockDim.x) sterm[i] = c_terms[i];
     for (int i = threadIdx.x; i < (P + 1) * (P + 1); i += blockDim.x) {
         const int n = i / (P + 1), k = i - n * (P + 1);
-        sbin[n][k] = (T)c_binom[n][k];
+        sbin[n][k] = sizeof(T) == 4 ? (T)c_binom32[n][k] : (T)c_binom[n][k];
     }
     // ---- P2M of this block's leaf (the 4-source quad scheme of p2m_kernel)
     // power rows padded by 4 values: threads owning different terms read
@@ -1238,7 +1249,7 @@ __global__ void __launch_bounds__(256) upward_kernel(int nleaves, const int32_t 
         }
     }
     // ---- climb: the last child to finish computes the parent
-    climb_m2m<T>(up, NT, 2 * NT, centre, link, ucnt, mom, region, region + 8 * 2 * NT, hs, sbin, sterm,
+    climb_m2m<T>(up, NT, 2 * NT, centre, pofs32, link, ucnt, mom, region, region + 8 * 2 * NT, hs, sbin, sterm,
                  s_next);
 }
 
@@ -1365,6 +1376,10 @@ void upload_term_tables() {
         for (int k = 1; k <= n; ++k) bin[n][k] = bin[n][k - 1] * (n - k + 1) / k;
     }
     PB_CUDA_TRY(cudaMemcpyToSymbol(c_binom, bin, sizeof(bin)));
+    float bin32[13][13];
+    for (int n = 0; n <= 12; ++n)
+        for (int k = 0; k <= 12; ++k) bin32[n][k] = (float)bin[n][k];
+    PB_CUDA_TRY(cudaMemcpyToSymbol(c_binom32, bin32, sizeof(bin32)));
 }
 
 void compute_strengths(Tree &Tr, const SurfDev &S, const double *phi, const double *dphi, bool mixed, cudaStream_t s) {
@@ -1393,7 +1408,8 @@ void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s) {
         Tr.mom32.alloc((size_t)Tr.nnodes * 2 * NT);
         SrcView<float> sv{Tr.srcA32.p, Tr.srcB32.p};
         upward_kernel<float><<<Tr.nleaves, 256, upward_smem(NT, 4), s>>>(
-            Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p, Tr.origin[0], Tr.origin[1], Tr.origin[2],
+            Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p, Tr.pofs32.p, Tr.origin[0], Tr.origin[1],
+            Tr.origin[2],
             sv, P, NT, Tr.link.p, Tr.ucnt.p, Tr.mom32.p);
         if (P <= kRadialMaxP) {
             PB_LAUNCH_CHECK();
@@ -1408,7 +1424,8 @@ void upward_pass(Tree &Tr, int P, bool mixed, cudaStream_t s) {
         Tr.mom64.alloc((size_t)Tr.nnodes * 2 * NT);
         SrcView<double> sv{Tr.src64.p};
         upward_kernel<double><<<Tr.nleaves, 256, upward_smem(NT, 8), s>>>(
-            Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p, Tr.origin[0], Tr.origin[1], Tr.origin[2],
+            Tr.nleaves, Tr.leaf_node.p, Tr.start.p, Tr.count.p, Tr.centre.p, Tr.pofs32.p, Tr.origin[0], Tr.origin[1],
+            Tr.origin[2],
             sv, P, NT, Tr.link.p, Tr.ucnt.p, Tr.mom64.p);
     }
     PB_LAUNCH_CHECK();
@@ -1429,10 +1446,10 @@ void m2m_climb(Tree &Tr, int P, bool mixed, void *mom, int nval, cudaStream_t s)
     const size_t shm = climb_smem(nval, mixed);
     if (shm > kClimbMaxShared) fail(PB_EINVAL, "internal: moment sets too large for the one-launch M2M");
     if (mixed)
-        climb_kernel<float><<<Tr.nleaves, 256, shm, s>>>(Tr.nleaves, Tr.leaf_node.p, Tr.centre.p, P, NT, nval,
+        climb_kernel<float><<<Tr.nleaves, 256, shm, s>>>(Tr.nleaves, Tr.leaf_node.p, Tr.centre.p, Tr.pofs32.p, P, NT, nval,
                                                          Tr.link.p, Tr.ucnt.p, (float *)mom);
     else
-        climb_kernel<double><<<Tr.nleaves, 256, shm, s>>>(Tr.nleaves, Tr.leaf_node.p, Tr.centre.p, P, NT, nval,
+        climb_kernel<double><<<Tr.nleaves, 256, shm, s>>>(Tr.nleaves, Tr.leaf_node.p, Tr.centre.p, Tr.pofs32.p, P, NT, nval,
                                                           Tr.link.p, Tr.ucnt.p, (double *)mom);
     PB_LAUNCH_CHECK();
 }
