@@ -73,9 +73,10 @@ typedef struct {
                           panel's 2x2 self block (not in the paper; same solution) [0] */
     int ncrit_adjoint; /* a box of the transposed treecode (pb_gradient, pb_apply_transpose)
                           with >= ncrit_adjoint collocation points is split [ncrit] */
-    int p2p_tile;      /* targets per direct-sum (P2P) work item, 1..32: a warp sums one leaf's
+    int p2p_tile;      /* targets per direct-sum (P2P) work item, 1..64: a warp sums one leaf's
                           sources, staged 32 at a time, for this many targets that list the
-                          leaf (not in the paper; the results do not depend on it) [32] */
+                          leaf, two per lane above 32 (PB_MIXED; PB_FP64 takes at most 32)
+                          (not in the paper; the results do not depend on it) [64] */
     int m2p_variant;   /* 1: the PB_MIXED far field of a Laplace/Yukawa pair (P <= 7) forms its
                           radial-form contraction on the tensor pipe (TF32 instructions, every
                           operand split in two TF32 parts, FP32 accumulation; rounding differs

@@ -30,7 +30,7 @@ from . import pbbem
 # (theta, P) pairs of roughly balanced accuracy, times leaf sizes
 THETA_P = ((0.7, 3), (0.6, 4), (0.5, 5), (0.5, 6), (0.4, 7), (0.4, 8))
 NCRIT = (100, 200, 300, 500)
-P2P_TILES = (32, 16, 8)
+P2P_TILES = (64, 32, 16, 8)
 REFERENCE = dict(theta=0.3, P=10, gmres_tol=1e-7)
 
 
@@ -41,7 +41,7 @@ class Choice:
     ncrit: int
     time_s: float
     rel_error: float
-    p2p_tile: int = 32
+    p2p_tile: int = 64
 
     def params(self) -> dict:
         return dict(theta=self.theta, P=self.P, ncrit=self.ncrit, p2p_tile=self.p2p_tile)
@@ -88,7 +88,7 @@ def tune(ctx, d, target=1e-4, base=None, cands=None, repeats=2, safety=2.0, refe
         e, t = _energy_and_time(ctx, d, dict(base, **c), repeats)
         measured.append((c, t, abs(e - reference) / abs(reference)))
     c, t, err = pick(measured, target, safety)
-    tile = c.get("p2p_tile", 32)
+    tile = c.get("p2p_tile", 64)
     for tl in tiles:
         if tl == tile:
             continue

@@ -84,7 +84,7 @@ Params resolve(const pb_params *p) {
     if (r.P < 0 || r.P > kMaxP) fail(PB_EINVAL, "P must be in 0..12");
     if (r.ncrit < 1) fail(PB_EINVAL, "ncrit must be >= 1");
     if (r.ncrit_adjoint < 0) fail(PB_EINVAL, "ncrit_adjoint must be >= 0");
-    if (r.p2p_tile < 1 || r.p2p_tile > 32) fail(PB_EINVAL, "p2p_tile must be in 1..32");
+    if (r.p2p_tile < 1 || r.p2p_tile > 64) fail(PB_EINVAL, "p2p_tile must be in 1..64");
     if (r.m2p_variant != 0 && r.m2p_variant != 1) fail(PB_EINVAL, "m2p_variant must be 0 or 1");
     if (r.restart < 1 || r.restart > 200) fail(PB_EINVAL, "restart must be in 1..200");
     if (r.max_iter < 1) fail(PB_EINVAL, "max_iter must be >= 1");

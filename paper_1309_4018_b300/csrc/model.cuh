@@ -17,7 +17,7 @@ struct Params {
     int precision = PB_FP64;
     bool precond = true;
     int ncrit_adjoint = 0;   // 0: ncrit
-    int p2p_tile = 32;       // targets per P2P work item
+    int p2p_tile = 64;       // targets per P2P work item (above 32: two per lane)
     int m2p_variant = 0;     // 1: FP32 radial M2P with its contraction on the tensor pipe
 };
 
@@ -88,6 +88,7 @@ struct Pair {
     DevBuf<int32_t> m2p_node, p2p_node, near_panel;
     int64_t n_m2p = 0, n_p2p = 0, n_near = 0, near_excl = 0, self_excl = 0, p2p_pairs = 0;
     DevBuf<unsigned long long> stats;   // list-build counters read back with the list sizes
+    int p2p_tile = 32;                  // targets per P2P item (above 32: two per lane)
     // Entry-major work: for every leaf (P2P) / box (M2P) the (sorted target,
     // list entry) pairs that use it, grouped by leaf / box and packed 32 per
     // work item (one warp); every pair writes one partial sum, and a gather

@@ -1423,9 +1423,11 @@ void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, 
     const int64_t m = G.n;
     ListBuild lb;
     double reach = 0.0, hmax = 0.0;
+    // the FP64 direct sum takes one target per lane: at most 32 per item
+    Pr.p2p_tile = prm.precision == PB_MIXED ? prm.p2p_tile : std::min(prm.p2p_tile, 32);
     far_count(Pr, G, T, &src, prm, lb, s);
     read_far_counts(Pr, lb, m, &reach, &hmax, s);
-    far_fill(Pr, G, T, prm, prm.p2p_tile, lb, s);
+    far_fill(Pr, G, T, prm, Pr.p2p_tile, lb, s);
     near_count(Pr, G, T, src, prm, use_self, hmax, lb, s);
     HostReads rd(s);
     const int64_t *hpi = rd.add(lb.gp.ioff->p + lb.gp.nkeys);
@@ -1439,7 +1441,7 @@ void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, 
     Pr.n_m2p_items = *hmi;
     Pr.n_near = m ? *hnn : 0;
     group_fill(lb.gp, Pr.n_p2p_items, Pr.p2p_items, s);
-    bucket_p2p_items(Pr, T, prm.ncrit, prm.p2p_tile, s);
+    bucket_p2p_items(Pr, T, prm.ncrit, Pr.p2p_tile, s);
     group_fill(lb.gm, Pr.n_m2p_items, Pr.m2p_items, s);
     near_fill(Pr, G, T, src, prm, use_self, reach, *hov != 0, lb, s);
 }
@@ -1448,6 +1450,7 @@ void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &pr
     const int64_t m = G.n;
     ListBuild lb;
     double reach = 0.0, hmax = 0.0;
+    Pr.p2p_tile = p2p_per_item;
     far_count(Pr, G, T, nullptr, prm, lb, s);
     read_far_counts(Pr, lb, m, &reach, &hmax, s);
     far_fill(Pr, G, T, prm, p2p_per_item, lb, s);

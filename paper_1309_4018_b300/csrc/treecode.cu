@@ -360,6 +360,120 @@ __device__ __forceinline__ void p2p32_item(const P2PArgs32 &g, int64_t item, int
     }
 }
 
+// One target's pair contribution with a staged source (a, b): Laplace or
+// Yukawa potential and normal derivative of each kernel, added to p.
+template <int NK, bool Y0, bool Y1, bool MASK>
+__device__ __forceinline__ void p2p32_pair(float tx, float ty, float tz, int me, const float4 &a, const float4 &b,
+                                           float k0, float k1, float l2e0, float l2e1, float p[4]) {
+    const float dx = tx - a.x, dy = ty - a.y, dz = tz - a.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float inv = (MASK && __float_as_int(b.w) == me) ? 0.f : fast_rsqrt(r2);
+    const float sv = a.w * inv;
+    const float rd = fmaf(dx, b.x, fmaf(dy, b.y, dz * b.z));
+    const float kv = rd * (inv * inv * inv);
+    if (!Y0) {
+        p[0] += sv;
+        p[1] += kv;
+    } else {
+        const float rho = r2 * inv;
+        const float ex = fast_ex2(l2e0 * rho);
+        p[0] = fmaf(sv, ex, p[0]);
+        p[1] = fmaf(kv * ex, fmaf(k0, rho, 1.f), p[1]);
+    }
+    if (NK == 2) {
+        if (!Y1) {
+            p[2] += sv;
+            p[3] += kv;
+        } else {
+            const float rho = r2 * inv;
+            const float ex = fast_ex2(l2e1 * rho);
+            p[2] = fmaf(sv, ex, p[2]);
+            p[3] = fmaf(kv * ex, fmaf(k1, rho, 1.f), p[3]);
+        }
+    }
+}
+
+// A work item of up to 64 targets: every lane sums the staged sources for
+// targets `lane` and `lane + 32`, so each staged source is read once for two
+// pairs.  Same arithmetic per pair, same order over the sources, same records
+// as p2p32_item.
+template <int NK, bool Y0, bool Y1, bool MASK>
+__device__ __forceinline__ void p2p32x2_item(const P2PArgs32 &g, int64_t item, int lane, float4 *sA, float4 *sB) {
+    const int4 it = g.items[item];
+    float tx[2] = {0.f, 0.f}, ty[2] = {0.f, 0.f}, tz[2] = {0.f, 0.f};
+    int me[2] = {-1, -1};
+    bool valid[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        valid[h] = lane + 32 * h < it.z;
+        if (valid[h]) {
+            const int t = g.inv[(int64_t)it.y + lane + 32 * h];
+            const float4 x = g.x32[t];
+            tx[h] = x.x;
+            ty[h] = x.y;
+            tz[h] = x.z;
+            if (MASK && g.use_self) me[h] = g.selfp[t];
+        }
+    }
+    const bool two = it.z > 32;   // warp-uniform
+    const float k0 = g.ks.kap[0], k1 = g.ks.kap[1];
+    const float l2e0 = -k0 * 1.4426950408889634f, l2e1 = -k1 * 1.4426950408889634f;
+    float hi[2][2 * NK], lo[2][2 * NK];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int a = 0; a < 2 * NK; ++a) { hi[h][a] = 0.f; lo[h][a] = 0.f; }
+    const int node = g.leaf_node[it.x];
+    const int64_t s0 = g.start[node];
+    const int cnt = (int)g.count[node];
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+        const int m = min(32, cnt - c0);
+        if (lane < m) {
+            sA[lane] = g.A[s0 + c0 + lane];
+            sB[lane] = g.B[s0 + c0 + lane];
+        }
+        __syncwarp();
+        float p0[4] = {0.f, 0.f, 0.f, 0.f}, p1[4] = {0.f, 0.f, 0.f, 0.f};
+        if (two) {
+#pragma unroll 4
+            for (int j = 0; j < m; ++j) {
+                const float4 a = sA[j];
+                const float4 b = sB[j];
+                p2p32_pair<NK, Y0, Y1, MASK>(tx[0], ty[0], tz[0], me[0], a, b, k0, k1, l2e0, l2e1, p0);
+                p2p32_pair<NK, Y0, Y1, MASK>(tx[1], ty[1], tz[1], me[1], a, b, k0, k1, l2e0, l2e1, p1);
+            }
+        } else if (valid[0]) {
+#pragma unroll 4
+            for (int j = 0; j < m; ++j)
+                p2p32_pair<NK, Y0, Y1, MASK>(tx[0], ty[0], tz[0], me[0], sA[j], sB[j], k0, k1, l2e0, l2e1, p0);
+        }
+#pragma unroll
+        for (int a = 0; a < 2 * NK; ++a) {
+            comp_add(hi[0][a], lo[0][a], p0[a]);
+            comp_add(hi[1][a], lo[1][a], p1[a]);
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (valid[h]) {
+            float2 *rec =
+                reinterpret_cast<float2 *>(g.part + (int64_t)2 * NK * g.sent[(int64_t)it.y + lane + 32 * h]);
+#pragma unroll
+            for (int a = 0; a < NK; ++a)
+                rec[a] = make_float2(hi[h][2 * a] + lo[h][2 * a], hi[h][2 * a + 1] + lo[h][2 * a + 1]);
+        }
+}
+
+template <int NK, bool Y0, bool Y1, bool MASK>
+__global__ void __launch_bounds__(128) p2p32x2_kernel(int64_t nitems, P2PArgs32 g) {
+    __shared__ float4 sA[4][32], sB[4][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * 4 + warp;
+    if (item >= nitems) return;
+    p2p32x2_item<NK, Y0, Y1, MASK>(g, item, lane, sA[warp], sB[warp]);
+}
+
 template <int NK, bool Y0, bool Y1, bool MASK>
 __global__ void __launch_bounds__(128) p2p32_kernel(int64_t nitems, P2PArgs32 g) {
     __shared__ float4 sA[4][32], sB[4][32];
@@ -1281,6 +1395,7 @@ struct BatchPair {
     int64_t n_m2p_items, ntg;
     int problem;          // index of the problem's active flag
     unsigned need;        // P2P and M2P entries of the pair
+    int p2p_two;          // P2P items of up to 64 targets, two per lane
 };
 
 // The pair descriptors travel in the launch's parameter space (up to
@@ -1335,7 +1450,12 @@ __global__ void __launch_bounds__(128, 6) batch_operator_kernel(const __grid_con
             continue;
         }
         if (e.y == 0) {
-            for (int u = 0; u < e.w; ++u) p2p32_item<2, false, true, false>(bp.p2p, (int64_t)e.z + u, lane, ws, ws + 32);
+            if (bp.p2p_two)
+                for (int u = 0; u < e.w; ++u)
+                    p2p32x2_item<2, false, true, false>(bp.p2p, (int64_t)e.z + u, lane, ws, ws + 32);
+            else
+                for (int u = 0; u < e.w; ++u)
+                    p2p32_item<2, false, true, false>(bp.p2p, (int64_t)e.z + u, lane, ws, ws + 32);
         } else {
             for (int u = 0; u < e.w; ++u) m2p_ly32x_task<P, 2>(bp.m2p, bp.n_m2p_items, (int64_t)e.z + 2 * u, lane, ws);
         }
@@ -1500,7 +1620,11 @@ void launch_p2p(const Pair &Pr, const Targets &G, const Tree &Tr, bool use_self,
     if (mixed) {
         const bool mask = use_self && !Pr.p2p_self_in;
         const P2PArgs32 ga = p2p_args32(Pr, G, Tr, use_self);
-#define PB_P2P32M(NK, A, B, M) p2p32_kernel<NK, A, B, M><<<grid, 128, 0, s>>>(ni, ga)
+#define PB_P2P32M(NK, A, B, M)                                                        \
+    do {                                                                              \
+        if (Pr.p2p_tile > 32) p2p32x2_kernel<NK, A, B, M><<<grid, 128, 0, s>>>(ni, ga); \
+        else p2p32_kernel<NK, A, B, M><<<grid, 128, 0, s>>>(ni, ga);                    \
+    } while (0)
 #define PB_P2P32(NK, A, B) do { if (mask) PB_P2P32M(NK, A, B, true); else PB_P2P32M(NK, A, B, false); } while (0)
         if (nk == 1) { if (y0) PB_P2P32(1, true, false); else PB_P2P32(1, false, false); }
         else if (!y0 && y1) PB_P2P32(2, false, true);
@@ -1708,6 +1832,7 @@ void batch_plan_build(BatchPlan &bp, const std::vector<BatchPairRef> &prs, int n
                 fail(PB_EINVAL, "internal: batched operator pair too large");
             BatchPair &b = args.p[k];
             b.p2p = p2p_args32(Pr, *r.G, *r.T, r.use_self);
+            b.p2p_two = Pr.p2p_tile > 32 ? 1 : 0;
             b.m2p = m2p_args32(Pr, *r.T);
             b.ga = gather_args32(Pr, *r.G, r.use_self, r.dphi, r.T->phf.p);
             b.n_m2p_items = Pr.n_m2p_items;

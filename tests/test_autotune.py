@@ -16,10 +16,10 @@ def test_size_classes_and_schedule_lookup():
     assert AT.size_class(8192) == 13 and AT.size_class(16383) == 13 and AT.size_class(16384) == 14
     s = AT.Schedule({13: AT.Choice(0.6, 4, 200, 0.0, 0.0), 15: AT.Choice(0.5, 6, 300, 0.0, 0.0)})
     mk = lambda n: {"surfaces": [{"tris": np.zeros((n, 3), np.int32)}]}
-    assert s.params_for(mk(10000)) == dict(theta=0.6, P=4, ncrit=200, p2p_tile=32)
-    assert s.params_for(mk(40000)) == dict(theta=0.5, P=6, ncrit=300, p2p_tile=32)
+    assert s.params_for(mk(10000)) == dict(theta=0.6, P=4, ncrit=200, p2p_tile=64)
+    assert s.params_for(mk(40000)) == dict(theta=0.5, P=6, ncrit=300, p2p_tile=64)
     assert s.params_for(mk(20000))["ncrit"] in (200, 300)     # nearest tuned class
-    assert s.params_for(mk(300000)) == dict(theta=0.5, P=6, ncrit=300, p2p_tile=32)
+    assert s.params_for(mk(300000)) == dict(theta=0.5, P=6, ncrit=300, p2p_tile=64)
 
 
 @pytest.mark.gpu
@@ -47,5 +47,5 @@ def test_p2p_tile_does_not_change_the_result():
     from gpu_util import problem
     from synth.configs import fleet_ligand
     d = fleet_ligand(1, 500)
-    e = [problem(d, precision="mixed", gmres_tol=1e-5, p2p_tile=t).solve().dG_solv for t in (32, 16, 8, 5)]
+    e = [problem(d, precision="mixed", gmres_tol=1e-5, p2p_tile=t).solve().dG_solv for t in (64, 48, 32, 16, 8, 5)]
     assert e[1:] == e[:-1]
