@@ -89,14 +89,39 @@ __global__ void axpby_kernel(double a, const double *__restrict__ x, double b, c
 }
 
 // y = H[0..k)^-1 g (back substitution) into st->y.
-__global__ void back_solve_kernel(GmresState *st, int k) {
-    if (threadIdx.x != 0) return;
+// y = R^-1 g for the k x k upper triangle of H (columns of stride m + 1).  Up
+// to kBackStage columns the block stages the triangle in shared memory first
+// and one thread runs the substitution there; longer cycles read it from
+// global memory.  Either way the same sums in the same order.
+constexpr int kBackThreads = 256;
+constexpr int kBackStage = 64;
+
+__global__ void __launch_bounds__(kBackThreads) back_solve_kernel(GmresState *st, int k) {
+    __shared__ double sH[kBackStage * kBackStage];
+    __shared__ double sy[kBackStage];
     const int m = st->m;
-    for (int i = k - 1; i >= 0; --i) {
-        double s = st->g[i];
-        for (int c = i + 1; c < k; ++c) s -= st->H[(int64_t)c * (m + 1) + i] * st->y[c];
-        st->y[i] = s / st->H[(int64_t)i * (m + 1) + i];
+    const double *H = st->H, *g = st->g;
+    if (k > kBackStage) {
+        if (threadIdx.x != 0) return;
+        for (int i = k - 1; i >= 0; --i) {
+            double s = g[i];
+            for (int c = i + 1; c < k; ++c) s -= H[(int64_t)c * (m + 1) + i] * st->y[c];
+            st->y[i] = s / H[(int64_t)i * (m + 1) + i];
+        }
+        return;
     }
+    for (int e = threadIdx.x; e < k * k; e += kBackThreads) {
+        const int c = e / k, i = e - c * k;
+        sH[e] = H[(int64_t)c * (m + 1) + i];
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int c = i + 1; c < k; ++c) s -= sH[c * k + i] * sy[c];
+        sy[i] = s / sH[i * k + i];
+    }
+    for (int i = 0; i < k; ++i) st->y[i] = sy[i];
 }
 
 // x += sum_c V[c] y[c]
@@ -627,7 +652,7 @@ void Gmres::read_cycle_async(cudaStream_t s) {
 
 void Gmres::update_solution(int k, double *x, cudaStream_t s) {
     if (k <= 0) return;
-    back_solve_kernel<<<1, 1, 0, s>>>(st.p, k);
+    back_solve_kernel<<<1, kBackThreads, 0, s>>>(st.p, k);
     PB_LAUNCH_CHECK();
     update_x_kernel<<<div_up(n, 256), 256, 0, s>>>(V.p, ld, k, st.p, x, n);
     PB_LAUNCH_CHECK();
@@ -648,7 +673,7 @@ void block_jacobi_apply(int64_t n, const double *minv, const double *u_in, const
 }
 
 void basis_combination(const Gmres &G, int k, double *out, cudaStream_t s) {
-    back_solve_kernel<<<1, 1, 0, s>>>(G.st.p, k);
+    back_solve_kernel<<<1, kBackThreads, 0, s>>>(G.st.p, k);
     PB_LAUNCH_CHECK();
     combination_kernel<<<div_up(G.n, 256), 256, 0, s>>>(G.V.p, G.ld, k, G.st.p, out, G.n);
     PB_LAUNCH_CHECK();

@@ -61,13 +61,19 @@ __global__ void bbox_blocks_kernel(const double *__restrict__ p, int64_t n, doub
 //   not finite), corner = centre - side / 2,
 // each operation rounded on its own (no fused multiply-add).
 __global__ void cube_final_kernel(const double *__restrict__ part, int nb, double *__restrict__ cube) {
-    if (threadIdx.x != 0) return;
+    // one warp: lanes take the block boxes in turn, then a butterfly (min and max are exact)
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = 0; b < nb; ++b)
+    for (int b = threadIdx.x; b < nb; b += 32)
         for (int a = 0; a < 3; ++a) {
             lo[a] = fmin(lo[a], part[6 * b + a]);
             hi[a] = fmax(hi[a], part[6 * b + 3 + a]);
         }
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    if (threadIdx.x != 0) return;
     double centre[3], ext[3];
     for (int a = 0; a < 3; ++a) {
         centre[a] = __dmul_rn(__dadd_rn(lo[a], hi[a]), 0.5);
@@ -1013,7 +1019,7 @@ __global__ void p2p_pairs_kernel(int64_t ntg, const int64_t *__restrict__ ptr, c
 }
 
 void root_cube_from(const double *d_points, int64_t n, cudaStream_t s, double *cube) {
-    const int nb = (int)std::min<int64_t>(256, std::max<int64_t>(1, (n + 4095) / 4096));
+    const int nb = (int)std::min<int64_t>(592, std::max<int64_t>(1, (n + 1023) / 1024));
     TmpBuf<double> part(6 * nb, s);
     bbox_blocks_kernel<<<nb, 256, 0, s>>>(d_points, n, part.p);
     PB_LAUNCH_CHECK();
