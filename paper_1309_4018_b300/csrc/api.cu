@@ -32,7 +32,10 @@ pb_problem::~pb_problem() {
     if (ev1) cudaEventDestroy(ev1);
     if (evf) cudaEventDestroy(evf);
     if (evj) cudaEventDestroy(evj);
+    if (ev2a) cudaEventDestroy(ev2a);
+    if (ev2b) cudaEventDestroy(ev2b);
     if (side) cudaStreamDestroy(side);
+    if (lists2) cudaStreamDestroy(lists2);
 }
 
 namespace {
@@ -170,13 +173,19 @@ void setup_problem(pb_problem *pb) {
         PB_CUDA_TRY(cudaMemcpyAsync(S.verts.p, si.v.p, 3 * S.nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
         PB_CUDA_TRY(cudaMemcpyAsync(S.tris.p, si.t.p, 3 * S.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
         surface_geometry(S, prm.K, s);
-        build_tree(pb->T[t], S, prm.K, prm.ncrit, s);
     }
     pb->N = pb->off[ns];
     pb->G.resize(ns + 1);
-    for (int t = 0; t < ns; ++t) build_targets(pb->G[t], pb->S[t].cen.p, pb->S[t].n, t, s);
+    // the target sorts run on the second list stream beside the trees
+    cudaStream_t s2 = pb->lists2 ? pb->lists2 : s;
+    if (s2 != s) {
+        PB_CUDA_TRY(cudaEventRecord(pb->ev2a, s));
+        PB_CUDA_TRY(cudaStreamWaitEvent(s2, pb->ev2a, 0));
+    }
+    for (int t = 0; t < ns; ++t) build_targets(pb->G[t], pb->S[t].cen.p, pb->S[t].n, t, s2);
     const int64_t nc = pb->nc;
-    build_targets(pb->G[ns], pb->cxyz_d.p, nc, -1, s);
+    build_targets(pb->G[ns], pb->cxyz_d.p, nc, -1, s2);
+    for (int t = 0; t < ns; ++t) build_tree(pb->T[t], pb->S[t], prm.K, prm.ncrit, s);
     // the charges must lie in their region: inside every surface that has it as
     // inner region, outside every surface that has it as outer region
     int n_wind = 0;
@@ -248,48 +257,27 @@ void setup_problem(pb_problem *pb) {
         if (pb->reac.size() > 8) fail(PB_EINVAL, "the charged region is bounded by more than 8 surfaces");
     }
     pb->need_far.assign(ns, false);
-    auto prepare = [&](Pair &P, bool charges) {
-        const Targets &G = pb->G[P.tgt];
-        const Tree &Tr = pb->T[P.tree];
+    const bool mixed = prm.precision == PB_MIXED;
+    // the side stream starts on what needs only the geometry and trees: the
+    // self integrals and the right-hand side, beside the list builds
+    if (fs != s) {
+        PB_CUDA_TRY(cudaEventRecord(pb->evf, s));
+        PB_CUDA_TRY(cudaStreamWaitEvent(fs, pb->evf, 0));
+    }
+    auto self_terms = [&](Pair &P) {
         const SurfDev &src = pb->S[P.tree];
-        const bool use_self = !charges && P.tgt == P.tree;
-        build_lists(P, G, Tr, src, prm, use_self, s);
-        if (P.n_m2p > 0) pb->need_far[P.tree] = true;
         const size_t nk = P.kappas.size();
         P.VK.resize(nk); P.dV.resize(nk); P.dK.resize(nk); P.selfV.resize(nk); P.selfV32.resize(nk);
         // the FP32 direct sum keeps a panel's own points when none sits at its centroid (K = 3);
         // the self value then carries the correction
-        P.p2p_self_in = prm.precision == PB_MIXED && use_self && prm.K == 3;
-        if (prm.precision == PB_MIXED) P.p2p_part32.alloc(2 * nk * std::max<int64_t>(1, P.n_p2p));
-        else P.p2p_part.alloc(2 * nk * std::max<int64_t>(1, P.n_p2p));
-        if (P.n_m2p > 0) {
-            if (prm.precision == PB_MIXED) P.m2p_part32.alloc(2 * nk * P.n_m2p);
-            else P.m2p_part64.alloc(2 * nk * P.n_m2p);
-        }
-        const bool mixed = prm.precision == PB_MIXED;
-        if (mixed) {
-            P.dV32.alloc(std::max<int64_t>(1, (int64_t)nk * P.n_near));
-            P.dK32.alloc(std::max<int64_t>(1, (int64_t)nk * P.n_near));
-        }
-        if (fs != s) {
-            PB_CUDA_TRY(cudaEventRecord(pb->evf, s));
-            PB_CUDA_TRY(cudaStreamWaitEvent(fs, pb->evf, 0));
-        }
-        if (mixed) near_values32(P, G, src, prm.K, prm.K_fine, P.dV32.p, P.dK32.p, fs);
+        P.p2p_self_in = mixed && P.tgt == P.tree && prm.K == 3;
+        if (P.tgt != P.tree) return;
         for (size_t k = 0; k < nk; ++k) {
-            P.VK[k].alloc(2 * std::max<int64_t>(1, G.n));
-            if (!mixed) {
-                P.dV[k].alloc(std::max<int64_t>(1, P.n_near));
-                P.dK[k].alloc(std::max<int64_t>(1, P.n_near));
-                near_values(P, G, src, prm.K, prm.K_fine, P.kappas[k], P.dV[k].p, P.dK[k].p, fs);
-            }
-            if (use_self) {
-                P.selfV[k].alloc(src.n);
-                if (nk == 2 && k == 1) {
-                    self_integrals2(src, prm.N_k, P.kappas[0], P.kappas[1], P.selfV[0].p, P.selfV[1].p, fs);
-                } else if (nk == 1) {
-                    self_integrals(src, prm.N_k, P.kappas[k], P.selfV[k].p, fs);
-                }
+            P.selfV[k].alloc(src.n);
+            if (nk == 2 && k == 1) {
+                self_integrals2(src, prm.N_k, P.kappas[0], P.kappas[1], P.selfV[0].p, P.selfV[1].p, fs);
+            } else if (nk == 1) {
+                self_integrals(src, prm.N_k, P.kappas[k], P.selfV[k].p, fs);
             }
         }
         if (P.p2p_self_in)
@@ -298,11 +286,11 @@ void setup_problem(pb_problem *pb) {
                 self_minus_kpoint(src, prm.K, P.kappas[k], P.selfV[k].p, P.selfV32[k].p, fs);
             }
     };
-    for (auto &P : pb->pairs) prepare(P, false);
-    for (auto &P : pb->cpairs) prepare(P, true);
-    if (prm.precision == PB_MIXED) {
-        for (auto &P : pb->pairs) targets_to_float(P, pb->G[P.tgt], pb->T[P.tree], s);
-        for (auto &P : pb->cpairs) targets_to_float(P, pb->G[P.tgt], pb->T[P.tree], s);
+    for (auto &P : pb->pairs) self_terms(P);
+    for (auto &P : pb->cpairs) {
+        const size_t nk = P.kappas.size();
+        P.VK.resize(nk); P.dV.resize(nk); P.dK.resize(nk); P.selfV.resize(nk); P.selfV32.resize(nk);
+        P.p2p_self_in = false;
     }
     // right-hand side
     pb->b.alloc(2 * pb->N);
@@ -314,9 +302,65 @@ void setup_problem(pb_problem *pb) {
             for (int side = 0; side < 2; ++side)
                 if (Rs[side] == pb->cregion)
                     rhs_rows(pb->S[sf], nc, pb->cq_d.p, pb->cxyz_d.p, Rg.kappa, Rg.eps,
-                             pb->b.p + 2 * pb->off[sf] + side * pb->S[sf].n,
-                             prm.precision == PB_MIXED ? pb->T[sf].origin : nullptr, fs);
+                             pb->b.p + 2 * pb->off[sf] + side * pb->S[sf].n, mixed ? pb->T[sf].origin : nullptr, fs);
         }
+    }
+    // the list builds, pairs alternating between the two list streams (both see the trees and the targets)
+    if (s2 != s) {
+        PB_CUDA_TRY(cudaEventRecord(pb->ev2a, s));
+        PB_CUDA_TRY(cudaStreamWaitEvent(s2, pb->ev2a, 0));
+        PB_CUDA_TRY(cudaEventRecord(pb->ev2b, s2));
+        PB_CUDA_TRY(cudaStreamWaitEvent(s, pb->ev2b, 0));
+    }
+    {
+        std::vector<ListJob> jobs;
+        int k = 0;
+        for (auto &P : pb->pairs)
+            jobs.push_back(ListJob{&P, &pb->G[P.tgt], &pb->T[P.tree], &pb->S[P.tree], P.tgt == P.tree,
+                                   (k++ % 2) ? s2 : s});
+        for (auto &P : pb->cpairs)
+            jobs.push_back(ListJob{&P, &pb->G[P.tgt], &pb->T[P.tree], &pb->S[P.tree], false, (k++ % 2) ? s2 : s});
+        build_lists_multi(jobs, prm);
+    }
+    if (s2 != s) {
+        PB_CUDA_TRY(cudaEventRecord(pb->ev2b, s2));
+        PB_CUDA_TRY(cudaStreamWaitEvent(s, pb->ev2b, 0));
+    }
+    // near-field values on the side stream once the lists exist
+    if (fs != s) {
+        PB_CUDA_TRY(cudaEventRecord(pb->evf, s));
+        PB_CUDA_TRY(cudaStreamWaitEvent(fs, pb->evf, 0));
+    }
+    auto near_field = [&](Pair &P) {
+        const Targets &G = pb->G[P.tgt];
+        const SurfDev &src = pb->S[P.tree];
+        if (P.n_m2p > 0) pb->need_far[P.tree] = true;
+        const size_t nk = P.kappas.size();
+        if (mixed) P.p2p_part32.alloc(2 * nk * std::max<int64_t>(1, P.n_p2p));
+        else P.p2p_part.alloc(2 * nk * std::max<int64_t>(1, P.n_p2p));
+        if (P.n_m2p > 0) {
+            if (mixed) P.m2p_part32.alloc(2 * nk * P.n_m2p);
+            else P.m2p_part64.alloc(2 * nk * P.n_m2p);
+        }
+        if (mixed) {
+            P.dV32.alloc(std::max<int64_t>(1, (int64_t)nk * P.n_near));
+            P.dK32.alloc(std::max<int64_t>(1, (int64_t)nk * P.n_near));
+            near_values32(P, G, src, prm.K, prm.K_fine, P.dV32.p, P.dK32.p, fs);
+        }
+        for (size_t k = 0; k < nk; ++k) {
+            P.VK[k].alloc(2 * std::max<int64_t>(1, G.n));
+            if (!mixed) {
+                P.dV[k].alloc(std::max<int64_t>(1, P.n_near));
+                P.dK[k].alloc(std::max<int64_t>(1, P.n_near));
+                near_values(P, G, src, prm.K, prm.K_fine, P.kappas[k], P.dV[k].p, P.dK[k].p, fs);
+            }
+        }
+    };
+    for (auto &P : pb->pairs) near_field(P);
+    for (auto &P : pb->cpairs) near_field(P);
+    if (mixed) {
+        for (auto &P : pb->pairs) targets_to_float(P, pb->G[P.tgt], pb->T[P.tree], s);
+        for (auto &P : pb->cpairs) targets_to_float(P, pb->G[P.tgt], pb->T[P.tree], s);
     }
     if (fs != s) {
         PB_CUDA_TRY(cudaEventRecord(pb->evj, fs));
@@ -1006,6 +1050,9 @@ int pb_problem_create(pb_ctx *c, pb_problem **out) {
         PB_CUDA_TRY(cudaStreamCreateWithFlags(&pb->side, cudaStreamNonBlocking));
         PB_CUDA_TRY(cudaEventCreateWithFlags(&pb->evf, cudaEventDisableTiming));
         PB_CUDA_TRY(cudaEventCreateWithFlags(&pb->evj, cudaEventDisableTiming));
+        PB_CUDA_TRY(cudaStreamCreateWithFlags(&pb->lists2, cudaStreamNonBlocking));
+        PB_CUDA_TRY(cudaEventCreateWithFlags(&pb->ev2a, cudaEventDisableTiming));
+        PB_CUDA_TRY(cudaEventCreateWithFlags(&pb->ev2b, cudaEventDisableTiming));
     });
     if (rc != PB_OK) return rc;
     *out = pb.release();

@@ -152,16 +152,35 @@ class HostReads {
     HostReads &operator=(const HostReads &) = delete;
     template <typename T>
     const T *add(const T *d, size_t n = 1) {
+        return add_on(s_, d, n);
+    }
+    // The copy queued on stream `on` instead (wait() then synchronises it too).
+    template <typename T>
+    const T *add_on(cudaStream_t on, const T *d, size_t n = 1) {
         void *h = take(n * sizeof(T));
-        PB_CUDA_TRY(cudaMemcpyAsync(h, d, n * sizeof(T), cudaMemcpyDeviceToHost, s_));
+        PB_CUDA_TRY(cudaMemcpyAsync(h, d, n * sizeof(T), cudaMemcpyDeviceToHost, on));
+        if (on != s_) {
+            bool seen = false;
+            for (int i = 0; i < nother_; ++i) seen = seen || other_[i] == on;
+            if (!seen) {
+                if (nother_ == kOther) fail(PB_EINVAL, "internal: too many streams in one host read");
+                other_[nother_++] = on;
+            }
+        }
         return static_cast<const T *>(h);
     }
-    void wait() { PB_CUDA_TRY(cudaStreamSynchronize(s_)); }
+    void wait() {
+        PB_CUDA_TRY(cudaStreamSynchronize(s_));
+        for (int i = 0; i < nother_; ++i) PB_CUDA_TRY(cudaStreamSynchronize(other_[i]));
+    }
 
   private:
+    static constexpr int kOther = 4;
     void *take(size_t bytes);
     cudaStream_t s_;
     size_t begin_, end_;
+    cudaStream_t other_[kOther] = {};
+    int nother_ = 0;
 };
 // One value read from the device (a stream synchronisation).
 template <typename T>

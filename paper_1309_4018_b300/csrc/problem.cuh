@@ -59,6 +59,8 @@ struct pb_problem {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaStream_t side = nullptr;              // the operator's direct sums run here beside the upward pass
     cudaEvent_t evf = nullptr, evj = nullptr; // fork and join of the side stream
+    cudaStream_t lists2 = nullptr;            // setup: target sorts and every other pair's list build
+    cudaEvent_t ev2a = nullptr, ev2b = nullptr; // setup: joins between the context stream and lists2
     cudaGraphExec_t mv_exec = nullptr;        // captured operator application z1 -> gm.w
     long long mv_kernels = 0;                 // kernels in that graph
     cudaGraphExec_t adj_exec = nullptr;       // captured transposed operator z1 -> gm.w (gradient)

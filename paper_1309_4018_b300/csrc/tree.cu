@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <optional>
 
 #include <cooperative_groups.h>
@@ -1426,30 +1427,84 @@ void read_far_counts(Pair &Pr, ListBuild &lb, int64_t m, double *reach, double *
 
 void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
                  cudaStream_t s) {
-    const int64_t m = G.n;
-    ListBuild lb;
-    double reach = 0.0, hmax = 0.0;
-    // the FP64 direct sum takes one target per lane: at most 32 per item
-    Pr.p2p_tile = prm.precision == PB_MIXED ? prm.p2p_tile : std::min(prm.p2p_tile, 32);
-    far_count(Pr, G, T, &src, prm, lb, s);
-    read_far_counts(Pr, lb, m, &reach, &hmax, s);
-    far_fill(Pr, G, T, prm, Pr.p2p_tile, lb, s);
-    near_count(Pr, G, T, src, prm, use_self, hmax, lb, s);
-    HostReads rd(s);
-    const int64_t *hpi = rd.add(lb.gp.ioff->p + lb.gp.nkeys);
-    const int64_t *hmi = rd.add(lb.gm.ioff->p + lb.gm.nkeys);
-    const int32_t *hov = rd.add(lb.ovf->p);
-    const int64_t *hnn = rd.add(Pr.near_ptr.p + m);
-    const unsigned long long *hst = rd.add(Pr.stats.p, 4);
-    rd.wait();
-    apply_list_stats(Pr, hst);
-    Pr.n_p2p_items = *hpi;
-    Pr.n_m2p_items = *hmi;
-    Pr.n_near = m ? *hnn : 0;
-    group_fill(lb.gp, Pr.n_p2p_items, Pr.p2p_items, s);
-    bucket_p2p_items(Pr, T, prm.ncrit, Pr.p2p_tile, s);
-    group_fill(lb.gm, Pr.n_m2p_items, Pr.m2p_items, s);
-    near_fill(Pr, G, T, src, prm, use_self, reach, *hov != 0, lb, s);
+    std::vector<ListJob> jobs{ListJob{&Pr, &G, &T, &src, use_self, s}};
+    build_lists_multi(jobs, prm);
+}
+
+// Every pair's list build in three phases on its own stream; the host reads
+// of a phase (list lengths and near-field reach; item counts, near-list
+// length, overflow flag and counters) are one wait over all the streams.
+void build_lists_multi(const std::vector<ListJob> &jobs, const Params &prm) {
+    const size_t nj = jobs.size();
+    if (!nj) return;
+    std::vector<std::unique_ptr<ListBuild>> lbs;
+    for (size_t j = 0; j < nj; ++j) lbs.emplace_back(new ListBuild());
+    std::vector<double> reach(nj, 0.0), hmax(nj, 0.0);
+    for (size_t j = 0; j < nj; ++j) {
+        const ListJob &jb = jobs[j];
+        // the FP64 direct sum takes one target per lane: at most 32 per item
+        jb.P->p2p_tile = prm.precision == PB_MIXED ? prm.p2p_tile : std::min(prm.p2p_tile, 32);
+        far_count(*jb.P, *jb.G, *jb.T, jb.src, prm, *lbs[j], jb.s);
+    }
+    {
+        HostReads rd(jobs[0].s);
+        std::vector<const int64_t *> hm(nj), hp(nj);
+        std::vector<const unsigned long long *> hr(nj);
+        for (size_t j = 0; j < nj; ++j) {
+            const ListJob &jb = jobs[j];
+            hm[j] = rd.add_on(jb.s, jb.P->m2p_ptr.p + jb.G->n);
+            hp[j] = rd.add_on(jb.s, jb.P->p2p_ptr.p + jb.G->n);
+            hr[j] = rd.add_on(jb.s, lbs[j]->reach->p, 2);
+        }
+        rd.wait();
+        for (size_t j = 0; j < nj; ++j) {
+            jobs[j].P->n_m2p = *hm[j];
+            jobs[j].P->n_p2p = *hp[j];
+            std::memcpy(&reach[j], &hr[j][0], sizeof(double));
+            std::memcpy(&hmax[j], &hr[j][1], sizeof(double));
+        }
+    }
+    for (size_t j = 0; j < nj; ++j) {
+        const ListJob &jb = jobs[j];
+        far_fill(*jb.P, *jb.G, *jb.T, prm, jb.P->p2p_tile, *lbs[j], jb.s);
+        near_count(*jb.P, *jb.G, *jb.T, *jb.src, prm, jb.use_self, hmax[j], *lbs[j], jb.s);
+    }
+    std::vector<int32_t> ovf(nj, 0);
+    {
+        HostReads rd(jobs[0].s);
+        std::vector<const int64_t *> hpi(nj), hmi(nj), hnn(nj);
+        std::vector<const int32_t *> hov(nj);
+        std::vector<const unsigned long long *> hst(nj);
+        for (size_t j = 0; j < nj; ++j) {
+            const ListJob &jb = jobs[j];
+            ListBuild &lb = *lbs[j];
+            hpi[j] = rd.add_on(jb.s, lb.gp.ioff->p + lb.gp.nkeys);
+            hmi[j] = rd.add_on(jb.s, lb.gm.ioff->p + lb.gm.nkeys);
+            hov[j] = rd.add_on(jb.s, lb.ovf->p);
+            hnn[j] = rd.add_on(jb.s, jb.P->near_ptr.p + jb.G->n);
+            hst[j] = rd.add_on(jb.s, jb.P->stats.p, 4);
+        }
+        rd.wait();
+        for (size_t j = 0; j < nj; ++j) {
+            Pair &Pr = *jobs[j].P;
+            apply_list_stats(Pr, hst[j]);
+            Pr.n_p2p_items = *hpi[j];
+            Pr.n_m2p_items = *hmi[j];
+            Pr.n_near = jobs[j].G->n ? *hnn[j] : 0;
+            ovf[j] = *hov[j];
+        }
+    }
+    for (size_t j = 0; j < nj; ++j) {
+        const ListJob &jb = jobs[j];
+        Pair &Pr = *jb.P;
+        ListBuild &lb = *lbs[j];
+        group_fill(lb.gp, Pr.n_p2p_items, Pr.p2p_items, jb.s);
+        bucket_p2p_items(Pr, *jb.T, prm.ncrit, Pr.p2p_tile, jb.s);
+        group_fill(lb.gm, Pr.n_m2p_items, Pr.m2p_items, jb.s);
+        near_fill(Pr, *jb.G, *jb.T, *jb.src, prm, jb.use_self, reach[j], ovf[j] != 0, lb, jb.s);
+    }
+    // the temporaries go back on their own streams, in reverse order of creation
+    while (!lbs.empty()) lbs.pop_back();
 }
 
 void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &prm, cudaStream_t s, int p2p_per_item) {

@@ -1,6 +1,8 @@
 // Setup-phase entry points of the octree and interaction-list code (tree.cu).
 #pragma once
 
+#include <vector>
+
 #include "model.cuh"
 
 namespace pb {
@@ -22,6 +24,18 @@ void build_targets(Targets &G, const double *d_x, int64_t n, int surface, cudaSt
 // the panels of the tree's own surface, so each skips its own panel.
 void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
                  cudaStream_t s);
+// The lists of several pairs, each on its own stream (job.s), their host reads
+// gathered into two waits.  Inputs (tree, targets) must be ready on every
+// job's stream.
+struct ListJob {
+    Pair *P;
+    const Targets *G;
+    const Tree *T;
+    const SurfDev *src;
+    bool use_self;
+    cudaStream_t s;
+};
+void build_lists_multi(const std::vector<ListJob> &jobs, const Params &prm);
 // The traversal (M2P / P2P lists, direct-sum pair count, entry-major items) alone;
 // P2P items hold up to p2p_per_item (32 or 64) (target, leaf) pairs, M2P items 32.
 void build_far_lists(Pair &Pr, const Targets &G, const Tree &T, const Params &prm, cudaStream_t s,
