@@ -315,11 +315,16 @@ void setup_problem(pb_problem *pb) {
     {
         std::vector<ListJob> jobs;
         int k = 0;
-        for (auto &P : pb->pairs)
-            jobs.push_back(ListJob{&P, &pb->G[P.tgt], &pb->T[P.tree], &pb->S[P.tree], P.tgt == P.tree,
-                                   (k++ % 2) ? s2 : s});
-        for (auto &P : pb->cpairs)
-            jobs.push_back(ListJob{&P, &pb->G[P.tgt], &pb->T[P.tree], &pb->S[P.tree], false, (k++ % 2) ? s2 : s});
+        for (auto &P : pb->pairs) {
+            const bool odd = k++ % 2;
+            jobs.push_back(ListJob{&P, &pb->G[P.tgt], &pb->T[P.tree], &pb->S[P.tree], P.tgt == P.tree, odd ? s2 : s,
+                                   odd ? s : s2});
+        }
+        for (auto &P : pb->cpairs) {
+            const bool odd = k++ % 2;
+            jobs.push_back(ListJob{&P, &pb->G[P.tgt], &pb->T[P.tree], &pb->S[P.tree], false, odd ? s2 : s,
+                                   odd ? s : s2});
+        }
         build_lists_multi(jobs, prm);
     }
     if (s2 != s) {

@@ -1286,7 +1286,7 @@ void far_count(Pair &Pr, const Targets &G, const Tree &T, const SurfDev *src, co
 // Phase 2 (Pr.n_m2p, Pr.n_p2p known): the lists, the direct-sum pair count and
 // the first half of both groupings.
 void far_fill(Pair &Pr, const Targets &G, const Tree &T, const Params &prm, int p2p_per_item, ListBuild &lb,
-              cudaStream_t s) {
+              cudaStream_t s, cudaEvent_t lists_done = nullptr) {
     const int64_t m = G.n, ms = m * ListBuild::nsplit;
     Pr.m2p_node.alloc(std::max<int64_t>(1, Pr.n_m2p));
     Pr.p2p_node.alloc(std::max<int64_t>(1, Pr.n_p2p));
@@ -1300,6 +1300,7 @@ void far_fill(Pair &Pr, const Targets &G, const Tree &T, const Params &prm, int 
                                                                                 T.count.p, Pr.stats.p + 1);
         PB_LAUNCH_CHECK();
     }
+    if (lists_done) PB_CUDA_TRY(cudaEventRecord(lists_done, s));   // the near lists may start
     group_count(m, Pr.p2p_ptr.p, Pr.p2p_node.p, T.node_leaf.p, T.nleaves, Pr.n_p2p, p2p_per_item, 1, Pr.p2p_inv,
                 Pr.p2p_ent, lb.gp, s);
     group_count(m, Pr.m2p_ptr.p, Pr.m2p_node.p, nullptr, T.nnodes, Pr.n_m2p, 32, 1, Pr.m2p_inv, Pr.m2p_ent, lb.gm, s);
@@ -1464,10 +1465,28 @@ void build_lists_multi(const std::vector<ListJob> &jobs, const Params &prm) {
             std::memcpy(&hmax[j], &hr[j][1], sizeof(double));
         }
     }
+    // the near lists of a pair on its helper stream, beside its list grouping
+    struct Events {
+        std::vector<cudaEvent_t> e;
+        ~Events() {
+            for (cudaEvent_t x : e) cudaEventDestroy(x);
+        }
+    } ev;
+    for (size_t j = 0; j < 2 * nj; ++j) {
+        cudaEvent_t x = nullptr;
+        PB_CUDA_TRY(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+        ev.e.push_back(x);
+    }
     for (size_t j = 0; j < nj; ++j) {
         const ListJob &jb = jobs[j];
-        far_fill(*jb.P, *jb.G, *jb.T, prm, jb.P->p2p_tile, *lbs[j], jb.s);
-        near_count(*jb.P, *jb.G, *jb.T, *jb.src, prm, jb.use_self, hmax[j], *lbs[j], jb.s);
+        const cudaStream_t hs = jb.helper ? jb.helper : jb.s;
+        far_fill(*jb.P, *jb.G, *jb.T, prm, jb.P->p2p_tile, *lbs[j], jb.s, hs != jb.s ? ev.e[2 * j] : nullptr);
+        if (hs != jb.s) PB_CUDA_TRY(cudaStreamWaitEvent(hs, ev.e[2 * j], 0));
+        near_count(*jb.P, *jb.G, *jb.T, *jb.src, prm, jb.use_self, hmax[j], *lbs[j], hs);
+        if (hs != jb.s) {
+            PB_CUDA_TRY(cudaEventRecord(ev.e[2 * j + 1], hs));
+            PB_CUDA_TRY(cudaStreamWaitEvent(jb.s, ev.e[2 * j + 1], 0));
+        }
     }
     std::vector<int32_t> ovf(nj, 0);
     {
@@ -1501,7 +1520,8 @@ void build_lists_multi(const std::vector<ListJob> &jobs, const Params &prm) {
         group_fill(lb.gp, Pr.n_p2p_items, Pr.p2p_items, jb.s);
         bucket_p2p_items(Pr, *jb.T, prm.ncrit, Pr.p2p_tile, jb.s);
         group_fill(lb.gm, Pr.n_m2p_items, Pr.m2p_items, jb.s);
-        near_fill(Pr, *jb.G, *jb.T, *jb.src, prm, jb.use_self, reach[j], ovf[j] != 0, lb, jb.s);
+        near_fill(Pr, *jb.G, *jb.T, *jb.src, prm, jb.use_self, reach[j], ovf[j] != 0, lb,
+                  jb.helper ? jb.helper : jb.s);
     }
     // the temporaries go back on their own streams, in reverse order of creation
     while (!lbs.empty()) lbs.pop_back();

@@ -24,9 +24,10 @@ void build_targets(Targets &G, const double *d_x, int64_t n, int surface, cudaSt
 // the panels of the tree's own surface, so each skips its own panel.
 void build_lists(Pair &Pr, const Targets &G, const Tree &T, const SurfDev &src, const Params &prm, bool use_self,
                  cudaStream_t s);
-// The lists of several pairs, each on its own stream (job.s), their host reads
-// gathered into two waits.  Inputs (tree, targets) must be ready on every
-// job's stream.
+// The lists of several pairs, each on its own stream (job.s; its near lists
+// on job.helper), their host reads gathered into two waits.  Inputs (tree,
+// targets) must be ready on every job's streams; the caller joins the helper
+// streams afterwards.
 struct ListJob {
     Pair *P;
     const Targets *G;
@@ -34,6 +35,7 @@ struct ListJob {
     const SurfDev *src;
     bool use_self;
     cudaStream_t s;
+    cudaStream_t helper = nullptr;   // the near lists run here (null: on s)
 };
 void build_lists_multi(const std::vector<ListJob> &jobs, const Params &prm);
 // The traversal (M2P / P2P lists, direct-sum pair count, entry-major items) alone;
