@@ -81,6 +81,11 @@ typedef struct {
                           radial-form contraction on the tensor pipe (TF32 instructions, every
                           operand split in two TF32 parts, FP32 accumulation; rounding differs
                           from 0, accuracy the same); 0: on the FP32 pipe (not in the paper) [0] */
+    int precond_block; /* panels per block of the right preconditioner, 1..64: runs of this many
+                          Morton-consecutive panels of a surface, whose 2 x 2 panel couplings
+                          (self terms exact, the rest by the K-point rule) form a dense block
+                          inverted at setup (FP32, applied with ~48-bit sums); 1: every panel's
+                          2 x 2 self block (not in the paper; same solution) [32] */
 } pb_params;
 
 typedef struct {

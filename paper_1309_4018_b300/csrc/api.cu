@@ -34,6 +34,7 @@ pb_problem::~pb_problem() {
     if (evj) cudaEventDestroy(evj);
     if (ev2a) cudaEventDestroy(ev2a);
     if (ev2b) cudaEventDestroy(ev2b);
+    if (ev2c) cudaEventDestroy(ev2c);
     if (side) cudaStreamDestroy(side);
     if (lists2) cudaStreamDestroy(lists2);
 }
@@ -80,6 +81,7 @@ Params resolve(const pb_params *p) {
         r.ncrit_adjoint = p->ncrit_adjoint;
         if (p->p2p_tile) r.p2p_tile = p->p2p_tile;
         r.m2p_variant = p->m2p_variant;
+        if (p->precond_block) r.precond_block = p->precond_block;
     }
     if (!valid_rule(r.K)) fail(PB_EINVAL, "K must be 1, 3, 7 or 19");
     if (!valid_rule(r.K_fine)) fail(PB_EINVAL, "K_fine must be 1, 3, 7 or 19");
@@ -89,6 +91,7 @@ Params resolve(const pb_params *p) {
     if (r.ncrit_adjoint < 0) fail(PB_EINVAL, "ncrit_adjoint must be >= 0");
     if (r.p2p_tile < 1 || r.p2p_tile > 64) fail(PB_EINVAL, "p2p_tile must be in 1..64");
     if (r.m2p_variant != 0 && r.m2p_variant != 1) fail(PB_EINVAL, "m2p_variant must be 0 or 1");
+    if (r.precond_block < 1 || r.precond_block > 64) fail(PB_EINVAL, "precond_block must be in 1..64");
     if (r.restart < 1 || r.restart > 200) fail(PB_EINVAL, "restart must be in 1..200");
     if (r.max_iter < 1) fail(PB_EINVAL, "max_iter must be >= 1");
     if (!(r.tol > 0.0)) fail(PB_EINVAL, "gmres_tol must be > 0");
@@ -185,6 +188,7 @@ void setup_problem(pb_problem *pb) {
     for (int t = 0; t < ns; ++t) build_targets(pb->G[t], pb->S[t].cen.p, pb->S[t].n, t, s2);
     const int64_t nc = pb->nc;
     build_targets(pb->G[ns], pb->cxyz_d.p, nc, -1, s2);
+    if (s2 != s) PB_CUDA_TRY(cudaEventRecord(pb->ev2c, s2));
     for (int t = 0; t < ns; ++t) build_tree(pb->T[t], pb->S[t], prm.K, prm.ncrit, s);
     // the charges must lie in their region: inside every surface that has it as
     // inner region, outside every surface that has it as outer region
@@ -305,6 +309,43 @@ void setup_problem(pb_problem *pb) {
                              pb->b.p + 2 * pb->off[sf] + side * pb->S[sf].n, mixed ? pb->T[sf].origin : nullptr, fs);
         }
     }
+    // cluster block preconditioner, on the side stream after the self values and the target sorts
+    pb->use_cluster = prm.precond && prm.precond_block > 1;
+    if (pb->use_cluster) {
+        pb->csurf.assign(ns, ClusterSurface{});
+        int64_t nblk = 0;
+        for (int sf = 0; sf < ns; ++sf) {
+            ClusterSurface &cs = pb->csurf[sf];
+            cs.n = pb->S[sf].n;
+            cs.off = pb->off[sf];
+            cs.order = pb->G[sf].order.p;
+            cs.cb = prm.precond_block;
+            cs.first = nblk;
+            nblk += cs.nblocks();
+        }
+        const int nb2 = cluster_block_dim(prm.precond_block);
+        pb->cinv.alloc((size_t)std::max<int64_t>(1, nblk) * nb2 * nb2);
+        pb->cerr.alloc(1);
+        pb->cerr.zero(fs);
+        pb->cerr_h.alloc(1);
+        if (s2 != fs) PB_CUDA_TRY(cudaStreamWaitEvent(fs, pb->ev2c, 0));
+        for (int sf = 0; sf < ns; ++sf) {
+            ClusterRows cr{};
+            for (int side = 0; side < 2; ++side)
+                for (const Term &tm : pb->rows[2 * sf + side]) {
+                    const Pair &P = pb->pairs[tm.pair];
+                    if (P.tree != sf || P.tgt != sf) continue;
+                    cr.cK[side] = tm.cK;
+                    cr.cV[side] = tm.cV;
+                    cr.kappa[side] = P.kappas[tm.kidx];
+                    cr.selfV[side] = P.selfV[tm.kidx].p;
+                }
+            const SurfDev &S = pb->S[sf];
+            cluster_blocks(pb->csurf[sf], ClusterGeom{S.cen.p, S.nrm.p, S.gy.p, S.gwa.p, prm.K}, cr, pb->cinv.p,
+                           pb->cerr.p, fs);
+        }
+        PB_CUDA_TRY(cudaMemcpyAsync(pb->cerr_h.p, pb->cerr.p, sizeof(int32_t), cudaMemcpyDeviceToHost, fs));
+    }
     // the list builds, pairs alternating between the two list streams (both see the trees and the targets)
     if (s2 != s) {
         PB_CUDA_TRY(cudaEventRecord(pb->ev2a, s));
@@ -409,6 +450,8 @@ void setup_problem(pb_problem *pb) {
         }
     PB_CUDA_TRY(cudaEventRecord(pb->ev1, s));
     PB_CUDA_TRY(cudaEventSynchronize(pb->ev1));
+    // a run whose block had a vanishing pivot: the 2 x 2 self blocks instead
+    if (pb->use_cluster && *pb->cerr_h.p) pb->use_cluster = false;
     if (n_wind > 0 && pb->wind_bad_h.p[0] > 0) {
         const int32_t *bad = pb->wind_bad_h.p;
         fail(PB_EINVAL, std::to_string(bad[0]) + " charge(s) lie outside their region (first: charge " +
@@ -547,6 +590,10 @@ void reaction(pb_problem *pb, const double *xd) {
 // z = M^-1 u (block-Jacobi), both 2N device vectors.
 void apply_precond(pb_problem *pb, const double *u, double *z) {
     cudaStream_t s = pb->stream;
+    if (pb->use_cluster) {
+        cluster_apply(pb->csurf, pb->cinv.p, u, z, s);
+        return;
+    }
     for (size_t sf = 0; sf < pb->S.size(); ++sf) {
         const int64_t n = pb->S[sf].n, o = 2 * pb->off[sf];
         block_jacobi_apply(n, pb->minv.p + 4 * pb->off[sf], u + o, u + o + n, z + o, z + o + n, s);
@@ -874,6 +921,11 @@ void solve_many(const std::vector<pb_problem *> &probs, const std::vector<const 
         jb.graph = [pb](cudaStream_t gs) { launch_operator_graph(pb, gs); };
         jb.cycle_op = [pb] { apply_operator(pb, pb->z1.p, pb->gm.w.p); };
         jb.prep = [pb](cudaStream_t ps) {
+            if (pb->use_cluster) {
+                Gmres &gm = pb->gm;
+                cluster_prep(pb->csurf, pb->cinv.p, gm.st.p, gm.V.p, gm.ld, gm.w.p, gm.scal.p + 1, pb->z1.p, ps);
+                return;
+            }
             std::vector<std::pair<int64_t, int64_t>> sf;
             for (size_t t = 0; t < pb->S.size(); ++t) sf.emplace_back(pb->off[t], pb->S[t].n);
             pb->gm.prep_step(pb->prm.precond ? pb->minv.p : nullptr, sf, pb->z1.p, ps);
@@ -1058,6 +1110,7 @@ int pb_problem_create(pb_ctx *c, pb_problem **out) {
         PB_CUDA_TRY(cudaStreamCreateWithFlags(&pb->lists2, cudaStreamNonBlocking));
         PB_CUDA_TRY(cudaEventCreateWithFlags(&pb->ev2a, cudaEventDisableTiming));
         PB_CUDA_TRY(cudaEventCreateWithFlags(&pb->ev2b, cudaEventDisableTiming));
+        PB_CUDA_TRY(cudaEventCreateWithFlags(&pb->ev2c, cudaEventDisableTiming));
     });
     if (rc != PB_OK) return rc;
     *out = pb.release();

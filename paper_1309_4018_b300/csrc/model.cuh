@@ -16,6 +16,7 @@ struct Params {
     int restart = 50, max_iter = 1000;
     int precision = PB_FP64;
     bool precond = true;
+    int precond_block = 32;  // panels per preconditioner block (1: 2 x 2 self blocks)
     int ncrit_adjoint = 0;   // 0: ncrit
     int p2p_tile = 64;       // targets per P2P work item (above 32: two per lane)
     int m2p_variant = 0;     // 1: FP32 radial M2P with its contraction on the tensor pipe

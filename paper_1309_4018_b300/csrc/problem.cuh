@@ -9,6 +9,7 @@
 
 #include "gmres.cuh"
 #include "model.cuh"
+#include "precond.cuh"
 #include "treecode.cuh"
 #include "validate.cuh"
 
@@ -61,6 +62,7 @@ struct pb_problem {
     cudaEvent_t evf = nullptr, evj = nullptr; // fork and join of the side stream
     cudaStream_t lists2 = nullptr;            // setup: target sorts and every other pair's list build
     cudaEvent_t ev2a = nullptr, ev2b = nullptr; // setup: joins between the context stream and lists2
+    cudaEvent_t ev2c = nullptr;               // setup: the target sorts done (lists2)
     cudaGraphExec_t mv_exec = nullptr;        // captured operator application z1 -> gm.w
     long long mv_kernels = 0;                 // kernels in that graph
     cudaGraphExec_t adj_exec = nullptr;       // captured transposed operator z1 -> gm.w (gradient)
@@ -92,6 +94,12 @@ struct pb_problem {
     pb::PinnedBuf<int32_t> wind_bad_h;
     pb::PinnedBuf<pb::MeshCheck> mesh_chk_h;
     pb::PinnedBuf<pb::ValueCheck> val_chk_h;  // outcome of the last pb_add_surface's mesh check
+    // cluster block preconditioner (precond_block > 1; else the 2 x 2 self blocks in minv)
+    bool use_cluster = false;
+    std::vector<pb::ClusterSurface> csurf;
+    pb::DevBuf<float> cinv;                    // 128 x 128 floats per block
+    pb::DevBuf<int32_t> cerr;                  // a vanished pivot
+    pb::PinnedBuf<int32_t> cerr_h;
     pb::Gmres gm;
     double setup_ms = 0.0;
     bool have_solution = false;

@@ -34,7 +34,8 @@ class pb_params(ctypes.Structure):
                 ("thres", ctypes.c_double), ("P", ctypes.c_int), ("theta", ctypes.c_double),
                 ("ncrit", ctypes.c_int), ("gmres_tol", ctypes.c_double), ("restart", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("no_precond", ctypes.c_int),
-                ("ncrit_adjoint", ctypes.c_int), ("p2p_tile", ctypes.c_int), ("m2p_variant", ctypes.c_int)]
+                ("ncrit_adjoint", ctypes.c_int), ("p2p_tile", ctypes.c_int), ("m2p_variant", ctypes.c_int),
+                ("precond_block", ctypes.c_int)]
 
 
 class pb_result(ctypes.Structure):

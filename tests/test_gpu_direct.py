@@ -103,3 +103,20 @@ def test_preconditioner_does_not_change_the_solution():
     assert r1.converged and r0.converged
     assert abs(r1.dG_solv - r0.dG_solv) <= 1e-8 * abs(r0.dG_solv)
     assert r1.iterations <= r0.iterations
+
+
+@pytest.mark.parametrize("block", [1, 8, 32, 64])
+def test_cluster_preconditioner_sizes_give_the_same_solution(block):
+    # right preconditioning: any block size solves the same system; the
+    # 2 x 2 self blocks (block 1) are the reference
+    from synth.configs import protein_problem
+    d = protein_problem(n_atoms=200, seed=5)
+    ref = problem(d, gmres_tol=1e-10, precond_block=1, **DIRECT)
+    r0 = ref.solve()
+    pb = problem(d, gmres_tol=1e-10, precond_block=block, **DIRECT)
+    r = pb.solve()
+    assert r.converged and r0.converged
+    assert abs(r.dG_solv - r0.dG_solv) <= 1e-8 * abs(r0.dG_solv)
+    assert np.linalg.norm(pb.solution() - ref.solution()) <= 1e-8 * np.linalg.norm(ref.solution())
+    if block > 1:
+        assert r.iterations < r0.iterations
