@@ -1744,6 +1744,10 @@ void apply_tpairs(pb_problem *pb, std::vector<TPair> &list, const double *u, dou
 
 void apply_precond_T(pb_problem *pb, const double *u, double *z) {
     cudaStream_t s = pb->stream;
+    if (pb->use_cluster) {
+        cluster_apply_T(pb->csurf, pb->cinv.p, u, z, s);
+        return;
+    }
     AdjointState &A = *pb->adj;
     for (size_t sf = 0; sf < pb->S.size(); ++sf) {
         const int64_t n = pb->S[sf].n, o = 2 * pb->off[sf];

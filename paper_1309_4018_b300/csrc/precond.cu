@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(2 * NB2) cluster_build_kernel(BuildArgs a) {
 // z = M^-1 v for the runs of one surface, one block per run, thread u for
 // local unknown u (FP64 sums of the FP32 inverse times the FP64 entries).
 // PREP: v is v_j of the device Arnoldi loop, formed and stored here.
-template <bool PREP, int NB2>
+template <bool PREP, int NB2, bool TRANS = false>
 __global__ void __launch_bounds__(NB2) cluster_apply_kernel(ClusterSurface sf, const float *__restrict__ binv,
                                                                   const double *__restrict__ u,
                                                                   double *__restrict__ z, const GmresState *st,
@@ -218,10 +218,11 @@ __global__ void __launch_bounds__(NB2) cluster_apply_kernel(ClusterSurface sf, c
     // FP32 pairs (hi + lo, ~48 significant bits) on the FP32 pipe: the products
     // m v_hi exactly by fma, m v_lo rounded, the sum compensated (TwoSum), so
     // the map is linear to ~1e-14 relative without FP64 arithmetic per term
-    const float *bt = binv + (sf.first + blockIdx.x) * (int64_t)kBlockDim * kBlockDim + t;
+    // TRANS: the transpose (z_w = sum_u Binv[u][w] v_u), row w of the stored block
+    const float *bt = binv + (sf.first + blockIdx.x) * (int64_t)kBlockDim * kBlockDim + (TRANS ? t * kBlockDim : t);
     float sh = 0.f, sl = 0.f;
     for (int c = 0; c < n2; ++c) {
-        const float m = bt[(int64_t)c * kBlockDim];
+        const float m = bt[TRANS ? c : (int64_t)c * kBlockDim];
         const float2 v = vl2[c];
         const float ph = m * v.x;
         const float pe = fmaf(m, v.y, fmaf(m, v.x, -ph));
@@ -252,21 +253,22 @@ void build_launch(const BuildArgs &a, cudaStream_t s) {
     PB_LAUNCH_CHECK();
 }
 
-template <bool PREP, int NB2>
+template <bool PREP, int NB2, bool TRANS>
 void apply_launch(const ClusterSurface &sf, const float *binv, const double *u, double *z, const GmresState *st,
                   double *V, int64_t ld, const double *w, const double *num_sq, cudaStream_t s) {
-    cluster_apply_kernel<PREP, NB2><<<(unsigned)sf.nblocks(), NB2, 0, s>>>(sf, binv, u, z, st, V, ld, w, num_sq);
+    cluster_apply_kernel<PREP, NB2, TRANS><<<(unsigned)sf.nblocks(), NB2, 0, s>>>(sf, binv, u, z, st, V, ld, w,
+                                                                                    num_sq);
     PB_LAUNCH_CHECK();
 }
 
-template <bool PREP>
+template <bool PREP, bool TRANS = false>
 void apply_any(const ClusterSurface &sf, const float *binv, const double *u, double *z, const GmresState *st,
                double *V, int64_t ld, const double *w, const double *num_sq, cudaStream_t s) {
     switch (cluster_block_dim(sf.cb)) {
-        case 16: apply_launch<PREP, 16>(sf, binv, u, z, st, V, ld, w, num_sq, s); break;
-        case 32: apply_launch<PREP, 32>(sf, binv, u, z, st, V, ld, w, num_sq, s); break;
-        case 64: apply_launch<PREP, 64>(sf, binv, u, z, st, V, ld, w, num_sq, s); break;
-        default: apply_launch<PREP, 128>(sf, binv, u, z, st, V, ld, w, num_sq, s);
+        case 16: apply_launch<PREP, 16, TRANS>(sf, binv, u, z, st, V, ld, w, num_sq, s); break;
+        case 32: apply_launch<PREP, 32, TRANS>(sf, binv, u, z, st, V, ld, w, num_sq, s); break;
+        case 64: apply_launch<PREP, 64, TRANS>(sf, binv, u, z, st, V, ld, w, num_sq, s); break;
+        default: apply_launch<PREP, 128, TRANS>(sf, binv, u, z, st, V, ld, w, num_sq, s);
     }
 }
 
@@ -289,6 +291,12 @@ void cluster_apply(const std::vector<ClusterSurface> &sfs, const float *binv, co
                    cudaStream_t s) {
     for (const ClusterSurface &sf : sfs)
         if (sf.n) apply_any<false>(sf, binv, u, z, nullptr, nullptr, 0, nullptr, nullptr, s);
+}
+
+void cluster_apply_T(const std::vector<ClusterSurface> &sfs, const float *binv, const double *u, double *z,
+                     cudaStream_t s) {
+    for (const ClusterSurface &sf : sfs)
+        if (sf.n) apply_any<false, true>(sf, binv, u, z, nullptr, nullptr, 0, nullptr, nullptr, s);
 }
 
 void cluster_prep(const std::vector<ClusterSurface> &sfs, const float *binv, const GmresState *st, double *V,

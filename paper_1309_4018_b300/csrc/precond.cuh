@@ -57,6 +57,10 @@ void cluster_blocks(const ClusterSurface &sf, const ClusterGeom &g, const Cluste
 void cluster_apply(const std::vector<ClusterSurface> &sfs, const float *binv, const double *u, double *z,
                    cudaStream_t s);
 
+// z = M^-T u (the adjoint solve's right preconditioner).
+void cluster_apply_T(const std::vector<ClusterSurface> &sfs, const float *binv, const double *u, double *z,
+                     cudaStream_t s);
+
 // Device-loop form (GMRES graph): v_j formed as in Gmres::prep_step (from w
 // and ||w|| when st->pend, else column j of V; stored as column j), then z = M^-1 v_j.
 struct GmresState;
