@@ -393,6 +393,88 @@ __device__ __forceinline__ void p2p32_pair(float tx, float ty, float tz, int me,
     }
 }
 
+// Packed FP32 pairs (f32x2: two lanes' worth of one FP32 operation in one
+// instruction on sm_100-family parts).  The FMA pipe takes a pair instruction
+// in two cycles, so the FP32 rate is unchanged, but the issue slot between
+// them is free for the MUFU, shared-memory and integer instructions: the
+// two-targets-per-lane P2P issues about 15 instead of 28 instructions per pair.
+// Each is the IEEE round-to-nearest operation of its scalar form.
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p f2_make(float lo, float hi) {
+    f2p r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float f2_lo(f2p v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return lo;
+}
+__device__ __forceinline__ float f2_hi(f2p v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return hi;
+}
+__device__ __forceinline__ f2p f2_sub(f2p a, f2p b) {
+    f2p d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2p f2_add(f2p a, f2p b) {
+    f2p d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2p f2_mul(f2p a, f2p b) {
+    f2p d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2p f2_fma(f2p a, f2p b, f2p c) {
+    f2p d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// The pair contributions of one staged source to two targets (tX.. hold the
+// two targets' coordinates), the same operations in the same order as
+// p2p32_pair, two at a time.  a*, b* hold the source's values twice.
+template <int NK, bool Y0, bool Y1, bool MASK>
+__device__ __forceinline__ void p2p32_pair2(f2p tX, f2p tY, f2p tZ, int me0, int me1, f2p aX, f2p aY, f2p aZ,
+                                            f2p aW, f2p bX, f2p bY, f2p bZ, int pid, f2p k0, f2p k1, f2p l2e0,
+                                            f2p l2e1, f2p one, f2p p[4]) {
+    const f2p dX = f2_sub(tX, aX), dY = f2_sub(tY, aY), dZ = f2_sub(tZ, aZ);
+    const f2p R2 = f2_fma(dX, dX, f2_fma(dY, dY, f2_mul(dZ, dZ)));
+    const float i0 = (MASK && pid == me0) ? 0.f : fast_rsqrt(f2_lo(R2));
+    const float i1 = (MASK && pid == me1) ? 0.f : fast_rsqrt(f2_hi(R2));
+    const f2p INV = f2_make(i0, i1);
+    const f2p SV = f2_mul(aW, INV);
+    const f2p RD = f2_fma(dX, bX, f2_fma(dY, bY, f2_mul(dZ, bZ)));
+    const f2p KV = f2_mul(RD, f2_mul(f2_mul(INV, INV), INV));
+    if (!Y0) {
+        p[0] = f2_add(p[0], SV);
+        p[1] = f2_add(p[1], KV);
+    } else {
+        const f2p RHO = f2_mul(R2, INV);
+        const f2p ARG = f2_mul(l2e0, RHO);
+        const f2p EX = f2_make(fast_ex2(f2_lo(ARG)), fast_ex2(f2_hi(ARG)));
+        p[0] = f2_fma(SV, EX, p[0]);
+        p[1] = f2_fma(f2_mul(KV, EX), f2_fma(k0, RHO, one), p[1]);
+    }
+    if (NK == 2) {
+        if (!Y1) {
+            p[2] = f2_add(p[2], SV);
+            p[3] = f2_add(p[3], KV);
+        } else {
+            const f2p RHO = f2_mul(R2, INV);
+            const f2p ARG = f2_mul(l2e1, RHO);
+            const f2p EX = f2_make(fast_ex2(f2_lo(ARG)), fast_ex2(f2_hi(ARG)));
+            p[2] = f2_fma(SV, EX, p[2]);
+            p[3] = f2_fma(f2_mul(KV, EX), f2_fma(k1, RHO, one), p[3]);
+        }
+    }
+}
+
 // A work item of up to 64 targets: every lane sums the staged sources for
 // targets `lane` and `lane + 32`, so each staged source is read once for two
 // pairs.  Same arithmetic per pair, same order over the sources, same records
@@ -435,12 +517,24 @@ __device__ __forceinline__ void p2p32x2_item(const P2PArgs32 &g, int64_t item, i
         __syncwarp();
         float p0[4] = {0.f, 0.f, 0.f, 0.f}, p1[4] = {0.f, 0.f, 0.f, 0.f};
         if (two) {
+            // both targets in packed pairs (lo: target lane, hi: target lane + 32)
+            const f2p tX = f2_make(tx[0], tx[1]), tY = f2_make(ty[0], ty[1]), tZ = f2_make(tz[0], tz[1]);
+            const f2p K0 = f2_make(k0, k0), K1 = f2_make(k1, k1), L0 = f2_make(l2e0, l2e0),
+                      L1 = f2_make(l2e1, l2e1), ONE = f2_make(1.f, 1.f);
+            f2p pp[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll 4
             for (int j = 0; j < m; ++j) {
                 const float4 a = sA[j];
                 const float4 b = sB[j];
-                p2p32_pair<NK, Y0, Y1, MASK>(tx[0], ty[0], tz[0], me[0], a, b, k0, k1, l2e0, l2e1, p0);
-                p2p32_pair<NK, Y0, Y1, MASK>(tx[1], ty[1], tz[1], me[1], a, b, k0, k1, l2e0, l2e1, p1);
+                p2p32_pair2<NK, Y0, Y1, MASK>(tX, tY, tZ, me[0], me[1], f2_make(a.x, a.x), f2_make(a.y, a.y),
+                                              f2_make(a.z, a.z), f2_make(a.w, a.w), f2_make(b.x, b.x),
+                                              f2_make(b.y, b.y), f2_make(b.z, b.z), __float_as_int(b.w), K0, K1, L0,
+                                              L1, ONE, pp);
+            }
+#pragma unroll
+            for (int v = 0; v < 2 * NK; ++v) {
+                p0[v] = f2_lo(pp[v]);
+                p1[v] = f2_hi(pp[v]);
             }
         } else if (valid[0]) {
 #pragma unroll 4
