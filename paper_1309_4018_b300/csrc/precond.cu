@@ -143,10 +143,13 @@ __global__ void __launch_bounds__(2 * NB2) cluster_build_kernel(BuildArgs a) {
         if (cc < n2) {
             const float akc = A[k * kPad + cc];
             const bool diag = cc == k;
-            for (int r = rg; r < n2; r += kRowStep) {
-                if (r == k) continue;
-                const float base = diag ? 0.f : A[r * kPad + cc];
-                A[r * kPad + cc] = base - fcol[r] * akc;
+#pragma unroll
+            for (int i = 0; i < kBlockDim / kRowStep; ++i) {
+                const int r = rg + kRowStep * i;
+                if (r < n2 && r != k) {
+                    const float base = diag ? 0.f : A[r * kPad + cc];
+                    A[r * kPad + cc] = base - fcol[r] * akc;
+                }
             }
         }
         __syncthreads();
@@ -162,6 +165,7 @@ __global__ void __launch_bounds__(2 * NB2) cluster_build_kernel(BuildArgs a) {
     }
     __syncthreads();
     float *out = a.binv + (sf.first + blockIdx.x) * (int64_t)kBlockDim * kBlockDim;
+#pragma unroll 4
     for (int e = tid; e < kBlockDim * kBlockDim; e += kBuildThreads) {
         const int w = e / kBlockDim, u = e & (kBlockDim - 1);
         out[e] = (u < n2 && w < n2) ? A[u * kPad + col[w]] : 0.f;
