@@ -808,10 +808,15 @@ __global__ void radial_moments_kernel(int nnodes, const float *__restrict__ mom,
 // moments R: every moment pair is read from shared memory once for all NTG
 // targets.  u = box centre - target; out = (VL, KL, VY, KY) per target.  The
 // arithmetic per target is that of the one-target form, in the same order.
+// The monopole and dipole sums of one radial index n share their monomial, so
+// they run as one packed FP32 pair (SM_n, SD_n) += (m, m) (N^M, N^D), with the
+// staged moment pair as the second operand; the closing sums pair (V, K) of
+// each kernel the same way.  Every half is the scalar fma of the unpacked form.
 template <int P, int NTG>
 __device__ __forceinline__ void m2p_ly_eval(const float4 *R, const float (&ux)[NTG], const float (&uy)[NTG],
                                             const float (&uz)[NTG], float kappa, float4 (&out)[NTG]) {
-    float px[NTG][P + 1], py[NTG][P + 1], pz[NTG][P + 1], SM[NTG][P + 1], SD[NTG][P + 1];
+    float px[NTG][P + 1], py[NTG][P + 1], pz[NTG][P + 1];
+    f2p S[NTG][P + 1];     // (SM_n, SD_n)
 #pragma unroll
     for (int t = 0; t < NTG; ++t) {
         px[t][0] = py[t][0] = pz[t][0] = 1.f;
@@ -822,9 +827,10 @@ __device__ __forceinline__ void m2p_ly_eval(const float4 *R, const float (&ux)[N
             pz[t][i] = pz[t][i - 1] * uz[t];
         }
 #pragma unroll
-        for (int n = 0; n <= P; ++n) { SM[t][n] = 0.f; SD[t][n] = 0.f; }
+        for (int n = 0; n <= P; ++n) S[t][n] = 0ull;
     }
-    float4 cur = make_float4(0.f, 0.f, 0.f, 0.f);
+    const ulonglong2 *R2 = reinterpret_cast<const ulonglong2 *>(R);
+    ulonglong2 cur = make_ulonglong2(0ull, 0ull);
     int o = 0;
 #pragma unroll
     for (int a1 = 0; a1 <= P; ++a1)
@@ -835,20 +841,19 @@ __device__ __forceinline__ void m2p_ly_eval(const float4 *R, const float (&ux)[N
             for (int t = 0; t < NTG; ++t) base[t] = px[t][a1] * py[t][a2];
 #pragma unroll
             for (int a3 = 0; a3 <= P - a1 - a2; ++a3) {
-                float mono[NTG];
+                f2p mono[NTG];
 #pragma unroll
-                for (int t = 0; t < NTG; ++t) mono[t] = base[t] * pz[t][a3];
+                for (int t = 0; t < NTG; ++t) {
+                    const float m = base[t] * pz[t][a3];
+                    mono[t] = f2_make(m, m);
+                }
                 const int a = a1 + a2 + a3;
 #pragma unroll
                 for (int n = a; 2 * n <= a + P; ++n) {
-                    if ((o & 3) == 0) cur = R[o >> 2];
-                    const float nm = (o & 3) == 0 ? cur.x : cur.z;
-                    const float nd = (o & 3) == 0 ? cur.y : cur.w;
+                    if ((o & 3) == 0) cur = R2[o >> 2];
+                    const f2p nmd = (o & 3) == 0 ? cur.x : cur.y;
 #pragma unroll
-                    for (int t = 0; t < NTG; ++t) {
-                        SM[t][n] = fmaf(mono[t], nm, SM[t][n]);
-                        SD[t][n] = fmaf(mono[t], nd, SD[t][n]);
-                    }
+                    for (int t = 0; t < NTG; ++t) S[t][n] = f2_fma(mono[t], nmd, S[t][n]);
                     o += 2;
                 }
             }
@@ -868,15 +873,13 @@ __device__ __forceinline__ void m2p_ly_eval(const float4 *R, const float (&ux)[N
         const float k2 = kappa * kappa;
 #pragma unroll
         for (int n = 1; n < P; ++n) FY[n + 1] = fmaf(k2, FY[n - 1], -(float)(2 * n + 1) * FY[n]) * ir2;
-        float VL = 0.f, KL = 0.f, VY = 0.f, KY = 0.f;
+        f2p L = 0ull, Y = 0ull;     // (VL, KL), (VY, KY)
 #pragma unroll
         for (int n = 0; n <= P; ++n) {
-            VL = fmaf(FL[n], SM[t][n], VL);
-            KL = fmaf(FL[n], SD[t][n], KL);
-            VY = fmaf(FY[n], SM[t][n], VY);
-            KY = fmaf(FY[n], SD[t][n], KY);
+            L = f2_fma(f2_make(FL[n], FL[n]), S[t][n], L);
+            Y = f2_fma(f2_make(FY[n], FY[n]), S[t][n], Y);
         }
-        out[t] = make_float4(VL, KL, VY, KY);
+        out[t] = make_float4(f2_lo(L), f2_hi(L), f2_lo(Y), f2_hi(Y));
     }
 }
 
@@ -889,8 +892,13 @@ __device__ __forceinline__ void m2p_ly_eval(const float4 *R, const float (&ux)[N
 // 32 targets), every lane evaluates one target of each, so each moment pair
 // is read once for NI targets; otherwise the items are evaluated one after
 // the other.  Lanes past the last item's count evaluate their first target
-// again and store it once.  Seven blocks per SM (72 registers, no spills):
-// 90 -> 86 us at P = 6 against the unbounded 80 registers and six blocks.
+// again and store it once.  Seven blocks per SM (72 registers; at P = 6 the
+// packed evaluation spills 12 bytes outside its loops): 90 -> 86 us at P = 6
+// against the unbounded 80 registers and six blocks.  A persistent form, each
+// warp walking its tasks with the next box's moments copied by cp.async and
+// the next targets' indices loaded one and two tasks ahead, was slower (103
+// against 92 us: 96 registers, 17 resident warps per SM, 13% more
+// instructions), so the short warps stay.
 
 // The NI items i0.. on the calling warp; sR: the warp's staging of one box's radial moments.
 template <int P, int NI>
