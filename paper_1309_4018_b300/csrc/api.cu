@@ -535,17 +535,18 @@ void operator_pre(pb_problem *pb, const double *xd, cudaStream_t s) {
 void operator_post(pb_problem *pb, const double *xd, double *yd, cudaStream_t s) {
     const int ns = (int)pb->S.size();
     for (int sf = 0; sf < ns; ++sf) {
+        CombineRow row[2]{};
         for (int side = 0; side < 2; ++side) {
-            CombineRow row{};
             const auto &terms = pb->rows[2 * sf + side];
-            row.nterm = (int)terms.size();
-            for (int k = 0; k < row.nterm; ++k) {
+            row[side].nterm = (int)terms.size();
+            for (int k = 0; k < row[side].nterm; ++k) {
                 const Pair &P = pb->pairs[terms[k].pair];
-                row.term[k] = CombineTerm{P.VK[terms[k].kidx].p, pb->G[P.tgt].n, terms[k].cK, terms[k].cV};
+                row[side].term[k] = CombineTerm{P.VK[terms[k].kidx].p, pb->G[P.tgt].n, terms[k].cK, terms[k].cV};
             }
-            launch_combine(pb->S[sf].n, pb->G[sf].rank.p, xd + 2 * pb->off[sf], 0.5, row,
-                           yd + 2 * pb->off[sf] + side * pb->S[sf].n, s);
         }
+        // both rows of the surface (the two sides of its panels) in one launch
+        launch_combine_pair(pb->S[sf].n, pb->G[sf].rank.p, xd + 2 * pb->off[sf], 0.5, row[0], row[1],
+                            yd + 2 * pb->off[sf], s);
     }
 }
 

@@ -331,64 +331,84 @@ __device__ __forceinline__ ArnoldiArgs device_column(ArnoldiArgs a) {
     return a;
 }
 
-// Block partials of V[v] . w over the block's slice, for v < nv, 16 vectors
-// per pass (16 independent loads per element in flight).  The FP64 pipe is
-// narrow on this part, so the block reduction is arranged to issue few FP64
+// Block partials of V[v] . w over the block's slice, for v < nv, up to 16
+// vectors per pass (all of a pass's loads per element in flight at once).
+// The FP64 pipe is narrow on this part, so a pass computes its vectors
+// rounded up to a multiple of four (not always 16) and the block reduction is arranged to issue few FP64
 // instructions: every thread's partials go to shared memory, each (vector,
 // 8-thread chunk) is summed by one thread, and one warp per vector adds the
 // 32 chunk sums by a butterfly (each warp takes two vectors of the pass).
+template <int NB>
+__device__ __forceinline__ void slice_pass(const ArnoldiArgs &a, int64_t lo, int64_t hi, int v0, int nb,
+                                           double (*red)[kRedThreads + 1]) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double acc[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) acc[b] = 0.0;
+#pragma unroll 1
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) {
+        const double wi = a.w[i];
+        // unconditional loads (the index clamped to the pass's last vector;
+        // the extra sums are never stored), so the NB are issued together
+        double x[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) x[b] = a.V[(int64_t)(v0 + min(b, nb - 1)) * a.ld + i];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) acc[b] += x[b] * wi;
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) red[b][threadIdx.x] = acc[b];
+    __syncthreads();
+    // warp wid sums vectors wid and wid + 8: lane adds the partials of threads 8 lane .. 8 lane + 7
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int vb = wid + 8 * h;
+        if (vb < nb) {
+            double t = 0.0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) t += red[vb][8 * lane + k];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) a.partial[(v0 + vb) * kRedBlocks + blockIdx.x] = t;
+        }
+    }
+    __syncthreads();
+}
+
+// A pass takes its nb vectors in a form for 4, 8, 12 or 16.
 __device__ void slice_dots(const ArnoldiArgs &a, int64_t lo, int64_t hi) {
     constexpr int G = kSliceGroup;
     static_assert(kRedThreads == 256 && G == 16, "the reduction layout assumes 256 threads, 16 vectors");
     __shared__ double red[G][kRedThreads + 1];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int v0 = 0; v0 < a.nv; v0 += G) {
         const int nb = min(G, a.nv - v0);
-        double acc[G];
-#pragma unroll
-        for (int b = 0; b < G; ++b) acc[b] = 0.0;
-        for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) {
-            const double wi = a.w[i];
-            // unconditional loads (the index clamped to the last vector; the
-            // extra sums are never stored), so the 16 are issued together
-            double x[G];
-#pragma unroll
-            for (int b = 0; b < G; ++b) x[b] = a.V[(int64_t)(v0 + min(b, nb - 1)) * a.ld + i];
-#pragma unroll
-            for (int b = 0; b < G; ++b) acc[b] += x[b] * wi;
-        }
-#pragma unroll
-        for (int b = 0; b < G; ++b) red[b][threadIdx.x] = acc[b];
-        __syncthreads();
-        // warp wid sums vectors wid and wid + 8: lane adds the partials of threads 8 lane .. 8 lane + 7
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int vb = wid + 8 * h;
-            if (vb < nb) {
-                double t = 0.0;
-#pragma unroll
-                for (int k = 0; k < 8; ++k) t += red[vb][8 * lane + k];
-                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                if (lane == 0) a.partial[(v0 + vb) * kRedBlocks + blockIdx.x] = t;
-            }
-        }
-        __syncthreads();
+        if (nb <= 4) slice_pass<4>(a, lo, hi, v0, nb, red);
+        else if (nb <= 8) slice_pass<8>(a, lo, hi, v0, nb, red);
+        else if (nb <= 12) slice_pass<12>(a, lo, hi, v0, nb, red);
+        else slice_pass<16>(a, lo, hi, v0, nb, red);
     }
 }
 
-// w[i] - sum_v V[v][i] h[v], subtracted in v order, eight basis loads in flight
-// per step.  sh holds h padded with zeros to a multiple of eight and the
-// padding steps load the last vector (finite), so they subtract zero.
+// w[i] - sum_v V[v][i] h[v], subtracted in v order: eight basis loads in
+// flight per step, then four, then one at a time for the last few.
 __device__ __forceinline__ double project_elem(const ArnoldiArgs &a, const double *__restrict__ sh, int64_t i,
                                                double t) {
-    const int nv8 = (a.nv + 7) & ~7;
-    for (int v = 0; v < nv8; v += 8) {
+    int v = 0;
+    for (; v + 8 <= a.nv; v += 8) {
         double x[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) x[u] = a.V[(int64_t)min(v + u, a.nv - 1) * a.ld + i];
+        for (int u = 0; u < 8; ++u) x[u] = a.V[(int64_t)(v + u) * a.ld + i];
 #pragma unroll
         for (int u = 0; u < 8; ++u) t -= x[u] * sh[v + u];
     }
+    if (v + 4 <= a.nv) {
+        double x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = a.V[(int64_t)(v + u) * a.ld + i];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t -= x[u] * sh[v + u];
+        v += 4;
+    }
+    for (; v < a.nv; ++v) t -= a.V[(int64_t)v * a.ld + i] * sh[v];
     return t;
 }
 
@@ -447,6 +467,18 @@ __global__ void __launch_bounds__(kRedThreads) arnoldi_project_norm_kernel(Arnol
     const int64_t per = (a.n + kRedBlocks - 1) / kRedBlocks;
     const int64_t lo = blockIdx.x * per, hi = min(a.n, lo + per);
     __shared__ double sh[kMaxRestart + 8];
+    // the Hessenberg column h1 + h2 and the earlier rotations, for the last
+    // block's Givens update: fixed since the previous launches, so every block
+    // stages them now and the last block does not wait for them after its arrival
+    __shared__ double scol[kMaxRestart + 2], scs[kMaxRestart], ssn[kMaxRestart];
+    {
+        const GmresState *st = a.st;
+        for (int i = threadIdx.x; i <= a.j; i += kRedThreads) scol[i] = a.h1[i] + a.h2[i];
+        for (int i = threadIdx.x; i < a.j; i += kRedThreads) {
+            scs[i] = st->cs[i];
+            ssn[i] = st->sn[i];
+        }
+    }
     stage_h(sh, a.h2, a.nv);
     double s2 = 0.0;
     for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) {
@@ -469,18 +501,10 @@ __global__ void __launch_bounds__(kRedThreads) arnoldi_project_norm_kernel(Arnol
         for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
         if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = p;
         __syncthreads();
-        // Hessenberg column j = h1 + h2 and the earlier rotations, staged in
-        // shared memory by the whole block; thread 0 applies the rotations
-        // there (no global round trip per step), then the block writes it back
-        __shared__ double scol[kMaxRestart + 2], scs[kMaxRestart], ssn[kMaxRestart];
+        // thread 0 applies the rotations to the staged column (no global
+        // round trip per step), then the block writes it back
         GmresState *st = a.st;
         const int m = st->m, j = a.j;
-        for (int i = threadIdx.x; i <= j; i += kRedThreads) scol[i] = a.h1[i] + a.h2[i];
-        for (int i = threadIdx.x; i < j; i += kRedThreads) {
-            scs[i] = st->cs[i];
-            ssn[i] = st->sn[i];
-        }
-        __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
             for (int k = 0; k < kRedThreads / 32; ++k) t += sm[k];

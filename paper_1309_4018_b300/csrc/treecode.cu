@@ -1199,6 +1199,23 @@ __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, GatherArgs32
 }
 
 // ---------------------------------------------------------------- near field and combine
+// Both block rows of one surface in one launch: element i < 2 n is entry i - s n of row s.
+__global__ void combine_pair_kernel(int64_t n, const int32_t *__restrict__ rank, const double *__restrict__ phi_s,
+                                    double half, CombineRow row0, CombineRow row1, double *__restrict__ y) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 2 * n) return;
+    const bool second = e >= n;
+    const int64_t i = second ? e - n : e;
+    const CombineRow &row = second ? row1 : row0;
+    const int r = rank[i];
+    double v = phi_s ? half * phi_s[i] : 0.0;
+    for (int k = 0; k < row.nterm; ++k) {
+        const CombineTerm &tm = row.term[k];
+        v += tm.cK * tm.VK[tm.ntg + r] + tm.cV * tm.VK[r];
+    }
+    y[e] = v;
+}
+
 __global__ void combine_kernel(int64_t n, const int32_t *__restrict__ rank, const double *__restrict__ phi_s,
                                double half, CombineRow row, double *__restrict__ y) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1864,6 +1881,13 @@ void targets_to_float(Pair &Pr, const Targets &G, const Tree &Tr, cudaStream_t s
     Pr.x32.alloc(std::max<int64_t>(1, G.n));
     if (!G.n) return;
     targets32_kernel<<<div_up(G.n, 256), 256, 0, s>>>(G.n, G.xs.p, Tr.origin[0], Tr.origin[1], Tr.origin[2], Pr.x32.p);
+    PB_LAUNCH_CHECK();
+}
+
+void launch_combine_pair(int64_t n, const int32_t *rank, const double *phi_s, double half, const CombineRow &row0,
+                         const CombineRow &row1, double *y, cudaStream_t s) {
+    if (!n) return;
+    combine_pair_kernel<<<div_up(2 * n, 256), 256, 0, s>>>(n, rank, phi_s, half, row0, row1, y);
     PB_LAUNCH_CHECK();
 }
 

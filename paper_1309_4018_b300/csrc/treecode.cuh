@@ -51,6 +51,9 @@ void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, 
 void targets_to_float(Pair &Pr, const Targets &G, const Tree &Tr, cudaStream_t s);
 void launch_combine(int64_t n, const int32_t *rank, const double *phi_s, double half, const CombineRow &row, double *y,
                     cudaStream_t s);
+// Rows 0 and 1 of one surface (y: 2 n values, row 0 first), the same sums as two launch_combine calls.
+void launch_combine_pair(int64_t n, const int32_t *rank, const double *phi_s, double half, const CombineRow &row0,
+                         const CombineRow &row1, double *y, cudaStream_t s);
 
 // Arguments of the FP32 radial-form M2P of one pair (Laplace slot 0, Yukawa slot 1).
 struct M2PArgs32 {
