@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import datetime
 import json
 import os
 import re
@@ -81,22 +82,31 @@ def m2p_ops_per_box(P):
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples every 50 ms from before the warm-up; summary() keeps
+    the samples taken between mark_start() and mark_end() (the timed steps)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index=0):
         self.idx = gpu_index
         self.proc = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
         return self
+
+    def mark_start(self):
+        self.t0 = datetime.datetime.now()
+
+    def mark_end(self):
+        self.t1 = datetime.datetime.now()
 
     def __exit__(self, *a):
         self.lines = []
@@ -109,23 +119,43 @@ class ClockSampler:
                 out, _ = self.proc.communicate()
             self.lines = [l for l in out.splitlines() if l.strip()]
 
-    def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+    def _parse(self):
+        out = []
         for l in getattr(self, "lines", []):
             f = [x.strip() for x in l.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
+                clk, cmax = float(f[2]), float(f[3])
             except ValueError:
                 continue
-            for name, v in zip(names, f[5:9]):
+            try:
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
+                ts = None   # an unexpected timestamp format: the sample counts as inside the window
+            out.append((ts, clk, cmax, f[6:10]))
+        return out
+
+    def summary(self):
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        rows = self._parse()
+        window = "timed steps"
+        def inside(r, lo, hi):
+            return r[0] is None or lo is None or (lo <= r[0] <= (hi or r[0]))
+        sel = [r for r in rows if inside(r, self.t0, self.t1)]
+        if not sel and self.t0 is not None:
+            # a timed region shorter than the sampling interval: the last second before it (the warm-up)
+            sel = [r for r in rows if inside(r, self.t0 - datetime.timedelta(seconds=1), self.t1)]
+            window = "warm-up (no sample fell inside the timed steps)"
+        reasons = set()
+        for r in sel:
+            for name, v in zip(names, r[3]):
                 if v.lower() == "active":
                     reasons.add(name)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        sm = [r[1] for r in sel]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": sel[-1][2] if sel else None,
+                "reasons": sorted(reasons), "samples": len(sm), "samples_total": len(rows), "interval_ms": 50,
+                "window": window}
 
 
 # ---------------------------------------------------------------- helpers
@@ -357,15 +387,17 @@ def run_gpu(args):
         prob.setup(precision="mixed", **PARAMS)
         return prob.solve()
 
-    for _ in range(args.warmup):
-        r = step(pb)
-    # timed steps (device time on the library stream, L2 flushed before each)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    results = []
-    launches0 = pbbem.launch_count()
-    _barrier(ws)
-    torch.cuda.synchronize()
+    # the clock sampler runs from before the warm-up; its summary keeps the timed steps' samples
     with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            r = step(pb)
+        # timed steps (device time on the library stream, L2 flushed before each)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        results = []
+        launches0 = pbbem.launch_count()
+        _barrier(ws)
+        torch.cuda.synchronize()
+        clk.mark_start()
         for i in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
@@ -373,6 +405,7 @@ def run_gpu(args):
             results.append(step(pb))
             ev[i][1].record(stream)
         torch.cuda.synchronize()
+        clk.mark_end()
     launches = pbbem.launch_count() - launches0
     _barrier(ws)
     step_ms = [a.elapsed_time(b) for a, b in ev]
