@@ -22,6 +22,7 @@ operator) on the host cores, on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import atexit
 import hashlib
 import datetime
 import json
@@ -82,7 +83,7 @@ def m2p_ops_per_box(P):
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples every 50 ms from before the warm-up; summary() keeps
+    """nvidia-smi samples every 20 ms from the start of the run; summary() keeps
     the samples taken between mark_start() and mark_end() (the timed steps)."""
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -91,12 +92,13 @@ class ClockSampler:
     def __init__(self, gpu_index=0):
         self.idx = gpu_index
         self.proc = None
+        self.lines = []
         self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -109,15 +111,16 @@ class ClockSampler:
         self.t1 = datetime.datetime.now()
 
     def __exit__(self, *a):
-        self.lines = []
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                out, _ = self.proc.communicate(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+        if self.proc is None:
+            return
+        proc, self.proc = self.proc, None
+        proc.terminate()
+        try:
+            out, _ = proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            proc.kill()
+            out, _ = proc.communicate()
+        self.lines = [l for l in out.splitlines() if l.strip()]
 
     def _parse(self):
         out = []
@@ -154,7 +157,7 @@ class ClockSampler:
                     reasons.add(name)
         sm = [r[1] for r in sel]
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": sel[-1][2] if sel else None,
-                "reasons": sorted(reasons), "samples": len(sm), "samples_total": len(rows), "interval_ms": 50,
+                "reasons": sorted(reasons), "samples": len(sm), "samples_total": len(rows), "interval_ms": 20,
                 "window": window}
 
 
@@ -367,6 +370,10 @@ def run_gpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     from paper_1309_4018_b300.build import build
+    # the clock sampler starts first, so that it is sampling well before the
+    # timed steps; its summary keeps the timed steps' samples
+    clk = ClockSampler(local).__enter__()
+    atexit.register(clk.__exit__, None, None, None)   # the sampler ends with the process whatever happens
     build()
     from paper_1309_4018_b300 import pbbem
 
@@ -387,25 +394,24 @@ def run_gpu(args):
         prob.setup(precision="mixed", **PARAMS)
         return prob.solve()
 
-    # the clock sampler runs from before the warm-up; its summary keeps the timed steps' samples
-    with ClockSampler(local) as clk:
-        for _ in range(args.warmup):
-            r = step(pb)
-        # timed steps (device time on the library stream, L2 flushed before each)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        results = []
-        launches0 = pbbem.launch_count()
-        _barrier(ws)
+    for _ in range(args.warmup):
+        r = step(pb)
+    # timed steps (device time on the library stream, L2 flushed before each)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    results = []
+    launches0 = pbbem.launch_count()
+    _barrier(ws)
+    torch.cuda.synchronize()
+    clk.mark_start()
+    for i in range(args.steps):
+        flush.zero_()
         torch.cuda.synchronize()
-        clk.mark_start()
-        for i in range(args.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            ev[i][0].record(stream)
-            results.append(step(pb))
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
-        clk.mark_end()
+        ev[i][0].record(stream)
+        results.append(step(pb))
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk.mark_end()
+    clk.__exit__(None, None, None)
     launches = pbbem.launch_count() - launches0
     _barrier(ws)
     step_ms = [a.elapsed_time(b) for a, b in ev]
