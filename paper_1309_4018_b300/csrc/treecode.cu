@@ -1062,9 +1062,13 @@ struct GatherArgs32 {
     double *VK0, *VK1;                     // outputs of kernel 0 and 1: V at [0, ntg), K at [ntg, 2 ntg)
 };
 
-// Target t on the calling warp.
-template <int NK>
-__device__ __forceinline__ void gather32_target(const GatherArgs32 &g, int64_t ntg, int64_t t, int lane) {
+// Target t on W consecutive lanes of the calling warp (the whole warp, or
+// one half with W = 16, the other half taking the next target); lane is the
+// lane within the group.  valid = false: the group has no target (the last
+// half-warp of an odd count) and only joins the shuffles.
+template <int NK, int W = 32>
+__device__ __forceinline__ void gather32_target(const GatherArgs32 &g, int64_t ntg, int64_t t, int lane,
+                                                bool valid = true) {
     float hi[2 * NK], lo[2 * NK], nh[2 * NK], nl[2 * NK];
 #pragma unroll
     for (int a = 0; a < 2 * NK; ++a) { hi[a] = 0.f; lo[a] = 0.f; nh[a] = 0.f; nl[a] = 0.f; }
@@ -1086,23 +1090,24 @@ __device__ __forceinline__ void gather32_target(const GatherArgs32 &g, int64_t n
     };
     const Rec *pp = reinterpret_cast<const Rec *>(g.p2p_part);
     const Rec *mp = reinterpret_cast<const Rec *>(g.m2p_part);
-    const int64_t pb = g.p2p_ptr[t] + lane, pe = g.p2p_ptr[t + 1];
-    const int64_t mb = g.m2p_part ? g.m2p_ptr[t] + lane : 0, me = g.m2p_part ? g.m2p_ptr[t + 1] : 0;
-    const int64_t nb = g.nr.ptr[t] + lane, ne = g.nr.ptr[t + 1];
-    const int sp = g.nr.use_self && lane < 2 * NK ? g.nr.selfp[t] : 0;
+    const int64_t tt = valid ? t : 0;
+    const int64_t pb = g.p2p_ptr[tt] + lane, pe = valid ? g.p2p_ptr[tt + 1] : 0;
+    const int64_t mb = g.m2p_part ? g.m2p_ptr[tt] + lane : 0, me = g.m2p_part && valid ? g.m2p_ptr[tt + 1] : 0;
+    const int64_t nb = g.nr.ptr[tt] + lane, ne = valid ? g.nr.ptr[tt + 1] : 0;
+    const int sp = g.nr.use_self && lane < 2 * NK ? g.nr.selfp[tt] : 0;
     // first load round
     Rec rp[4], rm[4];
     int jn[2];
     float dv[2][NK], dk[2][NK];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-        if (pb + 32 * u < pe) rp[u] = pp[pb + 32 * u];
+        if (pb + W * u < pe) rp[u] = pp[pb + W * u];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-        if (mb + 32 * u < me) rm[u] = mp[mb + 32 * u];
+        if (mb + W * u < me) rm[u] = mp[mb + W * u];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-        const int64_t e = nb + 32 * u;
+        const int64_t e = nb + W * u;
         jn[u] = e < ne ? g.nr.panel[e] : -1;
 #pragma unroll
         for (int a = 0; a < NK; ++a) {
@@ -1112,7 +1117,7 @@ __device__ __forceinline__ void gather32_target(const GatherArgs32 &g, int64_t n
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-        if (pb + 32 * u < pe) add_rec(rp[u]);
+        if (pb + W * u < pe) add_rec(rp[u]);
     // second load round: the densities of the near panels
     float2 pd[2];
 #pragma unroll
@@ -1123,27 +1128,27 @@ __device__ __forceinline__ void gather32_target(const GatherArgs32 &g, int64_t n
         sd = g.nr.dphi[sp];
     }
     // P2P beyond four entries per lane
-    for (int64_t e = pb + 128; e < pe; e += 128) {
+    for (int64_t e = pb + 4 * W; e < pe; e += 4 * W) {
         Rec r[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (e + 32 * u < pe) r[u] = pp[e + 32 * u];
+            if (e + W * u < pe) r[u] = pp[e + W * u];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (e + 32 * u < pe) add_rec(r[u]);
+            if (e + W * u < pe) add_rec(r[u]);
     }
     // M2P
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-        if (mb + 32 * u < me) add_rec(rm[u]);
-    for (int64_t e = mb + 128; e < me; e += 128) {
+        if (mb + W * u < me) add_rec(rm[u]);
+    for (int64_t e = mb + 4 * W; e < me; e += 4 * W) {
         Rec r[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (e + 32 * u < me) r[u] = mp[e + 32 * u];
+            if (e + W * u < me) r[u] = mp[e + W * u];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (e + 32 * u < me) add_rec(r[u]);
+            if (e + W * u < me) add_rec(r[u]);
     }
     // near-singular corrections
 #pragma unroll
@@ -1155,7 +1160,7 @@ __device__ __forceinline__ void gather32_target(const GatherArgs32 &g, int64_t n
                 two_add(nh[2 * a + 1], nl[2 * a + 1], dk[u][a] * pd[u].x);
             }
         }
-    for (int64_t e = nb + 64; e < ne; e += 32) {
+    for (int64_t e = nb + 2 * W; e < ne; e += W) {
         const int j = g.nr.panel[e];
         const float2 pdj = g.nr.phf[j];
 #pragma unroll
@@ -1167,7 +1172,7 @@ __device__ __forceinline__ void gather32_target(const GatherArgs32 &g, int64_t n
 #pragma unroll
     for (int a = 0; a < 2 * NK; ++a)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = W / 2; o > 0; o >>= 1) {
             const float oh = __shfl_xor_sync(0xffffffffu, hi[a], o), ol = __shfl_xor_sync(0xffffffffu, lo[a], o);
             const float ph = __shfl_xor_sync(0xffffffffu, nh[a], o), pl = __shfl_xor_sync(0xffffffffu, nl[a], o);
             two_add(hi[a], lo[a], oh);
@@ -1181,7 +1186,7 @@ __device__ __forceinline__ void gather32_target(const GatherArgs32 &g, int64_t n
 #pragma unroll
     for (int a = 1; a < 2 * NK; ++a)
         if (lane == a) { vh = hi[a]; vl = lo[a]; wh = nh[a]; wl = nl[a]; }
-    if (lane < 2 * NK) {
+    if (lane < 2 * NK && valid) {
         double out = ((double)vh + (double)vl) * kInv4Pi + ((double)wh + (double)wl);
         const int a = lane;
         if (g.nr.use_self && (a & 1) == 0) out += sv * sd;
@@ -1190,12 +1195,22 @@ __device__ __forceinline__ void gather32_target(const GatherArgs32 &g, int64_t n
     }
 }
 
+// Four targets per warp, eight lanes each: a target's records are few per
+// lane either way (~150 over 32 lanes), and its closing butterfly (four
+// values, each a compensated pair, for far and near) and FP64 epilogue cost
+// the same per warp whatever the width, so eight lanes serve four targets
+// with them (gather 49 -> 32 us against one target per warp; 37 us with 16
+// lanes, 34 with 4).
+constexpr int kGatherLanes = 8;
+
 template <int NK>
 __global__ void __launch_bounds__(128) gather32_kernel(int64_t ntg, GatherArgs32 g) {
+    constexpr int W = kGatherLanes;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t t = (int64_t)blockIdx.x * 4 + warp;
-    if (t >= ntg) return;
-    gather32_target<NK>(g, ntg, t, lane);
+    const int64_t t0 = (32 / W) * ((int64_t)blockIdx.x * 4 + warp);
+    if (t0 >= ntg) return;
+    const int64_t t = t0 + lane / W;
+    gather32_target<NK, W>(g, ntg, t, lane % W, t < ntg);
 }
 
 // ---------------------------------------------------------------- near field and combine
@@ -1565,7 +1580,10 @@ __global__ void __launch_bounds__(128, 6) batch_operator_kernel(const __grid_con
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) continue;
             __threadfence();
-            for (int u = 0; u < e.w; ++u) gather32_target<2>(bp.ga, bp.ntg, (int64_t)e.z + u, lane);
+            for (int u0 = 0; u0 < e.w; u0 += 32 / kGatherLanes) {   // the standalone gather's lane groups
+                const int u = u0 + lane / kGatherLanes;
+                gather32_target<2, kGatherLanes>(bp.ga, bp.ntg, (int64_t)e.z + u, lane % kGatherLanes, u < e.w);
+            }
             continue;
         }
         if (e.y == 0) {
@@ -1845,8 +1863,10 @@ void launch_gather(const Pair &Pr, const Targets &G, bool mixed, bool use_self, 
     const unsigned grid = (unsigned)((ntg + 3) / 4);
     if (mixed) {
         const GatherArgs32 ga = gather_args32(Pr, G, use_self, dphi, phf);
-        if (nk == 1) gather32_kernel<1><<<grid, 128, 0, s>>>(ntg, ga);
-        else gather32_kernel<2><<<grid, 128, 0, s>>>(ntg, ga);
+        constexpr int TPB = 4 * (32 / kGatherLanes);   // targets per block
+        const unsigned g8 = (unsigned)((ntg + TPB - 1) / TPB);
+        if (nk == 1) gather32_kernel<1><<<g8, 128, 0, s>>>(ntg, ga);
+        else gather32_kernel<2><<<g8, 128, 0, s>>>(ntg, ga);
     } else {
         NearArgs nr{};
         nr.ptr = Pr.near_ptr.p;
