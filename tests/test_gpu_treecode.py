@@ -117,3 +117,24 @@ def test_m2p_tensor_pipe_variant():
     e0 = problem(d, precision="mixed", gmres_tol=1e-6, **kw).solve().dG_solv
     e1 = problem(d, precision="mixed", gmres_tol=1e-6, m2p_variant=1, **kw).solve().dG_solv
     assert abs(e1 - e0) <= 1e-6 * abs(e0)
+
+
+@pytest.mark.parametrize("n_atoms", [101, 103])
+def test_mixed_gather_partial_lane_groups(n_atoms):
+    # the FP32 gather takes four targets per warp: with 101 or 103 charges the
+    # reaction potential's last warp holds one or three targets (the other
+    # lane groups only join the shuffles).  Same tree, lists and truncation as
+    # the FP64 treecode: the operator within the FP32 bound of the benchmark
+    # protein's (2e-5), the energy within 1e-5 (FP64 solved to 1e-8, the
+    # FP32 operator to 1e-6, near its rounding floor).
+    from synth.configs import protein_problem
+    d = protein_problem(n_atoms=n_atoms, seed=5 if n_atoms == 101 else 6)
+    assert d["charges"]["q"].size % 4 != 0
+    kw = dict(theta=0.5, P=6, ncrit=300)
+    x = np.random.default_rng(n_atoms).normal(size=2 * d["surfaces"][0]["tris"].shape[0])
+    y64 = problem(d, precision="fp64", **kw).apply(x)
+    y32 = problem(d, precision="mixed", **kw).apply(x)
+    assert rel_l2(y32, y64) <= 2e-5
+    e64 = problem(d, precision="fp64", gmres_tol=1e-8, **kw).solve().dG_solv
+    e32 = problem(d, precision="mixed", gmres_tol=1e-6, **kw).solve().dG_solv
+    assert abs(e32 - e64) <= 1e-5 * abs(e64)
