@@ -85,7 +85,8 @@ typedef struct {
                           Morton-consecutive panels of a surface, whose 2 x 2 panel couplings
                           (self terms exact, the rest by the K-point rule) form a dense block
                           inverted at setup (FP32, applied with ~48-bit sums); 1: every panel's
-                          2 x 2 self block (not in the paper; same solution) [32] */
+                          2 x 2 self block (not in the paper; the same solution to the GMRES
+                          tolerance) [32] */
 } pb_params;
 
 typedef struct {
